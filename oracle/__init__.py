@@ -1,0 +1,305 @@
+"""CPU oracle for BSPAI-GMRES-IR (Khan & Carson, arXiv 2307.03914).
+
+TEST INFRASTRUCTURE ONLY.  A plain, slow, obviously-sequential restatement of
+the paper's algorithms (Alg 2.1 with a fixed pattern, Alg 2.2, Alg 2.3,
+Alg 3.1) in C, wrapped here with ctypes and numpy.  Only the tests, the smoke
+check and the benchmark's CPU-baseline leg import this package; the product
+path never does, and the two share no code.
+
+Parity status of each routine is recorded next to it below ("pinned by").
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bspai_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+
+FMT = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "e4m3": 4, "drop": 5}
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp -ffp-contract=off)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_SRC[:-2] + ".h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+
+
+class _System(C.Structure):
+    _fields_ = [("n", C.c_int),
+                ("arp", C.c_void_p), ("aci", C.c_void_p), ("av", C.c_void_p),
+                ("mrp", C.c_void_p), ("mci", C.c_void_p), ("mstored", C.c_void_p),
+                ("mid", C.c_void_p), ("fmts", C.c_void_p), ("q", C.c_int)]
+
+
+def _declare(L):
+    L.orc_fmt_bits.argtypes = [C.c_int]
+    L.orc_fmt_bits.restype = C.c_int
+    L.orc_unit_roundoff.argtypes = [C.c_int]
+    L.orc_unit_roundoff.restype = C.c_double
+    L.orc_fmt_max.argtypes = [C.c_int]
+    L.orc_fmt_max.restype = C.c_double
+    L.orc_round.argtypes = [C.c_double, C.c_int]
+    L.orc_round.restype = C.c_double
+    L.orc_round_array.argtypes = [_f64p, _f64p, C.c_int64, C.c_int]
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_get_threads.restype = C.c_int
+    L.orc_residual_dd.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.orc_householder_ls.argtypes = [C.c_int, C.c_int, _f64p, _f64p, C.c_double, _f64p,
+                                     C.POINTER(C.c_double)]
+    L.orc_householder_ls.restype = C.c_int
+    L.orc_row_absmax_scale.argtypes = [C.c_int, _i32p, _f64p, _f64p]
+    L.orc_spai.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, C.c_double, C.c_double,
+                           C.c_int, C.c_int, _f64p, _f64p, _i32p, _i32p, _f64p]
+    L.orc_spai.restype = C.c_int
+    L.orc_norm_inf.argtypes = [C.c_int, _i32p, _f64p]
+    L.orc_norm_inf.restype = C.c_double
+    L.orc_bucket_ids.argtypes = [C.c_int, _i32p, _f64p, C.c_double, _i32p, C.c_int, _i8p,
+                                 _i64p, _f64p, C.POINTER(C.c_double)]
+    L.orc_bucket_ids.restype = C.c_int
+    L.orc_storage_pct.argtypes = [_i64p, _i32p, C.c_int, C.c_int]
+    L.orc_storage_pct.restype = C.c_double
+    L.orc_bucket_store.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i8p, _i32p, C.c_int,
+                                   _f64p, _f64p, _f64p]
+    L.orc_bucket_store.restype = C.c_int
+    L.orc_bspmv.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i8p, _i32p, C.c_int, _f64p, _f64p]
+    L.orc_bspmv_literal.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i8p, _i32p, C.c_int,
+                                    _f64p, _f64p]
+    L.orc_spmv_prec.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, _f64p, _f64p]
+    L.orc_gmres.argtypes = [C.POINTER(_System), _f64p, C.c_int, C.c_int, C.c_double, C.c_int,
+                            _f64p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.orc_gmres.restype = C.c_int
+    L.orc_gmres_ir.argtypes = [C.POINTER(_System), _f64p, _f64p, C.c_int, C.c_int, C.c_double,
+                               C.c_int, C.c_int, C.c_double, C.c_int, _f64p, _i32p, _f64p,
+                               _f64p, C.POINTER(C.c_int)]
+    L.orc_gmres_ir.restype = C.c_int
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _fmts(fmts):
+    return np.array([FMT[f] if isinstance(f, str) else int(f) for f in fmts], dtype=np.int32)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+# --------------------------------------------------------------- formats (O1)
+def unit_roundoff(fmt) -> float:
+    """Table 2 unit roundoffs.  Pinned by tests against the paper's printed values."""
+    return lib().orc_unit_roundoff(FMT[fmt])
+
+
+def fmt_bits(fmt) -> int:
+    return lib().orc_fmt_bits(FMT[fmt])
+
+
+def round_to(x, fmt) -> np.ndarray:
+    """RN-even into `fmt` with its own range.  Pinned by exhaustive comparison
+    against library casts (numpy/torch) in tests."""
+    x = _f64(np.atleast_1d(x))
+    y = np.empty_like(x)
+    lib().orc_round_array(x, y, x.size, FMT[fmt])
+    return y
+
+
+# -------------------------------------------------------------- residual (O2)
+def residual_dd(A, x, b) -> np.ndarray:
+    """r = b - A x in double-double, rounded to fp64.  Pinned by exact rational
+    arithmetic (fractions) in tests."""
+    r = np.empty(A.n)
+    lib().orc_residual_dd(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(x), _f64(b), r)
+    return r
+
+
+# ------------------------------------------------------------------ SPAI (O3, O4)
+def householder_ls(Ad: np.ndarray, b: np.ndarray, rank_tol: float = 0.0):
+    """Dense Householder least squares.  Pinned against LAPACK (numpy.linalg.lstsq)."""
+    m, k = Ad.shape
+    x = np.zeros(k)
+    res = C.c_double(0.0)
+    rd = lib().orc_householder_ls(m, k, _f64(np.asfortranarray(Ad).ravel(order="F")), _f64(b),
+                                  rank_tol, x, C.byref(res))
+    return x, res.value, rd
+
+
+def row_absmax_scale(A) -> np.ndarray:
+    d = np.empty(A.n)
+    lib().orc_row_absmax_scale(A.n, _i32(A.row_ptr), _f64(A.val), d)
+    return d
+
+
+def spai(A, P, spai_eps: float, u_f: float = 2.0 ** -24, cols=None) -> dict:
+    """Fixed-pattern SPAI on A^T D, returning M = M'^T D in P's structure.
+    Pinned by LAPACK lstsq, normal equations, M = A^-1 for a full pattern."""
+    c0, c1 = (0, A.n) if cols is None else cols
+    mval = np.zeros(P.nnz)
+    resid = np.zeros(A.n)
+    conv = np.zeros(A.n, dtype=np.int32)
+    rankdef = np.zeros(A.n, dtype=np.int32)
+    kappa = np.zeros(A.n)
+    nbad = lib().orc_spai(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _i32(P.row_ptr),
+                          _i32(P.col), spai_eps, u_f, c0, c1, mval, resid, conv, rankdef, kappa)
+    return dict(mval=mval, resid=resid, conv=conv, rankdef=rankdef, kappa=kappa, nbad=nbad)
+
+
+# ------------------------------------------------------------- bucketing (O5)
+def norm_inf(row_ptr, val) -> float:
+    return lib().orc_norm_inf(len(row_ptr) - 1, _i32(row_ptr), _f64(val))
+
+
+def bucket_ids(row_ptr, val, bucket_eps: float, fmts) -> dict:
+    """eq. (nint) / Alg 2.2.  Pinned by the Table 3 storage figures, hand-worked
+    cases and the Graillat et al. backward-error bound (tests)."""
+    f = _fmts(fmts)
+    q = len(f)
+    nnz = int(row_ptr[-1])
+    ids = np.zeros(nnz, dtype=np.int8)
+    nnz_k = np.zeros(q, dtype=np.int64)
+    thr = np.zeros(q)
+    nrm = C.c_double(0.0)
+    rc = lib().orc_bucket_ids(len(row_ptr) - 1, _i32(row_ptr), _f64(val), bucket_eps, f, q, ids,
+                              nnz_k, thr, C.byref(nrm))
+    if rc != 0:
+        raise ValueError("bucket precisions must have strictly increasing unit roundoff")
+    return dict(ids=ids, nnz_k=nnz_k, thr=thr, norm=nrm.value)
+
+
+def storage_pct(nnz_k, fmts, last_bits: int = 0) -> float:
+    f = _fmts(fmts)
+    return lib().orc_storage_pct(np.ascontiguousarray(nnz_k, dtype=np.int64), f, len(f), last_bits)
+
+
+def bucket_store(row_ptr, col, val, ids, fmts):
+    f = _fmts(fmts)
+    n = len(row_ptr) - 1
+    stored = np.zeros(len(val))
+    bscale = np.zeros(len(f))
+    cscale = np.zeros(n)
+    lib().orc_bucket_store(n, _i32(row_ptr), _i32(col), _f64(val), np.ascontiguousarray(ids, np.int8),
+                           f, len(f), stored, bscale, cscale)
+    return stored, bscale, cscale
+
+
+# ------------------------------------------------------------------ SpMV (O6)
+def bspmv(row_ptr, col, stored, ids, fmts, x) -> np.ndarray:
+    """Alg 2.3, decoupled storage/compute form."""
+    f = _fmts(fmts)
+    n = len(row_ptr) - 1
+    y = np.empty(n)
+    lib().orc_bspmv(n, _i32(row_ptr), _i32(col), _f64(stored), np.ascontiguousarray(ids, np.int8),
+                    f, len(f), _f64(x), y)
+    return y
+
+
+def bspmv_literal(row_ptr, col, val, ids, fmts, x) -> np.ndarray:
+    """Alg 2.3 as printed: each bucket in its own precision and range."""
+    f = _fmts(fmts)
+    n = len(row_ptr) - 1
+    y = np.empty(n)
+    lib().orc_bspmv_literal(n, _i32(row_ptr), _i32(col), _f64(val),
+                            np.ascontiguousarray(ids, np.int8), f, len(f), _f64(x), y)
+    return y
+
+
+def spmv_prec(row_ptr, col, val, fmt, x) -> np.ndarray:
+    n = len(row_ptr) - 1
+    y = np.empty(n)
+    lib().orc_spmv_prec(n, _i32(row_ptr), _i32(col), _f64(val), FMT[fmt], _f64(x), y)
+    return y
+
+
+# ----------------------------------------------------------- GMRES / IR (O7, O8)
+class System:
+    """A together with a bucketed M (structure, stored values, bucket ids)."""
+
+    def __init__(self, A, M_row_ptr, M_col, M_stored, M_ids, fmts):
+        self._keep = [_i32(A.row_ptr), _i32(A.col), _f64(A.val), _i32(M_row_ptr), _i32(M_col),
+                      _f64(M_stored), np.ascontiguousarray(M_ids, np.int8), _fmts(fmts)]
+        k = self._keep
+        self.n = A.n
+        self.s = _System(A.n, k[0].ctypes.data, k[1].ctypes.data, k[2].ctypes.data,
+                         k[3].ctypes.data, k[4].ctypes.data, k[5].ctypes.data, k[6].ctypes.data,
+                         k[7].ctypes.data, len(k[7]))
+
+
+def gmres(system: System, r, ug="fp32", up="fp32", tau=1e-4, kmax=500):
+    d = np.zeros(system.n)
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    lib().orc_gmres(C.byref(system.s), _f64(r), FMT[ug], FMT[up], tau, int(kmax), d,
+                    C.byref(it), C.byref(rr))
+    return d, it.value, rr.value
+
+
+def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, imax=10,
+             u_work=2.0 ** -53, x0=None) -> dict:
+    x = np.zeros(system.n) if x0 is None else _f64(x0).copy()
+    its = np.zeros(imax, dtype=np.int32)
+    nbe = np.zeros(imax)
+    dx = np.zeros(imax)
+    stop = C.c_int(0)
+    steps = lib().orc_gmres_ir(C.byref(system.s), _f64(muf), _f64(b), FMT[ug], FMT[up], tau,
+                               int(kmax), int(imax), u_work, int(x0 is not None), x, its, nbe,
+                               dx, C.byref(stop))
+    nsteps = min(imax, steps + (1 if stop.value == 1 else 0))
+    return dict(x=x, steps=steps, its=its[:max(steps, 0)].tolist(), nbe=nbe[:nsteps].tolist(),
+                dx=dx[:steps].tolist(), stop=stop.value)
+
+
+def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None) -> dict:
+    """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR."""
+    A, P = wl["A"], wl["pattern"]
+    sp = spai(A, P, wl["spai_eps"])
+    muf = round_to(sp["mval"], "fp32")  # M is held in u_f = fp32
+    precs = wl["precs"] if precs is None else precs
+    be = wl["bucket_eps"] if bucket_eps is None else bucket_eps
+    bk = bucket_ids(P.row_ptr, muf, be, precs)
+    stored, _, _ = bucket_store(P.row_ptr, P.col, muf, bk["ids"], precs)
+    S = System(A, P.row_ptr, P.col, stored, bk["ids"], precs)
+    out = gmres_ir(S, muf, wl["b"], wl["u_g"], wl["u_p"], wl["tau"] if tau is None else tau,
+                   kmax, imax)
+    out.update(spai=sp, muf=muf, buckets=bk, stored=stored)
+    return out

@@ -1,0 +1,236 @@
+"""Seeded synthetic inputs for BSPAI-GMRES-IR.
+
+This module produces the matrices, sparsity patterns and right-hand sides
+that both the CUDA path and the CPU oracle consume.  It holds none of the
+method's arithmetic (no SPAI, bucketing, SpMV-in-precision, GMRES or
+refinement); it only builds test problems shaped like the paper's workloads
+(sparse nonsymmetric systems with a nonzero diagonal, Section 4 and Table 1)
+plus the a-priori patterns named in Section 2.2 ("the sparsity pattern of A,
+A^T, or a power of a sparsified A").
+
+Everything is host-side numpy (CSR with int32 row pointers / columns and
+float64 values, columns sorted ascending within each row).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+DEFAULT_SEED = 20230707
+
+
+@dataclass
+class CSR:
+    """Host CSR matrix: ``row_ptr`` (n+1, int32), ``col`` (nnz, int32),
+    ``val`` (nnz, float64 or None for a pure pattern)."""
+
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray | None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+
+        v = self.val if self.val is not None else np.ones(self.nnz)
+        return sp.csr_matrix((v, self.col, self.row_ptr), shape=(self.n, self.n))
+
+    def row_lengths(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+
+def _from_dense_rows(cols: np.ndarray, vals: np.ndarray) -> CSR:
+    """Pack an (n, w) table of columns (-1 = absent, ascending per row) into CSR."""
+    mask = cols >= 0
+    lens = mask.sum(axis=1)
+    row_ptr = np.zeros(cols.shape[0] + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    return CSR(
+        n=cols.shape[0],
+        row_ptr=row_ptr.astype(np.int32),
+        col=cols[mask].astype(np.int32),
+        val=vals[mask].astype(np.float64),
+    )
+
+
+def convdiff2d(nx: int = 32, ny: int | None = None, peclet=(0.5, 0.5)) -> CSR:
+    """2D convection-diffusion on an nx-by-ny interior grid with Dirichlet
+    boundaries, 5-point centred stencil in dimensionless form: centre 4 and
+    neighbours -1 -/+ P per direction (upwind side gets -(1+P)), wind along +x, +y.
+    nx = ny = 32 gives n = 1024, nnz = 5n - 4*32 = 4992."""
+    ny = nx if ny is None else ny
+    px, py = peclet
+    n = nx * ny
+    r = np.arange(n, dtype=np.int64)
+    ix, iy = r % nx, r // nx
+    cols = np.full((n, 5), -1, dtype=np.int64)
+    vals = np.zeros((n, 5))
+    # ascending column order: south, west, centre, east, north
+    cols[:, 0] = np.where(iy > 0, r - nx, -1)
+    vals[:, 0] = -(1.0 + py)
+    cols[:, 1] = np.where(ix > 0, r - 1, -1)
+    vals[:, 1] = -(1.0 + px)
+    cols[:, 2] = r
+    vals[:, 2] = 4.0
+    cols[:, 3] = np.where(ix < nx - 1, r + 1, -1)
+    vals[:, 3] = -(1.0 - px)
+    cols[:, 4] = np.where(iy < ny - 1, r + nx, -1)
+    vals[:, 4] = -(1.0 - py)
+    return _from_dense_rows(cols, vals)
+
+
+def convdiff3d(g: int | tuple = 128, eps=(1.0, 10.0, 100.0), peclet: float = 0.8) -> CSR:
+    """3D anisotropic convection-diffusion, 7-point stencil on a gx*gy*gz interior
+    grid with Dirichlet boundaries.  Per direction d with diffusion eps_d and cell
+    Peclet P: centre += 2 eps_d, lower neighbour -eps_d (1+P), upper -eps_d (1-P).
+    g = 128 gives n = 2,097,152 and nnz = 7n - 6*128^2 = 14,581,760."""
+    gx, gy, gz = (g, g, g) if np.isscalar(g) else g
+    n = gx * gy * gz
+    r = np.arange(n, dtype=np.int64)
+    ix = r % gx
+    iy = (r // gx) % gy
+    iz = r // (gx * gy)
+    ex, ey, ez = eps
+    p = peclet
+    cols = np.full((n, 7), -1, dtype=np.int64)
+    vals = np.zeros((n, 7))
+    sxy = gx * gy
+    cols[:, 0] = np.where(iz > 0, r - sxy, -1)
+    vals[:, 0] = -ez * (1 + p)
+    cols[:, 1] = np.where(iy > 0, r - gx, -1)
+    vals[:, 1] = -ey * (1 + p)
+    cols[:, 2] = np.where(ix > 0, r - 1, -1)
+    vals[:, 2] = -ex * (1 + p)
+    cols[:, 3] = r
+    vals[:, 3] = 2.0 * (ex + ey + ez)
+    cols[:, 4] = np.where(ix < gx - 1, r + 1, -1)
+    vals[:, 4] = -ex * (1 - p)
+    cols[:, 5] = np.where(iy < gy - 1, r + gx, -1)
+    vals[:, 5] = -ey * (1 - p)
+    cols[:, 6] = np.where(iz < gz - 1, r + sxy, -1)
+    vals[:, 6] = -ez * (1 - p)
+    return _from_dense_rows(cols, vals)
+
+
+def random_sparse(n: int = 65536, k: int = 16, sigma: float = 2.0, delta: float = 1e-3,
+                  seed: int = DEFAULT_SEED) -> CSR:
+    """Random nonsymmetric sparse matrix: per row k distinct off-diagonal columns
+    drawn uniformly, values sign * exp(N(0, sigma)), and a diagonal
+    (1 + delta) * sum_j |a_ij| (strictly diagonally dominant, so nonsingular;
+    delta controls the conditioning)."""
+    rng = np.random.default_rng(seed)
+    k = min(k, n - 1)
+    cols = rng.integers(0, n - 1, size=(n, k), dtype=np.int64)
+    rows = np.arange(n, dtype=np.int64)[:, None]
+    while True:
+        cols.sort(axis=1)
+        dup = np.zeros(n, dtype=bool)
+        dup |= (np.diff(cols, axis=1) == 0).any(axis=1)
+        bad = np.nonzero(dup)[0]
+        if bad.size == 0:
+            break
+        cols[bad] = rng.integers(0, n - 1, size=(bad.size, k), dtype=np.int64)
+    # map [0, n-1) onto the off-diagonal columns of each row (skip the diagonal)
+    cols = np.where(cols >= rows, cols + 1, cols)
+    cols.sort(axis=1)
+    mag = np.exp(rng.normal(0.0, sigma, size=(n, k)))
+    sgn = np.where(rng.random((n, k)) < 0.5, -1.0, 1.0)
+    off = sgn * mag
+    diag = (1.0 + delta) * np.abs(off).sum(axis=1)
+    allc = np.concatenate([cols, rows], axis=1)
+    allv = np.concatenate([off, diag[:, None]], axis=1)
+    order = np.argsort(allc, axis=1, kind="stable")
+    allc = np.take_along_axis(allc, order, axis=1)
+    allv = np.take_along_axis(allv, order, axis=1)
+    return _from_dense_rows(allc, allv)
+
+
+def pattern_of(A: CSR) -> CSR:
+    """The a-priori pattern pattern(A) (values dropped)."""
+    return CSR(A.n, A.row_ptr.copy(), A.col.copy(), None)
+
+
+def pattern_power_topk(A: CSR, keep: int = 24) -> CSR:
+    """Pattern of |A|*|A| thinned to the `keep` largest entries per row,
+    always keeping the diagonal, ties broken by the smaller column index.
+    Row k of the result is the pattern of row k of M."""
+    import scipy.sparse as sp
+
+    S = abs(A.to_scipy())
+    C = (S @ S).tocsr()
+    C.sort_indices()
+    n = A.n
+    rp = C.indptr.astype(np.int64)
+    cc = C.indices.astype(np.int64)
+    vv = C.data.astype(np.float64).copy()
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    vv[cc == rows] = np.inf  # the diagonal is always kept
+    order = np.lexsort((cc, -vv, rows))
+    rank = np.empty_like(order)
+    starts = np.repeat(rp[:-1], np.diff(rp))
+    rank[order] = np.arange(order.size) - starts
+    keepm = rank < keep
+    kr, kc = rows[keepm], cc[keepm]
+    o = np.lexsort((kc, kr))
+    kr, kc = kr[o], kc[o]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, kr + 1, 1)
+    np.cumsum(row_ptr, out=row_ptr)
+    return CSR(n, row_ptr.astype(np.int32), kc.astype(np.int32), None)
+
+
+def rhs(A: CSR, seed: int = DEFAULT_SEED, nrhs: int = 1):
+    """x_true ~ U[-1, 1] (seeded) and b = A x_true in float64."""
+    rng = np.random.default_rng(seed + 1)
+    if nrhs == 1:
+        x = rng.uniform(-1.0, 1.0, size=A.n)
+    else:
+        x = rng.uniform(-1.0, 1.0, size=(nrhs, A.n))
+    As = A.to_scipy()
+    b = (As @ x.T).T if nrhs > 1 else As @ x
+    return x, np.ascontiguousarray(b)
+
+
+# ---------------------------------------------------------------------------
+# Named workloads.  Each returns a dict with the matrix, the SPAI pattern and
+# the solver settings of the workload; `scale` shrinks the grid for fast cases.
+# ---------------------------------------------------------------------------
+
+FP64, FP32, FP16, BF16, E4M3, DROP = "fp64", "fp32", "fp16", "bf16", "e4m3", "drop"
+
+
+def workload(name: str, grid: int | None = None, n: int | None = None, seed: int = DEFAULT_SEED):
+    """Named synthetic workloads.
+
+    * ``convdiff2d``: 2D 5-point convection-diffusion, 32x32, Peclet 0.5,
+      pattern(A), spai_eps 0.3, buckets {fp64, fp32, fp16}.
+    * ``random``: random sparse n = 65,536, 16 off-diagonals per row, log-normal(0, 2),
+      pattern(|A|^2) top-24, buckets {fp64, fp32, fp16, bf16}.
+    * ``convdiff3d``: 3D 7-point anisotropic (1:10:100) convection-diffusion 128^3,
+      Peclet 0.8, pattern(A), buckets {fp64, fp32, fp16, e4m3}.
+    """
+    if name == "convdiff2d":
+        g = 32 if grid is None else grid
+        A = convdiff2d(g, g, (0.5, 0.5))
+        P = pattern_of(A)
+        cfg = dict(spai_eps=0.3, precs=[FP64, FP32, FP16])
+    elif name == "convdiff3d":
+        g = 128 if grid is None else grid
+        A = convdiff3d(g, (1.0, 10.0, 100.0), 0.8)
+        P = pattern_of(A)
+        cfg = dict(spai_eps=0.3, precs=[FP64, FP32, FP16, E4M3])
+    elif name == "random":
+        nn = 65536 if n is None else n
+        A = random_sparse(nn, 16, 2.0, seed=seed)
+        P = pattern_power_topk(A, 24)
+        cfg = dict(spai_eps=0.3, precs=[FP64, FP32, FP16, BF16])
+    else:
+        raise ValueError(f"unknown workload {name!r}")
+    x_true, b = rhs(A, seed)
+    cfg.update(bucket_eps=2.0 ** -37, u_f=FP32, u=FP64, u_r="dd", u_g=FP32, u_p=FP32, tau=1e-4)
+    return dict(name=name, A=A, pattern=P, x_true=x_true, b=b, **cfg)

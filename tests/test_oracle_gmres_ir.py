@@ -1,0 +1,133 @@
+"""Pins for the oracle's left-preconditioned MGS-GMRES and the refinement
+driver (Alg 3.1), against dense linear algebra and exact arithmetic."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2307_03914_gb300 import workloads as W
+
+
+def _csr(Ad):
+    S = sp.csr_matrix(Ad)
+    S.sort_indices()
+    return W.CSR(Ad.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32),
+                 S.data.astype(float))
+
+
+def _system(orc, A, Mdense, fmts=("fp64",)):
+    Mc = _csr(Mdense)
+    ids = np.zeros(Mc.nnz, np.int8)
+    return orc.System(A, Mc.row_ptr, Mc.col, Mc.val, ids, list(fmts))
+
+
+def test_exact_inverse_preconditioner_converges_in_one_iteration(orc):
+    A = W.convdiff2d(6)
+    Ainv = np.linalg.inv(A.to_scipy().toarray())
+    S = _system(orc, A, Ainv)
+    r = np.random.default_rng(1).uniform(-1, 1, A.n)
+    d, its, rel = orc.gmres(S, r, ug="fp64", up="fp64", tau=1e-10, kmax=A.n)
+    assert its == 1
+    assert np.allclose(d, Ainv @ r, rtol=1e-12, atol=1e-14)
+
+
+def test_identity_preconditioner_full_krylov_equals_dense_solve(orc):
+    A = W.random_sparse(40, 5, sigma=1.0, delta=0.3, seed=4)
+    Ad = A.to_scipy().toarray()
+    S = _system(orc, A, np.eye(A.n))
+    r = np.random.default_rng(2).uniform(-1, 1, A.n)
+    d, its, rel = orc.gmres(S, r, ug="fp64", up="fp64", tau=0.0, kmax=A.n)
+    ref = np.linalg.solve(Ad, r)
+    assert np.linalg.norm(d - ref) <= 1e-10 * np.linalg.cond(Ad) * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_gmres_iterate_minimises_residual_over_krylov_space(orc, k):
+    """GMRES(k) returns argmin ||s - MA d|| over K_k(MA, s) (Saad, Prop. 6.x);
+    checked against a least-squares solve on an explicit Krylov basis."""
+    A = W.convdiff2d(5)
+    Ad = A.to_scipy().toarray()
+    rng = np.random.default_rng(k)
+    M = np.diag(1.0 / np.diag(Ad)) + 0.01 * rng.normal(size=Ad.shape) * (np.abs(Ad) > 0)
+    S = _system(orc, A, M)
+    r = rng.uniform(-1, 1, A.n)
+    d, its, _ = orc.gmres(S, r, ug="fp64", up="fp64", tau=0.0, kmax=k)
+    assert its == k
+    T = M @ Ad
+    s = M @ r
+    K = np.empty((A.n, k))
+    v = s / np.linalg.norm(s)
+    for j in range(k):
+        K[:, j] = v
+        v = T @ v
+        v /= np.linalg.norm(v)
+    Q, _ = np.linalg.qr(K)
+    c, *_ = np.linalg.lstsq(T @ Q, s, rcond=None)
+    ref = Q @ c
+    assert np.linalg.norm(d - ref) <= 1e-8 * np.linalg.norm(ref)
+    # and the reported residual estimate equals the true preconditioned residual
+    d2, _, rel = orc.gmres(S, r, ug="fp64", up="fp64", tau=0.0, kmax=k)
+    assert abs(rel - np.linalg.norm(s - T @ d2) / np.linalg.norm(s)) <= 1e-10
+
+
+def test_fp32_gmres_tracks_fp64(orc):
+    """u_g = u_p = fp32 vs fp64: the corrections agree to about kappa * u_g."""
+    wl = W.workload("convdiff2d", grid=10)
+    A = wl["A"]
+    sp_ = orc.spai(A, wl["pattern"], 0.3)
+    muf = orc.round_to(sp_["mval"], "fp32")
+    bk = orc.bucket_ids(wl["pattern"].row_ptr, muf, 2.0 ** -53, ["fp64"])
+    S = orc.System(A, wl["pattern"].row_ptr, wl["pattern"].col, muf, bk["ids"], ["fp64"])
+    r = wl["b"]
+    d64, it64, _ = orc.gmres(S, r, "fp64", "fp64", 1e-6, 200)
+    d32, it32, _ = orc.gmres(S, r, "fp32", "fp32", 1e-6, 200)
+    kap = np.linalg.cond(A.to_scipy().toarray(), np.inf)
+    assert np.abs(d32 - d64).max() <= 50 * kap * 2.0 ** -24 * np.abs(d64).max()
+    assert abs(it32 - it64) <= 3
+
+
+def _exact_solve(Ad, b):
+    n = len(b)
+    M = [[Fraction(Ad[i, j]) for j in range(n)] + [Fraction(b[i])] for i in range(n)]
+    for c in range(n):
+        piv = max(range(c, n), key=lambda i: abs(M[i][c]))
+        M[c], M[piv] = M[piv], M[c]
+        for i in range(c + 1, n):
+            f = M[i][c] / M[c][c]
+            for j in range(c, n + 1):
+                M[i][j] -= f * M[c][j]
+    x = [Fraction(0)] * n
+    for i in range(n - 1, -1, -1):
+        x[i] = (M[i][n] - sum(M[i][j] * x[j] for j in range(i + 1, n))) / M[i][i]
+    return x
+
+
+def test_ir_reaches_working_precision_on_tiny_system(orc):
+    """kappa_inf(A) well below u^(-1/3) u_f^(-2/3): forward error reaches the
+    level of u against the exact rational solution (Section 1, Alg 3.1)."""
+    wl = W.workload("convdiff2d", grid=4)
+    A = wl["A"]
+    Ad = A.to_scipy().toarray()
+    kap = np.linalg.cond(Ad, np.inf)
+    assert kap <= (2.0 ** -53) ** (-1 / 3) * (2.0 ** -24) ** (-2 / 3)
+    out = orc.solve(wl)
+    xe = _exact_solve(Ad, wl["b"])
+    xr = np.array([float(v) for v in xe])
+    fe = np.abs(out["x"] - xr).max() / np.abs(xr).max()
+    condx = np.abs(np.linalg.inv(Ad)) @ np.abs(Ad) @ np.abs(xr)
+    assert fe <= 4 * condx.max() / np.abs(xr).max() * 2.0 ** -53
+    assert out["nbe"][-1] <= 2.0 ** -53 or out["stop"] in (2, 3)
+
+
+@pytest.mark.parametrize("name,grid", [("convdiff2d", 32), ("convdiff3d", 8)])
+def test_ir_solves_workloads_to_forward_error_1e10(orc, name, grid):
+    wl = W.workload(name, grid=grid)
+    out = orc.solve(wl)
+    xt = wl["x_true"]
+    fe = np.abs(out["x"] - xt).max() / np.abs(xt).max()
+    assert fe <= 1e-10
+    assert out["steps"] >= 2
+    # bucketing with q = 1 is plain SPAI-GMRES-IR: same iterates as the unbucketed M
+    out1 = orc.solve(wl, precs=["fp64"])
+    assert np.abs(out1["x"] - xt).max() / np.abs(xt).max() <= 1e-10
