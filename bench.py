@@ -1,0 +1,417 @@
+"""Benchmark of the BSPAI-GMRES-IR hot path on GB300.
+
+One step = one pass of the whole path on one system: fixed-pattern SPAI build
+(Alg 2.1), bucketing (Alg 2.2), and GMRES-IR (Alg 3.1) with the bucketed M
+(Alg 2.3) -- i.e. one complete solve.  Default workload: 3D 7-point anisotropic
+(1:10:100) convection-diffusion on a 128^3 grid (n = 2,097,152), buckets
+{fp64, fp32, fp16, e4m3} with eps = 2^-10, u_f = u_g = u_p = fp32, u = fp64,
+u_r = double-double.  Inputs (A: 175 MB of CSR) exceed the 129 MB L2.
+
+Prints one JSON line (rank 0).  Metric: GMRES-IR solves/s at forward error
+<= 1e-10 (only solves that reach it count).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank solves its own replica of the system
+(independent problems, no data-path collective): weak scaling.
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES-IR solves/s at fwd err<=1e-10; bucketed M·v GB/s vs GB300 HBM peak"
+UNIT = "solves/s"
+FE_TARGET = 1e-10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="convdiff3d")
+    p.add_argument("--grid", type=int, default=128)
+    p.add_argument("--bucket-eps", type=float, default=2.0 ** -10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-comparator", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.1)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing (CPU baseline)
+def oracle_sample(wl, bucket_eps, its_profile, spai_cols=None, ks=(1, 2, 4)):
+    """Times the oracle's phases on the full workload and scales them to one
+    complete solve: SPAI on `spai_cols` columns (scaled by n / spai_cols),
+    bucketing, x0 = M b and one residual in full, and GMRES runs of ks steps
+    on the real first-step system, fitted to T(k) = c0 + c1 k + c2 k(k+1)/2
+    (c2: one modified Gram-Schmidt pass over a basis vector) and evaluated at
+    the per-step iteration counts `its_profile`."""
+    import oracle as O
+
+    A, P = wl["A"], wl["pattern"]
+    n = A.n
+    t = {}
+    cols = n if spai_cols is None else min(n, spai_cols)
+    t0 = time.perf_counter()
+    sp = O.spai(A, P, wl["spai_eps"], cols=(0, cols))
+    t["spai"] = (time.perf_counter() - t0) * n / cols
+    if cols < n:
+        # the remaining columns' values do not change the oracle's cost; reuse the sampled
+        # rows' values by pattern position so the later phases run on a full M
+        mval = sp["mval"].copy()
+        done = P.row_ptr[cols]
+        reps = int(np.ceil((P.nnz - done) / max(done, 1)))
+        mval[done:] = np.tile(sp["mval"][:done], reps)[:P.nnz - done]
+    else:
+        mval = sp["mval"]
+    muf = O.round_to(mval, "fp32")
+    t0 = time.perf_counter()
+    bk = O.bucket_ids(P.row_ptr, muf, bucket_eps, wl["precs"])
+    stored, _, _ = O.bucket_store(P.row_ptr, P.col, muf, bk["ids"], wl["precs"])
+    t["bucket"] = time.perf_counter() - t0
+    S = O.System(A, P.row_ptr, P.col, stored, bk["ids"], wl["precs"])
+    t0 = time.perf_counter()
+    x0 = O.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"])
+    t["x0"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = O.residual_dd(A, x0, wl["b"])
+    t["residual"] = time.perf_counter() - t0
+    tk = []
+    for k in ks:
+        t0 = time.perf_counter()
+        O.gmres(S, r, wl["u_g"], wl["u_p"], 0.0, k)
+        tk.append(time.perf_counter() - t0)
+    X = np.array([[1.0, k, k * (k + 1) / 2] for k in ks])
+    c0, c1, c2 = np.linalg.lstsq(X, np.array(tk), rcond=None)[0]
+    c0, c1, c2 = max(c0, 0.0), max(c1, 0.0), max(c2, 0.0)
+    gm = sum(c0 + c1 * k + c2 * k * (k + 1) / 2 for k in its_profile)
+    steps = len(its_profile)
+    total = t["spai"] + t["bucket"] + t["x0"] + (steps + 1) * t["residual"] + gm
+    measured = sum(tk) + t["bucket"] + t["x0"] + t["residual"] + t["spai"] * cols / n
+    return dict(seconds_per_solve=total, phases=t, fit=[c0, c1, c2], measured_s=measured,
+                sample=(f"oracle phases on the full n={n} workload: SPAI on {cols} of {n} columns "
+                        f"(scaled), full bucketing, x0 and residual, GMRES runs of {list(ks)} steps fitted to "
+                        f"c0+c1*k+c2*k(k+1)/2 and evaluated at the oracle's own per-step iteration counts "
+                        f"{list(its_profile)}"), cores=O.get_threads())
+
+
+def load_its_profile(name, grid, fallback):
+    path = os.path.join(ROOT, "oracle", f"iteration_profile_{name}_{grid}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)["its"], "oracle"
+    except Exception:
+        return fallback, "gpu"
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2307_03914_gb300 import workloads as W
+    import oracle as O
+
+    O.build()
+    wl = W.workload(args.workload, grid=args.grid)
+    its, src = load_its_profile(args.workload, args.grid, None)
+    if its is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "no oracle iteration profile for this workload; run oracle/iteration_profile.py"}))
+        return
+    for _ in range(args.warmup):
+        oracle_sample(wl, args.bucket_eps, its, spai_cols=wl["A"].n // 8, ks=(1, 2, 3))
+    secs = []
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(wl, args.bucket_eps, its, spai_cols=wl["A"].n // 8, ks=(1, 2, 3))
+        secs.append(last["seconds_per_solve"])
+    v = 1.0 / float(np.mean(secs))
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(secs)), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{args.workload}_{args.grid}^3", "n": wl["A"].n, "bucket_eps": args.bucket_eps,
+                      "precs": wl["precs"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2307_03914_gb300 import build as _b
+
+    _b.build()
+    from paper_2307_03914_gb300 import bspai as B
+    from paper_2307_03914_gb300 import workloads as W
+
+    wl = W.workload(args.workload, grid=args.grid, seed=W.DEFAULT_SEED + rank)
+    A, P = wl["A"], wl["pattern"]
+    n = A.n
+    precs = wl["precs"]
+    Ad = B.DeviceCSR.from_host(A)
+    Pd = B.DeviceCSR.from_host(P, with_values=False)
+    bd = torch.from_numpy(wl["b"]).cuda()
+    xt = torch.from_numpy(wl["x_true"]).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step(x, eps=args.bucket_eps, pl=precs, ug="fp32", up="fp32", tau=wl["tau"], A_in=Ad, P_in=Pd, b_in=bd):
+        M, _ = B.bspai_build(A_in, P_in, wl["spai_eps"])
+        BM, binfo = B.bspai_bucket(M, eps, pl)
+        info = B.gmres_ir_solve(A_in, b_in, BM, M, x, u_g=ug, u_p=up, tol=tau)
+        M.free()
+        BM.free()
+        return info, binfo
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    xs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        step(xs[0])
+    # ---------------- timed region (device-resident inputs)
+    sampler = ClockSampler(local)
+    barrier()
+    B.profile_enable(True)
+    B.profile_read(reset=True)
+    l0 = B.launch_count()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for k in range(args.steps):
+        infos.append(step(xs[k]))
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = B.launch_count() - l0
+    prof = B.profile_read(reset=True)
+    B.profile_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    fe = [float(((x - xt).abs().max() / xt.abs().max()).item()) for x in xs]
+    ok = sum(1 for f, (inf, _) in zip(fe, infos) if f <= FE_TARGET and inf["status"] == 0)
+    if world > 1:
+        t = torch.tensor([ok], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        ok = int(t.item())
+    value = ok / (ms / 1000.0)
+    info, binfo = infos[-1]
+
+    # ---------------- roofline of the kernels (algorithmic bytes / event time)
+    hbm, peak_src = peaks()
+    bytes_k = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1, "drop": 0}
+    m_bytes32 = sum(c * (bytes_k[p] + 4) for c, p in zip(binfo["nnz_k"], binfo["precs"]) if p != "drop")
+    m_bytes32 += n * 4 + n * 4 + (n * 4 if "e4m3" in binfo["precs"] else 0)
+    m_bytes64r = m_bytes32 + n * 4  # s = M r reads x in fp64
+    iters = [k for inf, _ in infos for k in inf["gmres_iters"]]
+    ir_steps = sum(inf["ir_steps"] for inf, _ in infos)
+    bsp_bytes = sum(iters) * m_bytes32 + ir_steps * m_bytes64r
+    mgs_bytes = sum(sum((j + 1) * n * 4 + n * 4 for j in range(k)) + 2 * n * 4 for k in iters)
+    a_bytes = sum(iters) * (A.nnz * 8 + n * 4 + n * 4)
+    res_bytes = (ir_steps + len(infos)) * (A.nnz * 12 + 3 * n * 8)
+    cls_bytes = {"bspmv": bsp_bytes, "mgs": mgs_bytes, "spmv_A": a_bytes, "residual": res_bytes}
+
+    def roof(cls):
+        t_ms, nl = prof[cls]
+        if t_ms <= 0:
+            return None
+        ach = cls_bytes[cls] / (t_ms / 1000.0) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": cls, "launches": nl, "ms_total": t_ms,
+                "algorithmic_bytes": cls_bytes[cls], "peak_source": peak_src}
+
+    dominant = max(prof, key=lambda c: prof[c][0])
+    roofline = roof(dominant) if dominant in cls_bytes else None
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{args.workload}_{args.grid}^3" if args.workload == "convdiff3d" else args.workload,
+                      "n": n, "nnz_A": A.nnz, "nnz_M": P.nnz, "bucket_eps": args.bucket_eps, "precs": precs,
+                      "u_f": "fp32", "u": "fp64", "u_r": "dd", "u_g": "fp32", "u_p": "fp32", "tau": wl["tau"],
+                      "l2": "inputs larger than L2 (A CSR 175 MB > 129 MB)", "parallelism": f"replicas{world}"},
+           "solve": {"fwd_err": fe, "ok": ok, "gmres_iters": info["gmres_iters"], "ir_steps": info["ir_steps"],
+                     "nbe": info["nbe"], "bucket_nnz": binfo["nnz_k"], "storage_pct": binfo["storage_pct"]},
+           "profile_ms": {c: prof[c][0] / args.steps for c in prof},
+           "roofline": roofline, "roofline_bspmv": roof("bspmv"), "roofline_spmv_A": roof("spmv_A"),
+           "gpu_launches": int(launches), "clocks": clocks}
+
+    # ---------------- comparator: q = 1 {fp64}, u_g = u_p = fp64 (plain SPAI-GMRES-IR)
+    if not args.no_comparator:
+        xc = torch.empty(n, dtype=torch.float64, device="cuda")
+        step(xc, eps=2.0 ** -53, pl=["fp64"], ug="fp64", up="fp64", tau=1e-8)
+        barrier()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cinfo, _ = step(xc, eps=2.0 ** -53, pl=["fp64"], ug="fp64", up="fp64", tau=1e-8)
+        c1.record(stream)
+        barrier()
+        cms = c0.elapsed_time(c1)
+        cfe = float(((xc - xt).abs().max() / xt.abs().max()).item())
+        out["comparator"] = {"what": "q=1 {fp64} SPAI-GMRES-IR, u_g=u_p=fp64, tau=1e-8", "solves_per_s":
+                             (1.0 if cfe <= FE_TARGET else 0.0) / (cms / 1000.0), "ms_per_solve": cms,
+                             "gmres_iters": cinfo["gmres_iters"], "fwd_err": cfe}
+
+    # ---------------- end to end through the API with host buffers
+    if not args.no_e2e:
+        hA = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (A.row_ptr, A.col, A.val)]
+        hP = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (P.row_ptr, P.col)]
+        hb = torch.from_numpy(wl["b"]).pin_memory()
+        hx = torch.empty(n, dtype=torch.float64).pin_memory()
+        dA = [torch.empty_like(t, device="cuda") for t in hA]
+        dP = [torch.empty_like(t, device="cuda") for t in hP]
+        db = torch.empty_like(hb, device="cuda")
+        dx = torch.empty(n, dtype=torch.float64, device="cuda")
+        h2d = sum(t.numel() * t.element_size() for t in hA + hP + [hb])
+        d2h = hx.numel() * hx.element_size()
+
+        def e2e_step():
+            for d, h in zip(dA + dP + [db], hA + hP + [hb]):
+                d.copy_(h, non_blocking=True)
+            inf, _ = step(dx, A_in=B.DeviceCSR(n, *dA), P_in=B.DeviceCSR(n, dP[0], dP[1]), b_in=db)
+            hx.copy_(dx, non_blocking=True)
+            return inf
+
+        e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e_ok = 0
+        for _ in range(args.steps):
+            inf = e2e_step()
+            torch.cuda.synchronize()
+            fe_e = float(np.abs(hx.numpy() - wl["x_true"]).max() / np.abs(wl["x_true"]).max())
+            e_ok += int(fe_e <= FE_TARGET and inf["status"] == 0)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems, e_ok], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
+            tt = torch.tensor([float(e_ok)], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt)
+            ems, e_ok = float(t[0].item()), int(tt.item())
+        out["e2e"] = {"value": e_ok / (ems / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+
+    # ---------------- CPU baseline: the oracle on the host cores (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        its, src = load_its_profile(args.workload, args.grid, info["gmres_iters"])
+        cb = oracle_sample(wl, args.bucket_eps, its, spai_cols=None if n <= 300000 else n // 4)
+        out["cpu_baseline"] = {"value": 1.0 / cb["seconds_per_solve"], "unit": UNIT, "cores": cb["cores"],
+                               "kind": "oracle", "sample": cb["sample"] + f" (iteration counts from: {src})",
+                               "measured_cpu_s": cb["measured_s"]}
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * bspai.h -- C ABI of the GB300 (sm_103a) BSPAI-GMRES-IR library, libbspai.so.
+ *
+ * Method: Khan & Carson, "Mixed Precision Iterative Refinement with Adaptive
+ * Precision Sparse Approximate Inverse Preconditioning" (arXiv 2307.03914):
+ *   - fixed-pattern sparse approximate inverse M (Section 2.2, eq. fronormmin,
+ *     eq. redprob, Alg 2.1 with alpha = 0) built on A^T D with the column
+ *     scaling of Section 4, then M = M'^T D (Alg 3.1, first line);
+ *   - precision buckets of M by magnitude (eq. nint, Alg 2.2);
+ *   - adaptive-precision SpMV (Alg 2.3);
+ *   - left-preconditioned MGS-GMRES inside iterative refinement (Alg 3.1).
+ *
+ * Conventions for every call:
+ *   - Pointers named as device pointers must be CUDA device memory on the
+ *     current device; host pointers are ordinary host memory.  Caller-owned
+ *     buffers stay owned by the caller; handles (bspai_A_h, bspai_M_h,
+ *     bspai_BM_h) are owned by the library and released with bspai_free().
+ *   - CSR inputs have int32 row pointers and int32 column indices sorted
+ *     ascending within each row; nnz < 2^31.
+ *   - All GPU work is enqueued on stream `s` (NULL = legacy default stream).
+ *     Calls that fill an `info` struct synchronise `s` before returning;
+ *     bspai_apply, bspai_apply_uf, bspai_residual and bspai_spmv_up do not.
+ *   - Every call returns a bspai_status_t.  Nothing is thrown across the ABI.
+ *     bspai_last_error() gives a per-thread message for the last failure.
+ *   - Handles are not thread-safe: one handle, one thread at a time.
+ */
+#ifndef BSPAI_H
+#define BSPAI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t (declared here so the header needs no CUDA headers). */
+typedef struct CUstream_st* bspai_stream_t;
+
+typedef enum {
+    BSPAI_OK = 0,
+    BSPAI_ERR_INVALID = 1,      /* bad argument (null pointer, size, unsorted precisions ...) */
+    BSPAI_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    BSPAI_ERR_NOMEM = 3,        /* device allocation failed */
+    BSPAI_NOT_CONVERGED = 4,    /* refinement hit i_max without meeting a stopping test */
+    BSPAI_RANK_DEFICIENT = 5,   /* some SPAI least-squares block was rank deficient */
+    BSPAI_NONFINITE = 6,        /* NaN or Inf in a residual or norm */
+    BSPAI_TIMEOUT = 7,          /* a device-side grid barrier gave up after its time limit */
+    BSPAI_ERR_UNSUPPORTED = 8   /* precision combination not built */
+} bspai_status_t;
+
+/* Number formats: Table 2 (half, single, double) plus bf16, OCP e4m3, "drop"
+ * (u = 1, the element is removed, Section 4) and double-double for u_r. */
+typedef enum {
+    BSPAI_FP64 = 0,
+    BSPAI_FP32 = 1,
+    BSPAI_FP16 = 2,
+    BSPAI_BF16 = 3,
+    BSPAI_E4M3 = 4,
+    BSPAI_DROP = 5,
+    BSPAI_DD = 6
+} bspai_prec_t;
+
+/* A CSR matrix in device memory (caller-owned).  val may be NULL for a pattern. */
+typedef struct {
+    int32_t n;              /* order */
+    int32_t nnz;            /* row_ptr[n] */
+    const int32_t* row_ptr; /* device, n + 1 */
+    const int32_t* col;     /* device, nnz, ascending within each row */
+    const double* val;      /* device, nnz (fp64), or NULL */
+} bspai_csr_t;
+
+typedef struct bspai_matrix* bspai_A_h;   /* A prepared for the GPU kernels */
+typedef struct bspai_spai* bspai_M_h;     /* M = SPAI(A) held in u_f = fp32 */
+typedef struct bspai_bucketed* bspai_BM_h;/* M split into precision buckets */
+
+typedef struct {
+    int32_t n;
+    int32_t max_cols;          /* largest |J_k| */
+    int32_t max_rows;          /* largest |I_k| (shadow size) */
+    int32_t n_converged;       /* columns with ||sbar_k||_2 <= spai_eps (Alg 2.1 test) */
+    int32_t n_rank_deficient;  /* columns whose block failed |R_jj| > |I| u_f ||Abar||_F */
+    int64_t nnz;               /* nnz(M) = nnz(pattern) */
+    double max_resid;          /* max_k ||sbar_k||_2 */
+} bspai_build_info_t;
+
+typedef struct {
+    int32_t q;                 /* number of buckets */
+    int32_t precs[8];          /* bspai_prec_t of each bucket, increasing unit roundoff */
+    int64_t nnz_k[8];          /* nonzeros per bucket (dropped ones counted in their bucket) */
+    int64_t slots_k[8];        /* stored slots per bucket including padding */
+    double thresholds[8];      /* thresholds[k] = eps ||M||_inf / u_k, k >= 1; [0] = +inf */
+    double norm_inf;           /* ||M||_inf */
+    double storage_pct;        /* sum_k nnz_k bits_k / (nnz bits_1), drop costed at 0 bits */
+    double storage_pct_last8;  /* same with a dropped last bucket costed at 8 bits */
+    int64_t bytes;             /* device bytes of the bucketed M (values, indices, scales) */
+} bspai_bucket_info_t;
+
+typedef struct {
+    double tau;            /* GMRES tolerance: stop when |g_{j+1}| <= tau ||M r||_2 (Alg 3.1) */
+    int32_t kmax;          /* max GMRES iterations per refinement step (no restart); 0 = min(n, 1000) */
+    int32_t i_max;         /* max refinement steps; 0 = 10 */
+    int32_t x0_given;      /* 1: x holds the initial iterate; 0: x0 = M b in u_f (Alg 3.1) */
+    double u_stop;         /* stop when nbe <= u_stop or ||d||_inf <= u_stop ||x||_inf; 0 = 2^-53 */
+    double stagnation;     /* stop when ||d_i|| > stagnation ||d_{i-1}||; 0 = 0.9 */
+    double barrier_timeout_s; /* device grid-barrier time limit in seconds; 0 = 2.0 */
+} bspai_opts_t;
+
+typedef struct {
+    int32_t status;            /* bspai_status_t of the solve */
+    int32_t ir_steps;          /* refinement steps that ran GMRES */
+    int32_t stop_reason;       /* 1 nbe <= u, 2 ||d|| <= u ||x||, 3 stagnation, 0 i_max */
+    int32_t total_iters;       /* sum of GMRES iterations */
+    int32_t gmres_iters[32];   /* GMRES iterations of each refinement step */
+    double nbe[33];            /* ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) at each residual */
+    double dx[32];             /* ||d_i||_inf / ||x_{i+1}||_inf */
+    double relres[32];         /* |g_k| / ||M r||_2 at the end of each GMRES */
+} bspai_solve_info_t;
+
+/* Kernel-class timing, recorded with CUDA events on the launching stream. */
+enum {
+    BSPAI_K_SPAI = 0, BSPAI_K_BUCKET = 1, BSPAI_K_SPMV_A = 2, BSPAI_K_BSPMV = 3,
+    BSPAI_K_MGS = 4, BSPAI_K_RESIDUAL = 5, BSPAI_K_UPDATE = 6, BSPAI_K_OTHER = 7,
+    BSPAI_K_COUNT = 8
+};
+typedef struct {
+    double ms[BSPAI_K_COUNT];        /* summed event time per class */
+    int64_t launches[BSPAI_K_COUNT]; /* kernel launches per class */
+} bspai_profile_t;
+
+/* ------------------------------------------------------------------ basics */
+const char* bspai_last_error(void);       /* per-thread message; never NULL */
+int bspai_version(void);                  /* 10000 * major + 100 * minor + patch */
+/* Kernel launches this library has issued since it was loaded (all threads). */
+long long bspai_launch_count(void);
+void bspai_opts_default(bspai_opts_t* opts);
+/* Releases any handle returned by this library (NULL is a no-op).  Enqueues
+ * the frees on the stream the handle was created on. */
+int bspai_free(void* handle);
+/* Enables (1) or disables (0) per-kernel-class event timing for later calls. */
+int bspai_profile_enable(int on);
+/* Synchronises the recorded events and returns the totals; reset = 1 clears them. */
+int bspai_profile_read(bspai_profile_t* out, int reset);
+
+/* ------------------------------------------------------------------ A */
+/* Prepares A (n x n, values required) for the kernels: sliced-ELL copies of
+ * its structure with fp64 values (residual, u_r) and fp32 values (u_p).
+ * A's buffers may be freed after the call's stream work completes. */
+int bspai_matrix_create(const bspai_csr_t* A, bspai_stream_t s, bspai_A_h* out);
+
+/* r = b - A x computed in double-double (u_r; the paper uses quad), stored in
+ * fp64 (Alg 3.1, residual line).  x, b, r: device fp64 vectors of length n. */
+int bspai_residual(bspai_A_h A, const double* x, const double* b, double* r, bspai_stream_t s);
+
+/* w = A v with A rounded to u_p = fp32 and fp32 products and sums (Alg 3.1,
+ * GMRES line: "A computed in precision u_p").  v, w: device fp32, length n. */
+int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s);
+
+/* ------------------------------------------------------------------ SPAI */
+/* Fixed-pattern SPAI (Alg 2.1 with alpha = 0; eq. redprob) run on B = A^T D,
+ * D = diag(1 / max_i |a_ji|) (Section 4), in u_f = fp32, giving the left
+ * preconditioner M = M'^T D (Alg 3.1, first line).  Row k of M has the
+ * structure of row k of `pattern` (pattern->val is ignored).  For each k the
+ * shadow I_k, the block Abar = B(I_k, J_k), its Householder QR, mbar =
+ * R^-1 Q^T ebar and ||sbar_k||_2 are computed on the GPU, one warp per column.
+ * Only u_f = BSPAI_FP32 is built.  Returns BSPAI_RANK_DEFICIENT (with M still
+ * created, those columns zero) if any block failed the rank test. */
+int bspai_build(const bspai_csr_t* A, const bspai_csr_t* pattern, double spai_eps,
+                bspai_prec_t u_f, bspai_stream_t s, bspai_M_h* M_out, bspai_build_info_t* info);
+
+/* Copies M out in CSR order (structure of the pattern): row_ptr (n+1), col
+ * (nnz), val (nnz, fp32, the u_f values) and resid (n, ||sbar_k||_2 per
+ * column of M' = row of M).  All device buffers; any may be NULL. */
+int bspai_M_export(bspai_M_h M, int32_t* row_ptr, int32_t* col, float* val, float* resid,
+                   bspai_stream_t s);
+
+/* y = M x with the unbucketed M in u_f = fp32 (x rounded to fp32, fp32
+ * products and sums), y stored in fp64: x0 = M b of Alg 3.1.  Device vectors. */
+int bspai_apply_uf(bspai_M_h M, const double* x, double* y, bspai_stream_t s);
+
+/* ------------------------------------------------------------------ buckets */
+/* Splits M into q <= 8 precision buckets (eq. nint, Alg 2.2) with
+ * ||M|| = ||M||_inf computed in fp64 (row sums in ascending column order).
+ * precs[0..q-1] must have strictly increasing unit roundoff (fp64 < fp32 <
+ * fp16 < bf16 < e4m3 < drop).  Storage: fp64/fp32/bf16 buckets hold RN(m);
+ * an fp16 bucket holds RN16(m / s) with one power-of-two scale s per bucket;
+ * an e4m3 bucket holds RNe4m3(m / s_j) with a power-of-two fp32 scale per
+ * column (s = least 2^e with max|m| <= fmt_max 2^e); drop removes entries.
+ * At most one e4m3 bucket.  BM keeps its own copy of everything it needs, so
+ * M may be freed afterwards. */
+int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q,
+                 bspai_stream_t s, bspai_BM_h* out, bspai_bucket_info_t* info);
+
+/* Per nonzero of M in CSR order: bucket id (0-based) and the stored value the
+ * product uses (scale applied), as fp64.  Device buffers of length nnz(M);
+ * either may be NULL. */
+int bspai_bucket_export(bspai_BM_h BM, int8_t* ids, double* stored, bspai_stream_t s);
+
+/* y = M x by the adaptive-precision SpMV (Alg 2.3): per row and bucket a
+ * partial sum accumulated in ascending column order, in fp64 for an fp64
+ * bucket and in fp32 (x rounded to fp32) for narrower buckets (storage in
+ * u_k, computation decoupled as in Section 5); partial sums added in fp64 in
+ * bucket order; the result rounded to y_prec.  x_prec, y_prec in {FP64, FP32}. */
+int bspai_apply(bspai_BM_h BM, const void* x, bspai_prec_t x_prec, void* y, bspai_prec_t y_prec,
+                bspai_stream_t s);
+
+/* ------------------------------------------------------------------ solves */
+/* One left-preconditioned MGS-GMRES solve of (M A) d = M r (Alg 3.1, GMRES
+ * line): vectors in u_g (FP32 or FP64), A v in u_p (FP32 or FP64), M v
+ * bucketed (Alg 2.3), Givens rotations and the triangular solve in fp64;
+ * x0 = 0, no restart, stop when |g_{j+1}| <= opts->tau ||M r||_2 or at kmax.
+ * r and d are device fp64 vectors.  info->gmres_iters[0], relres[0] are set. */
+int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
+                const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
+
+/* BSPAI-GMRES-IR (Alg 3.1 after the SPAI build): x0 = M b in u_f (unless
+ * opts->x0_given), then up to i_max steps of r = b - A x in u_r, GMRES on
+ * (M A) d = M r with tolerance tol, x = x + d in u.  Supported: u = FP64,
+ * u_r in {DD, FP64}, u_g and u_p in {FP32, FP64}.  A: caller CSR (device);
+ * b: device fp64; x: device fp64, in/out; M: the unbucketed M for x0 (may be
+ * NULL when x0_given).  Stopping: nbe <= u_stop, ||d||_inf <= u_stop
+ * ||x||_inf, or stagnation.  Returns BSPAI_OK on one of those, else
+ * BSPAI_NOT_CONVERGED / BSPAI_NONFINITE / BSPAI_TIMEOUT. */
+int gmres_ir_solve(const bspai_csr_t* A, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,
+                   bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, bspai_prec_t u_p,
+                   double tol, const bspai_opts_t* opts, double* x, bspai_stream_t s,
+                   bspai_solve_info_t* info);
+
+/* Same as gmres_ir_solve with A already prepared by bspai_matrix_create. */
+int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,
+                     bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, bspai_prec_t u_p,
+                     double tol, const bspai_opts_t* opts, double* x, bspai_stream_t s,
+                     bspai_solve_info_t* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSPAI_H */

@@ -1,0 +1,308 @@
+"""ctypes binding of libbspai.so (C ABI declared in include/bspai.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of the library.  Vectors and matrices are torch CUDA tensors (PyTorch provides
+device memory and streams); calls are enqueued on torch's current stream.
+There is no CPU fallback: importing this module fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libbspai.so is not built ({LIB_PATH}); run paper_2307_03914_gb300.build.build()")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, NOT_CONVERGED, RANK_DEFICIENT, NONFINITE, TIMEOUT, ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = ["OK", "ERR_INVALID", "ERR_CUDA", "ERR_NOMEM", "NOT_CONVERGED", "RANK_DEFICIENT",
+                "NONFINITE", "TIMEOUT", "ERR_UNSUPPORTED"]
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "e4m3": 4, "drop": 5, "dd": 6}
+PREC_NAME = {v: k for k, v in PREC.items()}
+K_CLASSES = ["spai", "bucket", "spmv_A", "bspmv", "mgs", "residual", "update", "other"]
+
+
+class BspaiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class CsrT(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class BuildInfo(C.Structure):
+    _fields_ = [("n", C.c_int32), ("max_cols", C.c_int32), ("max_rows", C.c_int32),
+                ("n_converged", C.c_int32), ("n_rank_deficient", C.c_int32), ("nnz", C.c_int64),
+                ("max_resid", C.c_double)]
+
+
+class BucketInfo(C.Structure):
+    _fields_ = [("q", C.c_int32), ("precs", C.c_int32 * 8), ("nnz_k", C.c_int64 * 8),
+                ("slots_k", C.c_int64 * 8), ("thresholds", C.c_double * 8), ("norm_inf", C.c_double),
+                ("storage_pct", C.c_double), ("storage_pct_last8", C.c_double), ("bytes", C.c_int64)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tau", C.c_double), ("kmax", C.c_int32), ("i_max", C.c_int32), ("x0_given", C.c_int32),
+                ("u_stop", C.c_double), ("stagnation", C.c_double), ("barrier_timeout_s", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("ir_steps", C.c_int32), ("stop_reason", C.c_int32),
+                ("total_iters", C.c_int32), ("gmres_iters", C.c_int32 * 32), ("nbe", C.c_double * 33),
+                ("dx", C.c_double * 32), ("relres", C.c_double * 32)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8)]
+
+
+_vp = C.c_void_p
+_i = C.c_int
+_d = C.c_double
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("bspai_last_error", C.c_char_p, [])
+_sig("bspai_version", _i, [])
+_sig("bspai_launch_count", C.c_longlong, [])
+_sig("bspai_opts_default", None, [C.POINTER(Opts)])
+_sig("bspai_free", _i, [_vp])
+_sig("bspai_profile_enable", _i, [_i])
+_sig("bspai_profile_read", _i, [C.POINTER(Profile), _i])
+_sig("bspai_matrix_create", _i, [C.POINTER(CsrT), _vp, C.POINTER(_vp)])
+_sig("bspai_residual", _i, [_vp, _vp, _vp, _vp, _vp])
+_sig("bspai_spmv_up", _i, [_vp, _vp, _vp, _vp])
+_sig("bspai_build", _i, [C.POINTER(CsrT), C.POINTER(CsrT), _d, _i, _vp, C.POINTER(_vp), C.POINTER(BuildInfo)])
+_sig("bspai_M_export", _i, [_vp, _vp, _vp, _vp, _vp, _vp])
+_sig("bspai_apply_uf", _i, [_vp, _vp, _vp, _vp])
+_sig("bspai_bucket", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINTER(_vp), C.POINTER(BucketInfo)])
+_sig("bspai_bucket_export", _i, [_vp, _vp, _vp, _vp])
+_sig("bspai_apply", _i, [_vp, _vp, _i, _vp, _i, _vp])
+_sig("bspai_gmres", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
+_sig("gmres_ir_solve", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
+                            C.POINTER(SolveInfo)])
+_sig("gmres_ir_solve_h", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
+                              C.POINTER(SolveInfo)])
+
+
+def last_error() -> str:
+    return _lib.bspai_last_error().decode()
+
+
+def _check(st: int, allow=(OK,)) -> int:
+    if st not in allow:
+        raise BspaiError(st, last_error())
+    return st
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def version() -> int:
+    return _lib.bspai_version()
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library since it was loaded."""
+    return int(_lib.bspai_launch_count())
+
+
+# --------------------------------------------------------------- containers
+class DeviceCSR:
+    """CSR in device memory: row_ptr/col int32, val float64 (or None)."""
+
+    def __init__(self, n, row_ptr, col, val=None):
+        self.n = int(n)
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+
+    @classmethod
+    def from_host(cls, A, device="cuda", with_values=True):
+        rp = torch.as_tensor(np.ascontiguousarray(A.row_ptr, np.int32)).to(device)
+        ci = torch.as_tensor(np.ascontiguousarray(A.col, np.int32)).to(device)
+        v = None
+        if with_values and A.val is not None:
+            v = torch.as_tensor(np.ascontiguousarray(A.val, np.float64)).to(device)
+        return cls(A.n, rp, ci, v)
+
+    @property
+    def nnz(self):
+        return int(self.col.numel())
+
+    def c(self) -> CsrT:
+        return CsrT(self.n, self.nnz, self.row_ptr.data_ptr(), self.col.data_ptr(),
+                    self.val.data_ptr() if self.val is not None else None)
+
+
+class _Handle:
+    def __init__(self, ptr, keep=None):
+        self.ptr = ptr
+        self._keep = keep
+
+    def free(self):
+        if self.ptr:
+            _check(_lib.bspai_free(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class AHandle(_Handle):
+    pass
+
+
+class MHandle(_Handle):
+    pass
+
+
+class BMHandle(_Handle):
+    pass
+
+
+def opts(tau=1e-4, kmax=0, i_max=0, x0_given=False, u_stop=0.0, stagnation=0.0, barrier_timeout_s=0.0) -> Opts:
+    return Opts(tau, kmax, i_max, int(x0_given), u_stop, stagnation, barrier_timeout_s)
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.bspai_profile_enable(int(on)))
+
+
+def profile_read(reset: bool = True) -> dict:
+    p = Profile()
+    _check(_lib.bspai_profile_read(C.byref(p), int(reset)))
+    return {K_CLASSES[i]: (p.ms[i], p.launches[i]) for i in range(8)}
+
+
+# ------------------------------------------------------------------ A
+def matrix_create(A: DeviceCSR, stream=None) -> AHandle:
+    h = C.c_void_p()
+    _check(_lib.bspai_matrix_create(C.byref(A.c()), _stream(stream), C.byref(h)))
+    return AHandle(h.value)
+
+
+def residual(Ah: AHandle, x, b, r, stream=None):
+    _check(_lib.bspai_residual(Ah.ptr, _ptr(x), _ptr(b), _ptr(r), _stream(stream)))
+    return r
+
+
+def spmv_up(Ah: AHandle, v, w, stream=None):
+    _check(_lib.bspai_spmv_up(Ah.ptr, _ptr(v), _ptr(w), _stream(stream)))
+    return w
+
+
+# ------------------------------------------------------------------ SPAI
+def bspai_build(A: DeviceCSR, P: DeviceCSR, spai_eps: float, u_f: str = "fp32", stream=None):
+    h = C.c_void_p()
+    info = BuildInfo()
+    st = _lib.bspai_build(C.byref(A.c()), C.byref(P.c()), float(spai_eps), PREC[u_f], _stream(stream),
+                          C.byref(h), C.byref(info))
+    _check(st, (OK, RANK_DEFICIENT))
+    d = {f: getattr(info, f) for f, _ in BuildInfo._fields_}
+    d["status"] = st
+    return MHandle(h.value), d
+
+
+def M_export(M: MHandle, n: int, nnz: int, stream=None):
+    dev = "cuda"
+    rp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(nnz, dtype=torch.int32, device=dev)
+    v = torch.empty(nnz, dtype=torch.float32, device=dev)
+    res = torch.empty(n, dtype=torch.float32, device=dev)
+    _check(_lib.bspai_M_export(M.ptr, _ptr(rp), _ptr(ci), _ptr(v), _ptr(res), _stream(stream)))
+    return rp, ci, v, res
+
+
+def apply_uf(M: MHandle, x, y, stream=None):
+    _check(_lib.bspai_apply_uf(M.ptr, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+# ------------------------------------------------------------------ buckets
+def bspai_bucket(M: MHandle, bucket_eps: float, precs, stream=None):
+    arr = (C.c_int32 * len(precs))(*[PREC[p] if isinstance(p, str) else int(p) for p in precs])
+    h = C.c_void_p()
+    info = BucketInfo()
+    _check(_lib.bspai_bucket(M.ptr, float(bucket_eps), arr, len(precs), _stream(stream), C.byref(h),
+                             C.byref(info)))
+    q = info.q
+    d = dict(q=q, precs=[PREC_NAME[info.precs[k]] for k in range(q)], nnz_k=list(info.nnz_k[:q]),
+             slots_k=list(info.slots_k[:q]), thresholds=list(info.thresholds[:q]), norm_inf=info.norm_inf,
+             storage_pct=info.storage_pct, storage_pct_last8=info.storage_pct_last8, bytes=info.bytes)
+    return BMHandle(h.value), d
+
+
+def bucket_export(BM: BMHandle, nnz: int, stream=None):
+    ids = torch.empty(nnz, dtype=torch.int8, device="cuda")
+    stored = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    _check(_lib.bspai_bucket_export(BM.ptr, _ptr(ids), _ptr(stored), _stream(stream)))
+    return ids, stored
+
+
+def apply(BM: BMHandle, x, y, stream=None):
+    xp = PREC["fp64"] if x.dtype == torch.float64 else PREC["fp32"]
+    yp = PREC["fp64"] if y.dtype == torch.float64 else PREC["fp32"]
+    _check(_lib.bspai_apply(BM.ptr, _ptr(x), xp, _ptr(y), yp, _stream(stream)))
+    return y
+
+
+# ------------------------------------------------------------------ solves
+def _solve_info(si: SolveInfo) -> dict:
+    k = si.ir_steps
+    return dict(status=si.status, status_name=STATUS_NAMES[si.status], ir_steps=k, stop_reason=si.stop_reason,
+                total_iters=si.total_iters, gmres_iters=list(si.gmres_iters[:k]),
+                nbe=list(si.nbe[:min(33, k + 1)]), dx=list(si.dx[:k]), relres=list(si.relres[:k]))
+
+
+def gmres(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | None = None, stream=None) -> dict:
+    si = SolveInfo()
+    st = _lib.bspai_gmres(Ah.ptr, BM.ptr, _ptr(r), PREC[u_g], PREC[u_p], C.byref(o or opts()), _ptr(d),
+                          _stream(stream), C.byref(si))
+    _check(st, (OK, NONFINITE))
+    out = _solve_info(si)
+    out["status"] = st
+    return out
+
+
+def gmres_ir_solve(A, b, BM: BMHandle, M: MHandle | None, x, u="fp64", u_r="dd", u_g="fp32", u_p="fp32",
+                   tol=1e-4, o: Opts | None = None, stream=None) -> dict:
+    """A: DeviceCSR (converted inside the call) or an AHandle from matrix_create."""
+    si = SolveInfo()
+    mp = M.ptr if M is not None else None
+    if isinstance(A, AHandle):
+        st = _lib.gmres_ir_solve_h(A.ptr, _ptr(b), BM.ptr, mp, PREC[u], PREC[u_r], PREC[u_g], PREC[u_p],
+                                   float(tol), C.byref(o or opts()), _ptr(x), _stream(stream), C.byref(si))
+    else:
+        st = _lib.gmres_ir_solve(C.byref(A.c()), _ptr(b), BM.ptr, mp, PREC[u], PREC[u_r], PREC[u_g], PREC[u_p],
+                                 float(tol), C.byref(o or opts()), _ptr(x), _stream(stream), C.byref(si))
+    _check(st, (OK, NOT_CONVERGED, NONFINITE))
+    out = _solve_info(si)
+    out["status"] = st
+    return out

@@ -1,0 +1,489 @@
+// bucket.cu -- precision buckets of M (eq. nint, Alg 2.2) and their storage.
+//
+// ||M||_inf is the max over rows of the fp64 sum of |m_ij| taken in ascending
+// column order (one thread per row), so it and the thresholds
+// t_k = eps ||M||_inf / u_k are bit-for-bit reproducible.  Each entry goes to
+//   bucket 0      if |m| > t_1,
+//   bucket q-1    if |m| <= t_{q-1},
+//   bucket k      if t_{k+1} < |m| <= t_k   (0 < k < q-1),
+// boundary values to the lower-precision bucket.  Every bucket gets its own
+// SELL-32 structure (entries of a row keep their ascending column order);
+// values are stored in the bucket's format: fp16 with one power-of-two scale
+// per bucket, e4m3 with a power-of-two fp32 scale per column, so that the
+// narrow formats' exponent range does not flush the small entries.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace bspai {
+
+double unit_roundoff(int prec) {
+    switch (prec) {
+    case BSPAI_FP64: return 0x1p-53;
+    case BSPAI_FP32: return 0x1p-24;
+    case BSPAI_FP16: return 0x1p-11;
+    case BSPAI_BF16: return 0x1p-8;
+    case BSPAI_E4M3: return 0x1p-4;
+    case BSPAI_DROP: return 1.0;
+    default: return -1.0;
+    }
+}
+
+static int prec_bits(int prec) {
+    switch (prec) {
+    case BSPAI_FP64: return 64;
+    case BSPAI_FP32: return 32;
+    case BSPAI_FP16: return 16;
+    case BSPAI_BF16: return 16;
+    case BSPAI_E4M3: return 8;
+    default: return 0;
+    }
+}
+
+static size_t prec_bytes(int prec) { return (size_t)prec_bits(prec) / 8; }
+
+struct BucketParams {
+    int32_t q;
+    int32_t precs[8];
+    double eps;
+    double uk[8];
+};
+
+struct PackDst {
+    int32_t q;
+    int32_t precs[8];
+    int64_t* sptr[8];
+    int32_t* col[8];
+    void* val[8];
+    float scale[8];
+};
+
+__global__ void k_norm_rows(int n, const int64_t* __restrict__ sptr, const float* __restrict__ val,
+                            const int32_t* __restrict__ rowlen, double* __restrict__ norm) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t b = sptr[r >> 5] + (r & 31);
+    const int len = rowlen[r];
+    double s = 0.0;
+    for (int l = 0; l < len; ++l) s = __dadd_rn(s, fabs((double)val[b + (int64_t)l * kSlice]));
+    atomic_max_nonneg(norm, s);
+}
+
+__global__ void k_thresholds(const __grid_constant__ BucketParams P, const double* __restrict__ norm,
+                             double* __restrict__ thr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    thr[0] = __longlong_as_double(0x7ff0000000000000LL);
+    for (int k = 1; k < P.q; ++k) thr[k] = __ddiv_rn(__dmul_rn(P.eps, *norm), P.uk[k]);
+}
+
+__device__ __forceinline__ int classify(double a, const double* thr, int q) {
+    if (q == 1 || a > thr[1]) return 0;
+    if (a <= thr[q - 1]) return q - 1;
+    int k = 0;
+    for (int b = 1; b <= q - 2; ++b)
+        if (a > thr[b + 1] && a <= thr[b]) k = b;
+    return k;
+}
+
+// bucket id of every entry; per-slice widths of every bucket; per-bucket
+// counts and max |m|; per-column max |m| of the e4m3 bucket
+__global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int64_t* __restrict__ sptr,
+                                                  const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                  const int32_t* __restrict__ rowlen,
+                                                  const __grid_constant__ BucketParams P,
+                                                  const double* __restrict__ thr_g, int8_t* __restrict__ id,
+                                                  int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
+                                                  float* __restrict__ bmax, float* __restrict__ colmax) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)nslices * kSlice) return;
+    double thr[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) thr[k] = k < P.q ? thr_g[k] : 0.0;
+    int cnt[8];
+    float mx[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cnt[k] = 0;
+        mx[k] = 0.0f;
+    }
+    if (r < n) {
+        const int64_t b = sptr[r >> 5] + (r & 31);
+        const int len = rowlen[r];
+        for (int l = 0; l < len; ++l) {
+            const int64_t slot = b + (int64_t)l * kSlice;
+            const float m = val[slot];
+            const float am = fabsf(m);
+            const int k = classify((double)am, thr, P.q);
+            id[slot] = (int8_t)k;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                if (kk == k) {
+                    cnt[kk] += 1;
+                    mx[kk] = fmaxf(mx[kk], am);
+                }
+            }
+            if (P.precs[k] == BSPAI_E4M3) atomic_max_nonneg(colmax + col[slot], am);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k >= P.q) break;
+        int w = cnt[k], c = cnt[k];
+        float m = mx[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        }
+        if (lane == 0) {
+            widths[(int64_t)k * (nslices + 1) + (r >> 5)] = (int64_t)w * kSlice;
+            if (c) atomicAdd(nnzk + k, (unsigned long long)c);
+            if (m > 0.0f) atomic_max_nonneg(bmax + k, m);
+        }
+    }
+}
+
+// least power of two s = 2^e with maxabs <= fmax * 2^e (1 if maxabs == 0)
+__device__ __forceinline__ float pow2_scale(float maxabs_f, double fmax) {
+    const double maxabs = (double)maxabs_f;
+    if (!(maxabs > 0.0)) return 1.0f;
+    int E;
+    frexp(maxabs / fmax, &E);
+    int e = E - 2;
+    while (maxabs > ldexp(fmax, e)) ++e;
+    while (e > -1074 && maxabs <= ldexp(fmax, e - 1)) --e;
+    return (float)ldexp(1.0, e);
+}
+
+__global__ void k_bucket_scales(const __grid_constant__ BucketParams P, const float* __restrict__ bmax,
+                                float* __restrict__ scale) {
+    const int k = threadIdx.x;
+    if (k >= P.q) return;
+    scale[k] = P.precs[k] == BSPAI_FP16 ? pow2_scale(bmax[k], 65504.0) : 1.0f;
+}
+
+__global__ void k_col_scales(int n, const float* __restrict__ colmax, float* __restrict__ colscale) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) colscale[j] = pow2_scale(colmax[j], 448.0);
+}
+
+__device__ __forceinline__ void store_val(void* dst, int64_t p, int prec, float m, float scale, float cs) {
+    switch (prec) {
+    case BSPAI_FP64: reinterpret_cast<double*>(dst)[p] = (double)m; break;
+    case BSPAI_FP32: reinterpret_cast<float*>(dst)[p] = m; break;
+    case BSPAI_FP16: reinterpret_cast<__half*>(dst)[p] = __float2half_rn(__fdiv_rn(m, scale)); break;
+    case BSPAI_BF16: reinterpret_cast<__nv_bfloat16*>(dst)[p] = __float2bfloat16_rn(m); break;
+    case BSPAI_E4M3:
+        reinterpret_cast<__nv_fp8_storage_t*>(dst)[p] =
+            __nv_cvt_float_to_fp8(__fdiv_rn(m, cs), __NV_SATFINITE, __NV_E4M3);
+        break;
+    default: break;
+    }
+}
+
+__device__ __forceinline__ void store_zero(void* dst, int64_t p, int prec) {
+    switch (prec) {
+    case BSPAI_FP64: reinterpret_cast<double*>(dst)[p] = 0.0; break;
+    case BSPAI_FP32: reinterpret_cast<float*>(dst)[p] = 0.0f; break;
+    case BSPAI_FP16: reinterpret_cast<__half*>(dst)[p] = __float2half_rn(0.0f); break;
+    case BSPAI_BF16: reinterpret_cast<__nv_bfloat16*>(dst)[p] = __float2bfloat16_rn(0.0f); break;
+    case BSPAI_E4M3: reinterpret_cast<__nv_fp8_storage_t*>(dst)[p] = 0; break;
+    default: break;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pack(int n, int nslices, const int64_t* __restrict__ sptr,
+                                              const int32_t* __restrict__ col, const float* __restrict__ val,
+                                              const int32_t* __restrict__ rowlen, const int8_t* __restrict__ id,
+                                              const __grid_constant__ PackDst D, const float* __restrict__ scale,
+                                              const float* __restrict__ colscale) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)nslices * kSlice) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    int cnt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cnt[k] = 0;
+    if (r < n) {
+        const int64_t b = sptr[s] + lane;
+        const int len = rowlen[r];
+        for (int l = 0; l < len; ++l) {
+            const int64_t slot = b + (int64_t)l * kSlice;
+            const int k = id[slot];
+            int pos = 0;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                if (kk == k) pos = cnt[kk]++;
+            if (D.precs[k] == BSPAI_DROP) continue;
+            const int c = col[slot];
+            const int64_t dst = D.sptr[k][s] + (int64_t)pos * kSlice + lane;
+            D.col[k][dst] = c;
+            store_val(D.val[k], dst, D.precs[k], val[slot], scale[k], colscale ? colscale[c] : 1.0f);
+        }
+    }
+    for (int k = 0; k < D.q; ++k) {
+        if (D.precs[k] == BSPAI_DROP) continue;
+        const int width = (int)((D.sptr[k][s + 1] - D.sptr[k][s]) / kSlice);
+        int c0 = 0;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            if (kk == k) c0 = cnt[kk];
+        for (int l = c0; l < width; ++l) {
+            const int64_t dst = D.sptr[k][s] + (int64_t)l * kSlice + lane;
+            D.col[k][dst] = -1;
+            store_zero(D.val[k], dst, D.precs[k]);
+        }
+    }
+}
+
+// per nonzero in CSR order: bucket id and the value the product uses
+__global__ void k_bucket_export(int n, const int64_t* __restrict__ msptr, const int32_t* __restrict__ mrowlen,
+                                const int32_t* __restrict__ mcsr, const int8_t* __restrict__ id_sell,
+                                const __grid_constant__ BMDev B, int8_t* __restrict__ ids,
+                                double* __restrict__ stored) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    const int64_t b = msptr[s] + lane;
+    const int len = mrowlen[r];
+    const int o = mcsr[r];
+    int cnt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cnt[k] = 0;
+    for (int l = 0; l < len; ++l) {
+        const int k = id_sell[b + (int64_t)l * kSlice];
+        int pos = 0;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            if (kk == k) pos = cnt[kk]++;
+        if (ids) ids[o + l] = (int8_t)k;
+        if (!stored) continue;
+        const BucketDev& D = B.b[k];
+        double v = 0.0;
+        if (D.prec != BSPAI_DROP) {
+            const int64_t p = D.sptr[s] + (int64_t)pos * kSlice + lane;
+            const int c = D.col[p];
+            switch (D.prec) {
+            case BSPAI_FP64: v = reinterpret_cast<const double*>(D.val)[p]; break;
+            case BSPAI_FP32: v = reinterpret_cast<const float*>(D.val)[p]; break;
+            case BSPAI_FP16: v = (double)__half2float(reinterpret_cast<const __half*>(D.val)[p]) * D.scale; break;
+            case BSPAI_BF16: v = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(D.val)[p]); break;
+            case BSPAI_E4M3: {
+                __nv_fp8_e4m3 e;
+                e.__x = reinterpret_cast<const __nv_fp8_storage_t*>(D.val)[p];
+                v = (double)float(e) * D.colscale[c];
+                break;
+            }
+            default: break;
+            }
+        }
+        stored[o + l] = v;
+    }
+}
+
+}  // namespace bspai
+
+using namespace bspai;
+
+extern "C" {
+
+int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, bspai_stream_t st,
+                 bspai_BM_h* out, bspai_bucket_info_t* info) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!out) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: null out");
+    *out = nullptr;
+    if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: bad M handle");
+    if (!precs || q < 1 || q > 8) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: need 1 <= q <= 8 precisions");
+    if (!(bucket_eps > 0.0)) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: bucket_eps must be > 0");
+    BucketParams P{};
+    P.q = q;
+    P.eps = bucket_eps;
+    int n_e4m3 = 0;
+    for (int k = 0; k < q; ++k) {
+        P.precs[k] = precs[k];
+        P.uk[k] = unit_roundoff(precs[k]);
+        if (P.uk[k] < 0) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: precision %d not a storage format", precs[k]);
+        if (k > 0 && !(P.uk[k] > P.uk[k - 1]))
+            return set_error(BSPAI_ERR_INVALID, "bspai_bucket: precisions must have increasing unit roundoff");
+        n_e4m3 += precs[k] == BSPAI_E4M3;
+    }
+    if (n_e4m3 > 1) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_bucket: at most one e4m3 bucket");
+    const int n = M->n;
+    const int nsl = M->sell.nslices;
+    auto* B = new bspai_bucketed();
+    B->magic = kMagicBM;
+    B->stream = s;
+    B->n = n;
+    B->nnz = M->nnz;
+    B->q = q;
+    for (int k = 0; k < q; ++k) B->precs[k] = precs[k];
+
+    // scratch: norm, thresholds, widths, counts, maxima
+    double* d_norm = nullptr;
+    double* d_thr = nullptr;
+    int64_t* d_w = nullptr;
+    unsigned long long* d_nnzk = nullptr;
+    float* d_bmax = nullptr;
+    float* d_scale = nullptr;
+    float* d_colmax = nullptr;
+    auto cleanup = [&]() {
+        dfree(d_norm, s); dfree(d_thr, s); dfree(d_w, s); dfree(d_nnzk, s);
+        dfree(d_bmax, s); dfree(d_scale, s); dfree(d_colmax, s);
+    };
+    auto fail = [&](int code) {
+        cleanup();
+        bspai_free(B);
+        return code;
+    };
+    int rc;
+    ProfScope ps(BSPAI_K_BUCKET, s);
+    // private copy of M's structure (for export) and the bucket id per slot
+    B->msell.n = n;
+    B->msell.nslices = nsl;
+    B->msell.slots = M->sell.slots;
+    if ((rc = dalloc_t(&B->msell.sptr, (size_t)nsl + 1, s))) return fail(rc);
+    if ((rc = dalloc_t(&B->msell.col, (size_t)M->sell.slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&B->mrowlen, (size_t)n, s))) return fail(rc);
+    if ((rc = dalloc_t(&B->mcsr_row_ptr, (size_t)n + 1, s))) return fail(rc);
+    if ((rc = dalloc_t(&B->id_sell, (size_t)M->sell.slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_norm, 1, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_thr, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_w, (size_t)q * (nsl + 1), s))) return fail(rc);
+    if ((rc = dalloc_t(&d_nnzk, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_bmax, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_scale, 8, s))) return fail(rc);
+    if (n_e4m3) {
+        if ((rc = dalloc_t(&d_colmax, (size_t)n, s))) return fail(rc);
+        if ((rc = dalloc_t(&B->colscale, (size_t)n, s))) return fail(rc);
+    }
+    cudaError_t e = cudaSuccess;
+    e = cudaMemcpyAsync(B->msell.sptr, M->sell.sptr, sizeof(int64_t) * ((size_t)nsl + 1), cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(B->msell.col, M->sell.col, sizeof(int32_t) * (size_t)M->sell.slots, cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(B->mrowlen, M->rowlen, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(B->mcsr_row_ptr, M->csr_row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemsetAsync(d_norm, 0, sizeof(double), s);
+    if (!e) e = cudaMemsetAsync(d_nnzk, 0, 8 * sizeof(unsigned long long), s);
+    if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(float), s);
+    if (!e) e = cudaMemsetAsync(d_w, 0, sizeof(int64_t) * (size_t)q * (nsl + 1), s);
+    if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(float) * (size_t)n, s);
+    if (e) return fail(cuda_error(e, "bspai_bucket setup", __FILE__, __LINE__));
+    const unsigned g_rows = (unsigned)ceil_div((int64_t)nsl * kSlice, 256);
+    if (n > 0) {
+        k_norm_rows<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, M->sell.sptr, M->val, M->rowlen, d_norm);
+        note_launch();
+        k_thresholds<<<1, 32, 0, s>>>(P, d_norm, d_thr);
+        note_launch();
+        k_classify<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, P, d_thr,
+                                          B->id_sell, d_w, d_nnzk, d_bmax, d_colmax);
+        note_launch();
+        k_bucket_scales<<<1, 32, 0, s>>>(P, d_bmax, d_scale);
+        note_launch();
+        if (d_colmax) {
+            k_col_scales<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, d_colmax, B->colscale);
+            note_launch();
+        }
+    } else {
+        k_thresholds<<<1, 32, 0, s>>>(P, d_norm, d_thr);
+        note_launch();
+        k_bucket_scales<<<1, 32, 0, s>>>(P, d_bmax, d_scale);
+        note_launch();
+    }
+    if ((e = cudaGetLastError())) return fail(cuda_error(e, "bucket classify", __FILE__, __LINE__));
+    for (int k = 0; k < q; ++k) {
+        B->b[k].n = n;
+        B->b[k].nslices = nsl;
+        if ((rc = dalloc_t(&B->b[k].sptr, (size_t)nsl + 1, s))) return fail(rc);
+        if ((rc = scan_exclusive_i64(d_w + (size_t)k * (nsl + 1), B->b[k].sptr, nsl, s))) return fail(rc);
+    }
+    // sizes back to the host
+    int64_t slots[8] = {0};
+    unsigned long long nnzk[8] = {0};
+    double hthr[8] = {0};
+    double hnorm = 0.0;
+    float hscale[8] = {0};
+    for (int k = 0; k < q; ++k)
+        if ((e = cudaMemcpyAsync(&slots[k], B->b[k].sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s)))
+            return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
+    e = cudaMemcpyAsync(nnzk, d_nnzk, sizeof nnzk, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hthr, d_thr, sizeof hthr, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&hnorm, d_norm, sizeof hnorm, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hscale, d_scale, sizeof hscale, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
+    PackDst D{};
+    D.q = q;
+    int64_t bytes = 0;
+    for (int k = 0; k < q; ++k) {
+        B->nnz_k[k] = (int64_t)nnzk[k];
+        B->scale[k] = hscale[k];
+        D.precs[k] = precs[k];
+        D.sptr[k] = B->b[k].sptr;
+        D.scale[k] = hscale[k];
+        bytes += (int64_t)sizeof(int64_t) * (nsl + 1);
+        if (precs[k] == BSPAI_DROP) {
+            B->b[k].slots = 0;
+            continue;
+        }
+        B->b[k].slots = slots[k];
+        if ((rc = dalloc_t(&B->b[k].col, (size_t)slots[k], s))) return fail(rc);
+        if ((rc = dalloc(&B->val[k], (size_t)slots[k] * prec_bytes(precs[k]), s))) return fail(rc);
+        D.col[k] = B->b[k].col;
+        D.val[k] = B->val[k];
+        bytes += slots[k] * (int64_t)(4 + prec_bytes(precs[k]));
+    }
+    if (B->colscale) bytes += (int64_t)sizeof(float) * n;
+    if (n > 0) {
+        k_pack<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, B->id_sell, D, d_scale,
+                                      B->colscale);
+        note_launch();
+        if ((e = cudaGetLastError())) return fail(cuda_error(e, "k_pack", __FILE__, __LINE__));
+    }
+    cleanup();
+    if (info) {
+        info->q = q;
+        double num = 0, num8 = 0, tot = 0;
+        for (int k = 0; k < 8; ++k) {
+            info->precs[k] = k < q ? precs[k] : -1;
+            info->nnz_k[k] = k < q ? B->nnz_k[k] : 0;
+            info->slots_k[k] = k < q ? B->b[k].slots : 0;
+            info->thresholds[k] = k < q ? hthr[k] : 0.0;
+        }
+        for (int k = 0; k < q; ++k) {
+            int bits = prec_bits(precs[k]);
+            int bits8 = (k == q - 1 && precs[k] == BSPAI_DROP) ? 8 : bits;
+            num += (double)B->nnz_k[k] * bits;
+            num8 += (double)B->nnz_k[k] * bits8;
+            tot += (double)B->nnz_k[k];
+        }
+        double den = tot * prec_bits(precs[0]);
+        info->norm_inf = hnorm;
+        info->storage_pct = den > 0 ? 100.0 * num / den : 0.0;
+        info->storage_pct_last8 = den > 0 ? 100.0 * num8 / den : 0.0;
+        info->bytes = bytes;
+        e = cudaStreamSynchronize(s);
+        if (e) {
+            int code = cuda_error(e, "bspai_bucket", __FILE__, __LINE__);
+            bspai_free(B);
+            return code;
+        }
+    }
+    *out = B;
+    return BSPAI_OK;
+}
+
+int bspai_bucket_export(bspai_BM_h BM, int8_t* ids, double* stored, bspai_stream_t st) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket_export: bad handle");
+    if (BM->n == 0 || (!ids && !stored)) return BSPAI_OK;
+    k_bucket_export<<<(unsigned)ceil_div(BM->n, 256), 256, 0, s>>>(BM->n, BM->msell.sptr, BM->mrowlen,
+                                                                   BM->mcsr_row_ptr, BM->id_sell, BM->dev(), ids,
+                                                                   stored);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    return BSPAI_OK;
+}
+
+}  // extern "C"

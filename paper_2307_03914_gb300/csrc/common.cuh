@@ -1,0 +1,250 @@
+// common.cuh -- internal declarations shared by the libbspai.so translation units.
+//
+// Storage layout used by every sparse kernel: SELL-32 ("sliced ELLPACK" with
+// slices of 32 consecutive rows).  Slice s covers rows 32s..32s+31; its entries
+// occupy slots [sptr[s], sptr[s+1]) with sptr[s+1]-sptr[s] = 32 * width_s, and
+// entry l of row r sits at slot sptr[r/32] + 32*l + r%32.  One warp handles one
+// slice, one thread one row: the 32 lanes read 32 consecutive slots per step
+// (fully coalesced), and each row is still accumulated sequentially in
+// ascending column order.  Padding slots carry column -1 and value 0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "bspai.h"
+
+namespace bspai {
+
+constexpr int kSlice = 32;
+
+// ------------------------------------------------------------------ errors
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define CUDA_TRY(expr)                                                          \
+    do {                                                                        \
+        cudaError_t _e = (expr);                                                \
+        if (_e != cudaSuccess) return ::bspai::cuda_error(_e, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+#define CUDA_LAUNCH_CHECK() CUDA_TRY(cudaGetLastError())
+
+#define BSPAI_TRY(expr)                                                         \
+    do {                                                                        \
+        int _s = (expr);                                                        \
+        if (_s != BSPAI_OK) return _s;                                          \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+// Stream-ordered device allocation from the device's default memory pool
+// (pooled: repeated solves do not return memory to the driver).
+int dalloc(void** p, size_t bytes, cudaStream_t s);
+template <typename T>
+inline int dalloc_t(T** p, size_t count, cudaStream_t s) {
+    return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+void dfree(void* p, cudaStream_t s);
+
+// ------------------------------------------------------------------ handles
+enum : uint32_t {
+    kMagicA = 0xB5A10001u,
+    kMagicM = 0xB5A10002u,
+    kMagicBM = 0xB5A10003u,
+    kMagicDead = 0xDEADBEEFu
+};
+
+struct Sell {
+    int32_t n = 0;
+    int32_t nslices = 0;
+    int64_t slots = 0;
+    int64_t* sptr = nullptr;   // nslices + 1
+    int32_t* col = nullptr;    // slots, -1 = padding
+};
+
+// Device view of one precision bucket for the SpMV kernels.
+struct BucketDev {
+    int32_t prec;              // bspai_prec_t
+    float scale;               // fp16 bucket: power-of-two scale (else 1)
+    const int64_t* sptr;
+    const int32_t* col;
+    const void* val;           // typed by prec
+    const float* colscale;     // e4m3 bucket: per-column scale (else null)
+};
+
+struct BMDev {
+    int32_t n;
+    int32_t q;
+    BucketDev b[8];
+};
+
+}  // namespace bspai
+
+struct bspai_matrix {
+    uint32_t magic;
+    cudaStream_t stream;
+    int32_t n;
+    int64_t nnz;
+    bspai::Sell sell;
+    double* val64 = nullptr;   // A in fp64 (residual, u_r)
+    float* val32 = nullptr;    // A rounded to fp32 (u_p)
+    double* norm_inf = nullptr;// device scalar ||A||_inf
+};
+
+struct bspai_spai {
+    uint32_t magic;
+    cudaStream_t stream;
+    int32_t n;
+    int64_t nnz;
+    bspai::Sell sell;          // structure of the pattern (rows of M)
+    int32_t* rowlen = nullptr; // entries per row
+    int32_t* csr_row_ptr = nullptr;
+    float* val = nullptr;      // M in u_f = fp32
+    float* resid = nullptr;    // ||sbar_k||_2 per column of M'
+};
+
+struct bspai_bucketed {
+    uint32_t magic;
+    cudaStream_t stream;
+    int32_t n;
+    int64_t nnz;
+    int32_t q;
+    int32_t precs[8];
+    bspai::Sell b[8];          // one SELL structure per bucket
+    void* val[8] = {nullptr};
+    float scale[8];
+    float* colscale = nullptr; // per column (e4m3 bucket)
+    int64_t nnz_k[8];
+    // copy of M's structure for exporting in CSR order
+    bspai::Sell msell;
+    int32_t* mrowlen = nullptr;
+    int32_t* mcsr_row_ptr = nullptr;
+    int8_t* id_sell = nullptr; // bucket id per slot of msell
+    bspai::BMDev dev() const;
+};
+
+namespace bspai {
+
+// ------------------------------------------------------------------ helpers
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t s);
+int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                  Sell* out, double** val64, float** val32, int32_t** rowlen, cudaStream_t s);
+void sell_free(Sell* S, cudaStream_t s);
+
+// launches (defined in spmv.cu)
+int launch_bspmv(const BMDev& M, const void* x, int x_prec, void* y, int y_prec, cudaStream_t s);
+int launch_bspmv_idx(const BMDev& M, const void* x, int x_prec, void* y, int y_prec, const int* jd,
+                     int64_t ldx, int64_t ldy, int yoff, cudaStream_t s);
+BMDev single_bucket_view(const Sell& S, const void* val, int prec);
+
+// defined in matrix.cu
+int matrix_create(const bspai_csr_t* A, cudaStream_t s, bspai_matrix** out);
+int launch_residual(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
+                    cudaStream_t s);
+int validate_csr(const bspai_csr_t* A, bool need_val, const char* who, cudaStream_t s);
+double unit_roundoff(int prec);
+
+// ------------------------------------------------------------------ profiling
+bool prof_enabled();
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s);
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    bool on;
+    ProfScope(int c, cudaStream_t st) : cls(c), s(st), on(prof_enabled()) {
+        if (on) prof_begin(cls, s);
+    }
+    ~ProfScope() {
+        if (on) prof_end(cls, s);
+    }
+};
+
+int num_sms();
+void note_launch();  // counts kernel launches (reported by bspai_launch_count)
+
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------------ device
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// atomic max of a non-negative double (bit patterns of non-negative doubles
+// order like their values)
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
+    atomicMax(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));
+}
+
+// Grid-wide barrier for cooperative launches (all blocks co-resident).
+// Generation counting: the last block to arrive resets the counter and bumps
+// the generation; the others wait for the bump.  Every wait is bounded by
+// `timeout_ns` of %globaltimer; on expiry the block sets bar->err and every
+// waiter returns false, so the kernel can exit and the host can report
+// BSPAI_TIMEOUT (and must reset the barrier before reusing it).
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned long long timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned nb = gridDim.x;
+        unsigned gen = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nb - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar->gen) == gen) {
+                if (*(volatile int*)&bar->err) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicExch(&bar->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (*(volatile int*)&bar->err) ok = 0;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace bspai

@@ -1,0 +1,658 @@
+// gmres.cu -- left-preconditioned MGS-GMRES and the refinement loop of Alg 3.1.
+//
+// Per Arnoldi step j (the "hot loop" of the method) three launches run on the
+// solve's stream, with no host synchronisation between steps:
+//   w = A v_j               (u_p, SELL SpMV)                       spmv.cu
+//   z = M w -> V(:, j+1)    (Alg 2.3 bucketed SpMV, stored in u_g) spmv.cu
+//   k_mgs                   (cooperative, persistent)              this file
+// The Krylov index j and the "done" flag live in device memory (GmresState);
+// every kernel of a step reads them, so the host enqueues steps in chunks and
+// only reads the flag between chunks.  Steps enqueued after convergence
+// return immediately.
+//
+// k_mgs keeps one contiguous range of rows per block.  Modified Gram-Schmidt
+// needs the j+1 dot products in sequence; pass i fuses the update by the
+// previous coefficient with the next dot product, z <- z - h_{i-1} v_{i-1};
+// partial += v_i . z, so each basis vector is streamed once per step.  The
+// block partial sums go to a global array, one grid barrier, and every block
+// then adds the partials in the same fixed order, so all blocks hold the same
+// h_ij (deterministic, no atomics).  The last pass forms ||z||_2 and
+// normalises v_{j+1}; block 0 then applies the Givens rotations (fp64) and
+// tests |g_{j+1}| <= tau ||M r||_2.  j + 2 barriers per step, each bounded in
+// time (BSPAI_TIMEOUT).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bspai {
+
+struct GmresState {
+    int j;        // completed Arnoldi steps (= k)
+    int done;     // 1 once converged, broken down, failed or at kmax
+    int status;   // BSPAI_OK, BSPAI_TIMEOUT, BSPAI_NONFINITE
+    int kmax;
+    double beta;  // ||M r||_2 (in u_g)
+    double tau;
+    double res;   // |g_k|
+    double hlast;
+    GridBar bar;
+};
+
+template <typename T>
+struct Ar;
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+    static __device__ __forceinline__ float from(double a) { return __double2float_rn(a); }
+};
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+    static __device__ __forceinline__ double from(double a) { return a; }
+};
+
+__global__ void k_state_init(GmresState* st, int kmax, double tau) {
+    st->j = 0;
+    st->done = 0;
+    st->status = BSPAI_OK;
+    st->kmax = kmax;
+    st->beta = 0.0;
+    st->tau = tau;
+    st->res = 0.0;
+    st->hlast = 0.0;
+    st->bar.count = 0;
+    st->bar.err = 0;
+}
+
+__device__ __forceinline__ void block_rows(int n, int64_t& r0, int64_t& r1) {
+    int64_t chunk = ceil_div(ceil_div(n, gridDim.x), 32) * 32;
+    r0 = (int64_t)blockIdx.x * chunk;
+    r1 = r0 + chunk < n ? r0 + chunk : n;
+}
+
+// Sum of `v` over the whole grid, identical in every block: block sum in a
+// fixed tree, partials to part[slot*G + block], barrier, then every block adds
+// the G partials in the same order.  `ok` is false if the barrier failed.
+template <typename T>
+__device__ __forceinline__ T grid_sum(T v, T* part, int slot, GridBar* bar, unsigned long long tmo, bool& ok) {
+    __shared__ T s_w[32];
+    __shared__ T s_tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < nw ? s_w[lane] : T(0);
+        t = warp_sum(t);
+        if (lane == 0) part[(int64_t)slot * gridDim.x + blockIdx.x] = t;
+    }
+    ok = grid_sync(bar, tmo);
+    if (!ok) return T(0);
+    if (w == 0) {
+        T t = T(0);
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+            t = Ar<T>::add(t, *(volatile T*)&part[(int64_t)slot * gridDim.x + b]);
+        t = warp_sum(t);
+        if (lane == 0) s_tot = t;
+    }
+    __syncthreads();
+    return s_tot;
+}
+
+// beta = ||s||_2 of V(:, 0) = s = M r, then v_0 = s / beta and g_0 = beta
+template <typename T>
+__global__ void __launch_bounds__(512) k_gmres_start(T* __restrict__ V, int n, GmresState* st, double* g, T* part,
+                                                     unsigned long long tmo) {
+    int64_t r0, r1;
+    block_rows(n, r0, r1);
+    T acc = T(0);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) acc = Ar<T>::add(acc, Ar<T>::mul(V[r], V[r]));
+    bool ok;
+    const T tot = grid_sum(acc, part, 0, &st->bar, tmo, ok);
+    if (!ok) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->status = BSPAI_TIMEOUT;
+            st->done = 1;
+        }
+        return;
+    }
+    const T beta = Ar<T>::sqrt(tot);
+    const bool fin = isfinite((double)beta);
+    if (beta > T(0) && fin)
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) V[r] = Ar<T>::div(V[r], beta);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->beta = (double)beta;
+        st->res = (double)beta;
+        g[0] = (double)beta;
+        st->done = !(beta > T(0)) || !fin;
+        if (!fin) st->status = BSPAI_NONFINITE;
+    }
+}
+
+// Givens rotations on column j of H, update of g and the tau test (fp64)
+__device__ void givens_step(int j, int kmax, double hn, double* H, double* cs, double* sn, double* g,
+                            GmresState* st) {
+    double* hc = H + (int64_t)j * (kmax + 1);
+    hc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t1 = __dadd_rn(__dmul_rn(cs[i], hc[i]), __dmul_rn(sn[i], hc[i + 1]));
+        const double t2 = __dadd_rn(__dmul_rn(-sn[i], hc[i]), __dmul_rn(cs[i], hc[i + 1]));
+        hc[i] = t1;
+        hc[i + 1] = t2;
+    }
+    const double a = hc[j], b = hc[j + 1];
+    const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+    double c = 1.0, s = 0.0;
+    if (rr != 0.0) {
+        c = __ddiv_rn(a, rr);
+        s = __ddiv_rn(b, rr);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    hc[j] = rr;
+    hc[j + 1] = 0.0;
+    g[j + 1] = __dmul_rn(-s, g[j]);
+    g[j] = __dmul_rn(c, g[j]);
+    const double res = fabs(g[j + 1]);
+    const int k = j + 1;
+    const bool fin = isfinite(res) && isfinite(hn) && isfinite(rr);
+    st->res = res;
+    st->hlast = hn;
+    st->j = k;
+    if (!fin) st->status = BSPAI_NONFINITE;
+    st->done = (res <= __dmul_rn(st->tau, st->beta)) || hn == 0.0 || k >= kmax || !fin;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_mgs(T* __restrict__ V, int64_t ldv, int n, GmresState* st, double* H,
+                                             double* cs, double* sn, double* g, T* part, unsigned long long tmo) {
+    __shared__ int s_j, s_done, s_kmax;
+    if (threadIdx.x == 0) {
+        s_j = st->j;
+        s_done = st->done;
+        s_kmax = st->kmax;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int j = s_j, kmax = s_kmax;
+    int64_t r0, r1;
+    block_rows(n, r0, r1);
+    T* z = V + (int64_t)(j + 1) * ldv;
+    T hprev = T(0);
+    for (int i = 0; i <= j + 1; ++i) {
+        const T* vi = V + (int64_t)(i <= j ? i : j) * ldv;
+        const T* vp = V + (int64_t)(i > 0 ? i - 1 : 0) * ldv;
+        T acc = T(0);
+        if (i == 0) {
+            for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+                acc = Ar<T>::add(acc, Ar<T>::mul(vi[r], z[r]));
+        } else if (i <= j) {
+            for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+                const T zr = Ar<T>::sub(z[r], Ar<T>::mul(hprev, vp[r]));
+                z[r] = zr;
+                acc = Ar<T>::add(acc, Ar<T>::mul(vi[r], zr));
+            }
+        } else {
+            for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+                const T zr = Ar<T>::sub(z[r], Ar<T>::mul(hprev, vp[r]));
+                z[r] = zr;
+                acc = Ar<T>::add(acc, Ar<T>::mul(zr, zr));
+            }
+        }
+        bool ok;
+        const T h = grid_sum(acc, part, i & 1, &st->bar, tmo, ok);
+        if (!ok) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->status = BSPAI_TIMEOUT;
+                st->done = 1;
+            }
+            return;
+        }
+        if (i <= j) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) H[(int64_t)j * (kmax + 1) + i] = (double)h;
+            hprev = h;
+        } else {
+            const T hn = Ar<T>::sqrt(h);
+            if (hn > T(0) && isfinite((double)hn))
+                for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) z[r] = Ar<T>::div(z[r], hn);
+            if (blockIdx.x == 0 && threadIdx.x == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
+        }
+    }
+}
+
+// y = R^-1 g by column-oriented back substitution (fp64), one block
+__global__ void k_backsolve(const GmresState* st, const double* __restrict__ H, const double* __restrict__ g,
+                            double* __restrict__ y, int kmax) {
+    extern __shared__ double sg[];
+    __shared__ double s_yi;
+    const int k = st->j;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) sg[t] = g[t];
+    __syncthreads();
+    for (int i = k - 1; i >= 0; --i) {
+        const double* hc = H + (int64_t)i * (kmax + 1);
+        if (threadIdx.x == 0) {
+            s_yi = __ddiv_rn(sg[i], hc[i]);
+            y[i] = s_yi;
+        }
+        __syncthreads();
+        const double yi = s_yi;
+        for (int t = threadIdx.x; t < i; t += blockDim.x) sg[t] = __dsub_rn(sg[t], __dmul_rn(hc[t], yi));
+        __syncthreads();
+    }
+}
+
+// d = V y in u_g (y rounded to u_g, sequential over j), then x += d in fp64;
+// max|d| -> norms[0], max|x| -> norms[1]
+template <typename T>
+__global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, int64_t ldv, int n,
+                                                      const GmresState* st, const double* __restrict__ y,
+                                                      double* __restrict__ x, double* __restrict__ dout,
+                                                      double* __restrict__ norms) {
+    extern __shared__ unsigned char sraw[];
+    T* sy = reinterpret_cast<T*>(sraw);
+    const int k = st->j;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) sy[t] = Ar<T>::from(y[t]);
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dabs = 0.0, xabs = 0.0;
+    if (r < n) {
+        T acc = T(0);
+        for (int jj = 0; jj < k; ++jj) acc = Ar<T>::add(acc, Ar<T>::mul(V[(int64_t)jj * ldv + r], sy[jj]));
+        const double d = (double)acc;
+        if (dout) dout[r] = d;
+        double xn = 0.0;
+        if (x) {
+            xn = __dadd_rn(x[r], d);
+            x[r] = xn;
+        }
+        dabs = fabs(d);
+        xabs = fabs(xn);
+        if (!(dabs <= 1.7976931348623157e308)) dabs = __longlong_as_double(0x7ff0000000000000LL);
+        if (!(xabs <= 1.7976931348623157e308)) xabs = __longlong_as_double(0x7ff0000000000000LL);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dabs = fmax(dabs, __shfl_xor_sync(0xffffffffu, dabs, o));
+        xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(norms, dabs);
+        atomic_max_nonneg(norms + 1, xabs);
+    }
+}
+
+__global__ void k_absmax(int n, const double* __restrict__ v, double* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double a = r < n ? fabs(v[r]) : 0.0;
+    if (!(a <= 1.7976931348623157e308)) a = __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, a);
+}
+
+// ---------------------------------------------------------------- host side
+struct HostFlags {
+    int j, done, status, kmax;
+};
+
+struct GmresWork {
+    int n = 0, kmax = 0, G = 0, ug = BSPAI_FP32, up = BSPAI_FP32;
+    int64_t ldv = 0;
+    void* V = nullptr;
+    void* w = nullptr;
+    void* part = nullptr;
+    GmresState* st = nullptr;
+    double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *norms = nullptr;
+    HostFlags* hflags = nullptr;  // pinned
+    unsigned long long tmo_ns = 2000000000ull;
+    cudaStream_t s = nullptr;
+
+    int alloc(int n_, int kmax_, int ug_, int up_, double timeout_s, cudaStream_t st_) {
+        n = n_;
+        kmax = kmax_;
+        ug = ug_;
+        up = up_;
+        s = st_;
+        tmo_ns = (unsigned long long)((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
+        const size_t es = ug == BSPAI_FP64 ? 8 : 4;
+        ldv = ceil_div(n > 0 ? n : 1, 64) * 64;
+        int occ = 0;
+        cudaError_t e;
+        if (ug == BSPAI_FP64) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs<double>, 512, 0);
+            int occ2 = 0;
+            if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_gmres_start<double>, 512, 0);
+            occ = occ < occ2 ? occ : occ2;
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs<float>, 512, 0);
+            int occ2 = 0;
+            if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_gmres_start<float>, 512, 0);
+            occ = occ < occ2 ? occ : occ2;
+        }
+        if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
+        if (occ < 1) return set_error(BSPAI_ERR_CUDA, "gmres: cooperative kernel does not fit on an SM");
+        G = (occ >= 2 ? 2 : 1) * num_sms();
+        BSPAI_TRY(dalloc(&V, es * (size_t)ldv * (size_t)(kmax + 1), s));
+        BSPAI_TRY(dalloc(&w, es * (size_t)ldv, s));
+        BSPAI_TRY(dalloc(&part, es * 2 * (size_t)G, s));
+        BSPAI_TRY(dalloc_t(&st, 1, s));
+        BSPAI_TRY(dalloc_t(&H, (size_t)(kmax + 1) * kmax, s));
+        BSPAI_TRY(dalloc_t(&cs, (size_t)kmax + 1, s));
+        BSPAI_TRY(dalloc_t(&sn, (size_t)kmax + 1, s));
+        BSPAI_TRY(dalloc_t(&g, (size_t)kmax + 2, s));
+        BSPAI_TRY(dalloc_t(&y, (size_t)kmax + 1, s));
+        BSPAI_TRY(dalloc_t(&norms, 4, s));
+        CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(GmresState), s));
+        CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * ((size_t)kmax + 2), s));
+        // one pinned flag word per host thread, kept for the life of the process
+        static thread_local HostFlags* t_flags = nullptr;
+        if (!t_flags) CUDA_TRY(cudaMallocHost(&t_flags, sizeof(HostFlags)));
+        hflags = t_flags;
+        return BSPAI_OK;
+    }
+    void release() {
+        dfree(V, s); dfree(w, s); dfree(part, s); dfree(st, s); dfree(H, s); dfree(cs, s);
+        dfree(sn, s); dfree(g, s); dfree(y, s); dfree(norms, s);
+        V = w = part = nullptr;
+        st = nullptr;
+        H = cs = sn = g = y = norms = nullptr;
+    }
+};
+
+static int coop_launch(void* fn, int G, void** args, cudaStream_t s) {
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(512), args, 0, s);
+    note_launch();
+    if (e) return cuda_error(e, "cudaLaunchCooperativeKernel", __FILE__, __LINE__);
+    return BSPAI_OK;
+}
+
+struct GmresResult {
+    int k = 0;
+    int status = BSPAI_OK;
+    double beta = 0.0, res = 0.0, dmax = 0.0, xmax = 0.0;
+};
+
+// One GMRES solve of (M A) d = M r.  x != null: x += d; dout != null: d out.
+template <typename T>
+static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* BM, const double* r, double tau,
+                     double* x, double* dout, GmresResult& out) {
+    cudaStream_t s = W.s;
+    const int n = W.n;
+    const int tprec = W.ug;  // T matches u_g
+    const BMDev Aview = single_bucket_view(A->sell, W.up == BSPAI_FP64 ? (const void*)A->val64 : (const void*)A->val32,
+                                           W.up);
+    const BMDev Mview = BM->dev();
+    T* V = reinterpret_cast<T*>(W.V);
+    T* w = reinterpret_cast<T*>(W.w);
+    T* part = reinterpret_cast<T*>(W.part);
+    {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        k_state_init<<<1, 1, 0, s>>>(W.st, W.kmax, tau);
+        note_launch();
+        CUDA_LAUNCH_CHECK();
+        CUDA_TRY(cudaMemsetAsync(W.norms, 0, 4 * sizeof(double), s));
+    }
+    {
+        ProfScope ps(BSPAI_K_BSPMV, s);
+        BSPAI_TRY(launch_bspmv(Mview, r, BSPAI_FP64, V, tprec, s));
+    }
+    {
+        ProfScope ps(BSPAI_K_MGS, s);
+        int nn = n;
+        void* args[] = {&V, &nn, &W.st, &W.g, &part, &W.tmo_ns};
+        BSPAI_TRY(coop_launch((void*)k_gmres_start<T>, W.G, args, s));
+    }
+    int launched = 0, chunk = 4;
+    const int* jd = &W.st->j;
+    while (launched < W.kmax) {
+        for (int c = 0; c < chunk && launched < W.kmax; ++c, ++launched) {
+            {
+                ProfScope ps(BSPAI_K_SPMV_A, s);
+                BSPAI_TRY(launch_bspmv_idx(Aview, V, tprec, w, tprec, jd, W.ldv, 0, 0, s));
+            }
+            {
+                ProfScope ps(BSPAI_K_BSPMV, s);
+                BSPAI_TRY(launch_bspmv_idx(Mview, w, tprec, V, tprec, jd, 0, W.ldv, 1, s));
+            }
+            {
+                ProfScope ps(BSPAI_K_MGS, s);
+                int nn = n;
+                int64_t ld = W.ldv;
+                void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};
+                BSPAI_TRY(coop_launch((void*)k_mgs<T>, W.G, args, s));
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(W.hflags, W.st, sizeof(HostFlags), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (W.hflags->done) break;
+        chunk = chunk < 32 ? chunk * 2 : 32;
+    }
+    {
+        ProfScope ps(BSPAI_K_UPDATE, s);
+        k_backsolve<<<1, 1024, sizeof(double) * (size_t)(W.kmax + 1), s>>>(W.st, W.H, W.g, W.y, W.kmax);
+        note_launch();
+        CUDA_LAUNCH_CHECK();
+        if (n > 0) {
+            k_gmres_update<T><<<(unsigned)ceil_div(n, 256), 256, sizeof(T) * (size_t)(W.kmax + 1), s>>>(
+                V, W.ldv, n, W.st, W.y, x, dout, W.norms);
+            note_launch();
+            CUDA_LAUNCH_CHECK();
+        }
+    }
+    GmresState hs;
+    double hn[2];
+    CUDA_TRY(cudaMemcpyAsync(&hs, W.st, sizeof hs, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hn, W.norms, sizeof hn, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    out.k = hs.j;
+    out.status = hs.status;
+    out.beta = hs.beta;
+    out.res = hs.res;
+    out.dmax = hn[0];
+    out.xmax = hn[1];
+    if (hs.status == BSPAI_TIMEOUT) {
+        // the barrier state is undefined after a timeout: reset it for reuse
+        CUDA_TRY(cudaMemsetAsync(&W.st->bar, 0, sizeof(GridBar), s));
+        return set_error(BSPAI_TIMEOUT, "gmres: a grid barrier exceeded its time limit");
+    }
+    return BSPAI_OK;
+}
+
+static int check_solver_precs(int u, int u_r, int u_g, int u_p) {
+    if (u != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "working precision u must be FP64");
+    if (u_r != BSPAI_DD && u_r != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_r must be DD or FP64");
+    if (u_g != BSPAI_FP32 && u_g != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_g must be FP32 or FP64");
+    if (u_p != BSPAI_FP32 && u_p != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_p must be FP32 or FP64");
+    return BSPAI_OK;
+}
+
+static constexpr int kKmaxLimit = 4000;  // shared-memory bound of k_backsolve / k_gmres_update
+
+static int resolve_kmax(const bspai_opts_t* o, int n) {
+    int k = o && o->kmax > 0 ? o->kmax : (n < 1000 ? n : 1000);
+    if (k > n) k = n;
+    if (k > kKmaxLimit) k = kKmaxLimit;
+    return k < 1 ? 1 : k;
+}
+
+int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
+                         int u_r, cudaStream_t s);
+
+static int ir_solve(bspai_matrix* A, const double* b, const bspai_bucketed* BM, const bspai_spai* M, int u_r,
+                    int u_g, int u_p, double tol, const bspai_opts_t* opts, double* x, cudaStream_t s,
+                    bspai_solve_info_t* info) {
+    bspai_opts_t o;
+    bspai_opts_default(&o);
+    if (opts) o = *opts;
+    const int n = A->n;
+    const int kmax = resolve_kmax(&o, n);
+    int imax = o.i_max > 0 ? o.i_max : 10;
+    if (imax > 32) imax = 32;
+    const double ustop = o.u_stop > 0 ? o.u_stop : 0x1p-53;
+    const double stag = o.stagnation > 0 ? o.stagnation : 0.9;
+    const double tau = tol > 0 ? tol : o.tau;
+    bspai_solve_info_t inf;
+    memset(&inf, 0, sizeof inf);
+    if (BM->n != n || (M && M->n != n)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: size mismatch");
+    if (!o.x0_given && !M) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: need M for x0 = M b");
+    if (n == 0) {
+        if (info) *info = inf;
+        return BSPAI_OK;
+    }
+    double* r = nullptr;
+    double* nrm = nullptr;
+    GmresWork W;
+    int rc = BSPAI_OK;
+    auto finish = [&](int code) {
+        dfree(r, s);
+        dfree(nrm, s);
+        W.release();
+        inf.status = code;
+        if (info) *info = inf;
+        return code;
+    };
+    if ((rc = dalloc_t(&r, (size_t)n, s))) return finish(rc);
+    if ((rc = dalloc_t(&nrm, 4, s))) return finish(rc);
+    if ((rc = W.alloc(n, kmax, u_g, u_p, o.barrier_timeout_s, s))) return finish(rc);
+    // ||A||_inf, ||b||_inf
+    double anorm = 0.0, bnorm = 0.0;
+    {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        cudaError_t e0 = cudaMemsetAsync(nrm, 0, 4 * sizeof(double), s);
+        if (e0) return finish(cuda_error(e0, "memset", __FILE__, __LINE__));
+        k_absmax<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, b, nrm);
+        note_launch();
+        if (!o.x0_given) {
+            // x0 = M b with the unbucketed M in u_f = fp32, stored in fp64
+            if ((rc = launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), b, BSPAI_FP64, x, BSPAI_FP64, s)))
+                return finish(rc);
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(&bnorm, nrm, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&anorm, A->norm_inf, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return finish(cuda_error(e, "norms", __FILE__, __LINE__));
+    double dprev = INFINITY;
+    int code = BSPAI_NOT_CONVERGED;
+    for (int i = 0; i < imax; ++i) {
+        double hn[2] = {0, 0};
+        e = cudaMemsetAsync(nrm, 0, 2 * sizeof(double), s);
+        if (e) return finish(cuda_error(e, "memset", __FILE__, __LINE__));
+        if ((rc = launch_residual_prec(A, x, b, r, nrm, u_r, s))) return finish(rc);
+        e = cudaMemcpyAsync(hn, nrm, sizeof hn, cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return finish(cuda_error(e, "residual norms", __FILE__, __LINE__));
+        const double nbe = hn[0] / (anorm * hn[1] + bnorm);
+        inf.nbe[i] = nbe;
+        if (!std::isfinite(nbe)) {
+            code = set_error(BSPAI_NONFINITE, "gmres_ir_solve: non-finite residual at step %d", i);
+            break;
+        }
+        if (nbe <= ustop) {
+            inf.stop_reason = 1;
+            code = BSPAI_OK;
+            break;
+        }
+        GmresResult gr;
+        rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, tau, x, nullptr, gr)
+                               : gmres_run<float>(W, A, BM, r, tau, x, nullptr, gr);
+        if (rc) return finish(rc);
+        inf.gmres_iters[i] = gr.k;
+        inf.total_iters += gr.k;
+        inf.relres[i] = gr.beta > 0 ? gr.res / gr.beta : 0.0;
+        inf.ir_steps = i + 1;
+        inf.dx[i] = gr.xmax > 0 ? gr.dmax / gr.xmax : gr.dmax;
+        if (gr.status == BSPAI_NONFINITE || !std::isfinite(gr.dmax) || !std::isfinite(gr.xmax)) {
+            code = set_error(BSPAI_NONFINITE, "gmres_ir_solve: non-finite value in GMRES at step %d", i);
+            break;
+        }
+        if (gr.dmax <= ustop * gr.xmax) {
+            inf.stop_reason = 2;
+            code = BSPAI_OK;
+            break;
+        }
+        if (i > 0 && gr.dmax > stag * dprev) {
+            inf.stop_reason = 3;
+            code = BSPAI_OK;
+            break;
+        }
+        dprev = gr.dmax;
+    }
+    if (code == BSPAI_NOT_CONVERGED) set_error(code, "gmres_ir_solve: i_max = %d steps without meeting a stopping test", imax);
+    return finish(code);
+}
+
+}  // namespace bspai
+
+using namespace bspai;
+
+extern "C" {
+
+int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h BM, bspai_M_h M, bspai_prec_t u, bspai_prec_t u_r,
+                     bspai_prec_t u_g, bspai_prec_t u_p, double tol, const bspai_opts_t* opts, double* x,
+                     bspai_stream_t s, bspai_solve_info_t* info) {
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: bad A handle");
+    if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: bad bucketed M handle");
+    if (M && M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: bad M handle");
+    if (A->n > 0 && (!b || !x)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: null vector");
+    BSPAI_TRY(check_solver_precs(u, u_r, u_g, u_p));
+    return ir_solve(A, b, BM, M, u_r, u_g, u_p, tol, opts, x, (cudaStream_t)s, info);
+}
+
+int gmres_ir_solve(const bspai_csr_t* Acsr, const double* b, bspai_BM_h BM, bspai_M_h M, bspai_prec_t u,
+                   bspai_prec_t u_r, bspai_prec_t u_g, bspai_prec_t u_p, double tol, const bspai_opts_t* opts,
+                   double* x, bspai_stream_t s, bspai_solve_info_t* info) {
+    BSPAI_TRY(check_solver_precs(u, u_r, u_g, u_p));
+    bspai_matrix* A = nullptr;
+    BSPAI_TRY(matrix_create(Acsr, (cudaStream_t)s, &A));
+    int rc = gmres_ir_solve_h(A, b, BM, M, u, u_r, u_g, u_p, tol, opts, x, s, info);
+    bspai_free(A);
+    return rc;
+}
+
+int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
+                const bspai_opts_t* opts, double* d, bspai_stream_t st, bspai_solve_info_t* info) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_gmres: bad A handle");
+    if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "bspai_gmres: bad M handle");
+    if (BM->n != A->n) return set_error(BSPAI_ERR_INVALID, "bspai_gmres: size mismatch");
+    if (A->n > 0 && (!r || !d)) return set_error(BSPAI_ERR_INVALID, "bspai_gmres: null vector");
+    BSPAI_TRY(check_solver_precs(BSPAI_FP64, BSPAI_DD, u_g, u_p));
+    bspai_opts_t o;
+    bspai_opts_default(&o);
+    if (opts) o = *opts;
+    bspai_solve_info_t inf;
+    memset(&inf, 0, sizeof inf);
+    if (A->n == 0) {
+        if (info) *info = inf;
+        return BSPAI_OK;
+    }
+    GmresWork W;
+    int rc = W.alloc(A->n, resolve_kmax(&o, A->n), u_g, u_p, o.barrier_timeout_s, s);
+    GmresResult gr;
+    if (!rc)
+        rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, o.tau, nullptr, d, gr)
+                               : gmres_run<float>(W, A, BM, r, o.tau, nullptr, d, gr);
+    W.release();
+    inf.status = rc ? rc : gr.status;
+    inf.ir_steps = 1;
+    inf.gmres_iters[0] = gr.k;
+    inf.total_iters = gr.k;
+    inf.relres[0] = gr.beta > 0 ? gr.res / gr.beta : 0.0;
+    if (info) *info = inf;
+    if (!rc && gr.status == BSPAI_NONFINITE) return set_error(BSPAI_NONFINITE, "bspai_gmres: non-finite value");
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+// matrix.cu -- A on the GPU: CSR -> SELL-32 conversion, ||A||_inf, and the
+// residual r = b - A x in double-double (u_r; Alg 3.1 residual line).
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace bspai {
+
+// width of each 32-row slice (max row length), times 32
+__global__ void k_slice_width(int n, const int32_t* __restrict__ row_ptr, int64_t* __restrict__ w) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nsl = ceil_div(n, kSlice);
+    if (r >= nsl * kSlice) return;
+    int len = r < n ? row_ptr[r + 1] - row_ptr[r] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if ((r & 31) == 0) w[r >> 5] = (int64_t)len * kSlice;
+}
+
+// scatter the CSR rows into their slices; padding slots get column -1, value 0
+__global__ void k_sell_fill(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const int64_t* __restrict__ sptr,
+                            int32_t* __restrict__ scol, double* __restrict__ v64, float* __restrict__ v32,
+                            int32_t* __restrict__ rowlen) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nsl = ceil_div(n, kSlice);
+    if (r >= nsl * kSlice) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    const int64_t base = sptr[s];
+    const int width = (int)((sptr[s + 1] - base) / kSlice);
+    int b = 0, len = 0;
+    if (r < n) {
+        b = row_ptr[r];
+        len = row_ptr[r + 1] - b;
+    }
+    for (int l = 0; l < width; ++l) {
+        const int64_t slot = base + (int64_t)l * kSlice + lane;
+        if (l < len) {
+            scol[slot] = col[b + l];
+            if (val) {
+                double a = val[b + l];
+                if (v64) v64[slot] = a;
+                if (v32) v32[slot] = __double2float_rn(a);
+            }
+        } else {
+            scol[slot] = -1;
+            if (v64) v64[slot] = 0.0;
+            if (v32) v32[slot] = 0.0f;
+        }
+    }
+    if (rowlen && r < n) rowlen[r] = len;
+}
+
+int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const double* val, Sell* out,
+                  double** val64, float** val32, int32_t** rowlen, cudaStream_t s) {
+    Sell S;
+    S.n = n;
+    S.nslices = (int32_t)ceil_div(n, kSlice);
+    int64_t* w = nullptr;
+    BSPAI_TRY(dalloc_t(&w, (size_t)S.nslices + 1, s));
+    BSPAI_TRY(dalloc_t(&S.sptr, (size_t)S.nslices + 1, s));
+    const int64_t rows = (int64_t)S.nslices * kSlice;
+    const unsigned grid = (unsigned)ceil_div(rows, 256);
+    if (n > 0) {
+        k_slice_width<<<grid, 256, 0, s>>>(n, row_ptr, w);
+        note_launch();
+        CUDA_LAUNCH_CHECK();
+    }
+    BSPAI_TRY(scan_exclusive_i64(w, S.sptr, S.nslices, s));
+    CUDA_TRY(cudaMemcpyAsync(&S.slots, S.sptr + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    dfree(w, s);
+    BSPAI_TRY(dalloc_t(&S.col, (size_t)S.slots, s));
+    double* v64 = nullptr;
+    float* v32 = nullptr;
+    int32_t* rl = nullptr;
+    if (val64) BSPAI_TRY(dalloc_t(&v64, (size_t)S.slots, s));
+    if (val32) BSPAI_TRY(dalloc_t(&v32, (size_t)S.slots, s));
+    if (rowlen) BSPAI_TRY(dalloc_t(&rl, (size_t)n, s));
+    if (n > 0) {
+        k_sell_fill<<<grid, 256, 0, s>>>(n, row_ptr, col, val, S.sptr, S.col, v64, v32, rl);
+        note_launch();
+        CUDA_LAUNCH_CHECK();
+    }
+    *out = S;
+    if (val64) *val64 = v64;
+    if (val32) *val32 = v32;
+    if (rowlen) *rowlen = rl;
+    return BSPAI_OK;
+}
+
+__global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                                  const double* __restrict__ val, double* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t s = r >> 5;
+    double sum = 0.0;
+    for (int64_t p = sptr[s] + (r & 31); p < sptr[s + 1]; p += kSlice)
+        if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
+    atomic_max_nonneg(out, sum);
+}
+
+// ------------------------------------------------------------ double-double
+// Knuth TwoSum, the "fast" variant for |a| >= |b|, and the FMA TwoProduct.
+__device__ __forceinline__ void dd_two_sum(double a, double b, double& s, double& e) {
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bv)), __dsub_rn(b, bv));
+}
+__device__ __forceinline__ void dd_fast_two_sum(double a, double b, double& s, double& e) {
+    s = __dadd_rn(a, b);
+    e = __dsub_rn(b, __dsub_rn(s, a));
+}
+// (hi, lo) += (bh, bl) with the accurate double-double addition
+__device__ __forceinline__ void dd_accumulate(double& hi, double& lo, double bh, double bl) {
+    double s1, s2, t1, t2;
+    dd_two_sum(hi, bh, s1, s2);
+    dd_two_sum(lo, bl, t1, t2);
+    s2 = __dadd_rn(s2, t1);
+    dd_fast_two_sum(s1, s2, s1, s2);
+    s2 = __dadd_rn(s2, t2);
+    dd_fast_two_sum(s1, s2, hi, lo);
+}
+
+// r = b - A x, each product split exactly by an FMA, accumulated in
+// double-double in ascending column order (DD = true; DD = false is the plain
+// fp64 recurrence); also max|r| and max|x| over rows.
+template <bool DD>
+__global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __restrict__ sptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const double* __restrict__ val,
+                                                     const double* __restrict__ x,
+                                                     const double* __restrict__ b, double* __restrict__ r,
+                                                     double* __restrict__ norms) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rabs = 0.0, xabs = 0.0;
+    if (i < n) {
+        const int64_t s = i >> 5;
+        double hi = b[i], lo = 0.0;
+        const int64_t end = sptr[s + 1];
+        for (int64_t p = sptr[s] + (i & 31); p < end; p += kSlice) {
+            const int c = __ldg(col + p);
+            if (c < 0) break;
+            const double a = __ldg(val + p);
+            const double xv = __ldg(x + c);
+            const double ph = __dmul_rn(a, xv);
+            if (DD) {
+                const double pl = __fma_rn(a, xv, -ph);
+                dd_accumulate(hi, lo, -ph, -pl);
+            } else {
+                hi = __dsub_rn(hi, ph);
+            }
+        }
+        const double ri = __dadd_rn(hi, lo);
+        r[i] = ri;
+        rabs = fabs(ri);
+        xabs = fabs(x[i]);
+        if (!(rabs <= 1.7976931348623157e308)) rabs = __longlong_as_double(0x7ff0000000000000LL);  // NaN -> Inf
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rabs = fmax(rabs, __shfl_xor_sync(0xffffffffu, rabs, o));
+        xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
+    }
+    if ((threadIdx.x & 31) == 0 && norms) {
+        atomic_max_nonneg(norms, rabs);
+        atomic_max_nonneg(norms + 1, xabs);
+    }
+}
+
+int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
+                         int u_r, cudaStream_t s) {
+    if (A->n == 0) return BSPAI_OK;
+    ProfScope ps(BSPAI_K_RESIDUAL, s);
+    const unsigned grid = (unsigned)ceil_div(A->n, 256);
+    if (u_r == BSPAI_FP64)
+        k_residual_dd<false><<<grid, 256, 0, s>>>(A->n, A->sell.sptr, A->sell.col, A->val64, x, b, r, norms);
+    else
+        k_residual_dd<true><<<grid, 256, 0, s>>>(A->n, A->sell.sptr, A->sell.col, A->val64, x, b, r, norms);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    return BSPAI_OK;
+}
+
+int launch_residual(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
+                    cudaStream_t s) {
+    return launch_residual_prec(A, x, b, r, norms, BSPAI_DD, s);
+}
+
+// Structural check of a caller CSR before any kernel indexes through it:
+// row_ptr[0] = 0, row_ptr[n] = nnz, non-decreasing, columns in [0, n) and
+// strictly ascending within each row.  Bit 0: bad row pointers, bit 1: bad
+// column, bit 2: unsorted or repeated column.
+__global__ void k_validate_csr(int n, int nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               int* __restrict__ bad) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > n) return;
+    if (r == n) {
+        if (rp[n] != nnz || rp[0] != 0) atomicOr(bad, 1);
+        return;
+    }
+    const int b = rp[r], e = rp[r + 1];
+    if (b < 0 || e < b || e > nnz) {
+        atomicOr(bad, 1);
+        return;
+    }
+    if (!col) return;
+    for (int p = b; p < e; ++p) {
+        const int c = col[p];
+        if (c < 0 || c >= n) atomicOr(bad, 2);
+        else if (p > b && c <= col[p - 1]) atomicOr(bad, 4);
+    }
+}
+
+int validate_csr(const bspai_csr_t* A, bool need_val, const char* who, cudaStream_t s) {
+    if (!A) return set_error(BSPAI_ERR_INVALID, "%s: null matrix", who);
+    if (A->n < 0 || A->nnz < 0) return set_error(BSPAI_ERR_INVALID, "%s: negative size", who);
+    if (A->n == 0) return BSPAI_OK;
+    if (!A->row_ptr || (A->nnz > 0 && !A->col) || (need_val && A->nnz > 0 && !A->val))
+        return set_error(BSPAI_ERR_INVALID, "%s: missing CSR arrays", who);
+    int* d_bad = nullptr;
+    BSPAI_TRY(dalloc_t(&d_bad, 1, s));
+    CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    k_validate_csr<<<(unsigned)ceil_div((int64_t)A->n + 1, 256), 256, 0, s>>>(A->n, A->nnz, A->row_ptr, A->col,
+                                                                              d_bad);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    int bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    dfree(d_bad, s);
+    if (bad)
+        return set_error(BSPAI_ERR_INVALID, "%s: malformed CSR (%s%s%s)", who, (bad & 1) ? "row pointers " : "",
+                         (bad & 2) ? "column out of range " : "", (bad & 4) ? "columns not strictly ascending" : "");
+    return BSPAI_OK;
+}
+
+int matrix_create(const bspai_csr_t* A, cudaStream_t s, bspai_matrix** out) {
+    if (!A || !out) return set_error(BSPAI_ERR_INVALID, "matrix_create: null argument");
+    if (A->n < 0 || A->nnz < 0) return set_error(BSPAI_ERR_INVALID, "matrix_create: negative size");
+    if (A->n > 0 && (!A->row_ptr || !A->col || !A->val))
+        return set_error(BSPAI_ERR_INVALID, "matrix_create: A needs row_ptr, col and val");
+    BSPAI_TRY(validate_csr(A, true, "matrix_create", s));
+    auto* M = new bspai_matrix();
+    M->magic = kMagicA;
+    M->stream = s;
+    M->n = A->n;
+    M->nnz = A->nnz;
+    int st;
+    {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        st = sell_from_csr(A->n, A->row_ptr, A->col, A->val, &M->sell, &M->val64, &M->val32, nullptr, s);
+        if (st == BSPAI_OK) st = dalloc_t(&M->norm_inf, 1, s);
+        if (st == BSPAI_OK) {
+            cudaError_t e = cudaMemsetAsync(M->norm_inf, 0, sizeof(double), s);
+            if (e != cudaSuccess) st = cuda_error(e, "memset", __FILE__, __LINE__);
+        }
+        if (st == BSPAI_OK && A->n > 0) {
+            k_row_abs_sum_max<<<(unsigned)ceil_div(A->n, 256), 256, 0, s>>>(A->n, M->sell.sptr, M->sell.col,
+                                                                            M->val64, M->norm_inf);
+            note_launch();
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = cuda_error(e, "k_row_abs_sum_max", __FILE__, __LINE__);
+        }
+    }
+    if (st != BSPAI_OK) {
+        bspai_free(M);
+        return st;
+    }
+    *out = M;
+    return BSPAI_OK;
+}
+
+}  // namespace bspai
+
+using namespace bspai;
+
+extern "C" {
+
+int bspai_matrix_create(const bspai_csr_t* A, bspai_stream_t s, bspai_A_h* out) {
+    if (!out) return set_error(BSPAI_ERR_INVALID, "bspai_matrix_create: null out");
+    *out = nullptr;
+    return matrix_create(A, (cudaStream_t)s, out);
+}
+
+int bspai_residual(bspai_A_h A, const double* x, const double* b, double* r, bspai_stream_t s) {
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_residual: bad handle");
+    if (A->n > 0 && (!x || !b || !r)) return set_error(BSPAI_ERR_INVALID, "bspai_residual: null vector");
+    return launch_residual(A, x, b, r, nullptr, (cudaStream_t)s);
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times: the 3D 7-point anisotropic convection-diffusion problem on a
+128^3 grid (n = 2,097,152; FP8 bucket) and the random sparse problem with
+n = 65,536 and pattern(|A|^2) top-24.  The oracle checks sampled SPAI columns
+one by one, the full bucket ids and bucketed products (O(nnz) in C), the full
+double-double residual, and the solve by properties that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib
+from paper_2307_03914_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BENCH_EPS = 2.0 ** -10
+
+
+@pytest.fixture(scope="module")
+def B():
+    return lib()
+
+
+def _tol(kappa, resid):
+    s = np.minimum(resid, 0.999)
+    return np.maximum(1e-5, 10 * 2.0 ** -24 * (2 * kappa + kappa ** 2 * s / np.sqrt(1 - s ** 2)))
+
+
+@pytest.mark.parametrize("name,eps", [("convdiff3d", BENCH_EPS), ("random", 2.0 ** -16)])
+def test_full_size(B, name, eps):
+    wl = W.workload(name)
+    A, P = wl["A"], wl["pattern"]
+    n = A.n
+    g = gpu_build(B, wl)
+    assert g["info"]["n_rank_deficient"] == 0
+    # sampled SPAI columns (three contiguous windows, one of them the ragged end)
+    for c0 in (0, n // 2, n - 1500):
+        c1 = c0 + 1500
+        ref = O.spai(A, P, wl["spai_eps"], cols=(c0, c1))
+        a, b = P.row_ptr[c0], P.row_ptr[c1]
+        tol = _tol(ref["kappa"][c0:c1], ref["resid"][c0:c1])
+        for k in range(c0, c1):
+            lo, hi = P.row_ptr[k], P.row_ptr[k + 1]
+            e = np.linalg.norm(g["val"][lo:hi] - ref["mval"][lo:hi]) / np.linalg.norm(ref["mval"][lo:hi])
+            assert e <= tol[k - c0], (k, e)
+        assert np.allclose(g["resid"][c0:c1], ref["resid"][c0:c1], rtol=1e-4, atol=1e-6)
+    # buckets and the bucketed product on the whole M (same M on both sides)
+    bk = gpu_bucket(B, g["M"], P.nnz, eps, wl["precs"])
+    ref = O.bucket_ids(P.row_ptr, g["val"], eps, wl["precs"])
+    assert np.array_equal(bk["ids"], ref["ids"])
+    assert bk["info"]["norm_inf"] == ref["norm"]
+    stored, _, _ = O.bucket_store(P.row_ptr, P.col, g["val"], ref["ids"], wl["precs"])
+    assert np.array_equal(bk["stored"], stored)
+    xin = np.random.default_rng(1).uniform(-1, 1, n).astype(np.float32)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    g_stream = torch.cuda.current_stream()
+    B.apply(bk["BM"], dev(xin), y, stream=g_stream)
+    yr = O.bspmv(P.row_ptr, P.col, stored, ref["ids"], wl["precs"], xin.astype(np.float64))
+    assert np.array_equal(host(y).astype(np.float64), yr.astype(np.float32).astype(np.float64))
+    # residual of a perturbed solution: bit-exact double-double
+    Ah = B.matrix_create(g["A"])
+    xp = wl["x_true"] * (1 + 1e-9)
+    r = torch.empty(n, dtype=torch.float64, device="cuda")
+    B.residual(Ah, dev(xp), dev(wl["b"]), r)
+    assert np.array_equal(host(r), O.residual_dd(A, xp, wl["b"]))
+    # the solve: forward error <= 1e-10 and a normwise backward error at the level of u
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    info = B.gmres_ir_solve(Ah, dev(wl["b"]), bk["BM"], g["M"], x, tol=wl["tau"])
+    assert info["status"] == 0, info
+    xg = host(x)
+    fe = np.abs(xg - wl["x_true"]).max() / np.abs(wl["x_true"]).max()
+    assert fe <= 1e-10, (fe, info)
+    rr = O.residual_dd(A, xg, wl["b"])
+    nbe = np.abs(rr).max() / (O.norm_inf(A.row_ptr, A.val) * np.abs(xg).max() + np.abs(wl["b"]).max())
+    assert nbe <= 4 * 2.0 ** -53, nbe
+    print(name, info["gmres_iters"], f"fe={fe:.2e} nbe={nbe:.2e}", bk["info"]["nnz_k"])
