@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparator", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--kmax", type=int, default=0, help="cap on GMRES steps per refinement step (0: library default)")
     return p.parse_args()
 
 
@@ -251,7 +252,7 @@ def main():
     def step(x, eps=args.bucket_eps, pl=precs, ug="fp32", up="fp32", tau=wl["tau"], A_in=Ad, P_in=Pd, b_in=bd):
         M, _ = B.bspai_build(A_in, P_in, wl["spai_eps"])
         BM, binfo = B.bspai_bucket(M, eps, pl)
-        info = B.gmres_ir_solve(A_in, b_in, BM, M, x, u_g=ug, u_p=up, tol=tau)
+        info = B.gmres_ir_solve(A_in, b_in, BM, M, x, u_g=ug, u_p=up, tol=tau, o=B.opts(tau=tau, kmax=args.kmax))
         M.free()
         BM.free()
         return info, binfo
