@@ -212,6 +212,32 @@ int bspai_apply(bspai_BM_h BM, const void* x, bspai_prec_t x_prec, void* y, bspa
 int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
                 const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
 
+/* The same GMRES solve as bspai_gmres, for callers that cannot allocate
+ * device memory at the time of the call -- for example a host program that
+ * has handed the GPU's memory to its own pool allocator up front, or one that
+ * must not call cudaMalloc/cudaFree (which can synchronise the device) once
+ * it is running.  The paper has no counterpart to this entry point; it only
+ * changes where the workspace lives.
+ *   - Workspace: one fixed 64 MiB block of device memory that belongs to the
+ *     library image (every GPU that loads the library holds it until the
+ *     process exits).  The call needs n_pad * (kmax + 1) values in u_g
+ *     (n_pad = n rounded up to 64) plus about 8 (kmax + 1)^2 bytes; larger
+ *     problems are rejected with BSPAI_ERR_INVALID and a message giving the
+ *     bytes needed, and nothing is launched.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or stream-ordered pool
+ *     allocation, and no pinned host buffer.  (Leave kernel-class timing,
+ *     bspai_profile_enable, off: it creates CUDA events.)
+ *   - The first call on a device looks up the device address of the block
+ *     with that device current; make that first call before any stream
+ *     capture begins.
+ *   - Every call uses the same block, which keeps the previous call's
+ *     contents; each call clears the parts that must start at zero.  Two calls
+ *     whose GPU work overlaps (for example on two streams of one device) race
+ *     on the block and give undefined results: run them one after another.
+ * A, BM, r, d, opts and info as for bspai_gmres. */
+int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
+                        const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
+
 /* BSPAI-GMRES-IR (Alg 3.1 after the SPAI build): x0 = M b in u_f (unless
  * opts->x0_given), then up to i_max steps of r = b - A x in u_r, GMRES on
  * (M A) d = M r with tolerance tol, x = x + d in u.  Supported: u = FP64,

@@ -98,6 +98,7 @@ _sig("bspai_bucket", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINT
 _sig("bspai_bucket_export", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_apply", _i, [_vp, _vp, _i, _vp, _i, _vp])
 _sig("bspai_gmres", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
+_sig("bspai_gmres_noalloc", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
 _sig("gmres_ir_solve", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                             C.POINTER(SolveInfo)])
 _sig("gmres_ir_solve_h", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
@@ -285,6 +286,19 @@ def gmres(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | Non
     si = SolveInfo()
     st = _lib.bspai_gmres(Ah.ptr, BM.ptr, _ptr(r), PREC[u_g], PREC[u_p], C.byref(o or opts()), _ptr(d),
                           _stream(stream), C.byref(si))
+    _check(st, (OK, NONFINITE))
+    out = _solve_info(si)
+    out["status"] = st
+    return out
+
+
+def gmres_noalloc(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | None = None,
+                  stream=None) -> dict:
+    """bspai_gmres with its workspace in the library's fixed device block
+    (for callers that cannot allocate device memory during the call)."""
+    si = SolveInfo()
+    st = _lib.bspai_gmres_noalloc(Ah.ptr, BM.ptr, _ptr(r), PREC[u_g], PREC[u_p], C.byref(o or opts()), _ptr(d),
+                                  _stream(stream), C.byref(si))
     _check(st, (OK, NONFINITE))
     out = _solve_info(si)
     out["status"] = st

@@ -22,6 +22,7 @@
 // time (BSPAI_TIMEOUT).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -652,6 +653,126 @@ int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, b
     inf.relres[0] = gr.beta > 0 ? gr.res / gr.beta : 0.0;
     if (info) *info = inf;
     if (!rc && gr.status == BSPAI_NONFINITE) return set_error(BSPAI_NONFINITE, "bspai_gmres: non-finite value");
+    return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation GMRES
+// bspai_gmres_noalloc runs exactly the kernels of bspai_gmres, but takes its
+// whole workspace (Krylov basis, Hessenberg matrix, rotations, partial sums,
+// solver state) from one fixed block of device memory that is part of the
+// library image, so it never asks the CUDA runtime for memory.  That block is
+// set aside on every GPU that loads the library and stays there until the
+// process exits.
+namespace bspai {
+
+constexpr size_t kNoallocScratchBytes = 64ull << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_base[128];  // device address of the scratch, per device ordinal
+
+// The host-side name of a __device__ array is only a stand-in, not a device
+// address: the address is looked up once per device, with that device current.
+static int noalloc_scratch_address(void** out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_gmres_noalloc: device ordinal %d", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation scratch)", __FILE__, __LINE__);
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return BSPAI_OK;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace bspai
+
+extern "C" {
+
+int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
+                        const bspai_opts_t* opts, double* d, bspai_stream_t st, bspai_solve_info_t* info) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_gmres_noalloc: bad A handle");
+    if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "bspai_gmres_noalloc: bad M handle");
+    if (BM->n != A->n) return set_error(BSPAI_ERR_INVALID, "bspai_gmres_noalloc: size mismatch");
+    if (A->n > 0 && (!r || !d)) return set_error(BSPAI_ERR_INVALID, "bspai_gmres_noalloc: null vector");
+    BSPAI_TRY(check_solver_precs(BSPAI_FP64, BSPAI_DD, u_g, u_p));
+    bspai_opts_t o;
+    bspai_opts_default(&o);
+    if (opts) o = *opts;
+    bspai_solve_info_t inf;
+    memset(&inf, 0, sizeof inf);
+    if (A->n == 0) {
+        if (info) *info = inf;
+        return BSPAI_OK;
+    }
+    // workspace layout inside the fixed scratch block
+    GmresWork W;
+    W.n = A->n;
+    W.kmax = resolve_kmax(&o, A->n);
+    W.ug = u_g;
+    W.up = u_p;
+    W.s = s;
+    W.tmo_ns = (unsigned long long)((o.barrier_timeout_s > 0 ? o.barrier_timeout_s : 2.0) * 1e9);
+    const size_t es = u_g == BSPAI_FP64 ? 8 : 4;
+    W.ldv = ceil_div(W.n, 64) * 64;
+    int occ = 0, occ2 = 0;
+    cudaError_t e = u_g == BSPAI_FP64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs<double>, 512, 0)
+                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs<float>, 512, 0);
+    if (!e)
+        e = u_g == BSPAI_FP64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_gmres_start<double>, 512, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_gmres_start<float>, 512, 0);
+    if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
+    occ = occ < occ2 ? occ : occ2;
+    if (occ < 1) return set_error(BSPAI_ERR_CUDA, "bspai_gmres_noalloc: cooperative kernel does not fit on an SM");
+    W.G = (occ >= 2 ? 2 : 1) * num_sms();
+    const size_t kx = (size_t)W.kmax;
+    size_t off[11];
+    size_t sz[10] = {es * (size_t)W.ldv * (kx + 1), es * (size_t)W.ldv, es * 2 * (size_t)W.G, sizeof(GmresState),
+                     sizeof(double) * (kx + 1) * kx, sizeof(double) * (kx + 1), sizeof(double) * (kx + 1),
+                     sizeof(double) * (kx + 2), sizeof(double) * (kx + 1), sizeof(double) * 4};
+    off[0] = 0;
+    for (int i = 0; i < 10; ++i) off[i + 1] = align256(off[i] + sz[i]);
+    if (off[10] > kNoallocScratchBytes)
+        return set_error(BSPAI_ERR_INVALID,
+                         "bspai_gmres_noalloc: n = %d with kmax = %d needs %zu bytes of scratch; the fixed block "
+                         "holds %zu bytes (lower kmax or use bspai_gmres)",
+                         W.n, W.kmax, off[10], kNoallocScratchBytes);
+    unsigned char* base = nullptr;
+    BSPAI_TRY(noalloc_scratch_address(reinterpret_cast<void**>(&base)));
+    W.V = base + off[0];
+    W.w = base + off[1];
+    W.part = base + off[2];
+    W.st = reinterpret_cast<GmresState*>(base + off[3]);
+    W.H = reinterpret_cast<double*>(base + off[4]);
+    W.cs = reinterpret_cast<double*>(base + off[5]);
+    W.sn = reinterpret_cast<double*>(base + off[6]);
+    W.g = reinterpret_cast<double*>(base + off[7]);
+    W.y = reinterpret_cast<double*>(base + off[8]);
+    W.norms = reinterpret_cast<double*>(base + off[9]);
+    static thread_local HostFlags t_flags;  // ordinary host memory
+    W.hflags = &t_flags;
+    // the scratch keeps whatever the previous call left there: clear the parts
+    // that must start at zero (solver state with its grid barrier, g)
+    CUDA_TRY(cudaMemsetAsync(W.st, 0, sizeof(GmresState), s));
+    CUDA_TRY(cudaMemsetAsync(W.g, 0, sizeof(double) * (kx + 2), s));
+    GmresResult gr;
+    int rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, o.tau, nullptr, d, gr)
+                               : gmres_run<float>(W, A, BM, r, o.tau, nullptr, d, gr);
+    inf.status = rc ? rc : gr.status;
+    inf.ir_steps = 1;
+    inf.gmres_iters[0] = gr.k;
+    inf.total_iters = gr.k;
+    inf.relres[0] = gr.beta > 0 ? gr.res / gr.beta : 0.0;
+    if (info) *info = inf;
+    if (!rc && gr.status == BSPAI_NONFINITE) return set_error(BSPAI_NONFINITE, "bspai_gmres_noalloc: non-finite value");
     return rc;
 }
 
