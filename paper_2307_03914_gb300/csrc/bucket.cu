@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
                                                   const __grid_constant__ BucketParams P,
                                                   const double* __restrict__ thr_g, int8_t* __restrict__ id,
                                                   int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
-                                                  float* __restrict__ bmax, float* __restrict__ colmax) {
+                                                  float* __restrict__ bmax, float* __restrict__ colmax,
+                                                  int* __restrict__ wmax) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nslices * kSlice) return;
     double thr[8];
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
             widths[(int64_t)k * (nslices + 1) + (r >> 5)] = (int64_t)w * kSlice;
             if (c) atomicAdd(nnzk + k, (unsigned long long)c);
             if (m > 0.0f) atomic_max_nonneg(bmax + k, m);
+            if (w) atomicMax(wmax + k, w);
         }
     }
 }
@@ -329,9 +331,10 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     float* d_bmax = nullptr;
     float* d_scale = nullptr;
     float* d_colmax = nullptr;
+    int* d_wmax = nullptr;
     auto cleanup = [&]() {
         dfree(d_norm, s); dfree(d_thr, s); dfree(d_w, s); dfree(d_nnzk, s);
-        dfree(d_bmax, s); dfree(d_scale, s); dfree(d_colmax, s);
+        dfree(d_bmax, s); dfree(d_scale, s); dfree(d_colmax, s); dfree(d_wmax, s);
     };
     auto fail = [&](int code) {
         cleanup();
@@ -355,6 +358,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     if ((rc = dalloc_t(&d_nnzk, 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_bmax, 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_scale, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_wmax, 8, s))) return fail(rc);
     if (n_e4m3) {
         if ((rc = dalloc_t(&d_colmax, (size_t)n, s))) return fail(rc);
         if ((rc = dalloc_t(&B->colscale, (size_t)n, s))) return fail(rc);
@@ -367,6 +371,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     if (!e) e = cudaMemsetAsync(d_norm, 0, sizeof(double), s);
     if (!e) e = cudaMemsetAsync(d_nnzk, 0, 8 * sizeof(unsigned long long), s);
     if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(float), s);
+    if (!e) e = cudaMemsetAsync(d_wmax, 0, 8 * sizeof(int), s);
     if (!e) e = cudaMemsetAsync(d_w, 0, sizeof(int64_t) * (size_t)q * (nsl + 1), s);
     if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(float) * (size_t)n, s);
     if (e) return fail(cuda_error(e, "bspai_bucket setup", __FILE__, __LINE__));
@@ -377,7 +382,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
         k_thresholds<<<1, 32, 0, s>>>(P, d_norm, d_thr);
         note_launch();
         k_classify<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, P, d_thr,
-                                          B->id_sell, d_w, d_nnzk, d_bmax, d_colmax);
+                                          B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax);
         note_launch();
         k_bucket_scales<<<1, 32, 0, s>>>(P, d_bmax, d_scale);
         note_launch();
@@ -404,6 +409,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     double hthr[8] = {0};
     double hnorm = 0.0;
     float hscale[8] = {0};
+    int hwmax[8] = {0};
     for (int k = 0; k < q; ++k)
         if ((e = cudaMemcpyAsync(&slots[k], B->b[k].sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s)))
             return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
@@ -411,6 +417,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     if (!e) e = cudaMemcpyAsync(hthr, d_thr, sizeof hthr, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&hnorm, d_norm, sizeof hnorm, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hscale, d_scale, sizeof hscale, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hwmax, d_wmax, sizeof hwmax, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
     PackDst D{};
@@ -419,6 +426,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     for (int k = 0; k < q; ++k) {
         B->nnz_k[k] = (int64_t)nnzk[k];
         B->scale[k] = hscale[k];
+        B->maxw[k] = hwmax[k];
         D.precs[k] = precs[k];
         D.sptr[k] = B->b[k].sptr;
         D.scale[k] = hscale[k];

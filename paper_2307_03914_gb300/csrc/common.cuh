@@ -73,6 +73,8 @@ struct BucketDev {
     const int32_t* col;
     const void* val;           // typed by prec
     const float* colscale;     // e4m3 bucket: per-column scale (else null)
+    int64_t nnz;               // entries in the bucket (-1: unknown)
+    int32_t maxw;              // widest slice of the bucket in slots per row (-1: unknown)
 };
 
 struct BMDev {
@@ -118,6 +120,7 @@ struct bspai_bucketed {
     float scale[8];
     float* colscale = nullptr; // per column (e4m3 bucket)
     int64_t nnz_k[8];
+    int32_t maxw[8];           // widest slice per bucket (slots per row)
     // copy of M's structure for exporting in CSR order
     bspai::Sell msell;
     int32_t* mrowlen = nullptr;

@@ -232,6 +232,170 @@ __global__ void __launch_bounds__(512) k_mgs(T* __restrict__ V, int64_t ldv, int
     }
 }
 
+// Split grid reduction for k_mgs_res: grid_arrive publishes this block's
+// partial sum and arrives at the barrier; grid_wait completes the barrier and
+// returns the grid total (the block partials added in a fixed order, the same
+// value in every block).  Work placed between the two overlaps the barrier.
+template <typename T>
+__device__ __forceinline__ void grid_arrive(T v, T* part, int slot, GridBar* bar, unsigned* s_gen, T* s_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < nw ? s_w[lane] : T(0);
+        t = warp_sum(t);
+        if (lane == 0) {
+            part[(int64_t)slot * gridDim.x + blockIdx.x] = t;
+            const unsigned gen = ld_acquire_u32(&bar->gen);
+            __threadfence();
+            const unsigned arrived = atomicAdd(&bar->count, 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(&bar->count, 0u);
+                __threadfence();
+                atomicAdd(&bar->gen, 1u);
+            }
+            *s_gen = gen;  // released once bar->gen differs from this value
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T grid_wait(const T* part, int slot, GridBar* bar, unsigned long long tmo,
+                                       const unsigned* s_gen, T* s_tot, int* s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = *s_gen;
+        if (ld_acquire_u32(&bar->gen) == gen) {
+            const unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar->gen) == gen) {
+                if (*(volatile int*)&bar->err) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > tmo) {
+                    atomicExch(&bar->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (*(volatile int*)&bar->err) ok = 0;
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    if (!*s_ok) return T(0);
+    if (threadIdx.x < 32) {
+        T t = T(0);
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+            t = Ar<T>::add(t, *(const volatile T*)&part[(int64_t)slot * gridDim.x + b]);
+        t = warp_sum(t);
+        if (threadIdx.x == 0) *s_tot = t;
+    }
+    __syncthreads();
+    return *s_tot;
+}
+
+// MGS step with the new vector z resident on chip: one block per SM owns a
+// contiguous range of rows, holds z for them in shared memory for all j + 2
+// passes, and streams each basis vector v_i exactly once (R rows per thread,
+// all loads of a pass issued before the thread waits on the previous pass's
+// barrier).  Per pass i: z <- z - h_{i-1} v_{i-1} (v_{i-1} kept in registers),
+// partial += v_i . z, arrive; the last pass forms ||z||_2 and writes v_{j+1}.
+// Same arithmetic as k_mgs (fp32 or fp64, no fused multiply-add).
+template <typename T, int R>
+__global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t ldv, int n, GmresState* st,
+                                                     double* H, double* cs, double* sn, double* g, T* part,
+                                                     unsigned long long tmo) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* zs = reinterpret_cast<T*>(smraw);
+    __shared__ T s_w[32];
+    __shared__ T s_tot;
+    __shared__ unsigned s_gen;
+    __shared__ int s_ok, s_j, s_done, s_kmax;
+    if (threadIdx.x == 0) {
+        s_j = st->j;
+        s_done = st->done;
+        s_kmax = st->kmax;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int j = s_j, kmax = s_kmax;
+    int64_t r0, r1;
+    block_rows(n, r0, r1);
+    const int nb = r1 > r0 ? (int)(r1 - r0) : 0;
+    const int tid = threadIdx.x;
+    const int bd = blockDim.x;
+    T* z = V + (int64_t)(j + 1) * ldv + r0;
+    const T* v0 = V + r0;
+    T vcur[R], vnext[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        const int lr = tid + t * bd;
+        vcur[t] = T(0);
+        vnext[t] = T(0);
+        if (lr < nb) {
+            zs[lr] = z[lr];
+            vcur[t] = v0[lr];
+        }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        const int lr = tid + t * bd;
+        if (lr < nb) acc = Ar<T>::add(acc, Ar<T>::mul(vcur[t], zs[lr]));
+    }
+    grid_arrive(acc, part, 0, &st->bar, &s_gen, s_w);
+    for (int i = 1; i <= j + 1; ++i) {
+        if (i <= j) {
+            const T* vi = V + (int64_t)i * ldv + r0;
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                const int lr = tid + t * bd;
+                if (lr < nb) vnext[t] = vi[lr];
+            }
+        }
+        const T h = grid_wait(part, (i - 1) & 1, &st->bar, tmo, &s_gen, &s_tot, &s_ok);
+        if (!s_ok) {
+            if (blockIdx.x == 0 && tid == 0) {
+                st->status = BSPAI_TIMEOUT;
+                st->done = 1;
+            }
+            return;
+        }
+        if (blockIdx.x == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
+        acc = T(0);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int lr = tid + t * bd;
+            if (lr < nb) {
+                const T zr = Ar<T>::sub(zs[lr], Ar<T>::mul(h, vcur[t]));
+                zs[lr] = zr;
+                acc = Ar<T>::add(acc, Ar<T>::mul(i <= j ? vnext[t] : zr, zr));
+            }
+        }
+        grid_arrive(acc, part, i & 1, &st->bar, &s_gen, s_w);
+#pragma unroll
+        for (int t = 0; t < R; ++t) vcur[t] = vnext[t];
+    }
+    const T h2 = grid_wait(part, (j + 1) & 1, &st->bar, tmo, &s_gen, &s_tot, &s_ok);
+    if (!s_ok) {
+        if (blockIdx.x == 0 && tid == 0) {
+            st->status = BSPAI_TIMEOUT;
+            st->done = 1;
+        }
+        return;
+    }
+    const T hn = Ar<T>::sqrt(h2);
+    const bool norm = hn > T(0) && isfinite((double)hn);
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        const int lr = tid + t * bd;
+        if (lr < nb) z[lr] = norm ? Ar<T>::div(zs[lr], hn) : zs[lr];
+    }
+    if (blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
+}
+
 // y = R^-1 g by column-oriented back substitution (fp64), one block
 __global__ void k_backsolve(const GmresState* st, const double* __restrict__ H, const double* __restrict__ g,
                             double* __restrict__ y, int kmax) {
@@ -307,6 +471,9 @@ struct HostFlags {
     int j, done, status, kmax;
 };
 
+struct GmresWork;
+static int choose_mgs(GmresWork& W);
+
 struct GmresWork {
     int n = 0, kmax = 0, G = 0, ug = BSPAI_FP32, up = BSPAI_FP32;
     int64_t ldv = 0;
@@ -317,6 +484,9 @@ struct GmresWork {
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *norms = nullptr;
     HostFlags* hflags = nullptr;  // pinned
     unsigned long long tmo_ns = 2000000000ull;
+    void* res_fn = nullptr;  // k_mgs_res instance, or null for k_mgs
+    int Gr = 0;              // its grid: one block of 1024 threads per SM
+    size_t res_smem = 0;
     cudaStream_t s = nullptr;
 
     int alloc(int n_, int kmax_, int ug_, int up_, double timeout_s, cudaStream_t st_) {
@@ -360,7 +530,7 @@ struct GmresWork {
         static thread_local HostFlags* t_flags = nullptr;
         if (!t_flags) CUDA_TRY(cudaMallocHost(&t_flags, sizeof(HostFlags)));
         hflags = t_flags;
-        return BSPAI_OK;
+        return choose_mgs(*this);
     }
     void release() {
         dfree(V, s); dfree(w, s); dfree(part, s); dfree(st, s); dfree(H, s); dfree(cs, s);
@@ -370,6 +540,47 @@ struct GmresWork {
         H = cs = sn = g = y = norms = nullptr;
     }
 };
+
+template <typename T>
+static void* pick_res(int R) {
+    if (R <= 1) return (void*)k_mgs_res<T, 1>;
+    if (R <= 2) return (void*)k_mgs_res<T, 2>;
+    if (R <= 4) return (void*)k_mgs_res<T, 4>;
+    if (R <= 8) return (void*)k_mgs_res<T, 8>;
+    if (sizeof(T) == 4 && R <= 12) return (void*)k_mgs_res<float, 12>;
+    if (sizeof(T) == 4 && R <= 14) return (void*)k_mgs_res<float, 14>;
+    if (sizeof(T) == 4 && R <= 16) return (void*)k_mgs_res<float, 16>;
+    return nullptr;
+}
+
+// Use the on-chip MGS kernel when one block of 1024 threads per SM can hold
+// its rows of z in shared memory with at most 16 (fp32) / 8 (fp64) rows per thread.
+static int choose_mgs(GmresWork& W) {
+    W.res_fn = nullptr;
+    const int Gr = num_sms();
+    const int64_t chunk = ceil_div(ceil_div(W.n, Gr), 32) * 32;
+    const int R = (int)ceil_div(chunk, 1024);
+    const size_t es = W.ug == BSPAI_FP64 ? 8 : 4;
+    const size_t smem = (size_t)chunk * es;
+    if (smem > 200 * 1024) return BSPAI_OK;
+    void* fn = es == 8 ? pick_res<double>(R) : pick_res<float>(R);
+    if (!fn) return BSPAI_OK;
+    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, smem));
+    if (occ < 1) return BSPAI_OK;
+    W.res_fn = fn;
+    W.Gr = Gr;
+    W.res_smem = smem;
+    return BSPAI_OK;
+}
+
+static int coop_launch_cfg(void* fn, int G, int block, size_t smem, void** args, cudaStream_t s) {
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(block), args, smem, s);
+    note_launch();
+    if (e) return cuda_error(e, "cudaLaunchCooperativeKernel", __FILE__, __LINE__);
+    return BSPAI_OK;
+}
 
 static int coop_launch(void* fn, int G, void** args, cudaStream_t s) {
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(512), args, 0, s);
@@ -431,7 +642,10 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
                 int nn = n;
                 int64_t ld = W.ldv;
                 void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};
-                BSPAI_TRY(coop_launch((void*)k_mgs<T>, W.G, args, s));
+                if (W.res_fn)
+                    BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr, 1024, W.res_smem, args, s));
+                else
+                    BSPAI_TRY(coop_launch((void*)k_mgs<T>, W.G, args, s));
             }
         }
         CUDA_TRY(cudaMemcpyAsync(W.hflags, W.st, sizeof(HostFlags), cudaMemcpyDeviceToHost, s));
@@ -554,7 +768,8 @@ static int ir_solve(bspai_matrix* A, const double* b, const bspai_bucketed* BM, 
         e = cudaMemcpyAsync(hn, nrm, sizeof hn, cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
         if (e) return finish(cuda_error(e, "residual norms", __FILE__, __LINE__));
-        const double nbe = hn[0] / (anorm * hn[1] + bnorm);
+        // a zero residual is an exact solution (b = 0, x = 0 gives 0 / 0 otherwise)
+        const double nbe = hn[0] == 0.0 ? 0.0 : hn[0] / (anorm * hn[1] + bnorm);
         inf.nbe[i] = nbe;
         if (!std::isfinite(nbe)) {
             code = set_error(BSPAI_NONFINITE, "gmres_ir_solve: non-finite residual at step %d", i);
@@ -759,6 +974,7 @@ int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_
     W.norms = reinterpret_cast<double*>(base + off[9]);
     static thread_local HostFlags t_flags;  // ordinary host memory
     W.hflags = &t_flags;
+    BSPAI_TRY(choose_mgs(W));
     // the scratch keeps whatever the previous call left there: clear the parts
     // that must start at zero (solver state with its grid barrier, g)
     CUDA_TRY(cudaMemsetAsync(W.st, 0, sizeof(GmresState), s));

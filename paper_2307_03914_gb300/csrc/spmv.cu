@@ -143,6 +143,112 @@ __global__ void __launch_bounds__(256) k_bspmv(const __grid_constant__ BMDev M, 
     if (r < M.n) y[r] = from_f64<YT>(yi);
 }
 
+// one narrow-bucket value to fp32, format chosen at run time (uniform per warp)
+__device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c) {
+    switch (B.prec) {
+    case BSPAI_FP32: return decode<BSPAI_FP32>(B.val, p, B.scale, B.colscale, c);
+    case BSPAI_FP16: return decode<BSPAI_FP16>(B.val, p, B.scale, B.colscale, c);
+    case BSPAI_BF16: return decode<BSPAI_BF16>(B.val, p, B.scale, B.colscale, c);
+    default: return decode<BSPAI_E4M3>(B.val, p, B.scale, B.colscale, c);
+    }
+}
+
+// The same product as k_bspmv for Q non-empty buckets, organised for memory-
+// level parallelism: the slice bounds of all buckets, then the first W column
+// indices of every bucket, then all their values and x entries are loaded
+// before any arithmetic, and only then is each bucket's partial sum formed in
+// ascending column order (slots beyond W follow in a plain loop) and the
+// partial sums added in bucket order.  Identical operations in identical order,
+// hence identical bits.  F64: bucket 0 is the fp64 bucket.
+template <typename XT, typename YT, int Q, int W, bool F64>
+__global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M, const XT* __restrict__ x,
+                                                 YT* __restrict__ y, const int* __restrict__ jd, int64_t ldx,
+                                                 int64_t ldy, int yoff) {
+    if (jd) {
+        if (jd[1]) return;
+        const int64_t j = jd[0];
+        x += j * ldx;
+        y += (j + yoff) * ldy;
+    }
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    if (r >= (int64_t)ceil_div(M.n, kSlice) * kSlice) return;
+    int64_t base[Q];
+    int w[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        base[k] = __ldg(M.b[k].sptr + s) + lane;
+        w[k] = (int)((__ldg(M.b[k].sptr + s + 1) - (base[k] - lane)) >> 5);
+    }
+    int c[Q][W];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int l = 0; l < W; ++l) c[k][l] = l < w[k] ? __ldg(M.b[k].col + base[k] + 32 * l) : -1;
+    float v[Q][W], xf[Q][W];
+    double vd[W], xd[W];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            const int cc = c[k][l];
+            if (cc >= 0) {
+                if (F64 && k == 0) {
+                    vd[l] = __ldg(reinterpret_cast<const double*>(M.b[0].val) + base[0] + 32 * l);
+                    xd[l] = (double)__ldg(x + cc);
+                } else {
+                    v[k][l] = decode_rt(M.b[k], base[k] + 32 * l, cc);
+                    xf[k][l] = to_f32<XT>(__ldg(x + cc));
+                }
+            }
+        }
+    }
+    double yi = 0.0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const BucketDev& B = M.b[k];
+        if (F64 && k == 0) {
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < W; ++l)
+                if (c[k][l] >= 0) acc = __dadd_rn(acc, __dmul_rn(vd[l], xd[l]));
+            for (int l = W; l < w[k]; ++l) {
+                const int cc = __ldg(B.col + base[k] + 32 * l);
+                if (cc >= 0)
+                    acc = __dadd_rn(acc, __dmul_rn(__ldg(reinterpret_cast<const double*>(B.val) + base[k] + 32 * l),
+                                                   (double)__ldg(x + cc)));
+            }
+            yi = __dadd_rn(yi, acc);
+        } else {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < W; ++l)
+                if (c[k][l] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[k][l], xf[k][l]));
+            for (int l = W; l < w[k]; ++l) {
+                const int cc = __ldg(B.col + base[k] + 32 * l);
+                if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(decode_rt(B, base[k] + 32 * l, cc), to_f32<XT>(__ldg(x + cc))));
+            }
+            yi = __dadd_rn(yi, (double)acc);
+        }
+    }
+    if (r < M.n) y[r] = from_f64<YT>(yi);
+}
+
+template <typename XT, typename YT>
+using BspmvFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int);
+
+// pick the k_bspmv_q instance for (Q, W, F64); null if none fits
+template <typename XT, typename YT>
+static BspmvFn<XT, YT> pick_q(int Q, int W, bool f64) {
+#define BSPAI_PICK(q, w)                                                                  \
+    if (Q == q && W == w) return f64 ? (BspmvFn<XT, YT>)k_bspmv_q<XT, YT, q, w, true>      \
+                                     : (BspmvFn<XT, YT>)k_bspmv_q<XT, YT, q, w, false>;
+    BSPAI_PICK(1, 4) BSPAI_PICK(1, 8) BSPAI_PICK(2, 4) BSPAI_PICK(2, 8) BSPAI_PICK(3, 4) BSPAI_PICK(4, 4)
+#undef BSPAI_PICK
+    return nullptr;
+}
+
 BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     BMDev d{};
     d.n = S.n;
@@ -153,7 +259,37 @@ BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     d.b[0].col = S.col;
     d.b[0].val = val;
     d.b[0].colscale = nullptr;
+    d.b[0].nnz = -1;
+    d.b[0].maxw = -1;
     return d;
+}
+
+// Buckets that contribute nothing (dropped, or with no entries) are left out:
+// their partial sums are +0 and adding +0 to a sum that is never -0 changes nothing.
+static BMDev compact_buckets(const BMDev& M) {
+    BMDev c = M;
+    c.q = 0;
+    for (int k = 0; k < M.q; ++k)
+        if (M.b[k].prec != BSPAI_DROP && M.b[k].nnz != 0) c.b[c.q++] = M.b[k];
+    return c;
+}
+
+template <typename XT, typename YT>
+static void launch_typed(const BMDev& M0, const XT* x, YT* y, const int* jd, int64_t ldx, int64_t ldy, int yoff,
+                         unsigned grid, cudaStream_t s) {
+    const BMDev M = compact_buckets(M0);
+    int maxw = 0;
+    bool known = true;
+    for (int k = 0; k < M.q; ++k) {
+        if (M.b[k].maxw < 0) known = false;
+        maxw = M.b[k].maxw > maxw ? M.b[k].maxw : maxw;
+    }
+    const int W = (M.q <= 2 && (!known || maxw > 4)) ? 8 : 4;
+    BspmvFn<XT, YT> fn = M.q >= 1 ? pick_q<XT, YT>(M.q, W, M.b[0].prec == BSPAI_FP64) : nullptr;
+    if (fn)
+        fn<<<grid, 256, 0, s>>>(M, x, y, jd, ldx, ldy, yoff);
+    else
+        k_bspmv<XT, YT><<<grid, 256, 0, s>>>(M, x, y, jd, ldx, ldy, yoff);
 }
 
 int launch_bspmv_idx(const BMDev& M, const void* x, int x_prec, void* y, int y_prec, const int* jd,
@@ -162,13 +298,13 @@ int launch_bspmv_idx(const BMDev& M, const void* x, int x_prec, void* y, int y_p
     const int64_t rows = ceil_div(M.n, kSlice) * kSlice;
     const unsigned grid = (unsigned)ceil_div(rows, 256);
     if (x_prec == BSPAI_FP64 && y_prec == BSPAI_FP64)
-        k_bspmv<double, double><<<grid, 256, 0, s>>>(M, (const double*)x, (double*)y, jd, ldx, ldy, yoff);
+        launch_typed<double, double>(M, (const double*)x, (double*)y, jd, ldx, ldy, yoff, grid, s);
     else if (x_prec == BSPAI_FP64 && y_prec == BSPAI_FP32)
-        k_bspmv<double, float><<<grid, 256, 0, s>>>(M, (const double*)x, (float*)y, jd, ldx, ldy, yoff);
+        launch_typed<double, float>(M, (const double*)x, (float*)y, jd, ldx, ldy, yoff, grid, s);
     else if (x_prec == BSPAI_FP32 && y_prec == BSPAI_FP64)
-        k_bspmv<float, double><<<grid, 256, 0, s>>>(M, (const float*)x, (double*)y, jd, ldx, ldy, yoff);
+        launch_typed<float, double>(M, (const float*)x, (double*)y, jd, ldx, ldy, yoff, grid, s);
     else if (x_prec == BSPAI_FP32 && y_prec == BSPAI_FP32)
-        k_bspmv<float, float><<<grid, 256, 0, s>>>(M, (const float*)x, (float*)y, jd, ldx, ldy, yoff);
+        launch_typed<float, float>(M, (const float*)x, (float*)y, jd, ldx, ldy, yoff, grid, s);
     else
         return set_error(BSPAI_ERR_UNSUPPORTED, "bspmv: x/y precision must be FP64 or FP32");
     note_launch();
@@ -195,6 +331,8 @@ BMDev bspai_bucketed::dev() const {
         d.b[k].col = b[k].col;
         d.b[k].val = val[k];
         d.b[k].colscale = precs[k] == BSPAI_E4M3 ? colscale : nullptr;
+        d.b[k].nnz = nnz_k[k];
+        d.b[k].maxw = maxw[k];
     }
     return d;
 }
