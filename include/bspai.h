@@ -173,6 +173,12 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* pattern, double spai_ep
 int bspai_M_export(bspai_M_h M, int32_t* row_ptr, int32_t* col, float* val, float* resid,
                    bspai_stream_t s);
 
+/* Creates an M handle from a sparse approximate inverse computed elsewhere:
+ * Mcsr holds M (device CSR, fp64 values, rounded once to u_f = fp32).  The
+ * handle behaves like one from bspai_build (bucketing, x0 = M b), with zero
+ * column residuals.  Only u_f = BSPAI_FP32. */
+int bspai_M_create(const bspai_csr_t* Mcsr, bspai_prec_t u_f, bspai_stream_t s, bspai_M_h* M_out);
+
 /* y = M x with the unbucketed M in u_f = fp32 (x rounded to fp32, fp32
  * products and sums), y stored in fp64: x0 = M b of Alg 3.1.  Device vectors. */
 int bspai_apply_uf(bspai_M_h M, const double* x, double* y, bspai_stream_t s);
@@ -189,6 +195,18 @@ int bspai_apply_uf(bspai_M_h M, const double* x, double* y, bspai_stream_t s);
  * M may be freed afterwards. */
 int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q,
                  bspai_stream_t s, bspai_BM_h* out, bspai_bucket_info_t* info);
+
+/* Bucketing of a batch of nsys independent systems stacked block-diagonally in
+ * M (all systems built by one bspai_build call on the block-diagonal A and
+ * pattern): system s owns rows row_off[s] .. row_off[s+1]-1 (device int32,
+ * nsys + 1 entries, multiples of 32, row_off[0] = 0, row_off[nsys] = n; rows
+ * that pad a system to a multiple of 32 have no entries).  Each system is
+ * bucketed exactly as bspai_bucket would bucket it alone: its own ||M_s||_inf,
+ * thresholds and fp16 scale (eq. nint per system).  info: bucket counts over
+ * the whole batch, norm_inf = max_s ||M_s||_inf, thresholds of system 0. */
+int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, double bucket_eps,
+                         const int32_t* precs, int32_t q, bspai_stream_t s, bspai_BM_h* out,
+                         bspai_bucket_info_t* info);
 
 /* Per nonzero of M in CSR order: bucket id (0-based) and the stored value the
  * product uses (scale applied), as fp64.  Device buffers of length nnz(M);
@@ -250,6 +268,28 @@ int gmres_ir_solve(const bspai_csr_t* A, const double* b, bspai_BM_h M_bucketed,
                    bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, bspai_prec_t u_p,
                    double tol, const bspai_opts_t* opts, double* x, bspai_stream_t s,
                    bspai_solve_info_t* info);
+
+/* ------------------------------------------------------------------ adjoint */
+/* Operators for the adjoint system A^T lambda = g (a differentiation
+ * extension; Alg 3.1 applied to A^T with the transposed bucketed M as left
+ * preconditioner).  Each returns a new library-owned handle:
+ *   bspai_matrix_transpose: A^T with the same fp64 / fp32 values (SELL-32);
+ *   bspai_M_transpose:      M^T in u_f (for x0 = M^T g);
+ *   bspai_bucket_transpose: M^T keeping every entry's bucket and stored value
+ *     (fp16 bucket scales unchanged; an e4m3 bucket's per-column scales of M
+ *     become per-row scales of M^T), so M^T v is the exact transpose of the
+ *     operator bspai_apply uses.  bspai_bucket_export is not available on it.
+ * Solve with gmres_ir_solve_h(At, g, BMt, Mt, ...). */
+int bspai_matrix_transpose(bspai_A_h A, bspai_stream_t s, bspai_A_h* At);
+int bspai_M_transpose(bspai_M_h M, bspai_stream_t s, bspai_M_h* Mt);
+int bspai_bucket_transpose(bspai_BM_h BM, bspai_stream_t s, bspai_BM_h* BMt);
+
+/* Gradient of a loss L(x) with respect to the nonzeros of A, where A x = b and
+ * lambda = A^-T dL/dx: dA[p] = -lambda_i x_j for the p-th nonzero (i, j) of
+ * A's CSR (fp64, one rounding).  A: caller CSR (values unused); lambda, x: device
+ * fp64 length n; dA: device fp64 length nnz(A).  (dL/db = lambda.) */
+int bspai_adjoint_grad_A(const bspai_csr_t* A, const double* lambda, const double* x, double* dA,
+                         bspai_stream_t s);
 
 /* Same as gmres_ir_solve with A already prepared by bspai_matrix_create. */
 int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,

@@ -289,6 +289,38 @@ def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, i
                 dx=dx[:steps].tolist(), stop=stop.value)
 
 
+def transpose_csr(row_ptr, col, val):
+    """CSR of the transpose (columns ascending), via scipy."""
+    import scipy.sparse as sp
+
+    n = len(row_ptr) - 1
+    T = sp.csr_matrix((np.asarray(val, np.float64), np.asarray(col), np.asarray(row_ptr)), shape=(n, n)).T.tocsr()
+    T.sort_indices()
+    return T.indptr.astype(np.int32), T.indices.astype(np.int32), T.data.astype(np.float64)
+
+
+class _Csr:
+    def __init__(self, n, row_ptr, col, val):
+        self.n, self.row_ptr, self.col, self.val = n, row_ptr, col, val
+
+
+def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
+    """Adjoint of x = A^-1 b for a loss with dL/dx = g: lambda = A^-T g by the
+    refinement driver in fp64 (u_g = u_p = fp64, tau = 1e-12) on A^T, left-
+    preconditioned by M^T (q = 1, fp64); dL/db = lambda and dL/dA_ij =
+    -lambda_i x_j on the nonzeros of A.  Pinned by dense solves and central
+    finite differences (tests)."""
+    trp, tcol, tval = transpose_csr(A.row_ptr, A.col, A.val)
+    mrp, mcol, mval = transpose_csr(P.row_ptr, P.col, muf)
+    At = _Csr(A.n, trp, tcol, tval)
+    S = System(At, mrp, mcol, mval, np.zeros(len(mval), np.int8), ["fp64"])
+    out = gmres_ir(S, mval, g, "fp64", "fp64", 1e-12, kmax, imax)
+    lam = out["x"]
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    dA = -lam[rows] * np.asarray(x)[A.col]
+    return dict(lam=lam, dA=dA, db=lam, info=out)
+
+
 def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None) -> dict:
     """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR."""
     A, P = wl["A"], wl["pattern"]

@@ -1,0 +1,84 @@
+"""torch.autograd.Function for x = A^-1 b computed by BSPAI-GMRES-IR.
+
+Forward: SPAI build (Alg 2.1, fixed pattern), bucketing (Alg 2.2) and
+GMRES-IR (Alg 3.1) for every right-hand side.  Backward, for a loss L(x):
+lambda = A^-T dL/dx by BSPAI-GMRES-IR on A^T, left-preconditioned by the
+transposed bucketed M; dL/db = lambda and dL/dA_ij = -lambda_i x_j on the
+nonzeros of A.  The preconditioner is a function of A but does not change the
+solution, so no derivative flows through it.  Every step runs in the CUDA
+library through the C ABI; this module only sequences the calls.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import bspai as B
+
+
+@dataclass
+class SolverSettings:
+    spai_eps: float = 0.3
+    bucket_eps: float = 2.0 ** -16
+    precs: list = field(default_factory=lambda: ["fp64", "fp32", "fp16"])
+    u_g: str = "fp32"
+    u_p: str = "fp32"
+    tol: float = 1e-4
+
+
+class BspaiSolve(torch.autograd.Function):
+    """x = BspaiSolve.apply(a_val, b, row_ptr, col, pattern, settings)
+
+    a_val: (nnz,) float64 CUDA tensor, the values of A in CSR order;
+    b: (n,) or (nrhs, n) float64 CUDA tensor; row_ptr, col: int32 CUDA
+    tensors of A's CSR structure; pattern: DeviceCSR of M's pattern."""
+
+    @staticmethod
+    def forward(ctx, a_val, b, row_ptr, col, pattern, settings: SolverSettings):
+        n = int(row_ptr.numel() - 1)
+        A = B.DeviceCSR(n, row_ptr, col, a_val.detach().contiguous())
+        Ah = B.matrix_create(A)
+        M, _ = B.bspai_build(A, pattern, settings.spai_eps)
+        BM, _ = B.bspai_bucket(M, settings.bucket_eps, settings.precs)
+        bb = b.detach().reshape(-1, n).contiguous()
+        x = torch.empty_like(bb)
+        infos = []
+        for r in range(bb.shape[0]):
+            info = B.gmres_ir_solve(Ah, bb[r], BM, M, x[r], u_g=settings.u_g, u_p=settings.u_p, tol=settings.tol)
+            if info["status"] != B.OK:
+                raise B.BspaiError(info["status"], f"forward solve of right-hand side {r}: {info}")
+            infos.append(info)
+        ctx.handles = (A, Ah, M, BM, settings)
+        ctx.infos = infos
+        ctx.b_shape = b.shape
+        ctx.save_for_backward(x)
+        return x.reshape(b.shape)
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        A, Ah, M, BM, settings = ctx.handles
+        n = A.n
+        At = B.matrix_transpose(Ah)
+        Mt = B.M_transpose(M)
+        BMt = B.bucket_transpose(BM)
+        g = gx.detach().reshape(-1, n).contiguous()
+        lam = torch.empty_like(g)
+        grad_a = torch.zeros_like(A.val)
+        tmp = torch.empty_like(A.val)
+        ctx.adjoint_infos = []
+        for r in range(g.shape[0]):
+            info = B.gmres_ir_solve(At, g[r], BMt, Mt, lam[r], u_g=settings.u_g, u_p=settings.u_p,
+                                    tol=settings.tol)
+            if info["status"] != B.OK:
+                raise B.BspaiError(info["status"], f"adjoint solve of right-hand side {r}: {info}")
+            ctx.adjoint_infos.append(info)
+            B.adjoint_grad_A(A, lam[r], x[r], tmp)
+            grad_a += tmp
+        return grad_a, lam.reshape(ctx.b_shape), None, None, None, None
+
+
+def solve(a_val, b, row_ptr, col, pattern, settings: SolverSettings | None = None):
+    """Differentiable x = A^-1 b (see BspaiSolve)."""
+    return BspaiSolve.apply(a_val, b, row_ptr, col, pattern, settings or SolverSettings())

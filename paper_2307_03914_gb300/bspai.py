@@ -93,11 +93,18 @@ _sig("bspai_residual", _i, [_vp, _vp, _vp, _vp, _vp])
 _sig("bspai_spmv_up", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_build", _i, [C.POINTER(CsrT), C.POINTER(CsrT), _d, _i, _vp, C.POINTER(_vp), C.POINTER(BuildInfo)])
 _sig("bspai_M_export", _i, [_vp, _vp, _vp, _vp, _vp, _vp])
+_sig("bspai_M_create", _i, [C.POINTER(CsrT), _i, _vp, C.POINTER(_vp)])
 _sig("bspai_apply_uf", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_bucket", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINTER(_vp), C.POINTER(BucketInfo)])
 _sig("bspai_bucket_export", _i, [_vp, _vp, _vp, _vp])
+_sig("bspai_bucket_batched", _i, [_vp, _vp, C.c_int32, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINTER(_vp),
+                                  C.POINTER(BucketInfo)])
 _sig("bspai_apply", _i, [_vp, _vp, _i, _vp, _i, _vp])
 _sig("bspai_gmres", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
+_sig("bspai_matrix_transpose", _i, [_vp, _vp, C.POINTER(_vp)])
+_sig("bspai_M_transpose", _i, [_vp, _vp, C.POINTER(_vp)])
+_sig("bspai_bucket_transpose", _i, [_vp, _vp, C.POINTER(_vp)])
+_sig("bspai_adjoint_grad_A", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _vp])
 _sig("bspai_gmres_noalloc", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
 _sig("gmres_ir_solve", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                             C.POINTER(SolveInfo)])
@@ -231,6 +238,13 @@ def bspai_build(A: DeviceCSR, P: DeviceCSR, spai_eps: float, u_f: str = "fp32", 
     return MHandle(h.value), d
 
 
+def M_create(Mcsr: DeviceCSR, u_f: str = "fp32", stream=None) -> MHandle:
+    """M handle from given values (CSR, fp64, rounded to u_f)."""
+    h = C.c_void_p()
+    _check(_lib.bspai_M_create(C.byref(Mcsr.c()), PREC[u_f], _stream(stream), C.byref(h)))
+    return MHandle(h.value)
+
+
 def M_export(M: MHandle, n: int, nnz: int, stream=None):
     dev = "cuda"
     rp = torch.empty(n + 1, dtype=torch.int32, device=dev)
@@ -260,6 +274,23 @@ def bspai_bucket(M: MHandle, bucket_eps: float, precs, stream=None):
     return BMHandle(h.value), d
 
 
+def _bucket_info(info: BucketInfo) -> dict:
+    q = info.q
+    return dict(q=q, precs=[PREC_NAME[info.precs[k]] for k in range(q)], nnz_k=list(info.nnz_k[:q]),
+                slots_k=list(info.slots_k[:q]), thresholds=list(info.thresholds[:q]), norm_inf=info.norm_inf,
+                storage_pct=info.storage_pct, storage_pct_last8=info.storage_pct_last8, bytes=info.bytes)
+
+
+def bspai_bucket_batched(M: MHandle, row_off, bucket_eps: float, precs, stream=None):
+    """Per-system bucketing of a block-diagonal batch (row_off: device int32, nsys + 1)."""
+    arr = (C.c_int32 * len(precs))(*[PREC[p] if isinstance(p, str) else int(p) for p in precs])
+    h = C.c_void_p()
+    info = BucketInfo()
+    _check(_lib.bspai_bucket_batched(M.ptr, _ptr(row_off), int(row_off.numel() - 1), float(bucket_eps), arr,
+                                     len(precs), _stream(stream), C.byref(h), C.byref(info)))
+    return BMHandle(h.value), _bucket_info(info)
+
+
 def bucket_export(BM: BMHandle, nnz: int, stream=None):
     ids = torch.empty(nnz, dtype=torch.int8, device="cuda")
     stored = torch.empty(nnz, dtype=torch.float64, device="cuda")
@@ -272,6 +303,30 @@ def apply(BM: BMHandle, x, y, stream=None):
     yp = PREC["fp64"] if y.dtype == torch.float64 else PREC["fp32"]
     _check(_lib.bspai_apply(BM.ptr, _ptr(x), xp, _ptr(y), yp, _stream(stream)))
     return y
+
+
+# ------------------------------------------------------------------ adjoint
+def matrix_transpose(Ah: AHandle, stream=None) -> AHandle:
+    h = C.c_void_p()
+    _check(_lib.bspai_matrix_transpose(Ah.ptr, _stream(stream), C.byref(h)))
+    return AHandle(h.value)
+
+
+def M_transpose(M: MHandle, stream=None) -> MHandle:
+    h = C.c_void_p()
+    _check(_lib.bspai_M_transpose(M.ptr, _stream(stream), C.byref(h)))
+    return MHandle(h.value)
+
+
+def bucket_transpose(BM: BMHandle, stream=None) -> BMHandle:
+    h = C.c_void_p()
+    _check(_lib.bspai_bucket_transpose(BM.ptr, _stream(stream), C.byref(h)))
+    return BMHandle(h.value)
+
+
+def adjoint_grad_A(A: DeviceCSR, lam, x, dA, stream=None):
+    _check(_lib.bspai_adjoint_grad_A(C.byref(A.c()), _ptr(lam), _ptr(x), _ptr(dA), _stream(stream)))
+    return dA
 
 
 # ------------------------------------------------------------------ solves

@@ -12,6 +12,7 @@
 // per bucket, e4m3 with a power-of-two fp32 scale per column, so that the
 // narrow formats' exponent range does not flush the small entries.
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -58,22 +59,32 @@ struct PackDst {
     float scale[8];
 };
 
+// In a batch of independent systems stacked block-diagonally, every 32-row
+// slice belongs to one system (slice_seg[s]); each system gets its own
+// ||M_s||_inf, thresholds and fp16 scales, exactly as if it were bucketed
+// alone.  slice_seg = null means one system.
+__device__ __forceinline__ int seg_of(const int32_t* slice_seg, int64_t slice) {
+    return slice_seg ? slice_seg[slice] : 0;
+}
+
 __global__ void k_norm_rows(int n, const int64_t* __restrict__ sptr, const float* __restrict__ val,
-                            const int32_t* __restrict__ rowlen, double* __restrict__ norm) {
+                            const int32_t* __restrict__ rowlen, const int32_t* __restrict__ slice_seg,
+                            double* __restrict__ norm) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int64_t b = sptr[r >> 5] + (r & 31);
     const int len = rowlen[r];
     double s = 0.0;
     for (int l = 0; l < len; ++l) s = __dadd_rn(s, fabs((double)val[b + (int64_t)l * kSlice]));
-    atomic_max_nonneg(norm, s);
+    atomic_max_nonneg(norm + seg_of(slice_seg, r >> 5), s);
 }
 
-__global__ void k_thresholds(const __grid_constant__ BucketParams P, const double* __restrict__ norm,
+__global__ void k_thresholds(const __grid_constant__ BucketParams P, int nseg, const double* __restrict__ norm,
                              double* __restrict__ thr) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    thr[0] = __longlong_as_double(0x7ff0000000000000LL);
-    for (int k = 1; k < P.q; ++k) thr[k] = __ddiv_rn(__dmul_rn(P.eps, *norm), P.uk[k]);
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nseg) return;
+    thr[sg * 8] = __longlong_as_double(0x7ff0000000000000LL);
+    for (int k = 1; k < P.q; ++k) thr[sg * 8 + k] = __ddiv_rn(__dmul_rn(P.eps, norm[sg]), P.uk[k]);
 }
 
 __device__ __forceinline__ int classify(double a, const double* thr, int q) {
@@ -94,12 +105,13 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
                                                   const double* __restrict__ thr_g, int8_t* __restrict__ id,
                                                   int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
                                                   float* __restrict__ bmax, float* __restrict__ colmax,
-                                                  int* __restrict__ wmax) {
+                                                  int* __restrict__ wmax, const int32_t* __restrict__ slice_seg) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nslices * kSlice) return;
+    const int sg = seg_of(slice_seg, r >> 5);
     double thr[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) thr[k] = k < P.q ? thr_g[k] : 0.0;
+    for (int k = 0; k < 8; ++k) thr[k] = k < P.q ? thr_g[sg * 8 + k] : 0.0;
     int cnt[8];
     float mx[8];
 #pragma unroll
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
         if (lane == 0) {
             widths[(int64_t)k * (nslices + 1) + (r >> 5)] = (int64_t)w * kSlice;
             if (c) atomicAdd(nnzk + k, (unsigned long long)c);
-            if (m > 0.0f) atomic_max_nonneg(bmax + k, m);
+            if (m > 0.0f) atomic_max_nonneg(bmax + sg * 8 + k, m);
             if (w) atomicMax(wmax + k, w);
         }
     }
@@ -159,11 +171,19 @@ __device__ __forceinline__ float pow2_scale(float maxabs_f, double fmax) {
     return (float)ldexp(1.0, e);
 }
 
-__global__ void k_bucket_scales(const __grid_constant__ BucketParams P, const float* __restrict__ bmax,
+__global__ void k_bucket_scales(const __grid_constant__ BucketParams P, int nseg, const float* __restrict__ bmax,
                                 float* __restrict__ scale) {
-    const int k = threadIdx.x;
-    if (k >= P.q) return;
-    scale[k] = P.precs[k] == BSPAI_FP16 ? pow2_scale(bmax[k], 65504.0) : 1.0f;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = i & 7;
+    if (i >= nseg * 8 || k >= P.q) return;
+    scale[i] = P.precs[k] == BSPAI_FP16 ? pow2_scale(bmax[i], 65504.0) : 1.0f;
+}
+
+// per-slice copy of an fp16 bucket's scale (batches of several systems)
+__global__ void k_slice_scales(int nslices, const int32_t* __restrict__ slice_seg, const float* __restrict__ scale,
+                               int k, float* __restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nslices) out[s] = scale[slice_seg[s] * 8 + k];
 }
 
 __global__ void k_col_scales(int n, const float* __restrict__ colmax, float* __restrict__ colscale) {
@@ -199,12 +219,14 @@ __device__ __forceinline__ void store_zero(void* dst, int64_t p, int prec) {
 __global__ void __launch_bounds__(256) k_pack(int n, int nslices, const int64_t* __restrict__ sptr,
                                               const int32_t* __restrict__ col, const float* __restrict__ val,
                                               const int32_t* __restrict__ rowlen, const int8_t* __restrict__ id,
-                                              const __grid_constant__ PackDst D, const float* __restrict__ scale,
-                                              const float* __restrict__ colscale) {
+                                              const __grid_constant__ PackDst D, const float* __restrict__ scale_g,
+                                              const float* __restrict__ colscale,
+                                              const int32_t* __restrict__ slice_seg) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nslices * kSlice) return;
     const int64_t s = r >> 5;
     const int lane = (int)(r & 31);
+    const float* scale = scale_g + seg_of(slice_seg, s) * 8;
     int cnt[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) cnt[k] = 0;
@@ -271,7 +293,10 @@ __global__ void k_bucket_export(int n, const int64_t* __restrict__ msptr, const 
             switch (D.prec) {
             case BSPAI_FP64: v = reinterpret_cast<const double*>(D.val)[p]; break;
             case BSPAI_FP32: v = reinterpret_cast<const float*>(D.val)[p]; break;
-            case BSPAI_FP16: v = (double)__half2float(reinterpret_cast<const __half*>(D.val)[p]) * D.scale; break;
+            case BSPAI_FP16:
+                v = (double)__half2float(reinterpret_cast<const __half*>(D.val)[p]) *
+                    (D.slicescale ? D.slicescale[s] : D.scale);
+                break;
             case BSPAI_BF16: v = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(D.val)[p]); break;
             case BSPAI_E4M3: {
                 __nv_fp8_e4m3 e;
@@ -290,11 +315,11 @@ __global__ void k_bucket_export(int n, const int64_t* __restrict__ msptr, const 
 
 using namespace bspai;
 
-extern "C" {
-
-int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, bspai_stream_t st,
-                 bspai_BM_h* out, bspai_bucket_info_t* info) {
-    cudaStream_t s = (cudaStream_t)st;
+// Bucketing of M, of one system (slice_seg = null, nseg = 1) or of nseg
+// independent systems stacked block-diagonally (slice_seg: system of every
+// 32-row slice).
+static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, const int32_t* slice_seg,
+                       int nseg, cudaStream_t s, bspai_BM_h* out, bspai_bucket_info_t* info) {
     if (!out) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: null out");
     *out = nullptr;
     if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: bad M handle");
@@ -352,12 +377,12 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     if ((rc = dalloc_t(&B->mrowlen, (size_t)n, s))) return fail(rc);
     if ((rc = dalloc_t(&B->mcsr_row_ptr, (size_t)n + 1, s))) return fail(rc);
     if ((rc = dalloc_t(&B->id_sell, (size_t)M->sell.slots, s))) return fail(rc);
-    if ((rc = dalloc_t(&d_norm, 1, s))) return fail(rc);
-    if ((rc = dalloc_t(&d_thr, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_norm, (size_t)nseg, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_thr, (size_t)nseg * 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_w, (size_t)q * (nsl + 1), s))) return fail(rc);
     if ((rc = dalloc_t(&d_nnzk, 8, s))) return fail(rc);
-    if ((rc = dalloc_t(&d_bmax, 8, s))) return fail(rc);
-    if ((rc = dalloc_t(&d_scale, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_bmax, (size_t)nseg * 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_scale, (size_t)nseg * 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_wmax, 8, s))) return fail(rc);
     if (n_e4m3) {
         if ((rc = dalloc_t(&d_colmax, (size_t)n, s))) return fail(rc);
@@ -368,32 +393,33 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     if (!e) e = cudaMemcpyAsync(B->msell.col, M->sell.col, sizeof(int32_t) * (size_t)M->sell.slots, cudaMemcpyDeviceToDevice, s);
     if (!e) e = cudaMemcpyAsync(B->mrowlen, M->rowlen, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
     if (!e) e = cudaMemcpyAsync(B->mcsr_row_ptr, M->csr_row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s);
-    if (!e) e = cudaMemsetAsync(d_norm, 0, sizeof(double), s);
+    if (!e) e = cudaMemsetAsync(d_norm, 0, sizeof(double) * (size_t)nseg, s);
     if (!e) e = cudaMemsetAsync(d_nnzk, 0, 8 * sizeof(unsigned long long), s);
-    if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(float), s);
+    if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(float) * (size_t)nseg, s);
     if (!e) e = cudaMemsetAsync(d_wmax, 0, 8 * sizeof(int), s);
     if (!e) e = cudaMemsetAsync(d_w, 0, sizeof(int64_t) * (size_t)q * (nsl + 1), s);
     if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(float) * (size_t)n, s);
     if (e) return fail(cuda_error(e, "bspai_bucket setup", __FILE__, __LINE__));
     const unsigned g_rows = (unsigned)ceil_div((int64_t)nsl * kSlice, 256);
+    const unsigned g_seg = (unsigned)ceil_div(nseg, 256), g_seg8 = (unsigned)ceil_div((int64_t)nseg * 8, 256);
     if (n > 0) {
-        k_norm_rows<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, M->sell.sptr, M->val, M->rowlen, d_norm);
+        k_norm_rows<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, M->sell.sptr, M->val, M->rowlen, slice_seg, d_norm);
         note_launch();
-        k_thresholds<<<1, 32, 0, s>>>(P, d_norm, d_thr);
+        k_thresholds<<<g_seg, 256, 0, s>>>(P, nseg, d_norm, d_thr);
         note_launch();
         k_classify<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, P, d_thr,
-                                          B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax);
+                                          B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax, slice_seg);
         note_launch();
-        k_bucket_scales<<<1, 32, 0, s>>>(P, d_bmax, d_scale);
+        k_bucket_scales<<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
         note_launch();
         if (d_colmax) {
             k_col_scales<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, d_colmax, B->colscale);
             note_launch();
         }
     } else {
-        k_thresholds<<<1, 32, 0, s>>>(P, d_norm, d_thr);
+        k_thresholds<<<g_seg, 256, 0, s>>>(P, nseg, d_norm, d_thr);
         note_launch();
-        k_bucket_scales<<<1, 32, 0, s>>>(P, d_bmax, d_scale);
+        k_bucket_scales<<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
         note_launch();
     }
     if ((e = cudaGetLastError())) return fail(cuda_error(e, "bucket classify", __FILE__, __LINE__));
@@ -407,7 +433,7 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     int64_t slots[8] = {0};
     unsigned long long nnzk[8] = {0};
     double hthr[8] = {0};
-    double hnorm = 0.0;
+    std::vector<double> hnorms((size_t)nseg, 0.0);
     float hscale[8] = {0};
     int hwmax[8] = {0};
     for (int k = 0; k < q; ++k)
@@ -415,11 +441,13 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
             return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
     e = cudaMemcpyAsync(nnzk, d_nnzk, sizeof nnzk, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hthr, d_thr, sizeof hthr, cudaMemcpyDeviceToHost, s);
-    if (!e) e = cudaMemcpyAsync(&hnorm, d_norm, sizeof hnorm, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hnorms.data(), d_norm, sizeof(double) * (size_t)nseg, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hscale, d_scale, sizeof hscale, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hwmax, d_wmax, sizeof hwmax, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
+    double hnorm = 0.0;
+    for (double v : hnorms) hnorm = v > hnorm ? v : hnorm;
     PackDst D{};
     D.q = q;
     int64_t bytes = 0;
@@ -445,9 +473,20 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     if (B->colscale) bytes += (int64_t)sizeof(float) * n;
     if (n > 0) {
         k_pack<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, B->id_sell, D, d_scale,
-                                      B->colscale);
+                                      B->colscale, slice_seg);
         note_launch();
         if ((e = cudaGetLastError())) return fail(cuda_error(e, "k_pack", __FILE__, __LINE__));
+    }
+    if (slice_seg && nsl > 0) {
+        // each system's fp16 scale, per 32-row slice, for the SpMV kernels
+        for (int k = 0; k < q; ++k) {
+            if (precs[k] != BSPAI_FP16) continue;
+            if ((rc = dalloc_t(&B->sscale[k], (size_t)nsl, s))) return fail(rc);
+            k_slice_scales<<<(unsigned)ceil_div(nsl, 256), 256, 0, s>>>(nsl, slice_seg, d_scale, k, B->sscale[k]);
+            note_launch();
+            bytes += (int64_t)sizeof(float) * nsl;
+        }
+        if ((e = cudaGetLastError())) return fail(cuda_error(e, "k_slice_scales", __FILE__, __LINE__));
     }
     cleanup();
     if (info) {
@@ -482,9 +521,67 @@ int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q
     return BSPAI_OK;
 }
 
+// system of every 32-row slice from the system row offsets (multiples of 32)
+__global__ void k_slice_seg(int nseg, const int32_t* __restrict__ row_off, int32_t* __restrict__ slice_seg,
+                            int* __restrict__ bad) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nseg) return;
+    const int a = row_off[sg], b = row_off[sg + 1];
+    if ((a & 31) || (b & 31) || b < a) {
+        atomicOr(bad, 1);
+        return;
+    }
+    for (int s = a >> 5; s < (b >> 5); ++s) slice_seg[s] = sg;
+}
+
+extern "C" {
+
+int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, bspai_stream_t st,
+                 bspai_BM_h* out, bspai_bucket_info_t* info) {
+    return bucket_impl(M, bucket_eps, precs, q, nullptr, 1, (cudaStream_t)st, out, info);
+}
+
+int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, double bucket_eps, const int32_t* precs,
+                         int32_t q, bspai_stream_t st, bspai_BM_h* out, bspai_bucket_info_t* info) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!out) return set_error(BSPAI_ERR_INVALID, "bspai_bucket_batched: null out");
+    *out = nullptr;
+    if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket_batched: bad M handle");
+    if (!row_off || nsys < 1) return set_error(BSPAI_ERR_INVALID, "bspai_bucket_batched: need nsys >= 1 offsets");
+    int last = -1, first = -1;
+    CUDA_TRY(cudaMemcpyAsync(&first, row_off, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&last, row_off + nsys, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (first != 0 || last != M->n)
+        return set_error(BSPAI_ERR_INVALID, "bspai_bucket_batched: row_off must run from 0 to n = %d", M->n);
+    const int nsl = M->sell.nslices;
+    int32_t* slice_seg = nullptr;
+    int* bad = nullptr;
+    BSPAI_TRY(dalloc_t(&slice_seg, (size_t)(nsl > 0 ? nsl : 1), s));
+    BSPAI_TRY(dalloc_t(&bad, 1, s));
+    CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(slice_seg, 0, sizeof(int32_t) * (size_t)(nsl > 0 ? nsl : 1), s));
+    k_slice_seg<<<(unsigned)ceil_div(nsys, 256), 256, 0, s>>>(nsys, row_off, slice_seg, bad);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    int hbad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int rc;
+    if (hbad)
+        rc = set_error(BSPAI_ERR_INVALID, "bspai_bucket_batched: system offsets must be non-decreasing multiples of 32");
+    else
+        rc = bucket_impl(M, bucket_eps, precs, q, slice_seg, nsys, s, out, info);
+    dfree(slice_seg, s);
+    dfree(bad, s);
+    return rc;
+}
+
 int bspai_bucket_export(bspai_BM_h BM, int8_t* ids, double* stored, bspai_stream_t st) {
     cudaStream_t s = (cudaStream_t)st;
     if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket_export: bad handle");
+    if (!BM->msell.sptr)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_bucket_export: not available for a transposed bucketed M");
     if (BM->n == 0 || (!ids && !stored)) return BSPAI_OK;
     k_bucket_export<<<(unsigned)ceil_div(BM->n, 256), 256, 0, s>>>(BM->n, BM->msell.sptr, BM->mrowlen,
                                                                    BM->mcsr_row_ptr, BM->id_sell, BM->dev(), ids,

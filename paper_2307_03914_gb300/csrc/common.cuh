@@ -73,6 +73,8 @@ struct BucketDev {
     const int32_t* col;
     const void* val;           // typed by prec
     const float* colscale;     // e4m3 bucket: per-column scale (else null)
+    const float* rowscale;     // e4m3 bucket of a transposed M: per-row scale (else null)
+    const float* slicescale;   // fp16 bucket of a batch: per-slice scale (else null: use scale)
     int64_t nnz;               // entries in the bucket (-1: unknown)
     int32_t maxw;              // widest slice of the bucket in slots per row (-1: unknown)
 };
@@ -119,6 +121,8 @@ struct bspai_bucketed {
     void* val[8] = {nullptr};
     float scale[8];
     float* colscale = nullptr; // per column (e4m3 bucket)
+    float* rowscale = nullptr; // per row (e4m3 bucket of a transposed M)
+    float* sscale[8] = {nullptr}; // per 32-row slice (fp16 buckets of a batch of systems)
     int64_t nnz_k[8];
     int32_t maxw[8];           // widest slice per bucket (slots per row)
     // copy of M's structure for exporting in CSR order

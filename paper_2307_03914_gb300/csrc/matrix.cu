@@ -101,6 +101,14 @@ __global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const
     atomic_max_nonneg(out, sum);
 }
 
+int launch_row_abs_sum_max(const Sell& S, const double* val, double* out, cudaStream_t s) {
+    if (S.n == 0) return BSPAI_OK;
+    k_row_abs_sum_max<<<(unsigned)ceil_div(S.n, 256), 256, 0, s>>>(S.n, S.sptr, S.col, val, out);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    return BSPAI_OK;
+}
+
 // ------------------------------------------------------------ double-double
 // Knuth TwoSum, the "fast" variant for |a| >= |b|, and the FMA TwoProduct.
 __device__ __forceinline__ void dd_two_sum(double a, double b, double& s, double& e) {

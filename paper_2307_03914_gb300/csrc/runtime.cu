@@ -259,8 +259,10 @@ int bspai_free(void* h) {
         for (int k = 0; k < B->q; ++k) {
             sell_free(&B->b[k], s);
             dfree(B->val[k], s);
+            dfree(B->sscale[k], s);
         }
         dfree(B->colscale, s);
+        dfree(B->rowscale, s);
         sell_free(&B->msell, s);
         dfree(B->mrowlen, s);
         dfree(B->mcsr_row_ptr, s);

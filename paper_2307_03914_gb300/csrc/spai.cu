@@ -372,6 +372,39 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
     return BSPAI_OK;
 }
 
+int bspai_M_create(const bspai_csr_t* Mcsr, bspai_prec_t u_f, bspai_stream_t st, bspai_M_h* M_out) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!M_out) return set_error(BSPAI_ERR_INVALID, "bspai_M_create: null M_out");
+    *M_out = nullptr;
+    if (u_f != BSPAI_FP32) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_M_create: only u_f = FP32 is built");
+    BSPAI_TRY(validate_csr(Mcsr, true, "bspai_M_create", s));
+    const int n = Mcsr->n;
+    auto* M = new bspai_spai();
+    M->magic = kMagicM;
+    M->stream = s;
+    M->n = n;
+    M->nnz = Mcsr->nnz;
+    int rc;
+    {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        rc = sell_from_csr(n, Mcsr->row_ptr, Mcsr->col, Mcsr->val, &M->sell, nullptr, &M->val, &M->rowlen, s);
+        if (!rc) rc = dalloc_t(&M->csr_row_ptr, (size_t)n + 1, s);
+        if (!rc) rc = dalloc_t(&M->resid, (size_t)(n > 0 ? n : 1), s);
+        if (!rc) {
+            cudaError_t e = cudaMemcpyAsync(M->csr_row_ptr, Mcsr->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
+                                            cudaMemcpyDeviceToDevice, s);
+            if (!e) e = cudaMemsetAsync(M->resid, 0, sizeof(float) * (size_t)(n > 0 ? n : 1), s);
+            if (e) rc = cuda_error(e, "bspai_M_create", __FILE__, __LINE__);
+        }
+    }
+    if (rc) {
+        bspai_free(M);
+        return rc;
+    }
+    *M_out = M;
+    return BSPAI_OK;
+}
+
 int bspai_M_export(bspai_M_h M, int32_t* row_ptr, int32_t* col, float* val, float* resid, bspai_stream_t st) {
     cudaStream_t s = (cudaStream_t)st;
     if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_M_export: bad handle");

@@ -53,7 +53,10 @@ __device__ __forceinline__ float decode<BSPAI_E4M3>(const void* val, int64_t p, 
 // slots ahead of the (strictly sequential) accumulation.
 template <int PREC, typename XT>
 __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, int64_t end,
-                                                 const XT* __restrict__ x) {
+                                                 const XT* __restrict__ x, int64_t r) {
+    // e4m3 scales: per column of M, or per row of a transposed M; fp16: per bucket or per slice
+    const float* st = B.colscale ? B.colscale : B.rowscale;
+    const float sc = B.slicescale ? __ldg(B.slicescale + (r >> 5)) : B.scale;
     float acc = 0.0f;
     for (; p + 96 < end; p += 128) {
         int c[4];
@@ -63,7 +66,7 @@ __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, 
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (c[u] >= 0) {
-                v[u] = decode<PREC>(B.val, p + 32 * u, B.scale, B.colscale, c[u]);
+                v[u] = decode<PREC>(B.val, p + 32 * u, sc, st, B.colscale ? c[u] : (int)r);
                 xv[u] = to_f32<XT>(__ldg(x + c[u]));
             }
         }
@@ -74,7 +77,7 @@ __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, 
     for (; p < end; p += 32) {
         int c = __ldg(B.col + p);
         if (c >= 0) {
-            float v = decode<PREC>(B.val, p, B.scale, B.colscale, c);
+            float v = decode<PREC>(B.val, p, sc, st, B.colscale ? c : (int)r);
             acc = __fadd_rn(acc, __fmul_rn(v, to_f32<XT>(__ldg(x + c))));
         }
     }
@@ -133,10 +136,10 @@ __global__ void __launch_bounds__(256) k_bspmv(const __grid_constant__ BMDev M, 
         const int64_t end = B.sptr[s + 1];
         switch (B.prec) {
         case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT>(B, p0, end, x)); break;
-        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, p0, end, x)); break;
-        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT>(B, p0, end, x)); break;
-        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT>(B, p0, end, x)); break;
-        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT>(B, p0, end, x)); break;
+        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, p0, end, x, r)); break;
+        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT>(B, p0, end, x, r)); break;
+        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT>(B, p0, end, x, r)); break;
+        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT>(B, p0, end, x, r)); break;
         default: break;  // dropped entries are not stored
         }
     }
@@ -144,12 +147,15 @@ __global__ void __launch_bounds__(256) k_bspmv(const __grid_constant__ BMDev M, 
 }
 
 // one narrow-bucket value to fp32, format chosen at run time (uniform per warp)
-__device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c) {
+__device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c, int64_t r) {
     switch (B.prec) {
-    case BSPAI_FP32: return decode<BSPAI_FP32>(B.val, p, B.scale, B.colscale, c);
-    case BSPAI_FP16: return decode<BSPAI_FP16>(B.val, p, B.scale, B.colscale, c);
-    case BSPAI_BF16: return decode<BSPAI_BF16>(B.val, p, B.scale, B.colscale, c);
-    default: return decode<BSPAI_E4M3>(B.val, p, B.scale, B.colscale, c);
+    case BSPAI_FP32: return decode<BSPAI_FP32>(B.val, p, B.scale, nullptr, c);
+    case BSPAI_FP16:
+        return decode<BSPAI_FP16>(B.val, p, B.slicescale ? __ldg(B.slicescale + (r >> 5)) : B.scale, nullptr, c);
+    case BSPAI_BF16: return decode<BSPAI_BF16>(B.val, p, B.scale, nullptr, c);
+    default:
+        return B.colscale ? decode<BSPAI_E4M3>(B.val, p, B.scale, B.colscale, c)
+                          : decode<BSPAI_E4M3>(B.val, p, B.scale, B.rowscale, (int)r);
     }
 }
 
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
                     vd[l] = __ldg(reinterpret_cast<const double*>(M.b[0].val) + base[0] + 32 * l);
                     xd[l] = (double)__ldg(x + cc);
                 } else {
-                    v[k][l] = decode_rt(M.b[k], base[k] + 32 * l, cc);
+                    v[k][l] = decode_rt(M.b[k], base[k] + 32 * l, cc, r);
                     xf[k][l] = to_f32<XT>(__ldg(x + cc));
                 }
             }
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
                 if (c[k][l] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[k][l], xf[k][l]));
             for (int l = W; l < w[k]; ++l) {
                 const int cc = __ldg(B.col + base[k] + 32 * l);
-                if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(decode_rt(B, base[k] + 32 * l, cc), to_f32<XT>(__ldg(x + cc))));
+                if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(decode_rt(B, base[k] + 32 * l, cc, r), to_f32<XT>(__ldg(x + cc))));
             }
             yi = __dadd_rn(yi, (double)acc);
         }
@@ -259,6 +265,8 @@ BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     d.b[0].col = S.col;
     d.b[0].val = val;
     d.b[0].colscale = nullptr;
+    d.b[0].rowscale = nullptr;
+    d.b[0].slicescale = nullptr;
     d.b[0].nnz = -1;
     d.b[0].maxw = -1;
     return d;
@@ -331,6 +339,8 @@ BMDev bspai_bucketed::dev() const {
         d.b[k].col = b[k].col;
         d.b[k].val = val[k];
         d.b[k].colscale = precs[k] == BSPAI_E4M3 ? colscale : nullptr;
+        d.b[k].rowscale = precs[k] == BSPAI_E4M3 ? rowscale : nullptr;
+        d.b[k].slicescale = sscale[k];
         d.b[k].nnz = nnz_k[k];
         d.b[k].maxw = maxw[k];
     }

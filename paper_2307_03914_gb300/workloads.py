@@ -150,6 +150,50 @@ def random_sparse(n: int = 65536, k: int = 16, sigma: float = 2.0, delta: float 
     return _from_dense_rows(allc, allv)
 
 
+def lognormal_field(g: int, sigma: float = 1.0, corr: float = 8.0, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """kappa = exp(f) on a g x g grid, f a zero-mean Gaussian field with
+    standard deviation sigma and squared-exponential correlation of length
+    `corr` cells, made by filtering seeded white noise in Fourier space."""
+    rng = np.random.default_rng(seed + 7)
+    w = rng.normal(size=(g, g))
+    k = np.fft.fftfreq(g)
+    kx, ky = np.meshgrid(k, k, indexing="ij")
+    filt = np.exp(-0.5 * (2 * np.pi) ** 2 * (kx ** 2 + ky ** 2) * corr ** 2 / 2.0)
+    f = np.real(np.fft.ifft2(np.fft.fft2(w) * filt))
+    f = (f - f.mean()) / f.std() * sigma
+    return np.exp(f)
+
+
+def diffusion2d(kappa: np.ndarray) -> CSR:
+    """-div(kappa grad u) on the cell grid of `kappa` (g x g), Dirichlet u = 0
+    outside, 5-point finite volumes: face coefficient = harmonic mean of the
+    two cells' kappa (2 kappa_cell towards the boundary).  Symmetric, positive
+    definite; rows ordered r = ix + g * iy."""
+    g = kappa.shape[0]
+    n = g * g
+    kap = kappa.reshape(-1)  # index ix + g * iy with kappa[iy, ix]
+    r = np.arange(n, dtype=np.int64)
+    ix, iy = r % g, r // g
+
+    def face(a, b):
+        return 2.0 * a * b / (a + b)
+
+    cols = np.full((n, 5), -1, dtype=np.int64)
+    vals = np.zeros((n, 5))
+    diag = np.zeros(n)
+    nbrs = [(iy > 0, -g), (ix > 0, -1), (ix < g - 1, 1), (iy < g - 1, g)]
+    slot = {-g: 0, -1: 1, 1: 3, g: 4}
+    for ok, off in nbrs:
+        j = np.where(ok, r + off, r)
+        t = np.where(ok, face(kap, kap[j]), 2.0 * kap)
+        diag += t
+        cols[:, slot[off]] = np.where(ok, r + off, -1)
+        vals[:, slot[off]] = -t
+    cols[:, 2] = r
+    vals[:, 2] = diag
+    return _from_dense_rows(cols, vals)
+
+
 def pattern_of(A: CSR) -> CSR:
     """The a-priori pattern pattern(A) (values dropped)."""
     return CSR(A.n, A.row_ptr.copy(), A.col.copy(), None)
@@ -229,6 +273,11 @@ def workload(name: str, grid: int | None = None, n: int | None = None, seed: int
         A = random_sparse(nn, 16, 2.0, seed=seed)
         P = pattern_power_topk(A, 24)
         cfg = dict(spai_eps=0.3, precs=[FP64, FP32, FP16, BF16])
+    elif name == "diffusion2d":
+        g = 256 if grid is None else grid
+        A = diffusion2d(lognormal_field(g, 1.0, 8.0, seed))
+        P = pattern_of(A)
+        cfg = dict(spai_eps=0.3, precs=[FP64, FP32, FP16])
     else:
         raise ValueError(f"unknown workload {name!r}")
     x_true, b = rhs(A, seed)

@@ -38,6 +38,19 @@ def gpu_build(B, wl):
                 resid=host(res).astype(np.float64))
 
 
+def oracle_M(B, wl):
+    """The oracle's SPAI of the workload (fp64, rounded to u_f = fp32), and the
+    same matrix handed to the GPU library with bspai_M_create, so that steps
+    after the SPAI build are compared on one M that came from the oracle."""
+    import oracle as O
+
+    P = wl["pattern"]
+    sp = O.spai(wl["A"], P, wl["spai_eps"])
+    muf = O.round_to(sp["mval"], "fp32")
+    Md = B.DeviceCSR(P.n, dev(P.row_ptr.astype(np.int32)), dev(P.col.astype(np.int32)), dev(muf))
+    return B.M_create(Md), muf
+
+
 def gpu_bucket(B, M, nnz, eps, precs):
     BM, info = B.bspai_bucket(M, eps, precs)
     ids, stored = B.bucket_export(BM, nnz)

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib
+from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib, oracle_M
 from paper_2307_03914_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -73,18 +73,20 @@ def test_diagonal_pattern(B):
 
 def test_empty_and_fully_dropped_buckets(B):
     wl = _wl(W.convdiff3d(6), precs=["fp64", "fp32", "fp16", "e4m3"])
-    g = gpu_build(B, wl)
+    M, muf = oracle_M(B, wl)
     P = wl["pattern"]
     # eps so small that every entry lands in the fp64 bucket: three empty buckets
-    bk = gpu_bucket(B, g["M"], P.nnz, 2.0 ** -53, wl["precs"])
+    bk = gpu_bucket(B, M, P.nnz, 2.0 ** -53, wl["precs"])
     assert bk["info"]["nnz_k"][1:] == [0, 0, 0]
     xin = np.random.default_rng(0).uniform(-1, 1, P.n)
     y = torch.empty(P.n, dtype=torch.float64, device="cuda")
     B.apply(bk["BM"], dev(xin), y)
-    ref = O.bspmv(P.row_ptr, P.col, bk["stored"], bk["ids"], wl["precs"], xin)
+    ids = O.bucket_ids(P.row_ptr, muf, 2.0 ** -53, wl["precs"])["ids"]
+    stored, _, _ = O.bucket_store(P.row_ptr, P.col, muf, ids, wl["precs"])
+    ref = O.bspmv(P.row_ptr, P.col, stored, ids, wl["precs"], xin)
     assert np.array_equal(host(y), ref)
     # eps = 1 with (fp64, drop): everything is dropped and M v = 0
-    bk = gpu_bucket(B, g["M"], P.nnz, 1.0, ["fp64", "drop"])
+    bk = gpu_bucket(B, M, P.nnz, 1.0, ["fp64", "drop"])
     assert bk["info"]["nnz_k"] == [0, P.nnz] and bk["info"]["storage_pct"] == 0.0
     B.apply(bk["BM"], dev(xin), y)
     assert np.all(host(y) == 0)
@@ -138,15 +140,16 @@ def test_deterministic(B):
 def test_fp64_comparator_path(B):
     """q = 1 {fp64}, u_g = u_p = fp64: plain SPAI-GMRES-IR with the paper's u_g = u_p = u."""
     wl = W.workload("convdiff2d")
-    g = gpu_build(B, wl)
-    bk = gpu_bucket(B, g["M"], wl["pattern"].nnz, 2.0 ** -53, ["fp64"])
+    M, muf = oracle_M(B, wl)
+    bk = gpu_bucket(B, M, wl["pattern"].nnz, 2.0 ** -53, ["fp64"])
     x = torch.empty(wl["A"].n, dtype=torch.float64, device="cuda")
-    info = B.gmres_ir_solve(g["A"], dev(wl["b"]), bk["BM"], g["M"], x, u_g="fp64", u_p="fp64", tol=1e-8)
+    info = B.gmres_ir_solve(B.DeviceCSR.from_host(wl["A"]), dev(wl["b"]), bk["BM"], M, x, u_g="fp64", u_p="fp64",
+                            tol=1e-8)
     xg = host(x)
     assert info["status"] == 0
     assert np.abs(xg - wl["x_true"]).max() <= 1e-12
-    S = O.System(wl["A"], wl["pattern"].row_ptr, wl["pattern"].col, g["val"], np.zeros(wl["pattern"].nnz, np.int8),
+    S = O.System(wl["A"], wl["pattern"].row_ptr, wl["pattern"].col, muf, np.zeros(wl["pattern"].nnz, np.int8),
                  ["fp64"])
-    ref = O.gmres_ir(S, g["val"], wl["b"], "fp64", "fp64", 1e-8, 500, 10)
+    ref = O.gmres_ir(S, muf, wl["b"], "fp64", "fp64", 1e-8, 500, 10)
     assert np.abs(xg - ref["x"]).max() <= 1e-12 * np.abs(ref["x"]).max()
     assert info["gmres_iters"][0] == ref["its"][0]

@@ -16,7 +16,7 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib, small_workloads
+from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib, oracle_M, small_workloads
 from paper_2307_03914_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -89,17 +89,17 @@ EPS = [2.0 ** -37, 2.0 ** -24, 2.0 ** -16, 2.0 ** -10]
 @pytest.mark.parametrize("wl", WLS, ids=IDS)
 def test_buckets_bitexact(B, wl):
     P = wl["pattern"]
-    g = gpu_build(B, wl)
+    M, muf = oracle_M(B, wl)
     plists = [wl["precs"], wl["precs"] + ["drop"], ["fp64"], ["fp32", "bf16", "e4m3"]]
     for precs in plists:
         for eps in EPS:
-            b = gpu_bucket(B, g["M"], P.nnz, eps, precs)
-            ref = O.bucket_ids(P.row_ptr, g["val"], eps, precs)
+            b = gpu_bucket(B, M, P.nnz, eps, precs)
+            ref = O.bucket_ids(P.row_ptr, muf, eps, precs)
             assert b["info"]["norm_inf"] == ref["norm"]
             assert np.array_equal(b["ids"], ref["ids"]), (precs, eps)
             assert b["info"]["nnz_k"] == ref["nnz_k"].tolist()
             assert b["info"]["thresholds"][1:] == ref["thr"][1:].tolist()
-            stored, _, _ = O.bucket_store(P.row_ptr, P.col, g["val"], ref["ids"], precs)
+            stored, _, _ = O.bucket_store(P.row_ptr, P.col, muf, ref["ids"], precs)
             assert np.array_equal(b["stored"], stored), (precs, eps)
             assert abs(b["info"]["storage_pct"] - O.storage_pct(ref["nnz_k"], precs, 0)) < 1e-9
 
@@ -107,15 +107,15 @@ def test_buckets_bitexact(B, wl):
 @pytest.mark.parametrize("wl", WLS, ids=IDS)
 def test_bucketed_spmv_bitexact(B, wl):
     P = wl["pattern"]
-    g = gpu_build(B, wl)
+    M, muf = oracle_M(B, wl)
     rng = np.random.default_rng(5)
     x64 = rng.uniform(-1, 1, P.n)
     x32 = rng.uniform(-1, 1, P.n).astype(np.float32)
     for precs in [wl["precs"], wl["precs"] + ["drop"], ["fp64", "fp32", "fp16", "bf16", "e4m3"]]:
         for eps in EPS:
-            b = gpu_bucket(B, g["M"], P.nnz, eps, precs)
-            ref = O.bucket_ids(P.row_ptr, g["val"], eps, precs)
-            stored, _, _ = O.bucket_store(P.row_ptr, P.col, g["val"], ref["ids"], precs)
+            b = gpu_bucket(B, M, P.nnz, eps, precs)
+            ref = O.bucket_ids(P.row_ptr, muf, eps, precs)
+            stored, _, _ = O.bucket_store(P.row_ptr, P.col, muf, ref["ids"], precs)
             for xin, ydt in [(x64, torch.float64), (x32, torch.float32), (x64, torch.float32)]:
                 y = torch.empty(P.n, dtype=ydt, device="cuda")
                 B.apply(b["BM"], dev(xin), y)
@@ -131,10 +131,10 @@ def test_bucketed_spmv_bitexact(B, wl):
 @pytest.mark.parametrize("wl", WLS, ids=IDS)
 def test_x0_apply_uf_bitexact(B, wl):
     P = wl["pattern"]
-    g = gpu_build(B, wl)
+    M, muf = oracle_M(B, wl)
     y = torch.empty(P.n, dtype=torch.float64, device="cuda")
-    B.apply_uf(g["M"], dev(wl["b"]), y)
-    ref = O.spmv_prec(P.row_ptr, P.col, g["val"], "fp32", wl["b"])
+    B.apply_uf(M, dev(wl["b"]), y)
+    ref = O.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"])
     assert np.array_equal(host(y), ref)
 
 
@@ -142,14 +142,14 @@ def test_x0_apply_uf_bitexact(B, wl):
 @pytest.mark.parametrize("wl", WLS[:4], ids=IDS[:4])
 def test_gmres_fixed_steps_matches_oracle(B, wl, ug, tol):
     A, P = wl["A"], wl["pattern"]
-    g = gpu_build(B, wl)
+    M, muf = oracle_M(B, wl)
     precs = wl["precs"]
     eps = 2.0 ** -16
-    b = gpu_bucket(B, g["M"], P.nnz, eps, precs)
-    ids = O.bucket_ids(P.row_ptr, g["val"], eps, precs)["ids"]
-    stored, _, _ = O.bucket_store(P.row_ptr, P.col, g["val"], ids, precs)
+    b = gpu_bucket(B, M, P.nnz, eps, precs)
+    ids = O.bucket_ids(P.row_ptr, muf, eps, precs)["ids"]
+    stored, _, _ = O.bucket_store(P.row_ptr, P.col, muf, ids, precs)
     S = O.System(A, P.row_ptr, P.col, stored, ids, precs)
-    r = O.residual_dd(A, O.spmv_prec(P.row_ptr, P.col, g["val"], "fp32", wl["b"]), wl["b"])
+    r = O.residual_dd(A, O.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"]), wl["b"])
     k = 8
     d_ref, it_ref, _ = O.gmres(S, r, ug, ug, 0.0, k)
     Ah = B.matrix_create(B.DeviceCSR.from_host(A))
