@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-comparator", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--kmax", type=int, default=0, help="cap on GMRES steps per refinement step (0: library default)")
+    p.add_argument("--no-batch", action="store_true", help="skip the 512-system x 32-RHS batched measurement")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (differentiation) measurement")
     return p.parse_args()
 
 
@@ -217,6 +219,95 @@ def run_reference(args):
                             "sample": last["sample"]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ extension legs
+def measure_batch(B, W, world, dist, barrier):
+    """SPAI build + per-system bucketing + batched GMRES-IR of the whole batch,
+    timed with CUDA events after one warm-up run (which also autotunes)."""
+    import torch
+
+    bw = W.batch_workload()
+    A = B.DeviceCSR.from_host(bw["A"])
+    P = B.DeviceCSR.from_host(bw["pattern"], with_values=False)
+    row_off = torch.from_numpy(bw["row_off"]).cuda()
+    Bd = torch.from_numpy(bw["B"].reshape(-1)).cuda()
+    Xt = torch.from_numpy(bw["X_true"]).cuda()
+    X = torch.zeros_like(Bd)
+
+    def run():
+        Ah = B.matrix_create(A)
+        M, _ = B.bspai_build(A, P, bw["spai_eps"])
+        BM, kinfo = B.bspai_bucket_batched(M, row_off, bw["bucket_eps"], bw["precs"])
+        info = B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, tol=bw["tau"])
+        return info, kinfo
+
+    run()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    info, kinfo = run()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    n = bw["A"].n
+    err = (X.reshape(bw["nrhs"], n) - Xt).abs()
+    ro = bw["row_off"]
+    worst, ok = 0.0, 0
+    for s, m in enumerate(bw["mats"]):
+        fe = err[:, ro[s]:ro[s] + m.n].amax(dim=1) / Xt[:, ro[s]:ro[s] + m.n].abs().amax(dim=1)
+        ok += int((fe <= FE_TARGET).sum())
+        worst = max(worst, float(fe.max()))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([float(ok)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        ms, ok = float(t.item()), int(c.item())
+    return {"workload": "512 systems (n log-uniform in [1e3, 6.4e4], 5/9-point convection-diffusion) x 32 RHS",
+            "pairs": info["pairs"] * world, "solves_per_s": ok / (ms / 1000.0), "ms": ms, "ok": ok,
+            "worst_fwd_err": worst, "total_gmres_iters": info["total_iters"], "max_iters": info["max_iters"],
+            "ir_launches": info["ir_launches"], "cta_threads": info["block_threads"], "grid": info["grid"],
+            "kmax": info["kmax"], "rows": n, "nnz_A": bw["A"].nnz, "storage_pct": kinfo["storage_pct"]}
+
+
+def measure_adjoint(B, W, barrier):
+    """Forward solve and adjoint (backward) of L = ||x - x_target||^2 for the
+    256^2 log-normal diffusion problem with 16 right-hand sides."""
+    import torch
+    from paper_2307_03914_gb300 import autograd as AG
+
+    wl = W.workload("diffusion2d", grid=256)
+    A = wl["A"]
+    rng = np.random.default_rng(1)
+    xs = rng.uniform(-1, 1, (16, A.n))
+    bs = np.ascontiguousarray((A.to_scipy() @ xs.T).T)
+    xt = torch.from_numpy(rng.uniform(-1, 1, (16, A.n))).cuda()
+    rp = torch.from_numpy(A.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(A.col.astype(np.int32)).cuda()
+    Pd = B.DeviceCSR.from_host(wl["pattern"], with_values=False)
+    st = AG.SolverSettings(spai_eps=wl["spai_eps"], bucket_eps=2.0 ** -16, precs=wl["precs"])
+    stream = torch.cuda.current_stream()
+
+    def once():
+        aval = torch.from_numpy(A.val).cuda().requires_grad_(True)
+        b = torch.from_numpy(bs).cuda().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        x = AG.solve(aval, b, rp, col, Pd, st)
+        loss = ((x - xt) ** 2).sum()
+        e1.record(stream)
+        loss.backward()
+        e2.record(stream)
+        barrier()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    once()
+    fwd, bwd = once()
+    return {"workload": "2D diffusion 256^2, log-normal coefficient (sigma 1, correlation 8 cells), 16 RHS",
+            "forward_ms": fwd, "backward_ms": bwd, "forward_solves_per_s": 16 / (fwd / 1000.0),
+            "adjoint_solves_per_s": 16 / (bwd / 1000.0)}
 
 
 # ------------------------------------------------------------------ our arm
@@ -395,6 +486,14 @@ def main():
             ems, e_ok = float(t[0].item()), int(tt.item())
         out["e2e"] = {"value": e_ok / (ems / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
+
+    # ---------------- batched solves: 512 systems x 32 right-hand sides (one replica per rank)
+    if not args.no_batch:
+        out["batch"] = measure_batch(B, W, world, dist, barrier)
+
+    # ---------------- adjoint: 2D diffusion 256^2, 16 right-hand sides, forward + backward
+    if not args.no_adjoint:
+        out["adjoint"] = measure_adjoint(B, W, barrier)
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

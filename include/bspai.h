@@ -291,6 +291,42 @@ int bspai_bucket_transpose(bspai_BM_h BM, bspai_stream_t s, bspai_BM_h* BMt);
 int bspai_adjoint_grad_A(const bspai_csr_t* A, const double* lambda, const double* x, double* dA,
                          bspai_stream_t s);
 
+/* ------------------------------------------------------------------ batches */
+typedef struct {
+    int32_t pairs;          /* nsys * nrhs (system, right-hand side) solves */
+    int32_t converged;      /* pairs that met a stopping test */
+    int32_t nonfinite;      /* pairs that hit NaN / Inf */
+    int32_t ir_launches;    /* refinement steps launched for the batch */
+    int32_t max_ir_steps;   /* most GMRES runs of any pair */
+    int32_t max_iters;      /* most GMRES steps of any pair, summed over its refinement steps */
+    int64_t total_iters;    /* GMRES steps over all pairs */
+    int32_t block_threads;  /* CTA size picked by the autotuner */
+    int32_t grid;           /* CTAs of the persistent GMRES launch */
+    int32_t kmax;           /* GMRES steps allowed per refinement step */
+} bspai_batch_info_t;
+
+/* BSPAI-GMRES-IR (Alg 3.1) for nsys independent systems with nrhs right-hand
+ * sides each.  A, the pattern and M hold the systems block-diagonally: system s
+ * owns rows row_off[s] .. row_off[s+1]-1 (device int32, nsys + 1 entries,
+ * multiples of 32; rows that pad a system have no entries), so one bspai_build
+ * and one bspai_bucket_batched call serve the whole batch.  B and X (device
+ * fp64) hold nrhs vectors of length n one after another; X is in/out.  Every
+ * (system, right-hand side) pair runs its own refinement: per pair x0 = M b
+ * (u_f), residuals in double-double, nbe / ||d|| / stagnation tests as in
+ * gmres_ir_solve, and its own left-preconditioned MGS-GMRES (vectors in u_g,
+ * A v in u_p, bucketed M v, Givens in fp64).  Each refinement step of the
+ * batch is one persistent launch in which a CTA takes pairs, largest systems
+ * first, and runs each GMRES with CTA barriers only; the CTA size is chosen by
+ * timing the candidates on the batch (cached per shape).  kmax defaults to
+ * min(largest system, 300).  pair_status (0 not converged, 1 nbe, 2 dx,
+ * 3 stagnation, -1 non-finite) and pair_iters (device int32, nsys * nrhs,
+ * pair p = rhs * nsys + system) may be NULL.  Returns BSPAI_OK when every
+ * pair met a stopping test, else BSPAI_NOT_CONVERGED / BSPAI_NONFINITE. */
+int gmres_ir_solve_batched(bspai_A_h A, const int32_t* row_off, int32_t nsys, int32_t nrhs, const double* B,
+                           bspai_BM_h BM, bspai_M_h M, bspai_prec_t u_g, bspai_prec_t u_p, double tol,
+                           const bspai_opts_t* opts, double* X, bspai_stream_t s, bspai_batch_info_t* info,
+                           int32_t* pair_status, int32_t* pair_iters);
+
 /* Same as gmres_ir_solve with A already prepared by bspai_matrix_create. */
 int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,
                      bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, bspai_prec_t u_p,

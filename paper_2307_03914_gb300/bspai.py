@@ -65,6 +65,12 @@ class SolveInfo(C.Structure):
                 ("dx", C.c_double * 32), ("relres", C.c_double * 32)]
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("pairs", C.c_int32), ("converged", C.c_int32), ("nonfinite", C.c_int32),
+                ("ir_launches", C.c_int32), ("max_ir_steps", C.c_int32), ("max_iters", C.c_int32),
+                ("total_iters", C.c_int64), ("block_threads", C.c_int32), ("grid", C.c_int32), ("kmax", C.c_int32)]
+
+
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("launches", C.c_int64 * 8)]
 
@@ -108,6 +114,8 @@ _sig("bspai_adjoint_grad_A", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _vp])
 _sig("bspai_gmres_noalloc", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
 _sig("gmres_ir_solve", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                             C.POINTER(SolveInfo)])
+_sig("gmres_ir_solve_batched", _i, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _i, _i, _d, C.POINTER(Opts),
+                                    _vp, _vp, C.POINTER(BatchInfo), _vp, _vp])
 _sig("gmres_ir_solve_h", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                               C.POINTER(SolveInfo)])
 
@@ -375,3 +383,20 @@ def gmres_ir_solve(A, b, BM: BMHandle, M: MHandle | None, x, u="fp64", u_r="dd",
     out = _solve_info(si)
     out["status"] = st
     return out
+
+
+def gmres_ir_solve_batched(Ah: AHandle, row_off, nrhs: int, B, BM: BMHandle, M: MHandle | None, X, u_g="fp32",
+                           u_p="fp32", tol=1e-4, o: Opts | None = None, pair_status=None, pair_iters=None,
+                           stream=None) -> dict:
+    """Batched BSPAI-GMRES-IR over block-diagonally stacked systems (row_off:
+    device int32, nsys + 1; B, X: device fp64, nrhs * n)."""
+    bi = BatchInfo()
+    nsys = int(row_off.numel() - 1)
+    st = _lib.gmres_ir_solve_batched(Ah.ptr, _ptr(row_off), nsys, int(nrhs), _ptr(B), BM.ptr,
+                                     M.ptr if M is not None else None, PREC[u_g], PREC[u_p], float(tol),
+                                     C.byref(o or opts()), _ptr(X), _stream(stream), C.byref(bi), _ptr(pair_status),
+                                     _ptr(pair_iters))
+    _check(st, (OK, NOT_CONVERGED, NONFINITE))
+    d = {f: getattr(bi, f) for f, _ in BatchInfo._fields_}
+    d["status"] = st
+    return d

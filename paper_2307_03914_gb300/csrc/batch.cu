@@ -1,0 +1,684 @@
+// batch.cu -- BSPAI-GMRES-IR for many independent systems and right-hand
+// sides at once (the batching extension).
+//
+// Layout: the nsys systems are stacked block-diagonally in one A, one pattern
+// and one M (each system padded to a multiple of 32 rows with empty rows), so
+// the SPAI build (bspai_build) and the per-system bucketing
+// (bspai_bucket_batched) run as single launches over the whole batch.
+// Right-hand sides and solutions are nrhs vectors of length n stored one after
+// another.  A (system, right-hand side) pair is independent of every other, so
+// the GMRES of a refinement step is one persistent launch: each CTA takes pairs
+// from a queue (largest systems first) and runs the whole left-preconditioned
+// MGS-GMRES of that pair on its own -- bucketed M v and A v over the system's
+// rows (the same row arithmetic as the single-system kernels), MGS dot products
+// as CTA reductions, Givens rotations and the triangular solve in fp64 -- with
+// only CTA barriers, no grid-wide synchronisation.  Per-pair residuals and
+// stopping tests (Alg 3.1 loop) run as batched kernels between those launches.
+// The CTA size is chosen by timing the candidates on a short fixed-length
+// GMRES run of the batch (cached per batch shape).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "spmv_row.cuh"
+
+namespace bspai {
+
+int launch_residual_batch(const bspai_matrix* A, int nrhs, const double* X, const double* Bv, double* R,
+                          const int32_t* slice_seg, int nsys, double* prmax, double* pxmax, cudaStream_t s);
+
+template <typename T>
+struct BAr;
+template <>
+struct BAr<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+};
+template <>
+struct BAr<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+};
+
+// CTA-wide sum, identical in every thread (fixed reduction tree)
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* s_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < nw ? s_w[lane] : T(0);
+        t = warp_sum(t);
+        if (lane == 0) s_w[32] = t;
+    }
+    __syncthreads();
+    const T r = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* s_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < nw ? s_w[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane == 0) s_w[32] = t;
+    }
+    __syncthreads();
+    const double r = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+// Givens rotations on column j of H, update of g, tau test (fp64); thread 0
+__device__ void givens_pair(int j, int kmax, double hn, double* H, double* cs, double* sn, double* g, double tau,
+                            double beta, double* res, int* done) {
+    double* hc = H + (int64_t)j * (kmax + 1);
+    hc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t1 = __dadd_rn(__dmul_rn(cs[i], hc[i]), __dmul_rn(sn[i], hc[i + 1]));
+        const double t2 = __dadd_rn(__dmul_rn(-sn[i], hc[i]), __dmul_rn(cs[i], hc[i + 1]));
+        hc[i] = t1;
+        hc[i + 1] = t2;
+    }
+    const double a = hc[j], b = hc[j + 1];
+    const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+    double c = 1.0, s = 0.0;
+    if (rr != 0.0) {
+        c = __ddiv_rn(a, rr);
+        s = __ddiv_rn(b, rr);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    hc[j] = rr;
+    hc[j + 1] = 0.0;
+    g[j + 1] = __dmul_rn(-s, g[j]);
+    g[j] = __dmul_rn(c, g[j]);
+    *res = fabs(g[j + 1]);
+    const bool fin = isfinite(*res) && isfinite(hn) && isfinite(rr);
+    *done = (*res <= __dmul_rn(tau, beta)) || hn == 0.0 || j + 1 >= kmax || !fin;
+}
+
+// y[lr] = (M x)_{r0 + lr} for the rows of one system, the CTA's threads
+// striding over them (kept out of line: the kernel calls it three times)
+template <typename XT, typename YT>
+__device__ __noinline__ void rows_apply(const BMDev& M, int r0, int ns, const XT* __restrict__ x, YT* __restrict__ y) {
+    for (int lr = threadIdx.x; lr < ns; lr += blockDim.x) y[lr] = from_f64<YT>(bucketed_row<XT>(M, r0 + lr, x));
+}
+
+struct PairState {
+    int32_t* status;   // 0 active; 1 nbe <= u; 2 ||d|| <= u ||x||; 3 stagnation; -1 non-finite
+    int32_t* iters;    // GMRES steps summed over refinement steps
+    int32_t* steps;    // refinement steps that ran GMRES
+    double* rmax;      // per step: max |r| of the pair
+    double* xmax;      // per step: max |x| before the update
+    double* bmax;      // max |b|
+    double* anorm;     // per system ||A_s||_inf
+    double* dmax;      // per step: max |d|
+    double* dxmax;     // per step: max |x| after the update
+    double* dprev;     // previous step's max |d|
+    double* relres;    // last GMRES |g_k| / beta
+    double* nbe;       // last normwise backward error
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ BMDev Av, const __grid_constant__ BMDev Mv,
+                                                      const int32_t* __restrict__ row_off, int nsys, int n,
+                                                      const int32_t* __restrict__ order, int npairs, int* queue,
+                                                      const int32_t* __restrict__ status, const double* __restrict__ R,
+                                                      double* __restrict__ X, T* Vws, T* Wws, int64_t ldv,
+                                                      double* Hws, double* Sws, int kmax, double tau,
+                                                      int32_t* __restrict__ iters, int32_t* __restrict__ steps,
+                                                      double* __restrict__ relres, double* __restrict__ dmax,
+                                                      double* __restrict__ dxmax) {
+    __shared__ T s_w[33];
+    __shared__ double s_d[33];
+    __shared__ int s_p, s_done;
+    __shared__ double s_res;
+    using Ar = BAr<T>;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    T* V = Vws + (int64_t)blockIdx.x * ldv * (kmax + 1);
+    T* w = Wws + (int64_t)blockIdx.x * ldv;
+    double* H = Hws + (int64_t)blockIdx.x * (kmax + 1) * kmax;
+    double* cs = Sws + (int64_t)blockIdx.x * 4 * (kmax + 2);
+    double* sn = cs + (kmax + 2);
+    double* g = sn + (kmax + 2);
+    double* y = g + (kmax + 2);
+    while (true) {
+        if (tid == 0) s_p = atomicAdd(queue, 1);
+        __syncthreads();
+        const int p = s_p;
+        __syncthreads();
+        if (p >= npairs) break;
+        const int pair = order[p];
+        if (status[pair] != 0) continue;
+        const int rhs = pair / nsys, sys = pair - rhs * nsys;
+        const int r0 = row_off[sys], ns = row_off[sys + 1] - r0;
+        const double* rr = R + (int64_t)rhs * n;
+        double* xx = X + (int64_t)rhs * n;
+        // s = M r (Alg 2.3), stored in u_g; beta = ||s||_2
+        rows_apply<double, T>(Mv, r0, ns, rr, V);
+        T acc = T(0);
+        for (int lr = tid; lr < ns; lr += bd) acc = Ar::add(acc, Ar::mul(V[lr], V[lr]));
+        const T beta = Ar::sqrt(block_sum(acc, s_w));
+        const bool fin = isfinite((double)beta);
+        int k = 0;
+        double res = (double)beta;
+        if (beta > T(0) && fin) {
+            for (int lr = tid; lr < ns; lr += bd) V[lr] = Ar::div(V[lr], beta);
+            if (tid == 0) g[0] = (double)beta;
+            for (int j = 0; j < kmax; ++j) {
+                __syncthreads();
+                const T* vj = V + (int64_t)j * ldv;
+                rows_apply<T, T>(Av, r0, ns, vj - r0, w);
+                __syncthreads();
+                T* z = V + (int64_t)(j + 1) * ldv;
+                rows_apply<T, T>(Mv, r0, ns, w - r0, z);
+                // modified Gram-Schmidt: pass i updates z by the previous coefficient and
+                // dots it with v_i; the last pass forms ||z||_2 (each thread owns its rows of z)
+                T hprev = T(0);
+                for (int i = 0; i <= j + 1; ++i) {
+                    const T* vi = V + (int64_t)(i <= j ? i : j) * ldv;
+                    const T* vp = V + (int64_t)(i > 0 ? i - 1 : 0) * ldv;
+                    T a = T(0);
+                    for (int lr = tid; lr < ns; lr += bd) {
+                        T zr = z[lr];
+                        if (i > 0) {
+                            zr = Ar::sub(zr, Ar::mul(hprev, vp[lr]));
+                            z[lr] = zr;
+                        }
+                        a = Ar::add(a, Ar::mul(i <= j ? vi[lr] : zr, zr));
+                    }
+                    const T h = block_sum(a, s_w);
+                    if (i <= j) {
+                        if (tid == 0) H[(int64_t)j * (kmax + 1) + i] = (double)h;
+                        hprev = h;
+                    } else {
+                        const T hn = Ar::sqrt(h);
+                        if (hn > T(0) && isfinite((double)hn))
+                            for (int lr = tid; lr < ns; lr += bd) z[lr] = Ar::div(z[lr], hn);
+                        if (tid == 0) {
+                            double rs;
+                            int dn;
+                            givens_pair(j, kmax, (double)hn, H, cs, sn, g, tau, (double)beta, &rs, &dn);
+                            s_res = rs;
+                            s_done = dn;
+                        }
+                    }
+                }
+                __syncthreads();
+                k = j + 1;
+                res = s_res;
+                if (s_done) break;
+            }
+            // y = R^-1 g, column-oriented back substitution (fp64)
+            __syncthreads();
+            for (int i = k - 1; i >= 0; --i) {
+                const double* hc = H + (int64_t)i * (kmax + 1);
+                if (tid == 0) y[i] = __ddiv_rn(g[i], hc[i]);
+                __syncthreads();
+                const double yi = y[i];
+                for (int t = tid; t < i; t += bd) g[t] = __dsub_rn(g[t], __dmul_rn(hc[t], yi));
+                __syncthreads();
+            }
+        }
+        // d = V y in u_g, x += d in fp64
+        double dm = 0.0, xm = 0.0;
+        for (int lr = tid; lr < ns; lr += bd) {
+            T a = T(0);
+            for (int jj = 0; jj < k; ++jj) a = Ar::add(a, Ar::mul(V[(int64_t)jj * ldv + lr], from_f64<T>(y[jj])));
+            const double d = (double)a;
+            const double xn = __dadd_rn(xx[r0 + lr], d);
+            xx[r0 + lr] = xn;
+            double ad = fabs(d), ax = fabs(xn);
+            if (!(ad <= 1.7976931348623157e308)) ad = __longlong_as_double(0x7ff0000000000000LL);
+            if (!(ax <= 1.7976931348623157e308)) ax = __longlong_as_double(0x7ff0000000000000LL);
+            dm = fmax(dm, ad);
+            xm = fmax(xm, ax);
+        }
+        dm = block_max(dm, s_d);
+        xm = block_max(xm, s_d);
+        if (tid == 0) {
+            iters[pair] += k;
+            steps[pair] += 1;
+            relres[pair] = beta > T(0) ? res / (double)beta : 0.0;
+            dmax[pair] = fin ? dm : __longlong_as_double(0x7ff0000000000000LL);
+            dxmax[pair] = xm;
+        }
+        __syncthreads();
+    }
+}
+
+// per pair: nbe = ||r|| / (||A_s|| ||x|| + ||b||); stop when <= u; count active pairs
+__global__ void k_batch_flags(int npairs, int nsys, PairState S, double ustop, int* active) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    if (S.status[p] != 0) return;
+    const double rm = S.rmax[p];
+    const double den = S.anorm[p % nsys] * S.xmax[p] + S.bmax[p];
+    const double nbe = rm == 0.0 ? 0.0 : rm / den;
+    S.nbe[p] = nbe;
+    if (!isfinite(nbe)) {
+        S.status[p] = -1;
+        return;
+    }
+    if (nbe <= ustop) {
+        S.status[p] = 1;
+        return;
+    }
+    atomicAdd(active, 1);
+}
+
+// per pair after the update: ||d|| <= u ||x||, or stagnation ||d_i|| > stag ||d_{i-1}||
+__global__ void k_batch_after(int npairs, PairState S, double ustop, double stag) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    if (S.status[p] != 0) return;
+    const double d = S.dmax[p], xm = S.dxmax[p];
+    if (!isfinite(d) || !isfinite(xm)) {
+        S.status[p] = -1;
+        return;
+    }
+    if (d <= __dmul_rn(ustop, xm)) S.status[p] = 2;
+    else if (d > __dmul_rn(stag, S.dprev[p])) S.status[p] = 3;
+    S.dprev[p] = d;
+}
+
+__global__ void k_system_norms(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ val, const int32_t* __restrict__ slice_seg,
+                               double* __restrict__ anorm) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double sum = 0.0;
+    for (int64_t p = sptr[r >> 5] + (r & 31); p < sptr[(r >> 5) + 1]; p += kSlice)
+        if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
+    atomic_max_nonneg(anorm + slice_seg[r >> 5], sum);
+}
+
+__global__ void k_pair_bmax(int n, int nrhs, int nsys, const double* __restrict__ Bv,
+                            const int32_t* __restrict__ slice_seg, double* __restrict__ bmax) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    const int64_t rhs = t / n, i = t - rhs * n;
+    double a = fabs(Bv[t]);
+    if (!(a <= 1.7976931348623157e308)) a = __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(bmax + rhs * nsys + slice_seg[i >> 5], a);
+}
+
+__global__ void k_fill_d(int64_t count, double* __restrict__ p, double v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) p[i] = v;
+}
+
+__global__ void k_slice_seg_b(int nsys, const int32_t* __restrict__ row_off, int32_t* __restrict__ slice_seg) {
+    const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sg >= nsys) return;
+    for (int s = row_off[sg] >> 5; s < (row_off[sg + 1] >> 5); ++s) slice_seg[s] = sg;
+}
+
+// ------------------------------------------------------------------ host
+struct TuneKey {
+    int n, nsys, nrhs, ug, kmax;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(n, nsys, nrhs, ug, kmax) < std::tie(o.n, o.nsys, o.nrhs, o.ug, o.kmax);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tuned;  // CTA size per batch shape
+
+template <typename T>
+static int occupancy_blocks(int bd, int* occ) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_gmres_batch<T>, bd, 0);
+    if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
+    return BSPAI_OK;
+}
+
+template <typename T>
+static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs, const double* Bv,
+                    const bspai_bucketed* BM, const bspai_spai* M, int u_p, double tol, const bspai_opts_t& o,
+                    double* X, cudaStream_t s, bspai_batch_info_t* info, int32_t* pair_status, int32_t* pair_iters) {
+    const int n = A->n;
+    const int npairs = nsys * nrhs;
+    const int nsl = A->sell.nslices;
+    const int ug = sizeof(T) == 8 ? BSPAI_FP64 : BSPAI_FP32;
+    // host copy of the offsets: sizes, ordering, workspace
+    std::vector<int32_t> hoff((size_t)nsys + 1);
+    CUDA_TRY(cudaMemcpyAsync(hoff.data(), row_off, sizeof(int32_t) * ((size_t)nsys + 1), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hoff[0] != 0 || hoff[nsys] != n) return set_error(BSPAI_ERR_INVALID, "batched solve: row_off must run from 0 to n");
+    int nmax = 0;
+    for (int k = 0; k < nsys; ++k) {
+        const int len = hoff[k + 1] - hoff[k];
+        if (len < 0 || (hoff[k] & 31)) return set_error(BSPAI_ERR_INVALID, "batched solve: offsets must be multiples of 32");
+        nmax = len > nmax ? len : nmax;
+    }
+    int kmax = o.kmax > 0 ? o.kmax : (nmax < 300 ? nmax : 300);
+    if (kmax < 1) kmax = 1;
+    int imax = o.i_max > 0 ? o.i_max : 10;
+    if (imax > 32) imax = 32;
+    const double ustop = o.u_stop > 0 ? o.u_stop : 0x1p-53;
+    const double stag = o.stagnation > 0 ? o.stagnation : 0.9;
+    const double tau = tol > 0 ? tol : o.tau;
+    // pairs, largest systems first
+    std::vector<int32_t> hord((size_t)npairs);
+    {
+        std::vector<int32_t> sys(nsys);
+        for (int k = 0; k < nsys; ++k) sys[k] = k;
+        std::stable_sort(sys.begin(), sys.end(), [&](int a, int b) {
+            return (hoff[a + 1] - hoff[a]) > (hoff[b + 1] - hoff[b]);
+        });
+        size_t c = 0;
+        for (int k : sys)
+            for (int r = 0; r < nrhs; ++r) hord[c++] = r * nsys + k;
+    }
+    const int64_t ldv = ceil_div(nmax > 0 ? nmax : 1, 64) * 64;
+    // device buffers
+    std::vector<void*> bufs;
+    auto take = [&](void** p, size_t bytes) {
+        int rc = dalloc(p, bytes, s);
+        if (!rc) bufs.push_back(*p);
+        return rc;
+    };
+    auto done = [&](int code) {
+        for (void* p : bufs) dfree(p, s);
+        return code;
+    };
+    PairState S{};
+    int32_t *d_order = nullptr, *d_seg = nullptr, *d_queue = nullptr, *d_active = nullptr;
+    double* R = nullptr;
+    int rc;
+    if ((rc = take((void**)&d_order, sizeof(int32_t) * npairs))) return done(rc);
+    if ((rc = take((void**)&d_seg, sizeof(int32_t) * (size_t)(nsl > 0 ? nsl : 1)))) return done(rc);
+    if ((rc = take((void**)&d_queue, sizeof(int) * 2))) return done(rc);
+    d_active = d_queue + 1;
+    if ((rc = take((void**)&R, sizeof(double) * (size_t)n * nrhs))) return done(rc);
+    void* p;
+    if ((rc = take(&p, sizeof(int32_t) * npairs * 3))) return done(rc);
+    S.status = (int32_t*)p;
+    S.iters = S.status + npairs;
+    S.steps = S.iters + npairs;
+    if ((rc = take(&p, sizeof(double) * ((size_t)npairs * 9 + nsys)))) return done(rc);
+    S.rmax = (double*)p;
+    S.xmax = S.rmax + npairs;
+    S.bmax = S.xmax + npairs;
+    S.dmax = S.bmax + npairs;
+    S.dxmax = S.dmax + npairs;
+    S.dprev = S.dxmax + npairs;
+    S.relres = S.dprev + npairs;
+    S.nbe = S.relres + npairs;
+    S.anorm = S.nbe + npairs + npairs;  // one spare slot of npairs
+    CUDA_TRY(cudaMemcpyAsync(d_order, hord.data(), sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(S.status, 0, sizeof(int32_t) * npairs * 3, s));
+    CUDA_TRY(cudaMemsetAsync(S.rmax, 0, sizeof(double) * ((size_t)npairs * 9 + nsys), s));
+    {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        k_slice_seg_b<<<(unsigned)ceil_div(nsys, 256), 256, 0, s>>>(nsys, row_off, d_seg);
+        note_launch();
+        k_fill_d<<<(unsigned)ceil_div(npairs, 256), 256, 0, s>>>(npairs, S.dprev, INFINITY);
+        note_launch();
+        if (n > 0) {
+            k_system_norms<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, A->sell.sptr, A->sell.col, A->val64, d_seg,
+                                                                      S.anorm);
+            note_launch();
+            k_pair_bmax<<<(unsigned)ceil_div((int64_t)n * nrhs, 256), 256, 0, s>>>(n, nrhs, nsys, Bv, d_seg, S.bmax);
+            note_launch();
+        }
+        CUDA_LAUNCH_CHECK();
+        // x0 = M b in u_f for every right-hand side (Alg 3.1)
+        if (!o.x0_given)
+            for (int r = 0; r < nrhs; ++r)
+                if ((rc = launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), Bv + (size_t)r * n, BSPAI_FP64,
+                                       X + (size_t)r * n, BSPAI_FP64, s)))
+                    return done(rc);
+    }
+    const BMDev Av = single_bucket_view(A->sell, u_p == BSPAI_FP64 ? (const void*)A->val64 : (const void*)A->val32,
+                                        u_p);
+    const BMDev Mv = BM->dev();
+    // CTA size: cached per batch shape, else timed on a short fixed-length run
+    const size_t ws_budget = (size_t)24 << 30;
+    int sms = num_sms();
+    auto grid_for = [&](int bd, int* grid) -> int {
+        int occ = 0;
+        int r2 = occupancy_blocks<T>(bd, &occ);
+        if (r2) return r2;
+        if (occ < 1) return set_error(BSPAI_ERR_CUDA, "batched GMRES kernel does not fit on an SM");
+        const size_t per = sizeof(T) * (size_t)ldv * (kmax + 2) + sizeof(double) * ((size_t)(kmax + 1) * kmax + 4 * (kmax + 2));
+        int gmax = (int)(ws_budget / per);
+        int gr = sms * occ;
+        if (gr > gmax) gr = gmax;
+        if (gr > npairs) gr = npairs;
+        *grid = gr < 1 ? 1 : gr;
+        return BSPAI_OK;
+    };
+    int bd = 0;
+    const TuneKey key{n, nsys, nrhs, ug, kmax};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) bd = it->second;
+    }
+    // workspace for the largest grid among the candidates
+    int gmax_all = 0;
+    for (int cand : {128, 256, 512}) {
+        int gr;
+        if ((rc = grid_for(cand, &gr))) return done(rc);
+        gmax_all = gr > gmax_all ? gr : gmax_all;
+    }
+    T *Vws = nullptr, *Wws = nullptr;
+    double *Hws = nullptr, *Sws = nullptr;
+    if ((rc = take((void**)&Vws, sizeof(T) * (size_t)gmax_all * ldv * (kmax + 1)))) return done(rc);
+    if ((rc = take((void**)&Wws, sizeof(T) * (size_t)gmax_all * ldv))) return done(rc);
+    if ((rc = take((void**)&Hws, sizeof(double) * (size_t)gmax_all * (kmax + 1) * kmax))) return done(rc);
+    if ((rc = take((void**)&Sws, sizeof(double) * (size_t)gmax_all * 4 * (kmax + 2)))) return done(rc);
+    auto launch_gmres = [&](int bdim, int grid, const double* Rin, double* Xout, int kcap, double tcap, PairState& St,
+                            cudaStream_t st) {
+        k_gmres_batch<T><<<grid, bdim, 0, st>>>(Av, Mv, row_off, nsys, n, d_order, npairs, d_queue, St.status, Rin,
+                                                Xout, Vws, Wws, ldv, Hws, Sws, kcap, tcap, St.iters, St.steps,
+                                                St.relres, St.dmax, St.dxmax);
+        note_launch();
+        return cudaGetLastError();
+    };
+    if (bd == 0) {
+        // autotune: 8 Arnoldi steps (tau = 0) of every pair on the right-hand sides, into scratch
+        double* Xs = nullptr;
+        void* ps2 = nullptr;
+        if ((rc = take((void**)&Xs, sizeof(double) * (size_t)n * nrhs))) return done(rc);
+        if ((rc = take(&ps2, sizeof(int32_t) * npairs * 2 + sizeof(double) * npairs * 3))) return done(rc);
+        PairState T2 = S;
+        T2.iters = (int32_t*)ps2;
+        T2.steps = T2.iters + npairs;
+        T2.relres = (double*)(T2.steps + npairs);
+        T2.dmax = T2.relres + npairs;
+        T2.dxmax = T2.dmax + npairs;
+        cudaEvent_t e0, e1;
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        float best = 1e30f;
+        for (int cand : {128, 256, 512}) {
+            int gr;
+            if ((rc = grid_for(cand, &gr))) return done(rc);
+            CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+            CUDA_TRY(cudaMemsetAsync(Xs, 0, sizeof(double) * (size_t)n * nrhs, s));
+            CUDA_TRY(cudaEventRecord(e0, s));
+            CUDA_TRY(launch_gmres(cand, gr, Bv, Xs, kmax < 8 ? kmax : 8, 0.0, T2, s));
+            CUDA_TRY(cudaEventRecord(e1, s));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bd = cand;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = bd;
+    }
+    int grid = 0;
+    if ((rc = grid_for(bd, &grid))) return done(rc);
+    // one refinement step: residuals, tests, the persistent GMRES launch, tests
+    auto step = [&](cudaStream_t st) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(S.rmax, 0, sizeof(double) * npairs * 2, st);  // rmax, xmax
+        if (!e) e = cudaMemsetAsync(d_queue, 0, sizeof(int) * 2, st);                // queue, active
+        if (e) return e;
+        if (launch_residual_batch(A, nrhs, X, Bv, R, d_seg, nsys, S.rmax, S.xmax, st)) return cudaErrorUnknown;
+        k_batch_flags<<<(unsigned)ceil_div(npairs, 256), 256, 0, st>>>(npairs, nsys, S, ustop, d_active);
+        note_launch();
+        {
+            ProfScope ps(BSPAI_K_MGS, st);
+            if ((e = launch_gmres(bd, grid, R, X, kmax, tau, S, st))) return e;
+        }
+        k_batch_after<<<(unsigned)ceil_div(npairs, 256), 256, 0, st>>>(npairs, S, ustop, stag);
+        note_launch();
+        return cudaGetLastError();
+    };
+    static thread_local int* t_active = nullptr;
+    if (!t_active) CUDA_TRY(cudaMallocHost(&t_active, sizeof(int)));
+    // Every refinement step issues the same five operations on the same buffers, so the
+    // sequence is captured once into a CUDA graph and replayed.  Capture runs on a private
+    // stream (the legacy default stream cannot be captured); replays go to the caller's
+    // stream.  With kernel-class profiling on, the step is launched directly so that its
+    // events land on the caller's stream.
+    struct GraphGuard {
+        cudaGraphExec_t e = nullptr;
+        ~GraphGuard() {
+            if (e) cudaGraphExecDestroy(e);
+        }
+    } gexec;
+    long long graph_kernels = 0;
+    if (!prof_enabled()) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (!e) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (!e) {
+            count_launches(false);  // the replays are counted, not the capture
+            cudaError_t e2 = step(cs);
+            count_launches(true);
+            e = cudaStreamEndCapture(cs, &g);
+            if (!e) e = e2;
+        }
+        if (!e) e = cudaGraphInstantiate(&gexec.e, g, 0);
+        if (!e) {
+            size_t nn = 0;
+            e = cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (!e && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+            for (size_t i = 0; !e && i < nn; ++i) {
+                cudaGraphNodeType t;
+                e = cudaGraphNodeGetType(nodes[i], &t);
+                graph_kernels += !e && t == cudaGraphNodeTypeKernel;
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+        if (cs) cudaStreamDestroy(cs);
+        if (e) return done(cuda_error(e, "capturing the batched refinement step", __FILE__, __LINE__));
+    }
+    int ir = 0, launched = 0;
+    for (; ir < imax; ++ir) {
+        ++launched;
+        cudaError_t e;
+        if (gexec.e) {
+            e = cudaGraphLaunch(gexec.e, s);
+            for (long long k = 0; k < graph_kernels; ++k) note_launch();
+        } else {
+            e = step(s);
+        }
+        if (!e) e = cudaMemcpyAsync(t_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return done(cuda_error(e, "batched refinement step", __FILE__, __LINE__));
+        if (*t_active == 0) break;
+    }
+    // results
+    std::vector<int32_t> hst(npairs), hit(npairs), hsteps(npairs);
+    std::vector<double> hnbe(npairs);
+    CUDA_TRY(cudaMemcpyAsync(hst.data(), S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hit.data(), S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hsteps.data(), S.steps, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hnbe.data(), S.nbe, sizeof(double) * npairs, cudaMemcpyDeviceToHost, s));
+    if (pair_status) CUDA_TRY(cudaMemcpyAsync(pair_status, S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
+    if (pair_iters) CUDA_TRY(cudaMemcpyAsync(pair_iters, S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int conv = 0, nonfin = 0, maxit = 0, maxsteps = 0;
+    int64_t tot = 0;
+    for (int q = 0; q < npairs; ++q) {
+        conv += hst[q] > 0;
+        nonfin += hst[q] < 0;
+        tot += hit[q];
+        maxit = hit[q] > maxit ? hit[q] : maxit;
+        maxsteps = hsteps[q] > maxsteps ? hsteps[q] : maxsteps;
+    }
+    if (info) {
+        info->pairs = npairs;
+        info->converged = conv;
+        info->nonfinite = nonfin;
+        info->ir_launches = launched;
+        info->max_ir_steps = maxsteps;
+        info->total_iters = tot;
+        info->max_iters = maxit;
+        info->block_threads = bd;
+        info->grid = grid;
+        info->kmax = kmax;
+    }
+    done(BSPAI_OK);
+    if (nonfin) return set_error(BSPAI_NONFINITE, "batched solve: %d pairs hit a non-finite value", nonfin);
+    if (conv < npairs)
+        return set_error(BSPAI_NOT_CONVERGED, "batched solve: %d of %d pairs met no stopping test", npairs - conv,
+                         npairs);
+    return BSPAI_OK;
+}
+
+}  // namespace bspai
+
+using namespace bspai;
+
+extern "C" {
+
+int gmres_ir_solve_batched(bspai_A_h A, const int32_t* row_off, int32_t nsys, int32_t nrhs, const double* B,
+                           bspai_BM_h BM, bspai_M_h M, bspai_prec_t u_g, bspai_prec_t u_p, double tol,
+                           const bspai_opts_t* opts, double* X, bspai_stream_t st, bspai_batch_info_t* info,
+                           int32_t* pair_status, int32_t* pair_iters) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: bad A handle");
+    if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: bad M handle");
+    if (M && M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: bad M handle");
+    if (nsys < 1 || nrhs < 1 || !row_off || !B || !X)
+        return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: bad batch description");
+    if (BM->n != A->n || (M && M->n != A->n)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: size mismatch");
+    if ((A->n & 31) != 0) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: n must be a multiple of 32");
+    if (u_g != BSPAI_FP32 && u_g != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_g must be FP32 or FP64");
+    if (u_p != BSPAI_FP32 && u_p != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_p must be FP32 or FP64");
+    bspai_opts_t o;
+    bspai_opts_default(&o);
+    if (opts) o = *opts;
+    if (!o.x0_given && !M) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: need M for x0 = M b");
+    if (info) memset(info, 0, sizeof *info);
+    return u_g == BSPAI_FP64 ? batch_ir<double>(A, row_off, nsys, nrhs, B, BM, M, u_p, tol, o, X, s, info, pair_status,
+                                                pair_iters)
+                             : batch_ir<float>(A, row_off, nsys, nrhs, B, BM, M, u_p, tol, o, X, s, info, pair_status,
+                                               pair_iters);
+}
+
+}  // extern "C"

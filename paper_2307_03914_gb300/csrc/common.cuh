@@ -172,6 +172,7 @@ struct ProfScope {
 
 int num_sms();
 void note_launch();  // counts kernel launches (reported by bspai_launch_count)
+void count_launches(bool on);  // this thread's launches are (not) counted, e.g. during graph capture
 
 __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

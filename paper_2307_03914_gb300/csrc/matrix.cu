@@ -177,6 +177,62 @@ __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __res
     }
 }
 
+// The same residual for nrhs right-hand sides of a block-diagonal batch
+// (vectors stored one after another, n each; n a multiple of 32): thread per
+// (right-hand side, row), and per (system, right-hand side) pair p = rhs * nsys
+// + system the max |r| and max |x|, found through the system of each slice.
+__global__ void __launch_bounds__(256) k_residual_batch(int n, int nrhs, const int64_t* __restrict__ sptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const double* __restrict__ X,
+                                                        const double* __restrict__ Bv, double* __restrict__ R,
+                                                        const int32_t* __restrict__ slice_seg, int nsys,
+                                                        double* __restrict__ prmax, double* __restrict__ pxmax) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    const int64_t rhs = t / n;
+    const int64_t i = t - rhs * n;
+    const double* x = X + rhs * n;
+    const int64_t s = i >> 5;
+    double hi = Bv[t], lo = 0.0;
+    const int64_t end = sptr[s + 1];
+    for (int64_t p = sptr[s] + (i & 31); p < end; p += kSlice) {
+        const int c = __ldg(col + p);
+        if (c < 0) break;
+        const double a = __ldg(val + p);
+        const double xv = __ldg(x + c);
+        const double ph = __dmul_rn(a, xv);
+        const double pl = __fma_rn(a, xv, -ph);
+        dd_accumulate(hi, lo, -ph, -pl);
+    }
+    const double ri = __dadd_rn(hi, lo);
+    R[t] = ri;
+    double rabs = fabs(ri), xabs = fabs(x[i]);
+    if (!(rabs <= 1.7976931348623157e308)) rabs = __longlong_as_double(0x7ff0000000000000LL);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rabs = fmax(rabs, __shfl_xor_sync(0xffffffffu, rabs, o));
+        xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t pair = rhs * nsys + slice_seg[s];
+        atomic_max_nonneg(prmax + pair, rabs);
+        atomic_max_nonneg(pxmax + pair, xabs);
+    }
+}
+
+int launch_residual_batch(const bspai_matrix* A, int nrhs, const double* X, const double* Bv, double* R,
+                          const int32_t* slice_seg, int nsys, double* prmax, double* pxmax, cudaStream_t s) {
+    const int64_t total = (int64_t)A->n * nrhs;
+    if (total == 0) return BSPAI_OK;
+    ProfScope ps(BSPAI_K_RESIDUAL, s);
+    k_residual_batch<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(A->n, nrhs, A->sell.sptr, A->sell.col, A->val64,
+                                                                    X, Bv, R, slice_seg, nsys, prmax, pxmax);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    return BSPAI_OK;
+}
+
 int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
                          int u_r, cudaStream_t s) {
     if (A->n == 0) return BSPAI_OK;

@@ -33,7 +33,11 @@ int cuda_error(cudaError_t e, const char* what, const char* file, int line) {
 }
 
 static std::atomic<long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool t_count_on = true;
+void count_launches(bool on) { t_count_on = on; }
+void note_launch() {
+    if (t_count_on) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 static std::once_flag g_pool_once;
 

@@ -9,108 +9,9 @@
 // order.  Products and sums use explicit round-to-nearest intrinsics so that
 // no fused multiply-add changes the rounding of the textbook model.
 #include "common.cuh"
+#include "spmv_row.cuh"
 
 namespace bspai {
-
-template <typename XT>
-__device__ __forceinline__ float to_f32(XT v);
-template <>
-__device__ __forceinline__ float to_f32<double>(double v) { return __double2float_rn(v); }
-template <>
-__device__ __forceinline__ float to_f32<float>(float v) { return v; }
-
-template <typename YT>
-__device__ __forceinline__ YT from_f64(double v);
-template <>
-__device__ __forceinline__ double from_f64<double>(double v) { return v; }
-template <>
-__device__ __forceinline__ float from_f64<float>(double v) { return __double2float_rn(v); }
-
-// Decode one stored value of a narrow bucket to fp32 (exact: the scales are
-// powers of two and the narrow formats embed in fp32).
-template <int PREC>
-__device__ __forceinline__ float decode(const void* val, int64_t p, float scale, const float* colscale, int c);
-template <>
-__device__ __forceinline__ float decode<BSPAI_FP32>(const void* val, int64_t p, float, const float*, int) {
-    return __ldg(reinterpret_cast<const float*>(val) + p);
-}
-template <>
-__device__ __forceinline__ float decode<BSPAI_FP16>(const void* val, int64_t p, float scale, const float*, int) {
-    return __fmul_rn(__half2float(reinterpret_cast<const __half*>(val)[p]), scale);
-}
-template <>
-__device__ __forceinline__ float decode<BSPAI_BF16>(const void* val, int64_t p, float, const float*, int) {
-    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(val)[p]);
-}
-template <>
-__device__ __forceinline__ float decode<BSPAI_E4M3>(const void* val, int64_t p, float, const float* colscale, int c) {
-    __nv_fp8_e4m3 e;
-    e.__x = reinterpret_cast<const __nv_fp8_storage_t*>(val)[p];
-    return __fmul_rn(float(e), __ldg(colscale + c));
-}
-
-// fp32 partial sum of one row over one narrow bucket.  Loads are issued four
-// slots ahead of the (strictly sequential) accumulation.
-template <int PREC, typename XT>
-__device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, int64_t end,
-                                                 const XT* __restrict__ x, int64_t r) {
-    // e4m3 scales: per column of M, or per row of a transposed M; fp16: per bucket or per slice
-    const float* st = B.colscale ? B.colscale : B.rowscale;
-    const float sc = B.slicescale ? __ldg(B.slicescale + (r >> 5)) : B.scale;
-    float acc = 0.0f;
-    for (; p + 96 < end; p += 128) {
-        int c[4];
-        float v[4], xv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = __ldg(B.col + p + 32 * u);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (c[u] >= 0) {
-                v[u] = decode<PREC>(B.val, p + 32 * u, sc, st, B.colscale ? c[u] : (int)r);
-                xv[u] = to_f32<XT>(__ldg(x + c[u]));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (c[u] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[u], xv[u]));
-    }
-    for (; p < end; p += 32) {
-        int c = __ldg(B.col + p);
-        if (c >= 0) {
-            float v = decode<PREC>(B.val, p, sc, st, B.colscale ? c : (int)r);
-            acc = __fadd_rn(acc, __fmul_rn(v, to_f32<XT>(__ldg(x + c))));
-        }
-    }
-    return acc;
-}
-
-template <typename XT>
-__device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t p, int64_t end,
-                                                  const XT* __restrict__ x) {
-    const double* val = reinterpret_cast<const double*>(B.val);
-    double acc = 0.0;
-    for (; p + 96 < end; p += 128) {
-        int c[4];
-        double v[4], xv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = __ldg(B.col + p + 32 * u);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (c[u] >= 0) {
-                v[u] = __ldg(val + p + 32 * u);
-                xv[u] = (double)__ldg(x + c[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (c[u] >= 0) acc = __dadd_rn(acc, __dmul_rn(v[u], xv[u]));
-    }
-    for (; p < end; p += 32) {
-        int c = __ldg(B.col + p);
-        if (c >= 0) acc = __dadd_rn(acc, __dmul_rn(__ldg(val + p), (double)__ldg(x + c)));
-    }
-    return acc;
-}
 
 // `jd` (optional) points at a device pair {j, done} of a running GMRES: the
 // kernel does nothing once done is set, and otherwise reads x from column j
@@ -129,34 +30,8 @@ __global__ void __launch_bounds__(256) k_bspmv(const __grid_constant__ BMDev M, 
     const int64_t s = r >> 5;
     const int lane = (int)(r & 31);
     if (r >= (int64_t)ceil_div(M.n, kSlice) * kSlice) return;
-    double yi = 0.0;
-    for (int k = 0; k < M.q; ++k) {
-        const BucketDev& B = M.b[k];
-        const int64_t p0 = B.sptr[s] + lane;
-        const int64_t end = B.sptr[s + 1];
-        switch (B.prec) {
-        case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT>(B, p0, end, x)); break;
-        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, p0, end, x, r)); break;
-        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT>(B, p0, end, x, r)); break;
-        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT>(B, p0, end, x, r)); break;
-        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT>(B, p0, end, x, r)); break;
-        default: break;  // dropped entries are not stored
-        }
-    }
+    const double yi = bucketed_row<XT>(M, r, x);
     if (r < M.n) y[r] = from_f64<YT>(yi);
-}
-
-// one narrow-bucket value to fp32, format chosen at run time (uniform per warp)
-__device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c, int64_t r) {
-    switch (B.prec) {
-    case BSPAI_FP32: return decode<BSPAI_FP32>(B.val, p, B.scale, nullptr, c);
-    case BSPAI_FP16:
-        return decode<BSPAI_FP16>(B.val, p, B.slicescale ? __ldg(B.slicescale + (r >> 5)) : B.scale, nullptr, c);
-    case BSPAI_BF16: return decode<BSPAI_BF16>(B.val, p, B.scale, nullptr, c);
-    default:
-        return B.colscale ? decode<BSPAI_E4M3>(B.val, p, B.scale, B.colscale, c)
-                          : decode<BSPAI_E4M3>(B.val, p, B.scale, B.rowscale, (int)r);
-    }
 }
 
 // The same product as k_bspmv for Q non-empty buckets, organised for memory-

@@ -240,6 +240,81 @@ def rhs(A: CSR, seed: int = DEFAULT_SEED, nrhs: int = 1):
     return x, np.ascontiguousarray(b)
 
 
+def convdiff2d_9pt(g: int, peclet=(0.5, 0.5)) -> CSR:
+    """2D 9-point compact Laplacian (centre 8, eight neighbours -1) plus centred
+    convection on the four edge neighbours (-/+ P per direction, upwind side
+    -(1+P)), g x g interior grid, Dirichlet boundaries."""
+    px, py = peclet
+    n = g * g
+    r = np.arange(n, dtype=np.int64)
+    ix, iy = r % g, r // g
+    offs = [(-1, -1), (0, -1), (1, -1), (-1, 0), (0, 0), (1, 0), (-1, 1), (0, 1), (1, 1)]
+    cols = np.full((n, 9), -1, dtype=np.int64)
+    vals = np.zeros((n, 9))
+    for k, (dx, dy) in enumerate(offs):  # ascending column order: row above, own row, row below
+        ok = (ix + dx >= 0) & (ix + dx < g) & (iy + dy >= 0) & (iy + dy < g)
+        cols[:, k] = np.where(ok, r + dx + g * dy, -1)
+        v = 8.0 if (dx, dy) == (0, 0) else -1.0
+        if (dx, dy) == (-1, 0):
+            v = -(1.0 + px)
+        elif (dx, dy) == (1, 0):
+            v = -(1.0 - px)
+        elif (dx, dy) == (0, -1):
+            v = -(1.0 + py)
+        elif (dx, dy) == (0, 1):
+            v = -(1.0 - py)
+        vals[:, k] = v
+    return _from_dense_rows(cols, vals)
+
+
+def block_diagonal(mats, align: int = 32):
+    """Stack CSR matrices block-diagonally, each padded with empty rows to a
+    multiple of `align` rows.  Returns (CSR, row_off) with row_off[s] the first
+    row of system s (len nsys + 1)."""
+    row_off = [0]
+    for M in mats:
+        row_off.append(row_off[-1] + -(-M.n // align) * align)
+    n = row_off[-1]
+    lens = np.zeros(n, dtype=np.int64)
+    cols, vals = [], []
+    for s, M in enumerate(mats):
+        lens[row_off[s]:row_off[s] + M.n] = np.diff(M.row_ptr)
+        cols.append(M.col.astype(np.int64) + row_off[s])
+        if M.val is not None:
+            vals.append(M.val)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    val = np.concatenate(vals) if vals else None
+    return CSR(n, row_ptr.astype(np.int32), np.concatenate(cols).astype(np.int32), val), np.array(row_off, np.int32)
+
+
+def batch_workload(nsys: int = 512, nrhs: int = 32, nmin: float = 1e3, nmax: float = 6.4e4,
+                   seed: int = DEFAULT_SEED) -> dict:
+    """Many independent 2D convection-diffusion systems: n = g^2 with
+    g = round(sqrt(exp(U[ln nmin, ln nmax]))) (log-uniform sizes), a 5-point or
+    9-point stencil with probability 1/2, cell Peclet ~ U[0.1, 1] per direction,
+    pattern(A), nrhs right-hand sides b = A x_true with x_true ~ U[-1, 1].
+    Systems are stacked block-diagonally (padded to multiples of 32 rows); B
+    and X_true hold nrhs vectors of the stacked length."""
+    rng = np.random.default_rng(seed + 11)
+    mats, sizes = [], []
+    for _ in range(nsys):
+        g = int(round(np.sqrt(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))))
+        pe = tuple(rng.uniform(0.1, 1.0, 2))
+        A = convdiff2d(g, g, pe) if rng.random() < 0.5 else convdiff2d_9pt(g, pe)
+        mats.append(A)
+        sizes.append(A.n)
+    A, row_off = block_diagonal(mats)
+    real = np.zeros(A.n, dtype=bool)
+    for s, m in enumerate(mats):
+        real[row_off[s]:row_off[s] + m.n] = True
+    X = rng.uniform(-1.0, 1.0, size=(nrhs, A.n)) * real
+    B = np.ascontiguousarray((A.to_scipy() @ X.T).T)
+    return dict(name="batch", A=A, pattern=pattern_of(A), row_off=row_off, sizes=np.array(sizes), mats=mats,
+                nrhs=nrhs, X_true=np.ascontiguousarray(X), B=B, real=real, spai_eps=0.3,
+                precs=[FP64, FP32, FP16], bucket_eps=2.0 ** -16, tau=1e-4, u_g=FP32, u_p=FP32)
+
+
 # ---------------------------------------------------------------------------
 # Named workloads.  Each returns a dict with the matrix, the SPAI pattern and
 # the solver settings of the workload; `scale` shrinks the grid for fast cases.
