@@ -132,6 +132,17 @@ const char* bspai_last_error(void);       /* per-thread message; never NULL */
 int bspai_version(void);                  /* 10000 * major + 100 * minor + patch */
 /* Kernel launches this library has issued since it was loaded (all threads). */
 long long bspai_launch_count(void);
+/* Failure-detection self-test of the bounded grid barrier that the cooperative
+ * GMRES kernels use (no counterpart in the paper).  Launches `blocks` CTAs
+ * (1..1024, all co-resident: a cooperative launch) that meet once at that
+ * barrier.  hold = 0: an ordinary barrier, returns BSPAI_OK.  hold != 0: the
+ * arrival counter starts past the value at which the last arrival releases
+ * the barrier, so no arrival releases it; every CTA gives up after
+ * `timeout_s` seconds (0 < timeout_s <= 10) and the call returns
+ * BSPAI_TIMEOUT.  No memory fault, trap or unbounded wait is involved and the
+ * CUDA context stays usable.  Synchronises stream s.  *waited_ms, if not
+ * NULL, receives the kernel's duration (CUDA events). */
+int bspai_barrier_selftest(int blocks, int hold, double timeout_s, bspai_stream_t s, float* waited_ms);
 void bspai_opts_default(bspai_opts_t* opts);
 /* Releases any handle returned by this library (NULL is a no-op).  Enqueues
  * the frees on the stream the handle was created on. */
@@ -212,6 +223,16 @@ int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, doub
  * product uses (scale applied), as fp64.  Device buffers of length nnz(M);
  * either may be NULL. */
 int bspai_bucket_export(bspai_BM_h BM, int8_t* ids, double* stored, bspai_stream_t s);
+
+/* Which kernel form the sparse products (bspai_apply, A v and M w inside the
+ * solvers) use.  Both compute the same operations in the same order and give
+ * identical bits.  BSPAI_SPMV_AUTO (default): the form whose matrix stream is
+ * staged into shared memory by bulk copies (TMA) wherever it applies (large
+ * matrices, at most 4 stored buckets, known slice widths), else the register
+ * form.  BSPAI_SPMV_REGISTERS: always the register form.  Process-wide;
+ * affects launches issued after the call.  No counterpart in the paper. */
+enum { BSPAI_SPMV_AUTO = 0, BSPAI_SPMV_REGISTERS = 1 };
+int bspai_set_spmv_form(int form);
 
 /* y = M x by the adaptive-precision SpMV (Alg 2.3): per row and bucket a
  * partial sum accumulated in ascending column order, in fp64 for an fp64

@@ -90,6 +90,8 @@ def _sig(name, res, args):
 _sig("bspai_last_error", C.c_char_p, [])
 _sig("bspai_version", _i, [])
 _sig("bspai_launch_count", C.c_longlong, [])
+_sig("bspai_barrier_selftest", _i, [_i, _i, _d, _vp, C.POINTER(C.c_float)])
+_sig("bspai_set_spmv_form", _i, [_i])
 _sig("bspai_opts_default", None, [C.POINTER(Opts)])
 _sig("bspai_free", _i, [_vp])
 _sig("bspai_profile_enable", _i, [_i])
@@ -141,6 +143,24 @@ def _ptr(t):
 
 def version() -> int:
     return _lib.bspai_version()
+
+
+def barrier_selftest(blocks: int, hold: bool, timeout_s: float, stream=None):
+    """Runs the bounded grid barrier once; hold=True makes it never release so
+    every wait must run out.  Returns (status, kernel milliseconds)."""
+    ms = C.c_float(0.0)
+    st = _lib.bspai_barrier_selftest(int(blocks), int(bool(hold)), float(timeout_s), _stream(stream), C.byref(ms))
+    _check(st, (OK, TIMEOUT))
+    return st, float(ms.value)
+
+
+SPMV_AUTO, SPMV_REGISTERS = 0, 1
+
+
+def set_spmv_form(form: int):
+    """SPMV_AUTO: shared-memory (TMA) staged sparse products where they apply;
+    SPMV_REGISTERS: always the register form.  Same bits either way."""
+    _check(_lib.bspai_set_spmv_form(int(form)))
 
 
 def launch_count() -> int:

@@ -125,6 +125,12 @@ __device__ __noinline__ void rows_apply(const BMDev& M, int r0, int ns, const XT
     for (int lr = threadIdx.x; lr < ns; lr += blockDim.x) y[lr] = from_f64<YT>(bucketed_row<XT>(M, r0 + lr, x));
 }
 
+// rows per thread whose loads an MGS pass issues together
+template <typename T>
+struct MgsU {
+    static constexpr int U = sizeof(T) == 4 ? 8 : 4;
+};
+
 struct PairState {
     int32_t* status;   // 0 active; 1 nbe <= u; 2 ||d|| <= u ||x||; 3 stagnation; -1 non-finite
     int32_t* iters;    // GMRES steps summed over refinement steps
@@ -200,13 +206,33 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
                     const T* vi = V + (int64_t)(i <= j ? i : j) * ldv;
                     const T* vp = V + (int64_t)(i > 0 ? i - 1 : 0) * ldv;
                     T a = T(0);
-                    for (int lr = tid; lr < ns; lr += bd) {
-                        T zr = z[lr];
-                        if (i > 0) {
-                            zr = Ar::sub(zr, Ar::mul(hprev, vp[lr]));
-                            z[lr] = zr;
+                    // U rows of the thread at a time, all their loads issued before
+                    // any store (z shares V's storage, so without this every load
+                    // would wait for the previous row's store); the rows are still
+                    // accumulated in the order tid, tid + bd, tid + 2 bd, ...
+                    constexpr int U = MgsU<T>::U;
+                    for (int b0 = tid; b0 < ns; b0 += bd * U) {
+                        T zr[U], pv[U], iv[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int lr = b0 + u * bd;
+                            if (lr < ns) {
+                                zr[u] = z[lr];
+                                pv[u] = i > 0 ? vp[lr] : T(0);
+                                iv[u] = i <= j ? vi[lr] : T(0);
+                            }
                         }
-                        a = Ar::add(a, Ar::mul(i <= j ? vi[lr] : zr, zr));
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int lr = b0 + u * bd;
+                            if (lr < ns) {
+                                if (i > 0) {
+                                    zr[u] = Ar::sub(zr[u], Ar::mul(hprev, pv[u]));
+                                    z[lr] = zr[u];
+                                }
+                                a = Ar::add(a, Ar::mul(i <= j ? iv[u] : zr[u], zr[u]));
+                            }
+                        }
                     }
                     const T h = block_sum(a, s_w);
                     if (i <= j) {

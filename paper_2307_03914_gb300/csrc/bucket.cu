@@ -455,6 +455,7 @@ static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int
         B->nnz_k[k] = (int64_t)nnzk[k];
         B->scale[k] = hscale[k];
         B->maxw[k] = hwmax[k];
+        B->b[k].maxw = hwmax[k];
         D.precs[k] = precs[k];
         D.sptr[k] = B->b[k].sptr;
         D.scale[k] = hscale[k];

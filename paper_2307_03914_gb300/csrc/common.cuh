@@ -63,6 +63,7 @@ struct Sell {
     int64_t slots = 0;
     int64_t* sptr = nullptr;   // nslices + 1
     int32_t* col = nullptr;    // slots, -1 = padding
+    int32_t maxw = -1;         // widest slice in slots per row (-1: unknown)
 };
 
 // Device view of one precision bucket for the SpMV kernels.
@@ -146,6 +147,7 @@ int launch_bspmv(const BMDev& M, const void* x, int x_prec, void* y, int y_prec,
 int launch_bspmv_idx(const BMDev& M, const void* x, int x_prec, void* y, int y_prec, const int* jd,
                      int64_t ldx, int64_t ldy, int yoff, cudaStream_t s);
 BMDev single_bucket_view(const Sell& S, const void* val, int prec);
+int stage_timeout_take(cudaStream_t s);  // BSPAI_TIMEOUT if a staged SpMV gave up waiting
 
 // defined in matrix.cu
 int matrix_create(const bspai_csr_t* A, cudaStream_t s, bspai_matrix** out);
@@ -219,7 +221,7 @@ struct GridBar {
     unsigned count;
     unsigned gen;
     int err;
-    int pad;
+    unsigned seq;  // tagged-slot reductions completed on this state (k_mgs_res)
 };
 
 __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned long long timeout_ns) {

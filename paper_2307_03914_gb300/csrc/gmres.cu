@@ -232,12 +232,62 @@ __global__ void __launch_bounds__(512) k_mgs(T* __restrict__ V, int64_t ldv, int
     }
 }
 
-// Split grid reduction for k_mgs_res: grid_arrive publishes this block's
-// partial sum and arrives at the barrier; grid_wait completes the barrier and
-// returns the grid total (the block partials added in a fixed order, the same
-// value in every block).  Work placed between the two overlaps the barrier.
+// Tagged-slot grid reduction for k_mgs_res.  Every block owns one slot per
+// parity of the pass number; it publishes its partial sum there together with
+// the reduction's sequence number, value and number travelling in the same
+// 64-bit store (fp32: one word {seq, bits}; fp64: two words {seq, high half},
+// {seq, low half}).  A block has the grid total once every slot carries the
+// current number: no atomics, no fences and no separate read of the partials
+// after a release.  The sequence numbers continue across launches (the count
+// lives in GridBar::seq, advanced by block 0 after the kernel's last
+// reduction), so slots left by earlier reductions never match.  The partials
+// are added in the same fixed order as grid_wait (lane-strided, then a warp
+// butterfly), so the total is the same in every block and in every run.
 template <typename T>
-__device__ __forceinline__ void grid_arrive(T v, T* part, int slot, GridBar* bar, unsigned* s_gen, T* s_w) {
+struct TagWords;
+template <>
+struct TagWords<float> {
+    static constexpr int W = 1;
+};
+template <>
+struct TagWords<double> {
+    static constexpr int W = 2;
+};
+constexpr int kTagMaxBlocks = 160;  // slots read per lane: kTagMaxBlocks / 32 (152 SMs)
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void tag_publish(float v, unsigned long long* slot, unsigned seq) {
+    st_relaxed_u64(slot, ((unsigned long long)seq << 32) | __float_as_uint(v));
+}
+__device__ __forceinline__ void tag_publish(double v, unsigned long long* slot, unsigned seq) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    st_relaxed_u64(slot, ((unsigned long long)seq << 32) | (b >> 32));
+    st_relaxed_u64(slot + 1, ((unsigned long long)seq << 32) | (b & 0xffffffffull));
+}
+// true (and *v set) once the slot carries `seq`
+__device__ __forceinline__ bool tag_read(const unsigned long long* slot, unsigned seq, float* v) {
+    const unsigned long long a = ld_relaxed_u64(slot);
+    if ((unsigned)(a >> 32) != seq) return false;
+    *v = __uint_as_float((unsigned)a);
+    return true;
+}
+__device__ __forceinline__ bool tag_read(const unsigned long long* slot, unsigned seq, double* v) {
+    const unsigned long long a = ld_relaxed_u64(slot), b = ld_relaxed_u64(slot + 1);
+    if ((unsigned)(a >> 32) != seq || (unsigned)(b >> 32) != seq) return false;
+    *v = __longlong_as_double((long long)((a << 32) | (b & 0xffffffffull)));
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void tag_arrive(T v, unsigned long long* tags, int set, unsigned seq, T* s_w) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
     v = warp_sum(v);
@@ -246,51 +296,63 @@ __device__ __forceinline__ void grid_arrive(T v, T* part, int slot, GridBar* bar
     if (w == 0) {
         T t = lane < nw ? s_w[lane] : T(0);
         t = warp_sum(t);
-        if (lane == 0) {
-            part[(int64_t)slot * gridDim.x + blockIdx.x] = t;
-            const unsigned gen = ld_acquire_u32(&bar->gen);
-            __threadfence();
-            const unsigned arrived = atomicAdd(&bar->count, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&bar->count, 0u);
-                __threadfence();
-                atomicAdd(&bar->gen, 1u);
-            }
-            *s_gen = gen;  // released once bar->gen differs from this value
-        }
+        if (lane == 0)
+            tag_publish(t, tags + ((int64_t)set * gridDim.x + blockIdx.x) * TagWords<T>::W, seq);
     }
 }
 
+// Warp 0 polls the slots of `set` until all carry `seq` (giving up after tmo
+// ns, or when another block has flagged an error), then every thread gets the
+// total; *s_ok = 0 after a timeout.
 template <typename T>
-__device__ __forceinline__ T grid_wait(const T* part, int slot, GridBar* bar, unsigned long long tmo,
-                                       const unsigned* s_gen, T* s_tot, int* s_ok) {
-    if (threadIdx.x == 0) {
+__device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, unsigned seq, GridBar* bar,
+                                      unsigned long long tmo, T* s_tot, int* s_ok) {
+    constexpr int MS = kTagMaxBlocks / 32;
+    constexpr int TW = TagWords<T>::W;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int G = gridDim.x;
+        const unsigned long long* base = tags + (int64_t)set * G * TW;
+        T val[MS];
+        unsigned pending = 0;
+#pragma unroll
+        for (int m = 0; m < MS; ++m) {
+            val[m] = T(0);
+            if (lane + 32 * m < G) pending |= 1u << m;
+        }
         int ok = 1;
-        const unsigned gen = *s_gen;
-        if (ld_acquire_u32(&bar->gen) == gen) {
-            const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_u32(&bar->gen) == gen) {
-                if (*(volatile int*)&bar->err) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > tmo) {
+        unsigned long long t0 = 0;
+        for (int it = 0;; ++it) {
+#pragma unroll
+            for (int m = 0; m < MS; ++m)
+                if ((pending >> m) & 1u)
+                    if (tag_read(base + (int64_t)(lane + 32 * m) * TW, seq, &val[m])) pending &= ~(1u << m);
+            if (!__any_sync(0xffffffffu, pending != 0)) break;
+            int stop = 0;
+            if (lane == 0) {
+                const unsigned long long now = globaltimer_ns();
+                if (it == 0) t0 = now;
+                if (now - t0 > tmo) {
                     atomicExch(&bar->err, 1);
-                    ok = 0;
-                    break;
+                    stop = 1;
+                } else if ((it & 63) == 63 && *(volatile int*)&bar->err) {
+                    stop = 1;
                 }
-                __nanosleep(32);
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) {
+                ok = 0;
+                break;
             }
         }
-        if (*(volatile int*)&bar->err) ok = 0;
-        __threadfence();
-        *s_ok = ok;
-    }
-    __syncthreads();
-    if (!*s_ok) return T(0);
-    if (threadIdx.x < 32) {
         T t = T(0);
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-            t = Ar<T>::add(t, *(const volatile T*)&part[(int64_t)slot * gridDim.x + b]);
+#pragma unroll
+        for (int m = 0; m < MS; ++m)
+            if (lane + 32 * m < G) t = Ar<T>::add(t, val[m]);
         t = warp_sum(t);
-        if (threadIdx.x == 0) *s_tot = t;
+        if (lane == 0) {
+            *s_tot = t;
+            *s_ok = ok;
+        }
     }
     __syncthreads();
     return *s_tot;
@@ -305,22 +367,24 @@ __device__ __forceinline__ T grid_wait(const T* part, int slot, GridBar* bar, un
 // Same arithmetic as k_mgs (fp32 or fp64, no fused multiply-add).
 template <typename T, int R>
 __global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t ldv, int n, GmresState* st,
-                                                     double* H, double* cs, double* sn, double* g, T* part,
-                                                     unsigned long long tmo) {
+                                                     double* H, double* cs, double* sn, double* g,
+                                                     unsigned long long* tags, unsigned long long tmo) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* zs = reinterpret_cast<T*>(smraw);
     __shared__ T s_w[32];
     __shared__ T s_tot;
-    __shared__ unsigned s_gen;
+    __shared__ unsigned s_seq;
     __shared__ int s_ok, s_j, s_done, s_kmax;
     if (threadIdx.x == 0) {
         s_j = st->j;
         s_done = st->done;
         s_kmax = st->kmax;
+        s_seq = *(volatile unsigned*)&st->bar.seq;  // reductions of this launch are s_seq + 1, s_seq + 2, ...
     }
     __syncthreads();
     if (s_done) return;
     const int j = s_j, kmax = s_kmax;
+    const unsigned seq0 = s_seq;
     int64_t r0, r1;
     block_rows(n, r0, r1);
     const int nb = r1 > r0 ? (int)(r1 - r0) : 0;
@@ -345,7 +409,7 @@ __global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t 
         const int lr = tid + t * bd;
         if (lr < nb) acc = Ar<T>::add(acc, Ar<T>::mul(vcur[t], zs[lr]));
     }
-    grid_arrive(acc, part, 0, &st->bar, &s_gen, s_w);
+    tag_arrive(acc, tags, 0, seq0 + 1u, s_w);
     for (int i = 1; i <= j + 1; ++i) {
         if (i <= j) {
             const T* vi = V + (int64_t)i * ldv + r0;
@@ -355,7 +419,7 @@ __global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t 
                 if (lr < nb) vnext[t] = vi[lr];
             }
         }
-        const T h = grid_wait(part, (i - 1) & 1, &st->bar, tmo, &s_gen, &s_tot, &s_ok);
+        const T h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -374,11 +438,11 @@ __global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t 
                 acc = Ar<T>::add(acc, Ar<T>::mul(i <= j ? vnext[t] : zr, zr));
             }
         }
-        grid_arrive(acc, part, i & 1, &st->bar, &s_gen, s_w);
+        tag_arrive(acc, tags, i & 1, seq0 + (unsigned)i + 1u, s_w);
 #pragma unroll
         for (int t = 0; t < R; ++t) vcur[t] = vnext[t];
     }
-    const T h2 = grid_wait(part, (j + 1) & 1, &st->bar, tmo, &s_gen, &s_tot, &s_ok);
+    const T h2 = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -386,6 +450,8 @@ __global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t 
         }
         return;
     }
+    // every block has read seq0 (its first slot carries seq0 + 1): advance it
+    if (blockIdx.x == 0 && tid == 0) st->bar.seq = seq0 + (unsigned)j + 2u;
     const T hn = Ar<T>::sqrt(h2);
     const bool norm = hn > T(0) && isfinite((double)hn);
 #pragma unroll
@@ -480,6 +546,7 @@ struct GmresWork {
     void* V = nullptr;
     void* w = nullptr;
     void* part = nullptr;
+    unsigned long long* tags = nullptr;  // k_mgs_res slots: 2 parities x blocks x 2 words
     GmresState* st = nullptr;
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *norms = nullptr;
     HostFlags* hflags = nullptr;  // pinned
@@ -489,6 +556,7 @@ struct GmresWork {
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
 
+    static size_t tag_words() { return (size_t)4 * kTagMaxBlocks; }
     int alloc(int n_, int kmax_, int ug_, int up_, double timeout_s, cudaStream_t st_) {
         n = n_;
         kmax = kmax_;
@@ -517,6 +585,8 @@ struct GmresWork {
         BSPAI_TRY(dalloc(&V, es * (size_t)ldv * (size_t)(kmax + 1), s));
         BSPAI_TRY(dalloc(&w, es * (size_t)ldv, s));
         BSPAI_TRY(dalloc(&part, es * 2 * (size_t)G, s));
+        BSPAI_TRY(dalloc_t(&tags, tag_words(), s));
+        CUDA_TRY(cudaMemsetAsync(tags, 0, sizeof(unsigned long long) * tag_words(), s));
         BSPAI_TRY(dalloc_t(&st, 1, s));
         BSPAI_TRY(dalloc_t(&H, (size_t)(kmax + 1) * kmax, s));
         BSPAI_TRY(dalloc_t(&cs, (size_t)kmax + 1, s));
@@ -533,7 +603,7 @@ struct GmresWork {
         return choose_mgs(*this);
     }
     void release() {
-        dfree(V, s); dfree(w, s); dfree(part, s); dfree(st, s); dfree(H, s); dfree(cs, s);
+        dfree(V, s); dfree(w, s); dfree(part, s); dfree(tags, s); dfree(st, s); dfree(H, s); dfree(cs, s);
         dfree(sn, s); dfree(g, s); dfree(y, s); dfree(norms, s);
         V = w = part = nullptr;
         st = nullptr;
@@ -558,6 +628,7 @@ static void* pick_res(int R) {
 static int choose_mgs(GmresWork& W) {
     W.res_fn = nullptr;
     const int Gr = num_sms();
+    if (Gr > kTagMaxBlocks) return BSPAI_OK;
     const int64_t chunk = ceil_div(ceil_div(W.n, Gr), 32) * 32;
     const int R = (int)ceil_div(chunk, 1024);
     const size_t es = W.ug == BSPAI_FP64 ? 8 : 4;
@@ -641,11 +712,13 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
                 ProfScope ps(BSPAI_K_MGS, s);
                 int nn = n;
                 int64_t ld = W.ldv;
-                void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};
-                if (W.res_fn)
+                if (W.res_fn) {
+                    void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &W.tags, &W.tmo_ns};
                     BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr, 1024, W.res_smem, args, s));
-                else
+                } else {
+                    void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};
                     BSPAI_TRY(coop_launch((void*)k_mgs<T>, W.G, args, s));
+                }
             }
         }
         CUDA_TRY(cudaMemcpyAsync(W.hflags, W.st, sizeof(HostFlags), cudaMemcpyDeviceToHost, s));
@@ -670,6 +743,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
     CUDA_TRY(cudaMemcpyAsync(&hs, W.st, sizeof hs, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(hn, W.norms, sizeof hn, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    BSPAI_TRY(stage_timeout_take(s));
     out.k = hs.j;
     out.status = hs.status;
     out.beta = hs.beta;
@@ -677,8 +751,10 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
     out.dmax = hn[0];
     out.xmax = hn[1];
     if (hs.status == BSPAI_TIMEOUT) {
-        // the barrier state is undefined after a timeout: reset it for reuse
+        // the barrier state is undefined after a timeout: reset it (and the
+        // tagged slots, whose numbers restart with it) for reuse
         CUDA_TRY(cudaMemsetAsync(&W.st->bar, 0, sizeof(GridBar), s));
+        CUDA_TRY(cudaMemsetAsync(W.tags, 0, sizeof(unsigned long long) * GmresWork::tag_words(), s));
         return set_error(BSPAI_TIMEOUT, "gmres: a grid barrier exceeded its time limit");
     }
     return BSPAI_OK;
@@ -809,11 +885,62 @@ static int ir_solve(bspai_matrix* A, const double* b, const bspai_bucketed* BM, 
     return finish(code);
 }
 
+// Failure-detection self-test: the bounded grid barrier, its arrival counter
+// pre-loaded past the value at which the last arrival releases it (hold != 0),
+// so that no arrival releases it and every block's wait must run out.
+__global__ void k_barrier_selftest(GridBar* bar, unsigned long long tmo, int* failed) {
+    const bool ok = grid_sync(bar, tmo);
+    if (!ok && threadIdx.x == 0) atomicExch(failed, 1);
+}
+
 }  // namespace bspai
 
 using namespace bspai;
 
 extern "C" {
+
+int bspai_barrier_selftest(int blocks, int hold, double timeout_s, bspai_stream_t st, float* waited_ms) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (blocks < 1 || blocks > 1024 || !(timeout_s > 0) || timeout_s > 10)
+        return set_error(BSPAI_ERR_INVALID, "barrier self-test: bad arguments");
+    int dev = 0, coop = 0, per_sm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_selftest, 32, 0));
+    if (!coop || blocks > per_sm * num_sms())
+        return set_error(BSPAI_ERR_INVALID, "barrier self-test: blocks cannot be co-resident");
+    void* p = nullptr;
+    int rc = dalloc(&p, sizeof(GridBar) + sizeof(int), s);
+    if (rc) return rc;
+    GridBar* bar = (GridBar*)p;
+    int* failed = (int*)(bar + 1);
+    GridBar init{hold ? (unsigned)blocks : 0u, 0u, 0, 0};  // arrivals count from here
+    int h_failed = 0;
+    float ms = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(bar, &init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemsetAsync(failed, 0, sizeof(int), s);
+    if (!e) e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    if (!e) e = cudaEventRecord(e0, s);
+    if (!e) {
+        unsigned long long tmo = (unsigned long long)(timeout_s * 1e9);
+        void* args[] = {&bar, &tmo, &failed};
+        e = cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(blocks), dim3(32), args, 0, s);
+        note_launch();
+    }
+    if (!e) e = cudaEventRecord(e1, s);
+    if (!e) e = cudaMemcpyAsync(&h_failed, failed, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(p, s);
+    if (e) return cuda_error(e, "barrier self-test", __FILE__, __LINE__);
+    if (waited_ms) *waited_ms = ms;
+    if (h_failed) return set_error(BSPAI_TIMEOUT, "barrier self-test: the grid barrier timed out");
+    return BSPAI_OK;
+}
 
 int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h BM, bspai_M_h M, bspai_prec_t u, bspai_prec_t u_r,
                      bspai_prec_t u_g, bspai_prec_t u_p, double tol, const bspai_opts_t* opts, double* x,
@@ -949,17 +1076,18 @@ int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_
     if (occ < 1) return set_error(BSPAI_ERR_CUDA, "bspai_gmres_noalloc: cooperative kernel does not fit on an SM");
     W.G = (occ >= 2 ? 2 : 1) * num_sms();
     const size_t kx = (size_t)W.kmax;
-    size_t off[11];
-    size_t sz[10] = {es * (size_t)W.ldv * (kx + 1), es * (size_t)W.ldv, es * 2 * (size_t)W.G, sizeof(GmresState),
+    size_t off[12];
+    size_t sz[11] = {es * (size_t)W.ldv * (kx + 1), es * (size_t)W.ldv, es * 2 * (size_t)W.G, sizeof(GmresState),
                      sizeof(double) * (kx + 1) * kx, sizeof(double) * (kx + 1), sizeof(double) * (kx + 1),
-                     sizeof(double) * (kx + 2), sizeof(double) * (kx + 1), sizeof(double) * 4};
+                     sizeof(double) * (kx + 2), sizeof(double) * (kx + 1), sizeof(double) * 4,
+                     sizeof(unsigned long long) * GmresWork::tag_words()};
     off[0] = 0;
-    for (int i = 0; i < 10; ++i) off[i + 1] = align256(off[i] + sz[i]);
-    if (off[10] > kNoallocScratchBytes)
+    for (int i = 0; i < 11; ++i) off[i + 1] = align256(off[i] + sz[i]);
+    if (off[11] > kNoallocScratchBytes)
         return set_error(BSPAI_ERR_INVALID,
                          "bspai_gmres_noalloc: n = %d with kmax = %d needs %zu bytes of scratch; the fixed block "
                          "holds %zu bytes (lower kmax or use bspai_gmres)",
-                         W.n, W.kmax, off[10], kNoallocScratchBytes);
+                         W.n, W.kmax, off[11], kNoallocScratchBytes);
     unsigned char* base = nullptr;
     BSPAI_TRY(noalloc_scratch_address(reinterpret_cast<void**>(&base)));
     W.V = base + off[0];
@@ -972,12 +1100,15 @@ int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_
     W.g = reinterpret_cast<double*>(base + off[7]);
     W.y = reinterpret_cast<double*>(base + off[8]);
     W.norms = reinterpret_cast<double*>(base + off[9]);
+    W.tags = reinterpret_cast<unsigned long long*>(base + off[10]);
     static thread_local HostFlags t_flags;  // ordinary host memory
     W.hflags = &t_flags;
     BSPAI_TRY(choose_mgs(W));
     // the scratch keeps whatever the previous call left there: clear the parts
-    // that must start at zero (solver state with its grid barrier, g)
+    // that must start at zero (solver state with its grid barrier, g, the
+    // tagged slots that the barrier's sequence numbers restart with)
     CUDA_TRY(cudaMemsetAsync(W.st, 0, sizeof(GmresState), s));
+    CUDA_TRY(cudaMemsetAsync(W.tags, 0, sizeof(unsigned long long) * GmresWork::tag_words(), s));
     CUDA_TRY(cudaMemsetAsync(W.g, 0, sizeof(double) * (kx + 2), s));
     GmresResult gr;
     int rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, o.tau, nullptr, d, gr)

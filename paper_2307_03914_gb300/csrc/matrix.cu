@@ -14,7 +14,10 @@ __global__ void k_slice_width(int n, const int32_t* __restrict__ row_ptr, int64_
     int len = r < n ? row_ptr[r + 1] - row_ptr[r] : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
-    if ((r & 31) == 0) w[r >> 5] = (int64_t)len * kSlice;
+    if ((r & 31) == 0) {
+        w[r >> 5] = (int64_t)len * kSlice;
+        if (len > 0) atomicMax(reinterpret_cast<unsigned long long*>(w + nsl), (unsigned long long)len);
+    }
 }
 
 // scatter the CSR rows into their slices; padding slots get column -1, value 0
@@ -62,14 +65,18 @@ int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const doubl
     BSPAI_TRY(dalloc_t(&S.sptr, (size_t)S.nslices + 1, s));
     const int64_t rows = (int64_t)S.nslices * kSlice;
     const unsigned grid = (unsigned)ceil_div(rows, 256);
+    CUDA_TRY(cudaMemsetAsync(w + S.nslices, 0, sizeof(int64_t), s));  // widest slice (rows per slot)
     if (n > 0) {
         k_slice_width<<<grid, 256, 0, s>>>(n, row_ptr, w);
         note_launch();
         CUDA_LAUNCH_CHECK();
     }
     BSPAI_TRY(scan_exclusive_i64(w, S.sptr, S.nslices, s));
+    int64_t wmax = 0;
     CUDA_TRY(cudaMemcpyAsync(&S.slots, S.sptr + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&wmax, w + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    S.maxw = (int32_t)wmax;
     dfree(w, s);
     BSPAI_TRY(dalloc_t(&S.col, (size_t)S.slots, s));
     double* v64 = nullptr;

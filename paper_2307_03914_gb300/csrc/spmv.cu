@@ -8,6 +8,11 @@
 // future work in Section 5).  The partial sums are added in fp64 in bucket
 // order.  Products and sums use explicit round-to-nearest intrinsics so that
 // no fused multiply-add changes the rounding of the textbook model.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 #include "spmv_row.cuh"
 
@@ -27,8 +32,6 @@ __global__ void __launch_bounds__(256) k_bspmv(const __grid_constant__ BMDev M, 
         y += (j + yoff) * ldy;
     }
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t s = r >> 5;
-    const int lane = (int)(r & 31);
     if (r >= (int64_t)ceil_div(M.n, kSlice) * kSlice) return;
     const double yi = bucketed_row<XT>(M, r, x);
     if (r < M.n) y[r] = from_f64<YT>(yi);
@@ -116,6 +119,231 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
     if (r < M.n) y[r] = from_f64<YT>(yi);
 }
 
+// ---------------------------------------------------------------- TMA-staged form
+// The same product again (same operations, same order, same bits), with the
+// matrix streamed into shared memory by the bulk-copy (TMA) engine instead of
+// through registers.  Each warp owns a contiguous run of slices and a ring of
+// NS stages in shared memory; for every slice, one lane posts the slice's
+// column indices and values of every bucket (contiguous ranges in SELL-32:
+// 128 w bytes of indices, 32 w b_k bytes of values) as cp.async.bulk copies
+// completing on the stage's mbarrier, NS slices ahead of the slice it
+// computes.  The bytes in flight per SM are then set by the ring size, not by
+// registers, which is what an SpMV with 5-9 entries per row needs to keep HBM
+// busy.  Only x (and the e4m3 column scales) are gathered with ordinary loads.
+struct StageLayout {
+    int32_t col_off[8];  // byte offset of bucket k's indices in a stage
+    int32_t val_off[8];  // byte offset of bucket k's values in a stage
+    int32_t vbytes[8];   // bytes per stored value of bucket k
+    int32_t stage_bytes; // bytes per stage (multiple of 16)
+    int32_t ns;          // stages per warp
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// one stored value (in shared memory) of a narrow bucket to fp32: as decode_rt
+__device__ __forceinline__ float decode_sm(const BucketDev& B, const unsigned char* v, int i, int c, int64_t r,
+                                           float sc) {
+    switch (B.prec) {
+    case BSPAI_FP32: return reinterpret_cast<const float*>(v)[i];
+    case BSPAI_FP16: return __fmul_rn(__half2float(reinterpret_cast<const __half*>(v)[i]), sc);
+    case BSPAI_BF16: return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(v)[i]);
+    default: {
+        __nv_fp8_e4m3 e;
+        e.__x = reinterpret_cast<const __nv_fp8_storage_t*>(v)[i];
+        return __fmul_rn(float(e), B.colscale ? __ldg(B.colscale + c) : __ldg(B.rowscale + r));
+    }
+    }
+}
+
+constexpr int kStageHeader = 32;  // per stage: the slice's width of every bucket (int32 x 8)
+
+// set when a warp gave up waiting for its copies (never expected: the copies
+// depend on nothing but the memory system); read by stage_timeout_take()
+__device__ int g_stage_timeout;
+
+// Launch: blockDim = 32 * warps (<= 256), dynamic shared memory =
+// warps * NS * (8 + stage_bytes).  Q: buckets (compacted), W: slots per row
+// whose loads are all issued before any arithmetic (wider rows continue in a
+// plain loop), F64: bucket 0 is the fp64 bucket.
+template <typename XT, typename YT, int Q, int W, bool F64>
+__global__ void __launch_bounds__(256) k_bspmv_tma(const __grid_constant__ BMDev M, const XT* __restrict__ x,
+                                                   YT* __restrict__ y, const int* __restrict__ jd, int64_t ldx,
+                                                   int64_t ldy, int yoff, const __grid_constant__ StageLayout L) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    if (jd) {
+        if (jd[1]) return;
+        const int64_t j = jd[0];
+        x += j * ldx;
+        y += (j + yoff) * ldy;
+    }
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const int NS = L.ns;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm) + (int64_t)wib * NS;
+    unsigned char* ring = sm + (size_t)nwb * NS * 8 + (size_t)wib * NS * L.stage_bytes;
+    const int64_t nsl = ceil_div(M.n, kSlice);
+    const int64_t nwarps = (int64_t)gridDim.x * nwb;
+    const int64_t gw = (int64_t)blockIdx.x * nwb + wib;
+    const int64_t per = ceil_div(nsl, nwarps);
+    const int64_t s0 = gw * per;
+    const int64_t s1 = s0 + per < nsl ? s0 + per : nsl;
+    if (s0 >= s1) return;
+    const int cnt = (int)(s1 - s0);
+    // slice pointers of the slices being posted: lane l holds sptr_k[s0 + wb + l]
+    int64_t sp[Q];
+    int wb = 0;
+    auto load_window = [&]() {
+        const int64_t si = s0 + wb + lane;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) sp[k] = si <= s1 ? __ldg(M.b[k].sptr + si) : 0;
+    };
+    // warp-collective: post the copies of slice s0 + p into stage `st`
+    auto post = [&](int p, int st) {
+        if (p - wb >= 31) {
+            wb += 31;
+            load_window();
+        }
+        unsigned char* stage = ring + (size_t)st * L.stage_bytes;
+        int64_t b0[Q], len[Q];
+        unsigned total = 0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            b0[k] = __shfl_sync(0xffffffffu, sp[k], p - wb);
+            len[k] = __shfl_sync(0xffffffffu, sp[k], p - wb + 1) - b0[k];
+            total += (unsigned)(len[k] * (4 + L.vbytes[k]));
+        }
+        if (lane == 0) {
+            int32_t* hdr = reinterpret_cast<int32_t*>(stage);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) hdr[k] = (int32_t)(len[k] >> 5);
+            mbar_arrive_expect(bars + st, total);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                if (len[k] == 0) continue;
+                bulk_g2s(stage + L.col_off[k], M.b[k].col + b0[k], (unsigned)(len[k] * 4), bars + st);
+                bulk_g2s(stage + L.val_off[k],
+                         reinterpret_cast<const unsigned char*>(M.b[k].val) + b0[k] * L.vbytes[k],
+                         (unsigned)(len[k] * L.vbytes[k]), bars + st);
+            }
+        }
+    };
+    load_window();
+    if (lane == 0) {
+        for (int t = 0; t < NS; ++t) mbar_init(bars + t, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    for (int t = 0; t < NS && t < cnt; ++t) post(t, t);
+    for (int i = 0; i < cnt; ++i) {
+        const int64_t s = s0 + i;
+        const int st = i % NS;
+        const unsigned char* stage = ring + (size_t)st * L.stage_bytes;
+        const unsigned par = (unsigned)((i / NS) & 1);
+        if (!mbar_try_wait(bars + st, par)) {  // bounded wait (2 s) for the stage's copies
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(bars + st, par)) {
+                if (globaltimer_ns() - t0 > 2000000000ull) {
+                    if (lane == 0) atomicExch(&g_stage_timeout, 1);
+                    return;
+                }
+            }
+        }
+        const int64_t r = s * kSlice + lane;
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(stage);
+        // every load of the slice first (indices and values from shared memory, x and
+        // e4m3 scales from global), then the partial sums in ascending column order
+        int w[Q], c[Q][W];
+        float v[Q][W], xf[Q][W];
+        double vd[F64 ? W : 1], xd[F64 ? W : 1];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            w[k] = hdr[k];
+            const int32_t* cs = reinterpret_cast<const int32_t*>(stage + L.col_off[k]);
+#pragma unroll
+            for (int l = 0; l < W; ++l) c[k][l] = l < w[k] ? cs[32 * l + lane] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const BucketDev& B = M.b[k];
+            const unsigned char* vs = stage + L.val_off[k];
+            const bool f64 = F64 && k == 0;
+            const float sc = (!f64 && B.slicescale) ? __ldg(B.slicescale + s) : B.scale;
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+                const int cc = c[k][l];
+                if (cc >= 0) {
+                    if (f64) {
+                        vd[F64 ? l : 0] = reinterpret_cast<const double*>(vs)[32 * l + lane];
+                        xd[F64 ? l : 0] = (double)__ldg(x + cc);
+                    } else {
+                        v[k][l] = decode_sm(B, vs, 32 * l + lane, cc, r, sc);
+                        xf[k][l] = to_f32<XT>(__ldg(x + cc));
+                    }
+                }
+            }
+        }
+        double yi = 0.0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const BucketDev& B = M.b[k];
+            const int32_t* cs = reinterpret_cast<const int32_t*>(stage + L.col_off[k]);
+            const unsigned char* vs = stage + L.val_off[k];
+            if (F64 && k == 0) {
+                double acc = 0.0;
+#pragma unroll
+                for (int l = 0; l < W; ++l)
+                    if (c[k][l] >= 0) acc = __dadd_rn(acc, __dmul_rn(vd[F64 ? l : 0], xd[F64 ? l : 0]));
+                for (int l = W; l < w[k]; ++l) {
+                    const int cc = cs[32 * l + lane];
+                    if (cc >= 0)
+                        acc = __dadd_rn(acc, __dmul_rn(reinterpret_cast<const double*>(vs)[32 * l + lane],
+                                                       (double)__ldg(x + cc)));
+                }
+                yi = __dadd_rn(yi, acc);
+            } else {
+                const float sc = B.slicescale ? __ldg(B.slicescale + s) : B.scale;
+                float acc = 0.0f;
+#pragma unroll
+                for (int l = 0; l < W; ++l)
+                    if (c[k][l] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[k][l], xf[k][l]));
+                for (int l = W; l < w[k]; ++l) {
+                    const int cc = cs[32 * l + lane];
+                    if (cc >= 0)
+                        acc = __fadd_rn(acc, __fmul_rn(decode_sm(B, vs, 32 * l + lane, cc, r, sc),
+                                                       to_f32<XT>(__ldg(x + cc))));
+                }
+                yi = __dadd_rn(yi, (double)acc);
+            }
+        }
+        __syncwarp();  // every lane is done with this stage
+        if (i + NS < cnt) post(i + NS, st);
+        if (r < M.n) y[r] = from_f64<YT>(yi);
+    }
+}
+
 template <typename XT, typename YT>
 using BspmvFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int);
 
@@ -143,7 +371,7 @@ BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     d.b[0].rowscale = nullptr;
     d.b[0].slicescale = nullptr;
     d.b[0].nnz = -1;
-    d.b[0].maxw = -1;
+    d.b[0].maxw = S.maxw;
     return d;
 }
 
@@ -158,6 +386,100 @@ static BMDev compact_buckets(const BMDev& M) {
 }
 
 template <typename XT, typename YT>
+using TmaFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int, StageLayout);
+
+template <typename XT, typename YT>
+static TmaFn<XT, YT> pick_tma(int Q, int W, bool f64) {
+#define BSPAI_PICK_TMA(q, w)                                                                  \
+    if (Q == q && W == w) return f64 ? (TmaFn<XT, YT>)k_bspmv_tma<XT, YT, q, w, true>          \
+                                     : (TmaFn<XT, YT>)k_bspmv_tma<XT, YT, q, w, false>;
+    BSPAI_PICK_TMA(1, 4) BSPAI_PICK_TMA(1, 8) BSPAI_PICK_TMA(2, 4) BSPAI_PICK_TMA(2, 8) BSPAI_PICK_TMA(3, 4)
+    BSPAI_PICK_TMA(4, 4)
+#undef BSPAI_PICK_TMA
+    return nullptr;
+}
+
+static int prec_value_bytes(int prec) {
+    switch (prec) {
+    case BSPAI_FP64: return 8;
+    case BSPAI_FP32: return 4;
+    case BSPAI_FP16:
+    case BSPAI_BF16: return 2;
+    case BSPAI_E4M3: return 1;
+    default: return 0;
+    }
+}
+
+constexpr int kTmaWarps = 8;
+static std::atomic<int> g_spmv_form{BSPAI_SPMV_AUTO};
+static bool tma_enabled() { return g_spmv_form.load(std::memory_order_relaxed) == BSPAI_SPMV_AUTO; }
+static int align16i(int v) { return (v + 15) & ~15; }
+
+// Stage layout for the compacted buckets of M, or false when the TMA form does
+// not apply (unknown slice widths, misaligned arrays, too few slices to keep
+// every warp busy, or a stage ring that does not fit).
+static bool tma_plan(const BMDev& M, StageLayout* L, size_t* smem) {
+    if (M.q < 1 || M.q > 4) return false;
+    if (ceil_div(M.n, kSlice) < (int64_t)2 * kTmaWarps * num_sms()) return false;
+    int off = kStageHeader;
+    for (int k = 0; k < M.q; ++k) {
+        const BucketDev& B = M.b[k];
+        const int vb = prec_value_bytes(B.prec);
+        if (B.maxw < 0 || vb == 0) return false;
+        if (((uintptr_t)B.col & 15) || ((uintptr_t)B.val & 15)) return false;
+        L->vbytes[k] = vb;
+        L->col_off[k] = off;
+        off += align16i(128 * B.maxw);
+        L->val_off[k] = off;
+        off += align16i(32 * B.maxw * vb);
+    }
+    L->stage_bytes = align16i(off);
+    // four stages per warp where four 8-warp blocks still fit on an SM, else fewer
+    for (int ns : {4, 3, 2}) {
+        const size_t need = (size_t)kTmaWarps * ns * (8 + (size_t)L->stage_bytes);
+        if (need <= 56 * 1024 || (ns == 2 && need <= 112 * 1024)) {
+            L->ns = ns;
+            *smem = need;
+            return true;
+        }
+    }
+    return false;
+}
+
+template <typename XT, typename YT>
+static bool launch_tma(const BMDev& M, const XT* x, YT* y, const int* jd, int64_t ldx, int64_t ldy, int yoff,
+                       cudaStream_t s) {
+    StageLayout L{};
+    size_t smem = 0;
+    if (!tma_plan(M, &L, &smem)) return false;
+    int maxw = 0;
+    for (int k = 0; k < M.q; ++k) maxw = M.b[k].maxw > maxw ? M.b[k].maxw : maxw;
+    TmaFn<XT, YT> fn = pick_tma<XT, YT>(M.q, (maxw > 4 && M.q <= 2) ? 8 : 4, M.b[0].prec == BSPAI_FP64);
+    if (!fn) return false;
+    // per-instance opt-in to the dynamic shared memory, and its occupancy
+    static std::mutex mu;
+    static std::map<std::pair<const void*, size_t>, int> occ_cache;
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto key = std::make_pair((const void*)fn, smem);
+        auto it = occ_cache.find(key);
+        if (it == occ_cache.end()) {
+            if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * kTmaWarps, smem))
+                occ = 0;
+            occ_cache[key] = occ;
+        } else {
+            occ = it->second;
+        }
+    }
+    if (occ < 1) return false;
+    const unsigned grid = (unsigned)(num_sms() * occ);
+    fn<<<grid, 32 * kTmaWarps, smem, s>>>(M, x, y, jd, ldx, ldy, yoff, L);
+    return true;
+}
+
+template <typename XT, typename YT>
 static void launch_typed(const BMDev& M0, const XT* x, YT* y, const int* jd, int64_t ldx, int64_t ldy, int yoff,
                          unsigned grid, cudaStream_t s) {
     const BMDev M = compact_buckets(M0);
@@ -167,6 +489,7 @@ static void launch_typed(const BMDev& M0, const XT* x, YT* y, const int* jd, int
         if (M.b[k].maxw < 0) known = false;
         maxw = M.b[k].maxw > maxw ? M.b[k].maxw : maxw;
     }
+    if (tma_enabled() && launch_tma<XT, YT>(M, x, y, jd, ldx, ldy, yoff, s)) return;
     const int W = (M.q <= 2 && (!known || maxw > 4)) ? 8 : 4;
     BspmvFn<XT, YT> fn = M.q >= 1 ? pick_q<XT, YT>(M.q, W, M.b[0].prec == BSPAI_FP64) : nullptr;
     if (fn)
@@ -222,7 +545,28 @@ BMDev bspai_bucketed::dev() const {
     return d;
 }
 
+namespace bspai {
+// BSPAI_TIMEOUT if a TMA-staged SpMV gave up waiting since the last call (and
+// clears the flag); synchronises stream s
+int stage_timeout_take(cudaStream_t s) {
+    int h = 0, z = 0;
+    CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_stage_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (!h) return BSPAI_OK;
+    CUDA_TRY(cudaMemcpyToSymbolAsync(g_stage_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return set_error(BSPAI_TIMEOUT, "spmv: a shared-memory stage was not filled within its time limit");
+}
+}  // namespace bspai
+
 extern "C" {
+
+int bspai_set_spmv_form(int form) {
+    if (form != BSPAI_SPMV_AUTO && form != BSPAI_SPMV_REGISTERS)
+        return set_error(BSPAI_ERR_INVALID, "bspai_set_spmv_form: unknown form %d", form);
+    g_spmv_form.store(form);
+    return BSPAI_OK;
+}
 
 int bspai_apply(bspai_BM_h BM, const void* x, bspai_prec_t x_prec, void* y, bspai_prec_t y_prec,
                 bspai_stream_t s) {

@@ -299,6 +299,7 @@ int bspai_bucket_transpose(bspai_BM_h BM, bspai_stream_t st, bspai_BM_h* out) {
                 }
             }
             if (!rc) rc = gather_payload(T->b[k], rowlen, map, (int)es, BM->val[k], &T->val[k], s);
+            if (!rc) T->maxw[k] = T->b[k].maxw;
             map.release(s);
             dfree(rowlen, s);
         }

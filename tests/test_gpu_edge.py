@@ -153,3 +153,22 @@ def test_fp64_comparator_path(B):
     ref = O.gmres_ir(S, muf, wl["b"], "fp64", "fp64", 1e-8, 500, 10)
     assert np.abs(xg - ref["x"]).max() <= 1e-12 * np.abs(ref["x"]).max()
     assert info["gmres_iters"][0] == ref["its"][0]
+
+
+def test_barrier_wait_runs_out_and_context_survives(B):
+    """Failure detection without a fault: a grid barrier that nothing releases
+    gives up after its time limit, the call reports BSPAI_TIMEOUT, and the next
+    barrier and a full solve on the same context still work."""
+    st, ms = B.barrier_selftest(8, hold=False, timeout_s=1.0)
+    assert st == B.OK and ms < 500.0
+    st, ms = B.barrier_selftest(8, hold=True, timeout_s=0.25)
+    assert st == B.TIMEOUT
+    assert 200.0 <= ms <= 5000.0, ms
+    assert "timed out" in B.last_error()
+    st, _ = B.barrier_selftest(152, hold=False, timeout_s=1.0)
+    assert st == B.OK
+    wl = _wl(W.convdiff2d(16))
+    x, info, _, _ = _solve(B, wl)
+    assert info["status"] == B.OK
+    xt = wl["x_true"]
+    assert np.abs(x - xt).max() / np.abs(xt).max() <= 1e-10
