@@ -338,7 +338,10 @@ typedef struct {
  * A v in u_p, bucketed M v, Givens in fp64).  Each refinement step of the
  * batch is one persistent launch in which a CTA takes pairs, largest systems
  * first, and runs each GMRES with CTA barriers only; the CTA size is chosen by
- * timing the candidates on the batch (cached per shape).  kmax defaults to
+ * timing the candidates on the batch (cached per shape).  The operations of
+ * one refinement step (residuals, tests, the GMRES launch, tests) are captured
+ * once into a CUDA graph and replayed for every step (launched directly while
+ * kernel-class profiling is on).  kmax defaults to
  * min(largest system, 300).  pair_status (0 not converged, 1 nbe, 2 dx,
  * 3 stagnation, -1 non-finite) and pair_iters (device int32, nsys * nrhs,
  * pair p = rhs * nsys + system) may be NULL.  Returns BSPAI_OK when every

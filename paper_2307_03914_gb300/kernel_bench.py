@@ -1,0 +1,96 @@
+"""Standalone timing of the path's memory-bound kernels on a convection-
+diffusion workload, for roofline work and for profiler captures.
+
+    python -m paper_2307_03914_gb300.kernel_bench [--grid 128] [--reps 20] [--once]
+
+Builds A, M = SPAI(A) and the bucketed M (buckets fp64/fp32/fp16/e4m3 at
+bucket_eps = 2^-10, the GMRES setting of the benchmark) on the GPU, then times
+with CUDA events, the L2 flushed (a 256 MiB write) before every repetition:
+the bucketed product M w (fp32 in and out, as inside GMRES) and A v in u_p =
+fp32, each in both kernel forms (shared-memory staged and register), and the
+double-double residual.  Prints one JSON line per form with the median time
+and the algorithmic bytes (indices int32, x read once, y written once).
+--once runs every kernel exactly once per form with no warm-up and no
+flush: a short, fixed launch sequence for a profiler (kernel order: staged
+M w, staged A v, register M w, register A v, residual).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import bspai as B
+from . import workloads as W
+
+VBYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1, "drop": 0}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--grid", type=int, default=128)
+    p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--bucket-eps", type=float, default=2.0 ** -10)
+    p.add_argument("--once", action="store_true")
+    a = p.parse_args()
+    wl = W.workload("convdiff3d", grid=a.grid)
+    A = B.DeviceCSR.from_host(wl["A"])
+    P = B.DeviceCSR.from_host(wl["pattern"], with_values=False)
+    Ah = B.matrix_create(A)
+    M, _ = B.bspai_build(A, P, wl["spai_eps"])
+    BM, bi = B.bspai_bucket(M, a.bucket_eps, wl["precs"])
+    n, nnz = wl["A"].n, wl["A"].nnz
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.rand(n, device="cuda", dtype=torch.float32, generator=g)
+    y = torch.empty(n, device="cuda", dtype=torch.float32)
+    xd = torch.rand(n, device="cuda", dtype=torch.float64, generator=g)
+    bd = torch.from_numpy(wl["b"]).cuda()
+    rd = torch.empty(n, device="cuda", dtype=torch.float64)
+    torch.cuda.synchronize()
+    e4m3 = "e4m3" in bi["precs"] and bi["nnz_k"][bi["precs"].index("e4m3")] > 0
+    m_bytes = sum(c * (VBYTES[q] + 4) for c, q in zip(bi["nnz_k"], bi["precs"]) if q != "drop")
+    m_bytes += 4 * n + 4 * n + (4 * n if e4m3 else 0)
+    a_bytes = nnz * (4 + 4) + 4 * n + 4 * n
+    r_bytes = nnz * (8 + 4) + 3 * 8 * n
+    if a.once:
+        for form in (B.SPMV_AUTO, B.SPMV_REGISTERS):
+            B.set_spmv_form(form)
+            B.apply(BM, x, y)
+            B.spmv_up(Ah, x, y)
+        B.set_spmv_form(B.SPMV_AUTO)
+        B.residual(Ah, xd, bd, rd)
+        torch.cuda.synchronize()
+        print(json.dumps({"once": True, "n": n}))
+        return
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timeit(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(a.reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for form, name in ((B.SPMV_AUTO, "staged"), (B.SPMV_REGISTERS, "registers")):
+        B.set_spmv_form(form)
+        tm = timeit(lambda: B.apply(BM, x, y))
+        ta = timeit(lambda: B.spmv_up(Ah, x, y))
+        print(json.dumps({"form": name, "n": n, "nnz_k": bi["nnz_k"], "precs": bi["precs"],
+                          "bspmv_us": tm * 1e3, "bspmv_GBs": m_bytes / tm / 1e6, "bspmv_bytes": m_bytes,
+                          "spmvA_us": ta * 1e3, "spmvA_GBs": a_bytes / ta / 1e6, "spmvA_bytes": a_bytes}))
+    B.set_spmv_form(B.SPMV_AUTO)
+    tr = timeit(lambda: B.residual(Ah, xd, bd, rd))
+    print(json.dumps({"kernel": "residual_dd", "n": n, "us": tr * 1e3, "GBs": r_bytes / tr / 1e6, "bytes": r_bytes}))
+
+
+if __name__ == "__main__":
+    main()
