@@ -225,13 +225,17 @@ int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, doub
 int bspai_bucket_export(bspai_BM_h BM, int8_t* ids, double* stored, bspai_stream_t s);
 
 /* Which kernel form the sparse products (bspai_apply, A v and M w inside the
- * solvers) use.  Both compute the same operations in the same order and give
- * identical bits.  BSPAI_SPMV_AUTO (default): the form whose matrix stream is
- * staged into shared memory by bulk copies (TMA) wherever it applies (large
- * matrices, at most 4 stored buckets, known slice widths), else the register
- * form.  BSPAI_SPMV_REGISTERS: always the register form.  Process-wide;
- * affects launches issued after the call.  No counterpart in the paper. */
-enum { BSPAI_SPMV_AUTO = 0, BSPAI_SPMV_REGISTERS = 1 };
+ * solvers) use.  All forms compute the same operations in the same order and
+ * give identical bits.  BSPAI_SPMV_AUTO (default): kernels with the storage
+ * format of every bucket fixed at compile time for the mixes the solvers meet
+ * (one fp32 / fp64 / fp16 bucket, or fp16 + e4m3, fp32 + fp16, fp64 + fp32),
+ * else the generic register form.  BSPAI_SPMV_REGISTERS: always the generic
+ * register form.  BSPAI_SPMV_STAGED: the form whose matrix stream is staged
+ * into shared memory by bulk copies (TMA) wherever it applies (large
+ * matrices, at most 4 stored buckets), else the generic register form.
+ * Process-wide; affects launches issued after the call.  No counterpart in
+ * the paper. */
+enum { BSPAI_SPMV_AUTO = 0, BSPAI_SPMV_REGISTERS = 1, BSPAI_SPMV_STAGED = 2 };
 int bspai_set_spmv_form(int form);
 
 /* y = M x by the adaptive-precision SpMV (Alg 2.3): per row and bucket a

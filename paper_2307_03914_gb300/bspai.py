@@ -154,12 +154,13 @@ def barrier_selftest(blocks: int, hold: bool, timeout_s: float, stream=None):
     return st, float(ms.value)
 
 
-SPMV_AUTO, SPMV_REGISTERS = 0, 1
+SPMV_AUTO, SPMV_REGISTERS, SPMV_STAGED = 0, 1, 2
 
 
 def set_spmv_form(form: int):
-    """SPMV_AUTO: shared-memory (TMA) staged sparse products where they apply;
-    SPMV_REGISTERS: always the register form.  Same bits either way."""
+    """SPMV_AUTO: compile-time-format kernels for the common bucket mixes;
+    SPMV_REGISTERS: always the generic register form; SPMV_STAGED: the
+    shared-memory (TMA) staged form where it applies.  Same bits in every form."""
     _check(_lib.bspai_set_spmv_form(int(form)))
 
 

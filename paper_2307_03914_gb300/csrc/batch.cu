@@ -333,11 +333,13 @@ __global__ void k_system_norms(int n, const int64_t* __restrict__ sptr, const in
                                const double* __restrict__ val, const int32_t* __restrict__ slice_seg,
                                double* __restrict__ anorm) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
     double sum = 0.0;
-    for (int64_t p = sptr[r >> 5] + (r & 31); p < sptr[(r >> 5) + 1]; p += kSlice)
-        if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
-    atomic_max_nonneg(anorm + slice_seg[r >> 5], sum);
+    if (r < n)
+        for (int64_t p = sptr[r >> 5] + (r & 31); p < sptr[(r >> 5) + 1]; p += kSlice)
+            if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
+    // one slice per warp, so one system: one atomic per warp
+    sum = warp_max_bits(sum);
+    if ((threadIdx.x & 31) == 0 && r < n && sum != 0.0) atomic_max_nonneg(anorm + slice_seg[r >> 5], sum);
 }
 
 __global__ void k_pair_bmax(int n, int nrhs, int nsys, const double* __restrict__ Bv,

@@ -71,12 +71,15 @@ __global__ void k_norm_rows(int n, const int64_t* __restrict__ sptr, const float
                             const int32_t* __restrict__ rowlen, const int32_t* __restrict__ slice_seg,
                             double* __restrict__ norm) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int64_t b = sptr[r >> 5] + (r & 31);
-    const int len = rowlen[r];
     double s = 0.0;
-    for (int l = 0; l < len; ++l) s = __dadd_rn(s, fabs((double)val[b + (int64_t)l * kSlice]));
-    atomic_max_nonneg(norm + seg_of(slice_seg, r >> 5), s);
+    if (r < n) {
+        const int64_t b = sptr[r >> 5] + (r & 31);
+        const int len = rowlen[r];
+        for (int l = 0; l < len; ++l) s = __dadd_rn(s, fabs((double)val[b + (int64_t)l * kSlice]));
+    }
+    // the warp's rows form one slice (one segment): one atomic per warp
+    s = warp_max_bits(s);
+    if ((threadIdx.x & 31) == 0 && r < n && s != 0.0) atomic_max_nonneg(norm + seg_of(slice_seg, r >> 5), s);
 }
 
 __global__ void k_thresholds(const __grid_constant__ BucketParams P, int nseg, const double* __restrict__ norm,

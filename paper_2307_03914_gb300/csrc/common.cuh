@@ -207,6 +207,18 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
+// max over the warp of a non-negative double (or NaN) by its bit pattern, the
+// order atomic_max_nonneg uses, so the warp's maximum then one atomic per warp
+// stores exactly what one atomic per thread would
+__device__ __forceinline__ double warp_max_bits(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    return __longlong_as_double((long long)b);
+}
 __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
     atomicMax(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));
 }

@@ -360,13 +360,14 @@ __device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, u
 
 // MGS step with the new vector z resident on chip: one block per SM owns a
 // contiguous range of rows, holds z for them in shared memory for all j + 2
-// passes, and streams each basis vector v_i exactly once (R rows per thread,
-// all loads of a pass issued before the thread waits on the previous pass's
-// barrier).  Per pass i: z <- z - h_{i-1} v_{i-1} (v_{i-1} kept in registers),
+// passes, and streams each basis vector v_i exactly once (R rows per thread
+// of a BD-thread block, all loads of a pass issued before the thread waits on
+// the previous pass's reduction; BD = 512 for many rows per block, so that
+// the 2 R values a thread keeps stay in registers).  Per pass i: z <- z - h_{i-1} v_{i-1} (v_{i-1} kept in registers),
 // partial += v_i . z, arrive; the last pass forms ||z||_2 and writes v_{j+1}.
 // Same arithmetic as k_mgs (fp32 or fp64, no fused multiply-add).
-template <typename T, int R>
-__global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t ldv, int n, GmresState* st,
+template <typename T, int R, int BD>
+__global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ldv, int n, GmresState* st,
                                                      double* H, double* cs, double* sn, double* g,
                                                      unsigned long long* tags, unsigned long long tmo) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(1024, 1) k_mgs_res(T* __restrict__ V, int64_t 
     block_rows(n, r0, r1);
     const int nb = r1 > r0 ? (int)(r1 - r0) : 0;
     const int tid = threadIdx.x;
-    const int bd = blockDim.x;
+    constexpr int bd = BD;
     T* z = V + (int64_t)(j + 1) * ldv + r0;
     const T* v0 = V + r0;
     T vcur[R], vnext[R];
@@ -552,6 +553,7 @@ struct GmresWork {
     HostFlags* hflags = nullptr;  // pinned
     unsigned long long tmo_ns = 2000000000ull;
     void* res_fn = nullptr;  // k_mgs_res instance, or null for k_mgs
+    int res_bd = 1024;       // its block size
     int Gr = 0;              // its grid: one block of 1024 threads per SM
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
@@ -612,35 +614,43 @@ struct GmresWork {
 };
 
 template <typename T>
-static void* pick_res(int R) {
-    if (R <= 1) return (void*)k_mgs_res<T, 1>;
-    if (R <= 2) return (void*)k_mgs_res<T, 2>;
-    if (R <= 4) return (void*)k_mgs_res<T, 4>;
-    if (R <= 8) return (void*)k_mgs_res<T, 8>;
-    if (sizeof(T) == 4 && R <= 12) return (void*)k_mgs_res<float, 12>;
-    if (sizeof(T) == 4 && R <= 14) return (void*)k_mgs_res<float, 14>;
-    if (sizeof(T) == 4 && R <= 16) return (void*)k_mgs_res<float, 16>;
+static void* pick_res(int64_t chunk, int* bd) {
+    const int R = (int)ceil_div(chunk, 1024);
+    *bd = 1024;
+    if (R <= 1) return (void*)k_mgs_res<T, 1, 1024>;
+    if (R <= 2) return (void*)k_mgs_res<T, 2, 1024>;
+    if (R <= 4) return (void*)k_mgs_res<T, 4, 1024>;
+    if (R <= 8) return (void*)k_mgs_res<T, 8, 1024>;
+    // more rows per block: 512 threads with twice the rows each
+    const int R2 = (int)ceil_div(chunk, 512);
+    *bd = 512;
+    if (R2 <= 16) return (void*)k_mgs_res<T, 16, 512>;
+    if (sizeof(T) == 4 && R2 <= 24) return (void*)k_mgs_res<float, 24, 512>;
+    if (sizeof(T) == 4 && R2 <= 28) return (void*)k_mgs_res<float, 28, 512>;
+    if (sizeof(T) == 4 && R2 <= 32) return (void*)k_mgs_res<float, 32, 512>;
     return nullptr;
 }
 
-// Use the on-chip MGS kernel when one block of 1024 threads per SM can hold
-// its rows of z in shared memory with at most 16 (fp32) / 8 (fp64) rows per thread.
+// Use the on-chip MGS kernel when one block per SM can hold its rows of z in
+// shared memory (at most 200 KB) with at most 32 (fp32) / 16 (fp64) rows per
+// thread of a 512-thread block.
 static int choose_mgs(GmresWork& W) {
     W.res_fn = nullptr;
     const int Gr = num_sms();
     if (Gr > kTagMaxBlocks) return BSPAI_OK;
     const int64_t chunk = ceil_div(ceil_div(W.n, Gr), 32) * 32;
-    const int R = (int)ceil_div(chunk, 1024);
     const size_t es = W.ug == BSPAI_FP64 ? 8 : 4;
     const size_t smem = (size_t)chunk * es;
     if (smem > 200 * 1024) return BSPAI_OK;
-    void* fn = es == 8 ? pick_res<double>(R) : pick_res<float>(R);
+    int bd = 1024;
+    void* fn = es == 8 ? pick_res<double>(chunk, &bd) : pick_res<float>(chunk, &bd);
     if (!fn) return BSPAI_OK;
     CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bd, smem));
     if (occ < 1) return BSPAI_OK;
     W.res_fn = fn;
+    W.res_bd = bd;
     W.Gr = Gr;
     W.res_smem = smem;
     return BSPAI_OK;
@@ -714,7 +724,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
                 int64_t ld = W.ldv;
                 if (W.res_fn) {
                     void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &W.tags, &W.tmo_ns};
-                    BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr, 1024, W.res_smem, args, s));
+                    BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr, W.res_bd, W.res_smem, args, s));
                 } else {
                     void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};
                     BSPAI_TRY(coop_launch((void*)k_mgs<T>, W.G, args, s));

@@ -100,12 +100,15 @@ int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const doubl
 __global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                   const double* __restrict__ val, double* __restrict__ out) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int64_t s = r >> 5;
     double sum = 0.0;
-    for (int64_t p = sptr[s] + (r & 31); p < sptr[s + 1]; p += kSlice)
-        if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
-    atomic_max_nonneg(out, sum);
+    if (r < n) {
+        const int64_t s = r >> 5;
+        for (int64_t p = sptr[s] + (r & 31); p < sptr[s + 1]; p += kSlice)
+            if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
+    }
+    // the max of the warp's rows first: one atomic per warp, not per row
+    sum = warp_max_bits(sum);
+    if ((threadIdx.x & 31) == 0 && sum != 0.0) atomic_max_nonneg(out, sum);
 }
 
 int launch_row_abs_sum_max(const Sell& S, const double* val, double* out, cudaStream_t s) {

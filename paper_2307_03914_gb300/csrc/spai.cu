@@ -56,6 +56,16 @@ struct SpaiCounters {
     int pad;
 };
 
+// Shared memory of one warp (bytes): dJ (fp64, |J|), J, mbar, R's diagonal,
+// A's row start and the entry offset of every j in J (int32, |J| + 1), the
+// sort buffer (lp2), I, Abar (|I| x |J|), ebar / Q^T ebar, sbar, and per
+// gathered entry its column (then its position in I), scaled value and q.
+__host__ __device__ __forceinline__ size_t spai_warp_bytes(int jmax, int lmax, int lp2) {
+    return ((size_t)jmax * 8 + (size_t)jmax * 4 * 4 + (size_t)(jmax + 1) * 4 + (size_t)lp2 * 4 +
+            (size_t)lmax * 4 + (size_t)lmax * jmax * 4 + (size_t)lmax * 4 * 2 + (size_t)lmax * 4 * 3 + 15) &
+           ~(size_t)15;
+}
+
 __device__ __forceinline__ int lower_bound_i32(const int* a, int n, int v) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -79,35 +89,61 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
     if (k >= n) return;
 
     // per-warp shared-memory carve-up
-    const size_t per_warp = ((size_t)jmax * 8 + (size_t)jmax * 4 * 3 + (size_t)lp2 * 4 + (size_t)lmax * 4 +
-                             (size_t)lmax * jmax * 4 + (size_t)lmax * 4 * 2 + 15) & ~(size_t)15;
+    const size_t per_warp = spai_warp_bytes(jmax, lmax, lp2);
     unsigned char* base = smem + per_warp * wib;
     double* dJ = reinterpret_cast<double*>(base);
     int* J = reinterpret_cast<int*>(dJ + jmax);
     float* mv = reinterpret_cast<float*>(J + jmax);
     float* rdiag = mv + jmax;
-    int* cand = reinterpret_cast<int*>(rdiag + jmax);
+    int* rbeg = reinterpret_cast<int*>(rdiag + jmax);
+    int* eoff = rbeg + jmax;
+    int* cand = eoff + jmax + 1;
     int* I = cand + lp2;
     float* Ab = reinterpret_cast<float*>(I + lmax);
     float* cv = Ab + (size_t)lmax * jmax;
     float* sv = cv + lmax;
+    int* ecol = reinterpret_cast<int*>(sv + lmax);
+    float* eval = reinterpret_cast<float*>(ecol + lmax);
+    int* eq = reinterpret_cast<int*>(eval + lmax);
 
+    // J, d_J and the bounds of rows J of A, all loads in one round
     const int nJ = mrowlen[k];
     const int64_t mbase = msptr[k >> 5] + (k & 31);
     for (int q = lane; q < nJ; q += 32) {
         const int j = mcol[mbase + (int64_t)q * kSlice];
         J[q] = j;
         dJ[q] = d[j];
+        const int rb = arp[j];
+        rbeg[q] = rb;
+        eoff[q] = arp[j + 1] - rb;
     }
     __syncwarp();
-
-    // gather the candidate rows of the shadow
-    int L = 0;
-    for (int q = 0; q < nJ; ++q) {
-        const int j = J[q];
-        const int rb = arp[j], len = arp[j + 1] - rb;
-        for (int t = lane; t < len; t += 32) cand[L + t] = acol[rb + t];
-        L += len;
+    if (lane == 0) {
+        int acc = 0;
+        for (int q = 0; q < nJ; ++q) {
+            const int len = eoff[q];
+            eoff[q] = acc;
+            acc += len;
+        }
+        eoff[nJ] = acc;
+    }
+    __syncwarp();
+    const int L = eoff[nJ];
+    // every entry of rows J of A, gathered at once: its column, its value
+    // scaled by d_j and rounded to u_f (the entries of Abar), and its q
+    for (int t = lane; t < L; t += 32) {
+        int lo = 0, hi = nJ;  // the q with eoff[q] <= t < eoff[q + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (eoff[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int e = rbeg[lo] + (t - eoff[lo]);
+        const int c = acol[e];
+        ecol[t] = c;
+        cand[t] = c;
+        eval[t] = __double2float_rn(__dmul_rn(aval[e], dJ[lo]));
+        eq[t] = lo;
     }
     int LP = 2;
     while (LP < L) LP <<= 1;
@@ -152,13 +188,10 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
         const int pk = lower_bound_i32(I, nI, (int)k);
         const bool k_in = pk < nI && I[pk] == (int)k;
         if (lane == 0 && k_in) cv[pk] = 1.0f;
-        for (int q = 0; q < nJ; ++q) {
-            const int j = J[q];
-            const int rb = arp[j], len = arp[j + 1] - rb;
-            for (int t = lane; t < len; t += 32) {
-                const int p = lower_bound_i32(I, nI, acol[rb + t]);
-                Ab[q * nI + p] = __double2float_rn(__dmul_rn(aval[rb + t], dJ[q]));
-            }
+        for (int t = lane; t < L; t += 32) {
+            const int p = lower_bound_i32(I, nI, ecol[t]);
+            ecol[t] = p;  // from here on: the entry's row in Abar
+            Ab[eq[t] * nI + p] = eval[t];
         }
         __syncwarp();
         float fro = 0.0f;
@@ -213,13 +246,10 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
             if (lane == 0 && k_in) sv[pk] = -1.0f;
             __syncwarp();
             for (int q = 0; q < nJ; ++q) {
-                const int j = J[q];
-                const int rb = arp[j], len = arp[j + 1] - rb;
                 const float mq = mv[q];
-                for (int t = lane; t < len; t += 32) {
-                    const int p = lower_bound_i32(I, nI, acol[rb + t]);
-                    const float a = __double2float_rn(__dmul_rn(aval[rb + t], dJ[q]));
-                    sv[p] = __fadd_rn(sv[p], __fmul_rn(a, mq));
+                for (int t = eoff[q] + lane; t < eoff[q + 1]; t += 32) {
+                    const int p = ecol[t];
+                    sv[p] = __fadd_rn(sv[p], __fmul_rn(eval[t], mq));
                 }
                 __syncwarp();
             }
@@ -327,8 +357,7 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
     const int lmax = hs[1] > 0 ? hs[1] : 1;
     int lp2 = 32;
     while (lp2 < lmax) lp2 <<= 1;
-    const size_t per_warp = ((size_t)jmax * 8 + (size_t)jmax * 4 * 3 + (size_t)lp2 * 4 + (size_t)lmax * 4 +
-                             (size_t)lmax * jmax * 4 + (size_t)lmax * 4 * 2 + 15) & ~(size_t)15;
+    const size_t per_warp = spai_warp_bytes(jmax, lmax, lp2);
     const size_t smem_cap = 200 * 1024;
     int warps = 8;
     while (warps > 1 && per_warp * warps > smem_cap) warps >>= 1;

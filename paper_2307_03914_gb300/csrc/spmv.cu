@@ -9,6 +9,7 @@
 // order.  Products and sums use explicit round-to-nearest intrinsics so that
 // no fused multiply-add changes the rounding of the textbook model.
 #include <atomic>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -344,6 +345,152 @@ __global__ void __launch_bounds__(256) k_bspmv_tma(const __grid_constant__ BMDev
     }
 }
 
+// ---------------------------------------------------------------- fixed-format form
+// The register form again with the storage format of every bucket fixed at
+// compile time (the bucket mixes that occur on the solver's hot path), so that
+// decoding needs no run-time dispatch.  Same operations, same order, same bits.
+template <int P>
+struct FixDec;
+template <>
+struct FixDec<BSPAI_FP32> {
+    static __device__ __forceinline__ float get(const BucketDev& B, int64_t p, float, int, int64_t) {
+        return __ldg(reinterpret_cast<const float*>(B.val) + p);
+    }
+};
+template <>
+struct FixDec<BSPAI_FP16> {
+    static __device__ __forceinline__ float get(const BucketDev& B, int64_t p, float sc, int, int64_t) {
+        return __fmul_rn(__half2float(__ldg(reinterpret_cast<const __half*>(B.val) + p)), sc);
+    }
+};
+template <>
+struct FixDec<BSPAI_BF16> {
+    static __device__ __forceinline__ float get(const BucketDev& B, int64_t p, float, int, int64_t) {
+        return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(B.val) + p));
+    }
+};
+template <>
+struct FixDec<BSPAI_E4M3> {
+    static __device__ __forceinline__ float get(const BucketDev& B, int64_t p, float, int c, int64_t r) {
+        __nv_fp8_e4m3 e;
+        e.__x = __ldg(reinterpret_cast<const __nv_fp8_storage_t*>(B.val) + p);
+        return __fmul_rn(float(e), B.colscale ? __ldg(B.colscale + c) : __ldg(B.rowscale + r));
+    }
+};
+
+// One row's share of one bucket: slot bounds, then W column indices, then
+// values and x entries, then the partial sum (slots beyond W in a plain loop).
+template <int P, int W, typename XT>
+struct FixRow {
+    using V = typename std::conditional<P == BSPAI_FP64, double, float>::type;
+    int64_t base;
+    int w;
+    int c[W];
+    V v[W], xv[W];
+    __device__ __forceinline__ void ptrs(const BucketDev& B, int64_t s, int lane) {
+        const int64_t b0 = __ldg(B.sptr + s);
+        base = b0 + lane;
+        w = (int)((__ldg(B.sptr + s + 1) - b0) >> 5);
+    }
+    __device__ __forceinline__ void cols(const BucketDev& B) {
+#pragma unroll
+        for (int l = 0; l < W; ++l) c[l] = l < w ? __ldg(B.col + base + 32 * l) : -1;
+    }
+    __device__ __forceinline__ V dec(const BucketDev& B, int64_t p, float sc, int cc, int64_t r) const {
+        if constexpr (P == BSPAI_FP64) return __ldg(reinterpret_cast<const double*>(B.val) + p);
+        else return FixDec<P>::get(B, p, sc, cc, r);
+    }
+    __device__ __forceinline__ V xin(const XT* __restrict__ x, int cc) const {
+        if constexpr (P == BSPAI_FP64) return (double)__ldg(x + cc);
+        else return to_f32<XT>(__ldg(x + cc));
+    }
+    __device__ __forceinline__ void vals(const BucketDev& B, const XT* __restrict__ x, float sc, int64_t r) {
+#pragma unroll
+        for (int l = 0; l < W; ++l)
+            if (c[l] >= 0) {
+                v[l] = dec(B, base + 32 * l, sc, c[l], r);
+                xv[l] = xin(x, c[l]);
+            }
+    }
+    __device__ __forceinline__ double sum(const BucketDev& B, const XT* __restrict__ x, float sc, int64_t r) const {
+        if constexpr (P == BSPAI_FP64) {
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < W; ++l)
+                if (c[l] >= 0) acc = __dadd_rn(acc, __dmul_rn(v[l], xv[l]));
+            for (int l = W; l < w; ++l) {
+                const int cc = __ldg(B.col + base + 32 * l);
+                if (cc >= 0) acc = __dadd_rn(acc, __dmul_rn(dec(B, base + 32 * l, sc, cc, r), xin(x, cc)));
+            }
+            return acc;
+        } else {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < W; ++l)
+                if (c[l] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[l], xv[l]));
+            for (int l = W; l < w; ++l) {
+                const int cc = __ldg(B.col + base + 32 * l);
+                if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(dec(B, base + 32 * l, sc, cc, r), xin(x, cc)));
+            }
+            return (double)acc;
+        }
+    }
+};
+
+// P1 < 0: one bucket
+template <typename XT, typename YT, int P0, int W0, int P1, int W1>
+__global__ void __launch_bounds__(256) k_bspmv_fix(const __grid_constant__ BMDev M, const XT* __restrict__ x,
+                                                   YT* __restrict__ y, const int* __restrict__ jd, int64_t ldx,
+                                                   int64_t ldy, int yoff) {
+    if (jd) {
+        if (jd[1]) return;
+        const int64_t j = jd[0];
+        x += j * ldx;
+        y += (j + yoff) * ldy;
+    }
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)ceil_div(M.n, kSlice) * kSlice) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    FixRow<P0, W0, XT> a;
+    FixRow<(P1 < 0 ? BSPAI_FP32 : P1), W1, XT> b;
+    const float sc0 = M.b[0].slicescale ? __ldg(M.b[0].slicescale + s) : M.b[0].scale;
+    float sc1 = 1.0f;
+    a.ptrs(M.b[0], s, lane);
+    if constexpr (P1 >= 0) {
+        sc1 = M.b[1].slicescale ? __ldg(M.b[1].slicescale + s) : M.b[1].scale;
+        b.ptrs(M.b[1], s, lane);
+    }
+    a.cols(M.b[0]);
+    if constexpr (P1 >= 0) b.cols(M.b[1]);
+    a.vals(M.b[0], x, sc0, r);
+    if constexpr (P1 >= 0) b.vals(M.b[1], x, sc1, r);
+    double yi = __dadd_rn(0.0, a.sum(M.b[0], x, sc0, r));
+    if constexpr (P1 >= 0) yi = __dadd_rn(yi, b.sum(M.b[1], x, sc1, r));
+    if (r < M.n) y[r] = from_f64<YT>(yi);
+}
+
+template <typename XT, typename YT>
+using FixFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int);
+
+// the compiled bucket mixes: one bucket (fp32, fp64, fp16), or two
+// consecutive stored formats (fp16 + e4m3, fp32 + fp16, fp64 + fp32)
+template <typename XT, typename YT>
+static FixFn<XT, YT> pick_fix(const BMDev& M, int W) {
+#define BSPAI_FIX1(p, w) \
+    if (M.q == 1 && M.b[0].prec == p && W == w) return k_bspmv_fix<XT, YT, p, w, -1, 4>;
+#define BSPAI_FIX2(p0, p1, w) \
+    if (M.q == 2 && M.b[0].prec == p0 && M.b[1].prec == p1 && W == w) return k_bspmv_fix<XT, YT, p0, w, p1, w>;
+    BSPAI_FIX1(BSPAI_FP32, 4) BSPAI_FIX1(BSPAI_FP32, 8) BSPAI_FIX1(BSPAI_FP64, 4) BSPAI_FIX1(BSPAI_FP64, 8)
+    BSPAI_FIX1(BSPAI_FP16, 4) BSPAI_FIX1(BSPAI_FP16, 8)
+    BSPAI_FIX2(BSPAI_FP16, BSPAI_E4M3, 4) BSPAI_FIX2(BSPAI_FP16, BSPAI_E4M3, 8)
+    BSPAI_FIX2(BSPAI_FP32, BSPAI_FP16, 4) BSPAI_FIX2(BSPAI_FP32, BSPAI_FP16, 8)
+    BSPAI_FIX2(BSPAI_FP64, BSPAI_FP32, 4) BSPAI_FIX2(BSPAI_FP64, BSPAI_FP32, 8)
+#undef BSPAI_FIX1
+#undef BSPAI_FIX2
+    return nullptr;
+}
+
 template <typename XT, typename YT>
 using BspmvFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int);
 
@@ -412,7 +559,6 @@ static int prec_value_bytes(int prec) {
 
 constexpr int kTmaWarps = 8;
 static std::atomic<int> g_spmv_form{BSPAI_SPMV_AUTO};
-static bool tma_enabled() { return g_spmv_form.load(std::memory_order_relaxed) == BSPAI_SPMV_AUTO; }
 static int align16i(int v) { return (v + 15) & ~15; }
 
 // Stage layout for the compacted buckets of M, or false when the TMA form does
@@ -489,8 +635,15 @@ static void launch_typed(const BMDev& M0, const XT* x, YT* y, const int* jd, int
         if (M.b[k].maxw < 0) known = false;
         maxw = M.b[k].maxw > maxw ? M.b[k].maxw : maxw;
     }
-    if (tma_enabled() && launch_tma<XT, YT>(M, x, y, jd, ldx, ldy, yoff, s)) return;
     const int W = (M.q <= 2 && (!known || maxw > 4)) ? 8 : 4;
+    const int form = g_spmv_form.load(std::memory_order_relaxed);
+    if (form == BSPAI_SPMV_AUTO && known) {
+        if (FixFn<XT, YT> ff = pick_fix<XT, YT>(M, W)) {
+            ff<<<grid, 256, 0, s>>>(M, x, y, jd, ldx, ldy, yoff);
+            return;
+        }
+    }
+    if (form == BSPAI_SPMV_STAGED && launch_tma<XT, YT>(M, x, y, jd, ldx, ldy, yoff, s)) return;
     BspmvFn<XT, YT> fn = M.q >= 1 ? pick_q<XT, YT>(M.q, W, M.b[0].prec == BSPAI_FP64) : nullptr;
     if (fn)
         fn<<<grid, 256, 0, s>>>(M, x, y, jd, ldx, ldy, yoff);
@@ -562,7 +715,7 @@ int stage_timeout_take(cudaStream_t s) {
 extern "C" {
 
 int bspai_set_spmv_form(int form) {
-    if (form != BSPAI_SPMV_AUTO && form != BSPAI_SPMV_REGISTERS)
+    if (form != BSPAI_SPMV_AUTO && form != BSPAI_SPMV_REGISTERS && form != BSPAI_SPMV_STAGED)
         return set_error(BSPAI_ERR_INVALID, "bspai_set_spmv_form: unknown form %d", form);
     g_spmv_form.store(form);
     return BSPAI_OK;

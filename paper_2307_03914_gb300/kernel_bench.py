@@ -7,12 +7,21 @@ Builds A, M = SPAI(A) and the bucketed M (buckets fp64/fp32/fp16/e4m3 at
 bucket_eps = 2^-10, the GMRES setting of the benchmark) on the GPU, then times
 with CUDA events, the L2 flushed (a 256 MiB write) before every repetition:
 the bucketed product M w (fp32 in and out, as inside GMRES) and A v in u_p =
-fp32, each in both kernel forms (shared-memory staged and register), and the
-double-double residual.  Prints one JSON line per form with the median time
-and the algorithmic bytes (indices int32, x read once, y written once).
+fp32, each in the three kernel forms (compile-time formats, shared-memory
+staged, generic register), and the double-double residual.  Prints one JSON
+line per form with the median time and the algorithmic bytes (indices int32,
+x read once, y written once).
 --once runs every kernel exactly once per form with no warm-up and no
-flush: a short, fixed launch sequence for a profiler (kernel order: staged
-M w, staged A v, register M w, register A v, residual).
+flush: a short, fixed launch sequence for a profiler (kernel order: fixed-
+format M w and A v, staged M w and A v, register M w and A v, residual).
+--mixes times M w (fp32 in and out, default kernel form) for several bucket
+lists of the same M (one fp32 bucket, one fp16 bucket, fp32 + fp16, fp16 +
+e4m3) to separate the cost of the formats from the cost of the mix.
+--mgs times GMRES runs of K = 2, 8, 16, 32, 64 steps (tau = 0) on the same
+system and fits the MGS kernel-class time to a K + b P(K), P(K) = sum over the
+steps j < K of the j + 2 grid reductions of step j: a is the cost per Arnoldi
+step outside the reductions (launch, prologue, epilogue), b the cost of one
+reduction pass.
 """
 from __future__ import annotations
 
@@ -34,6 +43,8 @@ def main():
     p.add_argument("--reps", type=int, default=20)
     p.add_argument("--bucket-eps", type=float, default=2.0 ** -10)
     p.add_argument("--once", action="store_true")
+    p.add_argument("--mgs", action="store_true")
+    p.add_argument("--mixes", action="store_true")
     a = p.parse_args()
     wl = W.workload("convdiff3d", grid=a.grid)
     A = B.DeviceCSR.from_host(wl["A"])
@@ -54,8 +65,52 @@ def main():
     m_bytes += 4 * n + 4 * n + (4 * n if e4m3 else 0)
     a_bytes = nnz * (4 + 4) + 4 * n + 4 * n
     r_bytes = nnz * (8 + 4) + 3 * 8 * n
+    if a.mixes:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+        def tmed(fn):
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(a.reps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts))
+
+        for precs, eps in ((["fp32"], 2.0 ** -24), (["fp16"], 2.0 ** -11), (["fp32", "fp16"], 2.0 ** -16),
+                           (["fp16", "e4m3"], 2.0 ** -10), (["fp64", "fp32", "fp16", "e4m3"], 2.0 ** -10)):
+            BMx, bx = B.bspai_bucket(M, eps, precs)
+            mb = sum(c * (VBYTES[q] + 4) for c, q in zip(bx["nnz_k"], bx["precs"]) if q != "drop") + 8 * n
+            mb += 4 * n if ("e4m3" in bx["precs"] and bx["nnz_k"][bx["precs"].index("e4m3")] > 0) else 0
+            t = tmed(lambda: B.apply(BMx, x, y))
+            print(json.dumps({"precs": precs, "eps": eps, "nnz_k": bx["nnz_k"], "us": t * 1e3, "GBs": mb / t / 1e6,
+                              "bytes": mb}))
+        return
+    if a.mgs:
+        r = torch.from_numpy(wl["b"]).cuda()
+        d = torch.empty(n, device="cuda", dtype=torch.float64)
+        ks = (2, 8, 16, 32, 64)
+        B.gmres(Ah, BM, r, d, "fp32", "fp32", B.opts(tau=0.0, kmax=8))  # warm-up
+        rows = []
+        for k in ks:
+            B.profile_enable(True)
+            B.profile_read(reset=True)
+            B.gmres(Ah, BM, r, d, "fp32", "fp32", B.opts(tau=0.0, kmax=k))
+            prof = B.profile_read(reset=True)
+            B.profile_enable(False)
+            rows.append((k, sum(j + 2 for j in range(k)), prof["mgs"][0], prof["bspmv"][0], prof["spmv_A"][0]))
+        X = np.array([[k, p] for k, p, *_ in rows], dtype=float)
+        coef = np.linalg.lstsq(X, np.array([t for *_, t, _, _ in rows]), rcond=None)[0]
+        print(json.dumps({"mgs": [dict(K=k, passes=p, mgs_ms=t, bspmv_ms=bm, spmvA_ms=am) for k, p, t, bm, am in rows],
+                          "per_step_us": coef[0] * 1e3, "per_pass_us": coef[1] * 1e3, "n": n}))
+        return
     if a.once:
-        for form in (B.SPMV_AUTO, B.SPMV_REGISTERS):
+        for form in (B.SPMV_AUTO, B.SPMV_STAGED, B.SPMV_REGISTERS):
             B.set_spmv_form(form)
             B.apply(BM, x, y)
             B.spmv_up(Ah, x, y)
@@ -80,7 +135,7 @@ def main():
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
 
-    for form, name in ((B.SPMV_AUTO, "staged"), (B.SPMV_REGISTERS, "registers")):
+    for form, name in ((B.SPMV_AUTO, "fixed-format"), (B.SPMV_STAGED, "staged"), (B.SPMV_REGISTERS, "registers")):
         B.set_spmv_form(form)
         tm = timeit(lambda: B.apply(BM, x, y))
         ta = timeit(lambda: B.spmv_up(Ah, x, y))

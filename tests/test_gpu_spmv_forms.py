@@ -1,10 +1,11 @@
-"""The two kernel forms of the sparse products -- the register form and the form
-that stages the matrix stream into shared memory with bulk copies (TMA) -- on
-matrices large enough for the staged form to engage (more than 2 x 8 x 152
-slices of 32 rows): both bit-exact against the oracle's Alg 2.3 product and
-its u_p product, for every bucket mix the staged form takes (1 to 4 stored
-buckets, an fp64 bucket or none, rows wider than the unrolled part, a ragged
-last slice), and GMRES iterates identical between the forms."""
+"""The kernel forms of the sparse products -- compile-time bucket formats
+(default), the generic register form, and the form that stages the matrix
+stream into shared memory with bulk copies (TMA) -- on matrices large enough
+for the staged form to engage (more than 2 x 8 x 152 slices of 32 rows): each
+bit-exact against the oracle's Alg 2.3 product and its u_p product, for every
+bucket mix (1 to 4 stored buckets, an fp64 bucket or none, rows wider than the
+unrolled part, a ragged last slice), and GMRES iterates identical between the
+forms."""
 import numpy as np
 import pytest
 import torch
@@ -14,6 +15,8 @@ from gpu_helpers import dev, gpu_bucket, host, lib, oracle_M
 from paper_2307_03914_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+FORMS = (0, 1, 2)  # SPMV_AUTO, SPMV_REGISTERS, SPMV_STAGED
 
 
 @pytest.fixture(scope="module")
@@ -70,10 +73,9 @@ def test_bucketed_product_forms_bitexact(B, cases, mix):
             yr = O.bspmv(P.row_ptr, P.col, stored, ref["ids"], precs, xin.astype(np.float64))
             if ydt == torch.float32:
                 yr = yr.astype(np.float32).astype(np.float64)
-            y_tma = _apply(B, b["BM"], xin, ydt, B.SPMV_AUTO)
-            y_reg = _apply(B, b["BM"], xin, ydt, B.SPMV_REGISTERS)
-            assert np.array_equal(y_tma, yr), (wl["name"], precs, eps, ydt)
-            assert np.array_equal(y_reg, yr), (wl["name"], precs, eps, ydt)
+            for form in FORMS:
+                yg = _apply(B, b["BM"], xin, ydt, form)
+                assert np.array_equal(yg, yr), (wl["name"], precs, eps, ydt, form)
 
 
 def test_up_product_and_x0_forms_bitexact(B, cases):
@@ -83,7 +85,7 @@ def test_up_product_and_x0_forms_bitexact(B, cases):
         v = np.random.default_rng(12).uniform(-1, 1, A.n).astype(np.float32)
         ref = O.spmv_prec(A.row_ptr, A.col, A.val, "fp32", v.astype(np.float64))
         x0r = O.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"])
-        for form in (B.SPMV_AUTO, B.SPMV_REGISTERS):
+        for form in FORMS:
             B.set_spmv_form(form)
             w = torch.empty(A.n, dtype=torch.float32, device="cuda")
             B.spmv_up(Ah, dev(v), w)
@@ -100,11 +102,12 @@ def test_gmres_iterates_identical_between_forms(B, cases):
     Ah = B.matrix_create(B.DeviceCSR.from_host(A))
     r = dev(O.residual_dd(A, O.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"]), wl["b"]))
     out = []
-    for form in (B.SPMV_AUTO, B.SPMV_REGISTERS):
+    for form in FORMS:
         B.set_spmv_form(form)
         d = torch.empty(A.n, dtype=torch.float64, device="cuda")
         info = B.gmres(Ah, b["BM"], r, d, "fp32", "fp32", B.opts(tau=1e-4))
         out.append((host(d), info["gmres_iters"]))
     B.set_spmv_form(B.SPMV_AUTO)
-    assert out[0][1] == out[1][1]
-    assert np.array_equal(out[0][0], out[1][0])
+    for d, its in out[1:]:
+        assert its == out[0][1]
+        assert np.array_equal(d, out[0][0])
