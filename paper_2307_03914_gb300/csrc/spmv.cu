@@ -412,7 +412,8 @@ struct FixRow {
                 xv[l] = xin(x, c[l]);
             }
     }
-    __device__ __forceinline__ double sum(const BucketDev& B, const XT* __restrict__ x, float sc, int64_t r) const {
+    // the partial sum y_i^(k): fp64 for an fp64 bucket, fp32 otherwise
+    __device__ __forceinline__ V sum(const BucketDev& B, const XT* __restrict__ x, float sc, int64_t r) const {
         if constexpr (P == BSPAI_FP64) {
             double acc = 0.0;
 #pragma unroll
@@ -432,14 +433,21 @@ struct FixRow {
                 const int cc = __ldg(B.col + base + 32 * l);
                 if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(dec(B, base + 32 * l, sc, cc, r), xin(x, cc)));
             }
-            return (double)acc;
+            return acc;
         }
     }
 };
 
-// P1 < 0: one bucket
+// P1 < 0: one bucket.  The register cap (min blocks per SM) buys occupancy:
+// with a handful of loads in flight per thread, more resident warps is what
+// keeps more bytes in flight.
+template <int P0, int W0, int P1>
+struct FixMinBlocks {
+    static constexpr int value = P1 < 0 ? (W0 > 4 ? 4 : (P0 == BSPAI_FP64 ? 6 : 8)) : (W0 > 4 ? 4 : 6);
+};
+
 template <typename XT, typename YT, int P0, int W0, int P1, int W1>
-__global__ void __launch_bounds__(256) k_bspmv_fix(const __grid_constant__ BMDev M, const XT* __restrict__ x,
+__global__ void __launch_bounds__(256, FixMinBlocks<P0, W0, P1>::value) k_bspmv_fix(const __grid_constant__ BMDev M, const XT* __restrict__ x,
                                                    YT* __restrict__ y, const int* __restrict__ jd, int64_t ldx,
                                                    int64_t ldy, int yoff) {
     if (jd) {
@@ -465,9 +473,20 @@ __global__ void __launch_bounds__(256) k_bspmv_fix(const __grid_constant__ BMDev
     if constexpr (P1 >= 0) b.cols(M.b[1]);
     a.vals(M.b[0], x, sc0, r);
     if constexpr (P1 >= 0) b.vals(M.b[1], x, sc1, r);
-    double yi = __dadd_rn(0.0, a.sum(M.b[0], x, sc0, r));
-    if constexpr (P1 >= 0) yi = __dadd_rn(yi, b.sum(M.b[1], x, sc1, r));
-    if (r < M.n) y[r] = from_f64<YT>(yi);
+    constexpr bool narrow = P0 != BSPAI_FP64 && P1 != BSPAI_FP64;
+    if constexpr (narrow && std::is_same<YT, float>::value) {
+        // fp32 partials, fp32 result: fl32(fl64(0 + a)) = a, and for two
+        // partials fl32(fl64(a + b)) = fl32(a + b) (double rounding through
+        // 53 >= 2 * 24 + 2 bits is innocuous), so the fp64 sum of Alg 2.3 in
+        // bucket order gives these bits without fp64 arithmetic
+        float yf = a.sum(M.b[0], x, sc0, r);
+        if constexpr (P1 >= 0) yf = __fadd_rn(yf, b.sum(M.b[1], x, sc1, r));
+        if (r < M.n) y[r] = yf;
+    } else {
+        double yi = __dadd_rn(0.0, (double)a.sum(M.b[0], x, sc0, r));
+        if constexpr (P1 >= 0) yi = __dadd_rn(yi, (double)b.sum(M.b[1], x, sc1, r));
+        if (r < M.n) y[r] = from_f64<YT>(yi);
+    }
 }
 
 template <typename XT, typename YT>
@@ -522,15 +541,6 @@ BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     return d;
 }
 
-// Buckets that contribute nothing (dropped, or with no entries) are left out:
-// their partial sums are +0 and adding +0 to a sum that is never -0 changes nothing.
-static BMDev compact_buckets(const BMDev& M) {
-    BMDev c = M;
-    c.q = 0;
-    for (int k = 0; k < M.q; ++k)
-        if (M.b[k].prec != BSPAI_DROP && M.b[k].nnz != 0) c.b[c.q++] = M.b[k];
-    return c;
-}
 
 template <typename XT, typename YT>
 using TmaFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int, StageLayout);

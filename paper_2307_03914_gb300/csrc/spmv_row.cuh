@@ -144,4 +144,14 @@ __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const 
     return yi;
 }
 
+// Buckets that contribute nothing (dropped, or with no entries) are left out:
+// their partial sums are +0 and adding +0 to a sum that is never -0 changes nothing.
+inline BMDev compact_buckets(const BMDev& M) {
+    BMDev c = M;
+    c.q = 0;
+    for (int k = 0; k < M.q; ++k)
+        if (M.b[k].prec != BSPAI_DROP && M.b[k].nnz != 0) c.b[c.q++] = M.b[k];
+    return c;
+}
+
 }  // namespace bspai
