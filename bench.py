@@ -221,6 +221,21 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ replicas
+def job_rate(ms, ok, world, dist, device):
+    """Whole-job throughput of N independent replicas: the slowest rank's
+    time over the units every rank completed.  Returns (ms, ok, units/s)."""
+    if world > 1:
+        import torch
+
+        t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([float(ok)], device=device, dtype=torch.float64)
+        dist.all_reduce(c)
+        ms, ok = float(t.item()), int(c.item())
+    return ms, ok, ok / (ms / 1000.0)
+
+
 # ------------------------------------------------------------------ extension legs
 def measure_batch(B, W, world, dist, barrier):
     """SPAI build + per-system bucketing + batched GMRES-IR of the whole batch,
@@ -259,14 +274,9 @@ def measure_batch(B, W, world, dist, barrier):
         fe = err[:, ro[s]:ro[s] + m.n].amax(dim=1) / Xt[:, ro[s]:ro[s] + m.n].abs().amax(dim=1)
         ok += int((fe <= FE_TARGET).sum())
         worst = max(worst, float(fe.max()))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([float(ok)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        ms, ok = float(t.item()), int(c.item())
+    ms, ok, rate = job_rate(ms, ok, world, dist, "cuda")
     return {"workload": "512 systems (n log-uniform in [1e3, 6.4e4], 5/9-point convection-diffusion) x 32 RHS",
-            "pairs": info["pairs"] * world, "solves_per_s": ok / (ms / 1000.0), "ms": ms, "ok": ok,
+            "pairs": info["pairs"] * world, "solves_per_s": rate, "ms": ms, "ok": ok,
             "worst_fwd_err": worst, "total_gmres_iters": info["total_iters"], "max_iters": info["max_iters"],
             "ir_launches": info["ir_launches"], "cta_threads": info["block_threads"], "grid": info["grid"],
             "kmax": info["kmax"], "rows": n, "nnz_A": bw["A"].nnz, "storage_pct": kinfo["storage_pct"]}
@@ -375,17 +385,9 @@ def main():
     prof = B.profile_read(reset=True)
     B.profile_enable(False)
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     fe = [float(((x - xt).abs().max() / xt.abs().max()).item()) for x in xs]
     ok = sum(1 for f, (inf, _) in zip(fe, infos) if f <= FE_TARGET and inf["status"] == 0)
-    if world > 1:
-        t = torch.tensor([ok], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        ok = int(t.item())
-    value = ok / (ms / 1000.0)
+    ms, ok, value = job_rate(ms, ok, world, dist, "cuda")
     info, binfo = infos[-1]
 
     # ---------------- roofline of the kernels (algorithmic bytes / event time)
@@ -478,13 +480,8 @@ def main():
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems, e_ok], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
-            tt = torch.tensor([float(e_ok)], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt)
-            ems, e_ok = float(t[0].item()), int(tt.item())
-        out["e2e"] = {"value": e_ok / (ems / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        ems, e_ok, erate = job_rate(ems, e_ok, world, dist, "cuda")
+        out["e2e"] = {"value": erate, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
 
     # ---------------- batched solves: 512 systems x 32 right-hand sides (one replica per rank)

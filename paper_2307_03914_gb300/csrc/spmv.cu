@@ -89,7 +89,12 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
             }
         }
     }
+    // an fp32 result of at most two narrow partials needs no fp64 arithmetic:
+    // fl32(fl64(a + b)) = fl32(a + b) (double rounding through 53 >= 2 * 24 + 2
+    // bits is innocuous), and fl64(0 + a) = a
+    constexpr bool F32OUT = std::is_same<YT, float>::value && !F64 && Q <= 2;
     double yi = 0.0;
+    float yf = 0.0f;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const BucketDev& B = M.b[k];
@@ -114,10 +119,14 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
                 const int cc = __ldg(B.col + base[k] + 32 * l);
                 if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(decode_rt(B, base[k] + 32 * l, cc, r), to_f32<XT>(__ldg(x + cc))));
             }
-            yi = __dadd_rn(yi, (double)acc);
+            if constexpr (F32OUT) yf = k == 0 ? acc : __fadd_rn(yf, acc);
+            else yi = __dadd_rn(yi, (double)acc);
         }
     }
-    if (r < M.n) y[r] = from_f64<YT>(yi);
+    if (r < M.n) {
+        if constexpr (F32OUT) y[r] = yf;
+        else y[r] = from_f64<YT>(yi);
+    }
 }
 
 // ---------------------------------------------------------------- TMA-staged form
@@ -306,7 +315,9 @@ __global__ void __launch_bounds__(256) k_bspmv_tma(const __grid_constant__ BMDev
                 }
             }
         }
+        constexpr bool F32OUT = std::is_same<YT, float>::value && !F64 && Q <= 2;  // as in k_bspmv_q
         double yi = 0.0;
+        float yf = 0.0f;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const BucketDev& B = M.b[k];
@@ -336,12 +347,16 @@ __global__ void __launch_bounds__(256) k_bspmv_tma(const __grid_constant__ BMDev
                         acc = __fadd_rn(acc, __fmul_rn(decode_sm(B, vs, 32 * l + lane, cc, r, sc),
                                                        to_f32<XT>(__ldg(x + cc))));
                 }
-                yi = __dadd_rn(yi, (double)acc);
+                if constexpr (F32OUT) yf = k == 0 ? acc : __fadd_rn(yf, acc);
+            else yi = __dadd_rn(yi, (double)acc);
             }
         }
         __syncwarp();  // every lane is done with this stage
         if (i + NS < cnt) post(i + NS, st);
-        if (r < M.n) y[r] = from_f64<YT>(yi);
+        if (r < M.n) {
+            if constexpr (F32OUT) y[r] = yf;
+            else y[r] = from_f64<YT>(yi);
+        }
     }
 }
 
