@@ -501,7 +501,10 @@ def main():
         cb = oracle_sample(wl, args.bucket_eps, its, spai_cols=None if n <= 300000 else n // 4)
         out["cpu_baseline"] = {"value": 1.0 / cb["seconds_per_solve"], "unit": UNIT, "cores": cb["cores"],
                                "kind": "oracle", "sample": cb["sample"] + f" (iteration counts from: {src})",
-                               "measured_cpu_s": cb["measured_s"]}
+                               "measured_cpu_s": cb["measured_s"],
+                               "model_s": {"spai": cb["phases"]["spai"], "bucket": cb["phases"]["bucket"],
+                                           "x0": cb["phases"]["x0"], "residual": cb["phases"]["residual"],
+                                           "gmres_c0_c1_c2": cb["fit"]}}
 
     if world > 1:
         dist.barrier()

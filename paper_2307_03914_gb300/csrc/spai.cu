@@ -66,6 +66,8 @@ __host__ __device__ __forceinline__ size_t spai_warp_bytes(int jmax, int lmax, i
            ~(size_t)15;
 }
 
+constexpr int kRegJ = 8;  // |J| up to which the register-resident QR path applies
+
 __device__ __forceinline__ int lower_bound_i32(const int* a, int n, int v) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
     for (int size = 2; size <= LP; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int t = lane; t < (LP >> 1); t += 32) {
-                const int i = (t / stride) * 2 * stride + (t % stride);
+                const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));  // stride is a power of two
                 const int jj = i + stride;
                 const bool asc = (i & size) == 0;
                 const int a = cand[i], b = cand[jj];
@@ -180,7 +182,89 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
 
     bool rankdef = (nJ > 0 && nI < nJ);
     float res_norm = 1.0f;
-    if (nJ > 0 && !rankdef) {
+    if (nJ > 0 && !rankdef && nI <= 32 && nJ <= kRegJ) {
+        // Small block (|I| <= 32, |J| <= 8): lane p holds row p of Abar, of
+        // Q^T ebar and of the original Abar in registers, so the Householder
+        // steps need no shared-memory traffic: the same algorithm as below.
+        for (int t = lane; t < nJ * nI; t += 32) Ab[t] = 0.0f;
+        __syncwarp();
+        const int pk = lower_bound_i32(I, nI, (int)k);
+        const bool k_in = pk < nI && I[pk] == (int)k;
+        for (int t = lane; t < L; t += 32) Ab[eq[t] * nI + lower_bound_i32(I, nI, ecol[t])] = eval[t];
+        __syncwarp();
+        const bool mine = lane < nI;
+        float a[kRegJ], a0[kRegJ];
+#pragma unroll
+        for (int q = 0; q < kRegJ; ++q) {
+            a[q] = (mine && q < nJ) ? Ab[q * nI + lane] : 0.0f;
+            a0[q] = a[q];
+        }
+        float cvp = (k_in && lane == pk) ? 1.0f : 0.0f;
+        float fro = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kRegJ; ++q) fro = __fadd_rn(fro, __fmul_rn(a[q], a[q]));
+        fro = __fsqrt_rn(warp_sum(fro));
+        float rd[kRegJ];
+#pragma unroll
+        for (int c = 0; c < kRegJ; ++c) {
+            rd[c] = 1.0f;
+            if (c >= nJ || rankdef) continue;
+            const bool act = mine && lane >= c;
+            const float xc = act ? a[c] : 0.0f;
+            const float sig = __fsqrt_rn(warp_sum(__fmul_rn(xc, xc)));
+            const float x0 = __shfl_sync(0xffffffffu, a[c], c);
+            if (!(sig > 0.0f)) {
+                rankdef = true;
+                continue;
+            }
+            const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
+            const float v0 = __fadd_rn(x0, sgn * sig);
+            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
+            const float twoinv = __fdiv_rn(2.0f, vtv);
+            const float vp = act ? (lane == c ? v0 : a[c]) : 0.0f;  // reflector v, entries c..|I|-1
+#pragma unroll
+            for (int cc = c + 1; cc < kRegJ; ++cc) {
+                if (cc >= nJ) break;
+                const float tau = __fmul_rn(warp_sum(__fmul_rn(vp, a[cc])), twoinv);
+                if (act) a[cc] = __fsub_rn(a[cc], __fmul_rn(tau, vp));
+            }
+            {
+                const float tau = __fmul_rn(warp_sum(__fmul_rn(vp, cvp)), twoinv);
+                if (act) cvp = __fsub_rn(cvp, __fmul_rn(tau, vp));
+            }
+            rd[c] = -sgn * sig;
+            if (!(fabsf(rd[c]) > (float)nI * u_f * fro)) rankdef = true;
+        }
+        if (!rankdef) {
+            // back substitution R mbar = (Q^T ebar)(1:|J|): lane c holds row c of R
+            float m[kRegJ];
+#pragma unroll
+            for (int q = 0; q < kRegJ; ++q) m[q] = 0.0f;
+#pragma unroll
+            for (int c = kRegJ - 1; c >= 0; --c) {
+                if (c >= nJ) continue;
+                float sum = cvp;
+#pragma unroll
+                for (int cc = c + 1; cc < kRegJ; ++cc)
+                    if (cc < nJ) sum = __fsub_rn(sum, __fmul_rn(a[cc], m[cc]));
+                m[c] = __shfl_sync(0xffffffffu, __fdiv_rn(sum, rd[c]), c);
+            }
+            // sbar = Abar mbar - ebar from the original rows
+            float sp = (k_in && lane == pk) ? -1.0f : 0.0f;
+#pragma unroll
+            for (int q = 0; q < kRegJ; ++q)
+                if (q < nJ) sp = __fadd_rn(sp, __fmul_rn(a0[q], m[q]));
+            res_norm = __fsqrt_rn(warp_sum(mine ? __fmul_rn(sp, sp) : 0.0f));
+            if (lane < nJ) {
+                float mq = 0.0f;
+#pragma unroll
+                for (int q = 0; q < kRegJ; ++q)
+                    if (q == lane) mq = m[q];
+                mv[lane] = mq;
+            }
+            __syncwarp();
+        }
+    } else if (nJ > 0 && !rankdef) {
         // Abar (column-major, leading dimension nI) and ebar
         for (int t = lane; t < nJ * nI; t += 32) Ab[t] = 0.0f;
         for (int t = lane; t < nI; t += 32) cv[t] = 0.0f;

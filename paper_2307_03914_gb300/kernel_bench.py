@@ -17,6 +17,9 @@ format M w and A v, staged M w and A v, register M w and A v, residual).
 --mixes times M w (fp32 in and out, default kernel form) for several bucket
 lists of the same M (one fp32 bucket, one fp16 bucket, fp32 + fp16, fp16 +
 e4m3) to separate the cost of the formats from the cost of the mix.
+--batch NSYS NRHS runs the batched solver once on a batch of NSYS systems
+with NRHS right-hand sides (the 512 x 32 workload's size distribution), and
+prints its statistics and time (a short launch sequence for a profiler).
 --mgs times GMRES runs of K = 2, 8, 16, 32, 64 steps (tau = 0) on the same
 system and fits the MGS kernel-class time to a K + b P(K), P(K) = sum over the
 steps j < K of the j + 2 grid reductions of step j: a is the cost per Arnoldi
@@ -45,7 +48,10 @@ def main():
     p.add_argument("--once", action="store_true")
     p.add_argument("--mgs", action="store_true")
     p.add_argument("--mixes", action="store_true")
+    p.add_argument("--batch", type=int, nargs=2, default=None, metavar=("NSYS", "NRHS"))
     a = p.parse_args()
+    if a.batch:
+        return batch(a.batch[0], a.batch[1])
     wl = W.workload("convdiff3d", grid=a.grid)
     A = B.DeviceCSR.from_host(wl["A"])
     P = B.DeviceCSR.from_host(wl["pattern"], with_values=False)
@@ -145,6 +151,25 @@ def main():
     B.set_spmv_form(B.SPMV_AUTO)
     tr = timeit(lambda: B.residual(Ah, xd, bd, rd))
     print(json.dumps({"kernel": "residual_dd", "n": n, "us": tr * 1e3, "GBs": r_bytes / tr / 1e6, "bytes": r_bytes}))
+
+
+def batch(nsys, nrhs):
+    bw = W.batch_workload(nsys=nsys, nrhs=nrhs)
+    A = B.DeviceCSR.from_host(bw["A"])
+    P = B.DeviceCSR.from_host(bw["pattern"], with_values=False)
+    row_off = torch.from_numpy(bw["row_off"]).cuda()
+    Bd = torch.from_numpy(bw["B"].reshape(-1)).cuda()
+    X = torch.zeros_like(Bd)
+    Ah = B.matrix_create(A)
+    M, _ = B.bspai_build(A, P, bw["spai_eps"])
+    BM, kinfo = B.bspai_bucket_batched(M, row_off, bw["bucket_eps"], bw["precs"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    info = B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, tol=bw["tau"])
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"batch": [nsys, nrhs], "rows": bw["A"].n, "ms": e0.elapsed_time(e1), **info}))
 
 
 if __name__ == "__main__":

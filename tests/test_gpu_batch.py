@@ -95,8 +95,9 @@ def test_batched_solve_matches_oracle_per_pair(B):
             xg = X[r, ro[s]:ro[s] + m.n]
             assert np.abs(xg - ref["x"]).max() <= 1e-12 * np.abs(ref["x"]).max(), (s, r)
             assert np.abs(xg - xt).max() / np.abs(xt).max() <= 1e-10
-            # same number of refinement steps ran GMRES, counts within a few steps
-            assert abs(g["iters"][r * len(bw["mats"]) + s] - sum(ref["its"])) <= max(3, 0.1 * sum(ref["its"]))
+            # GMRES steps summed over the refinement steps within a few steps (the late
+            # steps' counts move with the u_g summation order, see test_gpu_parity)
+            assert abs(g["iters"][r * len(bw["mats"]) + s] - sum(ref["its"])) <= max(4, 0.15 * sum(ref["its"]))
         # padding rows stay zero
         assert np.all(X[:, ro[s] + m.n:ro[s + 1]] == 0)
 
