@@ -49,7 +49,8 @@ typedef enum {
 } bspai_status_t;
 
 /* Number formats: Table 2 (half, single, double) plus bf16, OCP e4m3, "drop"
- * (u = 1, the element is removed, Section 4) and double-double for u_r. */
+ * (u = 1, the element is removed, Section 4) and BSPAI_DD for u_r: a residual
+ * as accurate as one carried in twice fp64 (compensated dot product Dot2). */
 typedef enum {
     BSPAI_FP64 = 0,
     BSPAI_FP32 = 1,
@@ -158,7 +159,8 @@ int bspai_profile_read(bspai_profile_t* out, int reset);
  * A's buffers may be freed after the call's stream work completes. */
 int bspai_matrix_create(const bspai_csr_t* A, bspai_stream_t s, bspai_A_h* out);
 
-/* r = b - A x computed in double-double (u_r; the paper uses quad), stored in
+/* r = b - A x computed with u_r ~ u^2 (Dot2: TwoProduct by FMA, TwoSum; the
+ * paper uses quad), stored in
  * fp64 (Alg 3.1, residual line).  x, b, r: device fp64 vectors of length n. */
 int bspai_residual(bspai_A_h A, const double* x, const double* b, double* r, bspai_stream_t s);
 
@@ -337,7 +339,7 @@ typedef struct {
  * and one bspai_bucket_batched call serve the whole batch.  B and X (device
  * fp64) hold nrhs vectors of length n one after another; X is in/out.  Every
  * (system, right-hand side) pair runs its own refinement: per pair x0 = M b
- * (u_f), residuals in double-double, nbe / ||d|| / stagnation tests as in
+ * (u_f), residuals with u_r ~ u^2 (Dot2), nbe / ||d|| / stagnation tests as in
  * gmres_ir_solve, and its own left-preconditioned MGS-GMRES (vectors in u_g,
  * A v in u_p, bucketed M v, Givens in fp64).  Each refinement step of the
  * batch is one persistent launch in which a CTA takes pairs, largest systems

@@ -147,7 +147,8 @@ def round_to(x, fmt) -> np.ndarray:
 
 # -------------------------------------------------------------- residual (O2)
 def residual_dd(A, x, b) -> np.ndarray:
-    """r = b - A x in double-double, rounded to fp64.  Pinned by exact rational
+    """r = b - A x by the compensated dot product Dot2 (as accurate as a sum in
+    twice fp64), rounded to fp64.  Pinned by exact rational
     arithmetic (fractions) in tests."""
     r = np.empty(A.n)
     lib().orc_residual_dd(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(x), _f64(b), r)

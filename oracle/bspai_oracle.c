@@ -10,8 +10,9 @@
  *   formats      Table 2 precisions; RN-even rounding written from the
  *                definition (round x / 2^(e-t+1) to an integer), as in the
  *                chop approach the paper uses for half precision (Section 4).
- *   residual     Alg 3.1 residual line in u_r = double-double (Knuth TwoSum,
- *                Dekker/FMA TwoProduct, accurate double-double addition).
+ *   residual     Alg 3.1 residual line with u_r ~ u^2: compensated dot
+ *                product Dot2 (Knuth TwoSum, FMA TwoProduct; Ogita, Rump,
+ *                Oishi 2005).
  *   SPAI         eq. (fronormmin), eq. (redprob), Alg 2.1 with alpha = 0;
  *                Householder QR (Golub & Van Loan Alg 5.2.1 sign choice);
  *                column scaling of Section 4.
@@ -101,18 +102,12 @@ int orc_get_threads(void) {
 /* emulated arithmetic in format f: one fp64 op, one rounding */
 static inline double rf(double x, int f) { return f == ORC_FP64 ? x : orc_round(x, f); }
 
-/* ------------------------------------------------------------ double-double */
+/* ------------------------------------------------ error-free transformations */
 
 static inline void two_sum(double a, double b, double* s, double* e) {
     double S = a + b;
     double bv = S - a;
     *e = (a - (S - bv)) + (b - bv);
-    *s = S;
-}
-
-static inline void quick_two_sum(double a, double b, double* s, double* e) {
-    double S = a + b;
-    *e = b - (S - a);
     *s = S;
 }
 
@@ -122,28 +117,25 @@ static inline void two_prod(double a, double b, double* p, double* e) {
     *p = P;
 }
 
-/* (ah, al) + (bh, bl), accurate double-double addition */
-static inline void dd_add(double* ah, double* al, double bh, double bl) {
-    double s1, s2, t1, t2;
-    two_sum(*ah, bh, &s1, &s2);
-    two_sum(*al, bl, &t1, &t2);
-    s2 += t1;
-    quick_two_sum(s1, s2, &s1, &s2);
-    s2 += t2;
-    quick_two_sum(s1, s2, ah, al);
-}
-
+/* r_i = b_i - sum_j a_ij x_j by Dot2 (Ogita, Rump and Oishi, "Accurate sum and
+ * dot product", 2005): every product split exactly (TwoProduct by FMA), the
+ * running sum p updated by TwoSum, the running error s collecting the TwoSum
+ * errors and the products' errors, r_i = fl(p + s); ascending column order.
+ * The result is as accurate as a sum in twice the working precision:
+ * |r_i - exact| <= u |exact| + gamma_n^2 sum |terms|, so u_r ~ u^2 (Alg 3.1
+ * residual line, with quad read as "at least twice fp64"). */
 void orc_residual_dd(int n, const int* rp, const int* ci, const double* av,
                      const double* x, const double* b, double* r) {
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
-        double hi = b[i], lo = 0.0;
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            double ph, pl;
-            two_prod(av[p], x[ci[p]], &ph, &pl);
-            dd_add(&hi, &lo, -ph, -pl);
+        double p = b[i], s = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            double ph, pl, q;
+            two_prod(av[k], x[ci[k]], &ph, &pl);
+            two_sum(p, -ph, &p, &q);
+            s = s + (q - pl);
         }
-        r[i] = hi + lo;
+        r[i] = p + s;
     }
 }
 

@@ -34,7 +34,7 @@ void   orc_round_array(const double* x, double* y, int64_t n, int fmt);
 void orc_set_threads(int nthreads);
 int  orc_get_threads(void);
 
-/* Residual in double-double (u_r), Alg 3.1 line "compute r_i = b - A x_i". */
+/* Residual with u_r ~ u^2 (compensated Dot2), Alg 3.1 line "compute r_i = b - A x_i". */
 void orc_residual_dd(int n, const int* rp, const int* ci, const double* av,
                      const double* x, const double* b, double* r);
 
@@ -113,7 +113,7 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
 
 /* BSPAI-GMRES-IR driver (Alg 3.1 after the SPAI build).
  *   x0 = M b with the unbucketed M (values muf, fp32 arithmetic) unless x0_given;
- *   loop i < imax: r = b - A x in double-double; nbe = ||r||_inf /
+ *   loop i < imax: r = b - A x with u_r ~ u^2 (Dot2); nbe = ||r||_inf /
  *   (||A||_inf ||x||_inf + ||b||_inf); stop if nbe <= u_work; d = GMRES; x += d
  *   in fp64; stop if ||d||_inf <= u_work ||x||_inf, or if ||d_i|| > 0.9 ||d_{i-1}||.
  * its[i] = GMRES iterations of step i; nbe[i], dx[i] histories; returns the

@@ -1,5 +1,5 @@
 // matrix.cu -- A on the GPU: CSR -> SELL-32 conversion, ||A||_inf, and the
-// residual r = b - A x in double-double (u_r; Alg 3.1 residual line).
+// residual r = b - A x with u_r ~ u^2 (Dot2; Alg 3.1 residual line).
 #include <cstdint>
 
 #include "common.cuh"
@@ -119,31 +119,26 @@ int launch_row_abs_sum_max(const Sell& S, const double* val, double* out, cudaSt
     return BSPAI_OK;
 }
 
-// ------------------------------------------------------------ double-double
-// Knuth TwoSum, the "fast" variant for |a| >= |b|, and the FMA TwoProduct.
+// ------------------------------------------------ error-free transformations
+// Knuth TwoSum.
 __device__ __forceinline__ void dd_two_sum(double a, double b, double& s, double& e) {
     s = __dadd_rn(a, b);
     double bv = __dsub_rn(s, a);
     e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bv)), __dsub_rn(b, bv));
 }
-__device__ __forceinline__ void dd_fast_two_sum(double a, double b, double& s, double& e) {
-    s = __dadd_rn(a, b);
-    e = __dsub_rn(b, __dsub_rn(s, a));
-}
-// (hi, lo) += (bh, bl) with the accurate double-double addition
-__device__ __forceinline__ void dd_accumulate(double& hi, double& lo, double bh, double bl) {
-    double s1, s2, t1, t2;
-    dd_two_sum(hi, bh, s1, s2);
-    dd_two_sum(lo, bl, t1, t2);
-    s2 = __dadd_rn(s2, t1);
-    dd_fast_two_sum(s1, s2, s1, s2);
-    s2 = __dadd_rn(s2, t2);
-    dd_fast_two_sum(s1, s2, hi, lo);
+// One term of the compensated dot product Dot2 (Ogita, Rump and Oishi, 2005):
+// the running sum p absorbs -ph by TwoSum, the running error s collects the
+// TwoSum error and the product's own error -pl; the result p + s is as
+// accurate as a sum carried in twice the working precision (u_r ~ u^2).
+__device__ __forceinline__ void dot2_sub(double& p, double& s, double ph, double pl) {
+    double q;
+    dd_two_sum(p, -ph, p, q);
+    s = __dadd_rn(s, __dsub_rn(q, pl));
 }
 
-// r = b - A x, each product split exactly by an FMA, accumulated in
-// double-double in ascending column order (DD = true; DD = false is the plain
-// fp64 recurrence); also max|r| and max|x| over rows.
+// r = b - A x, each product split exactly by an FMA and the terms summed by
+// Dot2 in ascending column order (DD = true: u_r ~ u^2; DD = false is the
+// plain fp64 recurrence); also max|r| and max|x| over rows.
 template <bool DD>
 __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __restrict__ sptr,
                                                      const int32_t* __restrict__ col,
@@ -165,7 +160,7 @@ __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __res
             const double ph = __dmul_rn(a, xv);
             if (DD) {
                 const double pl = __fma_rn(a, xv, -ph);
-                dd_accumulate(hi, lo, -ph, -pl);
+                dot2_sub(hi, lo, ph, pl);
             } else {
                 hi = __dsub_rn(hi, ph);
             }
@@ -213,7 +208,7 @@ __global__ void __launch_bounds__(256) k_residual_batch(int n, int nrhs, const i
         const double xv = __ldg(x + c);
         const double ph = __dmul_rn(a, xv);
         const double pl = __fma_rn(a, xv, -ph);
-        dd_accumulate(hi, lo, -ph, -pl);
+        dot2_sub(hi, lo, ph, pl);
     }
     const double ri = __dadd_rn(hi, lo);
     R[t] = ri;

@@ -8,7 +8,7 @@ bucket_eps = 2^-10, the GMRES setting of the benchmark) on the GPU, then times
 with CUDA events, the L2 flushed (a 256 MiB write) before every repetition:
 the bucketed product M w (fp32 in and out, as inside GMRES) and A v in u_p =
 fp32, each in the three kernel forms (compile-time formats, shared-memory
-staged, generic register), and the double-double residual.  Prints one JSON
+staged, generic register), and the Dot2 residual.  Prints one JSON
 line per form with the median time and the algorithmic bytes (indices int32,
 x read once, y written once).
 --once runs every kernel exactly once per form with no warm-up and no

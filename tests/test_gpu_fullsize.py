@@ -3,7 +3,7 @@ benchmark times: the 3D 7-point anisotropic convection-diffusion problem on a
 128^3 grid (n = 2,097,152; FP8 bucket) and the random sparse problem with
 n = 65,536 and pattern(|A|^2) top-24.  The oracle checks sampled SPAI columns
 one by one, the full bucket ids and bucketed products (O(nnz) in C), the full
-double-double residual, and the solve by properties that hold at any size."""
+Dot2 residual, and the solve by properties that hold at any size."""
 import numpy as np
 import pytest
 import torch
@@ -59,7 +59,7 @@ def test_full_size(B, name, eps):
     B.apply(bko["BM"], dev(xin), y, stream=g_stream)
     yr = O.bspmv(P.row_ptr, P.col, stored, ref["ids"], wl["precs"], xin.astype(np.float64))
     assert np.array_equal(host(y).astype(np.float64), yr.astype(np.float32).astype(np.float64))
-    # residual of a perturbed solution: bit-exact double-double
+    # residual of a perturbed solution: bit-exact Dot2
     Ah = B.matrix_create(g["A"])
     xp = wl["x_true"] * (1 + 1e-9)
     r = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -73,7 +73,7 @@ def test_full_size(B, name, eps):
     xg = host(x)
     fe = np.abs(xg - wl["x_true"]).max() / np.abs(wl["x_true"]).max()
     assert fe <= 1e-10, (fe, info)
-    # nbe of the GPU solution from the library's double-double residual (bit-exact above)
+    # nbe of the GPU solution from the library's Dot2 residual (bit-exact above)
     B.residual(Ah, x, dev(wl["b"]), r)
     rr = host(r)
     anorm = np.abs(A.to_scipy()).sum(axis=1).max()

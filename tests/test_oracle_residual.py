@@ -1,4 +1,5 @@
-"""Pins for the oracle's double-double residual r = b - A x (u_r, Alg 3.1)
+"""Pins for the oracle's residual r = b - A x with u_r ~ u^2 (compensated dot
+product Dot2; Alg 3.1 residual line)
 against exact rational arithmetic."""
 from fractions import Fraction
 
@@ -28,17 +29,19 @@ def test_residual_dd_vs_exact_rational(orc):
         r = orc.residual_dd(A, x, b)
         rex = _exact_residual(A, x, b)
         absax = abs(A.to_scipy()) @ np.abs(x) + np.abs(b)
+        u = Fraction(1, 2 ** 53)
         for i in range(A.n):
-            ref = float(rex[i])  # correctly rounded fp64 of the exact value
             err = abs(Fraction(r[i]) - rex[i])
-            # final rounding (half an ulp) plus the double-double error of ~nnz terms
-            ulp = np.spacing(abs(ref)) if ref != 0 else 0.0
-            bound = Fraction(ulp) / 2 + Fraction(16 * 2.0 ** -104) * Fraction(absax[i])
+            # the Dot2 error bound (Ogita, Rump, Oishi 2005) for the n terms
+            # b_i, -a_i1 x_1, ...: |res - r| <= u |r| + gamma_n^2 sum |terms|
+            nt = int(A.row_ptr[i + 1] - A.row_ptr[i]) + 1
+            gam = nt * u / (1 - nt * u)
+            bound = u * abs(rex[i]) + gam * gam * Fraction(absax[i])
             assert err <= bound, (trial, i, float(err), float(bound))
 
 
 def test_residual_dd_beats_fp64_on_cancellation(orc):
-    # one row where fp64 evaluation loses everything but double-double does not
+    # one row where fp64 evaluation loses everything but Dot2 does not
     A = W.CSR(1, np.array([0, 3], np.int32), np.array([0, 1, 2], np.int32),
               np.array([1.0, 1.0, 1.0]))
     x = np.array([1e16, 1.0, -1e16])
