@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 METRIC = "GMRES-IR solves/s at fwd err<=1e-10; bucketed M·v GB/s vs GB300 HBM peak"
 UNIT = "solves/s"
 FE_TARGET = 1e-10
+# DRAM bytes over algorithmic bytes of the MGS kernel (k_mgs_res<float, 28, 512>) from one ncu
+# capture of an Arnoldi step (j = 20, 128^3): dram read + write 188.67 MB against (j+1) n 4 + n 4
+# = 184.55 MB.  Both grow linearly in j, so the per-launch traffic of the timed launches is this
+# ratio times their algorithmic bytes.
+MGS_TRAFFIC_RATIO = 188.67 / 184.55
 
 
 def parse():
@@ -409,8 +414,11 @@ def main():
         if t_ms <= 0:
             return None
         ach = cls_bytes[cls] / (t_ms / 1000.0) / 1e9
+        # DRAM bytes per launch, from the ncu ratio of the MGS kernel (none taken for the others)
+        traffic = MGS_TRAFFIC_RATIO * cls_bytes[cls] / nl if cls == "mgs" and nl else None
         return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": cls, "launches": nl, "ms_total": t_ms,
+                "traffic": traffic, "traffic_unit": "bytes per launch", "kernel": cls, "launches": nl,
+                "ms_total": t_ms,
                 "algorithmic_bytes": cls_bytes[cls], "peak_source": peak_src}
 
     dominant = max(prof, key=lambda c: prof[c][0])

@@ -101,6 +101,9 @@ typedef struct {
     int32_t kmax;          /* max GMRES iterations per refinement step (no restart); 0 = min(n, 1000) */
     int32_t i_max;         /* max refinement steps; 0 = 10 */
     int32_t x0_given;      /* 1: x holds the initial iterate; 0: x0 = M b in u_f (Alg 3.1) */
+    int32_t max_blocks;    /* cap on the blocks (one per SM) of the cooperative GMRES kernels;
+                              0 = every SM.  Several solves on different streams, each capped,
+                              share the GPU concurrently (e.g. one solve per right-hand side). */
     double u_stop;         /* stop when nbe <= u_stop or ||d||_inf <= u_stop ||x||_inf; 0 = 2^-53 */
     double stagnation;     /* stop when ||d_i|| > stagnation ||d_{i-1}||; 0 = 0.9 */
     double barrier_timeout_s; /* device grid-barrier time limit in seconds; 0 = 2.0 */

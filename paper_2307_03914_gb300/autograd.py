@@ -10,6 +10,8 @@ library through the C ABI; this module only sequences the calls.
 """
 from __future__ import annotations
 
+import queue
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import torch
@@ -25,6 +27,44 @@ class SolverSettings:
     u_g: str = "fp32"
     u_p: str = "fp32"
     tol: float = 1e-4
+    # right-hand sides solved at the same time, each on its own CUDA stream with
+    # its cooperative GMRES kernels capped at (SM count / concurrent) blocks
+    concurrent: int = 16
+
+
+def _solve_rhs(Ah, rhs, BM, M, out, settings: SolverSettings, what: str):
+    """out[r] = A^-1 rhs[r] by BSPAI-GMRES-IR for every row r, several at once."""
+    nr = rhs.shape[0]
+    k = max(1, min(nr, settings.concurrent))
+    if k == 1:
+        infos = [B.gmres_ir_solve(Ah, rhs[r], BM, M, out[r], u_g=settings.u_g, u_p=settings.u_p, tol=settings.tol)
+                 for r in range(nr)]
+    else:
+        sms = torch.cuda.get_device_properties(rhs.device).multi_processor_count
+        o = B.opts(tau=settings.tol, max_blocks=max(1, sms // k))
+        main = torch.cuda.current_stream()
+        streams = queue.Queue()
+        for _ in range(k):
+            st = torch.cuda.Stream()
+            st.wait_stream(main)
+            streams.put(st)
+
+        def one(r):
+            st = streams.get()
+            try:
+                return B.gmres_ir_solve(Ah, rhs[r], BM, M, out[r], u_g=settings.u_g, u_p=settings.u_p,
+                                        tol=settings.tol, o=o, stream=st)
+            finally:
+                streams.put(st)
+
+        with ThreadPoolExecutor(k) as ex:
+            infos = list(ex.map(one, range(nr)))
+        while not streams.empty():
+            main.wait_stream(streams.get())
+    for r, info in enumerate(infos):
+        if info["status"] != B.OK:
+            raise B.BspaiError(info["status"], f"{what} solve of right-hand side {r}: {info}")
+    return infos
 
 
 class BspaiSolve(torch.autograd.Function):
@@ -43,12 +83,7 @@ class BspaiSolve(torch.autograd.Function):
         BM, _ = B.bspai_bucket(M, settings.bucket_eps, settings.precs)
         bb = b.detach().reshape(-1, n).contiguous()
         x = torch.empty_like(bb)
-        infos = []
-        for r in range(bb.shape[0]):
-            info = B.gmres_ir_solve(Ah, bb[r], BM, M, x[r], u_g=settings.u_g, u_p=settings.u_p, tol=settings.tol)
-            if info["status"] != B.OK:
-                raise B.BspaiError(info["status"], f"forward solve of right-hand side {r}: {info}")
-            infos.append(info)
+        infos = _solve_rhs(Ah, bb, BM, M, x, settings, "forward")
         ctx.handles = (A, Ah, M, BM, settings)
         ctx.infos = infos
         ctx.b_shape = b.shape
@@ -67,13 +102,8 @@ class BspaiSolve(torch.autograd.Function):
         lam = torch.empty_like(g)
         grad_a = torch.zeros_like(A.val)
         tmp = torch.empty_like(A.val)
-        ctx.adjoint_infos = []
+        ctx.adjoint_infos = _solve_rhs(At, g, BMt, Mt, lam, settings, "adjoint")
         for r in range(g.shape[0]):
-            info = B.gmres_ir_solve(At, g[r], BMt, Mt, lam[r], u_g=settings.u_g, u_p=settings.u_p,
-                                    tol=settings.tol)
-            if info["status"] != B.OK:
-                raise B.BspaiError(info["status"], f"adjoint solve of right-hand side {r}: {info}")
-            ctx.adjoint_infos.append(info)
             B.adjoint_grad_A(A, lam[r], x[r], tmp)
             grad_a += tmp
         return grad_a, lam.reshape(ctx.b_shape), None, None, None, None

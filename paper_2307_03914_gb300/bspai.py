@@ -56,7 +56,8 @@ class BucketInfo(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("tau", C.c_double), ("kmax", C.c_int32), ("i_max", C.c_int32), ("x0_given", C.c_int32),
-                ("u_stop", C.c_double), ("stagnation", C.c_double), ("barrier_timeout_s", C.c_double)]
+                ("max_blocks", C.c_int32), ("u_stop", C.c_double), ("stagnation", C.c_double),
+                ("barrier_timeout_s", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -224,8 +225,9 @@ class BMHandle(_Handle):
     pass
 
 
-def opts(tau=1e-4, kmax=0, i_max=0, x0_given=False, u_stop=0.0, stagnation=0.0, barrier_timeout_s=0.0) -> Opts:
-    return Opts(tau, kmax, i_max, int(x0_given), u_stop, stagnation, barrier_timeout_s)
+def opts(tau=1e-4, kmax=0, i_max=0, x0_given=False, u_stop=0.0, stagnation=0.0, barrier_timeout_s=0.0,
+         max_blocks=0) -> Opts:
+    return Opts(tau, kmax, i_max, int(x0_given), int(max_blocks), u_stop, stagnation, barrier_timeout_s)
 
 
 def profile_enable(on: bool = True):

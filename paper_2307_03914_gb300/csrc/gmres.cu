@@ -559,7 +559,9 @@ struct GmresWork {
     cudaStream_t s = nullptr;
 
     static size_t tag_words() { return (size_t)4 * kTagMaxBlocks; }
-    int alloc(int n_, int kmax_, int ug_, int up_, double timeout_s, cudaStream_t st_) {
+    int sms = 0;  // SMs the cooperative kernels may use (one block of k_mgs_res each)
+    int alloc(int n_, int kmax_, int ug_, int up_, double timeout_s, int max_blocks, cudaStream_t st_) {
+        sms = max_blocks > 0 && max_blocks < num_sms() ? max_blocks : num_sms();
         n = n_;
         kmax = kmax_;
         ug = ug_;
@@ -583,7 +585,7 @@ struct GmresWork {
         }
         if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
         if (occ < 1) return set_error(BSPAI_ERR_CUDA, "gmres: cooperative kernel does not fit on an SM");
-        G = (occ >= 2 ? 2 : 1) * num_sms();
+        G = (occ >= 2 ? 2 : 1) * sms;
         BSPAI_TRY(dalloc(&V, es * (size_t)ldv * (size_t)(kmax + 1), s));
         BSPAI_TRY(dalloc(&w, es * (size_t)ldv, s));
         BSPAI_TRY(dalloc(&part, es * 2 * (size_t)G, s));
@@ -636,7 +638,7 @@ static void* pick_res(int64_t chunk, int* bd) {
 // thread of a 512-thread block.
 static int choose_mgs(GmresWork& W) {
     W.res_fn = nullptr;
-    const int Gr = num_sms();
+    const int Gr = W.sms;
     if (Gr > kTagMaxBlocks) return BSPAI_OK;
     const int64_t chunk = ceil_div(ceil_div(W.n, Gr), 32) * 32;
     const size_t es = W.ug == BSPAI_FP64 ? 8 : 4;
@@ -825,7 +827,7 @@ static int ir_solve(bspai_matrix* A, const double* b, const bspai_bucketed* BM, 
     };
     if ((rc = dalloc_t(&r, (size_t)n, s))) return finish(rc);
     if ((rc = dalloc_t(&nrm, 4, s))) return finish(rc);
-    if ((rc = W.alloc(n, kmax, u_g, u_p, o.barrier_timeout_s, s))) return finish(rc);
+    if ((rc = W.alloc(n, kmax, u_g, u_p, o.barrier_timeout_s, o.max_blocks, s))) return finish(rc);
     // ||A||_inf, ||b||_inf
     double anorm = 0.0, bnorm = 0.0;
     {
@@ -992,7 +994,7 @@ int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, b
         return BSPAI_OK;
     }
     GmresWork W;
-    int rc = W.alloc(A->n, resolve_kmax(&o, A->n), u_g, u_p, o.barrier_timeout_s, s);
+    int rc = W.alloc(A->n, resolve_kmax(&o, A->n), u_g, u_p, o.barrier_timeout_s, o.max_blocks, s);
     GmresResult gr;
     if (!rc)
         rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, o.tau, nullptr, d, gr)
@@ -1084,7 +1086,8 @@ int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_
     if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
     occ = occ < occ2 ? occ : occ2;
     if (occ < 1) return set_error(BSPAI_ERR_CUDA, "bspai_gmres_noalloc: cooperative kernel does not fit on an SM");
-    W.G = (occ >= 2 ? 2 : 1) * num_sms();
+    W.sms = o.max_blocks > 0 && o.max_blocks < num_sms() ? o.max_blocks : num_sms();
+    W.G = (occ >= 2 ? 2 : 1) * W.sms;
     const size_t kx = (size_t)W.kmax;
     size_t off[12];
     size_t sz[11] = {es * (size_t)W.ldv * (kx + 1), es * (size_t)W.ldv, es * 2 * (size_t)W.G, sizeof(GmresState),

@@ -196,6 +196,7 @@ void bspai_opts_default(bspai_opts_t* o) {
     o->kmax = 0;
     o->i_max = 0;
     o->x0_given = 0;
+    o->max_blocks = 0;
     o->u_stop = 0.0;
     o->stagnation = 0.0;
     o->barrier_timeout_s = 0.0;
