@@ -494,6 +494,7 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         const size_t per = sizeof(T) * (size_t)ldv * (kmax + 2) + sizeof(double) * ((size_t)(kmax + 1) * kmax + 4 * (kmax + 2));
         int gmax = (int)(ws_budget / per);
         int gr = sms * occ;
+        if (o.max_blocks > 0 && gr > o.max_blocks) gr = o.max_blocks;
         if (gr > gmax) gr = gmax;
         if (gr > npairs) gr = npairs;
         *grid = gr < 1 ? 1 : gr;
