@@ -224,6 +224,17 @@ int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, doub
                          const int32_t* precs, int32_t q, bspai_stream_t s, bspai_BM_h* out,
                          bspai_bucket_info_t* info);
 
+/* Buckets of A itself (Section 3, eq. nbe2: the adaptive-precision SpMV also
+ * applied to A inside GMRES, with the same precision list and bucket_eps as
+ * M): ||A||_inf from A's fp64 values, t_k = bucket_eps ||A||_inf / u_k, every
+ * entry to its bucket by eq. (nint), stored in the bucket's format with one
+ * rounding from fp64 (fp16 / e4m3 scaled as for M).  A: from
+ * bspai_matrix_create (not a transposed A: BSPAI_ERR_UNSUPPORTED).  The result
+ * is used by gmres_ir_solve_hb / bspai_gmres_b, and by bspai_apply (y = A x)
+ * and bspai_bucket_export like a bucketed M. */
+int bspai_bucket_A(bspai_A_h A, double bucket_eps, const int32_t* precs, int32_t q, bspai_stream_t s,
+                   bspai_BM_h* out, bspai_bucket_info_t* info);
+
 /* Per nonzero of M in CSR order: bucket id (0-based) and the stored value the
  * product uses (scale applied), as fp64.  Device buffers of length nnz(M);
  * either may be NULL. */
@@ -259,6 +270,12 @@ int bspai_apply(bspai_BM_h BM, const void* x, bspai_prec_t x_prec, void* y, bspa
  * r and d are device fp64 vectors.  info->gmres_iters[0], relres[0] are set. */
 int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
                 const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
+
+/* bspai_gmres with A v by the adaptive-precision SpMV on A's buckets
+ * (bspai_bucket_A) instead of A in u_p (eq. nbe2); products accumulated as in
+ * bspai_apply, results rounded to u_g. */
+int bspai_gmres_b(bspai_A_h A, bspai_BM_h A_bucketed, bspai_BM_h BM, const double* r, bspai_prec_t u_g,
+                  const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
 
 /* The same GMRES solve as bspai_gmres, for callers that cannot allocate
  * device memory at the time of the call -- for example a host program that
@@ -365,6 +382,13 @@ int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h M_bucketed, bspai_
                      bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, bspai_prec_t u_p,
                      double tol, const bspai_opts_t* opts, double* x, bspai_stream_t s,
                      bspai_solve_info_t* info);
+
+/* gmres_ir_solve_h with A v inside GMRES by the adaptive-precision SpMV on A's
+ * buckets (bspai_bucket_A; Section 3, eq. nbe2 and fe2).  The residual still
+ * uses A's fp64 values in u_r; x0 = M b in u_f; u_p is replaced by the buckets. */
+int gmres_ir_solve_hb(bspai_A_h A, bspai_BM_h A_bucketed, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,
+                      bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, double tol, const bspai_opts_t* opts,
+                      double* x, bspai_stream_t s, bspai_solve_info_t* info);
 
 #ifdef __cplusplus
 }

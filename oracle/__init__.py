@@ -60,7 +60,8 @@ class _System(C.Structure):
     _fields_ = [("n", C.c_int),
                 ("arp", C.c_void_p), ("aci", C.c_void_p), ("av", C.c_void_p),
                 ("mrp", C.c_void_p), ("mci", C.c_void_p), ("mstored", C.c_void_p),
-                ("mid", C.c_void_p), ("fmts", C.c_void_p), ("q", C.c_int)]
+                ("mid", C.c_void_p), ("fmts", C.c_void_p), ("q", C.c_int),
+                ("astored", C.c_void_p), ("aid", C.c_void_p)]
 
 
 def _declare(L):
@@ -254,16 +255,22 @@ def spmv_prec(row_ptr, col, val, fmt, x) -> np.ndarray:
 
 # ----------------------------------------------------------- GMRES / IR (O7, O8)
 class System:
-    """A together with a bucketed M (structure, stored values, bucket ids)."""
+    """A together with a bucketed M (structure, stored values, bucket ids), and
+    optionally A's own buckets (stored values and ids on A's pattern, same
+    formats) for A v by the bucketed SpMV (eq. nbe2)."""
 
-    def __init__(self, A, M_row_ptr, M_col, M_stored, M_ids, fmts):
+    def __init__(self, A, M_row_ptr, M_col, M_stored, M_ids, fmts, A_stored=None, A_ids=None):
         self._keep = [_i32(A.row_ptr), _i32(A.col), _f64(A.val), _i32(M_row_ptr), _i32(M_col),
                       _f64(M_stored), np.ascontiguousarray(M_ids, np.int8), _fmts(fmts)]
         k = self._keep
+        astored = aid = None
+        if A_stored is not None:
+            self._keep += [_f64(A_stored), np.ascontiguousarray(A_ids, np.int8)]
+            astored, aid = self._keep[8].ctypes.data, self._keep[9].ctypes.data
         self.n = A.n
         self.s = _System(A.n, k[0].ctypes.data, k[1].ctypes.data, k[2].ctypes.data,
                          k[3].ctypes.data, k[4].ctypes.data, k[5].ctypes.data, k[6].ctypes.data,
-                         k[7].ctypes.data, len(k[7]))
+                         k[7].ctypes.data, len(k[7]), astored, aid)
 
 
 def gmres(system: System, r, ug="fp32", up="fp32", tau=1e-4, kmax=500):
@@ -322,8 +329,10 @@ def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
     return dict(lam=lam, dA=dA, db=lam, info=out)
 
 
-def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None) -> dict:
-    """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR."""
+def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False) -> dict:
+    """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR.
+    bucket_A: A v inside GMRES by the bucketed SpMV on A's own buckets (same
+    precisions and bucket_eps, thresholds from ||A||_inf; eq. nbe2)."""
     A, P = wl["A"], wl["pattern"]
     sp = spai(A, P, wl["spai_eps"])
     muf = round_to(sp["mval"], "fp32")  # M is held in u_f = fp32
@@ -331,7 +340,12 @@ def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None) ->
     be = wl["bucket_eps"] if bucket_eps is None else bucket_eps
     bk = bucket_ids(P.row_ptr, muf, be, precs)
     stored, _, _ = bucket_store(P.row_ptr, P.col, muf, bk["ids"], precs)
-    S = System(A, P.row_ptr, P.col, stored, bk["ids"], precs)
+    a_stored = a_ids = None
+    if bucket_A:
+        ak = bucket_ids(A.row_ptr, A.val, be, precs)
+        a_ids = ak["ids"]
+        a_stored, _, _ = bucket_store(A.row_ptr, A.col, A.val, a_ids, precs)
+    S = System(A, P.row_ptr, P.col, stored, bk["ids"], precs, a_stored, a_ids)
     out = gmres_ir(S, muf, wl["b"], wl["u_g"], wl["u_p"], wl["tau"] if tau is None else tau,
                    kmax, imax)
     out.update(spai=sp, muf=muf, buckets=bk, stored=stored)

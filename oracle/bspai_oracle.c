@@ -509,8 +509,12 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
         res = beta;
         for (int j = 0; j < kmax; ++j) {
             double* vj = V + (size_t)j * n;
-            /* w = A v_j in u_p, stored in u_g;  z = M w (bucketed), stored in u_g */
-            orc_spmv_prec(n, S->arp, S->aci, S->av, up, vj, w);
+            /* w = A v_j in u_p (or by the bucketed SpMV on A's buckets, eq. nbe2), stored
+             * in u_g;  z = M w (bucketed), stored in u_g */
+            if (S->astored)
+                orc_bspmv(n, S->arp, S->aci, S->astored, S->aid, S->fmts, S->q, vj, w);
+            else
+                orc_spmv_prec(n, S->arp, S->aci, S->av, up, vj, w);
             for (int i = 0; i < n; ++i) w[i] = rf(w[i], ug);
             orc_bspmv(n, S->mrp, S->mci, S->mstored, S->mid, S->fmts, S->q, w, z);
             for (int i = 0; i < n; ++i) z[i] = rf(z[i], ug);

@@ -106,6 +106,9 @@ typedef struct {
     const int* arp; const int* aci; const double* av;          /* A */
     const int* mrp; const int* mci; const double* mstored;     /* bucketed M */
     const int8_t* mid; const int* fmts; int q;
+    /* bucketed A (Section 3, eq. nbe2): stored values and bucket ids on A's
+     * pattern, same formats as M; astored == NULL: A v in u_p */
+    const double* astored; const int8_t* aid;
 } orc_system_t;
 
 int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau, int kmax,

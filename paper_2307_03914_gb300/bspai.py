@@ -121,6 +121,10 @@ _sig("gmres_ir_solve_batched", _i, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _v
                                     _vp, _vp, C.POINTER(BatchInfo), _vp, _vp])
 _sig("gmres_ir_solve_h", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                               C.POINTER(SolveInfo)])
+_sig("bspai_bucket_A", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINTER(_vp), C.POINTER(BucketInfo)])
+_sig("bspai_gmres_b", _i, [_vp, _vp, _vp, _vp, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
+_sig("gmres_ir_solve_hb", _i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
+                               C.POINTER(SolveInfo)])
 
 
 def last_error() -> str:
@@ -305,6 +309,19 @@ def bspai_bucket(M: MHandle, bucket_eps: float, precs, stream=None):
     return BMHandle(h.value), d
 
 
+def bucket_A(Ah: AHandle, bucket_eps: float, precs, stream=None):
+    """Bucket A's own entries like M's (Section 3, eq. nbe2): row inf-norms of
+    A, thresholds from bucket_eps, stored in the listed formats.  The handle
+    works wherever a bucketed M does (apply, bucket_export) and as the A of
+    gmres_b / gmres_ir_solve_hb."""
+    arr = (C.c_int32 * len(precs))(*[PREC[p] if isinstance(p, str) else int(p) for p in precs])
+    h = C.c_void_p()
+    info = BucketInfo()
+    _check(_lib.bspai_bucket_A(Ah.ptr, float(bucket_eps), arr, len(precs), _stream(stream), C.byref(h),
+                               C.byref(info)))
+    return BMHandle(h.value), _bucket_info(info)
+
+
 def _bucket_info(info: BucketInfo) -> dict:
     q = info.q
     return dict(q=q, precs=[PREC_NAME[info.precs[k]] for k in range(q)], nnz_k=list(info.nnz_k[:q]),
@@ -378,6 +395,18 @@ def gmres(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | Non
     return out
 
 
+def gmres_b(Ah: AHandle, BA: BMHandle, BM: BMHandle, r, d, u_g="fp32", o: Opts | None = None,
+            stream=None) -> dict:
+    """bspai_gmres with A v taken through A's buckets (bucket_A) instead of A in u_p."""
+    si = SolveInfo()
+    st = _lib.bspai_gmres_b(Ah.ptr, BA.ptr, BM.ptr, _ptr(r), PREC[u_g], C.byref(o or opts()), _ptr(d),
+                            _stream(stream), C.byref(si))
+    _check(st, (OK, NONFINITE))
+    out = _solve_info(si)
+    out["status"] = st
+    return out
+
+
 def gmres_noalloc(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | None = None,
                   stream=None) -> dict:
     """bspai_gmres with its workspace in the library's fixed device block
@@ -402,6 +431,19 @@ def gmres_ir_solve(A, b, BM: BMHandle, M: MHandle | None, x, u="fp64", u_r="dd",
     else:
         st = _lib.gmres_ir_solve(C.byref(A.c()), _ptr(b), BM.ptr, mp, PREC[u], PREC[u_r], PREC[u_g], PREC[u_p],
                                  float(tol), C.byref(o or opts()), _ptr(x), _stream(stream), C.byref(si))
+    _check(st, (OK, NOT_CONVERGED, NONFINITE))
+    out = _solve_info(si)
+    out["status"] = st
+    return out
+
+
+def gmres_ir_solve_hb(Ah: AHandle, BA: BMHandle, b, BM: BMHandle, M: MHandle | None, x, u="fp64", u_r="dd",
+                      u_g="fp32", tol=1e-4, o: Opts | None = None, stream=None) -> dict:
+    """gmres_ir_solve with A v inside GMRES through A's buckets (bucket_A)."""
+    si = SolveInfo()
+    st = _lib.gmres_ir_solve_hb(Ah.ptr, BA.ptr, _ptr(b), BM.ptr, M.ptr if M is not None else None, PREC[u],
+                                PREC[u_r], PREC[u_g], float(tol), C.byref(o or opts()), _ptr(x), _stream(stream),
+                                C.byref(si))
     _check(st, (OK, NOT_CONVERGED, NONFINITE))
     out = _solve_info(si)
     out["status"] = st

@@ -1,4 +1,5 @@
-// bucket.cu -- precision buckets of M (eq. nint, Alg 2.2) and their storage.
+// bucket.cu -- precision buckets of M (eq. nint, Alg 2.2) and their storage;
+// the same bucketing applied to A (fp64 values) for the bucketed A v.
 //
 // ||M||_inf is the max over rows of the fp64 sum of |m_ij| taken in ascending
 // column order (one thread per row), so it and the thresholds
@@ -67,7 +68,8 @@ __device__ __forceinline__ int seg_of(const int32_t* slice_seg, int64_t slice) {
     return slice_seg ? slice_seg[slice] : 0;
 }
 
-__global__ void k_norm_rows(int n, const int64_t* __restrict__ sptr, const float* __restrict__ val,
+template <typename VT>
+__global__ void k_norm_rows(int n, const int64_t* __restrict__ sptr, const VT* __restrict__ val,
                             const int32_t* __restrict__ rowlen, const int32_t* __restrict__ slice_seg,
                             double* __restrict__ norm) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,13 +103,14 @@ __device__ __forceinline__ int classify(double a, const double* thr, int q) {
 
 // bucket id of every entry; per-slice widths of every bucket; per-bucket
 // counts and max |m|; per-column max |m| of the e4m3 bucket
+template <typename VT>
 __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int64_t* __restrict__ sptr,
-                                                  const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                  const int32_t* __restrict__ col, const VT* __restrict__ val,
                                                   const int32_t* __restrict__ rowlen,
                                                   const __grid_constant__ BucketParams P,
                                                   const double* __restrict__ thr_g, int8_t* __restrict__ id,
                                                   int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
-                                                  float* __restrict__ bmax, float* __restrict__ colmax,
+                                                  VT* __restrict__ bmax, VT* __restrict__ colmax,
                                                   int* __restrict__ wmax, const int32_t* __restrict__ slice_seg) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nslices * kSlice) return;
@@ -116,26 +119,26 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
 #pragma unroll
     for (int k = 0; k < 8; ++k) thr[k] = k < P.q ? thr_g[sg * 8 + k] : 0.0;
     int cnt[8];
-    float mx[8];
+    VT mx[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         cnt[k] = 0;
-        mx[k] = 0.0f;
+        mx[k] = VT(0);
     }
     if (r < n) {
         const int64_t b = sptr[r >> 5] + (r & 31);
         const int len = rowlen[r];
         for (int l = 0; l < len; ++l) {
             const int64_t slot = b + (int64_t)l * kSlice;
-            const float m = val[slot];
-            const float am = fabsf(m);
+            const VT m = val[slot];
+            const VT am = fabs(m);
             const int k = classify((double)am, thr, P.q);
             id[slot] = (int8_t)k;
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 if (kk == k) {
                     cnt[kk] += 1;
-                    mx[kk] = fmaxf(mx[kk], am);
+                    mx[kk] = fmax(mx[kk], am);
                 }
             }
             if (P.precs[k] == BSPAI_E4M3) atomic_max_nonneg(colmax + col[slot], am);
@@ -146,25 +149,24 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
     for (int k = 0; k < 8; ++k) {
         if (k >= P.q) break;
         int w = cnt[k], c = cnt[k];
-        float m = mx[k];
+        VT m = mx[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
             c += __shfl_xor_sync(0xffffffffu, c, o);
-            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            m = fmax(m, (VT)__shfl_xor_sync(0xffffffffu, m, o));
         }
         if (lane == 0) {
             widths[(int64_t)k * (nslices + 1) + (r >> 5)] = (int64_t)w * kSlice;
             if (c) atomicAdd(nnzk + k, (unsigned long long)c);
-            if (m > 0.0f) atomic_max_nonneg(bmax + sg * 8 + k, m);
+            if (m > VT(0)) atomic_max_nonneg(bmax + sg * 8 + k, m);
             if (w) atomicMax(wmax + k, w);
         }
     }
 }
 
 // least power of two s = 2^e with maxabs <= fmax * 2^e (1 if maxabs == 0)
-__device__ __forceinline__ float pow2_scale(float maxabs_f, double fmax) {
-    const double maxabs = (double)maxabs_f;
+__device__ __forceinline__ float pow2_scale(double maxabs, double fmax) {
     if (!(maxabs > 0.0)) return 1.0f;
     int E;
     frexp(maxabs / fmax, &E);
@@ -174,12 +176,13 @@ __device__ __forceinline__ float pow2_scale(float maxabs_f, double fmax) {
     return (float)ldexp(1.0, e);
 }
 
-__global__ void k_bucket_scales(const __grid_constant__ BucketParams P, int nseg, const float* __restrict__ bmax,
+template <typename VT>
+__global__ void k_bucket_scales(const __grid_constant__ BucketParams P, int nseg, const VT* __restrict__ bmax,
                                 float* __restrict__ scale) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = i & 7;
     if (i >= nseg * 8 || k >= P.q) return;
-    scale[i] = P.precs[k] == BSPAI_FP16 ? pow2_scale(bmax[i], 65504.0) : 1.0f;
+    scale[i] = P.precs[k] == BSPAI_FP16 ? pow2_scale((double)bmax[i], 65504.0) : 1.0f;
 }
 
 // per-slice copy of an fp16 bucket's scale (batches of several systems)
@@ -189,9 +192,10 @@ __global__ void k_slice_scales(int nslices, const int32_t* __restrict__ slice_se
     if (s < nslices) out[s] = scale[slice_seg[s] * 8 + k];
 }
 
-__global__ void k_col_scales(int n, const float* __restrict__ colmax, float* __restrict__ colscale) {
+template <typename VT>
+__global__ void k_col_scales(int n, const VT* __restrict__ colmax, float* __restrict__ colscale) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) colscale[j] = pow2_scale(colmax[j], 448.0);
+    if (j < n) colscale[j] = pow2_scale((double)colmax[j], 448.0);
 }
 
 __device__ __forceinline__ void store_val(void* dst, int64_t p, int prec, float m, float scale, float cs) {
@@ -208,6 +212,21 @@ __device__ __forceinline__ void store_val(void* dst, int64_t p, int prec, float 
     }
 }
 
+// the same from an fp64 value (bucketing A): one rounding from fp64 to the format
+__device__ __forceinline__ void store_val(void* dst, int64_t p, int prec, double m, float scale, float cs) {
+    switch (prec) {
+    case BSPAI_FP64: reinterpret_cast<double*>(dst)[p] = m; break;
+    case BSPAI_FP32: reinterpret_cast<float*>(dst)[p] = __double2float_rn(m); break;
+    case BSPAI_FP16: reinterpret_cast<__half*>(dst)[p] = __double2half(__ddiv_rn(m, (double)scale)); break;
+    case BSPAI_BF16: reinterpret_cast<__nv_bfloat16*>(dst)[p] = __double2bfloat16(m); break;
+    case BSPAI_E4M3:
+        reinterpret_cast<__nv_fp8_storage_t*>(dst)[p] =
+            __nv_cvt_double_to_fp8(__ddiv_rn(m, (double)cs), __NV_SATFINITE, __NV_E4M3);
+        break;
+    default: break;
+    }
+}
+
 __device__ __forceinline__ void store_zero(void* dst, int64_t p, int prec) {
     switch (prec) {
     case BSPAI_FP64: reinterpret_cast<double*>(dst)[p] = 0.0; break;
@@ -219,8 +238,9 @@ __device__ __forceinline__ void store_zero(void* dst, int64_t p, int prec) {
     }
 }
 
+template <typename VT>
 __global__ void __launch_bounds__(256) k_pack(int n, int nslices, const int64_t* __restrict__ sptr,
-                                              const int32_t* __restrict__ col, const float* __restrict__ val,
+                                              const int32_t* __restrict__ col, const VT* __restrict__ val,
                                               const int32_t* __restrict__ rowlen, const int8_t* __restrict__ id,
                                               const __grid_constant__ PackDst D, const float* __restrict__ scale_g,
                                               const float* __restrict__ colscale,
@@ -318,14 +338,26 @@ __global__ void k_bucket_export(int n, const int64_t* __restrict__ msptr, const 
 
 using namespace bspai;
 
-// Bucketing of M, of one system (slice_seg = null, nseg = 1) or of nseg
-// independent systems stacked block-diagonally (slice_seg: system of every
-// 32-row slice).
-static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, const int32_t* slice_seg,
-                       int nseg, cudaStream_t s, bspai_BM_h* out, bspai_bucket_info_t* info) {
+// The matrix a bucketing reads: SELL structure, values (fp32 for M, fp64 for
+// A), row lengths and CSR row pointers (for export in CSR order).
+template <typename VT>
+struct BucketSrc {
+    int n;
+    int64_t nnz;
+    const Sell* sell;
+    const VT* val;
+    const int32_t* rowlen;
+    const int32_t* csr_row_ptr;
+};
+
+// Bucketing of one system (slice_seg = null, nseg = 1) or of nseg independent
+// systems stacked block-diagonally (slice_seg: system of every 32-row slice).
+template <typename VT>
+static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t* precs, int32_t q,
+                       const int32_t* slice_seg, int nseg, cudaStream_t s, bspai_BM_h* out,
+                       bspai_bucket_info_t* info) {
     if (!out) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: null out");
     *out = nullptr;
-    if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: bad M handle");
     if (!precs || q < 1 || q > 8) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: need 1 <= q <= 8 precisions");
     if (!(bucket_eps > 0.0)) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: bucket_eps must be > 0");
     BucketParams P{};
@@ -341,13 +373,13 @@ static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int
         n_e4m3 += precs[k] == BSPAI_E4M3;
     }
     if (n_e4m3 > 1) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_bucket: at most one e4m3 bucket");
-    const int n = M->n;
-    const int nsl = M->sell.nslices;
+    const int n = S.n;
+    const int nsl = S.sell->nslices;
     auto* B = new bspai_bucketed();
     B->magic = kMagicBM;
     B->stream = s;
     B->n = n;
-    B->nnz = M->nnz;
+    B->nnz = S.nnz;
     B->q = q;
     for (int k = 0; k < q; ++k) B->precs[k] = precs[k];
 
@@ -356,9 +388,9 @@ static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int
     double* d_thr = nullptr;
     int64_t* d_w = nullptr;
     unsigned long long* d_nnzk = nullptr;
-    float* d_bmax = nullptr;
+    VT* d_bmax = nullptr;
     float* d_scale = nullptr;
-    float* d_colmax = nullptr;
+    VT* d_colmax = nullptr;
     int* d_wmax = nullptr;
     auto cleanup = [&]() {
         dfree(d_norm, s); dfree(d_thr, s); dfree(d_w, s); dfree(d_nnzk, s);
@@ -374,12 +406,12 @@ static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int
     // private copy of M's structure (for export) and the bucket id per slot
     B->msell.n = n;
     B->msell.nslices = nsl;
-    B->msell.slots = M->sell.slots;
+    B->msell.slots = S.sell->slots;
     if ((rc = dalloc_t(&B->msell.sptr, (size_t)nsl + 1, s))) return fail(rc);
-    if ((rc = dalloc_t(&B->msell.col, (size_t)M->sell.slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&B->msell.col, (size_t)S.sell->slots, s))) return fail(rc);
     if ((rc = dalloc_t(&B->mrowlen, (size_t)n, s))) return fail(rc);
     if ((rc = dalloc_t(&B->mcsr_row_ptr, (size_t)n + 1, s))) return fail(rc);
-    if ((rc = dalloc_t(&B->id_sell, (size_t)M->sell.slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&B->id_sell, (size_t)S.sell->slots, s))) return fail(rc);
     if ((rc = dalloc_t(&d_norm, (size_t)nseg, s))) return fail(rc);
     if ((rc = dalloc_t(&d_thr, (size_t)nseg * 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_w, (size_t)q * (nsl + 1), s))) return fail(rc);
@@ -392,37 +424,37 @@ static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int
         if ((rc = dalloc_t(&B->colscale, (size_t)n, s))) return fail(rc);
     }
     cudaError_t e = cudaSuccess;
-    e = cudaMemcpyAsync(B->msell.sptr, M->sell.sptr, sizeof(int64_t) * ((size_t)nsl + 1), cudaMemcpyDeviceToDevice, s);
-    if (!e) e = cudaMemcpyAsync(B->msell.col, M->sell.col, sizeof(int32_t) * (size_t)M->sell.slots, cudaMemcpyDeviceToDevice, s);
-    if (!e) e = cudaMemcpyAsync(B->mrowlen, M->rowlen, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
-    if (!e) e = cudaMemcpyAsync(B->mcsr_row_ptr, M->csr_row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(B->msell.sptr, S.sell->sptr, sizeof(int64_t) * ((size_t)nsl + 1), cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(B->msell.col, S.sell->col, sizeof(int32_t) * (size_t)S.sell->slots, cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(B->mrowlen, S.rowlen, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaMemcpyAsync(B->mcsr_row_ptr, S.csr_row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s);
     if (!e) e = cudaMemsetAsync(d_norm, 0, sizeof(double) * (size_t)nseg, s);
     if (!e) e = cudaMemsetAsync(d_nnzk, 0, 8 * sizeof(unsigned long long), s);
-    if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(float) * (size_t)nseg, s);
+    if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(VT) * (size_t)nseg, s);
     if (!e) e = cudaMemsetAsync(d_wmax, 0, 8 * sizeof(int), s);
     if (!e) e = cudaMemsetAsync(d_w, 0, sizeof(int64_t) * (size_t)q * (nsl + 1), s);
-    if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(float) * (size_t)n, s);
+    if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(VT) * (size_t)n, s);
     if (e) return fail(cuda_error(e, "bspai_bucket setup", __FILE__, __LINE__));
     const unsigned g_rows = (unsigned)ceil_div((int64_t)nsl * kSlice, 256);
     const unsigned g_seg = (unsigned)ceil_div(nseg, 256), g_seg8 = (unsigned)ceil_div((int64_t)nseg * 8, 256);
     if (n > 0) {
-        k_norm_rows<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, M->sell.sptr, M->val, M->rowlen, slice_seg, d_norm);
+        k_norm_rows<VT><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, S.sell->sptr, S.val, S.rowlen, slice_seg, d_norm);
         note_launch();
         k_thresholds<<<g_seg, 256, 0, s>>>(P, nseg, d_norm, d_thr);
         note_launch();
-        k_classify<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, P, d_thr,
-                                          B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax, slice_seg);
+        k_classify<VT><<<g_rows, 256, 0, s>>>(n, nsl, S.sell->sptr, S.sell->col, S.val, S.rowlen, P, d_thr,
+                                              B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax, slice_seg);
         note_launch();
-        k_bucket_scales<<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
+        k_bucket_scales<VT><<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
         note_launch();
         if (d_colmax) {
-            k_col_scales<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, d_colmax, B->colscale);
+            k_col_scales<VT><<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, d_colmax, B->colscale);
             note_launch();
         }
     } else {
         k_thresholds<<<g_seg, 256, 0, s>>>(P, nseg, d_norm, d_thr);
         note_launch();
-        k_bucket_scales<<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
+        k_bucket_scales<VT><<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
         note_launch();
     }
     if ((e = cudaGetLastError())) return fail(cuda_error(e, "bucket classify", __FILE__, __LINE__));
@@ -476,8 +508,8 @@ static int bucket_impl(bspai_M_h M, double bucket_eps, const int32_t* precs, int
     }
     if (B->colscale) bytes += (int64_t)sizeof(float) * n;
     if (n > 0) {
-        k_pack<<<g_rows, 256, 0, s>>>(n, nsl, M->sell.sptr, M->sell.col, M->val, M->rowlen, B->id_sell, D, d_scale,
-                                      B->colscale, slice_seg);
+        k_pack<VT><<<g_rows, 256, 0, s>>>(n, nsl, S.sell->sptr, S.sell->col, S.val, S.rowlen, B->id_sell, D, d_scale,
+                                          B->colscale, slice_seg);
         note_launch();
         if ((e = cudaGetLastError())) return fail(cuda_error(e, "k_pack", __FILE__, __LINE__));
     }
@@ -540,9 +572,25 @@ __global__ void k_slice_seg(int nseg, const int32_t* __restrict__ row_off, int32
 
 extern "C" {
 
+static BucketSrc<float> m_source(const bspai_spai* M) {
+    return BucketSrc<float>{M->n, M->nnz, &M->sell, M->val, M->rowlen, M->csr_row_ptr};
+}
+
 int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, bspai_stream_t st,
                  bspai_BM_h* out, bspai_bucket_info_t* info) {
-    return bucket_impl(M, bucket_eps, precs, q, nullptr, 1, (cudaStream_t)st, out, info);
+    if (out) *out = nullptr;
+    if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_bucket: bad M handle");
+    return bucket_impl(m_source(M), bucket_eps, precs, q, nullptr, 1, (cudaStream_t)st, out, info);
+}
+
+int bspai_bucket_A(bspai_A_h A, double bucket_eps, const int32_t* precs, int32_t q, bspai_stream_t st,
+                   bspai_BM_h* out, bspai_bucket_info_t* info) {
+    if (out) *out = nullptr;
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_bucket_A: bad A handle");
+    if (!A->rowlen || !A->csr_row_ptr)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_bucket_A: A has no row lengths (a transposed A)");
+    const BucketSrc<double> src{A->n, A->nnz, &A->sell, A->val64, A->rowlen, A->csr_row_ptr};
+    return bucket_impl(src, bucket_eps, precs, q, nullptr, 1, (cudaStream_t)st, out, info);
 }
 
 int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, double bucket_eps, const int32_t* precs,
@@ -575,7 +623,7 @@ int bspai_bucket_batched(bspai_M_h M, const int32_t* row_off, int32_t nsys, doub
     if (hbad)
         rc = set_error(BSPAI_ERR_INVALID, "bspai_bucket_batched: system offsets must be non-decreasing multiples of 32");
     else
-        rc = bucket_impl(M, bucket_eps, precs, q, slice_seg, nsys, s, out, info);
+        rc = bucket_impl(m_source(M), bucket_eps, precs, q, slice_seg, nsys, s, out, info);
     dfree(slice_seg, s);
     dfree(bad, s);
     return rc;

@@ -97,6 +97,8 @@ struct bspai_matrix {
     double* val64 = nullptr;   // A in fp64 (residual, u_r)
     float* val32 = nullptr;    // A rounded to fp32 (u_p)
     double* norm_inf = nullptr;// device scalar ||A||_inf
+    int32_t* rowlen = nullptr; // entries per row (null for a transposed A)
+    int32_t* csr_row_ptr = nullptr; // copy of A's CSR row pointers (null for a transposed A)
 };
 
 struct bspai_spai {

@@ -552,6 +552,7 @@ struct GmresWork {
     double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *norms = nullptr;
     HostFlags* hflags = nullptr;  // pinned
     unsigned long long tmo_ns = 2000000000ull;
+    const bspai_bucketed* BA = nullptr;  // bucketed A for A v (null: A in u_p)
     void* res_fn = nullptr;  // k_mgs_res instance, or null for k_mgs
     int res_bd = 1024;       // its block size
     int Gr = 0;              // its grid: one block of 1024 threads per SM
@@ -685,8 +686,11 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
     cudaStream_t s = W.s;
     const int n = W.n;
     const int tprec = W.ug;  // T matches u_g
-    const BMDev Aview = single_bucket_view(A->sell, W.up == BSPAI_FP64 ? (const void*)A->val64 : (const void*)A->val32,
-                                           W.up);
+    // A v: A in u_p, or A's buckets by the adaptive-precision SpMV (Alg 2.3 applied to A)
+    const BMDev Aview = W.BA ? W.BA->dev()
+                             : single_bucket_view(A->sell, W.up == BSPAI_FP64 ? (const void*)A->val64
+                                                                              : (const void*)A->val32,
+                                                  W.up);
     const BMDev Mview = BM->dev();
     T* V = reinterpret_cast<T*>(W.V);
     T* w = reinterpret_cast<T*>(W.w);
@@ -792,9 +796,9 @@ static int resolve_kmax(const bspai_opts_t* o, int n) {
 int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
                          int u_r, cudaStream_t s);
 
-static int ir_solve(bspai_matrix* A, const double* b, const bspai_bucketed* BM, const bspai_spai* M, int u_r,
-                    int u_g, int u_p, double tol, const bspai_opts_t* opts, double* x, cudaStream_t s,
-                    bspai_solve_info_t* info) {
+static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, const bspai_bucketed* BM,
+                    const bspai_spai* M, int u_r, int u_g, int u_p, double tol, const bspai_opts_t* opts, double* x,
+                    cudaStream_t s, bspai_solve_info_t* info) {
     bspai_opts_t o;
     bspai_opts_default(&o);
     if (opts) o = *opts;
@@ -828,6 +832,7 @@ static int ir_solve(bspai_matrix* A, const double* b, const bspai_bucketed* BM, 
     if ((rc = dalloc_t(&r, (size_t)n, s))) return finish(rc);
     if ((rc = dalloc_t(&nrm, 4, s))) return finish(rc);
     if ((rc = W.alloc(n, kmax, u_g, u_p, o.barrier_timeout_s, o.max_blocks, s))) return finish(rc);
+    W.BA = BA;
     // ||A||_inf, ||b||_inf
     double anorm = 0.0, bnorm = 0.0;
     {
@@ -962,7 +967,20 @@ int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h BM, bspai_M_h M, b
     if (M && M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: bad M handle");
     if (A->n > 0 && (!b || !x)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: null vector");
     BSPAI_TRY(check_solver_precs(u, u_r, u_g, u_p));
-    return ir_solve(A, b, BM, M, u_r, u_g, u_p, tol, opts, x, (cudaStream_t)s, info);
+    return ir_solve(A, nullptr, b, BM, M, u_r, u_g, u_p, tol, opts, x, (cudaStream_t)s, info);
+}
+
+int gmres_ir_solve_hb(bspai_A_h A, bspai_BM_h A_bucketed, const double* b, bspai_BM_h BM, bspai_M_h M,
+                      bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, double tol, const bspai_opts_t* opts,
+                      double* x, bspai_stream_t s, bspai_solve_info_t* info) {
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: bad A handle");
+    if (!A_bucketed || A_bucketed->magic != kMagicBM || A_bucketed->n != A->n)
+        return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: bad bucketed A handle");
+    if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: bad bucketed M handle");
+    if (M && M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: bad M handle");
+    if (A->n > 0 && (!b || !x)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: null vector");
+    BSPAI_TRY(check_solver_precs(u, u_r, u_g, u_g));
+    return ir_solve(A, A_bucketed, b, BM, M, u_r, u_g, u_g, tol, opts, x, (cudaStream_t)s, info);
 }
 
 int gmres_ir_solve(const bspai_csr_t* Acsr, const double* b, bspai_BM_h BM, bspai_M_h M, bspai_prec_t u,
@@ -976,8 +994,9 @@ int gmres_ir_solve(const bspai_csr_t* Acsr, const double* b, bspai_BM_h BM, bspa
     return rc;
 }
 
-int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
-                const bspai_opts_t* opts, double* d, bspai_stream_t st, bspai_solve_info_t* info) {
+static int gmres_one(bspai_matrix* A, const bspai_bucketed* BA, const bspai_bucketed* BM, const double* r,
+                     bspai_prec_t u_g, bspai_prec_t u_p, const bspai_opts_t* opts, double* d, bspai_stream_t st,
+                     bspai_solve_info_t* info) {
     cudaStream_t s = (cudaStream_t)st;
     if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_gmres: bad A handle");
     if (!BM || BM->magic != kMagicBM) return set_error(BSPAI_ERR_INVALID, "bspai_gmres: bad M handle");
@@ -995,6 +1014,7 @@ int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, b
     }
     GmresWork W;
     int rc = W.alloc(A->n, resolve_kmax(&o, A->n), u_g, u_p, o.barrier_timeout_s, o.max_blocks, s);
+    W.BA = BA;
     GmresResult gr;
     if (!rc)
         rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, o.tau, nullptr, d, gr)
@@ -1008,6 +1028,18 @@ int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, b
     if (info) *info = inf;
     if (!rc && gr.status == BSPAI_NONFINITE) return set_error(BSPAI_NONFINITE, "bspai_gmres: non-finite value");
     return rc;
+}
+
+int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
+                const bspai_opts_t* opts, double* d, bspai_stream_t st, bspai_solve_info_t* info) {
+    return gmres_one(A, nullptr, BM, r, u_g, u_p, opts, d, st, info);
+}
+
+int bspai_gmres_b(bspai_A_h A, bspai_BM_h A_bucketed, bspai_BM_h BM, const double* r, bspai_prec_t u_g,
+                  const bspai_opts_t* opts, double* d, bspai_stream_t st, bspai_solve_info_t* info) {
+    if (!A_bucketed || A_bucketed->magic != kMagicBM || (A && A_bucketed->n != A->n))
+        return set_error(BSPAI_ERR_INVALID, "bspai_gmres_b: bad bucketed A handle");
+    return gmres_one(A, A_bucketed, BM, r, u_g, u_g, opts, d, st, info);
 }
 
 }  // extern "C"

@@ -319,7 +319,13 @@ int matrix_create(const bspai_csr_t* A, cudaStream_t s, bspai_matrix** out) {
     int st;
     {
         ProfScope ps(BSPAI_K_OTHER, s);
-        st = sell_from_csr(A->n, A->row_ptr, A->col, A->val, &M->sell, &M->val64, &M->val32, nullptr, s);
+        st = sell_from_csr(A->n, A->row_ptr, A->col, A->val, &M->sell, &M->val64, &M->val32, &M->rowlen, s);
+        if (st == BSPAI_OK) st = dalloc_t(&M->csr_row_ptr, (size_t)A->n + 1, s);
+        if (st == BSPAI_OK) {
+            cudaError_t e = cudaMemcpyAsync(M->csr_row_ptr, A->row_ptr, sizeof(int32_t) * ((size_t)A->n + 1),
+                                            cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = cuda_error(e, "copy", __FILE__, __LINE__);
+        }
         if (st == BSPAI_OK) st = dalloc_t(&M->norm_inf, 1, s);
         if (st == BSPAI_OK) {
             cudaError_t e = cudaMemsetAsync(M->norm_inf, 0, sizeof(double), s);

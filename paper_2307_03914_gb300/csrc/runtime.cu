@@ -246,6 +246,8 @@ int bspai_free(void* h) {
         dfree(A->val64, s);
         dfree(A->val32, s);
         dfree(A->norm_inf, s);
+        dfree(A->rowlen, s);
+        dfree(A->csr_row_ptr, s);
         A->magic = kMagicDead;
         delete A;
     } else if (magic == kMagicM) {

@@ -131,3 +131,78 @@ def test_ir_solves_workloads_to_forward_error_1e10(orc, name, grid):
     # bucketing with q = 1 is plain SPAI-GMRES-IR: same iterates as the unbucketed M
     out1 = orc.solve(wl, precs=["fp64"])
     assert np.abs(out1["x"] - xt).max() / np.abs(xt).max() <= 1e-10
+
+
+def _a_buckets(orc, A, eps, fmts):
+    ids = orc.bucket_ids(A.row_ptr, A.val, eps, fmts)["ids"]
+    stored, _, _ = orc.bucket_store(A.row_ptr, A.col, A.val, ids, fmts)
+    return stored, ids
+
+
+def test_single_fp64_bucket_of_A_is_A_in_fp64(orc):
+    """A v through one fp64 bucket of A (eq. nbe2 with q = 1) is A v with u_p =
+    fp64: the GMRES iterates agree to the last bit."""
+    A = W.convdiff2d(7)
+    Ad = A.to_scipy().toarray()
+    M = np.diag(1.0 / np.diag(Ad))
+    Mc = _csr(M)
+    mids = np.zeros(Mc.nnz, np.int8)
+    a_stored, a_ids = _a_buckets(orc, A, 2.0 ** -20, ["fp64"])
+    assert np.array_equal(a_stored, A.val) and not a_ids.any()
+    r = np.random.default_rng(7).uniform(-1, 1, A.n)
+    S0 = orc.System(A, Mc.row_ptr, Mc.col, Mc.val, mids, ["fp64"])
+    S1 = orc.System(A, Mc.row_ptr, Mc.col, Mc.val, mids, ["fp64"], a_stored, a_ids)
+    d0, i0, _ = orc.gmres(S0, r, ug="fp64", up="fp64", tau=0.0, kmax=9)
+    d1, i1, _ = orc.gmres(S1, r, ug="fp64", up="fp64", tau=0.0, kmax=9)
+    assert i0 == i1 == 9 and np.array_equal(d0, d1)
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_gmres_with_bucketed_A_minimises_over_perturbed_krylov_space(orc, k):
+    """With A bucketed into {fp64, drop}, A v inside GMRES is A~ v where A~
+    keeps the fp64 bucket and zeroes the dropped entries; GMRES(k) then
+    returns argmin ||s - M A~ d|| over K_k(M A~, s), s = M r."""
+    A = W.random_sparse(60, 6, sigma=2.0, delta=0.3, seed=11)
+    fmts = ["fp64", "drop"]
+    a_stored, a_ids = _a_buckets(orc, A, 2.0 ** -14, fmts)
+    assert (a_ids == 1).any() and (a_ids == 0).any()
+    At = sp.csr_matrix((np.where(a_ids == 0, a_stored, 0.0), A.col, A.row_ptr), shape=(A.n, A.n)).toarray()
+    Ad = A.to_scipy().toarray()
+    assert not np.array_equal(At, Ad)
+    M = np.diag(1.0 / np.diag(Ad))
+    Mc = _csr(M)
+    S = orc.System(A, Mc.row_ptr, Mc.col, Mc.val, np.zeros(Mc.nnz, np.int8), fmts, a_stored, a_ids)
+    r = np.random.default_rng(k).uniform(-1, 1, A.n)
+    d, its, _ = orc.gmres(S, r, ug="fp64", up="fp64", tau=0.0, kmax=k)
+    assert its == k
+    T = M @ At
+    s = M @ r
+    K = np.empty((A.n, k))
+    v = s.copy()
+    for j in range(k):
+        K[:, j] = v / np.linalg.norm(v)
+        v = T @ K[:, j]
+    c, *_ = np.linalg.lstsq(T @ K, s, rcond=None)
+    ref = K @ c
+    assert np.linalg.norm(d - ref) <= 1e-12 * np.linalg.norm(ref)
+    # and not the minimiser over the unperturbed operator
+    T0 = M @ Ad
+    K0 = np.empty((A.n, k))
+    v = s.copy()
+    for j in range(k):
+        K0[:, j] = v / np.linalg.norm(v)
+        v = T0 @ K0[:, j]
+    c0, *_ = np.linalg.lstsq(T0 @ K0, s, rcond=None)
+    assert np.linalg.norm(d - K0 @ c0) > 1e-4 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name,grid", [("convdiff2d", 32), ("convdiff3d", 8)])
+def test_ir_with_bucketed_A_reaches_forward_error_1e10(orc, name, grid):
+    """Refinement with A v in the bucketed precisions still converges: the
+    residual uses A itself, so the perturbation of A inside GMRES only slows
+    the correction solves down (Section 3, fe2)."""
+    wl = W.workload(name, grid=grid)
+    for eps in [2.0 ** -16, 2.0 ** -10]:
+        out = orc.solve(wl, bucket_eps=eps, bucket_A=True)
+        xt = wl["x_true"]
+        assert np.abs(out["x"] - xt).max() / np.abs(xt).max() <= 1e-10
