@@ -77,6 +77,7 @@ def _declare(L):
     L.orc_set_threads.argtypes = [C.c_int]
     L.orc_get_threads.restype = C.c_int
     L.orc_residual_dd.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.orc_residual_fp64.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
     L.orc_householder_ls.argtypes = [C.c_int, C.c_int, _f64p, _f64p, C.c_double, _f64p,
                                      C.POINTER(C.c_double)]
     L.orc_householder_ls.restype = C.c_int
@@ -102,8 +103,8 @@ def _declare(L):
                             _f64p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.orc_gmres.restype = C.c_int
     L.orc_gmres_ir.argtypes = [C.POINTER(_System), _f64p, _f64p, C.c_int, C.c_int, C.c_double,
-                               C.c_int, C.c_int, C.c_double, C.c_int, _f64p, _i32p, _f64p,
-                               _f64p, C.POINTER(C.c_int)]
+                               C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, _f64p, _i32p,
+                               _f64p, _f64p, C.POINTER(C.c_int)]
     L.orc_gmres_ir.restype = C.c_int
 
 
@@ -153,6 +154,15 @@ def residual_dd(A, x, b) -> np.ndarray:
     arithmetic (fractions) in tests."""
     r = np.empty(A.n)
     lib().orc_residual_dd(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(x), _f64(b), r)
+    return r
+
+
+def residual_fp64(A, x, b) -> np.ndarray:
+    """r = b - A x in plain fp64 (u_r = double), products and differences
+    rounded in ascending column order.  Pinned by exact rational arithmetic
+    (the textbook bound gamma_p (|b| + |A||x|)) and by exactness on integer data."""
+    r = np.empty(A.n)
+    lib().orc_residual_fp64(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _f64(x), _f64(b), r)
     return r
 
 
@@ -282,16 +292,26 @@ def gmres(system: System, r, ug="fp32", up="fp32", tau=1e-4, kmax=500):
     return d, it.value, rr.value
 
 
+UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
+
+
 def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, imax=10,
-             u_work=2.0 ** -53, x0=None) -> dict:
+             u_work=None, x0=None, u="fp64", u_r="dd") -> dict:
+    """Alg 3.1 with working precision u (fp64, or fp32 for the (single,
+    single, double) setting of Section 4) and residual precision u_r ("dd":
+    Dot2, about twice fp64; "fp64": plain fp64).  x, r and the correction are
+    held in u; u_work (the stopping level) defaults to u's unit roundoff."""
+    if u not in UNIT_ROUNDOFF or u_r not in ("dd", "fp64"):
+        raise ValueError("u must be fp64 or fp32, u_r dd or fp64")
+    u_work = UNIT_ROUNDOFF[u] if u_work is None else u_work
     x = np.zeros(system.n) if x0 is None else _f64(x0).copy()
     its = np.zeros(imax, dtype=np.int32)
     nbe = np.zeros(imax)
     dx = np.zeros(imax)
     stop = C.c_int(0)
     steps = lib().orc_gmres_ir(C.byref(system.s), _f64(muf), _f64(b), FMT[ug], FMT[up], tau,
-                               int(kmax), int(imax), u_work, int(x0 is not None), x, its, nbe,
-                               dx, C.byref(stop))
+                               int(kmax), int(imax), u_work, FMT[u], int(u_r == "dd"),
+                               int(x0 is not None), x, its, nbe, dx, C.byref(stop))
     nsteps = min(imax, steps + (1 if stop.value == 1 else 0))
     return dict(x=x, steps=steps, its=its[:max(steps, 0)].tolist(), nbe=nbe[:nsteps].tolist(),
                 dx=dx[:steps].tolist(), stop=stop.value)
@@ -329,7 +349,8 @@ def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
     return dict(lam=lam, dA=dA, db=lam, info=out)
 
 
-def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False) -> dict:
+def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False, u="fp64",
+          u_r="dd", ug=None, up=None) -> dict:
     """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR.
     bucket_A: A v inside GMRES by the bucketed SpMV on A's own buckets (same
     precisions and bucket_eps, thresholds from ||A||_inf; eq. nbe2)."""
@@ -346,7 +367,7 @@ def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bu
         a_ids = ak["ids"]
         a_stored, _, _ = bucket_store(A.row_ptr, A.col, A.val, a_ids, precs)
     S = System(A, P.row_ptr, P.col, stored, bk["ids"], precs, a_stored, a_ids)
-    out = gmres_ir(S, muf, wl["b"], wl["u_g"], wl["u_p"], wl["tau"] if tau is None else tau,
-                   kmax, imax)
+    out = gmres_ir(S, muf, wl["b"], wl["u_g"] if ug is None else ug, wl["u_p"] if up is None else up,
+                   wl["tau"] if tau is None else tau, kmax, imax, u=u, u_r=u_r)
     out.update(spai=sp, muf=muf, buckets=bk, stored=stored)
     return out

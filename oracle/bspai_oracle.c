@@ -139,6 +139,23 @@ void orc_residual_dd(int n, const int* rp, const int* ci, const double* av,
     }
 }
 
+/* r = b - A x in plain fp64: r_i = (...((b_i - a_i1 x_1) - a_i2 x_2) ...), every
+ * product and every difference rounded to fp64, ascending column order (Alg 3.1
+ * residual line with u_r = double, the (single, single, double) setting of
+ * Section 4). */
+void orc_residual_fp64(int n, const int* rp, const int* ci, const double* av,
+                       const double* x, const double* b, double* r) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+        double acc = b[i];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            double p = av[k] * x[ci[k]];
+            acc = acc - p;
+        }
+        r[i] = acc;
+    }
+}
+
 /* ----------------------------------------------------------- Householder LS */
 
 int orc_householder_ls(int m, int k, const double* A0, const double* b0, double rank_tol,
@@ -576,26 +593,38 @@ static double vnorm_inf(int n, const double* v) {
 
 int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
                  int ug, int up, double tau, int kmax, int imax, double u_work,
+                 int uw, int ur_dd,
                  int x0_given, double* x, int* its, double* nbe, double* dx, int* stop) {
     int n = S->n;
     double* r = (double*)malloc(sizeof(double) * (size_t)n);
     double* d = (double*)malloc(sizeof(double) * (size_t)n);
     /* x0 = M b with the unbucketed M in u_f = fp32, stored in fp64 */
     if (!x0_given) orc_spmv_prec(n, S->mrp, S->mci, muf, ORC_FP32, b, x);
+    /* x is held in the working precision u */
+    for (int t = 0; t < n; ++t) x[t] = rf(x[t], uw);
     double anorm = orc_norm_inf(n, S->arp, S->av);
     double bnorm = vnorm_inf(n, b);
     double dprev = INFINITY;
     int steps = 0;
     *stop = 0;
     for (int i = 0; i < imax; ++i) {
-        orc_residual_dd(n, S->arp, S->aci, S->av, x, b, r);
+        /* r = b - A x in u_r, stored in u */
+        if (ur_dd)
+            orc_residual_dd(n, S->arp, S->aci, S->av, x, b, r);
+        else
+            orc_residual_fp64(n, S->arp, S->aci, S->av, x, b, r);
+        for (int t = 0; t < n; ++t) r[t] = rf(r[t], uw);
         double e = vnorm_inf(n, r) / (anorm * vnorm_inf(n, x) + bnorm);
         nbe[i] = e;
         if (e <= u_work) { *stop = 1; its[i] = 0; dx[i] = 0.0; break; }
         int k = 0;
         orc_gmres(S, r, ug, up, tau, kmax, d, &k, NULL);
         its[i] = k;
-        for (int t = 0; t < n; ++t) x[t] = x[t] + d[t];
+        /* x = x + d in u, the correction first stored in u */
+        for (int t = 0; t < n; ++t) {
+            d[t] = rf(d[t], uw);
+            x[t] = rf(x[t] + d[t], uw);
+        }
         steps = i + 1;
         double dn = vnorm_inf(n, d), xn = vnorm_inf(n, x);
         dx[i] = xn > 0.0 ? dn / xn : dn;

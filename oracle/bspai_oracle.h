@@ -38,6 +38,10 @@ int  orc_get_threads(void);
 void orc_residual_dd(int n, const int* rp, const int* ci, const double* av,
                      const double* x, const double* b, double* r);
 
+/* Residual in plain fp64 (u_r = double): every product and difference rounded. */
+void orc_residual_fp64(int n, const int* rp, const int* ci, const double* av,
+                       const double* x, const double* b, double* r);
+
 /* Dense Householder least squares min ||b - A x||_2, A m-by-k column-major (m >= k).
  * Returns 0, or 1 if a diagonal of R is <= rank_tol.  resid = ||A x - b||_2. */
 int orc_householder_ls(int m, int k, const double* A, const double* b, double rank_tol,
@@ -115,16 +119,18 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
               double* d, int* iters, double* relres);
 
 /* BSPAI-GMRES-IR driver (Alg 3.1 after the SPAI build).
- *   x0 = M b with the unbucketed M (values muf, fp32 arithmetic) unless x0_given;
- *   loop i < imax: r = b - A x with u_r ~ u^2 (Dot2); nbe = ||r||_inf /
- *   (||A||_inf ||x||_inf + ||b||_inf); stop if nbe <= u_work; d = GMRES; x += d
- *   in fp64; stop if ||d||_inf <= u_work ||x||_inf, or if ||d_i|| > 0.9 ||d_{i-1}||.
+ *   x0 = M b with the unbucketed M (values muf, fp32 arithmetic) unless x0_given,
+ *   rounded to the working precision u (format uw: ORC_FP64 or ORC_FP32);
+ *   loop i < imax: r = b - A x in u_r (ur_dd = 1: Dot2, u_r ~ u^2; 0: plain
+ *   fp64), rounded to u; nbe = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf);
+ *   stop if nbe <= u_work; d = GMRES, rounded to u; x = fl_u(x + d); stop if
+ *   ||d||_inf <= u_work ||x||_inf, or if ||d_i|| > 0.9 ||d_{i-1}||.
  * its[i] = GMRES iterations of step i; nbe[i], dx[i] histories; returns the
  * number of refinement steps taken.  *stop = 1 (nbe), 2 (dx), 3 (stagnation),
  * 0 (imax). */
 int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
                  int ug, int up, double tau, int kmax, int imax, double u_work,
-                 int x0_given, double* x, int* its, double* nbe, double* dx, int* stop);
+                 int uw, int ur_dd, int x0_given, double* x, int* its, double* nbe, double* dx, int* stop);
 
 #ifdef __cplusplus
 }

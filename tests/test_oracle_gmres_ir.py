@@ -206,3 +206,59 @@ def test_ir_with_bucketed_A_reaches_forward_error_1e10(orc, name, grid):
         out = orc.solve(wl, bucket_eps=eps, bucket_A=True)
         xt = wl["x_true"]
         assert np.abs(out["x"] - xt).max() / np.abs(xt).max() <= 1e-10
+
+
+SSD = dict(precs=["fp32", "fp16", "drop"], u="fp32", u_r="fp64", ug="fp32", up="fp32", tau=1e-4)
+
+
+@pytest.mark.parametrize("name,grid", [("convdiff2d", 32), ("convdiff3d", 8)])
+@pytest.mark.parametrize("eps", [2.0 ** -24, 2.0 ** -18])
+def test_ir_single_single_double_reaches_single_accuracy(orc, name, grid, eps):
+    """(u_f, u, u_r) = (single, single, double) with buckets {single, half, drop}
+    (Section 4, Table 4 setting): x is held in fp32 and the forward error
+    reaches the level of u = 2^-24 (u_r = u^2 makes cond(A, x) u_r negligible
+    for these systems, so the limiting accuracy is u itself)."""
+    wl = W.workload(name, grid=grid)
+    out = orc.solve(wl, bucket_eps=eps, **SSD)
+    x, xt = out["x"], wl["x_true"]
+    assert np.array_equal(x, x.astype(np.float32).astype(np.float64))
+    assert np.abs(x - xt).max() / np.abs(xt).max() <= 2 * 2.0 ** -24
+    assert out["stop"] in (1, 2, 3)
+    if out["stop"] == 1:
+        assert out["nbe"][-1] <= 2.0 ** -24
+    # a half bucket that holds entries at the larger epsilon
+    if eps == 2.0 ** -18 and name == "convdiff3d":
+        assert out["buckets"]["nnz_k"][1] > 0
+
+
+def test_ir_single_working_precision_step_follows_alg31(orc):
+    """One refinement step with u = fp32, u_r = fp64 equals Alg 3.1's steps
+    taken one at a time: x0 = M b in u_f, stored in u; r = b - A x0 in u_r,
+    stored in u; d from GMRES, stored in u; x1 = x0 + d in u."""
+    wl = W.workload("convdiff3d", grid=8)
+    A, P = wl["A"], wl["pattern"]
+    sp_ = orc.spai(A, P, wl["spai_eps"])
+    muf = orc.round_to(sp_["mval"], "fp32")
+    fm = SSD["precs"]
+    ids = orc.bucket_ids(P.row_ptr, muf, 2.0 ** -18, fm)["ids"]
+    stored, _, _ = orc.bucket_store(P.row_ptr, P.col, muf, ids, fm)
+    S = orc.System(A, P.row_ptr, P.col, stored, ids, fm)
+    out = orc.gmres_ir(S, muf, wl["b"], "fp32", "fp32", 1e-4, 500, 1, u="fp32", u_r="fp64")
+    r32 = lambda v: orc.round_to(v, "fp32")  # noqa: E731
+    x0 = r32(orc.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"]))
+    r = r32(orc.residual_fp64(A, x0, wl["b"]))
+    d, its, _ = orc.gmres(S, r, "fp32", "fp32", 1e-4, 500)
+    x1 = r32(x0 + r32(d))
+    assert out["its"] == [its]
+    assert np.array_equal(out["x"], x1)
+    # and u = fp64 keeps the Dot2 residual and the unrounded update
+    out64 = orc.gmres_ir(S, muf, wl["b"], "fp32", "fp32", 1e-4, 500, 1)
+    x0 = orc.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"])
+    d, _, _ = orc.gmres(S, orc.residual_dd(A, x0, wl["b"]), "fp32", "fp32", 1e-4, 500)
+    assert np.array_equal(out64["x"], x0 + d)
+
+
+def test_gmres_ir_rejects_unknown_working_precision(orc):
+    wl = W.workload("convdiff2d", grid=6)
+    with pytest.raises(ValueError):
+        orc.solve(wl, u="fp16")

@@ -48,3 +48,34 @@ def test_residual_dd_beats_fp64_on_cancellation(orc):
     b = np.array([0.0])
     r = orc.residual_dd(A, x, b)
     assert r[0] == -1.0  # exact: 0 - (1e16 + 1 - 1e16) = -1
+
+
+def test_residual_fp64_textbook_bound_and_exact_integers(orc):
+    """u_r = double: the plain recurrence obeys |r - exact| <= gamma_(p) (|b| +
+    |A||x|) (Higham, Thm 3.5 read for b - sum a x), and is exact on small
+    integer data (every intermediate is an integer below 2^53)."""
+    rng = np.random.default_rng(9)
+    for trial in range(4):
+        A = W.random_sparse(40, 6, sigma=3.0, delta=0.5, seed=200 + trial)
+        x = rng.uniform(-1, 1, A.n) * np.exp(rng.normal(0, 4, A.n))
+        b = (A.to_scipy() @ x) * (1 + rng.normal(0, 1e-10, A.n))
+        r = orc.residual_fp64(A, x, b)
+        rex = _exact_residual(A, x, b)
+        absax = abs(A.to_scipy()) @ np.abs(x) + np.abs(b)
+        u = Fraction(1, 2 ** 53)
+        worst = 0.0
+        for i in range(A.n):
+            p = int(A.row_ptr[i + 1] - A.row_ptr[i])
+            gam = p * u / (1 - p * u)
+            err = abs(Fraction(r[i]) - rex[i])
+            assert err <= gam * Fraction(absax[i] * (1 + 2.0 ** -50)), (trial, i)
+            worst = max(worst, float(err / Fraction(absax[i])))
+        # the Dot2 residual is far more accurate on the same data
+        rdd = orc.residual_dd(A, x, b)
+        assert max(abs(Fraction(rdd[i]) - rex[i]) / Fraction(absax[i]) for i in range(A.n)) <= worst
+    A = W.random_sparse(30, 5, sigma=1.0, delta=0.5, seed=9)
+    Ai = W.CSR(A.n, A.row_ptr, A.col, np.round(A.val * 8))
+    xi = rng.integers(-50, 50, A.n).astype(float)
+    bi = rng.integers(-1000, 1000, A.n).astype(float)
+    r = orc.residual_fp64(Ai, xi, bi)
+    assert [Fraction(v) for v in r] == _exact_residual(Ai, xi, bi)
