@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparator", action="store_true")
     p.add_argument("--no-bucketed-A", action="store_true")
+    p.add_argument("--no-single", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--kmax", type=int, default=0, help="cap on GMRES steps per refinement step (0: library default)")
     p.add_argument("--no-batch", action="store_true", help="skip the 512-system x 32-RHS batched measurement")
@@ -501,6 +502,38 @@ def main():
                              "A_bucket_nnz": ainfo["nnz_k"], "A_storage_pct": ainfo["storage_pct"],
                              "profile_ms": {c: aprof[c][0] for c in aprof}}
         Ah.free()
+
+    # ---------------- (u_f, u, u_r) = (single, single, double), buckets {fp32, fp16, drop} (Section 4)
+    if not args.no_single:
+        sres = []
+        for eps in (2.0 ** -24, 2.0 ** -18):
+            def step_s(x):
+                M, _ = B.bspai_build(Ad, Pd, wl["spai_eps"])
+                BM, sinfo = B.bspai_bucket(M, eps, ["fp32", "fp16", "drop"])
+                inf = B.gmres_ir_solve(Ad, bd, BM, M, x, u="fp32", u_r="fp64", u_g="fp32", u_p="fp32", tol=1e-4,
+                                       o=B.opts(tau=1e-4, kmax=args.kmax))
+                M.free()
+                BM.free()
+                return inf, sinfo
+
+            xs1 = torch.empty(n, dtype=torch.float64, device="cuda")
+            step_s(xs1)
+            barrier()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            sinf, sinfo = step_s(xs1)
+            s1.record(stream)
+            barrier()
+            sms_ = s0.elapsed_time(s1)
+            sfe = float(((xs1 - xt).abs().max() / xt.abs().max()).item())
+            good = sfe <= 4 * 2.0 ** -24 and sinf["status"] == 0
+            sres.append({"bucket_eps": eps, "solves_per_s": (1.0 if good else 0.0) / (sms_ / 1000.0),
+                         "ms_per_solve": sms_, "gmres_iters": sinf["gmres_iters"], "fwd_err": sfe,
+                         "bucket_nnz": sinfo["nnz_k"], "storage_pct_of_fp32": sinfo["storage_pct"]})
+        out["single_single_double"] = {"what": "u_f = u = fp32, u_r = fp64, u_g = u_p = fp32, tau = 1e-4, "
+                                               "buckets {fp32, fp16, drop}; solves reaching forward error <= 4u = 2^-22",
+                                       "runs": sres}
 
     # ---------------- end to end through the API with host buffers
     if not args.no_e2e:

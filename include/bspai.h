@@ -167,6 +167,15 @@ int bspai_matrix_create(const bspai_csr_t* A, bspai_stream_t s, bspai_A_h* out);
  * fp64 (Alg 3.1, residual line).  x, b, r: device fp64 vectors of length n. */
 int bspai_residual(bspai_A_h A, const double* x, const double* b, double* r, bspai_stream_t s);
 
+/* r = b - A x computed in u_r and stored in the working precision u (Alg 3.1
+ * residual line; Section 4's (single, single, double) setting has u_r = FP64,
+ * u = FP32).  u_r: BSPAI_DD (as bspai_residual) or BSPAI_FP64 (every product
+ * and difference rounded to fp64, ascending column order); u: BSPAI_FP64 or
+ * BSPAI_FP32 (r rounded to fp32, held in the fp64 buffer).  x, b, r: device
+ * fp64, length n.  Other precisions: BSPAI_ERR_UNSUPPORTED. */
+int bspai_residual_prec(bspai_A_h A, const double* x, const double* b, bspai_prec_t u_r, bspai_prec_t u, double* r,
+                        bspai_stream_t s);
+
 /* w = A v with A rounded to u_p = fp32 and fp32 products and sums (Alg 3.1,
  * GMRES line: "A computed in precision u_p").  v, w: device fp32, length n. */
 int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s);
@@ -305,10 +314,14 @@ int bspai_gmres_noalloc(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_
 
 /* BSPAI-GMRES-IR (Alg 3.1 after the SPAI build): x0 = M b in u_f (unless
  * opts->x0_given), then up to i_max steps of r = b - A x in u_r, GMRES on
- * (M A) d = M r with tolerance tol, x = x + d in u.  Supported: u = FP64,
- * u_r in {DD, FP64}, u_g and u_p in {FP32, FP64}.  A: caller CSR (device);
- * b: device fp64; x: device fp64, in/out; M: the unbucketed M for x0 (may be
- * NULL when x0_given).  Stopping: nbe <= u_stop, ||d||_inf <= u_stop
+ * (M A) d = M r with tolerance tol, x = x + d in u.  Supported: u in {FP64,
+ * FP32}, u_r in {DD, FP64}, u_g and u_p in {FP32, FP64}.  With u = FP32 (the
+ * (single, single, double) setting of Section 4) x, r and d are held in fp32
+ * (values rounded to fp32 inside the fp64 buffers): x0 (also a given one) is
+ * rounded to fp32, r is rounded after its computation in u_r, d is rounded and
+ * x = fl32(x + d); u_stop defaults to 2^-24 instead of 2^-53.  A: caller CSR
+ * (device); b: device fp64; x: device fp64, in/out; M: the unbucketed M for x0
+ * (may be NULL when x0_given).  Stopping: nbe <= u_stop, ||d||_inf <= u_stop
  * ||x||_inf, or stagnation.  Returns BSPAI_OK on one of those, else
  * BSPAI_NOT_CONVERGED / BSPAI_NONFINITE / BSPAI_TIMEOUT. */
 int gmres_ir_solve(const bspai_csr_t* A, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,

@@ -99,6 +99,7 @@ _sig("bspai_profile_enable", _i, [_i])
 _sig("bspai_profile_read", _i, [C.POINTER(Profile), _i])
 _sig("bspai_matrix_create", _i, [C.POINTER(CsrT), _vp, C.POINTER(_vp)])
 _sig("bspai_residual", _i, [_vp, _vp, _vp, _vp, _vp])
+_sig("bspai_residual_prec", _i, [_vp, _vp, _vp, _i, _i, _vp, _vp])
 _sig("bspai_spmv_up", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_build", _i, [C.POINTER(CsrT), C.POINTER(CsrT), _d, _i, _vp, C.POINTER(_vp), C.POINTER(BuildInfo)])
 _sig("bspai_M_export", _i, [_vp, _vp, _vp, _vp, _vp, _vp])
@@ -253,6 +254,12 @@ def matrix_create(A: DeviceCSR, stream=None) -> AHandle:
 
 def residual(Ah: AHandle, x, b, r, stream=None):
     _check(_lib.bspai_residual(Ah.ptr, _ptr(x), _ptr(b), _ptr(r), _stream(stream)))
+    return r
+
+
+def residual_prec(Ah: AHandle, x, b, r, u_r="dd", u="fp64", stream=None):
+    """r = b - A x computed in u_r ("dd" or "fp64") and stored in u ("fp64" or "fp32")."""
+    _check(_lib.bspai_residual_prec(Ah.ptr, _ptr(x), _ptr(b), PREC[u_r], PREC[u], _ptr(r), _stream(stream)))
     return r
 
 

@@ -490,7 +490,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, int64_t ldv, int n,
                                                       const GmresState* st, const double* __restrict__ y,
                                                       double* __restrict__ x, double* __restrict__ dout,
-                                                      double* __restrict__ norms) {
+                                                      double* __restrict__ norms, int u32) {
     extern __shared__ unsigned char sraw[];
     T* sy = reinterpret_cast<T*>(sraw);
     const int k = st->j;
@@ -501,11 +501,15 @@ __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, i
     if (r < n) {
         T acc = T(0);
         for (int jj = 0; jj < k; ++jj) acc = Ar<T>::add(acc, Ar<T>::mul(V[(int64_t)jj * ldv + r], sy[jj]));
-        const double d = (double)acc;
+        double d = (double)acc;
+        // working precision u = fp32: d stored in u, x = fl32(x + d) (x and d
+        // are fp32 values, so the fp64 sum rounds to the correctly rounded fp32 sum)
+        if (u32) d = (double)__double2float_rn(d);
         if (dout) dout[r] = d;
         double xn = 0.0;
         if (x) {
             xn = __dadd_rn(x[r], d);
+            if (u32) xn = (double)__double2float_rn(xn);
             x[r] = xn;
         }
         dabs = fabs(d);
@@ -553,6 +557,7 @@ struct GmresWork {
     HostFlags* hflags = nullptr;  // pinned
     unsigned long long tmo_ns = 2000000000ull;
     const bspai_bucketed* BA = nullptr;  // bucketed A for A v (null: A in u_p)
+    int u32 = 0;                         // working precision u = fp32: d and x rounded to fp32
     void* res_fn = nullptr;  // k_mgs_res instance, or null for k_mgs
     int res_bd = 1024;       // its block size
     int Gr = 0;              // its grid: one block of 1024 threads per SM
@@ -749,7 +754,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
         CUDA_LAUNCH_CHECK();
         if (n > 0) {
             k_gmres_update<T><<<(unsigned)ceil_div(n, 256), 256, sizeof(T) * (size_t)(W.kmax + 1), s>>>(
-                V, W.ldv, n, W.st, W.y, x, dout, W.norms);
+                V, W.ldv, n, W.st, W.y, x, dout, W.norms, W.u32);
             note_launch();
             CUDA_LAUNCH_CHECK();
         }
@@ -777,7 +782,8 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
 }
 
 static int check_solver_precs(int u, int u_r, int u_g, int u_p) {
-    if (u != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "working precision u must be FP64");
+    if (u != BSPAI_FP64 && u != BSPAI_FP32)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "working precision u must be FP64 or FP32");
     if (u_r != BSPAI_DD && u_r != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_r must be DD or FP64");
     if (u_g != BSPAI_FP32 && u_g != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_g must be FP32 or FP64");
     if (u_p != BSPAI_FP32 && u_p != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_p must be FP32 or FP64");
@@ -794,11 +800,16 @@ static int resolve_kmax(const bspai_opts_t* o, int n) {
 }
 
 int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
-                         int u_r, cudaStream_t s);
+                         int u_r, int u, cudaStream_t s);
+
+__global__ void k_round_f32(int n, double* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (double)__double2float_rn(x[i]);
+}
 
 static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, const bspai_bucketed* BM,
-                    const bspai_spai* M, int u_r, int u_g, int u_p, double tol, const bspai_opts_t* opts, double* x,
-                    cudaStream_t s, bspai_solve_info_t* info) {
+                    const bspai_spai* M, int u, int u_r, int u_g, int u_p, double tol, const bspai_opts_t* opts,
+                    double* x, cudaStream_t s, bspai_solve_info_t* info) {
     bspai_opts_t o;
     bspai_opts_default(&o);
     if (opts) o = *opts;
@@ -806,7 +817,7 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
     const int kmax = resolve_kmax(&o, n);
     int imax = o.i_max > 0 ? o.i_max : 10;
     if (imax > 32) imax = 32;
-    const double ustop = o.u_stop > 0 ? o.u_stop : 0x1p-53;
+    const double ustop = o.u_stop > 0 ? o.u_stop : (u == BSPAI_FP32 ? 0x1p-24 : 0x1p-53);
     const double stag = o.stagnation > 0 ? o.stagnation : 0.9;
     const double tau = tol > 0 ? tol : o.tau;
     bspai_solve_info_t inf;
@@ -833,6 +844,7 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
     if ((rc = dalloc_t(&nrm, 4, s))) return finish(rc);
     if ((rc = W.alloc(n, kmax, u_g, u_p, o.barrier_timeout_s, o.max_blocks, s))) return finish(rc);
     W.BA = BA;
+    W.u32 = u == BSPAI_FP32;
     // ||A||_inf, ||b||_inf
     double anorm = 0.0, bnorm = 0.0;
     {
@@ -845,6 +857,10 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
             // x0 = M b with the unbucketed M in u_f = fp32, stored in fp64
             if ((rc = launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), b, BSPAI_FP64, x, BSPAI_FP64, s)))
                 return finish(rc);
+        } else if (W.u32) {
+            // a given x0 is held in u = fp32 (M b in u_f = fp32 already is)
+            k_round_f32<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, x);
+            note_launch();
         }
     }
     cudaError_t e = cudaMemcpyAsync(&bnorm, nrm, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -857,7 +873,7 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
         double hn[2] = {0, 0};
         e = cudaMemsetAsync(nrm, 0, 2 * sizeof(double), s);
         if (e) return finish(cuda_error(e, "memset", __FILE__, __LINE__));
-        if ((rc = launch_residual_prec(A, x, b, r, nrm, u_r, s))) return finish(rc);
+        if ((rc = launch_residual_prec(A, x, b, r, nrm, u_r, u, s))) return finish(rc);
         e = cudaMemcpyAsync(hn, nrm, sizeof hn, cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
         if (e) return finish(cuda_error(e, "residual norms", __FILE__, __LINE__));
@@ -967,7 +983,7 @@ int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h BM, bspai_M_h M, b
     if (M && M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: bad M handle");
     if (A->n > 0 && (!b || !x)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve: null vector");
     BSPAI_TRY(check_solver_precs(u, u_r, u_g, u_p));
-    return ir_solve(A, nullptr, b, BM, M, u_r, u_g, u_p, tol, opts, x, (cudaStream_t)s, info);
+    return ir_solve(A, nullptr, b, BM, M, u, u_r, u_g, u_p, tol, opts, x, (cudaStream_t)s, info);
 }
 
 int gmres_ir_solve_hb(bspai_A_h A, bspai_BM_h A_bucketed, const double* b, bspai_BM_h BM, bspai_M_h M,
@@ -980,7 +996,7 @@ int gmres_ir_solve_hb(bspai_A_h A, bspai_BM_h A_bucketed, const double* b, bspai
     if (M && M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: bad M handle");
     if (A->n > 0 && (!b || !x)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_hb: null vector");
     BSPAI_TRY(check_solver_precs(u, u_r, u_g, u_g));
-    return ir_solve(A, A_bucketed, b, BM, M, u_r, u_g, u_g, tol, opts, x, (cudaStream_t)s, info);
+    return ir_solve(A, A_bucketed, b, BM, M, u, u_r, u_g, u_g, tol, opts, x, (cudaStream_t)s, info);
 }
 
 int gmres_ir_solve(const bspai_csr_t* Acsr, const double* b, bspai_BM_h BM, bspai_M_h M, bspai_prec_t u,

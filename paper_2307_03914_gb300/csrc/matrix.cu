@@ -138,8 +138,9 @@ __device__ __forceinline__ void dot2_sub(double& p, double& s, double ph, double
 
 // r = b - A x, each product split exactly by an FMA and the terms summed by
 // Dot2 in ascending column order (DD = true: u_r ~ u^2; DD = false is the
-// plain fp64 recurrence); also max|r| and max|x| over rows.
-template <bool DD>
+// plain fp64 recurrence), stored in the working precision (U32: rounded to
+// fp32); also max|r| (of the stored r) and max|x| over rows.
+template <bool DD, bool U32>
 __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __restrict__ sptr,
                                                      const int32_t* __restrict__ col,
                                                      const double* __restrict__ val,
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __res
                 hi = __dsub_rn(hi, ph);
             }
         }
-        const double ri = __dadd_rn(hi, lo);
+        double ri = __dadd_rn(hi, lo);
+        if (U32) ri = (double)__double2float_rn(ri);
         r[i] = ri;
         rabs = fabs(ri);
         xabs = fabs(x[i]);
@@ -239,14 +241,23 @@ int launch_residual_batch(const bspai_matrix* A, int nrhs, const double* X, cons
 }
 
 int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
-                         int u_r, cudaStream_t s) {
+                         int u_r, int u, cudaStream_t s) {
     if (A->n == 0) return BSPAI_OK;
     ProfScope ps(BSPAI_K_RESIDUAL, s);
     const unsigned grid = (unsigned)ceil_div(A->n, 256);
-    if (u_r == BSPAI_FP64)
-        k_residual_dd<false><<<grid, 256, 0, s>>>(A->n, A->sell.sptr, A->sell.col, A->val64, x, b, r, norms);
-    else
-        k_residual_dd<true><<<grid, 256, 0, s>>>(A->n, A->sell.sptr, A->sell.col, A->val64, x, b, r, norms);
+    const int64_t* sp = A->sell.sptr;
+    const int32_t* ci = A->sell.col;
+    if (u == BSPAI_FP32) {
+        if (u_r == BSPAI_FP64)
+            k_residual_dd<false, true><<<grid, 256, 0, s>>>(A->n, sp, ci, A->val64, x, b, r, norms);
+        else
+            k_residual_dd<true, true><<<grid, 256, 0, s>>>(A->n, sp, ci, A->val64, x, b, r, norms);
+    } else {
+        if (u_r == BSPAI_FP64)
+            k_residual_dd<false, false><<<grid, 256, 0, s>>>(A->n, sp, ci, A->val64, x, b, r, norms);
+        else
+            k_residual_dd<true, false><<<grid, 256, 0, s>>>(A->n, sp, ci, A->val64, x, b, r, norms);
+    }
     note_launch();
     CUDA_LAUNCH_CHECK();
     return BSPAI_OK;
@@ -254,7 +265,7 @@ int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b
 
 int launch_residual(const bspai_matrix* A, const double* x, const double* b, double* r, double* norms,
                     cudaStream_t s) {
-    return launch_residual_prec(A, x, b, r, norms, BSPAI_DD, s);
+    return launch_residual_prec(A, x, b, r, norms, BSPAI_DD, BSPAI_FP64, s);
 }
 
 // Structural check of a caller CSR before any kernel indexes through it:
@@ -363,6 +374,17 @@ int bspai_residual(bspai_A_h A, const double* x, const double* b, double* r, bsp
     if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_residual: bad handle");
     if (A->n > 0 && (!x || !b || !r)) return set_error(BSPAI_ERR_INVALID, "bspai_residual: null vector");
     return launch_residual(A, x, b, r, nullptr, (cudaStream_t)s);
+}
+
+int bspai_residual_prec(bspai_A_h A, const double* x, const double* b, bspai_prec_t u_r, bspai_prec_t u, double* r,
+                        bspai_stream_t s) {
+    if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_residual_prec: bad handle");
+    if (u_r != BSPAI_DD && u_r != BSPAI_FP64)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_residual_prec: u_r must be DD or FP64");
+    if (u != BSPAI_FP64 && u != BSPAI_FP32)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_residual_prec: u must be FP64 or FP32");
+    if (A->n > 0 && (!x || !b || !r)) return set_error(BSPAI_ERR_INVALID, "bspai_residual_prec: null vector");
+    return launch_residual_prec(A, x, b, r, nullptr, u_r, u, (cudaStream_t)s);
 }
 
 }  // extern "C"
