@@ -85,6 +85,15 @@ def _declare(L):
     L.orc_spai.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, C.c_double, C.c_double,
                            C.c_int, C.c_int, _f64p, _f64p, _i32p, _i32p, _f64p]
     L.orc_spai.restype = C.c_int
+    L.orc_spai_adaptive.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, C.c_double, C.c_double,
+                                    C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _i32p, _f64p,
+                                    _i32p, _i8p, _f64p, _i32p, _i32p, _i32p, _i32p]
+    L.orc_spai_adaptive.restype = C.c_int
+    L.orc_spai_score.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, C.c_int, _i32p, C.c_int,
+                                 C.c_double, C.c_int, C.c_int, _f64p, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_int), _i32p, _f64p, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                 _i32p, C.POINTER(C.c_int)]
+    L.orc_spai_score.restype = C.c_int
     L.orc_norm_inf.argtypes = [C.c_int, _i32p, _f64p]
     L.orc_norm_inf.restype = C.c_double
     L.orc_bucket_ids.argtypes = [C.c_int, _i32p, _f64p, C.c_double, _i32p, C.c_int, _i8p,
@@ -195,6 +204,56 @@ def spai(A, P, spai_eps: float, u_f: float = 2.0 ** -24, cols=None) -> dict:
     nbad = lib().orc_spai(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _i32(P.row_ptr),
                           _i32(P.col), spai_eps, u_f, c0, c1, mval, resid, conv, rankdef, kappa)
     return dict(mval=mval, resid=resid, conv=conv, rankdef=rankdef, kappa=kappa, nbad=nbad)
+
+
+def spai_adaptive(A, spai_eps: float, alpha: int, beta: int = 8, u_f: float = 2.0 ** -24,
+                  imax_rows: int = 256, cap=None, cols=None) -> dict:
+    """Adaptive SPAI (Alg 2.1, alpha > 0, Grote-Huckle growth) on A^T D from
+    the identity pattern; M = M'^T D as CSR (row k = the final pattern J_k of
+    column k of M').  Pinned by dense least squares on the pattern it returns,
+    the 1-D minimisation behind rho (Section 2.2), the selection rule, the
+    monotone residual, and M = A^-1 once the pattern fills a small matrix."""
+    n = A.n
+    cap = 1 + alpha * beta if cap is None else cap
+    c0, c1 = (0, n) if cols is None else cols
+    trp, tci, _ = transpose_csr(A.row_ptr, A.col, np.ones(A.nnz))
+    Jo = np.full(n * cap, -1, dtype=np.int32)
+    mo = np.zeros(n * cap)
+    nJ = np.zeros(n, dtype=np.int32)
+    st = np.zeros(n * cap, dtype=np.int8)
+    resid = np.zeros(n)
+    conv = np.zeros(n, dtype=np.int32)
+    rankdef = np.zeros(n, dtype=np.int32)
+    nsolves = np.zeros(n, dtype=np.int32)
+    capped = np.zeros(n, dtype=np.int32)
+    nbad = lib().orc_spai_adaptive(n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _i32(trp), _i32(tci), spai_eps,
+                                   u_f, int(alpha), int(beta), int(imax_rows), c0, c1, int(cap), Jo, mo, nJ, st,
+                                   resid, conv, rankdef, nsolves, capped)
+    rows = np.arange(c0, c1)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(nJ)
+    sel = (np.arange(cap)[None, :] < nJ[:, None]).ravel()
+    return dict(row_ptr=row_ptr.astype(np.int32), col=Jo[sel], mval=mo[sel], step_added=st[sel], nJ=nJ,
+                resid=resid, conv=conv, rankdef=rankdef, nsolves=nsolves, capped=capped, nbad=nbad, rows=rows)
+
+
+def spai_score(A, k: int, J, beta: int = 8, u_f: float = 2.0 ** -24) -> dict:
+    """One scoring pass of the adaptive SPAI for column k with pattern J."""
+    trp, tci, _ = transpose_csr(A.row_ptr, A.col, np.ones(A.nnz))
+    d = row_absmax_scale(A)
+    J = np.ascontiguousarray(np.sort(np.asarray(J)), dtype=np.int32)
+    room = int(np.diff(trp).sum()) + 1
+    mbar = np.zeros(max(len(J), 1))
+    cand = np.zeros(room, dtype=np.int32)
+    rho = np.zeros(room)
+    picks = np.zeros(max(beta, 1), dtype=np.int32)
+    sres, mean = C.c_double(0.0), C.c_double(0.0)
+    rd, nc, npk = C.c_int(0), C.c_int(0), C.c_int(0)
+    nI = lib().orc_spai_score(A.n, _i32(A.row_ptr), _i32(A.col), _f64(A.val), _i32(trp), _i32(tci), d, int(k), J,
+                              len(J), u_f, int(beta), 1, mbar, C.byref(sres), C.byref(rd), cand, rho, C.byref(nc),
+                              C.byref(mean), picks, C.byref(npk))
+    return dict(nI=nI, mbar=mbar[:len(J)], sres=sres.value, rd=rd.value, cand=cand[:nc.value], rho=rho[:nc.value],
+                mean=mean.value, picks=picks[:npk.value])
 
 
 # ------------------------------------------------------------- bucketing (O5)

@@ -331,6 +331,242 @@ int orc_spai(int n, const int* arp, const int* aci, const double* av,
     return nbad;
 }
 
+/* ------------------------------------------------------- adaptive SPAI (f1) */
+
+/* One pass of Alg 2.1's inner loop for column k of M' (SPAI on B = A^T D),
+ * with the current pattern J (nJ indices, ascending):
+ *   I      = shadow of J: the union of the columns of rows J of A (ascending);
+ *   Abar   = B(I, J), ebar = e_k(I); mbar from Householder least squares;
+ *   sbar   = Abar mbar - ebar (explicit, fp64), sres = ||sbar||_2;
+ *   L      = I u {k}; Jt = (union over l in L of N_l) \ J, where N_l = {j :
+ *            b_lj != 0} = the rows of A with an entry in column l (row l of
+ *            A^T, given as trp/tci), ascending;
+ *   rho_j  = sqrt(||sbar||^2 - (sbar^T B(I, j))^2 / ||B e_j||^2) for j in Jt,
+ *            the residual norm after the best update along e_j alone;
+ *   mean   = the arithmetic mean of rho over Jt;
+ *   picks  = the up to beta indices of smallest rho (ties: smaller j) among
+ *            those with rho_j <= mean.
+ * The candidate part is skipped (ncand = npick = 0) when want_cand is 0.
+ * cand/rho need room for every candidate (the caller sizes them by the
+ * gathered count), picks for beta.  Returns the shadow size nI; *rd is the
+ * rank flag (|R_jj| <= |I| u_f ||Abar||_F or |I| < |J|), in which case mbar = 0
+ * and sres = 1. */
+static int cmp_rho(const void* a, const void* b) {
+    const double* x = (const double*)a;
+    const double* y = (const double*)b;
+    if (x[0] < y[0]) return -1;
+    if (x[0] > y[0]) return 1;
+    return (x[1] > y[1]) - (x[1] < y[1]);
+}
+
+static int shadow_of(const int* arp, const int* aci, const int* J, int nJ, int* I) {
+    int c = 0;
+    for (int q = 0; q < nJ; ++q)
+        for (int p = arp[J[q]]; p < arp[J[q] + 1]; ++p) I[c++] = aci[p];
+    qsort(I, (size_t)c, sizeof(int), cmp_int);
+    int nI = 0;
+    for (int t = 0; t < c; ++t)
+        if (nI == 0 || I[nI - 1] != I[t]) I[nI++] = I[t];
+    return nI;
+}
+
+int orc_spai_score(int n, const int* arp, const int* aci, const double* av, const int* trp,
+                   const int* tci, const double* d, int k, const int* J, int nJ, double u_f,
+                   int beta, int want_cand, double* mbar, double* sres, int* rd, int* cand,
+                   double* rho, int* ncand, double* mean, int* picks, int* npick) {
+    (void)n;
+    int gathered = 0;
+    for (int q = 0; q < nJ; ++q) gathered += arp[J[q] + 1] - arp[J[q]];
+    int* I = (int*)malloc(sizeof(int) * (size_t)(gathered > 0 ? gathered : 1));
+    const int nI = shadow_of(arp, aci, J, nJ, I);
+    double* Ab = (double*)calloc((size_t)nI * (size_t)(nJ > 0 ? nJ : 1) + 1, sizeof(double));
+    double* e = (double*)calloc((size_t)nI + 1, sizeof(double));
+    double* sb = (double*)calloc((size_t)nI + 1, sizeof(double));
+    for (int q = 0; q < nJ; ++q) {
+        const int j = J[q];
+        for (int p = arp[j]; p < arp[j + 1]; ++p) {
+            const int* hit = (const int*)bsearch(&aci[p], I, (size_t)nI, sizeof(int), cmp_int);
+            Ab[(size_t)q * nI + (size_t)(hit - I)] = av[p] * d[j];
+        }
+    }
+    int pk = -1;
+    for (int t = 0; t < nI; ++t)
+        if (I[t] == k) { e[t] = 1.0; pk = t; }
+    double fro = 0.0;
+    for (size_t t = 0; t < (size_t)nI * (size_t)nJ; ++t) fro += Ab[t] * Ab[t];
+    fro = sqrt(fro);
+    double res = 1.0;
+    *rd = 0;
+    if (nJ == 0 || nI < nJ) {
+        *rd = 1;
+    } else {
+        *rd = orc_householder_ls(nI, nJ, Ab, e, (double)nI * u_f * fro, mbar, &res);
+    }
+    if (*rd) {
+        for (int q = 0; q < nJ; ++q) mbar[q] = 0.0;
+        *sres = 1.0;
+        *ncand = 0;
+        *npick = 0;
+        *mean = 0.0;
+        free(I); free(Ab); free(e); free(sb);
+        return nI;
+    }
+    /* sbar = Abar mbar - ebar, and its norm */
+    double s2 = 0.0;
+    for (int t = 0; t < nI; ++t) {
+        double acc = -e[t];
+        for (int q = 0; q < nJ; ++q) acc += Ab[(size_t)q * nI + t] * mbar[q];
+        sb[t] = acc;
+        s2 += acc * acc;
+    }
+    *sres = sqrt(s2);
+    *ncand = 0;
+    *npick = 0;
+    *mean = 0.0;
+    if (want_cand) {
+        /* L = I u {k} */
+        int nL = nI + (pk < 0 ? 1 : 0);
+        int raw = 0;
+        for (int t = 0; t < nL; ++t) {
+            const int l = t < nI ? I[t] : k;
+            raw += trp[l + 1] - trp[l];
+        }
+        int* C = (int*)malloc(sizeof(int) * (size_t)(raw > 0 ? raw : 1));
+        int c = 0;
+        for (int t = 0; t < nL; ++t) {
+            const int l = t < nI ? I[t] : k;
+            for (int p = trp[l]; p < trp[l + 1]; ++p) C[c++] = tci[p];
+        }
+        qsort(C, (size_t)c, sizeof(int), cmp_int);
+        int nc = 0;
+        for (int t = 0; t < c; ++t) {
+            if (t > 0 && C[t] == C[t - 1]) continue;
+            if (bsearch(&C[t], J, (size_t)nJ, sizeof(int), cmp_int)) continue;
+            cand[nc++] = C[t];
+        }
+        double rsum = 0.0;
+        for (int t = 0; t < nc; ++t) {
+            const int j = cand[t];
+            /* the residual of the univariate update m_k + mu e_j: the full
+               residual is sbar on I (zero elsewhere), so sbar^T B e_j runs over
+               the entries of column j of B (row j of A) that lie in I, and the
+               denominator is the whole column's ||B e_j||^2 */
+            double num = 0.0, den = 0.0;
+            for (int p = arp[j]; p < arp[j + 1]; ++p) {
+                const double bij = av[p] * d[j];
+                den += bij * bij;
+                const int* hit = (const int*)bsearch(&aci[p], I, (size_t)nI, sizeof(int), cmp_int);
+                if (hit) num += sb[hit - I] * bij;
+            }
+            double r2 = s2;
+            if (den > 0.0) r2 = s2 - num * num / den;
+            rho[t] = sqrt(r2 > 0.0 ? r2 : 0.0);
+            rsum += rho[t];
+        }
+        *ncand = nc;
+        if (nc > 0) {
+            *mean = rsum / nc;
+            double* pr = (double*)malloc(sizeof(double) * 2 * (size_t)nc);
+            for (int t = 0; t < nc; ++t) { pr[2 * t] = rho[t]; pr[2 * t + 1] = (double)cand[t]; }
+            qsort(pr, (size_t)nc, 2 * sizeof(double), cmp_rho);
+            int np = 0;
+            for (int t = 0; t < nc && np < beta; ++t)
+                if (pr[2 * t] <= *mean) picks[np++] = (int)pr[2 * t + 1];
+            *npick = np;
+            free(pr);
+        }
+        free(C);
+    }
+    free(I); free(Ab); free(e); free(sb);
+    return nI;
+}
+
+int orc_spai_adaptive(int n, const int* arp, const int* aci, const double* av, const int* trp,
+                      const int* tci, double spai_eps, double u_f, int alpha, int beta,
+                      int imax_rows, int col_begin, int col_end, int cap, int* Jout, double* mout,
+                      int* nJout, signed char* step_added, double* resid, int* conv, int* rankdef,
+                      int* nsolves, int* capped) {
+    double* d = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_row_absmax_scale(n, arp, av, d);
+    int nbad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : nbad)
+    for (int k = col_begin; k < col_end; ++k) {
+        int* J = (int*)malloc(sizeof(int) * (size_t)cap);
+        signed char* st = (signed char*)malloc((size_t)cap);
+        double* mb = (double*)malloc(sizeof(double) * (size_t)cap);
+        int* picks = (int*)malloc(sizeof(int) * (size_t)(beta > 0 ? beta : 1));
+        int nJ = 1;
+        J[0] = k;
+        st[0] = 0;
+        double sres = 1.0;
+        int rd = 0, solves = 0, cp = 0;
+        for (int step = 0; step <= alpha; ++step) {
+            /* room for every candidate: at most sum over l in I u {k} of |N_l|,
+               bounded by the entries of the rows of A^T over the gathered shadow */
+            int gathered = 0;
+            for (int q = 0; q < nJ; ++q) gathered += arp[J[q] + 1] - arp[J[q]];
+            int* Itmp = (int*)malloc(sizeof(int) * (size_t)(gathered > 0 ? gathered : 1));
+            const int nI0 = shadow_of(arp, aci, J, nJ, Itmp);
+            int raw = trp[k + 1] - trp[k];
+            for (int t = 0; t < nI0; ++t) raw += trp[Itmp[t] + 1] - trp[Itmp[t]];
+            free(Itmp);
+            int* cand = (int*)malloc(sizeof(int) * (size_t)(raw > 0 ? raw : 1));
+            double* rho = (double*)malloc(sizeof(double) * (size_t)(raw > 0 ? raw : 1));
+            int ncand = 0, npick = 0;
+            double mean = 0.0;
+            const int last = (step == alpha);
+            orc_spai_score(n, arp, aci, av, trp, tci, d, k, J, nJ, u_f, beta, !last, mb, &sres, &rd,
+                           cand, rho, &ncand, &mean, picks, &npick);
+            ++solves;
+            free(cand);
+            free(rho);
+            if (rd || sres <= spai_eps || last || npick == 0) break;
+            /* J u picks, ascending; a pattern whose shadow would exceed imax_rows
+               rows (or whose size would exceed cap) is not taken */
+            int* Jn = (int*)malloc(sizeof(int) * (size_t)(nJ + npick));
+            signed char* sn = (signed char*)malloc((size_t)(nJ + npick));
+            int a = 0, b = 0, c = 0;
+            int* pk2 = (int*)malloc(sizeof(int) * (size_t)npick);
+            memcpy(pk2, picks, sizeof(int) * (size_t)npick);
+            qsort(pk2, (size_t)npick, sizeof(int), cmp_int);
+            while (a < nJ || b < npick) {
+                if (b >= npick || (a < nJ && J[a] < pk2[b])) { Jn[c] = J[a]; sn[c++] = st[a++]; }
+                else { Jn[c] = pk2[b++]; sn[c++] = (signed char)(step + 1); }
+            }
+            int g2 = 0;
+            for (int q = 0; q < c; ++q) g2 += arp[Jn[q] + 1] - arp[Jn[q]];
+            int* I2 = (int*)malloc(sizeof(int) * (size_t)(g2 > 0 ? g2 : 1));
+            const int nI2 = shadow_of(arp, aci, Jn, c, I2);
+            free(I2);
+            free(pk2);
+            if (c > cap || nI2 > imax_rows) {
+                cp = 1;
+                free(Jn); free(sn);
+                break;
+            }
+            memcpy(J, Jn, sizeof(int) * (size_t)c);
+            memcpy(st, sn, (size_t)c);
+            nJ = c;
+            free(Jn); free(sn);
+        }
+        for (int q = 0; q < nJ; ++q) {
+            Jout[(size_t)k * cap + q] = J[q];
+            mout[(size_t)k * cap + q] = rd ? 0.0 : mb[q] * d[J[q]];
+            step_added[(size_t)k * cap + q] = st[q];
+        }
+        nJout[k] = nJ;
+        resid[k] = rd ? 1.0 : sres;
+        conv[k] = !rd && sres <= spai_eps;
+        rankdef[k] = rd;
+        nsolves[k] = solves;
+        capped[k] = cp;
+        nbad += rd;
+        free(J); free(st); free(mb); free(picks);
+    }
+    free(d);
+    return nbad;
+}
+
 /* ----------------------------------------------------------------- bucketing */
 
 double orc_norm_inf(int n, const int* rp, const double* val) {

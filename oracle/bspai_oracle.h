@@ -60,6 +60,32 @@ int orc_spai(int n, const int* arp, const int* aci, const double* av,
              int col_begin, int col_end,
              double* mval, double* resid, int* conv, int* rankdef, double* kappa);
 
+/* Adaptive SPAI (Alg 2.1 with alpha > 0; Grote and Huckle's pattern growth),
+ * run on B = A^T D from the identity pattern, M = M'^T D.  trp/tci: the CSR
+ * structure of A^T (row l lists the rows of A with an entry in column l).
+ * Per column k in [col_begin, col_end): up to alpha + 1 least-squares solves;
+ * after a solve the column stops when ||sbar||_2 <= spai_eps, after the last
+ * solve, when no index qualifies, or when J u picks would have a shadow of
+ * more than imax_rows rows or more than cap indices (capped[k] = 1).
+ * Outputs (cap slots per column): Jout (ascending), mout = M[k, J] = mbar d_J,
+ * step_added (0 for k, s for an index added after solve s), nJout, resid
+ * (||sbar||_2), conv, rankdef, nsolves, capped.  Returns the number of
+ * rank-deficient columns. */
+int orc_spai_adaptive(int n, const int* arp, const int* aci, const double* av, const int* trp,
+                      const int* tci, double spai_eps, double u_f, int alpha, int beta,
+                      int imax_rows, int col_begin, int col_end, int cap, int* Jout, double* mout,
+                      int* nJout, signed char* step_added, double* resid, int* conv, int* rankdef,
+                      int* nsolves, int* capped);
+
+/* One scoring pass of the adaptive SPAI for column k and pattern J (the step
+ * that orc_spai_adaptive repeats): mbar, ||sbar||, the candidate indices with
+ * their rho, the mean of rho and the picks.  d: the Section 4 scaling. */
+int orc_spai_score(int n, const int* arp, const int* aci, const double* av, const int* trp,
+                   const int* tci, const double* d, int k, const int* J, int nJ, double u_f,
+                   int beta, int want_cand, double* mbar, double* sres, int* rd, int* cand,
+                   double* rho, int* ncand, double* mean, int* picks, int* npick);
+
+
 /* ||M||_inf = max_i sum_j |m_ij| (sequential, ascending column). */
 double orc_norm_inf(int n, const int* rp, const double* val);
 
