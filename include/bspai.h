@@ -80,8 +80,11 @@ typedef struct {
     int32_t max_rows;          /* largest |I_k| (shadow size) */
     int32_t n_converged;       /* columns with ||sbar_k||_2 <= spai_eps (Alg 2.1 test) */
     int32_t n_rank_deficient;  /* columns whose block failed |R_jj| > |I| u_f ||Abar||_F */
-    int64_t nnz;               /* nnz(M) = nnz(pattern) */
+    int64_t nnz;               /* nnz(M) (= nnz(pattern) for the fixed pattern) */
     double max_resid;          /* max_k ||sbar_k||_2 */
+    int32_t n_capped;          /* adaptive build: columns whose growth stopped at imax_rows */
+    int32_t reserved;
+    int64_t total_solves;      /* least-squares solves over all columns (n for the fixed pattern) */
 } bspai_build_info_t;
 
 typedef struct {
@@ -181,6 +184,32 @@ int bspai_residual_prec(bspai_A_h A, const double* x, const double* b, bspai_pre
 int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s);
 
 /* ------------------------------------------------------------------ SPAI */
+/* Adaptive SPAI (Alg 2.1 with alpha > 0, Grote and Huckle's pattern growth)
+ * run on B = A^T D from the identity pattern (Section 4), in u_f = fp32,
+ * giving M = M'^T D.  Per column k, at most alpha + 1 passes of: shadow I_k,
+ * least squares on B(I_k, J_k) by Householder QR, sbar; stop when ||sbar||_2
+ * <= spai_eps or after the last pass; otherwise score every j in (union over
+ * l in I_k u {k} of the nonzero columns of row l of B) \ J_k by
+ * rho_j = (||sbar||^2 - (sbar^T B(I_k, j))^2 / ||B e_j||^2)^(1/2) and add
+ * the up to beta of smallest rho_j (ties: smaller j) among those with rho_j
+ * <= the mean rho.  A pass whose new pattern would have a shadow of more than
+ * imax_rows rows is not taken (the column keeps its solution; counted in
+ * info->n_capped).  imax_rows must be >= the longest row of A; the shared
+ * memory of one column grows with 1 + alpha beta and imax_rows, and a
+ * configuration that does not fit returns BSPAI_ERR_UNSUPPORTED.  0 <= alpha
+ * <= 16, 0 <= beta <= 32.  A: device CSR (fp64 values).  The returned M works
+ * wherever a fixed-pattern M does.  Returns BSPAI_RANK_DEFICIENT (M still
+ * created) if any block failed the rank test. */
+int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, int32_t beta, int32_t imax_rows,
+                         bspai_prec_t u_f, bspai_stream_t s, bspai_M_h* M_out, bspai_build_info_t* info);
+
+/* For an M from bspai_build_adaptive: per entry in CSR order, the pass that
+ * added it (0 for the diagonal start, s for an index chosen after pass s;
+ * int8, nnz(M)), and per column solves | converged << 8 | rank deficient << 9
+ * | capped << 10 (int32, n).  Device buffers; either may be NULL.  Other
+ * handles: BSPAI_ERR_UNSUPPORTED. */
+int bspai_M_adaptive_export(bspai_M_h M, int8_t* step_added, int32_t* col_info, bspai_stream_t s);
+
 /* Fixed-pattern SPAI (Alg 2.1 with alpha = 0; eq. redprob) run on B = A^T D,
  * D = diag(1 / max_i |a_ji|) (Section 4), in u_f = fp32, giving the left
  * preconditioner M = M'^T D (Alg 3.1, first line).  Row k of M has the

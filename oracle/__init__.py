@@ -237,10 +237,17 @@ def spai_adaptive(A, spai_eps: float, alpha: int, beta: int = 8, u_f: float = 2.
                 resid=resid, conv=conv, rankdef=rankdef, nsolves=nsolves, capped=capped, nbad=nbad, rows=rows)
 
 
+_SCORE_MEMO: dict = {}
+
+
 def spai_score(A, k: int, J, beta: int = 8, u_f: float = 2.0 ** -24) -> dict:
     """One scoring pass of the adaptive SPAI for column k with pattern J."""
-    trp, tci, _ = transpose_csr(A.row_ptr, A.col, np.ones(A.nnz))
-    d = row_absmax_scale(A)
+    key = (id(A), A.n, A.nnz)
+    if key not in _SCORE_MEMO:  # A^T's structure and the scaling, once per matrix
+        trp_, tci_, _ = transpose_csr(A.row_ptr, A.col, np.ones(A.nnz))
+        _SCORE_MEMO.clear()
+        _SCORE_MEMO[key] = (A, trp_, tci_, row_absmax_scale(A))
+    _, trp, tci, d = _SCORE_MEMO[key]
     J = np.ascontiguousarray(np.sort(np.asarray(J)), dtype=np.int32)
     room = int(np.diff(trp).sum()) + 1
     mbar = np.zeros(max(len(J), 1))
@@ -409,12 +416,18 @@ def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
 
 
 def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False, u="fp64",
-          u_r="dd", ug=None, up=None) -> dict:
+          u_r="dd", ug=None, up=None, adaptive=None) -> dict:
     """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR.
     bucket_A: A v inside GMRES by the bucketed SpMV on A's own buckets (same
-    precisions and bucket_eps, thresholds from ||A||_inf; eq. nbe2)."""
+    precisions and bucket_eps, thresholds from ||A||_inf; eq. nbe2).
+    adaptive: build M by the adaptive SPAI (spai_adaptive's keyword arguments)
+    instead of on the workload's fixed pattern."""
     A, P = wl["A"], wl["pattern"]
-    sp = spai(A, P, wl["spai_eps"])
+    if adaptive is None:
+        sp = spai(A, P, wl["spai_eps"])
+    else:  # adaptive: dict(spai_eps, alpha, beta[, imax_rows]) -- Alg 2.1 from the identity pattern
+        sp = spai_adaptive(A, **adaptive)
+        P = _Csr(A.n, sp["row_ptr"], sp["col"], None)
     muf = round_to(sp["mval"], "fp32")  # M is held in u_f = fp32
     precs = wl["precs"] if precs is None else precs
     be = wl["bucket_eps"] if bucket_eps is None else bucket_eps

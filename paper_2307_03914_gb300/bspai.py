@@ -45,7 +45,8 @@ class CsrT(C.Structure):
 class BuildInfo(C.Structure):
     _fields_ = [("n", C.c_int32), ("max_cols", C.c_int32), ("max_rows", C.c_int32),
                 ("n_converged", C.c_int32), ("n_rank_deficient", C.c_int32), ("nnz", C.c_int64),
-                ("max_resid", C.c_double)]
+                ("max_resid", C.c_double), ("n_capped", C.c_int32), ("reserved", C.c_int32),
+                ("total_solves", C.c_int64)]
 
 
 class BucketInfo(C.Structure):
@@ -103,6 +104,9 @@ _sig("bspai_residual_prec", _i, [_vp, _vp, _vp, _i, _i, _vp, _vp])
 _sig("bspai_spmv_up", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_build", _i, [C.POINTER(CsrT), C.POINTER(CsrT), _d, _i, _vp, C.POINTER(_vp), C.POINTER(BuildInfo)])
 _sig("bspai_M_export", _i, [_vp, _vp, _vp, _vp, _vp, _vp])
+_sig("bspai_build_adaptive", _i, [C.POINTER(CsrT), _d, C.c_int32, C.c_int32, C.c_int32, _i, _vp, C.POINTER(_vp),
+                                  C.POINTER(BuildInfo)])
+_sig("bspai_M_adaptive_export", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_M_create", _i, [C.POINTER(CsrT), _i, _vp, C.POINTER(_vp)])
 _sig("bspai_apply_uf", _i, [_vp, _vp, _vp, _vp])
 _sig("bspai_bucket", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINTER(_vp), C.POINTER(BucketInfo)])
@@ -278,6 +282,27 @@ def bspai_build(A: DeviceCSR, P: DeviceCSR, spai_eps: float, u_f: str = "fp32", 
     d = {f: getattr(info, f) for f, _ in BuildInfo._fields_}
     d["status"] = st
     return MHandle(h.value), d
+
+
+def bspai_build_adaptive(A: DeviceCSR, spai_eps: float, alpha: int, beta: int = 8, imax_rows: int = 256,
+                         u_f: str = "fp32", stream=None):
+    """Adaptive SPAI (Alg 2.1, alpha > 0) from the identity pattern."""
+    h = C.c_void_p()
+    info = BuildInfo()
+    st = _lib.bspai_build_adaptive(C.byref(A.c()), float(spai_eps), int(alpha), int(beta), int(imax_rows), PREC[u_f],
+                                   _stream(stream), C.byref(h), C.byref(info))
+    _check(st, (OK, RANK_DEFICIENT))
+    d = {f: getattr(info, f) for f, _ in BuildInfo._fields_}
+    d["status"] = st
+    return MHandle(h.value), d
+
+
+def M_adaptive_export(M: MHandle, n: int, nnz: int, stream=None):
+    """(step_added int8[nnz], col_info int32[n]) of an adaptively built M."""
+    step = torch.empty(max(nnz, 1), dtype=torch.int8, device="cuda")
+    cinfo = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    _check(_lib.bspai_M_adaptive_export(M.ptr, _ptr(step), _ptr(cinfo), _stream(stream)))
+    return step[:nnz], cinfo[:n]
 
 
 def M_create(Mcsr: DeviceCSR, u_f: str = "fp32", stream=None) -> MHandle:

@@ -111,6 +111,8 @@ struct bspai_spai {
     int32_t* csr_row_ptr = nullptr;
     float* val = nullptr;      // M in u_f = fp32
     float* resid = nullptr;    // ||sbar_k||_2 per column of M'
+    int8_t* step_added = nullptr;  // adaptive build: the pass that added each entry (CSR order)
+    int32_t* col_info = nullptr;   // adaptive build: solves | conv << 8 | rankdef << 9 | capped << 10
 };
 
 struct bspai_bucketed {

@@ -258,6 +258,8 @@ int bspai_free(void* h) {
         dfree(M->csr_row_ptr, s);
         dfree(M->val, s);
         dfree(M->resid, s);
+        dfree(M->step_added, s);
+        dfree(M->col_info, s);
         M->magic = kMagicDead;
         delete M;
     } else if (magic == kMagicBM) {

@@ -32,6 +32,14 @@ __global__ void k_row_absmax_inv(int n, const int32_t* __restrict__ row_ptr, con
     d[j] = mx > 0.0 ? 1.0 / mx : 1.0;
 }
 
+int launch_row_absmax_inv(int n, const int32_t* row_ptr, const double* val, double* d, cudaStream_t s) {
+    if (n <= 0) return BSPAI_OK;
+    k_row_absmax_inv<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, row_ptr, val, d);
+    note_launch();
+    CUDA_LAUNCH_CHECK();
+    return BSPAI_OK;
+}
+
 // per column: |J_k| and the candidate count sum_{j in J_k} |row j of A|
 __global__ void k_spai_sizes(int n, const int64_t* __restrict__ msptr, const int32_t* __restrict__ mcol,
                              const int32_t* __restrict__ mrowlen, const int32_t* __restrict__ arp,
@@ -476,6 +484,8 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
         info->n_rank_deficient = hc.n_rankdef;
         info->nnz = P->nnz;
         info->max_resid = hc.max_resid;
+        info->n_capped = 0;
+        info->total_solves = n;
     }
     *M_out = M;
     if (hc.n_rankdef > 0) {

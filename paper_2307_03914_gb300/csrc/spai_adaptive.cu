@@ -1,0 +1,728 @@
+// spai_adaptive.cu -- adaptive sparse approximate inverse (Alg 2.1 with
+// alpha > 0: Grote and Huckle's pattern growth) on the GPU.
+//
+// As for the fixed pattern, SPAI runs on B = A^T D (Section 4) and gives the
+// left preconditioner M = M'^T D; column k of M' is row k of M and column j of
+// B is row j of A times d_j.  Each column starts from the identity pattern
+// J_k = {k} (Section 4) and repeats, at most alpha + 1 times:
+//   I_k    = shadow of J_k (the union of the columns of rows J_k of A);
+//   solve  min ||ebar - Abar mbar||_2 by Householder QR; sbar = Abar mbar - ebar;
+//   stop   when ||sbar||_2 <= spai_eps, or after the last solve;
+//   L_k    = I_k u {k};  Jt_k = (union over l in L_k of N_l) \ J_k, with
+//            N_l = {j : b_lj != 0}, the rows of A with an entry in column l
+//            (row l of A^T);
+//   rho_j  = (||sbar||^2 - (sbar^T B(I_k, j))^2 / ||B e_j||^2)^(1/2), the
+//            residual of the best update along e_j alone (Grote and Huckle's
+//            univariate minimisation; sbar is zero outside I_k);
+//   add    the up to beta indices of smallest rho_j (ties: smaller j) among
+//          those with rho_j <= the mean of rho over Jt_k.
+// A step whose new pattern would have a shadow of more than lmax rows is not
+// taken (the column keeps its current solution and is marked capped): lmax
+// bounds the shared memory of one column.
+//
+// One warp per column, everything in u_f = fp32 as in the fixed-pattern
+// kernel: the gathered rows of A, the shadow (bitonic sort + ballot
+// compaction), Abar in shared memory, the Householder QR with warp-shuffle
+// reductions, back substitution, sbar from the gathered entries, the
+// candidate set (gather of A^T rows over L_k, bitonic sort, compaction of the
+// distinct values not in J_k), rho per candidate (one lane per candidate),
+// the mean, and beta rounds of a warp argmin for the picks.  Every loop has a
+// bound set by jmax, lmax or the host-computed buffer sizes.
+#include <climits>
+
+#include "common.cuh"
+
+namespace bspai {
+
+int launch_row_absmax_inv(int n, const int32_t* row_ptr, const double* val, double* d, cudaStream_t s);
+
+struct AdaptiveCounters {
+    int n_conv;
+    int n_rankdef;
+    int n_capped;
+    int max_cols;
+    int max_rows;
+    float max_resid;
+    unsigned long long solves;
+};
+
+// shared memory of one warp, 16-byte aligned pieces
+struct AdaptiveLayout {
+    size_t dJ, J, Jn, stp, stpn, rbeg, eoff, picks, mv, rdiag, ecol, eq, eval, I, cv, sv, region, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, int gmax, int lp2) {
+    AdaptiveLayout L{};
+    size_t o = 0;
+    L.dJ = o;    o += al16((size_t)jmax * 8);
+    L.J = o;     o += al16((size_t)jmax * 4);
+    L.Jn = o;    o += al16((size_t)jmax * 4);
+    L.stp = o;   o += al16((size_t)jmax * 4);
+    L.stpn = o;  o += al16((size_t)jmax * 4);
+    L.rbeg = o;  o += al16((size_t)jmax * 4);
+    L.eoff = o;  o += al16((size_t)(jmax + 1) * 4);
+    L.picks = o; o += al16((size_t)jmax * 4);
+    L.mv = o;    o += al16((size_t)jmax * 4);
+    L.rdiag = o; o += al16((size_t)jmax * 4);
+    L.ecol = o;  o += al16((size_t)gmax * 4);
+    L.eq = o;    o += al16((size_t)gmax * 4);
+    L.eval = o;  o += al16((size_t)gmax * 4);
+    L.I = o;     o += al16((size_t)lmax * 4);
+    L.cv = o;    o += al16((size_t)lmax * 4);
+    L.sv = o;    o += al16((size_t)lmax * 4);
+    L.region = o;
+    const size_t ab = (size_t)lmax * jmax * 4;
+    const size_t keys = (size_t)lp2 * 8;  // sort keys (int) and rho (float)
+    o += al16(ab > keys ? ab : keys);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ int lb_i32(const int* a, int n, int v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool contains(const int* a, int n, int v) {
+    const int p = lb_i32(a, n, v);
+    return p < n && a[p] == v;
+}
+
+// bitonic sort of keys[0, LP), LP a power of two >= 2
+__device__ __forceinline__ void warp_bitonic(int* keys, int LP, int lane) {
+    for (int size = 2; size <= LP; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (LP >> 1); t += 32) {
+                const int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                const int jj = i + stride;
+                const bool asc = (i & size) == 0;
+                const int a = keys[i], b = keys[jj];
+                if ((a > b) == asc) {
+                    keys[i] = b;
+                    keys[jj] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__device__ __forceinline__ int pow2_at_least(int v) {
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Gather every entry of rows J[0, nJ) of A: its column, its value scaled by
+// d_j and rounded to u_f, and its q.  Returns the count (<= nJ * rowmax).
+__device__ __forceinline__ int gather_rows(const int* J, int nJ, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
+                           const double* __restrict__ aval, const double* __restrict__ d, double* dJ, int* rbeg,
+                           int* eoff, int* ecol, int* eq, float* eval, int lane) {
+    for (int q = lane; q < nJ; q += 32) {
+        const int j = J[q];
+        dJ[q] = d[j];
+        const int rb = arp[j];
+        rbeg[q] = rb;
+        eoff[q] = arp[j + 1] - rb;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int acc = 0;
+        for (int q = 0; q < nJ; ++q) {
+            const int len = eoff[q];
+            eoff[q] = acc;
+            acc += len;
+        }
+        eoff[nJ] = acc;
+    }
+    __syncwarp();
+    const int L = eoff[nJ];
+    for (int t = lane; t < L; t += 32) {
+        int lo = 0, hi = nJ;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (eoff[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int e = rbeg[lo] + (t - eoff[lo]);
+        ecol[t] = acol[e];
+        eval[t] = __double2float_rn(__dmul_rn(aval[e], dJ[lo]));
+        eq[t] = lo;
+    }
+    __syncwarp();
+    return L;
+}
+
+// The distinct columns among ecol[0, L) in ascending order into I (at most
+// lmax written); returns their number (which may exceed lmax).
+__device__ __forceinline__ int shadow_rows(const int* ecol, int L, int* keys, int* I, int lmax, int lane) {
+    const int LP = pow2_at_least(L > 2 ? L : 2);
+    for (int t = lane; t < LP; t += 32) keys[t] = t < L ? ecol[t] : INT_MAX;
+    __syncwarp();
+    warp_bitonic(keys, LP, lane);
+    int nI = 0;
+    for (int b0 = 0; b0 < L; b0 += 32) {
+        const int t = b0 + lane;
+        const int v = t < L ? keys[t] : INT_MAX;
+        const int prev = (t > 0 && t < L) ? keys[t - 1] : -1;
+        const bool flag = t < L && v != prev;
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        const int pos = nI + __popc(m & ((1u << lane) - 1u));
+        if (flag && pos < lmax) I[pos] = v;
+        nI += __popc(m);
+    }
+    __syncwarp();
+    return nI;
+}
+
+__global__ void __launch_bounds__(256, 1) k_spai_adaptive(
+    int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol, const double* __restrict__ aval,
+    const double* __restrict__ d, const int32_t* __restrict__ trp, const int32_t* __restrict__ tcol, float spai_eps,
+    float u_f, int alpha, int beta, int jmax, int lmax, int gmax, int lp2, int32_t* __restrict__ Jo,
+    float* __restrict__ Mo, int8_t* __restrict__ So, int32_t* __restrict__ nJo, float* __restrict__ resid,
+    int32_t* __restrict__ cinfo, AdaptiveCounters* __restrict__ cnt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (k >= n) return;
+    const AdaptiveLayout LY = adaptive_layout(jmax, lmax, gmax, lp2);
+    unsigned char* base = smem + LY.total * wib;
+    double* dJ = reinterpret_cast<double*>(base + LY.dJ);
+    int* J = reinterpret_cast<int*>(base + LY.J);
+    int* Jn = reinterpret_cast<int*>(base + LY.Jn);
+    int* stp = reinterpret_cast<int*>(base + LY.stp);
+    int* stpn = reinterpret_cast<int*>(base + LY.stpn);
+    int* rbeg = reinterpret_cast<int*>(base + LY.rbeg);
+    int* eoff = reinterpret_cast<int*>(base + LY.eoff);
+    int* picks = reinterpret_cast<int*>(base + LY.picks);
+    float* mv = reinterpret_cast<float*>(base + LY.mv);
+    float* rdiag = reinterpret_cast<float*>(base + LY.rdiag);
+    int* ecol = reinterpret_cast<int*>(base + LY.ecol);
+    int* eq = reinterpret_cast<int*>(base + LY.eq);
+    float* eval = reinterpret_cast<float*>(base + LY.eval);
+    int* I = reinterpret_cast<int*>(base + LY.I);
+    float* cv = reinterpret_cast<float*>(base + LY.cv);
+    float* sv = reinterpret_cast<float*>(base + LY.sv);
+    float* Ab = reinterpret_cast<float*>(base + LY.region);
+    int* keys = reinterpret_cast<int*>(base + LY.region);
+    float* rho = reinterpret_cast<float*>(base + LY.region + (size_t)lp2 * 4);
+
+    if (lane == 0) {
+        J[0] = (int)k;
+        stp[0] = 0;
+    }
+    __syncwarp();
+    int nJ = 1;
+    int L = gather_rows(J, nJ, arp, acol, aval, d, dJ, rbeg, eoff, ecol, eq, eval, lane);
+    int nI = shadow_rows(ecol, L, keys, I, lmax, lane);  // <= rowmax <= lmax (host check)
+    int max_rows = nI;
+    float res_norm = 1.0f, r2sum = 1.0f;
+    bool rankdef = false, conv = false, capped = false;
+    int solves = 0;
+
+    for (int step = 0; step <= alpha; ++step) {
+        // ---- least squares on B(I, J): Abar (column-major, ld nI), ebar
+        for (int t = lane; t < nJ * nI; t += 32) Ab[t] = 0.0f;
+        for (int t = lane; t < nI; t += 32) cv[t] = 0.0f;
+        __syncwarp();
+        const int pk = lb_i32(I, nI, (int)k);
+        const bool k_in = pk < nI && I[pk] == (int)k;
+        if (lane == 0 && k_in) cv[pk] = 1.0f;
+        for (int t = lane; t < L; t += 32) {
+            const int p = lb_i32(I, nI, ecol[t]);
+            ecol[t] = p;  // from here on: the entry's row in Abar
+            Ab[eq[t] * nI + p] = eval[t];
+        }
+        __syncwarp();
+        rankdef = nI < nJ;
+        float fro = 0.0f;
+        for (int t = lane; t < nJ * nI; t += 32) fro = __fadd_rn(fro, __fmul_rn(Ab[t], Ab[t]));
+        fro = __fsqrt_rn(warp_sum(fro));
+        for (int c = 0; c < nJ && !rankdef; ++c) {
+            float* col_c = Ab + c * nI;
+            float s2 = 0.0f;
+            for (int p = c + lane; p < nI; p += 32) s2 = __fadd_rn(s2, __fmul_rn(col_c[p], col_c[p]));
+            s2 = warp_sum(s2);
+            const float sig = __fsqrt_rn(s2);
+            const float x0 = col_c[c];
+            if (!(sig > 0.0f)) {
+                rankdef = true;
+                break;
+            }
+            const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
+            const float v0 = __fadd_rn(x0, sgn * sig);
+            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
+            __syncwarp();
+            if (lane == 0) col_c[c] = v0;
+            __syncwarp();
+            for (int cc = c + 1; cc <= nJ; ++cc) {
+                float* tgt = cc < nJ ? Ab + cc * nI : cv;
+                float dot = 0.0f;
+                for (int p = c + lane; p < nI; p += 32) dot = __fadd_rn(dot, __fmul_rn(col_c[p], tgt[p]));
+                dot = warp_sum(dot);
+                const float tau = __fdiv_rn(__fmul_rn(2.0f, dot), vtv);
+                for (int p = c + lane; p < nI; p += 32) tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, col_c[p]));
+                __syncwarp();
+            }
+            const float rcc = -sgn * sig;
+            if (lane == 0) rdiag[c] = rcc;
+            if (!(fabsf(rcc) > (float)nI * u_f * fro)) rankdef = true;
+        }
+        __syncwarp();
+        ++solves;
+        if (rankdef) break;
+        if (lane == 0) {
+            for (int c = nJ - 1; c >= 0; --c) {
+                float s = cv[c];
+                for (int cc = c + 1; cc < nJ; ++cc) s = __fsub_rn(s, __fmul_rn(Ab[cc * nI + c], mv[cc]));
+                mv[c] = __fdiv_rn(s, rdiag[c]);
+            }
+        }
+        __syncwarp();
+        // sbar = Abar mbar - ebar from the gathered entries (distinct rows within one q)
+        for (int t = lane; t < nI; t += 32) sv[t] = 0.0f;
+        __syncwarp();
+        if (lane == 0 && k_in) sv[pk] = -1.0f;
+        __syncwarp();
+        for (int q = 0; q < nJ; ++q) {
+            const float mq = mv[q];
+            for (int t = eoff[q] + lane; t < eoff[q + 1]; t += 32) {
+                const int p = ecol[t];
+                sv[p] = __fadd_rn(sv[p], __fmul_rn(eval[t], mq));
+            }
+            __syncwarp();
+        }
+        float r2 = 0.0f;
+        for (int t = lane; t < nI; t += 32) r2 = __fadd_rn(r2, __fmul_rn(sv[t], sv[t]));
+        r2sum = warp_sum(r2);
+        res_norm = __fsqrt_rn(r2sum);
+        if (res_norm <= spai_eps) {
+            conv = true;
+            break;
+        }
+        if (step == alpha) break;
+
+        // ---- candidates: (union over l in I u {k} of N_l) \ J, ascending
+        const int nL = nI + (k_in ? 0 : 1);
+        int raw = 0;
+        for (int c0 = 0; c0 < nL; c0 += 32) {
+            const int t = c0 + lane;
+            const int l = t < nI ? I[t] : (int)k;
+            const int b = t < nL ? trp[l] : 0;
+            const int cntl = t < nL ? trp[l + 1] - b : 0;
+            int incl = cntl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int off = raw + incl - cntl;
+            for (int u = 0; u < cntl; ++u) keys[off + u] = tcol[b + u];
+            raw += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        const int LP = pow2_at_least(raw > 2 ? raw : 2);
+        for (int t = raw + lane; t < LP; t += 32) keys[t] = INT_MAX;
+        __syncwarp();
+        warp_bitonic(keys, LP, lane);
+        int nc = 0;
+        int carry = INT_MIN;
+        for (int b0 = 0; b0 < raw; b0 += 32) {
+            const int t = b0 + lane;
+            const int v = t < raw ? keys[t] : INT_MAX;
+            int prev = __shfl_up_sync(0xffffffffu, v, 1);
+            if (lane == 0) prev = carry;
+            const bool flag = t < raw && v != prev && !contains(J, nJ, v);
+            carry = __shfl_sync(0xffffffffu, v, 31);
+            __syncwarp();
+            const unsigned m = __ballot_sync(0xffffffffu, flag);
+            if (flag) keys[nc + __popc(m & ((1u << lane) - 1u))] = v;
+            nc += __popc(m);
+            __syncwarp();
+        }
+        if (nc == 0) break;
+        // ---- rho per candidate, and their mean
+        float rsum = 0.0f;
+        for (int t = lane; t < nc; t += 32) {
+            const int j = keys[t];
+            const double dj = d[j];
+            float num = 0.0f, den = 0.0f;
+            for (int p = arp[j]; p < arp[j + 1]; ++p) {
+                const int c = acol[p];
+                const float b = __double2float_rn(__dmul_rn(aval[p], dj));
+                den = __fadd_rn(den, __fmul_rn(b, b));
+                const int pos = lb_i32(I, nI, c);
+                if (pos < nI && I[pos] == c) num = __fadd_rn(num, __fmul_rn(sv[pos], b));
+            }
+            float rr = r2sum;
+            if (den > 0.0f) rr = __fsub_rn(r2sum, __fdiv_rn(__fmul_rn(num, num), den));
+            const float rj = __fsqrt_rn(rr > 0.0f ? rr : 0.0f);
+            rho[t] = rj;
+            rsum = __fadd_rn(rsum, rj);
+        }
+        const float mean = __fdiv_rn(warp_sum(rsum), (float)nc);
+        __syncwarp();
+        // ---- up to beta picks: smallest rho (then smaller j) among rho <= mean
+        int npick = 0;
+        for (int r = 0; r < beta; ++r) {
+            float best = INFINITY;
+            int bj = INT_MAX, bt = -1;
+            for (int t = lane; t < nc; t += 32) {
+                const float rv = rho[t];
+                const int jv = keys[t];
+                if (rv <= mean && (rv < best || (rv == best && jv < bj))) {
+                    best = rv;
+                    bj = jv;
+                    bt = t;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                if (ob < best || (ob == best && oj < bj)) {
+                    best = ob;
+                    bj = oj;
+                    bt = ot;
+                }
+            }
+            if (bt < 0) break;
+            if (lane == 0) {
+                rho[bt] = INFINITY;
+                picks[npick] = bj;
+            }
+            ++npick;
+            __syncwarp();
+        }
+        if (npick == 0) break;
+        // ---- J u picks, ascending (lane 0; at most jmax + beta entries)
+        int nJn = 0;
+        if (lane == 0) {
+            for (int a = 1; a < npick; ++a) {  // insertion sort of the picks
+                const int v = picks[a];
+                int b = a - 1;
+                while (b >= 0 && picks[b] > v) {
+                    picks[b + 1] = picks[b];
+                    --b;
+                }
+                picks[b + 1] = v;
+            }
+            int a = 0, b = 0;
+            while ((a < nJ || b < npick) && nJn < jmax) {
+                if (b >= npick || (a < nJ && J[a] < picks[b])) {
+                    Jn[nJn] = J[a];
+                    stpn[nJn++] = stp[a++];
+                } else {
+                    Jn[nJn] = picks[b++];
+                    stpn[nJn++] = step + 1;
+                }
+            }
+            if (a < nJ || b < npick) nJn = jmax + 1;  // would not fit
+        }
+        nJn = __shfl_sync(0xffffffffu, nJn, 0);
+        __syncwarp();
+        if (nJn > jmax) {
+            capped = true;
+            break;
+        }
+        const int Ln = gather_rows(Jn, nJn, arp, acol, aval, d, dJ, rbeg, eoff, ecol, eq, eval, lane);
+        const int nIn = shadow_rows(ecol, Ln, keys, I, lmax, lane);
+        if (nIn > lmax) {
+            capped = true;
+            break;
+        }
+        for (int q = lane; q < nJn; q += 32) {
+            J[q] = Jn[q];
+            stp[q] = stpn[q];
+        }
+        __syncwarp();
+        nJ = nJn;
+        L = Ln;
+        nI = nIn;
+        max_rows = max(max_rows, nI);
+    }
+    if (rankdef) res_norm = 1.0f;
+    // M[k, J[q]] = mbar_q d_J[q]  (M = M'^T D)
+    for (int q = lane; q < nJ; q += 32) {
+        const int j = J[q];
+        const int64_t o = (int64_t)q * n + k;
+        Jo[o] = j;
+        Mo[o] = rankdef ? 0.0f : __double2float_rn(__dmul_rn((double)mv[q], d[j]));
+        So[o] = (int8_t)stp[q];
+    }
+    if (lane == 0) {
+        nJo[k] = nJ;
+        resid[k] = res_norm;
+        cinfo[k] = solves | (conv ? 1 << 8 : 0) | (rankdef ? 1 << 9 : 0) | (capped ? 1 << 10 : 0);
+        if (conv) atomicAdd(&cnt->n_conv, 1);
+        if (rankdef) atomicAdd(&cnt->n_rankdef, 1);
+        if (capped) atomicAdd(&cnt->n_capped, 1);
+        atomicMax(&cnt->max_cols, nJ);
+        atomicMax(&cnt->max_rows, max_rows);
+        atomic_max_nonneg(&cnt->max_resid, res_norm);
+        atomicAdd(&cnt->solves, (unsigned long long)solves);
+    }
+}
+
+// per column of A: its entry count (int64, for the scan), and the largest row
+__global__ void k_col_counts(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
+                             unsigned long long* __restrict__ cnt, int* __restrict__ rowmax) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = arp[i], e = arp[i + 1];
+    atomicMax(rowmax, e - b);
+    for (int p = b; p < e; ++p) atomicAdd(cnt + acol[p], 1ull);
+}
+
+__global__ void k_i64_to_i32_rp(int64_t count, const int64_t* __restrict__ in, int32_t* __restrict__ out,
+                                int* __restrict__ mx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > count) return;
+    out[i] = (int32_t)in[i];
+    if (i < count) atomicMax(mx, (int)(in[i + 1] - in[i]));
+}
+
+// row l of A^T lists the rows of A with an entry in column l (order within a
+// row is irrelevant: the kernel sorts every candidate set)
+__global__ void k_tfill(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
+                        const int32_t* __restrict__ trp, int32_t* __restrict__ cursor, int32_t* __restrict__ tcol) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = arp[i]; p < arp[i + 1]; ++p) {
+        const int c = acol[p];
+        tcol[trp[c] + atomicAdd(cursor + c, 1)] = (int32_t)i;
+    }
+}
+
+__global__ void k_counts_i64(int n, const int32_t* __restrict__ nJ, int64_t* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = nJ[i];
+}
+
+// the per-column slots (column-major, n per slot) to CSR rows of M
+__global__ void k_adaptive_to_csr(int n, const int32_t* __restrict__ Jo, const float* __restrict__ Mo,
+                                  const int8_t* __restrict__ So, const int32_t* __restrict__ nJ,
+                                  const int32_t* __restrict__ rp, int32_t* __restrict__ col, double* __restrict__ val,
+                                  int8_t* __restrict__ st) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int b = rp[k];
+    for (int q = 0; q < nJ[k]; ++q) {
+        const int64_t o = (int64_t)q * n + k;
+        col[b + q] = Jo[o];
+        val[b + q] = (double)Mo[o];
+        st[b + q] = So[o];
+    }
+}
+
+}  // namespace bspai
+
+using namespace bspai;
+
+// a CUDA runtime error inside bspai_build_adaptive: release everything, report it
+#define ATRY(expr)                                                                   \
+    do {                                                                             \
+        cudaError_t e_ = (expr);                                                     \
+        if (e_ != cudaSuccess) return fail(cuda_error(e_, #expr, __FILE__, __LINE__)); \
+    } while (0)
+
+extern "C" {
+
+int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, int32_t beta, int32_t imax_rows,
+                         bspai_prec_t u_f, bspai_stream_t st, bspai_M_h* M_out, bspai_build_info_t* info) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!M_out) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: null M_out");
+    *M_out = nullptr;
+    if (!A) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: null matrix");
+    if (A->n < 0) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: negative size");
+    if (A->n > 0 && (!A->row_ptr || !A->col || !A->val))
+        return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: missing CSR arrays");
+    if (u_f != BSPAI_FP32) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_build_adaptive: only u_f = FP32 is built");
+    if (!(spai_eps > 0.0)) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: spai_eps must be > 0");
+    if (alpha < 0 || alpha > 16 || beta < 0 || beta > 32)
+        return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: need 0 <= alpha <= 16 and 0 <= beta <= 32");
+    if (imax_rows < 1) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: imax_rows must be >= 1");
+    BSPAI_TRY(validate_csr(A, true, "bspai_build_adaptive (A)", s));
+    const int n = A->n;
+    const int jmax = 1 + alpha * beta;
+    auto* M = new bspai_spai();
+    M->magic = kMagicM;
+    M->stream = s;
+    M->n = n;
+    double* d = nullptr;
+    unsigned long long* ccount = nullptr;
+    int64_t* i64 = nullptr;
+    int32_t *trp = nullptr, *tcol = nullptr, *cursor = nullptr, *Jo = nullptr, *nJo = nullptr, *cinfo = nullptr;
+    int32_t* mcol = nullptr;
+    double* mval = nullptr;
+    float* Mo = nullptr;
+    int8_t* So = nullptr;
+    int* maxes = nullptr;
+    AdaptiveCounters* cnt = nullptr;
+    auto cleanup = [&]() {
+        dfree(d, s);
+        dfree(ccount, s);
+        dfree(i64, s);
+        dfree(trp, s);
+        dfree(tcol, s);
+        dfree(cursor, s);
+        dfree(Jo, s);
+        dfree(nJo, s);
+        dfree(mcol, s);
+        dfree(mval, s);
+        dfree(Mo, s);
+        dfree(So, s);
+        dfree(maxes, s);
+        dfree(cnt, s);
+    };
+    auto fail = [&](int code) {
+        cleanup();
+        dfree(cinfo, s);
+        bspai_free(M);
+        return code;
+    };
+    int rc = BSPAI_OK;
+    const size_t n1 = (size_t)n + 1;
+    if ((rc = dalloc_t(&maxes, 2, s))) return fail(rc);
+    if ((rc = dalloc_t(&cnt, 1, s))) return fail(rc);
+    if ((rc = dalloc_t(&M->resid, (size_t)(n > 0 ? n : 1), s))) return fail(rc);
+    if ((rc = dalloc_t(&cinfo, (size_t)(n > 0 ? n : 1), s))) return fail(rc);
+    ATRY(cudaMemsetAsync(maxes, 0, 2 * sizeof(int), s));
+    ATRY(cudaMemsetAsync(cnt, 0, sizeof(AdaptiveCounters), s));
+    int hmax[2] = {0, 0};  // largest row of A, largest column of A
+    int64_t nnzA = 0;
+    if (n > 0) {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        if ((rc = dalloc_t(&d, (size_t)n, s))) return fail(rc);
+        if ((rc = dalloc_t(&ccount, (size_t)n, s))) return fail(rc);
+        if ((rc = dalloc_t(&i64, n1, s))) return fail(rc);
+        if ((rc = dalloc_t(&trp, n1, s))) return fail(rc);
+        if ((rc = dalloc_t(&cursor, (size_t)n, s))) return fail(rc);
+        ATRY(cudaMemsetAsync(ccount, 0, sizeof(unsigned long long) * (size_t)n, s));
+        ATRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)n, s));
+        if ((rc = launch_row_absmax_inv(n, A->row_ptr, A->val, d, s))) return fail(rc);
+        const unsigned g = (unsigned)ceil_div(n, 256);
+        k_col_counts<<<g, 256, 0, s>>>(n, A->row_ptr, A->col, ccount, maxes);
+        note_launch();
+        if ((rc = scan_exclusive_i64(reinterpret_cast<const int64_t*>(ccount), i64, n, s))) return fail(rc);
+        k_i64_to_i32_rp<<<(unsigned)ceil_div((int64_t)n + 1, 256), 256, 0, s>>>(n, i64, trp, maxes + 1);
+        note_launch();
+        ATRY(cudaMemcpyAsync(&nnzA, i64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        ATRY(cudaMemcpyAsync(hmax, maxes, sizeof hmax, cudaMemcpyDeviceToHost, s));
+        ATRY(cudaStreamSynchronize(s));
+        if ((rc = dalloc_t(&tcol, (size_t)(nnzA > 0 ? nnzA : 1), s))) return fail(rc);
+        k_tfill<<<g, 256, 0, s>>>(n, A->row_ptr, A->col, trp, cursor, tcol);
+        note_launch();
+        ATRY(cudaGetLastError());
+    }
+    const int rowmax = hmax[0] > 0 ? hmax[0] : 1;
+    const int colmax = hmax[1] > 0 ? hmax[1] : 1;
+    if (imax_rows < rowmax)
+        return fail(set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: imax_rows = %d is below the longest row of A (%d)",
+                              imax_rows, rowmax));
+    // the shadow of jmax rows has at most jmax * rowmax entries
+    const int64_t gmax64 = (int64_t)jmax * rowmax;
+    const int lmax = (int)(gmax64 < imax_rows ? gmax64 : imax_rows);
+    const int gmax = (int)gmax64;
+    const int64_t cmax = (int64_t)(lmax + 1) * colmax;  // candidates gathered over I u {k}
+    int64_t need = gmax > cmax ? gmax : cmax;
+    int lp2 = 32;
+    while (lp2 < need && lp2 < (1 << 24)) lp2 <<= 1;
+    const size_t per_warp = adaptive_layout(jmax, lmax, gmax, lp2).total;
+    const size_t smem_cap = 200 * 1024;
+    int warps = 8;
+    while (warps > 1 && per_warp * warps > smem_cap) warps >>= 1;
+    if (per_warp * warps > smem_cap)
+        return fail(set_error(BSPAI_ERR_UNSUPPORTED,
+                              "bspai_build_adaptive: one column needs %zu bytes of shared memory (|J| <= %d, |I| <= %d, "
+                              "%lld candidates); lower alpha, beta or imax_rows",
+                              per_warp, jmax, lmax, (long long)need));
+    const size_t smem = per_warp * warps;
+    const size_t slots = (size_t)jmax * (size_t)(n > 0 ? n : 1);
+    if ((rc = dalloc_t(&Jo, slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&Mo, slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&So, slots, s))) return fail(rc);
+    if ((rc = dalloc_t(&nJo, (size_t)(n > 0 ? n : 1), s))) return fail(rc);
+    if (n > 0) {
+        ProfScope ps(BSPAI_K_SPAI, s);
+        ATRY(cudaFuncSetAttribute(k_spai_adaptive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_spai_adaptive<<<(unsigned)ceil_div(n, warps), 32 * warps, smem, s>>>(
+            n, A->row_ptr, A->col, A->val, d, trp, tcol, (float)spai_eps, 5.9604644775390625e-08f, alpha, beta, jmax,
+            lmax, gmax, lp2, Jo, Mo, So, nJo, M->resid, cinfo, cnt);
+        note_launch();
+        ATRY(cudaGetLastError());
+    }
+    // CSR of M from the per-column slots, then the SELL form every product uses
+    int64_t nnzM = 0;
+    if ((rc = dalloc_t(&M->csr_row_ptr, n1, s))) return fail(rc);
+    if (n > 0) {
+        ProfScope ps(BSPAI_K_OTHER, s);
+        const unsigned g = (unsigned)ceil_div(n, 256);
+        k_counts_i64<<<g, 256, 0, s>>>(n, nJo, reinterpret_cast<int64_t*>(ccount));
+        note_launch();
+        if ((rc = scan_exclusive_i64(reinterpret_cast<const int64_t*>(ccount), i64, n, s))) return fail(rc);
+        k_i64_to_i32_rp<<<(unsigned)ceil_div((int64_t)n + 1, 256), 256, 0, s>>>(n, i64, M->csr_row_ptr, maxes);
+        note_launch();
+        ATRY(cudaMemcpyAsync(&nnzM, i64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        ATRY(cudaStreamSynchronize(s));
+        if ((rc = dalloc_t(&mcol, (size_t)(nnzM > 0 ? nnzM : 1), s))) return fail(rc);
+        if ((rc = dalloc_t(&mval, (size_t)(nnzM > 0 ? nnzM : 1), s))) return fail(rc);
+        if ((rc = dalloc_t(&M->step_added, (size_t)(nnzM > 0 ? nnzM : 1), s))) return fail(rc);
+        k_adaptive_to_csr<<<g, 256, 0, s>>>(n, Jo, Mo, So, nJo, M->csr_row_ptr, mcol, mval, M->step_added);
+        note_launch();
+        ATRY(cudaGetLastError());
+        if ((rc = sell_from_csr(n, M->csr_row_ptr, mcol, mval, &M->sell, nullptr, &M->val, &M->rowlen, s)))
+            return fail(rc);
+    } else {
+        ATRY(cudaMemsetAsync(M->csr_row_ptr, 0, sizeof(int32_t), s));
+        if ((rc = sell_from_csr(0, M->csr_row_ptr, nullptr, nullptr, &M->sell, nullptr, &M->val, &M->rowlen, s)))
+            return fail(rc);
+    }
+    M->nnz = nnzM;
+    M->col_info = cinfo;
+    cinfo = nullptr;
+    AdaptiveCounters hc{};
+    ATRY(cudaMemcpyAsync(&hc, cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    ATRY(cudaStreamSynchronize(s));
+    cleanup();
+    if (info) {
+        info->n = n;
+        info->max_cols = hc.max_cols;
+        info->max_rows = hc.max_rows;
+        info->n_converged = hc.n_conv;
+        info->n_rank_deficient = hc.n_rankdef;
+        info->nnz = nnzM;
+        info->max_resid = hc.max_resid;
+        info->n_capped = hc.n_capped;
+        info->total_solves = (int64_t)hc.solves;
+    }
+    *M_out = M;
+    if (hc.n_rankdef > 0) {
+        set_error(BSPAI_RANK_DEFICIENT, "bspai_build_adaptive: %d least-squares blocks were rank deficient",
+                  hc.n_rankdef);
+        return BSPAI_RANK_DEFICIENT;
+    }
+    return BSPAI_OK;
+}
+
+int bspai_M_adaptive_export(bspai_M_h M, int8_t* step_added, int32_t* col_info, bspai_stream_t st) {
+    cudaStream_t s = (cudaStream_t)st;
+    if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_M_adaptive_export: bad handle");
+    if (!M->col_info)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_M_adaptive_export: M was not built by bspai_build_adaptive");
+    if (step_added && M->nnz > 0)
+        CUDA_TRY(cudaMemcpyAsync(step_added, M->step_added, (size_t)M->nnz, cudaMemcpyDeviceToDevice, s));
+    if (col_info && M->n > 0)
+        CUDA_TRY(cudaMemcpyAsync(col_info, M->col_info, sizeof(int32_t) * (size_t)M->n, cudaMemcpyDeviceToDevice, s));
+    return BSPAI_OK;
+}
+
+}  // extern "C"

@@ -51,6 +51,14 @@ def oracle_M(B, wl):
     return B.M_create(Md), muf
 
 
+def spai_tolerance(kappa, resid, u_f=2.0 ** -24):
+    """Per-column bound on the relative error of an SPAI row computed in u_f:
+    max(1e-5, 10 u_f (2 kappa + kappa^2 ||s|| / sqrt(1 - ||s||^2))) (first-order
+    least-squares perturbation bound with ||Abar mbar|| = sqrt(1 - ||s||^2))."""
+    s = np.minimum(resid, 0.999)
+    return np.maximum(1e-5, 10 * u_f * (2 * kappa + kappa ** 2 * s / np.sqrt(1 - s ** 2)))
+
+
 def gpu_bucket(B, M, nnz, eps, precs):
     BM, info = B.bspai_bucket(M, eps, precs)
     ids, stored = B.bucket_export(BM, nnz)

@@ -16,7 +16,7 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib, oracle_M, small_workloads
+from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib, oracle_M, small_workloads, spai_tolerance
 from paper_2307_03914_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -54,10 +54,7 @@ def test_spmv_up_bitexact(B, wl):
 
 
 def _spai_tolerance(kappa, resid):
-    """Per-column bound: max(1e-5, 10 u_f (2 kappa + kappa^2 ||s|| / sqrt(1 - ||s||^2)))
-    (first-order least-squares perturbation bound with ||Abar mbar|| = sqrt(1 - ||s||^2))."""
-    s = np.minimum(resid, 0.999)
-    return np.maximum(1e-5, 10 * U32 * (2 * kappa + kappa ** 2 * s / np.sqrt(1 - s ** 2)))
+    return spai_tolerance(kappa, resid, U32)
 
 
 @pytest.mark.parametrize("wl", WLS, ids=IDS)
