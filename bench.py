@@ -570,6 +570,7 @@ def main():
             "ms_per_solve": dms, "spai_ms": dprof["spai"][0], "gmres_iters": adinf["gmres_iters"], "fwd_err": dfe,
             "nnz_M": minfo["nnz"], "max_cols": minfo["max_cols"], "max_rows": minfo["max_rows"],
             "n_converged": minfo["n_converged"], "n_capped": minfo["n_capped"], "ls_solves": minfo["total_solves"],
+            "n_second_tier": minfo["n_second_tier"],
             "bucket_nnz": abinfo["nnz_k"], "profile_ms": {c: dprof[c][0] for c in dprof}}
 
     # ---------------- end to end through the API with host buffers

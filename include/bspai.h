@@ -83,7 +83,7 @@ typedef struct {
     int64_t nnz;               /* nnz(M) (= nnz(pattern) for the fixed pattern) */
     double max_resid;          /* max_k ||sbar_k||_2 */
     int32_t n_capped;          /* adaptive build: columns whose growth stopped at imax_rows */
-    int32_t reserved;
+    int32_t n_second_tier;     /* adaptive build: columns rerun with the full per-column bounds */
     int64_t total_solves;      /* least-squares solves over all columns (n for the fixed pattern) */
 } bspai_build_info_t;
 

@@ -45,7 +45,7 @@ class CsrT(C.Structure):
 class BuildInfo(C.Structure):
     _fields_ = [("n", C.c_int32), ("max_cols", C.c_int32), ("max_rows", C.c_int32),
                 ("n_converged", C.c_int32), ("n_rank_deficient", C.c_int32), ("nnz", C.c_int64),
-                ("max_resid", C.c_double), ("n_capped", C.c_int32), ("reserved", C.c_int32),
+                ("max_resid", C.c_double), ("n_capped", C.c_int32), ("n_second_tier", C.c_int32),
                 ("total_solves", C.c_int64)]
 
 

@@ -485,6 +485,7 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
         info->nnz = P->nnz;
         info->max_resid = hc.max_resid;
         info->n_capped = 0;
+        info->n_second_tier = 0;
         info->total_solves = n;
     }
     *M_out = M;

@@ -48,15 +48,18 @@ struct AdaptiveCounters {
 
 // shared memory of one warp, 16-byte aligned pieces
 struct AdaptiveLayout {
-    size_t dJ, J, Jn, stp, stpn, rbeg, eoff, picks, mv, rdiag, ecol, eq, eval, I, cv, sv, region, total;
+    size_t acc, J, Jn, stp, stpn, rbeg, eoff, picks, mv, rdiag, ecol, eq, eval, I, cv, sv, tab, region, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, int gmax, int lp2) {
+// jmax, lmax: bounds on |J| and |I|; gmax: on the gathered entries of rows J;
+// lp2: the shadow sort's length (a power of two >= gmax); H: the candidate
+// hash table's size (a power of two; every candidate passes through it).
+__host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, int gmax, int lp2, int H) {
     AdaptiveLayout L{};
     size_t o = 0;
-    L.dJ = o;    o += al16((size_t)jmax * 8);
+    L.acc = o;   o += al16((size_t)H * 8);  // the candidates' fixed-point sbar^T B e_j
     L.J = o;     o += al16((size_t)jmax * 4);
     L.Jn = o;    o += al16((size_t)jmax * 4);
     L.stp = o;   o += al16((size_t)jmax * 4);
@@ -72,10 +75,12 @@ __host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, in
     L.I = o;     o += al16((size_t)lmax * 4);
     L.cv = o;    o += al16((size_t)lmax * 4);
     L.sv = o;    o += al16((size_t)lmax * 4);
-    L.region = o;
-    const size_t ab = (size_t)lmax * jmax * 4;
-    const size_t keys = (size_t)lp2 * 8;  // sort keys (int) and rho (float)
-    o += al16(ab > keys ? ab : keys);
+    L.tab = o;   o += al16((size_t)H * 4);
+    L.region = o;  // Abar, or the shadow sort's keys, or the candidates and their rho
+    size_t r = (size_t)lmax * jmax * 4;
+    if ((size_t)lp2 * 4 > r) r = (size_t)lp2 * 4;
+    if ((size_t)H * 8 > r) r = (size_t)H * 8;
+    o += al16(r);
     L.total = o;
     return L;
 }
@@ -120,14 +125,14 @@ __device__ __forceinline__ int pow2_at_least(int v) {
     return p;
 }
 
-// Gather every entry of rows J[0, nJ) of A: its column, its value scaled by
-// d_j and rounded to u_f, and its q.  Returns the count (<= nJ * rowmax).
-__device__ __forceinline__ int gather_rows(const int* J, int nJ, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
-                           const double* __restrict__ aval, const double* __restrict__ d, double* dJ, int* rbeg,
-                           int* eoff, int* ecol, int* eq, float* eval, int lane) {
+// Gather every entry of rows J[0, nJ) of A: its column, its value in B
+// (a_jc d_j rounded to u_f, precomputed) and its q.  Returns the count
+// (<= nJ * rowmax).
+__device__ __forceinline__ int gather_rows(const int* J, int nJ, const int32_t* __restrict__ arp,
+                                           const int32_t* __restrict__ acol, const float* __restrict__ bval,
+                                           int* rbeg, int* eoff, int* ecol, int* eq, float* eval, int lane) {
     for (int q = lane; q < nJ; q += 32) {
         const int j = J[q];
-        dJ[q] = d[j];
         const int rb = arp[j];
         rbeg[q] = rb;
         eoff[q] = arp[j + 1] - rb;
@@ -153,7 +158,7 @@ __device__ __forceinline__ int gather_rows(const int* J, int nJ, const int32_t* 
         }
         const int e = rbeg[lo] + (t - eoff[lo]);
         ecol[t] = acol[e];
-        eval[t] = __double2float_rn(__dmul_rn(aval[e], dJ[lo]));
+        eval[t] = bval[e];
         eq[t] = lo;
     }
     __syncwarp();
@@ -182,20 +187,31 @@ __device__ __forceinline__ int shadow_rows(const int* ecol, int L, int* keys, in
     return nI;
 }
 
-__global__ void __launch_bounds__(256, 1) k_spai_adaptive(
-    int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol, const double* __restrict__ aval,
-    const double* __restrict__ d, const int32_t* __restrict__ trp, const int32_t* __restrict__ tcol, float spai_eps,
-    float u_f, int alpha, int beta, int jmax, int lmax, int gmax, int lp2, int32_t* __restrict__ Jo,
-    float* __restrict__ Mo, int8_t* __restrict__ So, int32_t* __restrict__ nJo, float* __restrict__ resid,
-    int32_t* __restrict__ cinfo, AdaptiveCounters* __restrict__ cnt) {
+// Two tiers share this kernel.  The first runs every column with a small
+// per-warp footprint (jmax, lmax below the full bounds, so more warps fit on
+// an SM); a column whose pattern or shadow outgrows it -- without reaching the
+// caller's cap_rows -- is appended to redo_list and left unwritten.  The second
+// tier (redo_list == nullptr) reruns exactly those columns (cols) from the
+// start with the full bounds.  Both run the same steps in the same order, so
+// a column's result does not depend on the tier that finished it.
+__global__ void __launch_bounds__(256, 3) k_spai_adaptive(
+    int n, int ncols, const int32_t* __restrict__ cols, const int32_t* __restrict__ arp,
+    const int32_t* __restrict__ acol, const float* __restrict__ bval, const float* __restrict__ bnorm2,
+    const double* __restrict__ d, const int32_t* __restrict__ trp, const int32_t* __restrict__ tcol,
+    const float* __restrict__ tval, float spai_eps, float u_f, int alpha, int beta,
+    int jmax, int lmax, int gmax, int lp2, int H, int cap_rows, int32_t* __restrict__ redo_list,
+    int* __restrict__ redo_count,
+    int32_t* __restrict__ Jo, float* __restrict__ Mo, int8_t* __restrict__ So, int32_t* __restrict__ nJo,
+    float* __restrict__ resid, int32_t* __restrict__ cinfo, AdaptiveCounters* __restrict__ cnt) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    if (k >= n) return;
-    const AdaptiveLayout LY = adaptive_layout(jmax, lmax, gmax, lp2);
+    const int64_t idx = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (idx >= ncols) return;
+    const int64_t k = cols ? (int64_t)cols[idx] : idx;
+    const AdaptiveLayout LY = adaptive_layout(jmax, lmax, gmax, lp2, H);
     unsigned char* base = smem + LY.total * wib;
-    double* dJ = reinterpret_cast<double*>(base + LY.dJ);
+    long long* acc = reinterpret_cast<long long*>(base + LY.acc);
     int* J = reinterpret_cast<int*>(base + LY.J);
     int* Jn = reinterpret_cast<int*>(base + LY.Jn);
     int* stp = reinterpret_cast<int*>(base + LY.stp);
@@ -211,9 +227,14 @@ __global__ void __launch_bounds__(256, 1) k_spai_adaptive(
     int* I = reinterpret_cast<int*>(base + LY.I);
     float* cv = reinterpret_cast<float*>(base + LY.cv);
     float* sv = reinterpret_cast<float*>(base + LY.sv);
+    int* tab = reinterpret_cast<int*>(base + LY.tab);
     float* Ab = reinterpret_cast<float*>(base + LY.region);
     int* keys = reinterpret_cast<int*>(base + LY.region);
-    float* rho = reinterpret_cast<float*>(base + LY.region + (size_t)lp2 * 4);
+    float* rho = reinterpret_cast<float*>(base + LY.region + (size_t)H * 4);
+    for (int t = lane; t < H; t += 32) {  // empty; every pass leaves it empty again
+        tab[t] = -1;
+        acc[t] = 0;
+    }
 
     if (lane == 0) {
         J[0] = (int)k;
@@ -221,11 +242,11 @@ __global__ void __launch_bounds__(256, 1) k_spai_adaptive(
     }
     __syncwarp();
     int nJ = 1;
-    int L = gather_rows(J, nJ, arp, acol, aval, d, dJ, rbeg, eoff, ecol, eq, eval, lane);
+    int L = gather_rows(J, nJ, arp, acol, bval, rbeg, eoff, ecol, eq, eval, lane);
     int nI = shadow_rows(ecol, L, keys, I, lmax, lane);  // <= rowmax <= lmax (host check)
     int max_rows = nI;
     float res_norm = 1.0f, r2sum = 1.0f;
-    bool rankdef = false, conv = false, capped = false;
+    bool rankdef = false, conv = false, capped = false, redo = false;
     int solves = 0;
 
     for (int step = 0; step <= alpha; ++step) {
@@ -310,65 +331,79 @@ __global__ void __launch_bounds__(256, 1) k_spai_adaptive(
         }
         if (step == alpha) break;
 
-        // ---- candidates: (union over l in I u {k} of N_l) \ J, ascending
+        // ---- candidates: (union over l in I u {k} of N_l) \ J, each once.  Row l
+        // of B lists the j with b_lj != 0 (tcol) and the values (tval), so one
+        // sweep over the rows l in I inserts every candidate j into an
+        // open-addressing hash table and accumulates sbar^T B(I, j) = sum over l
+        // in I of sbar_l b_lj in fixed point (2^-40 units, exact integer sums,
+        // independent of the order).  ||B e_j||^2 is precomputed per column.
+        // A full table (only possible in the first tier, whose table may have
+        // fewer slots than the candidate bound) sends the column to the second.
         const int nL = nI + (k_in ? 0 : 1);
-        int raw = 0;
-        for (int c0 = 0; c0 < nL; c0 += 32) {
-            const int t = c0 + lane;
+        const int hshift = 32 - (31 - __clz(H));
+        bool full = false;
+        for (int t = lane; t < nL; t += 32) {
             const int l = t < nI ? I[t] : (int)k;
-            const int b = t < nL ? trp[l] : 0;
-            const int cntl = t < nL ? trp[l + 1] - b : 0;
-            int incl = cntl;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
+            const float sl = t < nI ? sv[t] : 0.0f;
+            const int e = trp[l + 1];
+            for (int p = trp[l]; p < e; ++p) {
+                const int j = tcol[p];
+                if (contains(J, nJ, j)) continue;
+                const long long term = __float2ll_rn(__fmul_rn(__fmul_rn(sl, tval[p]), 1099511627776.0f));
+                unsigned h = ((unsigned)j * 0x9E3779B1u) >> hshift;
+                int probe = 0;
+                for (; probe < H; ++probe) {
+                    const int prev = atomicCAS(tab + h, -1, j);
+                    if (prev == -1 || prev == j) {
+                        atomicAdd(reinterpret_cast<unsigned long long*>(acc + h), (unsigned long long)term);
+                        break;
+                    }
+                    h = (h + 1) & (unsigned)(H - 1);
+                }
+                if (probe == H) full = true;
             }
-            const int off = raw + incl - cntl;
-            for (int u = 0; u < cntl; ++u) keys[off + u] = tcol[b + u];
-            raw += __shfl_sync(0xffffffffu, incl, 31);
         }
-        const int LP = pow2_at_least(raw > 2 ? raw : 2);
-        for (int t = raw + lane; t < LP; t += 32) keys[t] = INT_MAX;
         __syncwarp();
-        warp_bitonic(keys, LP, lane);
+        if (__any_sync(0xffffffffu, full)) {  // first tier only: the second's H exceeds every candidate count
+            for (int t = lane; t < H; t += 32) {
+                tab[t] = -1;
+                acc[t] = 0;
+            }
+            if (redo_list) redo = true;
+            else capped = true;
+            break;
+        }
+        // ---- rho per candidate while the table is emptied into keys/rho, and the
+        // mean of rho (<= ||sbar|| <= 1) as a fixed-point sum
         int nc = 0;
-        int carry = INT_MIN;
-        for (int b0 = 0; b0 < raw; b0 += 32) {
-            const int t = b0 + lane;
-            const int v = t < raw ? keys[t] : INT_MAX;
-            int prev = __shfl_up_sync(0xffffffffu, v, 1);
-            if (lane == 0) prev = carry;
-            const bool flag = t < raw && v != prev && !contains(J, nJ, v);
-            carry = __shfl_sync(0xffffffffu, v, 31);
-            __syncwarp();
-            const unsigned m = __ballot_sync(0xffffffffu, flag);
-            if (flag) keys[nc + __popc(m & ((1u << lane) - 1u))] = v;
-            nc += __popc(m);
-            __syncwarp();
-        }
-        if (nc == 0) break;
-        // ---- rho per candidate, and their mean
-        float rsum = 0.0f;
-        for (int t = lane; t < nc; t += 32) {
-            const int j = keys[t];
-            const double dj = d[j];
-            float num = 0.0f, den = 0.0f;
-            for (int p = arp[j]; p < arp[j + 1]; ++p) {
-                const int c = acol[p];
-                const float b = __double2float_rn(__dmul_rn(aval[p], dj));
-                den = __fadd_rn(den, __fmul_rn(b, b));
-                const int pos = lb_i32(I, nI, c);
-                if (pos < nI && I[pos] == c) num = __fadd_rn(num, __fmul_rn(sv[pos], b));
+        long long rsum = 0;
+        for (int b0 = 0; b0 < H; b0 += 32) {
+            const int v = tab[b0 + lane];
+            const bool flag = v >= 0;
+            float rj = 0.0f;
+            if (flag) {
+                const float num = __fmul_rn(__ll2float_rn(acc[b0 + lane]), 9.094947017729282e-13f);  // 2^-40
+                const float den = bnorm2[v];
+                float rr = r2sum;
+                if (den > 0.0f) rr = __fsub_rn(r2sum, __fdiv_rn(__fmul_rn(num, num), den));
+                rj = __fsqrt_rn(rr > 0.0f ? rr : 0.0f);
+                rsum += __float2ll_rn(__fmul_rn(rj, 1099511627776.0f));
+                tab[b0 + lane] = -1;
+                acc[b0 + lane] = 0;
             }
-            float rr = r2sum;
-            if (den > 0.0f) rr = __fsub_rn(r2sum, __fdiv_rn(__fmul_rn(num, num), den));
-            const float rj = __fsqrt_rn(rr > 0.0f ? rr : 0.0f);
-            rho[t] = rj;
-            rsum = __fadd_rn(rsum, rj);
+            const unsigned m = __ballot_sync(0xffffffffu, flag);
+            if (flag) {
+                const int o = nc + __popc(m & ((1u << lane) - 1u));
+                keys[o] = v;
+                rho[o] = rj;
+            }
+            nc += __popc(m);
         }
-        const float mean = __fdiv_rn(warp_sum(rsum), (float)nc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         __syncwarp();
+        if (nc == 0) break;
+        const float mean = __fdiv_rn(__fmul_rn(__ll2float_rn(rsum), 9.094947017729282e-13f), (float)nc);
         // ---- up to beta picks: smallest rho (then smaller j) among rho <= mean
         int npick = 0;
         for (int r = 0; r < beta; ++r) {
@@ -429,14 +464,16 @@ __global__ void __launch_bounds__(256, 1) k_spai_adaptive(
         }
         nJn = __shfl_sync(0xffffffffu, nJn, 0);
         __syncwarp();
-        if (nJn > jmax) {
-            capped = true;
+        if (nJn > jmax) {  // only the first tier's jmax is below 1 + alpha beta
+            if (redo_list) redo = true;
+            else capped = true;
             break;
         }
-        const int Ln = gather_rows(Jn, nJn, arp, acol, aval, d, dJ, rbeg, eoff, ecol, eq, eval, lane);
+        const int Ln = gather_rows(Jn, nJn, arp, acol, bval, rbeg, eoff, ecol, eq, eval, lane);
         const int nIn = shadow_rows(ecol, Ln, keys, I, lmax, lane);
         if (nIn > lmax) {
-            capped = true;
+            if (redo_list && nIn <= cap_rows) redo = true;
+            else capped = true;
             break;
         }
         for (int q = lane; q < nJn; q += 32) {
@@ -448,6 +485,10 @@ __global__ void __launch_bounds__(256, 1) k_spai_adaptive(
         L = Ln;
         nI = nIn;
         max_rows = max(max_rows, nI);
+    }
+    if (redo) {
+        if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = (int32_t)k;
+        return;
     }
     if (rankdef) res_norm = 1.0f;
     // M[k, J[q]] = mbar_q d_J[q]  (M = M'^T D)
@@ -490,15 +531,35 @@ __global__ void k_i64_to_i32_rp(int64_t count, const int64_t* __restrict__ in, i
     if (i < count) atomicMax(mx, (int)(in[i + 1] - in[i]));
 }
 
-// row l of A^T lists the rows of A with an entry in column l (order within a
-// row is irrelevant: the kernel sorts every candidate set)
+// B = A^T D in u_f: bval[p] = fl32(a_p d_i) for the entries p of row i of A
+// (column i of B), and bnorm2[i] = ||B e_i||^2 summed in fp32 in row order
+__global__ void k_bvals(int n, const int32_t* __restrict__ arp, const double* __restrict__ aval,
+                        const double* __restrict__ d, float* __restrict__ bval, float* __restrict__ bnorm2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double di = d[i];
+    float s2 = 0.0f;
+    for (int p = arp[i]; p < arp[i + 1]; ++p) {
+        const float b = __double2float_rn(__dmul_rn(aval[p], di));
+        bval[p] = b;
+        s2 = __fadd_rn(s2, __fmul_rn(b, b));
+    }
+    bnorm2[i] = s2;
+}
+
+// the rows of B: row l lists the j with b_lj = a_jl d_j != 0 (the rows of A
+// with an entry in column l) and those values; the order within a row is
+// irrelevant, every use of a row is order-independent
 __global__ void k_tfill(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
-                        const int32_t* __restrict__ trp, int32_t* __restrict__ cursor, int32_t* __restrict__ tcol) {
+                        const float* __restrict__ bval, const int32_t* __restrict__ trp, int32_t* __restrict__ cursor,
+                        int32_t* __restrict__ tcol, float* __restrict__ tval) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int p = arp[i]; p < arp[i + 1]; ++p) {
         const int c = acol[p];
-        tcol[trp[c] + atomicAdd(cursor + c, 1)] = (int32_t)i;
+        const int o = trp[c] + atomicAdd(cursor + c, 1);
+        tcol[o] = (int32_t)i;
+        tval[o] = bval[p];
     }
 }
 
@@ -553,6 +614,7 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
     BSPAI_TRY(validate_csr(A, true, "bspai_build_adaptive (A)", s));
     const int n = A->n;
     const int jmax = 1 + alpha * beta;
+    int second_tier = 0;
     auto* M = new bspai_spai();
     M->magic = kMagicM;
     M->stream = s;
@@ -563,6 +625,7 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
     int32_t *trp = nullptr, *tcol = nullptr, *cursor = nullptr, *Jo = nullptr, *nJo = nullptr, *cinfo = nullptr;
     int32_t* mcol = nullptr;
     double* mval = nullptr;
+    float *bval = nullptr, *bnorm2 = nullptr, *tval = nullptr;
     float* Mo = nullptr;
     int8_t* So = nullptr;
     int* maxes = nullptr;
@@ -578,6 +641,9 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         dfree(nJo, s);
         dfree(mcol, s);
         dfree(mval, s);
+        dfree(bval, s);
+        dfree(bnorm2, s);
+        dfree(tval, s);
         dfree(Mo, s);
         dfree(So, s);
         dfree(maxes, s);
@@ -619,7 +685,12 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         ATRY(cudaMemcpyAsync(hmax, maxes, sizeof hmax, cudaMemcpyDeviceToHost, s));
         ATRY(cudaStreamSynchronize(s));
         if ((rc = dalloc_t(&tcol, (size_t)(nnzA > 0 ? nnzA : 1), s))) return fail(rc);
-        k_tfill<<<g, 256, 0, s>>>(n, A->row_ptr, A->col, trp, cursor, tcol);
+        if ((rc = dalloc_t(&tval, (size_t)(nnzA > 0 ? nnzA : 1), s))) return fail(rc);
+        if ((rc = dalloc_t(&bval, (size_t)(nnzA > 0 ? nnzA : 1), s))) return fail(rc);
+        if ((rc = dalloc_t(&bnorm2, (size_t)n, s))) return fail(rc);
+        k_bvals<<<g, 256, 0, s>>>(n, A->row_ptr, A->val, d, bval, bnorm2);
+        note_launch();
+        k_tfill<<<g, 256, 0, s>>>(n, A->row_ptr, A->col, bval, trp, cursor, tcol, tval);
         note_launch();
         ATRY(cudaGetLastError());
     }
@@ -631,21 +702,44 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
     // the shadow of jmax rows has at most jmax * rowmax entries
     const int64_t gmax64 = (int64_t)jmax * rowmax;
     const int lmax = (int)(gmax64 < imax_rows ? gmax64 : imax_rows);
-    const int gmax = (int)gmax64;
-    const int64_t cmax = (int64_t)(lmax + 1) * colmax;  // candidates gathered over I u {k}
-    int64_t need = gmax > cmax ? gmax : cmax;
-    int lp2 = 32;
-    while (lp2 < need && lp2 < (1 << 24)) lp2 <<= 1;
-    const size_t per_warp = adaptive_layout(jmax, lmax, gmax, lp2).total;
+    auto pow2_len = [](int64_t need, bool strictly_above) {
+        int64_t p = 32;
+        while ((strictly_above ? p <= need : p < need) && p < ((int64_t)1 << 26)) p <<= 1;
+        return (int)p;
+    };
+    // the sizes of one tier: |J| <= jm, |I| <= lm; candidates come from the rows
+    // of A^T over I u {k} (at most (lm + 1) colmax of them, and at most n)
+    struct Tier {
+        int jmax, lmax, gmax, lp2, cmax, H, warps;
+        size_t per_warp;
+    };
     const size_t smem_cap = 200 * 1024;
-    int warps = 8;
-    while (warps > 1 && per_warp * warps > smem_cap) warps >>= 1;
-    if (per_warp * warps > smem_cap)
+    auto tier = [&](int jm, int lm, int hcap) {
+        Tier t{};
+        t.jmax = jm;
+        t.lmax = lm;
+        t.gmax = jm * rowmax;
+        t.lp2 = pow2_len(t.gmax, false);
+        const int64_t c = (int64_t)(lm + 1) * colmax;
+        t.cmax = (int)(c < n ? c : n);
+        t.H = pow2_len(t.cmax, true);  // more slots than candidates: no insertion can fail
+        if (hcap > 0 && t.H > hcap) t.H = hcap;  // first tier: a full table reruns the column
+        t.per_warp = adaptive_layout(t.jmax, t.lmax, t.gmax, t.lp2, t.H).total;
+        t.warps = 8;
+        while (t.warps > 1 && t.per_warp * t.warps > smem_cap) t.warps >>= 1;
+        return t;
+    };
+    const Tier full = tier(jmax, lmax, 0);
+    if (full.per_warp * full.warps > smem_cap)
         return fail(set_error(BSPAI_ERR_UNSUPPORTED,
                               "bspai_build_adaptive: one column needs %zu bytes of shared memory (|J| <= %d, |I| <= %d, "
-                              "%lld candidates); lower alpha, beta or imax_rows",
-                              per_warp, jmax, lmax, (long long)need));
-    const size_t smem = per_warp * warps;
+                              "%d candidates); lower alpha, beta or imax_rows",
+                              full.per_warp, jmax, lmax, full.cmax));
+    // first tier: |J| <= 12, |I| <= 64, 256 candidate slots (when that is smaller
+    // and the longest row fits): about 9 KB per column, three blocks of 8 warps per SM
+    const Tier small = tier(jmax < 12 ? jmax : 12, lmax < 64 ? lmax : 64, 256);
+    const bool two_tier = (small.jmax < jmax || small.lmax < lmax) && rowmax <= small.lmax &&
+                          small.per_warp < full.per_warp && small.per_warp * small.warps <= smem_cap;
     const size_t slots = (size_t)jmax * (size_t)(n > 0 ? n : 1);
     if ((rc = dalloc_t(&Jo, slots, s))) return fail(rc);
     if ((rc = dalloc_t(&Mo, slots, s))) return fail(rc);
@@ -653,12 +747,42 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
     if ((rc = dalloc_t(&nJo, (size_t)(n > 0 ? n : 1), s))) return fail(rc);
     if (n > 0) {
         ProfScope ps(BSPAI_K_SPAI, s);
-        ATRY(cudaFuncSetAttribute(k_spai_adaptive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_spai_adaptive<<<(unsigned)ceil_div(n, warps), 32 * warps, smem, s>>>(
-            n, A->row_ptr, A->col, A->val, d, trp, tcol, (float)spai_eps, 5.9604644775390625e-08f, alpha, beta, jmax,
-            lmax, gmax, lp2, Jo, Mo, So, nJo, M->resid, cinfo, cnt);
-        note_launch();
-        ATRY(cudaGetLastError());
+        const size_t smem_full = full.per_warp * full.warps, smem_s = small.per_warp * small.warps;
+        const size_t smem_max = two_tier && smem_s > smem_full ? smem_s : smem_full;
+        ATRY(cudaFuncSetAttribute(k_spai_adaptive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        const float uf = 5.9604644775390625e-08f;
+        int nredo = n;
+        int32_t* redo = nullptr;  // the columns the second tier runs (all of them without a first tier)
+        if (two_tier) {
+            // cursor (the redo count) is reused: it was the A^T fill cursor
+            if ((rc = dalloc_t(&redo, (size_t)n, s))) return fail(rc);
+            ATRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s));
+            k_spai_adaptive<<<(unsigned)ceil_div(n, small.warps), 32 * small.warps, smem_s, s>>>(
+                n, n, nullptr, A->row_ptr, A->col, bval, bnorm2, d, trp, tcol, tval, (float)spai_eps, uf, alpha, beta,
+                small.jmax,
+                small.lmax, small.gmax, small.lp2, small.H, imax_rows, redo, cursor, Jo, Mo, So, nJo,
+                M->resid, cinfo, cnt);
+            note_launch();
+            cudaError_t e = cudaGetLastError();
+            if (!e) e = cudaMemcpyAsync(&nredo, cursor, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            if (e) {
+                dfree(redo, s);
+                return fail(cuda_error(e, "adaptive SPAI first tier", __FILE__, __LINE__));
+            }
+        }
+        if (nredo > 0) {
+            k_spai_adaptive<<<(unsigned)ceil_div(nredo, full.warps), 32 * full.warps, smem_full, s>>>(
+                n, nredo, redo, A->row_ptr, A->col, bval, bnorm2, d, trp, tcol, tval, (float)spai_eps, uf, alpha, beta,
+                jmax, lmax,
+                full.gmax, full.lp2, full.H, imax_rows, nullptr, nullptr, Jo, Mo, So, nJo, M->resid, cinfo,
+                cnt);
+            note_launch();
+        }
+        cudaError_t e = cudaGetLastError();
+        dfree(redo, s);
+        if (e) return fail(cuda_error(e, "adaptive SPAI", __FILE__, __LINE__));
+        second_tier = nredo;
     }
     // CSR of M from the per-column slots, then the SELL form every product uses
     int64_t nnzM = 0;
@@ -702,6 +826,7 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         info->nnz = nnzM;
         info->max_resid = hc.max_resid;
         info->n_capped = hc.n_capped;
+        info->n_second_tier = second_tier;
         info->total_solves = (int64_t)hc.solves;
     }
     *M_out = M;

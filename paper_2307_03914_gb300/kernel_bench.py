@@ -20,6 +20,9 @@ e4m3) to separate the cost of the formats from the cost of the mix.
 --batch NSYS NRHS runs the batched solver once on a batch of NSYS systems
 with NRHS right-hand sides (the 512 x 32 workload's size distribution), and
 prints its statistics and time (a short launch sequence for a profiler).
+--adaptive EPS ALPHA times the adaptive SPAI build (beta = 8, identity
+start) on the grid (median of --reps builds) and prints its statistics; with
+--once it builds exactly once (a short launch sequence for a profiler).
 --mgs times GMRES runs of K = 2, 8, 16, 32, 64 steps (tau = 0) on the same
 system and fits the MGS kernel-class time to a K + b P(K), P(K) = sum over the
 steps j < K of the j + 2 grid reductions of step j: a is the cost per Arnoldi
@@ -49,9 +52,12 @@ def main():
     p.add_argument("--mgs", action="store_true")
     p.add_argument("--mixes", action="store_true")
     p.add_argument("--batch", type=int, nargs=2, default=None, metavar=("NSYS", "NRHS"))
+    p.add_argument("--adaptive", type=float, nargs=2, default=None, metavar=("EPS", "ALPHA"))
     a = p.parse_args()
     if a.batch:
         return batch(a.batch[0], a.batch[1])
+    if a.adaptive:
+        return adaptive(a.grid, a.adaptive[0], int(a.adaptive[1]), 1 if a.once else a.reps)
     wl = W.workload("convdiff3d", grid=a.grid)
     A = B.DeviceCSR.from_host(wl["A"])
     P = B.DeviceCSR.from_host(wl["pattern"], with_values=False)
@@ -151,6 +157,22 @@ def main():
     B.set_spmv_form(B.SPMV_AUTO)
     tr = timeit(lambda: B.residual(Ah, xd, bd, rd))
     print(json.dumps({"kernel": "residual_dd", "n": n, "us": tr * 1e3, "GBs": r_bytes / tr / 1e6, "bytes": r_bytes}))
+
+
+def adaptive(grid, eps, alpha, reps):
+    wl = W.workload("convdiff3d", grid=grid)
+    A = B.DeviceCSR.from_host(wl["A"])
+    ts = []
+    info = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        M, info = B.bspai_build_adaptive(A, eps, alpha, 8)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        M.free()
+    print(json.dumps({"grid": grid, "eps": eps, "alpha": alpha, "ms": float(np.median(ts)), "info": info}))
 
 
 def batch(nsys, nrhs):

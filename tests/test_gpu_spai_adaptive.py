@@ -167,3 +167,14 @@ def test_ir_with_adaptive_M_matches_oracle(B, wl):
     assert fe_g <= 1e-10 and fe_o <= 1e-10
     assert np.abs(xg - ref["x"]).max() <= 1e-12 * np.abs(ref["x"]).max()
     assert abs(info["ir_steps"] - ref["steps"]) <= 1
+
+
+def test_both_tiers_run(B):
+    """Columns that outgrow the first tier's footprint are rerun whole by the
+    second; the parity tests above cover their results."""
+    # random, 17 entries per row: columns that meet 0.5 with J = {k} stay in the
+    # first tier, the others grow shadows of ~150 rows and are rerun
+    g = _gpu_adaptive(B, WLS[4]["A"], 0.5, 2)
+    assert 0 < g["info"]["n_second_tier"] < WLS[4]["A"].n
+    g = _gpu_adaptive(B, WLS[0]["A"], 0.3, 3)  # 5-point stencil: everything fits the first tier
+    assert g["info"]["n_second_tier"] == 0
