@@ -85,6 +85,28 @@ __host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, in
     return L;
 }
 
+constexpr int QB = 8;  // products reduced per batch of shuffles in the QR
+
+// x * 2^40 as a 64-bit integer, truncated toward zero (|x| < 2^22), from the
+// bits of x with integer operations only (64-bit float-integer conversions
+// would use the narrow fp64 pipe)
+__device__ __forceinline__ long long fix40(float x) {
+    const unsigned u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xFFu);
+    if (e == 0) return 0;  // zero or subnormal: below 2^-126, nothing at 2^-40
+    const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 110;  // x = m 2^(e - 150), times 2^40
+    const long long r = sh >= 0 ? (m << sh) : (sh > -40 ? (m >> -sh) : 0);
+    return (u >> 31) ? -r : r;
+}
+
+// v * 2^-40 as a float, from the two 32-bit halves of v
+__device__ __forceinline__ float unfix40(long long v) {
+    const float hi = (float)(int)(v >> 32);
+    const float lo = (float)(unsigned)(v & 0xFFFFFFFFll);
+    return __fmul_rn(__fadd_rn(__fmul_rn(hi, 4294967296.0f), lo), 9.094947017729282e-13f);
+}
+
 __device__ __forceinline__ int lb_i32(const int* a, int n, int v) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -267,32 +289,77 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         float fro = 0.0f;
         for (int t = lane; t < nJ * nI; t += 32) fro = __fadd_rn(fro, __fmul_rn(Ab[t], Ab[t]));
         fro = __fsqrt_rn(warp_sum(fro));
+        // Householder QR, applied to ebar as well.  For reflector c the norm of
+        // column c and its products with every later column (and ebar) are
+        // formed in one sweep with the unreflected x0 at row c, then reduced
+        // together (QB values per batch of shuffles), and corrected for v_c =
+        // x0 + sgn sig: v^T t = (x^T t) + sgn sig t_c.
         for (int c = 0; c < nJ && !rankdef; ++c) {
             float* col_c = Ab + c * nI;
-            float s2 = 0.0f;
-            for (int p = c + lane; p < nI; p += 32) s2 = __fadd_rn(s2, __fmul_rn(col_c[p], col_c[p]));
-            s2 = warp_sum(s2);
-            const float sig = __fsqrt_rn(s2);
             const float x0 = col_c[c];
-            if (!(sig > 0.0f)) {
-                rankdef = true;
-                break;
-            }
-            const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
-            const float v0 = __fadd_rn(x0, sgn * sig);
-            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
-            __syncwarp();
-            if (lane == 0) col_c[c] = v0;
-            __syncwarp();
-            for (int cc = c + 1; cc <= nJ; ++cc) {
-                float* tgt = cc < nJ ? Ab + cc * nI : cv;
-                float dot = 0.0f;
-                for (int p = c + lane; p < nI; p += 32) dot = __fadd_rn(dot, __fmul_rn(col_c[p], tgt[p]));
-                dot = warp_sum(dot);
-                const float tau = __fdiv_rn(__fmul_rn(2.0f, dot), vtv);
-                for (int p = c + lane; p < nI; p += 32) tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, col_c[p]));
+            float sgn = 1.0f, sig = 0.0f, vtv = 1.0f, v0 = 0.0f;
+            for (int cc0 = c + 1; cc0 <= nJ; cc0 += QB) {  // c + 1 <= nJ: ebar is target nJ
+                const bool first = cc0 == c + 1;
+                float part[QB + 1];
+#pragma unroll
+                for (int i = 0; i <= QB; ++i) part[i] = 0.0f;
+                for (int p = c + lane; p < nI; p += 32) {
+                    const float xp = col_c[p];
+                    if (first) part[QB] = __fadd_rn(part[QB], __fmul_rn(xp, xp));
+#pragma unroll
+                    for (int i = 0; i < QB; ++i) {
+                        const int cc = cc0 + i;
+                        if (cc <= nJ) {
+                            const float* tgt = cc < nJ ? Ab + cc * nI : cv;
+                            part[i] = __fadd_rn(part[i], __fmul_rn(xp, tgt[p]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int i = 0; i <= QB; ++i) part[i] = __fadd_rn(part[i], __shfl_xor_sync(0xffffffffu, part[i], o));
+                }
+                if (first) {
+                    sig = __fsqrt_rn(part[QB]);
+                    if (!(sig > 0.0f)) {
+                        rankdef = true;
+                        break;
+                    }
+                    sgn = x0 >= 0.0f ? 1.0f : -1.0f;
+                    v0 = __fadd_rn(x0, sgn * sig);
+                    vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
+                }
+                // the products of this batch used x0 at row c when first, v0 otherwise;
+                // every lane reads row c of the targets before any lane updates it
+#pragma unroll
+                for (int i = 0; i < QB; ++i) {
+                    const int cc = cc0 + i;
+                    if (first && cc <= nJ) {
+                        const float* tgt = cc < nJ ? Ab + cc * nI : cv;
+                        part[i] = __fadd_rn(part[i], __fmul_rn(sgn * sig, tgt[c]));
+                    }
+                }
                 __syncwarp();
+#pragma unroll
+                for (int i = 0; i < QB; ++i) {
+                    const int cc = cc0 + i;
+                    if (cc <= nJ) {
+                        float* tgt = cc < nJ ? Ab + cc * nI : cv;
+                        const float tau = __fdiv_rn(__fmul_rn(2.0f, part[i]), vtv);
+                        for (int p = c + lane; p < nI; p += 32) {
+                            const float vp = p == c ? v0 : col_c[p];
+                            tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, vp));
+                        }
+                    }
+                }
+                __syncwarp();
+                if (first) {
+                    if (lane == 0) col_c[c] = v0;
+                    __syncwarp();
+                }
             }
+            if (rankdef) break;
             const float rcc = -sgn * sig;
             if (lane == 0) rdiag[c] = rcc;
             if (!(fabsf(rcc) > (float)nI * u_f * fro)) rankdef = true;
@@ -349,7 +416,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             for (int p = trp[l]; p < e; ++p) {
                 const int j = tcol[p];
                 if (contains(J, nJ, j)) continue;
-                const long long term = __float2ll_rn(__fmul_rn(__fmul_rn(sl, tval[p]), 1099511627776.0f));
+                const long long term = fix40(__fmul_rn(sl, tval[p]));
                 unsigned h = ((unsigned)j * 0x9E3779B1u) >> hshift;
                 int probe = 0;
                 for (; probe < H; ++probe) {
@@ -382,12 +449,12 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             const bool flag = v >= 0;
             float rj = 0.0f;
             if (flag) {
-                const float num = __fmul_rn(__ll2float_rn(acc[b0 + lane]), 9.094947017729282e-13f);  // 2^-40
+                const float num = unfix40(acc[b0 + lane]);
                 const float den = bnorm2[v];
                 float rr = r2sum;
                 if (den > 0.0f) rr = __fsub_rn(r2sum, __fdiv_rn(__fmul_rn(num, num), den));
                 rj = __fsqrt_rn(rr > 0.0f ? rr : 0.0f);
-                rsum += __float2ll_rn(__fmul_rn(rj, 1099511627776.0f));
+                rsum += fix40(rj);
                 tab[b0 + lane] = -1;
                 acc[b0 + lane] = 0;
             }
@@ -403,7 +470,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         __syncwarp();
         if (nc == 0) break;
-        const float mean = __fdiv_rn(__fmul_rn(__ll2float_rn(rsum), 9.094947017729282e-13f), (float)nc);
+        const float mean = __fdiv_rn(unfix40(rsum), (float)nc);
         // ---- up to beta picks: smallest rho (then smaller j) among rho <= mean
         int npick = 0;
         for (int r = 0; r < beta; ++r) {
