@@ -85,7 +85,6 @@ __host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, in
     return L;
 }
 
-constexpr int QB = 8;  // products reduced per batch of shuffles in the QR
 
 // x * 2^40 as a 64-bit integer, truncated toward zero (|x| < 2^22), from the
 // bits of x with integer operations only (64-bit float-integer conversions
@@ -289,77 +288,35 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         float fro = 0.0f;
         for (int t = lane; t < nJ * nI; t += 32) fro = __fadd_rn(fro, __fmul_rn(Ab[t], Ab[t]));
         fro = __fsqrt_rn(warp_sum(fro));
-        // Householder QR, applied to ebar as well.  For reflector c the norm of
-        // column c and its products with every later column (and ebar) are
-        // formed in one sweep with the unreflected x0 at row c, then reduced
-        // together (QB values per batch of shuffles), and corrected for v_c =
-        // x0 + sgn sig: v^T t = (x^T t) + sgn sig t_c.
+        // Householder QR with the sign choice v_1 = x_1 + sign(x_1) ||x||, applied
+        // to ebar as well; warp-shuffle reductions for every norm and product
         for (int c = 0; c < nJ && !rankdef; ++c) {
             float* col_c = Ab + c * nI;
+            float s2 = 0.0f;
+            for (int p = c + lane; p < nI; p += 32) s2 = __fadd_rn(s2, __fmul_rn(col_c[p], col_c[p]));
+            s2 = warp_sum(s2);
+            const float sig = __fsqrt_rn(s2);
             const float x0 = col_c[c];
-            float sgn = 1.0f, sig = 0.0f, vtv = 1.0f, v0 = 0.0f;
-            for (int cc0 = c + 1; cc0 <= nJ; cc0 += QB) {  // c + 1 <= nJ: ebar is target nJ
-                const bool first = cc0 == c + 1;
-                float part[QB + 1];
-#pragma unroll
-                for (int i = 0; i <= QB; ++i) part[i] = 0.0f;
-                for (int p = c + lane; p < nI; p += 32) {
-                    const float xp = col_c[p];
-                    if (first) part[QB] = __fadd_rn(part[QB], __fmul_rn(xp, xp));
-#pragma unroll
-                    for (int i = 0; i < QB; ++i) {
-                        const int cc = cc0 + i;
-                        if (cc <= nJ) {
-                            const float* tgt = cc < nJ ? Ab + cc * nI : cv;
-                            part[i] = __fadd_rn(part[i], __fmul_rn(xp, tgt[p]));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int i = 0; i <= QB; ++i) part[i] = __fadd_rn(part[i], __shfl_xor_sync(0xffffffffu, part[i], o));
-                }
-                if (first) {
-                    sig = __fsqrt_rn(part[QB]);
-                    if (!(sig > 0.0f)) {
-                        rankdef = true;
-                        break;
-                    }
-                    sgn = x0 >= 0.0f ? 1.0f : -1.0f;
-                    v0 = __fadd_rn(x0, sgn * sig);
-                    vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
-                }
-                // the products of this batch used x0 at row c when first, v0 otherwise;
-                // every lane reads row c of the targets before any lane updates it
-#pragma unroll
-                for (int i = 0; i < QB; ++i) {
-                    const int cc = cc0 + i;
-                    if (first && cc <= nJ) {
-                        const float* tgt = cc < nJ ? Ab + cc * nI : cv;
-                        part[i] = __fadd_rn(part[i], __fmul_rn(sgn * sig, tgt[c]));
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int i = 0; i < QB; ++i) {
-                    const int cc = cc0 + i;
-                    if (cc <= nJ) {
-                        float* tgt = cc < nJ ? Ab + cc * nI : cv;
-                        const float tau = __fdiv_rn(__fmul_rn(2.0f, part[i]), vtv);
-                        for (int p = c + lane; p < nI; p += 32) {
-                            const float vp = p == c ? v0 : col_c[p];
-                            tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, vp));
-                        }
-                    }
-                }
-                __syncwarp();
-                if (first) {
-                    if (lane == 0) col_c[c] = v0;
-                    __syncwarp();
-                }
+            if (!(sig > 0.0f)) {
+                rankdef = true;
+                break;
             }
-            if (rankdef) break;
+            const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
+            const float v0 = __fadd_rn(x0, sgn * sig);
+            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
+            const float twoinv = __fdiv_rn(2.0f, vtv);
+            __syncwarp();
+            if (lane == 0) col_c[c] = v0;
+            __syncwarp();
+            for (int cc = c + 1; cc <= nJ; ++cc) {
+                float* tgt = cc < nJ ? Ab + cc * nI : cv;
+                float dot = 0.0f;
+                for (int p = c + lane; p < nI; p += 32) dot = __fadd_rn(dot, __fmul_rn(col_c[p], tgt[p]));
+                dot = warp_sum(dot);
+                const float tau = __fmul_rn(dot, twoinv);
+                for (int p = c + lane; p < nI; p += 32) tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, col_c[p]));
+                __syncwarp();
+            }
             const float rcc = -sgn * sig;
             if (lane == 0) rdiag[c] = rcc;
             if (!(fabsf(rcc) > (float)nI * u_f * fro)) rankdef = true;
@@ -414,8 +371,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             const float sl = t < nI ? sv[t] : 0.0f;
             const int e = trp[l + 1];
             for (int p = trp[l]; p < e; ++p) {
-                const int j = tcol[p];
-                if (contains(J, nJ, j)) continue;
+                const int j = tcol[p];  // members of J are inserted too and skipped by the scan
                 const long long term = fix40(__fmul_rn(sl, tval[p]));
                 unsigned h = ((unsigned)j * 0x9E3779B1u) >> hshift;
                 int probe = 0;
@@ -446,17 +402,21 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         long long rsum = 0;
         for (int b0 = 0; b0 < H; b0 += 32) {
             const int v = tab[b0 + lane];
-            const bool flag = v >= 0;
+            const bool flag = v >= 0 && !contains(J, nJ, v);
             float rj = 0.0f;
+            long long av = 0;
+            if (v >= 0) {
+                av = acc[b0 + lane];
+                tab[b0 + lane] = -1;
+                acc[b0 + lane] = 0;
+            }
             if (flag) {
-                const float num = unfix40(acc[b0 + lane]);
+                const float num = unfix40(av);
                 const float den = bnorm2[v];
                 float rr = r2sum;
                 if (den > 0.0f) rr = __fsub_rn(r2sum, __fdiv_rn(__fmul_rn(num, num), den));
                 rj = __fsqrt_rn(rr > 0.0f ? rr : 0.0f);
                 rsum += fix40(rj);
-                tab[b0 + lane] = -1;
-                acc[b0 + lane] = 0;
             }
             const unsigned m = __ballot_sync(0xffffffffu, flag);
             if (flag) {
