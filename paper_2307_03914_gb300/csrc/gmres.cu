@@ -254,6 +254,7 @@ struct TagWords<double> {
     static constexpr int W = 2;
 };
 constexpr int kTagMaxBlocks = 160;  // slots read per lane: kTagMaxBlocks / 32 (152 SMs)
+constexpr int kMgsBlocks = 64;      // fewest blocks the on-chip MGS kernel is given
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -560,7 +561,7 @@ struct GmresWork {
     int u32 = 0;                         // working precision u = fp32: d and x rounded to fp32
     void* res_fn = nullptr;  // k_mgs_res instance, or null for k_mgs
     int res_bd = 1024;       // its block size
-    int Gr = 0;              // its grid: one block of 1024 threads per SM
+    int Gr = 0;              // its grid (at most one block per SM)
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
 
@@ -644,7 +645,17 @@ static void* pick_res(int64_t chunk, int* bd) {
 // thread of a 512-thread block.
 static int choose_mgs(GmresWork& W) {
     W.res_fn = nullptr;
-    const int Gr = W.sms;
+    // As few blocks as hold the rows of z on chip, but not fewer than kMgsBlocks: each
+    // grid reduction of the j + 2 per Arnoldi step waits for every block, and fewer
+    // blocks shorten it (measured per pass, n = 65,536 / 262,144: 2.5 / 3.1 us at 152
+    // blocks, 1.6 / 1.9 us at 64) while one block still streams its rows faster than
+    // the reduction completes.
+    // rows per block of the largest instance (a 768-thread instance holding 22,272 rows
+    // spilled registers and made the 128^3 solve 19 % slower at 95 blocks than at 128)
+    const int64_t cap = W.ug == BSPAI_FP64 ? 8192 : 16384;
+    int Gr = (int)ceil_div(W.n, cap);
+    if (Gr < kMgsBlocks) Gr = kMgsBlocks;
+    if (Gr > W.sms) Gr = W.sms;
     if (Gr > kTagMaxBlocks) return BSPAI_OK;
     const int64_t chunk = ceil_div(ceil_div(W.n, Gr), 32) * 32;
     const size_t es = W.ug == BSPAI_FP64 ? 8 : 4;
