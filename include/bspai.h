@@ -311,7 +311,9 @@ int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, b
 
 /* bspai_gmres with A v by the adaptive-precision SpMV on A's buckets
  * (bspai_bucket_A) instead of A in u_p (eq. nbe2); products accumulated as in
- * bspai_apply, results rounded to u_g. */
+ * bspai_apply, results rounded to u_g.  A_bucketed must hold A's n rows (a
+ * missing handle, another handle kind or another size: BSPAI_ERR_INVALID);
+ * the other arguments and the returns are those of bspai_gmres. */
 int bspai_gmres_b(bspai_A_h A, bspai_BM_h A_bucketed, bspai_BM_h BM, const double* r, bspai_prec_t u_g,
                   const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
 
@@ -427,7 +429,9 @@ int gmres_ir_solve_h(bspai_A_h A, const double* b, bspai_BM_h M_bucketed, bspai_
 
 /* gmres_ir_solve_h with A v inside GMRES by the adaptive-precision SpMV on A's
  * buckets (bspai_bucket_A; Section 3, eq. nbe2 and fe2).  The residual still
- * uses A's fp64 values in u_r; x0 = M b in u_f; u_p is replaced by the buckets. */
+ * uses A's fp64 values in u_r; x0 = M b in u_f; u_p is replaced by the buckets
+ * (u_g is used for both).  A_bucketed must hold A's n rows (else
+ * BSPAI_ERR_INVALID); precisions, vectors and returns as gmres_ir_solve. */
 int gmres_ir_solve_hb(bspai_A_h A, bspai_BM_h A_bucketed, const double* b, bspai_BM_h M_bucketed, bspai_M_h M,
                       bspai_prec_t u, bspai_prec_t u_r, bspai_prec_t u_g, double tol, const bspai_opts_t* opts,
                       double* x, bspai_stream_t s, bspai_solve_info_t* info);

@@ -167,3 +167,25 @@ def test_ir_single_fp64_bucket_equals_up_fp64(B, wl):
 def test_bucket_A_rejects_bad_handle(B):
     with pytest.raises(Exception):
         B.bucket_A(B.AHandle(0), 2.0 ** -16, ["fp32"])
+
+
+def test_bucketed_A_of_another_size_rejected(B):
+    """A bucketed matrix with a different number of rows is refused before any
+    launch, and the context stays usable."""
+    wl0, wl1 = WLS[0], WLS[1]
+    A0 = wl0["A"]
+    Ah0 = B.matrix_create(B.DeviceCSR.from_host(A0))
+    Ah1 = B.matrix_create(B.DeviceCSR.from_host(wl1["A"]))
+    BA1, _ = B.bucket_A(Ah1, 2.0 ** -16, ["fp64"])
+    BA0, _ = B.bucket_A(Ah0, 2.0 ** -16, ["fp64"])
+    g = gpu_build(B, wl0)
+    bm = gpu_bucket(B, g["M"], wl0["pattern"].nnz, 2.0 ** -16, wl0["precs"])
+    r = dev(wl0["b"])
+    d = torch.empty(A0.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(Exception):
+        B.gmres_b(Ah0, BA1, bm["BM"], r, d)
+    x = torch.empty(A0.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(Exception):
+        B.gmres_ir_solve_hb(Ah0, BA1, r, bm["BM"], g["M"], x, tol=wl0["tau"])
+    info = B.gmres_ir_solve_hb(Ah0, BA0, r, bm["BM"], g["M"], x, tol=wl0["tau"])
+    assert info["status"] == 0
