@@ -538,6 +538,122 @@ __global__ void k_absmax(int n, const double* __restrict__ v, double* __restrict
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, a);
 }
 
+// k_mgs_res for fp32 with the rows of a thread taken in adjacent pairs: every
+// multiply and add is a packed two-lane fp32 operation (each lane correctly
+// rounded, no fused multiply-add: the same arithmetic per element), the
+// shared-memory z and the basis rows move as float2, and the thread's partial
+// sum is carried in two lanes that are added at the end.  P pairs per thread;
+// the rows of a block are its contiguous chunk (an even start, at most one
+// unpaired last row).
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+template <int P, int BD>
+__global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64_t ldv, int n, GmresState* st,
+                                                      double* H, double* cs, double* sn, double* g,
+                                                      unsigned long long* tags, unsigned long long tmo) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2* zs = reinterpret_cast<float2*>(smraw);
+    __shared__ float s_w[32];
+    __shared__ float s_tot;
+    __shared__ unsigned s_seq;
+    __shared__ int s_ok, s_j, s_done, s_kmax;
+    if (threadIdx.x == 0) {
+        s_j = st->j;
+        s_done = st->done;
+        s_kmax = st->kmax;
+        s_seq = *(volatile unsigned*)&st->bar.seq;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int j = s_j, kmax = s_kmax;
+    const unsigned seq0 = s_seq;
+    int64_t r0, r1;
+    block_rows(n, r0, r1);
+    const int nb = r1 > r0 ? (int)(r1 - r0) : 0;
+    const int tid = threadIdx.x;
+    // pair q covers rows 2q, 2q + 1 of the chunk; the second may lie past nb
+    auto ld2 = [&](const float* p, int q) -> float2 {
+        if (2 * q + 1 < nb) return *reinterpret_cast<const float2*>(p + 2 * q);
+        return make_float2(p[2 * q], 0.0f);
+    };
+    float* z = V + (int64_t)(j + 1) * ldv + r0;
+    const float* v0 = V + r0;
+    float2 vcur[P], vnext[P];
+    const float2 zero2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const int q = tid + t * BD;
+        vcur[t] = zero2;
+        vnext[t] = zero2;
+        if (2 * q < nb) {
+            zs[q] = ld2(z, q);
+            vcur[t] = ld2(v0, q);
+        }
+    }
+    float2 acc2 = zero2;
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const int q = tid + t * BD;
+        if (2 * q < nb) acc2 = __fadd2_rn(acc2, __fmul2_rn(vcur[t], zs[q]));
+    }
+    tag_arrive(__fadd_rn(acc2.x, acc2.y), tags, 0, seq0 + 1u, s_w);
+    for (int i = 1; i <= j + 1; ++i) {
+        if (i <= j) {
+            const float* vi = V + (int64_t)i * ldv + r0;
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int q = tid + t * BD;
+                if (2 * q < nb) vnext[t] = ld2(vi, q);
+            }
+        }
+        const float h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok);
+        if (!s_ok) {
+            if (blockIdx.x == 0 && tid == 0) {
+                st->status = BSPAI_TIMEOUT;
+                st->done = 1;
+            }
+            return;
+        }
+        if (blockIdx.x == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
+        const float2 h2 = make_float2(h, h);
+        acc2 = zero2;
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const int q = tid + t * BD;
+            if (2 * q < nb) {
+                const float2 zr = f2_sub(zs[q], __fmul2_rn(h2, vcur[t]));
+                zs[q] = zr;
+                acc2 = __fadd2_rn(acc2, __fmul2_rn(i <= j ? vnext[t] : zr, zr));
+            }
+        }
+        tag_arrive(__fadd_rn(acc2.x, acc2.y), tags, i & 1, seq0 + (unsigned)i + 1u, s_w);
+#pragma unroll
+        for (int t = 0; t < P; ++t) vcur[t] = vnext[t];
+    }
+    const float hz = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok);
+    if (!s_ok) {
+        if (blockIdx.x == 0 && tid == 0) {
+            st->status = BSPAI_TIMEOUT;
+            st->done = 1;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && tid == 0) st->bar.seq = seq0 + (unsigned)j + 2u;
+    const float hn = __fsqrt_rn(hz);
+    const bool norm = hn > 0.0f && isfinite((double)hn);
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const int q = tid + t * BD;
+        if (2 * q < nb) {
+            float2 zr = zs[q];
+            if (norm) zr = make_float2(__fdiv_rn(zr.x, hn), __fdiv_rn(zr.y, hn));
+            if (2 * q + 1 < nb) *reinterpret_cast<float2*>(z + 2 * q) = zr;
+            else z[2 * q] = zr.x;
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
+}
+
 // ---------------------------------------------------------------- host side
 struct HostFlags {
     int j, done, status, kmax;
@@ -627,6 +743,19 @@ static void* pick_res(int64_t chunk, int* bd) {
     const int R = (int)ceil_div(chunk, 1024);
     *bd = 1024;
     if (R <= 1) return (void*)k_mgs_res<T, 1, 1024>;
+    if constexpr (sizeof(T) == 4) {
+        // fp32: rows in adjacent pairs, packed two-lane arithmetic
+        if (R <= 2) return (void*)k_mgs_res2<1, 1024>;
+        if (R <= 4) return (void*)k_mgs_res2<2, 1024>;
+        if (R <= 8) return (void*)k_mgs_res2<4, 1024>;
+        const int Rp = (int)ceil_div(chunk, 512);
+        *bd = 512;
+        if (Rp <= 16) return (void*)k_mgs_res2<8, 512>;
+        if (Rp <= 24) return (void*)k_mgs_res2<12, 512>;
+        if (Rp <= 28) return (void*)k_mgs_res2<14, 512>;
+        if (Rp <= 32) return (void*)k_mgs_res2<16, 512>;
+        return nullptr;
+    }
     if (R <= 2) return (void*)k_mgs_res<T, 2, 1024>;
     if (R <= 4) return (void*)k_mgs_res<T, 4, 1024>;
     if (R <= 8) return (void*)k_mgs_res<T, 8, 1024>;
