@@ -779,8 +779,10 @@ static int choose_mgs(GmresWork& W) {
     // blocks shorten it (measured per pass, n = 65,536 / 262,144: 2.5 / 3.1 us at 152
     // blocks, 1.6 / 1.9 us at 64) while one block still streams its rows faster than
     // the reduction completes.
-    // rows per block of the largest instance (a 768-thread instance holding 22,272 rows
-    // spilled registers and made the 128^3 solve 19 % slower at 95 blocks than at 128)
+    // rows per block of the largest instance.  At 128^3 fewer blocks stopped paying: 103
+    // blocks of 40 fp32 rows per thread solved in 90.8 ms against 87.7 ms at 128 blocks of
+    // 32 (the longer per-block update outweighs the shorter reduction), and a scalar
+    // 768-thread instance (22,272 rows, register spills) took 107.6 ms at 95 blocks.
     const int64_t cap = W.ug == BSPAI_FP64 ? 8192 : 16384;
     int Gr = (int)ceil_div(W.n, cap);
     if (Gr < kMgsBlocks) Gr = kMgsBlocks;
