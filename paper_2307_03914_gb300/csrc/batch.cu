@@ -92,14 +92,22 @@ __device__ __forceinline__ double block_max(double v, double* s_w) {
 // Givens rotations on column j of H, update of g, tau test (fp64); thread 0
 __device__ void givens_pair(int j, int kmax, double hn, double* H, double* cs, double* sn, double* g, double tau,
                             double beta, double* res, int* done) {
-    double* hc = H + (int64_t)j * (kmax + 1);
+    double* __restrict__ hc = H + (int64_t)j * (kmax + 1);
+    const double* __restrict__ c_ = cs;
+    const double* __restrict__ s_ = sn;
     hc[j + 1] = hn;
+    // the previous rotations applied to the new column; the entry each rotation hands
+    // to the next stays in a register, so only the running value is a dependent chain
+    // (the stored coefficients and column entries are independent loads)
+    double carry = j > 0 ? hc[0] : 0.0;
     for (int i = 0; i < j; ++i) {
-        const double t1 = __dadd_rn(__dmul_rn(cs[i], hc[i]), __dmul_rn(sn[i], hc[i + 1]));
-        const double t2 = __dadd_rn(__dmul_rn(-sn[i], hc[i]), __dmul_rn(cs[i], hc[i + 1]));
+        const double ci = c_[i], si = s_[i], hi1 = hc[i + 1];
+        const double t1 = __dadd_rn(__dmul_rn(ci, carry), __dmul_rn(si, hi1));
+        const double t2 = __dadd_rn(__dmul_rn(-si, carry), __dmul_rn(ci, hi1));
         hc[i] = t1;
-        hc[i + 1] = t2;
+        carry = t2;
     }
+    if (j > 0) hc[j] = carry;
     const double a = hc[j], b = hc[j + 1];
     const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
     double c = 1.0, s = 0.0;
