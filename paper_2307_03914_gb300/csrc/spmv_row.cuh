@@ -123,15 +123,27 @@ __device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c,
 // y_i = sum_k y_i^(k) for row r of a bucketed matrix: each bucket's partial sum
 // in ascending column order (fp64 for an fp64 bucket, fp32 otherwise), the
 // partial sums added in fp64 in bucket order.
+// The slot range of bucket k + 1 is loaded while bucket k's partial sum is
+// formed, so a row's dependent loads are the first range, then per bucket its
+// column indices and x entries.
 template <typename XT>
 __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const XT* __restrict__ x) {
     const int64_t s = r >> 5;
     const int lane = (int)(r & 31);
     double yi = 0.0;
+    int64_t pn = 0, en = 0;
+    if (M.q > 0) {
+        pn = M.b[0].sptr[s] + lane;
+        en = M.b[0].sptr[s + 1];
+    }
     for (int k = 0; k < M.q; ++k) {
         const BucketDev& B = M.b[k];
-        const int64_t p0 = B.sptr[s] + lane;
-        const int64_t end = B.sptr[s + 1];
+        const int64_t p0 = pn;
+        const int64_t end = en;
+        if (k + 1 < M.q) {
+            pn = M.b[k + 1].sptr[s] + lane;
+            en = M.b[k + 1].sptr[s + 1];
+        }
         switch (B.prec) {
         case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT>(B, p0, end, x)); break;
         case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, p0, end, x, r)); break;
