@@ -130,7 +130,16 @@ __device__ void givens_pair(int j, int kmax, double hn, double* H, double* cs, d
 // striding over them (kept out of line: the kernel calls it three times)
 template <typename XT, typename YT>
 __device__ __noinline__ void rows_apply(const BMDev& M, int r0, int ns, const XT* __restrict__ x, YT* __restrict__ y) {
-    for (int lr = threadIdx.x; lr < ns; lr += blockDim.x) y[lr] = from_f64<YT>(bucketed_row<XT>(M, r0 + lr, x));
+    // two rows per thread at a time (lr and lr + blockDim.x): two independent gather chains
+    const int bd = blockDim.x;
+    int lr = threadIdx.x;
+    for (; lr + bd < ns; lr += 2 * bd) {
+        double ya, yb;
+        bucketed_row2<XT>(M, r0 + lr, r0 + lr + bd, x, ya, yb);
+        y[lr] = from_f64<YT>(ya);
+        y[lr + bd] = from_f64<YT>(yb);
+    }
+    if (lr < ns) y[lr] = from_f64<YT>(bucketed_row<XT>(M, r0 + lr, x));
 }
 
 // rows per thread whose loads an MGS pass issues together

@@ -156,6 +156,105 @@ __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const 
     return yi;
 }
 
+// Two rows at once (rows ra and rb, in slices of their own): the same partial
+// sums as row_partial_f32 / row_partial_f64 for each row, in the same order,
+// with the loads of both rows issued together so that each thread keeps two
+// independent chains of gathers in flight.
+template <int PREC, typename XT>
+__device__ __forceinline__ void row_partial2_f32(const BucketDev& B, int64_t pa, int64_t ea, int64_t pb, int64_t eb,
+                                                 const XT* __restrict__ x, int64_t ra, int64_t rb, float& acc_a,
+                                                 float& acc_b) {
+    const float* st = B.colscale ? B.colscale : B.rowscale;
+    const float sca = B.slicescale ? __ldg(B.slicescale + (ra >> 5)) : B.scale;
+    const float scb = B.slicescale ? __ldg(B.slicescale + (rb >> 5)) : B.scale;
+    float aa = 0.0f, ab = 0.0f;
+    for (; pa < ea || pb < eb; pa += 64, pb += 64) {
+        int c[4];
+        c[0] = pa < ea ? __ldg(B.col + pa) : -1;
+        c[1] = pa + 32 < ea ? __ldg(B.col + pa + 32) : -1;
+        c[2] = pb < eb ? __ldg(B.col + pb) : -1;
+        c[3] = pb + 32 < eb ? __ldg(B.col + pb + 32) : -1;
+        float v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] >= 0) {
+                const int64_t p = u < 2 ? pa + 32 * u : pb + 32 * (u - 2);
+                const int64_t r = u < 2 ? ra : rb;
+                v[u] = decode<PREC>(B.val, p, u < 2 ? sca : scb, st, B.colscale ? c[u] : (int)r);
+                xv[u] = to_f32<XT>(__ldg(x + c[u]));
+            }
+        }
+        if (c[0] >= 0) aa = __fadd_rn(aa, __fmul_rn(v[0], xv[0]));
+        if (c[1] >= 0) aa = __fadd_rn(aa, __fmul_rn(v[1], xv[1]));
+        if (c[2] >= 0) ab = __fadd_rn(ab, __fmul_rn(v[2], xv[2]));
+        if (c[3] >= 0) ab = __fadd_rn(ab, __fmul_rn(v[3], xv[3]));
+    }
+    acc_a = aa;
+    acc_b = ab;
+}
+
+template <typename XT>
+__device__ __forceinline__ void row_partial2_f64(const BucketDev& B, int64_t pa, int64_t ea, int64_t pb, int64_t eb,
+                                                 const XT* __restrict__ x, double& acc_a, double& acc_b) {
+    const double* val = reinterpret_cast<const double*>(B.val);
+    double aa = 0.0, ab = 0.0;
+    for (; pa < ea || pb < eb; pa += 64, pb += 64) {
+        int c[4];
+        c[0] = pa < ea ? __ldg(B.col + pa) : -1;
+        c[1] = pa + 32 < ea ? __ldg(B.col + pa + 32) : -1;
+        c[2] = pb < eb ? __ldg(B.col + pb) : -1;
+        c[3] = pb + 32 < eb ? __ldg(B.col + pb + 32) : -1;
+        double v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] >= 0) {
+                const int64_t p = u < 2 ? pa + 32 * u : pb + 32 * (u - 2);
+                v[u] = __ldg(val + p);
+                xv[u] = (double)__ldg(x + c[u]);
+            }
+        }
+        if (c[0] >= 0) aa = __dadd_rn(aa, __dmul_rn(v[0], xv[0]));
+        if (c[1] >= 0) aa = __dadd_rn(aa, __dmul_rn(v[1], xv[1]));
+        if (c[2] >= 0) ab = __dadd_rn(ab, __dmul_rn(v[2], xv[2]));
+        if (c[3] >= 0) ab = __dadd_rn(ab, __dmul_rn(v[3], xv[3]));
+    }
+    acc_a = aa;
+    acc_b = ab;
+}
+
+// bucketed_row for two rows at once (the same sums, bucket by bucket in order)
+template <typename XT>
+__device__ __forceinline__ void bucketed_row2(const BMDev& M, int64_t ra, int64_t rb, const XT* __restrict__ x,
+                                              double& ya, double& yb) {
+    const int64_t sa = ra >> 5, sb = rb >> 5;
+    const int la = (int)(ra & 31), lb = (int)(rb & 31);
+    double ta = 0.0, tb = 0.0;
+    for (int k = 0; k < M.q; ++k) {
+        const BucketDev& B = M.b[k];
+        const int64_t pa = B.sptr[sa] + la, ea = B.sptr[sa + 1];
+        const int64_t pb = B.sptr[sb] + lb, eb = B.sptr[sb + 1];
+        if (B.prec == BSPAI_FP64) {
+            double a, b;
+            row_partial2_f64<XT>(B, pa, ea, pb, eb, x, a, b);
+            ta = __dadd_rn(ta, a);
+            tb = __dadd_rn(tb, b);
+            continue;
+        }
+        float a = 0.0f, b = 0.0f;
+        switch (B.prec) {
+        case BSPAI_FP32: row_partial2_f32<BSPAI_FP32, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_FP16: row_partial2_f32<BSPAI_FP16, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_BF16: row_partial2_f32<BSPAI_BF16, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_E4M3: row_partial2_f32<BSPAI_E4M3, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        default: continue;  // dropped entries are not stored
+        }
+        ta = __dadd_rn(ta, (double)a);
+        tb = __dadd_rn(tb, (double)b);
+    }
+    ya = ta;
+    yb = tb;
+}
+
 // Buckets that contribute nothing (dropped, or with no entries) are left out:
 // their partial sums are +0 and adding +0 to a sum that is never -0 changes nothing.
 inline BMDev compact_buckets(const BMDev& M) {
