@@ -21,13 +21,16 @@
 // bounds the shared memory of one column.
 //
 // One warp per column, everything in u_f = fp32 as in the fixed-pattern
-// kernel: the gathered rows of A, the shadow (bitonic sort + ballot
-// compaction), Abar in shared memory, the Householder QR with warp-shuffle
-// reductions, back substitution, sbar from the gathered entries, the
-// candidate set (gather of A^T rows over L_k, bitonic sort, compaction of the
-// distinct values not in J_k), rho per candidate (one lane per candidate),
-// the mean, and beta rounds of a warp argmin for the picks.  Every loop has a
-// bound set by jmax, lmax or the host-computed buffer sizes.
+// kernel: the gathered rows of A (B's fp32 values precomputed once), the
+// shadow (bitonic sort + ballot compaction), Abar in shared memory, the
+// Householder QR with warp-shuffle reductions, back substitution, sbar from
+// the gathered entries; the candidates by one sweep over the rows of B in I_k
+// into an open-addressing hash table that also accumulates sbar^T B(I_k, j)
+// in exact fixed point, rho per candidate from that sum and the precomputed
+// ||B e_j||^2, the mean as a fixed-point sum, and beta rounds of a warp argmin
+// over (rho, j) for the picks.  Every loop has a bound set by jmax, lmax or
+// the host-computed buffer sizes.  Two launches (tiers) share the kernel; see
+// k_spai_adaptive.
 #include <climits>
 
 #include "common.cuh"
