@@ -17,7 +17,6 @@ import torch
 
 import oracle as O
 from gpu_helpers import dev, gpu_bucket, gpu_build, host, lib, oracle_M, small_workloads, spai_tolerance
-from paper_2307_03914_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
