@@ -112,8 +112,8 @@ def _declare(L):
                             _f64p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.orc_gmres.restype = C.c_int
     L.orc_gmres_ir.argtypes = [C.POINTER(_System), _f64p, _f64p, C.c_int, C.c_int, C.c_double,
-                               C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, _f64p, _i32p,
-                               _f64p, _f64p, C.POINTER(C.c_int)]
+                               C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _f64p,
+                               _i32p, _f64p, _f64p, C.POINTER(C.c_int)]
     L.orc_gmres_ir.restype = C.c_int
 
 
@@ -362,13 +362,17 @@ UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
 
 
 def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, imax=10,
-             u_work=None, x0=None, u="fp64", u_r="dd") -> dict:
+             u_work=None, x0=None, u="fp64", u_r="dd", u_f="fp32") -> dict:
     """Alg 3.1 with working precision u (fp64, or fp32 for the (single,
-    single, double) setting of Section 4) and residual precision u_r ("dd":
-    Dot2, about twice fp64; "fp64": plain fp64).  x, r and the correction are
-    held in u; u_work (the stopping level) defaults to u's unit roundoff."""
+    single, double) and (half, single, double) settings of Section 4) and
+    residual precision u_r ("dd": Dot2, about twice fp64; "fp64": plain fp64).
+    x0 = M b is taken in u_f arithmetic (fp32, or fp16 with its own range) on
+    the values muf, which the caller holds in u_f.  x, r and the correction
+    are held in u; u_work (the stopping level) defaults to u's unit roundoff."""
     if u not in UNIT_ROUNDOFF or u_r not in ("dd", "fp64"):
         raise ValueError("u must be fp64 or fp32, u_r dd or fp64")
+    if u_f not in ("fp32", "fp16"):
+        raise ValueError("u_f must be fp32 or fp16")
     u_work = UNIT_ROUNDOFF[u] if u_work is None else u_work
     x = np.zeros(system.n) if x0 is None else _f64(x0).copy()
     its = np.zeros(imax, dtype=np.int32)
@@ -376,7 +380,7 @@ def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, i
     dx = np.zeros(imax)
     stop = C.c_int(0)
     steps = lib().orc_gmres_ir(C.byref(system.s), _f64(muf), _f64(b), FMT[ug], FMT[up], tau,
-                               int(kmax), int(imax), u_work, FMT[u], int(u_r == "dd"),
+                               int(kmax), int(imax), u_work, FMT[u], int(u_r == "dd"), FMT[u_f],
                                int(x0 is not None), x, its, nbe, dx, C.byref(stop))
     nsteps = min(imax, steps + (1 if stop.value == 1 else 0))
     return dict(x=x, steps=steps, its=its[:max(steps, 0)].tolist(), nbe=nbe[:nsteps].tolist(),
@@ -416,7 +420,7 @@ def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
 
 
 def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False, u="fp64",
-          u_r="dd", ug=None, up=None, adaptive=None) -> dict:
+          u_r="dd", ug=None, up=None, adaptive=None, u_f="fp32") -> dict:
     """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR.
     bucket_A: A v inside GMRES by the bucketed SpMV on A's own buckets (same
     precisions and bucket_eps, thresholds from ||A||_inf; eq. nbe2).
@@ -428,7 +432,7 @@ def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bu
     else:  # adaptive: dict(spai_eps, alpha, beta[, imax_rows]) -- Alg 2.1 from the identity pattern
         sp = spai_adaptive(A, **adaptive)
         P = _Csr(A.n, sp["row_ptr"], sp["col"], None)
-    muf = round_to(sp["mval"], "fp32")  # M is held in u_f = fp32
+    muf = round_to(sp["mval"], u_f)  # M is held in u_f (fp32, or fp16 for the (half, single, double) setting)
     precs = wl["precs"] if precs is None else precs
     be = wl["bucket_eps"] if bucket_eps is None else bucket_eps
     bk = bucket_ids(P.row_ptr, muf, be, precs)
@@ -440,6 +444,6 @@ def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bu
         a_stored, _, _ = bucket_store(A.row_ptr, A.col, A.val, a_ids, precs)
     S = System(A, P.row_ptr, P.col, stored, bk["ids"], precs, a_stored, a_ids)
     out = gmres_ir(S, muf, wl["b"], wl["u_g"] if ug is None else ug, wl["u_p"] if up is None else up,
-                   wl["tau"] if tau is None else tau, kmax, imax, u=u, u_r=u_r)
+                   wl["tau"] if tau is None else tau, kmax, imax, u=u, u_r=u_r, u_f=u_f)
     out.update(spai=sp, muf=muf, buckets=bk, stored=stored)
     return out

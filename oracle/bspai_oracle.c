@@ -829,13 +829,13 @@ static double vnorm_inf(int n, const double* v) {
 
 int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
                  int ug, int up, double tau, int kmax, int imax, double u_work,
-                 int uw, int ur_dd,
+                 int uw, int ur_dd, int uf,
                  int x0_given, double* x, int* its, double* nbe, double* dx, int* stop) {
     int n = S->n;
     double* r = (double*)malloc(sizeof(double) * (size_t)n);
     double* d = (double*)malloc(sizeof(double) * (size_t)n);
-    /* x0 = M b with the unbucketed M in u_f = fp32, stored in fp64 */
-    if (!x0_given) orc_spmv_prec(n, S->mrp, S->mci, muf, ORC_FP32, b, x);
+    /* x0 = M b with the unbucketed M (values muf) in u_f arithmetic, stored in fp64 */
+    if (!x0_given) orc_spmv_prec(n, S->mrp, S->mci, muf, uf, b, x);
     /* x is held in the working precision u */
     for (int t = 0; t < n; ++t) x[t] = rf(x[t], uw);
     double anorm = orc_norm_inf(n, S->arp, S->av);

@@ -145,7 +145,8 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
               double* d, int* iters, double* relres);
 
 /* BSPAI-GMRES-IR driver (Alg 3.1 after the SPAI build).
- *   x0 = M b with the unbucketed M (values muf, fp32 arithmetic) unless x0_given,
+ *   x0 = M b with the unbucketed M (values muf, arithmetic in u_f = format uf:
+ *   ORC_FP32 or ORC_FP16) unless x0_given,
  *   rounded to the working precision u (format uw: ORC_FP64 or ORC_FP32);
  *   loop i < imax: r = b - A x in u_r (ur_dd = 1: Dot2, u_r ~ u^2; 0: plain
  *   fp64), rounded to u; nbe = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf);
@@ -156,7 +157,7 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
  * 0 (imax). */
 int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
                  int ug, int up, double tau, int kmax, int imax, double u_work,
-                 int uw, int ur_dd, int x0_given, double* x, int* its, double* nbe, double* dx, int* stop);
+                 int uw, int ur_dd, int uf, int x0_given, double* x, int* its, double* nbe, double* dx, int* stop);
 
 #ifdef __cplusplus
 }

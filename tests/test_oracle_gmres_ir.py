@@ -262,3 +262,65 @@ def test_gmres_ir_rejects_unknown_working_precision(orc):
     wl = W.workload("convdiff2d", grid=6)
     with pytest.raises(ValueError):
         orc.solve(wl, u="fp16")
+
+
+def _half_textbook_spmv(P, val, b):
+    """Row sums in IEEE half with numpy's float16 type: each product and partial
+    sum is one half-precision operation, columns in ascending order."""
+    y = np.zeros(P.n)
+    for i in range(P.n):
+        acc = np.float16(0.0)
+        for p in range(P.row_ptr[i], P.row_ptr[i + 1]):
+            acc = np.float16(acc + np.float16(np.float16(val[p]) * np.float16(b[P.col[p]])))
+        y[i] = float(acc)
+    return y
+
+
+def test_x0_in_half_is_the_textbook_half_product(orc):
+    """(half, single, double): x0 = M b with M held in u_f = half and the
+    product taken in half (Alg 3.1, first lines), then held in u = fp32."""
+    wl = W.workload("convdiff2d", grid=8)
+    A, P = wl["A"], wl["pattern"]
+    sp_ = orc.spai(A, P, wl["spai_eps"])
+    m16 = orc.round_to(sp_["mval"], "fp16")
+    assert np.array_equal(m16, sp_["mval"].astype(np.float16).astype(np.float64))
+    ref = _half_textbook_spmv(P, m16, wl["b"])
+    assert np.array_equal(orc.spmv_prec(P.row_ptr, P.col, m16, "fp16", wl["b"]), ref)
+    ids = orc.bucket_ids(P.row_ptr, m16, 2.0 ** -24, SSD["precs"])["ids"]
+    stored, _, _ = orc.bucket_store(P.row_ptr, P.col, m16, ids, SSD["precs"])
+    S = orc.System(A, P.row_ptr, P.col, stored, ids, SSD["precs"])
+    out = orc.gmres_ir(S, m16, wl["b"], "fp32", "fp32", 1e-4, 500, 0, u="fp32", u_r="fp64", u_f="fp16")
+    assert np.array_equal(out["x"], ref)
+    # and the fp32 default is the same product in single
+    out = orc.gmres_ir(S, m16, wl["b"], "fp32", "fp32", 1e-4, 500, 0, u="fp32", u_r="fp64")
+    assert np.array_equal(out["x"], orc.spmv_prec(P.row_ptr, P.col, m16, "fp32", wl["b"]))
+    assert not np.array_equal(out["x"], ref)
+
+
+HSD = dict(SSD, u_f="fp16")
+
+
+@pytest.mark.parametrize("name,grid", [("convdiff2d", 32), ("convdiff3d", 8)])
+@pytest.mark.parametrize("eps", [2.0 ** -24, 2.0 ** -18])
+def test_ir_half_single_double_reaches_single_accuracy(orc, name, grid, eps):
+    """(u_f, u, u_r) = (half, single, double) (Section 4): M held in half, x0
+    in half; kappa_inf(A) of these systems is far below u^-1/3 u_f^-2/3 (about
+    4e4), so GMRES-IR reaches the level of u = 2^-24 as in the single setting,
+    with x held in fp32."""
+    wl = W.workload(name, grid=grid)
+    out = orc.solve(wl, bucket_eps=eps, **HSD)
+    x, xt = out["x"], wl["x_true"]
+    assert np.array_equal(out["muf"], out["muf"].astype(np.float16).astype(np.float64))
+    assert np.array_equal(x, x.astype(np.float32).astype(np.float64))
+    assert np.abs(x - xt).max() / np.abs(xt).max() <= 2 * 2.0 ** -24
+    assert out["stop"] in (1, 2, 3)
+    # the half-precision M is a weaker preconditioner than the single one: never fewer
+    # refinement steps than u_f = fp32 needs
+    ref = orc.solve(wl, bucket_eps=eps, **SSD)
+    assert out["steps"] >= ref["steps"] - 1
+
+
+def test_gmres_ir_rejects_unknown_u_f(orc):
+    wl = W.workload("convdiff2d", grid=6)
+    with pytest.raises(ValueError):
+        orc.solve(wl, u="fp32", u_r="fp64", u_f="bf16")
