@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-comparator", action="store_true")
     p.add_argument("--no-bucketed-A", action="store_true")
     p.add_argument("--no-single", action="store_true")
+    p.add_argument("--no-half", action="store_true")
     p.add_argument("--no-adaptive", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--kmax", type=int, default=0, help="cap on GMRES steps per refinement step (0: library default)")
@@ -504,12 +505,12 @@ def main():
                              "profile_ms": {c: aprof[c][0] for c in aprof}}
         Ah.free()
 
-    # ---------------- (u_f, u, u_r) = (single, single, double), buckets {fp32, fp16, drop} (Section 4)
-    if not args.no_single:
+    # ---------------- (u_f, u, u_r) = (single | half, single, double), buckets {fp32, fp16, drop} (Section 4)
+    def run_u32_setting(u_f):
         sres = []
         for eps in (2.0 ** -24, 2.0 ** -18):
             def step_s(x):
-                M, _ = B.bspai_build(Ad, Pd, wl["spai_eps"])
+                M, _ = B.bspai_build(Ad, Pd, wl["spai_eps"], u_f=u_f)
                 BM, sinfo = B.bspai_bucket(M, eps, ["fp32", "fp16", "drop"])
                 inf = B.gmres_ir_solve(Ad, bd, BM, M, x, u="fp32", u_r="fp64", u_g="fp32", u_p="fp32", tol=1e-4,
                                        o=B.opts(tau=1e-4, kmax=args.kmax))
@@ -532,9 +533,17 @@ def main():
             sres.append({"bucket_eps": eps, "solves_per_s": (1.0 if good else 0.0) / (sms_ / 1000.0),
                          "ms_per_solve": sms_, "gmres_iters": sinf["gmres_iters"], "fwd_err": sfe,
                          "bucket_nnz": sinfo["nnz_k"], "storage_pct_of_fp32": sinfo["storage_pct"]})
+        return sres
+
+    if not args.no_single:
         out["single_single_double"] = {"what": "u_f = u = fp32, u_r = fp64, u_g = u_p = fp32, tau = 1e-4, "
                                                "buckets {fp32, fp16, drop}; solves reaching forward error <= 4u = 2^-22",
-                                       "runs": sres}
+                                       "runs": run_u32_setting("fp32")}
+    if not args.no_half:
+        out["half_single_double"] = {"what": "u_f = fp16 (SPAI in half, M held in half, x0 in half), u = fp32, "
+                                             "u_r = fp64, u_g = u_p = fp32, tau = 1e-4, buckets {fp32, fp16, drop}; "
+                                             "solves reaching forward error <= 4u = 2^-22",
+                                     "runs": run_u32_setting("fp16")}
 
     # ---------------- adaptive SPAI (Alg 2.1, alpha = 3, beta = 8, from the identity pattern) + the same solve
     if not args.no_adaptive:

@@ -71,7 +71,7 @@ typedef struct {
 } bspai_csr_t;
 
 typedef struct bspai_matrix* bspai_A_h;   /* A prepared for the GPU kernels */
-typedef struct bspai_spai* bspai_M_h;     /* M = SPAI(A) held in u_f = fp32 */
+typedef struct bspai_spai* bspai_M_h;     /* M = SPAI(A) held in u_f (fp32 or fp16) */
 typedef struct bspai_bucketed* bspai_BM_h;/* M split into precision buckets */
 
 typedef struct {
@@ -211,30 +211,36 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
 int bspai_M_adaptive_export(bspai_M_h M, int8_t* step_added, int32_t* col_info, bspai_stream_t s);
 
 /* Fixed-pattern SPAI (Alg 2.1 with alpha = 0; eq. redprob) run on B = A^T D,
- * D = diag(1 / max_i |a_ji|) (Section 4), in u_f = fp32, giving the left
+ * D = diag(1 / max_i |a_ji|) (Section 4), in u_f, giving the left
  * preconditioner M = M'^T D (Alg 3.1, first line).  Row k of M has the
  * structure of row k of `pattern` (pattern->val is ignored).  For each k the
  * shadow I_k, the block Abar = B(I_k, J_k), its Householder QR, mbar =
  * R^-1 Q^T ebar and ||sbar_k||_2 are computed on the GPU, one warp per column.
- * Only u_f = BSPAI_FP32 is built.  Returns BSPAI_RANK_DEFICIENT (with M still
- * created, those columns zero) if any block failed the rank test. */
+ * u_f = BSPAI_FP32, or BSPAI_FP16 for the (half, single, double) setting of
+ * Section 4: every operation of the solve is then an IEEE half operation (the
+ * half format's own range; Section 4's scaling keeps B's entries in [-1, 1])
+ * and M's entries are half values.  Other u_f: BSPAI_ERR_UNSUPPORTED.
+ * Returns BSPAI_RANK_DEFICIENT (with M still created, those columns zero) if
+ * any block failed the rank test, BSPAI_NONFINITE (M created) if an entry of
+ * M = M'^T D overflowed the range of u_f. */
 int bspai_build(const bspai_csr_t* A, const bspai_csr_t* pattern, double spai_eps,
                 bspai_prec_t u_f, bspai_stream_t s, bspai_M_h* M_out, bspai_build_info_t* info);
 
 /* Copies M out in CSR order (structure of the pattern): row_ptr (n+1), col
- * (nnz), val (nnz, fp32, the u_f values) and resid (n, ||sbar_k||_2 per
+ * (nnz), val (nnz, fp32 holding the u_f values) and resid (n, ||sbar_k||_2 per
  * column of M' = row of M).  All device buffers; any may be NULL. */
 int bspai_M_export(bspai_M_h M, int32_t* row_ptr, int32_t* col, float* val, float* resid,
                    bspai_stream_t s);
 
 /* Creates an M handle from a sparse approximate inverse computed elsewhere:
- * Mcsr holds M (device CSR, fp64 values, rounded once to u_f = fp32).  The
- * handle behaves like one from bspai_build (bucketing, x0 = M b), with zero
- * column residuals.  Only u_f = BSPAI_FP32. */
+ * Mcsr holds M (device CSR, fp64 values, rounded once to u_f: BSPAI_FP32 or
+ * BSPAI_FP16, else BSPAI_ERR_UNSUPPORTED).  The handle behaves like one from
+ * bspai_build (bucketing, x0 = M b in u_f), with zero column residuals. */
 int bspai_M_create(const bspai_csr_t* Mcsr, bspai_prec_t u_f, bspai_stream_t s, bspai_M_h* M_out);
 
-/* y = M x with the unbucketed M in u_f = fp32 (x rounded to fp32, fp32
- * products and sums), y stored in fp64: x0 = M b of Alg 3.1.  Device vectors. */
+/* y = M x with the unbucketed M in its u_f (x rounded once to u_f, every
+ * product and sum in u_f, columns in ascending order), y stored in fp64:
+ * x0 = M b of Alg 3.1.  Device vectors. */
 int bspai_apply_uf(bspai_M_h M, const double* x, double* y, bspai_stream_t s);
 
 /* ------------------------------------------------------------------ buckets */

@@ -493,8 +493,7 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         // x0 = M b in u_f for every right-hand side (Alg 3.1)
         if (!o.x0_given)
             for (int r = 0; r < nrhs; ++r)
-                if ((rc = launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), Bv + (size_t)r * n, BSPAI_FP64,
-                                       X + (size_t)r * n, BSPAI_FP64, s)))
+                if ((rc = launch_apply_uf(M, Bv + (size_t)r * n, X + (size_t)r * n, s)))
                     return done(rc);
     }
     const BMDev Av = single_bucket_view(A->sell, u_p == BSPAI_FP64 ? (const void*)A->val64 : (const void*)A->val32,

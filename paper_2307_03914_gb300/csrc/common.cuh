@@ -109,7 +109,8 @@ struct bspai_spai {
     bspai::Sell sell;          // structure of the pattern (rows of M)
     int32_t* rowlen = nullptr; // entries per row
     int32_t* csr_row_ptr = nullptr;
-    float* val = nullptr;      // M in u_f = fp32
+    float* val = nullptr;      // M's values in u_f (fp32, or fp16 values held in fp32)
+    int32_t uf = BSPAI_FP32;   // u_f: BSPAI_FP32 or BSPAI_FP16
     float* resid = nullptr;    // ||sbar_k||_2 per column of M'
     int8_t* step_added = nullptr;  // adaptive build: the pass that added each entry (CSR order)
     int32_t* col_info = nullptr;   // adaptive build: solves | conv << 8 | rankdef << 9 | capped << 10
@@ -151,6 +152,8 @@ int launch_bspmv(const BMDev& M, const void* x, int x_prec, void* y, int y_prec,
 int launch_bspmv_idx(const BMDev& M, const void* x, int x_prec, void* y, int y_prec, const int* jd,
                      int64_t ldx, int64_t ldy, int yoff, cudaStream_t s);
 BMDev single_bucket_view(const Sell& S, const void* val, int prec);
+// x0 = M b with the unbucketed M in its u_f (fp32 or fp16 arithmetic), y in fp64
+int launch_apply_uf(const bspai_spai* M, const double* x, double* y, cudaStream_t s);
 int stage_timeout_take(cudaStream_t s);  // BSPAI_TIMEOUT if a staged SpMV gave up waiting
 
 // defined in matrix.cu

@@ -1004,11 +1004,10 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
         k_absmax<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, b, nrm);
         note_launch();
         if (!o.x0_given) {
-            // x0 = M b with the unbucketed M in u_f = fp32, stored in fp64
-            if ((rc = launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), b, BSPAI_FP64, x, BSPAI_FP64, s)))
-                return finish(rc);
+            // x0 = M b with the unbucketed M in u_f (fp32 or fp16), stored in fp64
+            if ((rc = launch_apply_uf(M, b, x, s))) return finish(rc);
         } else if (W.u32) {
-            // a given x0 is held in u = fp32 (M b in u_f = fp32 already is)
+            // a given x0 is held in u = fp32 (M b in u_f <= fp32 already is)
             k_round_f32<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, x);
             note_launch();
         }

@@ -61,7 +61,37 @@ struct SpaiCounters {
     int n_conv;
     int n_rankdef;
     float max_resid;
-    int pad;
+    int n_nonfinite;  // entries of M outside the range of u_f (fp16: |m| >= 65520 rounds to Inf)
+};
+
+// Arithmetic in u_f: fp32 (H = false) or fp16 (H = true), values held in fp32
+// registers.  An fp16 operation is the correctly rounded fp32 operation
+// rounded once more to fp16 (RN-even, fp16's own range with subnormals and
+// overflow to Inf).  fp32 carries 24 >= 2 * 11 + 2 significand bits, so by
+// Figueroa's double-rounding theorem that is the correctly rounded fp16
+// result of +, -, *, / and sqrt: each step is an fp16 operation.
+template <bool H>
+struct UfOps {
+    static __device__ __forceinline__ float r(float x) {
+        if constexpr (H) return __half2float(__float2half_rn(x));
+        else return x;
+    }
+    static __device__ __forceinline__ float add(float a, float b) { return r(__fadd_rn(a, b)); }
+    static __device__ __forceinline__ float sub(float a, float b) { return r(__fsub_rn(a, b)); }
+    static __device__ __forceinline__ float mul(float a, float b) { return r(__fmul_rn(a, b)); }
+    static __device__ __forceinline__ float div(float a, float b) { return r(__fdiv_rn(a, b)); }
+    static __device__ __forceinline__ float sqrt(float a) { return r(__fsqrt_rn(a)); }
+    // an fp64 value rounded once to u_f
+    static __device__ __forceinline__ float from64(double x) {
+        if constexpr (H) return __half2float(__double2half(x));
+        else return __double2float_rn(x);
+    }
+    // butterfly warp sum with every addition in u_f
+    static __device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = add(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
 };
 
 // Shared memory of one warp (bytes): dJ (fp64, |J|), J, mbar, R's diagonal,
@@ -86,12 +116,14 @@ __device__ __forceinline__ int lower_bound_i32(const int* a, int n, int v) {
     return lo;
 }
 
+template <bool H>
 __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
                                                const double* __restrict__ aval, const double* __restrict__ d,
                                                const int64_t* __restrict__ msptr, const int32_t* __restrict__ mcol,
                                                const int32_t* __restrict__ mrowlen, float* __restrict__ mval,
                                                float* __restrict__ resid, float spai_eps, float u_f, int jmax,
                                                int lmax, int lp2, SpaiCounters* __restrict__ cnt) {
+    using F = UfOps<H>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -152,7 +184,7 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
         const int c = acol[e];
         ecol[t] = c;
         cand[t] = c;
-        eval[t] = __double2float_rn(__dmul_rn(aval[e], dJ[lo]));
+        eval[t] = F::from64(__dmul_rn(aval[e], dJ[lo]));
         eq[t] = lo;
     }
     int LP = 2;
@@ -210,8 +242,8 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
         float cvp = (k_in && lane == pk) ? 1.0f : 0.0f;
         float fro = 0.0f;
 #pragma unroll
-        for (int q = 0; q < kRegJ; ++q) fro = __fadd_rn(fro, __fmul_rn(a[q], a[q]));
-        fro = __fsqrt_rn(warp_sum(fro));
+        for (int q = 0; q < kRegJ; ++q) fro = F::add(fro, F::mul(a[q], a[q]));
+        fro = F::sqrt(F::wsum(fro));
         float rd[kRegJ];
 #pragma unroll
         for (int c = 0; c < kRegJ; ++c) {
@@ -219,26 +251,26 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
             if (c >= nJ || rankdef) continue;
             const bool act = mine && lane >= c;
             const float xc = act ? a[c] : 0.0f;
-            const float sig = __fsqrt_rn(warp_sum(__fmul_rn(xc, xc)));
+            const float sig = F::sqrt(F::wsum(F::mul(xc, xc)));
             const float x0 = __shfl_sync(0xffffffffu, a[c], c);
             if (!(sig > 0.0f)) {
                 rankdef = true;
                 continue;
             }
             const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
-            const float v0 = __fadd_rn(x0, sgn * sig);
-            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
-            const float twoinv = __fdiv_rn(2.0f, vtv);
+            const float v0 = F::add(x0, sgn * sig);
+            const float vtv = F::mul(F::mul(2.0f, sig), F::add(sig, fabsf(x0)));
+            const float twoinv = F::div(2.0f, vtv);
             const float vp = act ? (lane == c ? v0 : a[c]) : 0.0f;  // reflector v, entries c..|I|-1
 #pragma unroll
             for (int cc = c + 1; cc < kRegJ; ++cc) {
                 if (cc >= nJ) break;
-                const float tau = __fmul_rn(warp_sum(__fmul_rn(vp, a[cc])), twoinv);
-                if (act) a[cc] = __fsub_rn(a[cc], __fmul_rn(tau, vp));
+                const float tau = F::mul(F::wsum(F::mul(vp, a[cc])), twoinv);
+                if (act) a[cc] = F::sub(a[cc], F::mul(tau, vp));
             }
             {
-                const float tau = __fmul_rn(warp_sum(__fmul_rn(vp, cvp)), twoinv);
-                if (act) cvp = __fsub_rn(cvp, __fmul_rn(tau, vp));
+                const float tau = F::mul(F::wsum(F::mul(vp, cvp)), twoinv);
+                if (act) cvp = F::sub(cvp, F::mul(tau, vp));
             }
             rd[c] = -sgn * sig;
             if (!(fabsf(rd[c]) > (float)nI * u_f * fro)) rankdef = true;
@@ -254,15 +286,15 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
                 float sum = cvp;
 #pragma unroll
                 for (int cc = c + 1; cc < kRegJ; ++cc)
-                    if (cc < nJ) sum = __fsub_rn(sum, __fmul_rn(a[cc], m[cc]));
-                m[c] = __shfl_sync(0xffffffffu, __fdiv_rn(sum, rd[c]), c);
+                    if (cc < nJ) sum = F::sub(sum, F::mul(a[cc], m[cc]));
+                m[c] = __shfl_sync(0xffffffffu, F::div(sum, rd[c]), c);
             }
             // sbar = Abar mbar - ebar from the original rows
             float sp = (k_in && lane == pk) ? -1.0f : 0.0f;
 #pragma unroll
             for (int q = 0; q < kRegJ; ++q)
-                if (q < nJ) sp = __fadd_rn(sp, __fmul_rn(a0[q], m[q]));
-            res_norm = __fsqrt_rn(warp_sum(mine ? __fmul_rn(sp, sp) : 0.0f));
+                if (q < nJ) sp = F::add(sp, F::mul(a0[q], m[q]));
+            res_norm = F::sqrt(F::wsum(mine ? F::mul(sp, sp) : 0.0f));
             if (lane < nJ) {
                 float mq = 0.0f;
 #pragma unroll
@@ -287,34 +319,34 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
         }
         __syncwarp();
         float fro = 0.0f;
-        for (int t = lane; t < nJ * nI; t += 32) fro = __fadd_rn(fro, __fmul_rn(Ab[t], Ab[t]));
-        fro = __fsqrt_rn(warp_sum(fro));
+        for (int t = lane; t < nJ * nI; t += 32) fro = F::add(fro, F::mul(Ab[t], Ab[t]));
+        fro = F::sqrt(F::wsum(fro));
 
         // Householder QR of Abar, applied to ebar as well
         for (int c = 0; c < nJ && !rankdef; ++c) {
             float* col_c = Ab + c * nI;
             float s2 = 0.0f;
-            for (int p = c + lane; p < nI; p += 32) s2 = __fadd_rn(s2, __fmul_rn(col_c[p], col_c[p]));
-            s2 = warp_sum(s2);
-            const float sig = __fsqrt_rn(s2);
+            for (int p = c + lane; p < nI; p += 32) s2 = F::add(s2, F::mul(col_c[p], col_c[p]));
+            s2 = F::wsum(s2);
+            const float sig = F::sqrt(s2);
             const float x0 = col_c[c];
             if (!(sig > 0.0f)) {
                 rankdef = true;
                 break;
             }
             const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
-            const float v0 = __fadd_rn(x0, sgn * sig);
-            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
+            const float v0 = F::add(x0, sgn * sig);
+            const float vtv = F::mul(F::mul(2.0f, sig), F::add(sig, fabsf(x0)));
             __syncwarp();
             if (lane == 0) col_c[c] = v0;
             __syncwarp();
             for (int cc = c + 1; cc <= nJ; ++cc) {
                 float* tgt = cc < nJ ? Ab + cc * nI : cv;  // the last pass applies the reflector to ebar
                 float dot = 0.0f;
-                for (int p = c + lane; p < nI; p += 32) dot = __fadd_rn(dot, __fmul_rn(col_c[p], tgt[p]));
-                dot = warp_sum(dot);
-                const float tau = __fdiv_rn(__fmul_rn(2.0f, dot), vtv);
-                for (int p = c + lane; p < nI; p += 32) tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, col_c[p]));
+                for (int p = c + lane; p < nI; p += 32) dot = F::add(dot, F::mul(col_c[p], tgt[p]));
+                dot = F::wsum(dot);
+                const float tau = F::div(F::mul(2.0f, dot), vtv);
+                for (int p = c + lane; p < nI; p += 32) tgt[p] = F::sub(tgt[p], F::mul(tau, col_c[p]));
                 __syncwarp();
             }
             const float rcc = -sgn * sig;
@@ -327,8 +359,8 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
             if (lane == 0) {
                 for (int c = nJ - 1; c >= 0; --c) {
                     float s = cv[c];
-                    for (int cc = c + 1; cc < nJ; ++cc) s = __fsub_rn(s, __fmul_rn(Ab[cc * nI + c], mv[cc]));
-                    mv[c] = __fdiv_rn(s, rdiag[c]);
+                    for (int cc = c + 1; cc < nJ; ++cc) s = F::sub(s, F::mul(Ab[cc * nI + c], mv[cc]));
+                    mv[c] = F::div(s, rdiag[c]);
                 }
             }
             __syncwarp();
@@ -341,19 +373,20 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
                 const float mq = mv[q];
                 for (int t = eoff[q] + lane; t < eoff[q + 1]; t += 32) {
                     const int p = ecol[t];
-                    sv[p] = __fadd_rn(sv[p], __fmul_rn(eval[t], mq));
+                    sv[p] = F::add(sv[p], F::mul(eval[t], mq));
                 }
                 __syncwarp();
             }
             float r2 = 0.0f;
-            for (int t = lane; t < nI; t += 32) r2 = __fadd_rn(r2, __fmul_rn(sv[t], sv[t]));
-            res_norm = __fsqrt_rn(warp_sum(r2));
+            for (int t = lane; t < nI; t += 32) r2 = F::add(r2, F::mul(sv[t], sv[t]));
+            res_norm = F::sqrt(F::wsum(r2));
         }
     }
     if (rankdef) res_norm = 1.0f;
     // M[k, J[q]] = mbar_q d_J[q]  (M = M'^T D)
     for (int q = lane; q < nJ; q += 32) {
-        const float m = rankdef ? 0.0f : __double2float_rn(__dmul_rn((double)mv[q], dJ[q]));
+        const float m = rankdef ? 0.0f : F::from64(__dmul_rn((double)mv[q], dJ[q]));
+        if (!isfinite(m)) atomicAdd(&cnt->n_nonfinite, 1);
         mval[mbase + (int64_t)q * kSlice] = m;
     }
     if (lane == 0) {
@@ -362,6 +395,12 @@ __global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__
         if (rankdef) atomicAdd(&cnt->n_rankdef, 1);
         atomic_max_nonneg(&cnt->max_resid, res_norm);
     }
+}
+
+// fp64 values rounded once to fp16 (held in fp64), for an M imported in u_f = fp16
+__global__ void k_round_f16_of_f64(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (double)__half2float(__double2half(x[i]));
 }
 
 __global__ void k_sell_to_csr_f32(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ scol,
@@ -394,7 +433,8 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
     if (A->n != P->n || A->n < 0) return set_error(BSPAI_ERR_INVALID, "bspai_build: A and pattern sizes differ");
     if (A->n > 0 && (!A->row_ptr || !A->col || !A->val || !P->row_ptr || !P->col))
         return set_error(BSPAI_ERR_INVALID, "bspai_build: missing CSR arrays");
-    if (u_f != BSPAI_FP32) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_build: only u_f = FP32 is built");
+    if (u_f != BSPAI_FP32 && u_f != BSPAI_FP16)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_build: u_f must be FP32 or FP16");
     if (!(spai_eps > 0.0)) return set_error(BSPAI_ERR_INVALID, "bspai_build: spai_eps must be > 0");
     BSPAI_TRY(validate_csr(A, true, "bspai_build (A)", s));
     BSPAI_TRY(validate_csr(P, false, "bspai_build (pattern)", s));
@@ -404,6 +444,7 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
     M->stream = s;
     M->n = n;
     M->nnz = P->nnz;
+    M->uf = u_f;
     double* d = nullptr;
     int* sizes = nullptr;
     SpaiCounters* cnt = nullptr;
@@ -460,11 +501,14 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
     const size_t smem = per_warp * warps;
     if (n > 0) {
         ProfScope ps(BSPAI_K_SPAI, s);
-        e = cudaFuncSetAttribute(k_spai, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const bool h = u_f == BSPAI_FP16;
+        e = cudaFuncSetAttribute(h ? k_spai<true> : k_spai<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return fail(cuda_error(e, "spai smem attribute", __FILE__, __LINE__));
-        k_spai<<<(unsigned)ceil_div(n, warps), 32 * warps, smem, s>>>(
+        // u_f: 2^-24 (fp32) or 2^-11 (fp16), the rank test's unit roundoff
+        (h ? k_spai<true> : k_spai<false>)<<<(unsigned)ceil_div(n, warps), 32 * warps, smem, s>>>(
             n, A->row_ptr, A->col, A->val, d, M->sell.sptr, M->sell.col, M->rowlen, M->val, M->resid,
-            (float)spai_eps, 5.9604644775390625e-08f, jmax, lmax, lp2, cnt);
+            (float)spai_eps, h ? 4.8828125e-04f : 5.9604644775390625e-08f, jmax, lmax, lp2, cnt);
         note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail(cuda_error(e, "k_spai", __FILE__, __LINE__));
@@ -489,6 +533,10 @@ int bspai_build(const bspai_csr_t* A, const bspai_csr_t* P, double spai_eps, bsp
         info->total_solves = n;
     }
     *M_out = M;
+    if (hc.n_nonfinite > 0) {
+        set_error(BSPAI_NONFINITE, "bspai_build: %d entries of M overflowed the range of u_f", hc.n_nonfinite);
+        return BSPAI_NONFINITE;
+    }
     if (hc.n_rankdef > 0) {
         set_error(BSPAI_RANK_DEFICIENT, "bspai_build: %d least-squares blocks were rank deficient", hc.n_rankdef);
         return BSPAI_RANK_DEFICIENT;
@@ -500,7 +548,8 @@ int bspai_M_create(const bspai_csr_t* Mcsr, bspai_prec_t u_f, bspai_stream_t st,
     cudaStream_t s = (cudaStream_t)st;
     if (!M_out) return set_error(BSPAI_ERR_INVALID, "bspai_M_create: null M_out");
     *M_out = nullptr;
-    if (u_f != BSPAI_FP32) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_M_create: only u_f = FP32 is built");
+    if (u_f != BSPAI_FP32 && u_f != BSPAI_FP16)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_M_create: u_f must be FP32 or FP16");
     BSPAI_TRY(validate_csr(Mcsr, true, "bspai_M_create", s));
     const int n = Mcsr->n;
     auto* M = new bspai_spai();
@@ -508,10 +557,25 @@ int bspai_M_create(const bspai_csr_t* Mcsr, bspai_prec_t u_f, bspai_stream_t st,
     M->stream = s;
     M->n = n;
     M->nnz = Mcsr->nnz;
-    int rc;
+    M->uf = u_f;
+    int rc = BSPAI_OK;
     {
         ProfScope ps(BSPAI_K_OTHER, s);
-        rc = sell_from_csr(n, Mcsr->row_ptr, Mcsr->col, Mcsr->val, &M->sell, nullptr, &M->val, &M->rowlen, s);
+        // fp16: round the fp64 values once to fp16 first; the fp32 copy below is then exact
+        double* v16 = nullptr;
+        if (u_f == BSPAI_FP16 && Mcsr->nnz > 0) {
+            rc = dalloc_t(&v16, (size_t)Mcsr->nnz, s);
+            if (!rc) {
+                k_round_f16_of_f64<<<(unsigned)ceil_div(Mcsr->nnz, 256), 256, 0, s>>>(Mcsr->nnz, Mcsr->val, v16);
+                note_launch();
+                cudaError_t e = cudaGetLastError();
+                if (e) rc = cuda_error(e, "k_round_f16_of_f64", __FILE__, __LINE__);
+            }
+        }
+        if (!rc)
+            rc = sell_from_csr(n, Mcsr->row_ptr, Mcsr->col, v16 ? v16 : Mcsr->val, &M->sell, nullptr, &M->val,
+                               &M->rowlen, s);
+        dfree(v16, s);
         if (!rc) rc = dalloc_t(&M->csr_row_ptr, (size_t)n + 1, s);
         if (!rc) rc = dalloc_t(&M->resid, (size_t)(n > 0 ? n : 1), s);
         if (!rc) {

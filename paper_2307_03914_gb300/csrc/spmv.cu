@@ -735,6 +735,41 @@ int stage_timeout_take(cudaStream_t s) {
     CUDA_TRY(cudaStreamSynchronize(s));
     return set_error(BSPAI_TIMEOUT, "spmv: a shared-memory stage was not filled within its time limit");
 }
+// y = M x with M in u_f = fp16 (Alg 3.1's x0 = M b in the (half, single,
+// double) setting): x_j rounded once from fp64 to fp16, every product and
+// partial sum an fp16 operation (the fp32 operation rounded once more, exact
+// for the product of two fp16 values and correctly rounded for the sum by the
+// double-rounding theorem, 24 >= 2 * 11 + 2), in ascending column order; y
+// stored in fp64.  One thread per row of the SELL-32 layout: the 32 rows of a
+// slice read consecutive slots.
+__global__ void k_spmv_uf16(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                            const float* __restrict__ val, const int32_t* __restrict__ rowlen,
+                            const double* __restrict__ x, double* __restrict__ y) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t b = sptr[r >> 5] + (r & 31);
+    const int len = rowlen[r];
+    float acc = 0.0f;
+    for (int l = 0; l < len; ++l) {
+        const int64_t p = b + (int64_t)l * kSlice;
+        const float xv = __half2float(__double2half(x[col[p]]));
+        const float pr = __half2float(__float2half_rn(__fmul_rn(val[p], xv)));
+        acc = __half2float(__float2half_rn(__fadd_rn(acc, pr)));
+    }
+    y[r] = (double)acc;
+}
+
+int launch_apply_uf(const bspai_spai* M, const double* x, double* y, cudaStream_t s) {
+    if (M->uf == BSPAI_FP16) {
+        if (M->n <= 0) return BSPAI_OK;
+        k_spmv_uf16<<<(unsigned)ceil_div(M->n, 256), 256, 0, s>>>(M->n, M->sell.sptr, M->sell.col, M->val,
+                                                                  M->rowlen, x, y);
+        note_launch();
+        CUDA_LAUNCH_CHECK();
+        return BSPAI_OK;
+    }
+    return launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), x, BSPAI_FP64, y, BSPAI_FP64, s);
+}
 }  // namespace bspai
 
 extern "C" {
@@ -758,8 +793,7 @@ int bspai_apply_uf(bspai_M_h M, const double* x, double* y, bspai_stream_t s) {
     if (!M || M->magic != kMagicM) return set_error(BSPAI_ERR_INVALID, "bspai_apply_uf: bad handle");
     if (!x || !y) return set_error(BSPAI_ERR_INVALID, "bspai_apply_uf: null vector");
     ProfScope ps(BSPAI_K_OTHER, (cudaStream_t)s);
-    return launch_bspmv(single_bucket_view(M->sell, M->val, BSPAI_FP32), x, BSPAI_FP64, y, BSPAI_FP64,
-                        (cudaStream_t)s);
+    return launch_apply_uf(M, x, y, (cudaStream_t)s);
 }
 
 int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s) {

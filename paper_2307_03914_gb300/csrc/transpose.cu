@@ -224,6 +224,7 @@ int bspai_M_transpose(bspai_M_h M, bspai_stream_t st, bspai_M_h* out) {
     T->stream = s;
     T->n = M->n;
     T->nnz = M->nnz;
+    T->uf = M->uf;
     TransposeMap map;
     int rc = BSPAI_OK;
     {
