@@ -26,9 +26,10 @@ from gpu_helpers import dev, gpu_bucket, host, lib, small_workloads, spai_tolera
 
 pytestmark = pytest.mark.gpu
 
-# the convection-diffusion cases: kappa_inf(A) within the setting's bound
-# u^-1/3 u_f^-2/3 (about 4e4).  The random case (kappa_inf ~ 1e6) is outside it
-# and is only checked for its rank flags below.
+# the convection-diffusion cases (|I| <= 33 rows per block).  The random case
+# has blocks of about 300 rows, where the rank test |R_jj| <= |I| u_f ||Abar||_F
+# becomes 0.15 ||Abar||_F in half and flags most columns; it is checked for
+# those flags only.
 ALL = small_workloads()
 WLS = [w for w in ALL if w["name"] != "random"]
 RANDOM = [w for w in ALL if w["name"] == "random"][0]
@@ -156,10 +157,11 @@ def test_ir_half_on_oracle_M_matches_oracle(B, wl):
     assert abs(info["gmres_iters"][0] - ref["its"][0]) <= max(2, 0.1 * ref["its"][0])
 
 
-def test_half_spai_flags_rank_deficiency_outside_the_bound(B):
+def test_half_spai_rank_test_on_wide_blocks(B):
     """With |I| of about 300 rows the rank test |R_jj| <= |I| u_f ||Abar||_F
-    flags many blocks in half; the oracle applies the same test and flags
-    them too.  Flagged columns of M are zero."""
+    flags most blocks in half although they are well conditioned (kappa of
+    about 27): the tolerance is 0.15 ||Abar||_F.  The oracle applies the same
+    test and flags them too.  Flagged columns of M are zero."""
     wl = RANDOM
     P = wl["pattern"]
     A = B.DeviceCSR.from_host(wl["A"])
