@@ -506,11 +506,14 @@ def main():
         Ah.free()
 
     # ---------------- (u_f, u, u_r) = (single | half, single, double), buckets {fp32, fp16, drop} (Section 4)
-    def run_u32_setting(u_f):
+    def run_u32_setting(u_f, adaptive=None, eps_list=(2.0 ** -24, 2.0 ** -18)):
         sres = []
-        for eps in (2.0 ** -24, 2.0 ** -18):
+        for eps in eps_list:
             def step_s(x):
-                M, _ = B.bspai_build(Ad, Pd, wl["spai_eps"], u_f=u_f)
+                if adaptive:  # Alg 2.1 from the identity pattern: (spai_eps, alpha, beta)
+                    M, _ = B.bspai_build_adaptive(Ad, *adaptive, u_f=u_f)
+                else:
+                    M, _ = B.bspai_build(Ad, Pd, wl["spai_eps"], u_f=u_f)
                 BM, sinfo = B.bspai_bucket(M, eps, ["fp32", "fp16", "drop"])
                 inf = B.gmres_ir_solve(Ad, bd, BM, M, x, u="fp32", u_r="fp64", u_g="fp32", u_p="fp32", tol=1e-4,
                                        o=B.opts(tau=1e-4, kmax=args.kmax))
@@ -543,7 +546,11 @@ def main():
         out["half_single_double"] = {"what": "u_f = fp16 (SPAI in half, M held in half, x0 in half), u = fp32, "
                                              "u_r = fp64, u_g = u_p = fp32, tau = 1e-4, buckets {fp32, fp16, drop}; "
                                              "solves reaching forward error <= 4u = 2^-22",
-                                     "runs": run_u32_setting("fp16")}
+                                     "runs": run_u32_setting("fp16"),
+                                     "adaptive_runs": run_u32_setting("fp16", adaptive=(0.3, 3, 8),
+                                                                      eps_list=(2.0 ** -18,)),
+                                     "adaptive": "SPAI by Alg 2.1 from the identity pattern in half, "
+                                                 "spai_eps 0.3, alpha 3, beta 8"}
 
     # ---------------- adaptive SPAI (Alg 2.1, alpha = 3, beta = 8, from the identity pattern) + the same solve
     if not args.no_adaptive:

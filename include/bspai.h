@@ -185,8 +185,10 @@ int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s);
 
 /* ------------------------------------------------------------------ SPAI */
 /* Adaptive SPAI (Alg 2.1 with alpha > 0, Grote and Huckle's pattern growth)
- * run on B = A^T D from the identity pattern (Section 4), in u_f = fp32,
- * giving M = M'^T D.  Per column k, at most alpha + 1 passes of: shadow I_k,
+ * run on B = A^T D from the identity pattern (Section 4), in u_f (BSPAI_FP32,
+ * or BSPAI_FP16 with every operation in IEEE half as in bspai_build; the
+ * candidate sums sbar^T B(I, j) are the u_f products added exactly, then
+ * rounded once to u_f; other u_f: BSPAI_ERR_UNSUPPORTED), giving M = M'^T D.  Per column k, at most alpha + 1 passes of: shadow I_k,
  * least squares on B(I_k, J_k) by Householder QR, sbar; stop when ||sbar||_2
  * <= spai_eps or after the last pass; otherwise score every j in (union over
  * l in I_k u {k} of the nonzero columns of row l of B) \ J_k by
@@ -199,7 +201,8 @@ int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s);
  * configuration that does not fit returns BSPAI_ERR_UNSUPPORTED.  0 <= alpha
  * <= 16, 0 <= beta <= 32.  A: device CSR (fp64 values).  The returned M works
  * wherever a fixed-pattern M does.  Returns BSPAI_RANK_DEFICIENT (M still
- * created) if any block failed the rank test. */
+ * created) if any block failed the rank test, BSPAI_NONFINITE (M created) if
+ * an entry of M overflowed the range of u_f. */
 int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, int32_t beta, int32_t imax_rows,
                          bspai_prec_t u_f, bspai_stream_t s, bspai_M_h* M_out, bspai_build_info_t* info);
 

@@ -197,6 +197,36 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Arithmetic in u_f: fp32 (H = false) or fp16 (H = true), values held in fp32
+// registers.  An fp16 operation is the correctly rounded fp32 operation
+// rounded once more to fp16 (RN-even, fp16's own range with subnormals and
+// overflow to Inf).  fp32 carries 24 >= 2 * 11 + 2 significand bits, so by
+// Figueroa's double-rounding theorem that is the correctly rounded fp16
+// result of +, -, *, / and sqrt: each step is an fp16 operation.
+template <bool H>
+struct UfOps {
+    static __device__ __forceinline__ float r(float x) {
+        if constexpr (H) return __half2float(__float2half_rn(x));
+        else return x;
+    }
+    static __device__ __forceinline__ float add(float a, float b) { return r(__fadd_rn(a, b)); }
+    static __device__ __forceinline__ float sub(float a, float b) { return r(__fsub_rn(a, b)); }
+    static __device__ __forceinline__ float mul(float a, float b) { return r(__fmul_rn(a, b)); }
+    static __device__ __forceinline__ float div(float a, float b) { return r(__fdiv_rn(a, b)); }
+    static __device__ __forceinline__ float sqrt(float a) { return r(__fsqrt_rn(a)); }
+    // an fp64 value rounded once to u_f
+    static __device__ __forceinline__ float from64(double x) {
+        if constexpr (H) return __half2float(__double2half(x));
+        else return __double2float_rn(x);
+    }
+    // butterfly warp sum with every addition in u_f
+    static __device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = add(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+};
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

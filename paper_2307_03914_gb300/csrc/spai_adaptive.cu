@@ -20,13 +20,15 @@
 // taken (the column keeps its current solution and is marked capped): lmax
 // bounds the shared memory of one column.
 //
-// One warp per column, everything in u_f = fp32 as in the fixed-pattern
-// kernel: the gathered rows of A (B's fp32 values precomputed once), the
+// One warp per column, every operation in u_f (fp32, or half through UfOps) as
+// in the fixed-pattern kernel: the gathered rows of A (B's u_f values
+// precomputed once), the
 // shadow (bitonic sort + ballot compaction), Abar in shared memory, the
 // Householder QR with warp-shuffle reductions, back substitution, sbar from
 // the gathered entries; the candidates by one sweep over the rows of B in I_k
 // into an open-addressing hash table that also accumulates sbar^T B(I_k, j)
-// in exact fixed point, rho per candidate from that sum and the precomputed
+// in exact fixed point (the u_f products summed exactly, then rounded once to
+// u_f), rho per candidate from that sum and the precomputed
 // ||B e_j||^2, the mean as a fixed-point sum, and beta rounds of a warp argmin
 // over (rho, j) for the picks.  Every loop has a bound set by jmax, lmax or
 // the host-computed buffer sizes.  Two launches (tiers) share the kernel; see
@@ -47,6 +49,7 @@ struct AdaptiveCounters {
     int max_rows;
     float max_resid;
     unsigned long long solves;
+    int n_nonfinite;  // entries of M outside the range of u_f
 };
 
 // shared memory of one warp, 16-byte aligned pieces
@@ -218,6 +221,7 @@ __device__ __forceinline__ int shadow_rows(const int* ecol, int L, int* keys, in
 // tier (redo_list == nullptr) reruns exactly those columns (cols) from the
 // start with the full bounds.  Both run the same steps in the same order, so
 // a column's result does not depend on the tier that finished it.
+template <bool HALF>
 __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
     int n, int ncols, const int32_t* __restrict__ cols, const int32_t* __restrict__ arp,
     const int32_t* __restrict__ acol, const float* __restrict__ bval, const float* __restrict__ bnorm2,
@@ -227,6 +231,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
     int* __restrict__ redo_count,
     int32_t* __restrict__ Jo, float* __restrict__ Mo, int8_t* __restrict__ So, int32_t* __restrict__ nJo,
     float* __restrict__ resid, int32_t* __restrict__ cinfo, AdaptiveCounters* __restrict__ cnt) {
+    using F = UfOps<HALF>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -289,35 +294,35 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         __syncwarp();
         rankdef = nI < nJ;
         float fro = 0.0f;
-        for (int t = lane; t < nJ * nI; t += 32) fro = __fadd_rn(fro, __fmul_rn(Ab[t], Ab[t]));
-        fro = __fsqrt_rn(warp_sum(fro));
+        for (int t = lane; t < nJ * nI; t += 32) fro = F::add(fro, F::mul(Ab[t], Ab[t]));
+        fro = F::sqrt(F::wsum(fro));
         // Householder QR with the sign choice v_1 = x_1 + sign(x_1) ||x||, applied
         // to ebar as well; warp-shuffle reductions for every norm and product
         for (int c = 0; c < nJ && !rankdef; ++c) {
             float* col_c = Ab + c * nI;
             float s2 = 0.0f;
-            for (int p = c + lane; p < nI; p += 32) s2 = __fadd_rn(s2, __fmul_rn(col_c[p], col_c[p]));
-            s2 = warp_sum(s2);
-            const float sig = __fsqrt_rn(s2);
+            for (int p = c + lane; p < nI; p += 32) s2 = F::add(s2, F::mul(col_c[p], col_c[p]));
+            s2 = F::wsum(s2);
+            const float sig = F::sqrt(s2);
             const float x0 = col_c[c];
             if (!(sig > 0.0f)) {
                 rankdef = true;
                 break;
             }
             const float sgn = x0 >= 0.0f ? 1.0f : -1.0f;
-            const float v0 = __fadd_rn(x0, sgn * sig);
-            const float vtv = __fmul_rn(__fmul_rn(2.0f, sig), __fadd_rn(sig, fabsf(x0)));
-            const float twoinv = __fdiv_rn(2.0f, vtv);
+            const float v0 = F::add(x0, sgn * sig);
+            const float vtv = F::mul(F::mul(2.0f, sig), F::add(sig, fabsf(x0)));
+            const float twoinv = F::div(2.0f, vtv);
             __syncwarp();
             if (lane == 0) col_c[c] = v0;
             __syncwarp();
             for (int cc = c + 1; cc <= nJ; ++cc) {
                 float* tgt = cc < nJ ? Ab + cc * nI : cv;
                 float dot = 0.0f;
-                for (int p = c + lane; p < nI; p += 32) dot = __fadd_rn(dot, __fmul_rn(col_c[p], tgt[p]));
-                dot = warp_sum(dot);
-                const float tau = __fmul_rn(dot, twoinv);
-                for (int p = c + lane; p < nI; p += 32) tgt[p] = __fsub_rn(tgt[p], __fmul_rn(tau, col_c[p]));
+                for (int p = c + lane; p < nI; p += 32) dot = F::add(dot, F::mul(col_c[p], tgt[p]));
+                dot = F::wsum(dot);
+                const float tau = F::mul(dot, twoinv);
+                for (int p = c + lane; p < nI; p += 32) tgt[p] = F::sub(tgt[p], F::mul(tau, col_c[p]));
                 __syncwarp();
             }
             const float rcc = -sgn * sig;
@@ -330,8 +335,8 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         if (lane == 0) {
             for (int c = nJ - 1; c >= 0; --c) {
                 float s = cv[c];
-                for (int cc = c + 1; cc < nJ; ++cc) s = __fsub_rn(s, __fmul_rn(Ab[cc * nI + c], mv[cc]));
-                mv[c] = __fdiv_rn(s, rdiag[c]);
+                for (int cc = c + 1; cc < nJ; ++cc) s = F::sub(s, F::mul(Ab[cc * nI + c], mv[cc]));
+                mv[c] = F::div(s, rdiag[c]);
             }
         }
         __syncwarp();
@@ -344,14 +349,14 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             const float mq = mv[q];
             for (int t = eoff[q] + lane; t < eoff[q + 1]; t += 32) {
                 const int p = ecol[t];
-                sv[p] = __fadd_rn(sv[p], __fmul_rn(eval[t], mq));
+                sv[p] = F::add(sv[p], F::mul(eval[t], mq));
             }
             __syncwarp();
         }
         float r2 = 0.0f;
-        for (int t = lane; t < nI; t += 32) r2 = __fadd_rn(r2, __fmul_rn(sv[t], sv[t]));
-        r2sum = warp_sum(r2);
-        res_norm = __fsqrt_rn(r2sum);
+        for (int t = lane; t < nI; t += 32) r2 = F::add(r2, F::mul(sv[t], sv[t]));
+        r2sum = F::wsum(r2);
+        res_norm = F::sqrt(r2sum);
         if (res_norm <= spai_eps) {
             conv = true;
             break;
@@ -375,7 +380,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             const int e = trp[l + 1];
             for (int p = trp[l]; p < e; ++p) {
                 const int j = tcol[p];  // members of J are inserted too and skipped by the scan
-                const long long term = fix40(__fmul_rn(sl, tval[p]));
+                const long long term = fix40(F::mul(sl, tval[p]));
                 unsigned h = ((unsigned)j * 0x9E3779B1u) >> hshift;
                 int probe = 0;
                 for (; probe < H; ++probe) {
@@ -414,11 +419,11 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
                 acc[b0 + lane] = 0;
             }
             if (flag) {
-                const float num = unfix40(av);
+                const float num = F::r(unfix40(av));
                 const float den = bnorm2[v];
                 float rr = r2sum;
-                if (den > 0.0f) rr = __fsub_rn(r2sum, __fdiv_rn(__fmul_rn(num, num), den));
-                rj = __fsqrt_rn(rr > 0.0f ? rr : 0.0f);
+                if (den > 0.0f) rr = F::sub(r2sum, F::div(F::mul(num, num), den));
+                rj = F::sqrt(rr > 0.0f ? rr : 0.0f);
                 rsum += fix40(rj);
             }
             const unsigned m = __ballot_sync(0xffffffffu, flag);
@@ -433,7 +438,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
         __syncwarp();
         if (nc == 0) break;
-        const float mean = __fdiv_rn(unfix40(rsum), (float)nc);
+        const float mean = F::div(F::r(unfix40(rsum)), (float)nc);
         // ---- up to beta picks: smallest rho (then smaller j) among rho <= mean
         int npick = 0;
         for (int r = 0; r < beta; ++r) {
@@ -526,7 +531,9 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         const int j = J[q];
         const int64_t o = (int64_t)q * n + k;
         Jo[o] = j;
-        Mo[o] = rankdef ? 0.0f : __double2float_rn(__dmul_rn((double)mv[q], d[j]));
+        const float m = rankdef ? 0.0f : F::from64(__dmul_rn((double)mv[q], d[j]));
+        if (!isfinite(m)) atomicAdd(&cnt->n_nonfinite, 1);
+        Mo[o] = m;
         So[o] = (int8_t)stp[q];
     }
     if (lane == 0) {
@@ -561,8 +568,9 @@ __global__ void k_i64_to_i32_rp(int64_t count, const int64_t* __restrict__ in, i
     if (i < count) atomicMax(mx, (int)(in[i + 1] - in[i]));
 }
 
-// B = A^T D in u_f: bval[p] = fl32(a_p d_i) for the entries p of row i of A
-// (column i of B), and bnorm2[i] = ||B e_i||^2 summed in fp32 in row order
+// B = A^T D in u_f: bval[p] = fl_uf(a_p d_i) for the entries p of row i of A
+// (column i of B), and bnorm2[i] = ||B e_i||^2 summed in u_f in row order
+template <bool HALF>
 __global__ void k_bvals(int n, const int32_t* __restrict__ arp, const double* __restrict__ aval,
                         const double* __restrict__ d, float* __restrict__ bval, float* __restrict__ bnorm2) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -570,9 +578,9 @@ __global__ void k_bvals(int n, const int32_t* __restrict__ arp, const double* __
     const double di = d[i];
     float s2 = 0.0f;
     for (int p = arp[i]; p < arp[i + 1]; ++p) {
-        const float b = __double2float_rn(__dmul_rn(aval[p], di));
+        const float b = UfOps<HALF>::from64(__dmul_rn(aval[p], di));
         bval[p] = b;
-        s2 = __fadd_rn(s2, __fmul_rn(b, b));
+        s2 = UfOps<HALF>::add(s2, UfOps<HALF>::mul(b, b));
     }
     bnorm2[i] = s2;
 }
@@ -636,7 +644,9 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
     if (A->n < 0) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: negative size");
     if (A->n > 0 && (!A->row_ptr || !A->col || !A->val))
         return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: missing CSR arrays");
-    if (u_f != BSPAI_FP32) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_build_adaptive: only u_f = FP32 is built");
+    if (u_f != BSPAI_FP32 && u_f != BSPAI_FP16)
+        return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_build_adaptive: u_f must be FP32 or FP16");
+    const bool half = u_f == BSPAI_FP16;
     if (!(spai_eps > 0.0)) return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: spai_eps must be > 0");
     if (alpha < 0 || alpha > 16 || beta < 0 || beta > 32)
         return set_error(BSPAI_ERR_INVALID, "bspai_build_adaptive: need 0 <= alpha <= 16 and 0 <= beta <= 32");
@@ -649,6 +659,7 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
     M->magic = kMagicM;
     M->stream = s;
     M->n = n;
+    M->uf = u_f;
     double* d = nullptr;
     unsigned long long* ccount = nullptr;
     int64_t* i64 = nullptr;
@@ -718,7 +729,7 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         if ((rc = dalloc_t(&tval, (size_t)(nnzA > 0 ? nnzA : 1), s))) return fail(rc);
         if ((rc = dalloc_t(&bval, (size_t)(nnzA > 0 ? nnzA : 1), s))) return fail(rc);
         if ((rc = dalloc_t(&bnorm2, (size_t)n, s))) return fail(rc);
-        k_bvals<<<g, 256, 0, s>>>(n, A->row_ptr, A->val, d, bval, bnorm2);
+        (half ? k_bvals<true> : k_bvals<false>)<<<g, 256, 0, s>>>(n, A->row_ptr, A->val, d, bval, bnorm2);
         note_launch();
         k_tfill<<<g, 256, 0, s>>>(n, A->row_ptr, A->col, bval, trp, cursor, tcol, tval);
         note_launch();
@@ -779,15 +790,16 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         ProfScope ps(BSPAI_K_SPAI, s);
         const size_t smem_full = full.per_warp * full.warps, smem_s = small.per_warp * small.warps;
         const size_t smem_max = two_tier && smem_s > smem_full ? smem_s : smem_full;
-        ATRY(cudaFuncSetAttribute(k_spai_adaptive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        const float uf = 5.9604644775390625e-08f;
+        auto kern = half ? k_spai_adaptive<true> : k_spai_adaptive<false>;
+        ATRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        const float uf = half ? 4.8828125e-04f : 5.9604644775390625e-08f;  // the rank test's unit roundoff
         int nredo = n;
         int32_t* redo = nullptr;  // the columns the second tier runs (all of them without a first tier)
         if (two_tier) {
             // cursor (the redo count) is reused: it was the A^T fill cursor
             if ((rc = dalloc_t(&redo, (size_t)n, s))) return fail(rc);
             ATRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t), s));
-            k_spai_adaptive<<<(unsigned)ceil_div(n, small.warps), 32 * small.warps, smem_s, s>>>(
+            kern<<<(unsigned)ceil_div(n, small.warps), 32 * small.warps, smem_s, s>>>(
                 n, n, nullptr, A->row_ptr, A->col, bval, bnorm2, d, trp, tcol, tval, (float)spai_eps, uf, alpha, beta,
                 small.jmax,
                 small.lmax, small.gmax, small.lp2, small.H, imax_rows, redo, cursor, Jo, Mo, So, nJo,
@@ -802,7 +814,7 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
             }
         }
         if (nredo > 0) {
-            k_spai_adaptive<<<(unsigned)ceil_div(nredo, full.warps), 32 * full.warps, smem_full, s>>>(
+            kern<<<(unsigned)ceil_div(nredo, full.warps), 32 * full.warps, smem_full, s>>>(
                 n, nredo, redo, A->row_ptr, A->col, bval, bnorm2, d, trp, tcol, tval, (float)spai_eps, uf, alpha, beta,
                 jmax, lmax,
                 full.gmax, full.lp2, full.H, imax_rows, nullptr, nullptr, Jo, Mo, So, nJo, M->resid, cinfo,
@@ -860,6 +872,10 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         info->total_solves = (int64_t)hc.solves;
     }
     *M_out = M;
+    if (hc.n_nonfinite > 0) {
+        set_error(BSPAI_NONFINITE, "bspai_build_adaptive: %d entries of M overflowed the range of u_f", hc.n_nonfinite);
+        return BSPAI_NONFINITE;
+    }
     if (hc.n_rankdef > 0) {
         set_error(BSPAI_RANK_DEFICIENT, "bspai_build_adaptive: %d least-squares blocks were rank deficient",
                   hc.n_rankdef);

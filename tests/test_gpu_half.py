@@ -23,6 +23,7 @@ import torch
 
 import oracle as O
 from gpu_helpers import dev, gpu_bucket, host, lib, small_workloads, spai_tolerance
+from paper_2307_03914_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -185,3 +186,96 @@ def test_half_u_f_only_fp16_or_fp32(B):
         B.bspai_build(A, P, wl["spai_eps"], u_f="bf16")
     with pytest.raises(Exception):
         B.M_create(B.DeviceCSR.from_host(wl["A"]), u_f="e4m3")
+
+
+# ---------------------------------------------------------------- adaptive SPAI in half
+# A rho computed in half differs from the oracle's fp64 rho by the rounding of
+# its half reductions, up to about |I| u_f relative with |I| <= 64 rows here:
+# picks may differ where two values lie within that of each other.
+TIE_H = 64 * UF
+
+
+def _near_tie_h(o, j, picks_other):
+    rho = dict(zip(o["cand"].tolist(), o["rho"].tolist()))
+    if j not in rho:
+        return False
+    ends = [o["mean"]]
+    for p in (o["picks"].tolist(), picks_other):
+        vals = [rho[x] for x in p if x in rho]
+        if vals:
+            ends.append(max(vals))
+    return any(abs(rho[j] - t) <= TIE_H * max(abs(t), 1e-30) for t in ends)
+
+
+@pytest.mark.parametrize("eps,alpha", [(0.3, 3), (0.1, 2)])
+@pytest.mark.parametrize("wl", WLS, ids=IDS)
+def test_adaptive_half_spai_matches_oracle(B, wl, eps, alpha):
+    """Alg 2.1 with alpha > 0 from the identity pattern, every operation in
+    half: each pass the GPU took is replayed with the oracle's fp64 scoring on
+    the GPU's own pattern (same picks, or a difference only at a near tie
+    within TIE_H); the final values are the least-squares solution on the
+    GPU's final pattern within the half perturbation bound."""
+    A = wl["A"]
+    n = A.n
+    M, info = B.bspai_build_adaptive(B.DeviceCSR.from_host(A), eps, alpha, 8, 256, u_f="fp16")
+    assert info["status"] == 0 and info["n_rank_deficient"] == 0
+    nnz = int(info["nnz"])
+    rp, ci, v, res = B.M_export(M, n, nnz)
+    step, cinfo = B.M_adaptive_export(M, n, nnz)
+    rp, ci, val, resid = host(rp), host(ci), host(v).astype(np.float64), host(res).astype(np.float64)
+    step, cinfo = host(step).astype(int), host(cinfo)
+    assert np.array_equal(val, O.round_to(val, "fp16"))
+    ref = O.spai_adaptive(A, eps, alpha, beta=8, imax_rows=256, u_f=UF)
+    differ = ties = 0
+    for k in range(n):
+        J, st = ci[rp[k]:rp[k + 1]], step[rp[k]:rp[k + 1]]
+        assert np.all(np.diff(J) > 0) and k in J
+        if not np.array_equal(J, ref["col"][ref["row_ptr"][k]:ref["row_ptr"][k + 1]]):
+            differ += 1
+        Js = [k]
+        for s in range(1, int(st.max()) + 1):
+            added = sorted(J[st == s].tolist())
+            o = O.spai_score(A, k, Js, beta=8, u_f=UF)
+            mine = sorted(o["picks"].tolist())
+            if added != mine:
+                for j in set(added) ^ set(mine):
+                    assert _near_tie_h(o, j, added), (k, s, added, mine)
+                ties += 1
+            Js = sorted(set(Js) | set(added))
+    P = W.CSR(n, rp, ci, np.ones(len(ci)))
+    fx = O.spai(A, P, eps, u_f=UF)
+    tol = spai_tolerance(fx["kappa"], fx["resid"], UF)
+    for k in range(n):
+        a, b = rp[k], rp[k + 1]
+        e = np.linalg.norm(val[a:b] - fx["mval"][a:b]) / np.linalg.norm(fx["mval"][a:b])
+        assert e <= tol[k], (k, e, tol[k])
+    Ms = sp.csr_matrix((np.abs(fx["mval"]), ci, rp), shape=(n, n))
+    As = sp.csr_matrix((np.abs(A.val), A.col, A.row_ptr), shape=(n, n))
+    w = np.sqrt(np.asarray((Ms @ As).multiply(Ms @ As).sum(axis=1)).ravel())
+    bar = 2 * (np.diff(rp) + 2) * UF * (w + 1) + (tol * w) ** 2 / (2 * np.maximum(fx["resid"], 1e-3))
+    assert np.all(np.abs(resid - fx["resid"]) <= bar)
+    conv = (cinfo >> 8) & 1
+    clear = np.abs(fx["resid"] - eps) > bar
+    assert np.array_equal(conv[clear] == 1, (resid <= eps)[clear])
+    assert info["n_converged"] == int(conv.sum())
+    assert differ <= max(3, 0.1 * n), (differ, ties)
+    print(f"{wl['name']} eps={eps} alpha={alpha} half: {differ} columns differ, {ties} near-tie passes")
+
+
+@pytest.mark.parametrize("wl", WLS[:3], ids=IDS[:3])
+def test_ir_half_adaptive_matches_oracle(B, wl):
+    """The paper's (half, single, double) configuration: adaptive SPAI from the
+    identity (beta = 8) in half, M in half, u = fp32, u_r = fp64."""
+    A, P = wl["A"], wl["pattern"]
+    eps = 2.0 ** -18
+    ad = dict(spai_eps=0.3, alpha=3, beta=8)
+    M, info = B.bspai_build_adaptive(B.DeviceCSR.from_host(A), ad["spai_eps"], ad["alpha"], ad["beta"], 256,
+                                     u_f="fp16")
+    bm = gpu_bucket(B, M, int(info["nnz"]), eps, PRECS)
+    Ah = B.matrix_create(B.DeviceCSR.from_host(A))
+    x = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    sinfo = B.gmres_ir_solve(Ah, dev(wl["b"]), bm["BM"], M, x, u="fp32", u_r="fp64", u_g="fp32", u_p="fp32",
+                             tol=1e-4)
+    ref = O.solve(wl, bucket_eps=eps, precs=PRECS, u="fp32", u_r="fp64", ug="fp32", up="fp32", tau=1e-4,
+                  u_f="fp16", adaptive=dict(ad, u_f=UF))
+    _check(sinfo, host(x), ref, wl)
