@@ -23,6 +23,9 @@ prints its statistics and time (a short launch sequence for a profiler).
 --adaptive EPS ALPHA times the adaptive SPAI build (beta = 8, identity
 start) on the grid (median of --reps builds) and prints its statistics; with
 --once it builds exactly once (a short launch sequence for a profiler).
+--spai-uf times the fixed-pattern and the adaptive (spai_eps 0.3, alpha 3,
+beta 8) SPAI builds on the grid with u_f = fp32 and u_f = half (median of
+--reps builds each, CUDA events around the whole build call).
 --mgs times GMRES runs of K = 2, 8, 16, 32, 64 steps (tau = 0) on the same
 system and fits the MGS kernel-class time to a K + b P(K), P(K) = sum over the
 steps j < K of the j + 2 grid reductions of step j: a is the cost per Arnoldi
@@ -43,6 +46,35 @@ from . import workloads as W
 VBYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1, "drop": 0}
 
 
+def spai_uf(grid, reps):
+    wl = W.workload("convdiff3d", grid=grid)
+    A = B.DeviceCSR.from_host(wl["A"])
+    P = B.DeviceCSR.from_host(wl["pattern"], with_values=False)
+    out = {"n": wl["A"].n}
+    for u_f in ("fp32", "fp16"):
+        for kind in ("fixed", "adaptive"):
+            def build():
+                if kind == "fixed":
+                    return B.bspai_build(A, P, wl["spai_eps"], u_f=u_f)
+                return B.bspai_build_adaptive(A, 0.3, 3, 8, u_f=u_f)
+
+            M, info = build()  # warm-up
+            M.free()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                M, info = build()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                M.free()
+            out[f"{kind}_{u_f}"] = {"ms": float(np.median(ts)), "n_converged": info["n_converged"],
+                                    "max_resid": info["max_resid"], "nnz": int(info["nnz"]),
+                                    "solves": int(info["total_solves"])}
+    print(json.dumps(out))
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--grid", type=int, default=128)
@@ -53,7 +85,10 @@ def main():
     p.add_argument("--mixes", action="store_true")
     p.add_argument("--batch", type=int, nargs=2, default=None, metavar=("NSYS", "NRHS"))
     p.add_argument("--adaptive", type=float, nargs=2, default=None, metavar=("EPS", "ALPHA"))
+    p.add_argument("--spai-uf", action="store_true")
     a = p.parse_args()
+    if a.spai_uf:
+        return spai_uf(a.grid, a.reps)
     if a.batch:
         return batch(a.batch[0], a.batch[1])
     if a.adaptive:

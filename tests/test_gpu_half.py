@@ -279,3 +279,55 @@ def test_ir_half_adaptive_matches_oracle(B, wl):
     ref = O.solve(wl, bucket_eps=eps, precs=PRECS, u="fp32", u_r="fp64", ug="fp32", up="fp32", tau=1e-4,
                   u_f="fp16", adaptive=dict(ad, u_f=UF))
     _check(sinfo, host(x), ref, wl)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_half_M_overflow_reported(B):
+    """A scaled by 2^-20: Section 4's scaling makes B = A^T D the same matrix,
+    so mbar is unchanged and M = M'^T D grows by exactly 2^20.  In fp32 that
+    is M's unscaled values times 2^20, to the bit; in half the entries leave
+    the range (the oracle's half rounding gives Inf there too) and both builds
+    report BSPAI_NONFINITE."""
+    wl = WLS[0]
+    A, P = wl["A"], wl["pattern"]
+    As = W.CSR(A.n, A.row_ptr, A.col, A.val * 2.0 ** -20)
+    Pd = B.DeviceCSR.from_host(P, with_values=False)
+    M1, i1 = B.bspai_build(B.DeviceCSR.from_host(A), Pd, wl["spai_eps"])
+    M2, i2 = B.bspai_build(B.DeviceCSR.from_host(As), Pd, wl["spai_eps"])
+    v1 = host(B.M_export(M1, A.n, P.nnz)[2]).astype(np.float64)
+    v2 = host(B.M_export(M2, A.n, P.nnz)[2]).astype(np.float64)
+    assert i1["status"] == i2["status"] == 0 and np.array_equal(v2, v1 * 2.0 ** 20)
+    ref = O.spai(As, P, wl["spai_eps"], u_f=UF)
+    assert np.isinf(O.round_to(ref["mval"], "fp16")).any()
+    with pytest.raises(B.BspaiError) as e:
+        B.bspai_build(B.DeviceCSR.from_host(As), Pd, wl["spai_eps"], u_f="fp16")
+    assert e.value.status == B.NONFINITE
+    with pytest.raises(B.BspaiError) as e:
+        B.bspai_build_adaptive(B.DeviceCSR.from_host(As), 0.3, 2, 8, 256, u_f="fp16")
+    assert e.value.status == B.NONFINITE
+    # and the library is still usable
+    M3, i3 = B.bspai_build(B.DeviceCSR.from_host(A), Pd, wl["spai_eps"], u_f="fp16")
+    assert i3["status"] == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 65])
+def test_half_ragged_1d(B, n):
+    """Tiny and ragged orders (one partial 32-row slice, or a full one plus a
+    tail) through the whole half setting."""
+    A = W.convdiff2d(n, 1, (0.5, 0.0))
+    x_true, b = W.rhs(A)
+    wl = dict(name="edge", A=A, pattern=W.pattern_of(A), x_true=x_true, b=b, spai_eps=0.3,
+              precs=PRECS, tau=1e-4, bucket_eps=2.0 ** -18, u_g="fp32", u_p="fp32")
+    g = _half_build(B, wl)
+    bm = gpu_bucket(B, g["M"], wl["pattern"].nnz, 2.0 ** -18, PRECS)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    info = B.gmres_ir_solve(g["A"], dev(b), bm["BM"], g["M"], x, u="fp32", u_r="fp64", u_g="fp32", u_p="fp32",
+                            tol=1e-4)
+    ref = O.solve(wl, bucket_eps=2.0 ** -18, precs=PRECS, u="fp32", u_r="fp64", ug="fp32", up="fp32", tau=1e-4,
+                  u_f="fp16")
+    _check(info, host(x), ref, wl)
+    # b = 0 gives x = 0
+    x0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    info = B.gmres_ir_solve(g["A"], dev(np.zeros(n)), bm["BM"], g["M"], x0, u="fp32", u_r="fp64", u_g="fp32",
+                            u_p="fp32", tol=1e-4)
+    assert info["status"] == 0 and torch.all(x0 == 0)
