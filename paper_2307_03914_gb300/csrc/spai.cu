@@ -86,8 +86,10 @@ __device__ __forceinline__ int lower_bound_i32(const int* a, int n, int v) {
     return lo;
 }
 
+// at most 51 registers (five 256-thread blocks per SM): the half instance would
+// otherwise take 60 and fit only four
 template <bool H>
-__global__ void __launch_bounds__(256) k_spai(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
+__global__ void __launch_bounds__(256, 5) k_spai(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ acol,
                                                const double* __restrict__ aval, const double* __restrict__ d,
                                                const int64_t* __restrict__ msptr, const int32_t* __restrict__ mcol,
                                                const int32_t* __restrict__ mrowlen, float* __restrict__ mval,

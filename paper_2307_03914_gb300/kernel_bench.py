@@ -25,7 +25,9 @@ start) on the grid (median of --reps builds) and prints its statistics; with
 --once it builds exactly once (a short launch sequence for a profiler).
 --spai-uf times the fixed-pattern and the adaptive (spai_eps 0.3, alpha 3,
 beta 8) SPAI builds on the grid with u_f = fp32 and u_f = half (median of
---reps builds each, CUDA events around the whole build call).
+--reps builds each, CUDA events around the whole build call); with --once
+every build runs exactly once, no warm-up (launch order: fixed fp32,
+adaptive fp32, fixed half, adaptive half).
 --mgs times GMRES runs of K = 2, 8, 16, 32, 64 steps (tau = 0) on the same
 system and fits the MGS kernel-class time to a K + b P(K), P(K) = sum over the
 steps j < K of the j + 2 grid reductions of step j: a is the cost per Arnoldi
@@ -46,7 +48,7 @@ from . import workloads as W
 VBYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1, "drop": 0}
 
 
-def spai_uf(grid, reps):
+def spai_uf(grid, reps, once=False):
     wl = W.workload("convdiff3d", grid=grid)
     A = B.DeviceCSR.from_host(wl["A"])
     P = B.DeviceCSR.from_host(wl["pattern"], with_values=False)
@@ -58,10 +60,11 @@ def spai_uf(grid, reps):
                     return B.bspai_build(A, P, wl["spai_eps"], u_f=u_f)
                 return B.bspai_build_adaptive(A, 0.3, 3, 8, u_f=u_f)
 
-            M, info = build()  # warm-up
-            M.free()
+            if not once:
+                M, info = build()  # warm-up
+                M.free()
             ts = []
-            for _ in range(reps):
+            for _ in range(1 if once else reps):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 M, info = build()
@@ -88,7 +91,7 @@ def main():
     p.add_argument("--spai-uf", action="store_true")
     a = p.parse_args()
     if a.spai_uf:
-        return spai_uf(a.grid, a.reps)
+        return spai_uf(a.grid, a.reps, a.once)
     if a.batch:
         return batch(a.batch[0], a.batch[1])
     if a.adaptive:
