@@ -80,3 +80,51 @@ def test_full_size(B, name, eps):
     nbe = np.abs(rr).max() / (anorm * np.abs(xg).max() + np.abs(wl["b"]).max())
     assert nbe <= 4 * 2.0 ** -53, nbe
     print(name, info["gmres_iters"], f"fe={fe:.2e} nbe={nbe:.2e}", bk["info"]["nnz_k"])
+
+
+def test_full_size_half_single_double(B):
+    """The (half, single, double) setting at 128^3 in the bench's configuration
+    (fixed-pattern SPAI in half, buckets {fp32, fp16, drop} at 2^-18, u = fp32,
+    u_r = fp64, tau = 1e-4): sampled SPAI columns within the half least-squares
+    bound of the oracle's, entries half values; x0 = M b in half bit-exact on
+    the oracle's M over the whole problem; the solve reaches forward error
+    <= 4u = 2^-22 (u = 2^-24) with x fp32-valued."""
+    uf = 2.0 ** -11
+    wl = W.workload("convdiff3d")
+    A, P = wl["A"], wl["pattern"]
+    n = A.n
+    Ad = B.DeviceCSR.from_host(A)
+    Pd = B.DeviceCSR.from_host(P, with_values=False)
+    M, info = B.bspai_build(Ad, Pd, wl["spai_eps"], u_f="fp16")
+    assert info["status"] == 0 and info["n_rank_deficient"] == 0
+    val = host(B.M_export(M, n, P.nnz)[2]).astype(np.float64)
+    assert np.array_equal(val, O.round_to(val, "fp16"))
+    for c0 in (0, n // 2, n - 1500):
+        c1 = c0 + 1500
+        ref = O.spai(A, P, wl["spai_eps"], u_f=uf, cols=(c0, c1))
+        s = np.minimum(ref["resid"][c0:c1], 0.999)
+        kap = ref["kappa"][c0:c1]
+        tol = np.maximum(1e-5, 10 * uf * (2 * kap + kap ** 2 * s / np.sqrt(1 - s ** 2)))
+        for k in range(c0, c1):
+            lo, hi = P.row_ptr[k], P.row_ptr[k + 1]
+            e = np.linalg.norm(val[lo:hi] - ref["mval"][lo:hi]) / np.linalg.norm(ref["mval"][lo:hi])
+            assert e <= tol[k - c0], (k, e)
+    # x0 in half on the whole problem, on the oracle's M (sampled SPAI rows would not do:
+    # every row of M enters x0); the oracle's full SPAI at this size takes seconds in C
+    sp = O.spai(A, P, wl["spai_eps"], u_f=uf)
+    Mo = B.M_create(B.DeviceCSR(n, Pd.row_ptr, Pd.col, dev(sp["mval"])), u_f="fp16")
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    B.apply_uf(Mo, dev(wl["b"]), y)
+    m16 = O.round_to(sp["mval"], "fp16")
+    assert np.array_equal(host(y), O.spmv_prec(P.row_ptr, P.col, m16, "fp16", wl["b"]))
+    # the solve with the GPU's own half M
+    bk = gpu_bucket(B, M, P.nnz, 2.0 ** -18, ["fp32", "fp16", "drop"])
+    Ah = B.matrix_create(Ad)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    sinfo = B.gmres_ir_solve(Ah, dev(wl["b"]), bk["BM"], M, x, u="fp32", u_r="fp64", u_g="fp32", u_p="fp32",
+                             tol=1e-4)
+    assert sinfo["status"] == 0, sinfo
+    xg = host(x)
+    assert np.array_equal(xg, xg.astype(np.float32).astype(np.float64))
+    fe = np.abs(xg - wl["x_true"]).max() / np.abs(wl["x_true"]).max()
+    assert fe <= 4 * 2.0 ** -24, (fe, sinfo)
