@@ -185,3 +185,35 @@ def test_full_size_adaptive_spai(B):
     assert sinfo["status"] == 0, sinfo
     fe = np.abs(host(x) - wl["x_true"]).max() / np.abs(wl["x_true"]).max()
     assert fe <= 1e-10, (fe, sinfo)
+
+
+def test_full_size_bucketed_A(B):
+    """A bucketed like M at the bench's bucket_eps (eq. nbe2), 128^3: A's bucket
+    ids, ||A||_inf and stored values, and the bucketed A v, bit-exact against
+    the oracle over the whole problem; GMRES-IR with the bucketed A v reaches
+    forward error <= 1e-10."""
+    wl = W.workload("convdiff3d")
+    A, P = wl["A"], wl["pattern"]
+    n = A.n
+    precs = wl["precs"]
+    Ad = B.DeviceCSR.from_host(A)
+    Ah = B.matrix_create(Ad)
+    BA, ainfo = B.bucket_A(Ah, BENCH_EPS, precs)
+    ids, stored = B.bucket_export(BA, A.nnz)
+    ref = O.bucket_ids(A.row_ptr, A.val, BENCH_EPS, precs)
+    rstored, _, _ = O.bucket_store(A.row_ptr, A.col, A.val, ref["ids"], precs)
+    assert ainfo["norm_inf"] == ref["norm"]
+    assert np.array_equal(host(ids), ref["ids"])
+    assert np.array_equal(host(stored), rstored)
+    xin = np.random.default_rng(2).uniform(-1, 1, n).astype(np.float32)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    B.apply(BA, dev(xin), y)
+    yr = O.bspmv(A.row_ptr, A.col, rstored, ref["ids"], precs, xin.astype(np.float64))
+    assert np.array_equal(host(y).astype(np.float64), yr.astype(np.float32).astype(np.float64))
+    M, _ = B.bspai_build(Ad, B.DeviceCSR.from_host(P, with_values=False), wl["spai_eps"])
+    bk = gpu_bucket(B, M, P.nnz, BENCH_EPS, precs)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    info = B.gmres_ir_solve_hb(Ah, BA, dev(wl["b"]), bk["BM"], M, x, tol=wl["tau"])
+    assert info["status"] == 0, info
+    fe = np.abs(host(x) - wl["x_true"]).max() / np.abs(wl["x_true"]).max()
+    assert fe <= 1e-10, (fe, info)
