@@ -324,3 +324,25 @@ def test_gmres_ir_rejects_unknown_u_f(orc):
     wl = W.workload("convdiff2d", grid=6)
     with pytest.raises(ValueError):
         orc.solve(wl, u="fp32", u_r="fp64", u_f="bf16")
+
+
+def test_half_product_keeps_the_half_range(orc):
+    """The half product of x0 is IEEE half with its own range, as numpy's
+    float16: entries and partial sums below 2^-14 become subnormal (spacing
+    2^-24), products above 65504 overflow to Inf."""
+    rng = np.random.default_rng(7)
+    n = 40
+    Ad = np.diag(rng.uniform(1, 2, n)) + np.diag(rng.uniform(-0.5, 0.5, n - 1), 1)
+    P = _csr(Ad)
+    vals = P.val * 2.0 ** rng.integers(-16, -6, P.nnz)  # many products in the subnormal range
+    b = rng.uniform(-1, 1, n) * 2.0 ** rng.integers(-12, 2, n)
+    m16 = orc.round_to(vals, "fp16")
+    got = orc.spmv_prec(P.row_ptr, P.col, m16, "fp16", b)
+    assert np.array_equal(got, _half_textbook_spmv(P, m16, b))
+    assert np.any((np.abs(got) < 2.0 ** -14) & (got != 0))
+    big = orc.round_to(P.val * 300.0, "fp16")
+    got = orc.spmv_prec(P.row_ptr, P.col, big, "fp16", np.full(n, 300.0))
+    with np.errstate(over="ignore"):  # the overflow is the point of this case
+        ref = _half_textbook_spmv(P, big, np.full(n, 300.0))
+    assert np.array_equal(np.isinf(got), np.isinf(ref)) and np.isinf(got).any()
+    assert np.array_equal(got[np.isfinite(got)], ref[np.isfinite(ref)])
