@@ -131,60 +131,97 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle timing (CPU baseline)
-def oracle_sample(wl, bucket_eps, its_profile, spai_cols=None, ks=(1, 3, 9)):
-    """Times the oracle's phases on the full workload and scales them to one
-    complete solve: SPAI on `spai_cols` columns (scaled by n / spai_cols),
-    bucketing, x0 = M b and one residual in full, and GMRES runs of ks steps
-    on the real first-step system, fitted to T(k) = c0 + c1 k + c2 k(k+1)/2
-    (c2: one modified Gram-Schmidt pass over a basis vector) and evaluated at
-    the per-step iteration counts `its_profile`."""
-    import oracle as O
+class OracleSampler:
+    """The oracle as it stands, timed on the host cores on a bounded sample of
+    one solve of the workload, and scaled to a solve by counting work units.
 
-    A, P = wl["A"], wl["pattern"]
-    n = A.n
-    t = {}
-    cols = n if spai_cols is None else min(n, spai_cols)
-    t0 = time.perf_counter()
-    sp = O.spai(A, P, wl["spai_eps"], cols=(0, cols))
-    t["spai"] = (time.perf_counter() - t0) * n / cols
-    if cols < n:
-        # the remaining columns' values do not change the oracle's cost; reuse the sampled
-        # rows' values by pattern position so the later phases run on a full M
-        mval = sp["mval"].copy()
-        done = P.row_ptr[cols]
-        reps = int(np.ceil((P.nnz - done) / max(done, 1)))
-        mval[done:] = np.tile(sp["mval"][:done], reps)[:P.nnz - done]
-    else:
-        mval = sp["mval"]
-    muf = O.round_to(mval, "fp32")
-    t0 = time.perf_counter()
-    bk = O.bucket_ids(P.row_ptr, muf, bucket_eps, wl["precs"])
-    stored, _, _ = O.bucket_store(P.row_ptr, P.col, muf, bk["ids"], wl["precs"])
-    t["bucket"] = time.perf_counter() - t0
-    S = O.System(A, P.row_ptr, P.col, stored, bk["ids"], wl["precs"])
-    t0 = time.perf_counter()
-    x0 = O.spmv_prec(P.row_ptr, P.col, muf, "fp32", wl["b"])
-    t["x0"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    r = O.residual_dd(A, x0, wl["b"])
-    t["residual"] = time.perf_counter() - t0
-    tk = []
-    for k in ks:
+    Set-up (untimed, once): the oracle's own complete SPAI of the workload,
+    rounded to u_f -- every later phase runs on that real M.
+    A sample (timed):
+      * SPAI on a contiguous block of n/16 columns (the block moves with the
+        sample index; the columns are independent least-squares problems);
+      * bucketing, x0 = M b and one residual, each on the whole problem;
+      * two GMRES runs of k1 and k2 Arnoldi steps on the real first system
+        (r of x0), with the oracle's per-step wall times.
+    Scaling: SPAI x 16; the residual x (refinement steps + 1); per Arnoldi step
+    j a + b (j + 1) (a: the two products, roundings, Givens; b: one Gram-
+    Schmidt pass over a basis vector; least squares over the measured steps),
+    per GMRES run c0 + c1 k (s = M r, the start, y and d = V y; from the two
+    runs' time outside their steps), summed over the oracle's own per-step
+    GMRES counts of the complete solve.  `seconds` is the sample's wall time."""
+
+    def __init__(self, wl, bucket_eps, its_profile, k1=2, k2=6):
+        import oracle as O
+
+        self.O = O
+        self.wl, self.eps, self.its = wl, bucket_eps, list(its_profile)
+        self.k1, self.k2 = k1, k2
+        A, P = wl["A"], wl["pattern"]
+        sp = O.spai(A, P, wl["spai_eps"])
+        self.muf = O.round_to(sp["mval"], "fp32")
+        self.count = 0
+
+    def sample(self):
+        O, wl = self.O, self.wl
+        A, P = wl["A"], wl["pattern"]
+        n = A.n
+        blocks = 16
+        lo = (self.count % blocks) * n // blocks
+        hi = (self.count % blocks + 1) * n // blocks
+        self.count += 1
+        t = {}
+        w0 = time.perf_counter()
         t0 = time.perf_counter()
-        O.gmres(S, r, wl["u_g"], wl["u_p"], 0.0, k)
-        tk.append(time.perf_counter() - t0)
-    X = np.array([[1.0, k, k * (k + 1) / 2] for k in ks])
-    c0, c1, c2 = np.linalg.lstsq(X, np.array(tk), rcond=None)[0]
-    c0, c1, c2 = max(c0, 0.0), max(c1, 0.0), max(c2, 0.0)
-    gm = sum(c0 + c1 * k + c2 * k * (k + 1) / 2 for k in its_profile)
-    steps = len(its_profile)
-    total = t["spai"] + t["bucket"] + t["x0"] + (steps + 1) * t["residual"] + gm
-    measured = sum(tk) + t["bucket"] + t["x0"] + t["residual"] + t["spai"] * cols / n
-    return dict(seconds_per_solve=total, phases=t, fit=[c0, c1, c2], measured_s=measured,
-                sample=(f"oracle phases on the full n={n} workload: SPAI on {cols} of {n} columns "
-                        f"(scaled), full bucketing, x0 and residual, GMRES runs of {list(ks)} steps fitted to "
-                        f"c0+c1*k+c2*k(k+1)/2 and evaluated at the oracle's own per-step iteration counts "
-                        f"{list(its_profile)}"), cores=O.get_threads())
+        O.spai(A, P, wl["spai_eps"], cols=(lo, hi))
+        t["spai_block"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        bk = O.bucket_ids(P.row_ptr, self.muf, self.eps, wl["precs"])
+        stored, _, _ = O.bucket_store(P.row_ptr, P.col, self.muf, bk["ids"], wl["precs"])
+        t["bucket"] = time.perf_counter() - t0
+        S = O.System(A, P.row_ptr, P.col, stored, bk["ids"], wl["precs"])
+        t0 = time.perf_counter()
+        x0 = O.spmv_prec(P.row_ptr, P.col, self.muf, "fp32", wl["b"])
+        t["x0"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = O.residual_dd(A, x0, wl["b"])
+        t["residual"] = time.perf_counter() - t0
+        steps, runs = [], []
+        for k in (self.k1, self.k2):
+            t0 = time.perf_counter()
+            _, kk, _, ts = O.gmres(S, r, wl["u_g"], wl["u_p"], 0.0, k, step_seconds=True)
+            tot = time.perf_counter() - t0
+            steps += [(j, float(ts[j])) for j in range(kk)]
+            runs.append((kk, tot - float(ts.sum())))
+        wall = time.perf_counter() - w0
+        X = np.array([[1.0, j + 1.0] for j, _ in steps])
+        a, b = np.linalg.lstsq(X, np.array([v for _, v in steps]), rcond=None)[0]
+        (ka, oa), (kb, ob) = runs
+        c1 = max((ob - oa) / (kb - ka), 0.0)
+        c0 = max(oa - c1 * ka, 0.0)
+        a, b = max(a, 0.0), max(b, 0.0)
+        gm = sum(c0 + c1 * k + a * k + b * k * (k + 1) / 2 for k in self.its)
+        spai = t["spai_block"] * n / (hi - lo)
+        total = spai + t["bucket"] + t["x0"] + (len(self.its) + 1) * t["residual"] + gm
+        return dict(seconds=wall, seconds_per_solve=total, phases=t, per_step=[a, b], per_run=[c0, c1],
+                    cores=O.get_threads(),
+                    sample=(f"oracle on the n={n} workload, its own complete SPAI as M: SPAI of columns "
+                            f"[{lo}, {hi}) of {n}, full bucketing, x0 and one residual, GMRES runs of {self.k1} "
+                            f"and {self.k2} Arnoldi steps on the real system with per-step times; scaled to a "
+                            f"solve by work units: SPAI x {blocks}, Arnoldi step j = a + b (j + 1), GMRES run "
+                            f"= c0 + c1 k, at the oracle's own GMRES counts {self.its}"))
+
+
+def recorded_full_run(name, grid):
+    """The oracle's recorded complete solve of the workload (seconds, threads), a cross-check."""
+    path = os.path.join(ROOT, "oracle", f"iteration_profile_{name}_{grid}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"seconds": d["seconds"], "threads": d["threads"], "its": d["its"],
+                "what": "one complete oracle solve of this workload, recorded by oracle/iteration_profile.py "
+                        "on the build host (x86)"}
+    except Exception:
+        return None
 
 
 def load_its_profile(name, grid, fallback):
@@ -211,21 +248,27 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable":
                           "no oracle iteration profile for this workload; run oracle/iteration_profile.py"}))
         return
+    sampler = OracleSampler(wl, args.bucket_eps, its)
     for _ in range(args.warmup):
-        oracle_sample(wl, args.bucket_eps, its, spai_cols=wl["A"].n // 8)
-    secs = []
+        sampler.sample()
+    walls, per_solve = [], []
     last = None
     for _ in range(args.steps):
-        last = oracle_sample(wl, args.bucket_eps, its, spai_cols=wl["A"].n // 8)
-        secs.append(last["seconds_per_solve"])
-    v = 1.0 / float(np.mean(secs))
+        last = sampler.sample()
+        walls.append(last["seconds"])
+        per_solve.append(last["seconds_per_solve"])
+    v = 1.0 / float(np.mean(per_solve))
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(secs)), "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(walls)), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": f"{args.workload}_{args.grid}^3", "n": wl["A"].n, "bucket_eps": args.bucket_eps,
                       "precs": wl["precs"]},
+           "step": "one bounded sample of a solve (ms_per_step is its wall time); value scales the samples to "
+                   "whole solves by work units",
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                            "sample": last["sample"]},
+                            "sample": last["sample"], "seconds_per_solve": float(np.mean(per_solve)),
+                            "per_step_a_b": last["per_step"], "per_run_c0_c1": last["per_run"]},
+           "full_run_recorded": recorded_full_run(args.workload, args.grid),
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -469,6 +512,126 @@ def main():
                              (1.0 if cfe <= FE_TARGET else 0.0) / (cms / 1000.0), "ms_per_solve": cms,
                              "gmres_iters": cinfo["gmres_iters"], "fwd_err": cfe}
 
+    # ---------------- legs that isolate bucketing: the headline solver settings (u_g = u_p = fp32, tau) with
+    # an unbucketed M (q = 1, fp64 or fp32), and the paper's Table 3 settings of eps with {fp64, fp32, fp16, drop}
+    if not args.no_comparator:
+        def leg(what, eps, pl):
+            x = torch.empty(n, dtype=torch.float64, device="cuda")
+            step(x, eps=eps, pl=pl)
+            barrier()
+            l0_ = torch.cuda.Event(enable_timing=True)
+            l1_ = torch.cuda.Event(enable_timing=True)
+            l0_.record(stream)
+            linf, lb = step(x, eps=eps, pl=pl)
+            l1_.record(stream)
+            barrier()
+            lms = l0_.elapsed_time(l1_)
+            lfe = float(((x - xt).abs().max() / xt.abs().max()).item())
+            B.profile_enable(True)
+            B.profile_read(reset=True)
+            step(x, eps=eps, pl=pl)
+            barrier()
+            lp = B.profile_read(reset=True)
+            B.profile_enable(False)
+            mw_ms, mw_l = lp["bspmv"]
+            good = lfe <= FE_TARGET and linf["status"] == 0
+            return {"what": what, "bucket_eps": eps, "precs": pl, "solves_per_s": (1.0 if good else 0.0) / (lms / 1000.0),
+                    "ms_per_solve": lms, "gmres_iters": linf["gmres_iters"], "fwd_err": lfe,
+                    "bucket_nnz": lb["nnz_k"], "storage_pct": lb["storage_pct"],
+                    "Mw_us_per_launch": 1000.0 * mw_ms / max(mw_l, 1), "Mw_launches": mw_l,
+                    "profile_ms": {c: lp[c][0] for c in lp}}
+
+        out["bucketing_legs"] = {
+            "what": "the headline solve (u_f = u_g = u_p = fp32, u = fp64, u_r = Dot2, tau = 1e-4) with other M "
+                    "storage; Mw_us_per_launch is the bucketed-product class time per launch (events)",
+            "headline": {"bucket_eps": args.bucket_eps, "precs": precs, "solves_per_s": value,
+                         "ms_per_solve": ms / args.steps, "gmres_iters": info["gmres_iters"],
+                         "Mw_us_per_launch": 1000.0 * prof["bspmv"][0] / max(prof["bspmv"][1], 1)},
+            "q1_fp64": leg("unbucketed M in fp64 (q = 1)", 2.0 ** -53, ["fp64"]),
+            "q1_fp32": leg("unbucketed M in fp32 (q = 1)", 2.0 ** -24, ["fp32"]),
+            "table3_eps_2^-53": leg("Table 3 buckets {fp64, fp32, fp16, drop}, eps = 2^-53", 2.0 ** -53,
+                                    ["fp64", "fp32", "fp16", "drop"]),
+            "table3_eps_2^-37": leg("Table 3 buckets {fp64, fp32, fp16, drop}, eps = 2^-37", 2.0 ** -37,
+                                    ["fp64", "fp32", "fp16", "drop"]),
+        }
+
+    # ---------------- cold-cache product times: L2 flushed (a 256 MiB write, twice L2) before each of 50
+    # launches after 5 warm-ups, median; M w as inside GMRES (fp32 in and out), A v in u_p
+    if not args.no_comparator:
+        Mc, _ = B.bspai_build(Ad, Pd, wl["spai_eps"])
+        BMc, bc = B.bspai_bucket(Mc, args.bucket_eps, precs)
+        Ahc = B.matrix_create(Ad)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        xv = torch.rand(n, device="cuda", dtype=torch.float32)
+        yv = torch.empty(n, device="cuda", dtype=torch.float32)
+
+        def cold(fn):
+            for _ in range(5):
+                flush.fill_(1)
+                fn()
+            ts_ = []
+            for _ in range(50):
+                flush.fill_(1)
+                c0_ = torch.cuda.Event(enable_timing=True)
+                c1_ = torch.cuda.Event(enable_timing=True)
+                c0_.record(stream)
+                fn()
+                c1_.record(stream)
+                torch.cuda.synchronize()
+                ts_.append(c0_.elapsed_time(c1_))
+            return float(np.median(ts_))
+
+        bytes_k = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "e4m3": 1, "drop": 0}
+        mb = sum(c * (bytes_k[q] + 4) for c, q in zip(bc["nnz_k"], bc["precs"]) if q != "drop") + 8 * n
+        mb += 4 * n if "e4m3" in bc["precs"] and bc["nnz_k"][bc["precs"].index("e4m3")] > 0 else 0
+        ab = A.nnz * 8 + 8 * n
+        hbm_, src_ = peaks()
+        tm_ = cold(lambda: B.apply(BMc, xv, yv))
+        ta_ = cold(lambda: B.spmv_up(Ahc, xv, yv))
+        out["cold_spmv"] = {
+            "what": "single launches, L2 flushed before each (256 MiB write), median of 50 after 5 warm-ups; "
+                    "CUDA events around the launch (includes its launch latency)",
+            "Mw": {"us": tm_ * 1e3, "algorithmic_bytes": mb, "GBs": mb / tm_ / 1e6, "frac": mb / tm_ / 1e6 / hbm_},
+            "Av": {"us": ta_ * 1e3, "algorithmic_bytes": ab, "GBs": ab / ta_ / 1e6, "frac": ab / ta_ / 1e6 / hbm_},
+            "peak_gbs": hbm_, "peak_source": src_}
+        del flush
+        Mc.free()
+        BMc.free()
+        Ahc.free()
+
+    # ---------------- ALU rooflines: SPAI build (fp32 flops) and the Dot2 residual (fp64 operations) against
+    # the measured issue rate of the plain FMA pipes (bspai_probe_fma)
+    if not args.no_comparator:
+        import scipy.sparse as sps
+
+        p32 = B.probe_fma("fp32", 16384)
+        p64 = B.probe_fma("fp64", 256)
+        Pb = sps.csr_matrix((np.ones(P.nnz), P.col, P.row_ptr), shape=(n, n))
+        Ab = sps.csr_matrix((np.ones(A.nnz), A.col, A.row_ptr), shape=(n, n))
+        ni = np.diff((Pb @ Ab).tocsr().indptr).astype(np.float64)  # |I_k|: the shadow of J_k
+        nj = np.diff(P.row_ptr).astype(np.float64)                  # |J_k|
+        spai_flops = float(np.sum(2 * nj ** 2 * (ni - nj / 3) + 4 * ni * nj))
+        res_ops = 10.0 * A.nnz + n  # Dot2: 10 fp64 operations per entry, one add per row
+        n_res = ir_steps + len(infos)
+        t_spai = prof["spai"][0] / args.steps / 1000.0
+        t_res = prof["residual"][0] / (n_res * 1000.0) if n_res else 0.0
+        out["roofline_spai"] = {"bound": "alu", "achieved": spai_flops / t_spai / 1e12 if t_spai else None,
+                                "peak": p32["flops"] / 1e12, "unit": "TFLOP/s",
+                                "frac": spai_flops / t_spai / p32["flops"] if t_spai else None, "traffic": None,
+                                "flops_per_build": spai_flops,
+                                "work": "sum over columns of 2|J|^2(|I| - |J|/3) + 4|I||J| (Householder QR of the "
+                                        "|I| x |J| block, Q^T e, back substitution)",
+                                "peak_source": "measured: bspai_probe_fma fp32 (2 flops per FMA)"}
+        out["roofline_residual"] = {"bound": "alu", "achieved": res_ops / t_res / 1e9 if t_res else None,
+                                    "peak": p64["fma_per_s"] / 1e9, "unit": "Gop/s fp64",
+                                    "frac": res_ops / t_res / p64["fma_per_s"] if t_res else None, "traffic": None,
+                                    "ops_per_launch": res_ops,
+                                    "work": "10 fp64 operations per entry (TwoProduct: mul + fma; TwoSum: 6; "
+                                            "error update: 2) and one per row",
+                                    "peak_source": "measured: bspai_probe_fma fp64 (one operation per FMA)"}
+        out["alu_peaks"] = {"fp32_tflops": p32["flops"] / 1e12, "fp64_gfma_per_s": p64["fma_per_s"] / 1e9,
+                            "fp64_tflops": p64["flops"] / 1e12}
+
     # ---------------- A v inside GMRES through A's own buckets (eq. nbe2), same eps and precisions
     if not args.no_bucketed_A:
         Ah = B.matrix_create(Ad)
@@ -642,13 +805,13 @@ def main():
 
         O.build()
         its, src = load_its_profile(args.workload, args.grid, info["gmres_iters"])
-        cb = oracle_sample(wl, args.bucket_eps, its, spai_cols=None if n <= 300000 else n // 4)
+        cb = OracleSampler(wl, args.bucket_eps, its).sample()
         out["cpu_baseline"] = {"value": 1.0 / cb["seconds_per_solve"], "unit": UNIT, "cores": cb["cores"],
                                "kind": "oracle", "sample": cb["sample"] + f" (iteration counts from: {src})",
-                               "measured_cpu_s": cb["measured_s"],
-                               "model_s": {"spai": cb["phases"]["spai"], "bucket": cb["phases"]["bucket"],
-                                           "x0": cb["phases"]["x0"], "residual": cb["phases"]["residual"],
-                                           "gmres_c0_c1_c2": cb["fit"]}}
+                               "sample_wall_s": cb["seconds"], "seconds_per_solve": cb["seconds_per_solve"],
+                               "phases_s": cb["phases"], "per_step_a_b": cb["per_step"],
+                               "per_run_c0_c1": cb["per_run"],
+                               "full_run_recorded": recorded_full_run(args.workload, args.grid)}
 
     if world > 1:
         dist.barrier()

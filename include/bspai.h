@@ -151,6 +151,18 @@ long long bspai_launch_count(void);
  * NULL, receives the kernel's duration (CUDA events). */
 int bspai_barrier_selftest(int blocks, int hold, double timeout_s, bspai_stream_t s, float* waited_ms);
 void bspai_opts_default(bspai_opts_t* opts);
+/* Measured issue rate of the SM's plain (non-tensor) fused multiply-add in
+ * prec (BSPAI_FP32 or BSPAI_FP64; otherwise BSPAI_ERR_UNSUPPORTED): a
+ * measurement aid with no counterpart in the paper, the denominator of the
+ * ALU rooflines of the SPAI build (fp32) and the Dot2 residual (fp64).  Runs
+ * eight 256-thread blocks per SM, every thread eight independent chains of
+ * 32 x iters dependent FMAs (8 <= iters <= 2^24, else BSPAI_ERR_INVALID),
+ * after one shorter warm-up launch, timed with CUDA events on stream s
+ * (synchronised).  *fma_per_s: lane FMAs per second over the whole GPU
+ * (flop/s = 2 x that); *ms (may be NULL): the timed launch's duration.
+ * Allocates and frees a small device buffer. */
+int bspai_probe_fma(bspai_prec_t prec, int32_t iters, bspai_stream_t s, double* fma_per_s, float* ms);
+
 /* Releases any handle returned by this library (NULL is a no-op).  Enqueues
  * the frees on the stream the handle was created on. */
 int bspai_free(void* handle);
@@ -254,8 +266,11 @@ int bspai_apply_uf(bspai_M_h M, const double* x, double* y, bspai_stream_t s);
  * an fp16 bucket holds RN16(m / s) with one power-of-two scale s per bucket;
  * an e4m3 bucket holds RNe4m3(m / s_j) with a power-of-two fp32 scale per
  * column (s = least 2^e with max|m| <= fmt_max 2^e); drop removes entries.
- * At most one e4m3 bucket.  BM keeps its own copy of everything it needs, so
- * M may be freed afterwards. */
+ * At most one e4m3 bucket.  Each bucket is a sliced ELL structure of 32-row
+ * slices whose rows keep their slots in groups of four consecutive elements
+ * (one vector load per row and group in bspai_apply), with column indices held
+ * as 16-bit differences to the row when every |c - r| <= 32767, else int32.
+ * BM keeps its own copy of everything it needs, so M may be freed afterwards. */
 int bspai_bucket(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q,
                  bspai_stream_t s, bspai_BM_h* out, bspai_bucket_info_t* info);
 
@@ -318,6 +333,24 @@ int bspai_apply(bspai_BM_h BM, const void* x, bspai_prec_t x_prec, void* y, bspa
 int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
                 const bspai_opts_t* opts, double* d, bspai_stream_t s, bspai_solve_info_t* info);
 
+/* Which kernel runs the modified Gram-Schmidt step of the GMRES solves
+ * (Alg 3.1, GMRES line; MGS as analysed in Section 3) for an order n, u_g in
+ * {FP32, FP64}, and a cap max_blocks on the cooperative grid (0: every SM),
+ * as bspai_gmres, gmres_ir_solve and their variants would pick it on the
+ * current device.  kernel: 0 = k_mgs (basis and new vector streamed from
+ * memory), 1 = k_mgs_res (the new vector held on chip; per_thread rows per
+ * thread), 2 = k_mgs_res2 (fp32, the new vector in registers; per_thread
+ * pairs of adjacent rows per thread); block_threads and blocks give the
+ * launch.  A query only: nothing is launched or allocated.  n < 1:
+ * BSPAI_ERR_INVALID; another u_g: BSPAI_ERR_UNSUPPORTED. */
+typedef struct {
+    int32_t kernel;
+    int32_t per_thread;
+    int32_t block_threads;
+    int32_t blocks;
+} bspai_gmres_plan_t;
+int bspai_gmres_plan(int32_t n, bspai_prec_t u_g, int32_t max_blocks, bspai_gmres_plan_t* out);
+
 /* bspai_gmres with A v by the adaptive-precision SpMV on A's buckets
  * (bspai_bucket_A) instead of A in u_p (eq. nbe2); products accumulated as in
  * bspai_apply, results rounded to u_g.  A_bucketed must hold A's n rows (a
@@ -343,7 +376,10 @@ int bspai_gmres_b(bspai_A_h A, bspai_BM_h A_bucketed, bspai_BM_h BM, const doubl
  *     bspai_profile_enable, off: it creates CUDA events.)
  *   - The first call on a device looks up the device address of the block
  *     with that device current; make that first call before any stream
- *     capture begins.
+ *     capture begins.  The address is kept per device together with the id
+ *     of the CUDA context it was found in: after a device reset (a new
+ *     context, in which the library's image may sit elsewhere) the next call
+ *     looks it up again, so make that call before any capture as well.
  *   - Every call uses the same block, which keeps the previous call's
  *     contents; each call clears the parts that must start at zero.  Two calls
  *     whose GPU work overlaps (for example on two streams of one device) race
@@ -384,11 +420,14 @@ int bspai_matrix_transpose(bspai_A_h A, bspai_stream_t s, bspai_A_h* At);
 int bspai_M_transpose(bspai_M_h M, bspai_stream_t s, bspai_M_h* Mt);
 int bspai_bucket_transpose(bspai_BM_h BM, bspai_stream_t s, bspai_BM_h* BMt);
 
-/* Gradient of a loss L(x) with respect to the nonzeros of A, where A x = b and
- * lambda = A^-T dL/dx: dA[p] = -lambda_i x_j for the p-th nonzero (i, j) of
- * A's CSR (fp64, one rounding).  A: caller CSR (values unused); lambda, x: device
- * fp64 length n; dA: device fp64 length nnz(A).  (dL/db = lambda.) */
-int bspai_adjoint_grad_A(const bspai_csr_t* A, const double* lambda, const double* x, double* dA,
+/* Gradient of a loss L(x) with respect to the nonzeros of A, where A x_r = b_r
+ * for nrhs right-hand sides and lambda_r = A^-T dL/dx_r: dA[p] = sum over r of
+ * -lambda_r[i] x_r[j] for the p-th nonzero (i, j) of A's CSR (fp64; r
+ * ascending from 0, each product and each sum rounded once).  A: caller CSR
+ * (values unused); lambda, x: device fp64, nrhs rows of length n (row r at
+ * offset r n); dA: device fp64 length nnz(A), overwritten.  nrhs < 1:
+ * BSPAI_ERR_INVALID.  (dL/db_r = lambda_r.) */
+int bspai_adjoint_grad_A(const bspai_csr_t* A, int32_t nrhs, const double* lambda, const double* x, double* dA,
                          bspai_stream_t s);
 
 /* ------------------------------------------------------------------ batches */
@@ -423,8 +462,10 @@ typedef struct {
  * kernel-class profiling is on).  kmax defaults to
  * min(largest system, 300).  pair_status (0 not converged, 1 nbe, 2 dx,
  * 3 stagnation, -1 non-finite) and pair_iters (device int32, nsys * nrhs,
- * pair p = rhs * nsys + system) may be NULL.  Returns BSPAI_OK when every
- * pair met a stopping test, else BSPAI_NOT_CONVERGED / BSPAI_NONFINITE. */
+ * pair p = rhs * nsys + system) may be NULL.  BM must come from
+ * bspai_bucket_batched (a bspai_bucket handle, whose buckets use another slot
+ * arrangement: BSPAI_ERR_INVALID).  Returns BSPAI_OK when every pair met a
+ * stopping test, else BSPAI_NOT_CONVERGED / BSPAI_NONFINITE. */
 int gmres_ir_solve_batched(bspai_A_h A, const int32_t* row_off, int32_t nsys, int32_t nrhs, const double* B,
                            bspai_BM_h BM, bspai_M_h M, bspai_prec_t u_g, bspai_prec_t u_p, double tol,
                            const bspai_opts_t* opts, double* X, bspai_stream_t s, bspai_batch_info_t* info,

@@ -111,6 +111,7 @@ def _declare(L):
     L.orc_gmres.argtypes = [C.POINTER(_System), _f64p, C.c_int, C.c_int, C.c_double, C.c_int,
                             _f64p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.orc_gmres.restype = C.c_int
+    L.orc_gmres_time_steps.argtypes = [C.c_void_p]
     L.orc_gmres_ir.argtypes = [C.POINTER(_System), _f64p, _f64p, C.c_int, C.c_int, C.c_double,
                                C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _f64p,
                                _i32p, _f64p, _f64p, C.POINTER(C.c_int)]
@@ -349,12 +350,25 @@ class System:
                          k[7].ctypes.data, len(k[7]), astored, aid)
 
 
-def gmres(system: System, r, ug="fp32", up="fp32", tau=1e-4, kmax=500):
+def gmres(system: System, r, ug="fp32", up="fp32", tau=1e-4, kmax=500, step_seconds=False):
+    """GMRES on (M A) d = M r (Alg 3.1, GMRES line): (d, iterations, |g_k|/beta),
+    plus the wall time of every Arnoldi step when step_seconds is set (a
+    measurement aid for the CPU baseline; the results are the same)."""
     d = np.zeros(system.n)
     it = C.c_int(0)
     rr = C.c_double(0.0)
-    lib().orc_gmres(C.byref(system.s), _f64(r), FMT[ug], FMT[up], tau, int(kmax), d,
+    L = lib()
+    ts = np.zeros(max(int(kmax), 1))
+    if step_seconds:  # the timing pointer is one per library: one timed call at a time
+        with _lock:
+            L.orc_gmres_time_steps(ts.ctypes.data)
+            L.orc_gmres(C.byref(system.s), _f64(r), FMT[ug], FMT[up], tau, int(kmax), d,
+                        C.byref(it), C.byref(rr))
+    else:
+        L.orc_gmres(C.byref(system.s), _f64(r), FMT[ug], FMT[up], tau, int(kmax), d,
                     C.byref(it), C.byref(rr))
+    if step_seconds:
+        return d, it.value, rr.value, ts[:it.value].copy()
     return d, it.value, rr.value
 
 
@@ -417,6 +431,23 @@ def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
     rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
     dA = -lam[rows] * np.asarray(x)[A.col]
     return dict(lam=lam, dA=dA, db=lam, info=out)
+
+
+def adjoint_grad_A(A, lam, x) -> np.ndarray:
+    """dL/dA_ij = -sum_r lam_r[i] x_r[j] on the nonzeros of A (CSR order) for
+    nrhs right-hand sides, A x_r = b_r and lam_r = A^-T dL/dx_r (the adjoint
+    extension; the gradient of a sum of losses is the sum of gradients).  The
+    sum runs over r ascending from 0, every product and sum one fp64 rounding.
+    lam, x: (n,) or (nrhs, n).  Pinned: nrhs = 1 is -lam_i x_j itself; on
+    integer-valued inputs the sum is exact and equals Python's integer sum
+    (tests)."""
+    lam = np.atleast_2d(np.asarray(lam, np.float64))
+    x = np.atleast_2d(np.asarray(x, np.float64))
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    acc = np.zeros(len(A.col))
+    for r in range(lam.shape[0]):
+        acc = acc + (-lam[r][rows]) * x[r][np.asarray(A.col)]
+    return acc
 
 
 def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False, u="fp64",

@@ -738,8 +738,16 @@ static double dot_g(int n, const double* a, const double* b, int ug) {
     return rf(dot_g(h, a, b, ug) + dot_g(n - h, a + h, b + h, ug), ug);
 }
 
+/* Wall-clock seconds of each Arnoldi step of the next orc_gmres call, for the
+ * CPU-baseline timing: a measurement aid that changes no result.  Set it right
+ * before the call (one caller at a time); the call clears it. */
+static double* g_step_seconds = NULL;
+void orc_gmres_time_steps(double* out) { g_step_seconds = out; }
+
 int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau, int kmax,
               double* d, int* iters, double* relres) {
+    double* step_seconds = g_step_seconds;
+    g_step_seconds = NULL;
     int n = S->n;
     double* V = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(kmax + 1));
     double* H = (double*)calloc((size_t)(kmax + 1) * (size_t)kmax, sizeof(double));
@@ -761,6 +769,7 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
         g[0] = beta;
         res = beta;
         for (int j = 0; j < kmax; ++j) {
+            const double t_step = step_seconds ? omp_get_wtime() : 0.0;
             double* vj = V + (size_t)j * n;
             /* w = A v_j in u_p (or by the bucketed SpMV on A's buckets, eq. nbe2), stored
              * in u_g;  z = M w (bucketed), stored in u_g */
@@ -798,9 +807,13 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
             g[j] = cs[j] * g[j];
             res = fabs(g[j + 1]);
             k = j + 1;
-            if (res <= tau * beta || hn == 0.0) break;
+            if (res <= tau * beta || hn == 0.0) {
+                if (step_seconds) step_seconds[j] = omp_get_wtime() - t_step;
+                break;
+            }
             double* vn = V + (size_t)(j + 1) * n;
             for (int t = 0; t < n; ++t) vn[t] = rf(z[t] / hn, ug);
+            if (step_seconds) step_seconds[j] = omp_get_wtime() - t_step;
         }
         /* y = R^-1 g, back substitution in fp64 */
         for (int i = k - 1; i >= 0; --i) {

@@ -141,6 +141,9 @@ typedef struct {
     const double* astored; const int8_t* aid;
 } orc_system_t;
 
+/* Records the wall time of each Arnoldi step of the next orc_gmres call into
+ * out[0 .. k-1] (timing aid only; no result changes). */
+void orc_gmres_time_steps(double* out);
 int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau, int kmax,
               double* d, int* iters, double* relres);
 

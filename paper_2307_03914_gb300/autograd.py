@@ -52,6 +52,8 @@ def _solve_rhs(Ah, rhs, BM, M, out, settings: SolverSettings, what: str):
         def one(r):
             st = streams.get()
             try:
+                # the library works on the calling thread's current device
+                torch.cuda.set_device(rhs.device)
                 return B.gmres_ir_solve(Ah, rhs[r], BM, M, out[r], u_g=settings.u_g, u_p=settings.u_p,
                                         tol=settings.tol, o=o, stream=st)
             finally:
@@ -100,12 +102,9 @@ class BspaiSolve(torch.autograd.Function):
         BMt = B.bucket_transpose(BM)
         g = gx.detach().reshape(-1, n).contiguous()
         lam = torch.empty_like(g)
-        grad_a = torch.zeros_like(A.val)
-        tmp = torch.empty_like(A.val)
+        grad_a = torch.empty_like(A.val)
         ctx.adjoint_infos = _solve_rhs(At, g, BMt, Mt, lam, settings, "adjoint")
-        for r in range(g.shape[0]):
-            B.adjoint_grad_A(A, lam[r], x[r], tmp)
-            grad_a += tmp
+        B.adjoint_grad_A(A, lam, x, grad_a)
         return grad_a, lam.reshape(ctx.b_shape), None, None, None, None
 
 

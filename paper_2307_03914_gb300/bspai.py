@@ -118,7 +118,16 @@ _sig("bspai_gmres", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POI
 _sig("bspai_matrix_transpose", _i, [_vp, _vp, C.POINTER(_vp)])
 _sig("bspai_M_transpose", _i, [_vp, _vp, C.POINTER(_vp)])
 _sig("bspai_bucket_transpose", _i, [_vp, _vp, C.POINTER(_vp)])
-_sig("bspai_adjoint_grad_A", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _vp])
+_sig("bspai_adjoint_grad_A", _i, [C.POINTER(CsrT), C.c_int32, _vp, _vp, _vp, _vp])
+_sig("bspai_probe_fma", _i, [_i, C.c_int32, _vp, C.POINTER(C.c_double), C.POINTER(C.c_float)])
+
+
+class GmresPlan(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("per_thread", C.c_int32), ("block_threads", C.c_int32),
+                ("blocks", C.c_int32)]
+
+
+_sig("bspai_gmres_plan", _i, [C.c_int32, _i, C.c_int32, C.POINTER(GmresPlan)])
 _sig("bspai_gmres_noalloc", _i, [_vp, _vp, _vp, _i, _i, C.POINTER(Opts), _vp, _vp, C.POINTER(SolveInfo)])
 _sig("gmres_ir_solve", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                             C.POINTER(SolveInfo)])
@@ -405,7 +414,11 @@ def bucket_transpose(BM: BMHandle, stream=None) -> BMHandle:
 
 
 def adjoint_grad_A(A: DeviceCSR, lam, x, dA, stream=None):
-    _check(_lib.bspai_adjoint_grad_A(C.byref(A.c()), _ptr(lam), _ptr(x), _ptr(dA), _stream(stream)))
+    """dA = sum over the right-hand sides r of -lambda_r[i] x_r[j] on A's
+    nonzeros; lam and x: (n,) or (nrhs, n) contiguous fp64 device tensors."""
+    nrhs = 1 if lam.dim() == 1 else int(lam.shape[0])
+    assert x.shape == lam.shape and lam.is_contiguous() and x.is_contiguous()
+    _check(_lib.bspai_adjoint_grad_A(C.byref(A.c()), nrhs, _ptr(lam), _ptr(x), _ptr(dA), _stream(stream)))
     return dA
 
 
@@ -415,6 +428,24 @@ def _solve_info(si: SolveInfo) -> dict:
     return dict(status=si.status, status_name=STATUS_NAMES[si.status], ir_steps=k, stop_reason=si.stop_reason,
                 total_iters=si.total_iters, gmres_iters=list(si.gmres_iters[:k]),
                 nbe=list(si.nbe[:min(33, k + 1)]), dx=list(si.dx[:k]), relres=list(si.relres[:k]))
+
+
+def probe_fma(prec="fp32", iters=4096, stream=None) -> dict:
+    """Measured lane-FMA rate of the plain fp32 / fp64 pipes (a measurement aid)."""
+    r, ms = C.c_double(0.0), C.c_float(0.0)
+    _check(_lib.bspai_probe_fma(PREC[prec], iters, _stream(stream), C.byref(r), C.byref(ms)))
+    return dict(fma_per_s=r.value, flops=2.0 * r.value, ms=ms.value)
+
+
+MGS_KERNELS = {0: "k_mgs", 1: "k_mgs_res", 2: "k_mgs_res2"}
+
+
+def gmres_plan(n: int, u_g="fp32", max_blocks=0) -> dict:
+    """The MGS kernel instance the GMRES solves pick for order n (a query)."""
+    p = GmresPlan()
+    _check(_lib.bspai_gmres_plan(n, PREC[u_g], max_blocks, C.byref(p)))
+    return dict(kernel=MGS_KERNELS[p.kernel], per_thread=p.per_thread, block_threads=p.block_threads,
+                blocks=p.blocks)
 
 
 def gmres(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | None = None, stream=None) -> dict:

@@ -556,28 +556,40 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         T2.relres = (double*)(T2.steps + npairs);
         T2.dmax = T2.relres + npairs;
         T2.dxmax = T2.dmax + npairs;
-        cudaEvent_t e0, e1;
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
+        // every failure below goes through done(), which releases the buffers taken
+        // above; the events are destroyed on every way out of this block
+        struct Events {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            ~Events() {
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
+            }
+        } ev;
+#define BSPAI_TUNE_TRY(expr)                                                         \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess) return done(cuda_error(_e, #expr, __FILE__, __LINE__)); \
+    } while (0)
+        BSPAI_TUNE_TRY(cudaEventCreate(&ev.e0));
+        BSPAI_TUNE_TRY(cudaEventCreate(&ev.e1));
         float best = 1e30f;
         for (int cand : {128, 256, 512}) {
             int gr;
             if ((rc = grid_for(cand, &gr))) return done(rc);
-            CUDA_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
-            CUDA_TRY(cudaMemsetAsync(Xs, 0, sizeof(double) * (size_t)n * nrhs, s));
-            CUDA_TRY(cudaEventRecord(e0, s));
-            CUDA_TRY(launch_gmres(cand, gr, Bv, Xs, kmax < 8 ? kmax : 8, 0.0, T2, s));
-            CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaEventSynchronize(e1));
+            BSPAI_TUNE_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+            BSPAI_TUNE_TRY(cudaMemsetAsync(Xs, 0, sizeof(double) * (size_t)n * nrhs, s));
+            BSPAI_TUNE_TRY(cudaEventRecord(ev.e0, s));
+            BSPAI_TUNE_TRY(launch_gmres(cand, gr, Bv, Xs, kmax < 8 ? kmax : 8, 0.0, T2, s));
+            BSPAI_TUNE_TRY(cudaEventRecord(ev.e1, s));
+            BSPAI_TUNE_TRY(cudaEventSynchronize(ev.e1));
             float ms = 0;
-            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            BSPAI_TUNE_TRY(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
             if (ms < best) {
                 best = ms;
                 bd = cand;
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+#undef BSPAI_TUNE_TRY
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = bd;
     }
@@ -600,7 +612,13 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         return cudaGetLastError();
     };
     static thread_local int* t_active = nullptr;
-    if (!t_active) CUDA_TRY(cudaMallocHost(&t_active, sizeof(int)));
+    if (!t_active) {
+        cudaError_t e = cudaMallocHost(&t_active, sizeof(int));
+        if (e != cudaSuccess) {
+            t_active = nullptr;
+            return done(cuda_error(e, "cudaMallocHost(active flag)", __FILE__, __LINE__));
+        }
+    }
     // Every refinement step issues the same five operations on the same buffers, so the
     // sequence is captured once into a CUDA graph and replayed.  Capture runs on a private
     // stream (the legacy default stream cannot be captured); replays go to the caller's
@@ -656,16 +674,22 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         if (e) return done(cuda_error(e, "batched refinement step", __FILE__, __LINE__));
         if (*t_active == 0) break;
     }
-    // results
+    // results (a failure still releases the buffers through done())
+#define BSPAI_RES_TRY(expr)                                                          \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess) return done(cuda_error(_e, #expr, __FILE__, __LINE__)); \
+    } while (0)
     std::vector<int32_t> hst(npairs), hit(npairs), hsteps(npairs);
     std::vector<double> hnbe(npairs);
-    CUDA_TRY(cudaMemcpyAsync(hst.data(), S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(hit.data(), S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(hsteps.data(), S.steps, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(hnbe.data(), S.nbe, sizeof(double) * npairs, cudaMemcpyDeviceToHost, s));
-    if (pair_status) CUDA_TRY(cudaMemcpyAsync(pair_status, S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
-    if (pair_iters) CUDA_TRY(cudaMemcpyAsync(pair_iters, S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    BSPAI_RES_TRY(cudaMemcpyAsync(hst.data(), S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+    BSPAI_RES_TRY(cudaMemcpyAsync(hit.data(), S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+    BSPAI_RES_TRY(cudaMemcpyAsync(hsteps.data(), S.steps, sizeof(int32_t) * npairs, cudaMemcpyDeviceToHost, s));
+    BSPAI_RES_TRY(cudaMemcpyAsync(hnbe.data(), S.nbe, sizeof(double) * npairs, cudaMemcpyDeviceToHost, s));
+    if (pair_status) BSPAI_RES_TRY(cudaMemcpyAsync(pair_status, S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
+    if (pair_iters) BSPAI_RES_TRY(cudaMemcpyAsync(pair_iters, S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
+    BSPAI_RES_TRY(cudaStreamSynchronize(s));
+#undef BSPAI_RES_TRY
     int conv = 0, nonfin = 0, maxit = 0, maxsteps = 0;
     int64_t tot = 0;
     for (int q = 0; q < npairs; ++q) {
@@ -712,6 +736,10 @@ int gmres_ir_solve_batched(bspai_A_h A, const int32_t* row_off, int32_t nsys, in
     if (nsys < 1 || nrhs < 1 || !row_off || !B || !X)
         return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: bad batch description");
     if (BM->n != A->n || (M && M->n != A->n)) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: size mismatch");
+    for (int k = 0; k < BM->q; ++k)
+        if (BM->b[k].packed || BM->b[k].col16)
+            return set_error(BSPAI_ERR_INVALID,
+                             "gmres_ir_solve_batched: M must come from bspai_bucket_batched (its slot arrangement)");
     if ((A->n & 31) != 0) return set_error(BSPAI_ERR_INVALID, "gmres_ir_solve_batched: n must be a multiple of 32");
     if (u_g != BSPAI_FP32 && u_g != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_g must be FP32 or FP64");
     if (u_p != BSPAI_FP32 && u_p != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_p must be FP32 or FP64");

@@ -55,9 +55,11 @@ struct PackDst {
     int32_t q;
     int32_t precs[8];
     int64_t* sptr[8];
-    int32_t* col[8];
+    int32_t* col[8];     // int32 columns, or null when col16 is used
+    int16_t* col16[8];   // 16-bit column differences c - r, or null
     void* val[8];
     float scale[8];
+    int32_t packed;      // slot arrangement of every bucket (Sell::packed)
 };
 
 // In a batch of independent systems stacked block-diagonally, every 32-row
@@ -111,9 +113,11 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
                                                   const double* __restrict__ thr_g, int8_t* __restrict__ id,
                                                   int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
                                                   VT* __restrict__ bmax, VT* __restrict__ colmax,
-                                                  int* __restrict__ wmax, const int32_t* __restrict__ slice_seg) {
+                                                  int* __restrict__ wmax, const int32_t* __restrict__ slice_seg,
+                                                  int packed, unsigned* __restrict__ dmax) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nslices * kSlice) return;
+    unsigned dm = 0;  // max |c - r| of the row
     const int sg = seg_of(slice_seg, r >> 5);
     double thr[8];
 #pragma unroll
@@ -142,9 +146,18 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
                 }
             }
             if (P.precs[k] == BSPAI_E4M3) atomic_max_nonneg(colmax + col[slot], am);
+            const int64_t d = (int64_t)col[slot] - r;
+            const unsigned ad = (unsigned)(d < 0 ? (d < -0x7fffffff ? 0x7fffffff : -d) : (d > 0x7fffffff ? 0x7fffffff : d));
+            dm = ad > dm ? ad : dm;
         }
     }
     const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned t = __shfl_xor_sync(0xffffffffu, dm, o);
+        dm = t > dm ? t : dm;
+    }
+    if (lane == 0 && dm) atomicMax(dmax, dm);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         if (k >= P.q) break;
@@ -156,6 +169,7 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
             c += __shfl_xor_sync(0xffffffffu, c, o);
             m = fmax(m, (VT)__shfl_xor_sync(0xffffffffu, m, o));
         }
+        if (packed) w = (w + 3) & ~3;  // groups of four slots per row
         if (lane == 0) {
             widths[(int64_t)k * (nslices + 1) + (r >> 5)] = (int64_t)w * kSlice;
             if (c) atomicAdd(nnzk + k, (unsigned long long)c);
@@ -265,8 +279,9 @@ __global__ void __launch_bounds__(256) k_pack(int n, int nslices, const int64_t*
                 if (kk == k) pos = cnt[kk]++;
             if (D.precs[k] == BSPAI_DROP) continue;
             const int c = col[slot];
-            const int64_t dst = D.sptr[k][s] + (int64_t)pos * kSlice + lane;
-            D.col[k][dst] = c;
+            const int64_t dst = sell_slot(D.sptr[k][s], lane, pos, D.packed);
+            if (D.col16[k]) D.col16[k][dst] = (int16_t)(c - r);
+            else D.col[k][dst] = c;
             store_val(D.val[k], dst, D.precs[k], val[slot], scale[k], colscale ? colscale[c] : 1.0f);
         }
     }
@@ -278,8 +293,9 @@ __global__ void __launch_bounds__(256) k_pack(int n, int nslices, const int64_t*
         for (int kk = 0; kk < 8; ++kk)
             if (kk == k) c0 = cnt[kk];
         for (int l = c0; l < width; ++l) {
-            const int64_t dst = D.sptr[k][s] + (int64_t)l * kSlice + lane;
-            D.col[k][dst] = -1;
+            const int64_t dst = sell_slot(D.sptr[k][s], lane, l, D.packed);
+            if (D.col16[k]) D.col16[k][dst] = kCol16Pad;
+            else D.col[k][dst] = -1;
             store_zero(D.val[k], dst, D.precs[k]);
         }
     }
@@ -311,8 +327,8 @@ __global__ void k_bucket_export(int n, const int64_t* __restrict__ msptr, const 
         const BucketDev& D = B.b[k];
         double v = 0.0;
         if (D.prec != BSPAI_DROP) {
-            const int64_t p = D.sptr[s] + (int64_t)pos * kSlice + lane;
-            const int c = D.col[p];
+            const int64_t p = sell_slot(D.sptr[s], lane, pos, D.packed);
+            const int c = sell_col(D.col, D.col16, p, r);
             switch (D.prec) {
             case BSPAI_FP64: v = reinterpret_cast<const double*>(D.val)[p]; break;
             case BSPAI_FP32: v = reinterpret_cast<const float*>(D.val)[p]; break;
@@ -392,10 +408,15 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     float* d_scale = nullptr;
     VT* d_colmax = nullptr;
     int* d_wmax = nullptr;
+    unsigned* d_dmax = nullptr;
     auto cleanup = [&]() {
         dfree(d_norm, s); dfree(d_thr, s); dfree(d_w, s); dfree(d_nnzk, s);
-        dfree(d_bmax, s); dfree(d_scale, s); dfree(d_colmax, s); dfree(d_wmax, s);
+        dfree(d_bmax, s); dfree(d_scale, s); dfree(d_colmax, s); dfree(d_wmax, s); dfree(d_dmax, s);
     };
+    // One system: the packed slot arrangement, with 16-bit column differences
+    // when every |c - r| fits (the SpMV reads a row's slots four at a time).
+    // A batch keeps the plain arrangement its batched solver reads.
+    const int packed = slice_seg ? 0 : 1;
     auto fail = [&](int code) {
         cleanup();
         bspai_free(B);
@@ -419,6 +440,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     if ((rc = dalloc_t(&d_bmax, (size_t)nseg * 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_scale, (size_t)nseg * 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_wmax, 8, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_dmax, 1, s))) return fail(rc);
     if (n_e4m3) {
         if ((rc = dalloc_t(&d_colmax, (size_t)n, s))) return fail(rc);
         if ((rc = dalloc_t(&B->colscale, (size_t)n, s))) return fail(rc);
@@ -432,6 +454,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     if (!e) e = cudaMemsetAsync(d_nnzk, 0, 8 * sizeof(unsigned long long), s);
     if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(VT) * (size_t)nseg, s);
     if (!e) e = cudaMemsetAsync(d_wmax, 0, 8 * sizeof(int), s);
+    if (!e) e = cudaMemsetAsync(d_dmax, 0, sizeof(unsigned), s);
     if (!e) e = cudaMemsetAsync(d_w, 0, sizeof(int64_t) * (size_t)q * (nsl + 1), s);
     if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(VT) * (size_t)n, s);
     if (e) return fail(cuda_error(e, "bspai_bucket setup", __FILE__, __LINE__));
@@ -443,7 +466,8 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
         k_thresholds<<<g_seg, 256, 0, s>>>(P, nseg, d_norm, d_thr);
         note_launch();
         k_classify<VT><<<g_rows, 256, 0, s>>>(n, nsl, S.sell->sptr, S.sell->col, S.val, S.rowlen, P, d_thr,
-                                              B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax, slice_seg);
+                                              B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax, slice_seg,
+                                              packed, d_dmax);
         note_launch();
         k_bucket_scales<VT><<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
         note_launch();
@@ -471,6 +495,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     std::vector<double> hnorms((size_t)nseg, 0.0);
     float hscale[8] = {0};
     int hwmax[8] = {0};
+    unsigned hdmax = 0;
     for (int k = 0; k < q; ++k)
         if ((e = cudaMemcpyAsync(&slots[k], B->b[k].sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s)))
             return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
@@ -479,18 +504,22 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     if (!e) e = cudaMemcpyAsync(hnorms.data(), d_norm, sizeof(double) * (size_t)nseg, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hscale, d_scale, sizeof hscale, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hwmax, d_wmax, sizeof hwmax, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&hdmax, d_dmax, sizeof hdmax, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
     double hnorm = 0.0;
     for (double v : hnorms) hnorm = v > hnorm ? v : hnorm;
     PackDst D{};
     D.q = q;
+    D.packed = packed;
+    const bool idx16 = packed && hdmax <= 32767u;
     int64_t bytes = 0;
     for (int k = 0; k < q; ++k) {
         B->nnz_k[k] = (int64_t)nnzk[k];
         B->scale[k] = hscale[k];
         B->maxw[k] = hwmax[k];
         B->b[k].maxw = hwmax[k];
+        B->b[k].packed = packed;
         D.precs[k] = precs[k];
         D.sptr[k] = B->b[k].sptr;
         D.scale[k] = hscale[k];
@@ -500,11 +529,16 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
             continue;
         }
         B->b[k].slots = slots[k];
-        if ((rc = dalloc_t(&B->b[k].col, (size_t)slots[k], s))) return fail(rc);
+        if (idx16) {
+            if ((rc = dalloc_t(&B->b[k].col16, (size_t)slots[k], s))) return fail(rc);
+        } else {
+            if ((rc = dalloc_t(&B->b[k].col, (size_t)slots[k], s))) return fail(rc);
+        }
         if ((rc = dalloc(&B->val[k], (size_t)slots[k] * prec_bytes(precs[k]), s))) return fail(rc);
         D.col[k] = B->b[k].col;
+        D.col16[k] = B->b[k].col16;
         D.val[k] = B->val[k];
-        bytes += slots[k] * (int64_t)(4 + prec_bytes(precs[k]));
+        bytes += slots[k] * (int64_t)((idx16 ? 2 : 4) + prec_bytes(precs[k]));
     }
     if (B->colscale) bytes += (int64_t)sizeof(float) * n;
     if (n > 0) {

@@ -57,14 +57,44 @@ enum : uint32_t {
     kMagicDead = 0xDEADBEEFu
 };
 
+// Sliced ELL with 32-row slices.  Slice s holds its rows' slots in
+// [sptr[s], sptr[s + 1]), (sptr[s + 1] - sptr[s]) / 32 slots per row, each
+// row's entries first in ascending column order, then padding.  Two
+// arrangements inside a slice (sell_slot):
+//   plain:  slot l of lane t at sptr[s] + 32 l + t (a warp's loads of slot l
+//           are 32 consecutive elements);
+//   packed: the slots of a row in groups of four consecutive elements,
+//           slot l of lane t at sptr[s] + 128 (l / 4) + 4 t + l % 4, slice
+//           widths a multiple of four (one 4-element vector load per lane and
+//           group; a warp's load is 128 consecutive elements).
+// Column indices are int32 (col; -1 = padding) or, when every entry of the
+// structure satisfies |c - r| <= 32767, 16-bit differences c - r to the row r
+// (col16; INT16_MIN = padding, col = null).
 struct Sell {
     int32_t n = 0;
     int32_t nslices = 0;
     int64_t slots = 0;
     int64_t* sptr = nullptr;   // nslices + 1
-    int32_t* col = nullptr;    // slots, -1 = padding
+    int32_t* col = nullptr;    // slots, -1 = padding (null when col16 is used)
     int32_t maxw = -1;         // widest slice in slots per row (-1: unknown)
+    int32_t packed = 0;        // 1: packed arrangement (groups of four slots per row)
+    int16_t* col16 = nullptr;  // slots of 16-bit column differences c - r, or null
 };
+
+constexpr int16_t kCol16Pad = -32768;
+
+// element index of slot l of the row in lane `lane` of a slice starting at sbase
+__host__ __device__ __forceinline__ int64_t sell_slot(int64_t sbase, int lane, int l, int packed) {
+    return packed ? sbase + ((int64_t)(l >> 2) << 7) + (lane << 2) + (l & 3) : sbase + ((int64_t)l << 5) + lane;
+}
+// column of slot p of row r (-1: padding)
+__device__ __forceinline__ int sell_col(const int32_t* col, const int16_t* col16, int64_t p, int64_t r) {
+    if (col16) {
+        const int d = col16[p];
+        return d == kCol16Pad ? -1 : (int)(r + d);
+    }
+    return col[p];
+}
 
 // Device view of one precision bucket for the SpMV kernels.
 struct BucketDev {
@@ -78,6 +108,8 @@ struct BucketDev {
     const float* slicescale;   // fp16 bucket of a batch: per-slice scale (else null: use scale)
     int64_t nnz;               // entries in the bucket (-1: unknown)
     int32_t maxw;              // widest slice of the bucket in slots per row (-1: unknown)
+    int32_t packed;            // slot arrangement (Sell::packed)
+    const int16_t* col16;      // 16-bit column differences (Sell::col16), or null: col
 };
 
 struct BMDev {

@@ -687,6 +687,8 @@ struct GmresWork {
     int u32 = 0;                         // working precision u = fp32: d and x rounded to fp32
     void* res_fn = nullptr;  // k_mgs_res instance, or null for k_mgs
     int res_bd = 1024;       // its block size
+    int res_kind = 0;        // 1: k_mgs_res, 2: k_mgs_res2 (see ResInstance)
+    int res_per_thread = 0;  // its rows (k_mgs_res) or row pairs (k_mgs_res2) per thread
     int Gr = 0;              // its grid (at most one block per SM)
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
@@ -748,35 +750,38 @@ struct GmresWork {
     }
 };
 
+// One k_mgs_res / k_mgs_res2 instance: its kernel, kind (1: k_mgs_res, rows of a
+// thread one by one; 2: k_mgs_res2, rows in packed pairs), rows (R) or pairs (P)
+// per thread, and block size.  The instance is the smallest that holds a
+// block's chunk of rows: every instance listed here is reachable from
+// choose_mgs for some order n (the parity tests run each one).
+struct ResInstance {
+    void* fn = nullptr;
+    int kind = 0, per_thread = 0, bd = 0;
+};
+
 template <typename T>
-static void* pick_res(int64_t chunk, int* bd) {
+static ResInstance pick_res(int64_t chunk) {
     const int R = (int)ceil_div(chunk, 1024);
-    *bd = 1024;
-    if (R <= 1) return (void*)k_mgs_res<T, 1, 1024>;
+    if (R <= 1) return {(void*)k_mgs_res<T, 1, 1024>, 1, 1, 1024};
     if constexpr (sizeof(T) == 4) {
         // fp32: rows in adjacent pairs, packed two-lane arithmetic
-        if (R <= 2) return (void*)k_mgs_res2<1, 1024>;
-        if (R <= 4) return (void*)k_mgs_res2<2, 1024>;
-        if (R <= 8) return (void*)k_mgs_res2<4, 1024>;
+        if (R <= 2) return {(void*)k_mgs_res2<1, 1024>, 2, 1, 1024};
+        if (R <= 4) return {(void*)k_mgs_res2<2, 1024>, 2, 2, 1024};
+        if (R <= 8) return {(void*)k_mgs_res2<4, 1024>, 2, 4, 1024};
+        // more rows per block: 512 threads with more pairs each (chunk > 8192)
         const int Rp = (int)ceil_div(chunk, 512);
-        *bd = 512;
-        if (Rp <= 16) return (void*)k_mgs_res2<8, 512>;
-        if (Rp <= 24) return (void*)k_mgs_res2<12, 512>;
-        if (Rp <= 28) return (void*)k_mgs_res2<14, 512>;
-        if (Rp <= 32) return (void*)k_mgs_res2<16, 512>;
-        return nullptr;
+        if (Rp <= 24) return {(void*)k_mgs_res2<12, 512>, 2, 12, 512};
+        if (Rp <= 28) return {(void*)k_mgs_res2<14, 512>, 2, 14, 512};
+        if (Rp <= 32) return {(void*)k_mgs_res2<16, 512>, 2, 16, 512};
+        return {};
+    } else {
+        // fp64: z in shared memory, at most 8192 rows of a block (64 KB)
+        if (R <= 2) return {(void*)k_mgs_res<T, 2, 1024>, 1, 2, 1024};
+        if (R <= 4) return {(void*)k_mgs_res<T, 4, 1024>, 1, 4, 1024};
+        if (R <= 8) return {(void*)k_mgs_res<T, 8, 1024>, 1, 8, 1024};
+        return {};
     }
-    if (R <= 2) return (void*)k_mgs_res<T, 2, 1024>;
-    if (R <= 4) return (void*)k_mgs_res<T, 4, 1024>;
-    if (R <= 8) return (void*)k_mgs_res<T, 8, 1024>;
-    // more rows per block: 512 threads with twice the rows each
-    const int R2 = (int)ceil_div(chunk, 512);
-    *bd = 512;
-    if (R2 <= 16) return (void*)k_mgs_res<T, 16, 512>;
-    if (sizeof(T) == 4 && R2 <= 24) return (void*)k_mgs_res<float, 24, 512>;
-    if (sizeof(T) == 4 && R2 <= 28) return (void*)k_mgs_res<float, 28, 512>;
-    if (sizeof(T) == 4 && R2 <= 32) return (void*)k_mgs_res<float, 32, 512>;
-    return nullptr;
 }
 
 // Use the on-chip MGS kernel when one block per SM can hold its rows of z on
@@ -802,15 +807,16 @@ static int choose_mgs(GmresWork& W) {
     const size_t es = W.ug == BSPAI_FP64 ? 8 : 4;
     const size_t smem = (size_t)chunk * es;
     if (smem > 200 * 1024) return BSPAI_OK;
-    int bd = 1024;
-    void* fn = es == 8 ? pick_res<double>(chunk, &bd) : pick_res<float>(chunk, &bd);
-    if (!fn) return BSPAI_OK;
-    CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const ResInstance ri = es == 8 ? pick_res<double>(chunk) : pick_res<float>(chunk);
+    if (!ri.fn) return BSPAI_OK;
+    CUDA_TRY(cudaFuncSetAttribute(ri.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bd, smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ri.fn, ri.bd, smem));
     if (occ < 1) return BSPAI_OK;
-    W.res_fn = fn;
-    W.res_bd = bd;
+    W.res_fn = ri.fn;
+    W.res_bd = ri.bd;
+    W.res_kind = ri.kind;
+    W.res_per_thread = ri.per_thread;
     W.Gr = Gr;
     W.res_smem = smem;
     return BSPAI_OK;
@@ -1197,6 +1203,38 @@ static int gmres_one(bspai_matrix* A, const bspai_bucketed* BA, const bspai_buck
     return rc;
 }
 
+int bspai_gmres_plan(int32_t n, bspai_prec_t u_g, int32_t max_blocks, bspai_gmres_plan_t* out) {
+    if (!out) return set_error(BSPAI_ERR_INVALID, "bspai_gmres_plan: null out");
+    memset(out, 0, sizeof *out);
+    if (n < 1) return set_error(BSPAI_ERR_INVALID, "bspai_gmres_plan: n = %d", n);
+    if (u_g != BSPAI_FP32 && u_g != BSPAI_FP64) return set_error(BSPAI_ERR_UNSUPPORTED, "u_g must be FP32 or FP64");
+    GmresWork W;
+    W.n = n;
+    W.ug = u_g;
+    W.sms = max_blocks > 0 && max_blocks < num_sms() ? max_blocks : num_sms();
+    BSPAI_TRY(choose_mgs(W));
+    if (W.res_fn) {
+        out->kernel = W.res_kind;
+        out->per_thread = W.res_per_thread;
+        out->block_threads = W.res_bd;
+        out->blocks = W.Gr;
+        return BSPAI_OK;
+    }
+    int occ = 0, occ2 = 0;
+    cudaError_t e = u_g == BSPAI_FP64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs<double>, 512, 0)
+                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs<float>, 512, 0);
+    if (!e)
+        e = u_g == BSPAI_FP64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_gmres_start<double>, 512, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_gmres_start<float>, 512, 0);
+    if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
+    occ = occ < occ2 ? occ : occ2;
+    out->kernel = 0;
+    out->per_thread = 0;
+    out->block_threads = 512;
+    out->blocks = (occ >= 2 ? 2 : 1) * W.sms;
+    return BSPAI_OK;
+}
+
 int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, bspai_prec_t u_p,
                 const bspai_opts_t* opts, double* d, bspai_stream_t st, bspai_solve_info_t* info) {
     return gmres_one(A, nullptr, BM, r, u_g, u_p, opts, d, st, info);
@@ -1224,22 +1262,60 @@ constexpr size_t kNoallocScratchBytes = 64ull << 20;  // 64 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_base[128];  // device address of the scratch, per device ordinal
+// Device address of the scratch per device ordinal, with the id of the CUDA
+// context it was looked up in: after a device reset the module is loaded again
+// in a new context (possibly at another address), so a cached address is used
+// only while the current context is the one it came from.
+struct NoallocAddr {
+    unsigned long long ctx_id = 0;
+    void* base = nullptr;
+};
+static NoallocAddr g_noalloc_base[128];
+
+// The current context's process-unique id through the driver entry points
+// (the library links the CUDA runtime only); false if they are unavailable.
+static bool current_context_id(unsigned long long* id) {
+    typedef int (*GetCurrentFn)(void**);
+    typedef int (*GetIdFn)(void*, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(f);
+    });
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
 
 // The host-side name of a __device__ array is only a stand-in, not a device
-// address: the address is looked up once per device, with that device current.
+// address: the address is looked up with the device current, once per device
+// and context (on every call if the driver cannot give the context's id).
 static int noalloc_scratch_address(void** out) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return set_error(BSPAI_ERR_UNSUPPORTED, "bspai_gmres_noalloc: device ordinal %d", dev);
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);  // false too while no context is current yet
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_base[dev]) {
+    NoallocAddr& a = g_noalloc_base[dev];
+    if (!have_id || !a.base || a.ctx_id != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-allocation scratch)", __FILE__, __LINE__);
-        g_noalloc_base[dev] = p;
+        a.base = p;
+        unsigned long long id2 = 0;  // the lookup made the device's context current
+        a.ctx_id = current_context_id(&id2) ? id2 : 0;
     }
-    *out = g_noalloc_base[dev];
+    *out = a.base;
     return BSPAI_OK;
 }
 

@@ -174,8 +174,10 @@ int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, cudaStrea
 void sell_free(Sell* S, cudaStream_t s) {
     dfree(S->sptr, s);
     dfree(S->col, s);
+    dfree(S->col16, s);
     S->sptr = nullptr;
     S->col = nullptr;
+    S->col16 = nullptr;
 }
 
 }  // namespace bspai

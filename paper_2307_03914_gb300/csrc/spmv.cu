@@ -63,14 +63,14 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
     int w[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        base[k] = __ldg(M.b[k].sptr + s) + lane;
-        w[k] = (int)((__ldg(M.b[k].sptr + s + 1) - (base[k] - lane)) >> 5);
+        base[k] = __ldg(M.b[k].sptr + s);
+        w[k] = (int)((__ldg(M.b[k].sptr + s + 1) - base[k]) >> 5);
     }
     int c[Q][W];
 #pragma unroll
     for (int k = 0; k < Q; ++k)
 #pragma unroll
-        for (int l = 0; l < W; ++l) c[k][l] = l < w[k] ? __ldg(M.b[k].col + base[k] + 32 * l) : -1;
+        for (int l = 0; l < W; ++l) c[k][l] = l < w[k] ? sell_col_ldg(M.b[k], sell_slot(base[k], lane, l, M.b[k].packed), r) : -1;
     float v[Q][W], xf[Q][W];
     double vd[W], xd[W];
 #pragma unroll
@@ -80,10 +80,10 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
             const int cc = c[k][l];
             if (cc >= 0) {
                 if (F64 && k == 0) {
-                    vd[l] = __ldg(reinterpret_cast<const double*>(M.b[0].val) + base[0] + 32 * l);
+                    vd[l] = __ldg(reinterpret_cast<const double*>(M.b[0].val) + sell_slot(base[0], lane, l, M.b[0].packed));
                     xd[l] = (double)__ldg(x + cc);
                 } else {
-                    v[k][l] = decode_rt(M.b[k], base[k] + 32 * l, cc, r);
+                    v[k][l] = decode_rt(M.b[k], sell_slot(base[k], lane, l, M.b[k].packed), cc, r);
                     xf[k][l] = to_f32<XT>(__ldg(x + cc));
                 }
             }
@@ -104,9 +104,10 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
             for (int l = 0; l < W; ++l)
                 if (c[k][l] >= 0) acc = __dadd_rn(acc, __dmul_rn(vd[l], xd[l]));
             for (int l = W; l < w[k]; ++l) {
-                const int cc = __ldg(B.col + base[k] + 32 * l);
+                const int64_t pp = sell_slot(base[k], lane, l, B.packed);
+                const int cc = sell_col_ldg(B, pp, r);
                 if (cc >= 0)
-                    acc = __dadd_rn(acc, __dmul_rn(__ldg(reinterpret_cast<const double*>(B.val) + base[k] + 32 * l),
+                    acc = __dadd_rn(acc, __dmul_rn(__ldg(reinterpret_cast<const double*>(B.val) + pp),
                                                    (double)__ldg(x + cc)));
             }
             yi = __dadd_rn(yi, acc);
@@ -116,8 +117,9 @@ __global__ void __launch_bounds__(256) k_bspmv_q(const __grid_constant__ BMDev M
             for (int l = 0; l < W; ++l)
                 if (c[k][l] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[k][l], xf[k][l]));
             for (int l = W; l < w[k]; ++l) {
-                const int cc = __ldg(B.col + base[k] + 32 * l);
-                if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(decode_rt(B, base[k] + 32 * l, cc, r), to_f32<XT>(__ldg(x + cc))));
+                const int64_t pp = sell_slot(base[k], lane, l, B.packed);
+                const int cc = sell_col_ldg(B, pp, r);
+                if (cc >= 0) acc = __fadd_rn(acc, __fmul_rn(decode_rt(B, pp, cc, r), to_f32<XT>(__ldg(x + cc))));
             }
             if constexpr (F32OUT) yf = k == 0 ? acc : __fadd_rn(yf, acc);
             else yi = __dadd_rn(yi, (double)acc);
@@ -525,6 +527,216 @@ static FixFn<XT, YT> pick_fix(const BMDev& M, int W) {
     return nullptr;
 }
 
+// ---------------------------------------------------------------- packed form
+// The product on buckets in the packed slot arrangement (a row's slots in
+// groups of four consecutive elements).  Per group and lane, one vector load
+// brings the four column indices (16 B of int32 or 8 B of 16-bit differences)
+// and one the four stored values (32 / 16 / 8 / 8 / 4 B in fp64 / fp32 / fp16 /
+// bf16 / e4m3), both streamed past L1 (ld.global.cs) so that L1 keeps the
+// gathered x entries and e4m3 column scales; a warp's loads are 128
+// consecutive elements.  Then x (and the column scales) are gathered and each
+// bucket's partial sum is formed in ascending column order with the same
+// operations as the other forms: the same bits.
+
+template <int P>
+struct PkRaw;  // the four stored values of one group, converted exactly to V
+template <>
+struct PkRaw<BSPAI_FP64> {
+    static __device__ __forceinline__ void get(const void* val, int64_t g, double v[4]) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(reinterpret_cast<const double*>(val) + g));
+        const double2 b = __ldcs(reinterpret_cast<const double2*>(reinterpret_cast<const double*>(val) + g + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <>
+struct PkRaw<BSPAI_FP32> {
+    static __device__ __forceinline__ void get(const void* val, int64_t g, float v[4]) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(val) + g));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+};
+template <>
+struct PkRaw<BSPAI_FP16> {
+    static __device__ __forceinline__ void get(const void* val, int64_t g, float v[4]) {
+        const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __half*>(val) + g));
+        const __half2 h01 = *reinterpret_cast<const __half2*>(&u.x), h23 = *reinterpret_cast<const __half2*>(&u.y);
+        v[0] = __low2float(h01); v[1] = __high2float(h01); v[2] = __low2float(h23); v[3] = __high2float(h23);
+    }
+};
+template <>
+struct PkRaw<BSPAI_BF16> {
+    static __device__ __forceinline__ void get(const void* val, int64_t g, float v[4]) {
+        const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(val) + g));
+        v[0] = __uint_as_float(u.x << 16); v[1] = __uint_as_float(u.x & 0xffff0000u);
+        v[2] = __uint_as_float(u.y << 16); v[3] = __uint_as_float(u.y & 0xffff0000u);
+    }
+};
+template <>
+struct PkRaw<BSPAI_E4M3> {
+    static __device__ __forceinline__ void get(const void* val, int64_t g, float v[4]) {
+        const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(reinterpret_cast<const __nv_fp8_storage_t*>(val) + g));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            __nv_fp8_e4m3 f;
+            f.__x = (__nv_fp8_storage_t)((u >> (8 * e)) & 0xffu);
+            v[e] = float(f);
+        }
+    }
+};
+
+// one row's share of one packed bucket
+template <int P, typename XT, bool I16>
+struct PkRow {
+    using V = typename std::conditional<P == BSPAI_FP64, double, float>::type;
+    int64_t sb;  // first element of the row's slice
+    int ng;      // groups of four slots per row in the slice
+    int c[4];
+    V v[4], xv[4];
+    __device__ __forceinline__ void ptrs(const BucketDev& B, int64_t s) {
+        sb = __ldg(B.sptr + s);
+        ng = (int)((__ldg(B.sptr + s + 1) - sb) >> 7);
+    }
+    // indices and stored values of group grp (none when the slice has no
+    // group); an fp16 value times its bucket's scale (exact: a power of two)
+    __device__ __forceinline__ void load(const BucketDev& B, int grp, int lane, int64_t r, float sc) {
+        if (grp >= ng) {
+            c[0] = c[1] = c[2] = c[3] = -1;
+            return;
+        }
+        const int64_t g = sb + ((int64_t)grp << 7) + (lane << 2);
+        if constexpr (I16) {
+            const uint2 u = __ldcs(reinterpret_cast<const uint2*>(B.col16 + g));
+            const int d0 = (int16_t)(u.x & 0xffffu), d1 = (int16_t)(u.x >> 16), d2 = (int16_t)(u.y & 0xffffu),
+                      d3 = (int16_t)(u.y >> 16);
+            c[0] = d0 == kCol16Pad ? -1 : (int)r + d0;
+            c[1] = d1 == kCol16Pad ? -1 : (int)r + d1;
+            c[2] = d2 == kCol16Pad ? -1 : (int)r + d2;
+            c[3] = d3 == kCol16Pad ? -1 : (int)r + d3;
+        } else {
+            const int4 u = __ldcs(reinterpret_cast<const int4*>(B.col + g));
+            c[0] = u.x; c[1] = u.y; c[2] = u.z; c[3] = u.w;
+        }
+        PkRaw<P>::get(B.val, g, v);
+        if constexpr (P == BSPAI_FP16) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = __fmul_rn(v[e], sc);
+        }
+    }
+    // x entries; an e4m3 value times its scale (per column of M, or per row of
+    // a transposed M; exact: a power of two)
+    __device__ __forceinline__ void gather(const BucketDev& B, const XT* __restrict__ x, int64_t r) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (c[e] >= 0) {
+                if constexpr (P == BSPAI_FP64) xv[e] = (double)__ldg(x + c[e]);
+                else xv[e] = to_f32<XT>(__ldg(x + c[e]));
+                if constexpr (P == BSPAI_E4M3)
+                    v[e] = __fmul_rn(v[e], B.colscale ? __ldg(B.colscale + c[e]) : __ldg(B.rowscale + r));
+            }
+    }
+    // add the group's products to acc in slot order
+    __device__ __forceinline__ void accumulate(V& acc) const {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (c[e] >= 0) {
+                if constexpr (P == BSPAI_FP64) acc = __dadd_rn(acc, __dmul_rn(v[e], xv[e]));
+                else acc = __fadd_rn(acc, __fmul_rn(v[e], xv[e]));
+            }
+    }
+    // the partial sum y_i^(k): group 0 (already loaded and gathered), then the
+    // rest (ONE: the slice has at most one group)
+    template <bool ONE>
+    __device__ __forceinline__ V sum(const BucketDev& B, const XT* __restrict__ x, float sc, int lane, int64_t r) {
+        V acc = V(0);
+        accumulate(acc);
+        if constexpr (!ONE) {
+            for (int grp = 1; grp < ng; ++grp) {
+                load(B, grp, lane, r, sc);
+                gather(B, x, r);
+                accumulate(acc);
+            }
+        }
+        return acc;
+    }
+};
+
+template <int P0, int P1, bool ONE>
+struct PkMinBlocks {
+    static constexpr int value = (P0 == BSPAI_FP64 || P1 == BSPAI_FP64) ? 4 : (ONE ? 8 : 4);
+};
+
+// P1 < 0: one bucket.  ONE: every row of the matrix has at most four slots
+// per bucket (one group), so the kernel has no loop and few registers: eight
+// 256-thread blocks fit per SM (four with the loop or with an fp64 bucket).
+template <typename XT, typename YT, int P0, int P1, bool I16, bool ONE>
+__global__ void __launch_bounds__(256, PkMinBlocks<P0, P1, ONE>::value)
+    k_bspmv_pk(const __grid_constant__ BMDev M, const XT* __restrict__ x, YT* __restrict__ y,
+               const int* __restrict__ jd, int64_t ldx, int64_t ldy, int yoff) {
+    if (jd) {
+        if (jd[1]) return;
+        const int64_t j = jd[0];
+        x += j * ldx;
+        y += (j + yoff) * ldy;
+    }
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)ceil_div(M.n, kSlice) * kSlice) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    PkRow<P0, XT, I16> a;
+    PkRow<(P1 < 0 ? BSPAI_FP32 : P1), XT, I16> b;
+    const float sc0 = M.b[0].slicescale ? __ldg(M.b[0].slicescale + s) : M.b[0].scale;
+    float sc1 = 1.0f;
+    a.ptrs(M.b[0], s);
+    if constexpr (P1 >= 0) {
+        sc1 = M.b[1].slicescale ? __ldg(M.b[1].slicescale + s) : M.b[1].scale;
+        b.ptrs(M.b[1], s);
+    }
+    a.load(M.b[0], 0, lane, r, sc0);
+    if constexpr (P1 >= 0) b.load(M.b[1], 0, lane, r, sc1);
+    a.gather(M.b[0], x, r);
+    if constexpr (P1 >= 0) b.gather(M.b[1], x, r);
+    constexpr bool narrow = P0 != BSPAI_FP64 && P1 != BSPAI_FP64;
+    if constexpr (narrow && std::is_same<YT, float>::value) {
+        // as in k_bspmv_fix: the fp32 result of at most two fp32 partials needs no fp64 arithmetic
+        float yf = a.template sum<ONE>(M.b[0], x, sc0, lane, r);
+        if constexpr (P1 >= 0) yf = __fadd_rn(yf, b.template sum<ONE>(M.b[1], x, sc1, lane, r));
+        if (r < M.n) y[r] = yf;
+    } else {
+        double yi = __dadd_rn(0.0, (double)a.template sum<ONE>(M.b[0], x, sc0, lane, r));
+        if constexpr (P1 >= 0) yi = __dadd_rn(yi, (double)b.template sum<ONE>(M.b[1], x, sc1, lane, r));
+        if (r < M.n) y[r] = from_f64<YT>(yi);
+    }
+}
+
+// the compiled packed mixes (as pick_fix), for either index width; null if
+// the buckets are not all packed alike or the mix is not compiled
+template <typename XT, typename YT, bool I16, bool ONE>
+static FixFn<XT, YT> pick_pk_mix(const BMDev& M) {
+#define BSPAI_PK1(p) \
+    if (M.q == 1 && M.b[0].prec == p) return k_bspmv_pk<XT, YT, p, -1, I16, ONE>;
+#define BSPAI_PK2(p0, p1) \
+    if (M.q == 2 && M.b[0].prec == p0 && M.b[1].prec == p1) return k_bspmv_pk<XT, YT, p0, p1, I16, ONE>;
+    BSPAI_PK1(BSPAI_FP32) BSPAI_PK1(BSPAI_FP64) BSPAI_PK1(BSPAI_FP16) BSPAI_PK1(BSPAI_BF16) BSPAI_PK1(BSPAI_E4M3)
+    BSPAI_PK2(BSPAI_FP16, BSPAI_E4M3) BSPAI_PK2(BSPAI_FP32, BSPAI_FP16) BSPAI_PK2(BSPAI_FP64, BSPAI_FP32)
+    BSPAI_PK2(BSPAI_FP32, BSPAI_E4M3) BSPAI_PK2(BSPAI_FP16, BSPAI_BF16)
+#undef BSPAI_PK1
+#undef BSPAI_PK2
+    return nullptr;
+}
+
+template <typename XT, typename YT>
+static FixFn<XT, YT> pick_pk(const BMDev& M) {
+    int maxw = 0;
+    for (int k = 0; k < M.q; ++k) {
+        if (!M.b[k].packed || (M.b[k].col16 != nullptr) != (M.b[0].col16 != nullptr) || M.b[k].maxw < 0)
+            return nullptr;
+        maxw = M.b[k].maxw > maxw ? M.b[k].maxw : maxw;
+    }
+    const bool i16 = M.b[0].col16 != nullptr, one = maxw <= 4;
+    if (i16) return one ? pick_pk_mix<XT, YT, true, true>(M) : pick_pk_mix<XT, YT, true, false>(M);
+    return one ? pick_pk_mix<XT, YT, false, true>(M) : pick_pk_mix<XT, YT, false, false>(M);
+}
+
 template <typename XT, typename YT>
 using BspmvFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int);
 
@@ -553,6 +765,8 @@ BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     d.b[0].slicescale = nullptr;
     d.b[0].nnz = -1;
     d.b[0].maxw = S.maxw;
+    d.b[0].packed = S.packed;
+    d.b[0].col16 = S.col16;
     return d;
 }
 
@@ -591,6 +805,8 @@ static int align16i(int v) { return (v + 15) & ~15; }
 // every warp busy, or a stage ring that does not fit).
 static bool tma_plan(const BMDev& M, StageLayout* L, size_t* smem) {
     if (M.q < 1 || M.q > 4) return false;
+    for (int k = 0; k < M.q; ++k)  // the staged form reads the plain arrangement with int32 columns
+        if (M.b[k].packed || M.b[k].col16) return false;
     if (ceil_div(M.n, kSlice) < (int64_t)2 * kTmaWarps * num_sms()) return false;
     int off = kStageHeader;
     for (int k = 0; k < M.q; ++k) {
@@ -662,7 +878,13 @@ static void launch_typed(const BMDev& M0, const XT* x, YT* y, const int* jd, int
     }
     const int W = (M.q <= 2 && (!known || maxw > 4)) ? 8 : 4;
     const int form = g_spmv_form.load(std::memory_order_relaxed);
-    if (form == BSPAI_SPMV_AUTO && known) {
+    if (form == BSPAI_SPMV_AUTO && M.q >= 1 && M.b[0].packed) {
+        if (FixFn<XT, YT> pf = pick_pk<XT, YT>(M)) {
+            pf<<<grid, 256, 0, s>>>(M, x, y, jd, ldx, ldy, yoff);
+            return;
+        }
+    }
+    if (form == BSPAI_SPMV_AUTO && known && !M.b[0].packed) {
         if (FixFn<XT, YT> ff = pick_fix<XT, YT>(M, W)) {
             ff<<<grid, 256, 0, s>>>(M, x, y, jd, ldx, ldy, yoff);
             return;
@@ -719,6 +941,8 @@ BMDev bspai_bucketed::dev() const {
         d.b[k].slicescale = sscale[k];
         d.b[k].nnz = nnz_k[k];
         d.b[k].maxw = maxw[k];
+        d.b[k].packed = b[k].packed;
+        d.b[k].col16 = b[k].col16;
     }
     return d;
 }

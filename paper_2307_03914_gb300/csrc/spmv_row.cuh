@@ -44,24 +44,40 @@ __device__ __forceinline__ float decode<BSPAI_E4M3>(const void* val, int64_t p, 
     return __fmul_rn(float(e), __ldg(colscale + c));
 }
 
-// fp32 partial sum of one row over one narrow bucket.  Loads are issued four
+// column of slot p of row r, read through the read-only path
+__device__ __forceinline__ int sell_col_ldg(const BucketDev& B, int64_t p, int64_t r) {
+    if (B.col16) {
+        const int d = __ldg(B.col16 + p);
+        return d == kCol16Pad ? -1 : (int)(r + d);
+    }
+    return __ldg(B.col + p);
+}
+
+// fp32 partial sum of one row over one narrow bucket (w slots per row of its
+// slice starting at sbase, either slot arrangement).  Loads are issued four
 // slots ahead of the (strictly sequential) accumulation.
 template <int PREC, typename XT>
-__device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, int64_t end,
+__device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t sbase, int w,
                                                  const XT* __restrict__ x, int64_t r) {
     // e4m3 scales: per column of M, or per row of a transposed M; fp16: per bucket or per slice
     const float* st = B.colscale ? B.colscale : B.rowscale;
     const float sc = B.slicescale ? __ldg(B.slicescale + (r >> 5)) : B.scale;
+    const int lane = (int)(r & 31);
     float acc = 0.0f;
-    for (; p + 96 < end; p += 128) {
+    int l = 0;
+    for (; l + 3 < w; l += 4) {
+        int64_t p[4];
         int c[4];
         float v[4], xv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = __ldg(B.col + p + 32 * u);
+        for (int u = 0; u < 4; ++u) {
+            p[u] = sell_slot(sbase, lane, l + u, B.packed);
+            c[u] = sell_col_ldg(B, p[u], r);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (c[u] >= 0) {
-                v[u] = decode<PREC>(B.val, p + 32 * u, sc, st, B.colscale ? c[u] : (int)r);
+                v[u] = decode<PREC>(B.val, p[u], sc, st, B.colscale ? c[u] : (int)r);
                 xv[u] = to_f32<XT>(__ldg(x + c[u]));
             }
         }
@@ -69,10 +85,11 @@ __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, 
         for (int u = 0; u < 4; ++u)
             if (c[u] >= 0) acc = __fadd_rn(acc, __fmul_rn(v[u], xv[u]));
     }
-    for (; p < end; p += 32) {
-        int c = __ldg(B.col + p);
+    for (; l < w; ++l) {
+        const int64_t p = sell_slot(sbase, lane, l, B.packed);
+        const int c = sell_col_ldg(B, p, r);
         if (c >= 0) {
-            float v = decode<PREC>(B.val, p, sc, st, B.colscale ? c : (int)r);
+            const float v = decode<PREC>(B.val, p, sc, st, B.colscale ? c : (int)r);
             acc = __fadd_rn(acc, __fmul_rn(v, to_f32<XT>(__ldg(x + c))));
         }
     }
@@ -80,19 +97,25 @@ __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t p, 
 }
 
 template <typename XT>
-__device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t p, int64_t end,
-                                                  const XT* __restrict__ x) {
+__device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t sbase, int w,
+                                                  const XT* __restrict__ x, int64_t r) {
     const double* val = reinterpret_cast<const double*>(B.val);
+    const int lane = (int)(r & 31);
     double acc = 0.0;
-    for (; p + 96 < end; p += 128) {
+    int l = 0;
+    for (; l + 3 < w; l += 4) {
+        int64_t p[4];
         int c[4];
         double v[4], xv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = __ldg(B.col + p + 32 * u);
+        for (int u = 0; u < 4; ++u) {
+            p[u] = sell_slot(sbase, lane, l + u, B.packed);
+            c[u] = sell_col_ldg(B, p[u], r);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (c[u] >= 0) {
-                v[u] = __ldg(val + p + 32 * u);
+                v[u] = __ldg(val + p[u]);
                 xv[u] = (double)__ldg(x + c[u]);
             }
         }
@@ -100,8 +123,9 @@ __device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t p,
         for (int u = 0; u < 4; ++u)
             if (c[u] >= 0) acc = __dadd_rn(acc, __dmul_rn(v[u], xv[u]));
     }
-    for (; p < end; p += 32) {
-        int c = __ldg(B.col + p);
+    for (; l < w; ++l) {
+        const int64_t p = sell_slot(sbase, lane, l, B.packed);
+        const int c = sell_col_ldg(B, p, r);
         if (c >= 0) acc = __dadd_rn(acc, __dmul_rn(__ldg(val + p), (double)__ldg(x + c)));
     }
     return acc;
@@ -123,34 +147,22 @@ __device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c,
 // y_i = sum_k y_i^(k) for row r of a bucketed matrix: each bucket's partial sum
 // in ascending column order (fp64 for an fp64 bucket, fp32 otherwise), the
 // partial sums added in fp64 in bucket order.
-// The slot range of bucket k + 1 is loaded while bucket k's partial sum is
-// formed, so a row's dependent loads are the first range, then per bucket its
-// column indices and x entries.
 template <typename XT>
 __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const XT* __restrict__ x) {
     const int64_t s = r >> 5;
-    const int lane = (int)(r & 31);
     double yi = 0.0;
-    int64_t pn = 0, en = 0;
-    if (M.q > 0) {
-        pn = M.b[0].sptr[s] + lane;
-        en = M.b[0].sptr[s + 1];
-    }
     for (int k = 0; k < M.q; ++k) {
         const BucketDev& B = M.b[k];
-        const int64_t p0 = pn;
-        const int64_t end = en;
-        if (k + 1 < M.q) {
-            pn = M.b[k + 1].sptr[s] + lane;
-            en = M.b[k + 1].sptr[s + 1];
-        }
+        if (B.prec == BSPAI_DROP) continue;  // dropped entries are not stored
+        const int64_t sb = B.sptr[s];
+        const int w = (int)((B.sptr[s + 1] - sb) >> 5);
         switch (B.prec) {
-        case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT>(B, p0, end, x)); break;
-        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, p0, end, x, r)); break;
-        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT>(B, p0, end, x, r)); break;
-        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT>(B, p0, end, x, r)); break;
-        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT>(B, p0, end, x, r)); break;
-        default: break;  // dropped entries are not stored
+        case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT>(B, sb, w, x, r)); break;
+        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, sb, w, x, r)); break;
+        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT>(B, sb, w, x, r)); break;
+        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT>(B, sb, w, x, r)); break;
+        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT>(B, sb, w, x, r)); break;
+        default: break;
         }
     }
     return yi;
@@ -159,7 +171,8 @@ __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const 
 // Two rows at once (rows ra and rb, in slices of their own): the same partial
 // sums as row_partial_f32 / row_partial_f64 for each row, in the same order,
 // with the loads of both rows issued together so that each thread keeps two
-// independent chains of gathers in flight.
+// independent chains of gathers in flight.  Plain slot arrangement and int32
+// columns only: the batched bucketing, whose solver uses these, keeps them.
 template <int PREC, typename XT>
 __device__ __forceinline__ void row_partial2_f32(const BucketDev& B, int64_t pa, int64_t ea, int64_t pb, int64_t eb,
                                                  const XT* __restrict__ x, int64_t ra, int64_t rb, float& acc_a,

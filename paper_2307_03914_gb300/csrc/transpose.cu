@@ -15,12 +15,15 @@ namespace bspai {
 
 int launch_row_abs_sum_max(const Sell& S, const double* val, double* out, cudaStream_t s);
 
+// (both read the source in either slot arrangement and either index width)
 __global__ void k_tcount(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
-                         unsigned long long* __restrict__ cnt) {
+                         const int16_t* __restrict__ col16, int packed, unsigned long long* __restrict__ cnt) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    for (int64_t p = sptr[r >> 5] + (r & 31); p < sptr[(r >> 5) + 1]; p += kSlice) {
-        const int c = col[p];
+    const int64_t b = sptr[r >> 5];
+    const int w = (int)((sptr[(r >> 5) + 1] - b) >> 5);
+    for (int l = 0; l < w; ++l) {
+        const int c = sell_col(col, col16, sell_slot(b, (int)(r & 31), l, packed), r);
         if (c >= 0) atomicAdd(cnt + c, 1ull);
     }
 }
@@ -31,12 +34,15 @@ __global__ void k_i64_to_i32(int64_t count, const int64_t* __restrict__ in, int3
 }
 
 __global__ void k_tscatter(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
-                           const int32_t* __restrict__ trp, unsigned* __restrict__ cur, int32_t* __restrict__ tcol,
-                           int64_t* __restrict__ tsrc) {
+                           const int16_t* __restrict__ col16, int packed, const int32_t* __restrict__ trp,
+                           unsigned* __restrict__ cur, int32_t* __restrict__ tcol, int64_t* __restrict__ tsrc) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    for (int64_t p = sptr[r >> 5] + (r & 31); p < sptr[(r >> 5) + 1]; p += kSlice) {
-        const int c = col[p];
+    const int64_t b = sptr[r >> 5];
+    const int w = (int)((sptr[(r >> 5) + 1] - b) >> 5);
+    for (int l = 0; l < w; ++l) {
+        const int64_t p = sell_slot(b, (int)(r & 31), l, packed);
+        const int c = sell_col(col, col16, p, r);
         if (c < 0) continue;
         const int64_t pos = trp[c] + atomicAdd(cur + c, 1u);
         tcol[pos] = (int32_t)r;
@@ -119,14 +125,14 @@ static int transpose_structure(const Sell& S, int64_t nnz, TransposeMap& T, Sell
     if (e) return done(cuda_error(e, "transpose setup", __FILE__, __LINE__));
     const unsigned g = (unsigned)ceil_div(n, 256);
     if (n > 0) {
-        k_tcount<<<g, 256, 0, s>>>(n, S.sptr, S.col, cnt);
+        k_tcount<<<g, 256, 0, s>>>(n, S.sptr, S.col, S.col16, S.packed, cnt);
         note_launch();
     }
     if ((rc = scan_exclusive_i64(reinterpret_cast<const int64_t*>(cnt), rp64, n, s))) return done(rc);
     k_i64_to_i32<<<(unsigned)ceil_div((int64_t)n + 1, 256), 256, 0, s>>>((int64_t)n + 1, rp64, T.trp);
     note_launch();
     if (n > 0) {
-        k_tscatter<<<g, 256, 0, s>>>(n, S.sptr, S.col, T.trp, cur, T.tcol, T.tsrc);
+        k_tscatter<<<g, 256, 0, s>>>(n, S.sptr, S.col, S.col16, S.packed, T.trp, cur, T.tcol, T.tsrc);
         note_launch();
         k_tsort<<<g, 256, 0, s>>>(n, T.trp, T.tcol, T.tsrc);
         note_launch();
@@ -160,13 +166,21 @@ static size_t prec_size(int prec) {
     }
 }
 
-__global__ void k_adjoint_grad(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+// dA[p] = sum_r -lambda_r[i] x_r[j] over the nrhs right-hand sides (r ascending,
+// fp64, each product and sum rounded once), for the p-th nonzero (i, j) of A
+__global__ void k_adjoint_grad(int n, int nrhs, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                const double* __restrict__ lambda, const double* __restrict__ x,
                                double* __restrict__ dA) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double li = -lambda[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) dA[p] = __dmul_rn(li, x[col[p]]);
+    const int p0 = rp[i], p1 = rp[i + 1];
+    for (int p = p0; p < p1; ++p) {
+        const int64_t c = col[p];
+        double acc = 0.0;
+        for (int r = 0; r < nrhs; ++r)
+            acc = __dadd_rn(acc, __dmul_rn(-lambda[(int64_t)r * n + i], x[(int64_t)r * n + c]));
+        dA[p] = acc;
+    }
 }
 
 }  // namespace bspai
@@ -322,13 +336,16 @@ int bspai_bucket_transpose(bspai_BM_h BM, bspai_stream_t st, bspai_BM_h* out) {
     return BSPAI_OK;
 }
 
-int bspai_adjoint_grad_A(const bspai_csr_t* A, const double* lambda, const double* x, double* dA, bspai_stream_t st) {
+int bspai_adjoint_grad_A(const bspai_csr_t* A, int32_t nrhs, const double* lambda, const double* x, double* dA,
+                         bspai_stream_t st) {
     cudaStream_t s = (cudaStream_t)st;
     if (!A || A->n < 0) return set_error(BSPAI_ERR_INVALID, "bspai_adjoint_grad_A: bad matrix");
+    if (nrhs < 1) return set_error(BSPAI_ERR_INVALID, "bspai_adjoint_grad_A: nrhs = %d", nrhs);
     if (A->n == 0) return BSPAI_OK;
     if (!A->row_ptr || !A->col || !lambda || !x || !dA)
         return set_error(BSPAI_ERR_INVALID, "bspai_adjoint_grad_A: null pointer");
-    k_adjoint_grad<<<(unsigned)ceil_div(A->n, 256), 256, 0, s>>>(A->n, A->row_ptr, A->col, lambda, x, dA);
+    ProfScope ps(BSPAI_K_OTHER, s);
+    k_adjoint_grad<<<(unsigned)ceil_div(A->n, 256), 256, 0, s>>>(A->n, nrhs, A->row_ptr, A->col, lambda, x, dA);
     note_launch();
     CUDA_LAUNCH_CHECK();
     return BSPAI_OK;

@@ -165,3 +165,18 @@ def test_adjoint_full_size_16_rhs(B):
     am[p] -= h
     fd = (L(dev(ap), b.detach()) - L(dev(am), b.detach())) / (2 * h)
     assert abs(fd - gA[p]) <= 1e-5 * max(abs(fd), 1e-3)
+
+
+def test_adjoint_grad_multi_rhs_bitexact(B):
+    """dL/dA summed over right-hand sides inside the kernel, bit-exact against
+    the oracle's sum (r ascending, one rounding per product and per sum)."""
+    wl = W.workload("diffusion2d", grid=32)
+    A = wl["A"]
+    rng = np.random.default_rng(21)
+    Ad = B.DeviceCSR.from_host(A)
+    for nrhs in (1, 3, 16):
+        lam = rng.uniform(-1, 1, (nrhs, A.n))
+        x = rng.uniform(-1, 1, (nrhs, A.n))
+        dA = torch.full((A.nnz,), np.nan, dtype=torch.float64, device="cuda")
+        B.adjoint_grad_A(Ad, dev(lam if nrhs > 1 else lam[0]), dev(x if nrhs > 1 else x[0]), dA)
+        assert np.array_equal(host(dA), O.adjoint_grad_A(A, lam, x)), nrhs

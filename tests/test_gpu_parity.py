@@ -2,7 +2,7 @@
 on the same seeded inputs (sizes that span several 32-row slices and end in a
 ragged slice).
 
-Bars (the design doc derives them):
+Bars:
   * residual (Dot2, u_r ~ u^2), A v in u_p, x0 = M b in u_f, the bucketed SpMV,
     bucket ids, ||M||_inf and the stored bucket values: bit-exact (both sides
     run the same sequence of correctly rounded operations per row);

@@ -73,3 +73,26 @@ def test_transpose_csr_roundtrip(orc):
     Ad = A.to_scipy().toarray()
     T = W.CSR(A.n, trp, tcol, tval).to_scipy().toarray()
     assert np.array_equal(T, Ad.T)
+
+
+def test_adjoint_grad_multi_rhs_pins(orc):
+    """The multi-right-hand-side gradient: nrhs = 1 is -lambda_i x_j on every
+    nonzero (i, j); on integer-valued inputs the fp64 sum is exact and equals
+    the integer sum over r of -lambda_r[i] x_r[j]; a wrong index (lambda_j x_i)
+    or a dropped right-hand side fails one of these."""
+    wl = W.workload("convdiff2d", grid=7)
+    A = wl["A"]
+    n = A.n
+    rng = np.random.default_rng(9)
+    lam1, x1 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    g1 = orc.adjoint_grad_A(A, lam1, x1)
+    for i in range(n):
+        for p in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            assert g1[p] == -lam1[i] * x1[A.col[p]]
+    lam = rng.integers(-1000, 1000, (5, n)).astype(np.float64)
+    x = rng.integers(-1000, 1000, (5, n)).astype(np.float64)
+    g = orc.adjoint_grad_A(A, lam, x)
+    for i in range(n):
+        for p in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            j = int(A.col[p])
+            assert g[p] == float(sum(-int(lam[r, i]) * int(x[r, j]) for r in range(5)))
