@@ -599,6 +599,44 @@ def main():
         BMc.free()
         Ahc.free()
 
+    # ---------------- componentwise (x-dependent) bucketing study: re-bucketing fused into every product
+    # (bspai_apply_cw) against the normwise bucketed product with the same precisions and eps on the same M
+    if not args.no_comparator:
+        cw_precs = ["fp64", "fp32", "bf16", "drop"]
+        Mq, _ = B.bspai_build(Ad, Pd, wl["spai_eps"])
+        BMq, bq = B.bspai_bucket(Mq, args.bucket_eps, cw_precs)
+        xq = torch.rand(n, device="cuda", dtype=torch.float32) * 2 - 1
+        yq = torch.empty(n, device="cuda", dtype=torch.float32)
+        cw_counts = B.apply_cw(Mq, args.bucket_eps, cw_precs, xq, yq, counts=True)
+
+        def med(fn, reps=20):
+            for _ in range(3):
+                fn()
+            ts_ = []
+            for _ in range(reps):
+                q0 = torch.cuda.Event(enable_timing=True)
+                q1 = torch.cuda.Event(enable_timing=True)
+                q0.record(stream)
+                for _ in range(10):
+                    fn()
+                q1.record(stream)
+                torch.cuda.synchronize()
+                ts_.append(q0.elapsed_time(q1) / 10)
+            return float(np.median(ts_))
+
+        t_cw = med(lambda: B.apply_cw(Mq, args.bucket_eps, cw_precs, xq, yq))
+        t_nw = med(lambda: B.apply(BMq, xq, yq))
+        out["componentwise_study"] = {
+            "what": "y = M x with buckets by |m_ij x_j| against eps (|M||x|)_i / u_k, formed inside every product "
+                    "(bspai_apply_cw), against the normwise buckets of eq. (nint) stored once (bspai_apply); "
+                    "same M, precisions and eps; 10 back-to-back launches per sample, median of 20",
+            "precs": cw_precs, "bucket_eps": args.bucket_eps,
+            "cw_us_per_product": t_cw * 1e3, "normwise_us_per_product": t_nw * 1e3,
+            "cw_bucket_nnz_for_one_x": cw_counts, "normwise_bucket_nnz": bq["nnz_k"],
+            "normwise_storage_pct": bq["storage_pct"]}
+        Mq.free()
+        BMq.free()
+
     # ---------------- ALU rooflines: SPAI build (fp32 flops) and the Dot2 residual (fp64 operations) against
     # the measured issue rate of the plain FMA pipes (bspai_probe_fma)
     if not args.no_comparator:

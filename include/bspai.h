@@ -171,6 +171,25 @@ int bspai_profile_enable(int on);
 /* Synchronises the recorded events and returns the totals; reset = 1 clears them. */
 int bspai_profile_read(bspai_profile_t* out, int reset);
 
+/* ------------------------------------------------------------------ componentwise study */
+/* The componentwise, x-dependent bucketed product y = M x: Section 2.3 notes
+ * that Graillat et al. also bucket by the products, for a componentwise
+ * backward-error bound, and sets that aside because the buckets depend on x.
+ * The paper does not print the rule; here, per row i, s_i = (|M||x|)_i (fp64,
+ * ascending columns) and entry (i, j) goes to bucket k by the intervals of
+ * eq. (nint) applied to fl64(|m_ij| |x_j|) against t_k = eps s_i / u_k.  The
+ * product is then Alg 2.3 on those buckets, decoupled as bspai_apply (fp64
+ * bucket in fp64, fp32 / bf16 buckets in fp32 with x rounded to fp32, partial
+ * sums added in fp64 in bucket order).  Both steps run in one launch per
+ * product, reading M in u_f (no stored buckets).  precs: q <= 4 of BSPAI_FP64,
+ * BSPAI_FP32, BSPAI_BF16, BSPAI_DROP with increasing unit roundoff (fp16 and
+ * e4m3 need a scale fitted to each bucket: BSPAI_ERR_UNSUPPORTED).  x, y:
+ * device, n entries, FP64 or FP32.  ids (device int8, nnz(M), CSR order) and
+ * nnz_k (host, q entries; the call then synchronises s) may be NULL. */
+int bspai_apply_cw(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t q, const void* x,
+                   bspai_prec_t x_prec, void* y, bspai_prec_t y_prec, int8_t* ids, int64_t* nnz_k,
+                   bspai_stream_t s);
+
 /* ------------------------------------------------------------------ A */
 /* Prepares A (n x n, values required) for the kernels: sliced-ELL copies of
  * its structure with fp64 values (residual, u_r) and fp32 values (u_p).

@@ -99,6 +99,9 @@ def _declare(L):
     L.orc_bucket_ids.argtypes = [C.c_int, _i32p, _f64p, C.c_double, _i32p, C.c_int, _i8p,
                                  _i64p, _f64p, C.POINTER(C.c_double)]
     L.orc_bucket_ids.restype = C.c_int
+    L.orc_bucket_ids_cw.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, C.c_double, _i32p, C.c_int, _i8p,
+                                    _i64p, _f64p]
+    L.orc_bucket_ids_cw.restype = C.c_int
     L.orc_storage_pct.argtypes = [_i64p, _i32p, C.c_int, C.c_int]
     L.orc_storage_pct.restype = C.c_double
     L.orc_bucket_store.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i8p, _i32p, C.c_int,
@@ -284,6 +287,24 @@ def bucket_ids(row_ptr, val, bucket_eps: float, fmts) -> dict:
     if rc != 0:
         raise ValueError("bucket precisions must have strictly increasing unit roundoff")
     return dict(ids=ids, nnz_k=nnz_k, thr=thr, norm=nrm.value)
+
+
+def bucket_ids_cw(row_ptr, col, val, x, bucket_eps: float, fmts) -> dict:
+    """Componentwise, x-dependent bucketing (Section 2.3 mentions it; reading:
+    eq. (nint) on |a_ij| |x_j| against eps (|A||x|)_i / u_k, row by row).
+    Pinned by the interval definition entry by entry and by the componentwise
+    backward-error bound with exact rationals (tests)."""
+    f = _fmts(fmts)
+    q = len(f)
+    n = len(row_ptr) - 1
+    ids = np.zeros(int(row_ptr[-1]), dtype=np.int8)
+    nnz_k = np.zeros(q, dtype=np.int64)
+    srow = np.zeros(n)
+    rc = lib().orc_bucket_ids_cw(n, _i32(row_ptr), _i32(col), _f64(val), _f64(x), bucket_eps, f, q, ids, nnz_k,
+                                 srow)
+    if rc != 0:
+        raise ValueError("bucket precisions must have strictly increasing unit roundoff")
+    return dict(ids=ids, nnz_k=nnz_k, srow=srow)
 
 
 def storage_pct(nnz_k, fmts, last_bits: int = 0) -> float:

@@ -610,6 +610,49 @@ int orc_bucket_ids(int n, const int* rp, const double* val, double bucket_eps,
     return 0;
 }
 
+/* Componentwise, x-dependent bucketing: the other strategy of Graillat et al.
+ * that Section 2.3 mentions (and sets aside, because the buckets depend on the
+ * vector x and must be redone for every product).  The paper does not state
+ * it; this is the reading used here.  Row i: s_i = (|A||x|)_i, the fp64 sum in
+ * ascending column order of the fp64 products |a_ij| |x_j|; thresholds
+ * t_ik = eps s_i / u_k; element (i, j) goes to a bucket by the intervals of
+ * eq. (nint) with |a_ij| replaced by |a_ij| |x_j| and ||A|| by s_i.  Bucket k
+ * then holds products summing to at most p_ik eps s_i / u_k, so the bucketed
+ * product (Alg 2.3 with these buckets) has componentwise backward error
+ * max_i |yhat_i - y_i| / (|A||x|)_i within (q - 1) u_1 + c eps, c of
+ * eq. (ccw) -- the normwise bound's form, row by row (pinned by exact
+ * rationals in the tests). */
+int orc_bucket_ids_cw(int n, const int* rp, const int* ci, const double* val, const double* x,
+                      double bucket_eps, const int* fmts, int q, int8_t* id, int64_t* nnz_k, double* srow) {
+    if (q < 1 || q > 8) return -1;
+    for (int b = 1; b < q; ++b)
+        if (!(orc_unit_roundoff(fmts[b]) > orc_unit_roundoff(fmts[b - 1]))) return -1;
+    for (int b = 0; b < q; ++b) nnz_k[b] = 0;
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) s += fabs(val[p]) * fabs(x[ci[p]]);
+        if (srow) srow[i] = s;
+        double t[8];
+        t[0] = INFINITY;
+        for (int b = 1; b < q; ++b) t[b] = bucket_eps * s / orc_unit_roundoff(fmts[b]);
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            double a = fabs(val[p]) * fabs(x[ci[p]]);
+            int k = 0;
+            if (q == 1 || a > t[1]) {
+                k = 0;
+            } else if (a <= t[q - 1]) {
+                k = q - 1;
+            } else {
+                for (int b = 1; b <= q - 2; ++b)
+                    if (a > t[b + 1] && a <= t[b]) k = b;
+            }
+            id[p] = (int8_t)k;
+            nnz_k[k]++;
+        }
+    }
+    return 0;
+}
+
 double orc_storage_pct(const int64_t* nnz_k, const int* fmts, int q, int last_bits) {
     double num = 0.0, tot = 0.0;
     for (int b = 0; b < q; ++b) {

@@ -98,6 +98,10 @@ int orc_bucket_ids(int n, const int* rp, const double* val, double bucket_eps,
 
 /* Storage cost sum_k nnz_k bits_k / (nnz bits_0) in percent; the last bucket
  * is costed at last_bits when it is the drop format (0 or 8, see Tables 3/4). */
+/* Componentwise (x-dependent) bucketing: s_i = (|A||x|)_i and the intervals of
+ * eq. (nint) on |a_ij| |x_j| against eps s_i / u_k, per row.  srow may be NULL. */
+int orc_bucket_ids_cw(int n, const int* rp, const int* ci, const double* val, const double* x,
+                      double bucket_eps, const int* fmts, int q, int8_t* id, int64_t* nnz_k, double* srow);
 double orc_storage_pct(const int64_t* nnz_k, const int* fmts, int q, int last_bits);
 
 /* Stored values mtilde of each nonzero (scaled storage):

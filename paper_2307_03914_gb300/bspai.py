@@ -122,6 +122,10 @@ _sig("bspai_adjoint_grad_A", _i, [C.POINTER(CsrT), C.c_int32, _vp, _vp, _vp, _vp
 _sig("bspai_probe_fma", _i, [_i, C.c_int32, _vp, C.POINTER(C.c_double), C.POINTER(C.c_float)])
 
 
+_sig("bspai_apply_cw", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, _i, _vp, _i, _vp,
+                           C.POINTER(C.c_int64), _vp])
+
+
 class GmresPlan(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("per_thread", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks", C.c_int32)]
@@ -435,6 +439,19 @@ def probe_fma(prec="fp32", iters=4096, stream=None) -> dict:
     r, ms = C.c_double(0.0), C.c_float(0.0)
     _check(_lib.bspai_probe_fma(PREC[prec], iters, _stream(stream), C.byref(r), C.byref(ms)))
     return dict(fma_per_s=r.value, flops=2.0 * r.value, ms=ms.value)
+
+
+def apply_cw(M: MHandle, bucket_eps: float, precs, x, y, ids=None, counts=False, stream=None):
+    """Componentwise, x-dependent bucketed product y = M x (bspai_apply_cw);
+    returns the per-bucket counts when counts is set."""
+    q = len(precs)
+    arr = (C.c_int32 * q)(*[PREC[p] for p in precs])
+    nk = (C.c_int64 * q)() if counts else None
+    xp = PREC["fp64"] if x.dtype == torch.float64 else PREC["fp32"]
+    yp = PREC["fp64"] if y.dtype == torch.float64 else PREC["fp32"]
+    _check(_lib.bspai_apply_cw(M.ptr, bucket_eps, arr, q, _ptr(x), xp, _ptr(y), yp,
+                               _ptr(ids) if ids is not None else None, nk, _stream(stream)))
+    return list(nk) if counts else None
 
 
 MGS_KERNELS = {0: "k_mgs", 1: "k_mgs_res", 2: "k_mgs_res2"}

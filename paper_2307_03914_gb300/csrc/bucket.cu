@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
                                                   int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
                                                   VT* __restrict__ bmax, VT* __restrict__ colmax,
                                                   int* __restrict__ wmax, const int32_t* __restrict__ slice_seg,
-                                                  int packed, unsigned* __restrict__ dmax) {
+                                                  int packed, unsigned* __restrict__ dmax, int* __restrict__ wmin) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nslices * kSlice) return;
     unsigned dm = 0;  // max |c - r| of the row
@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
             if (c) atomicAdd(nnzk + k, (unsigned long long)c);
             if (m > VT(0)) atomic_max_nonneg(bmax + sg * 8 + k, m);
             if (w) atomicMax(wmax + k, w);
+            atomicMin(wmin + k, w);
         }
     }
 }
@@ -409,9 +410,11 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     VT* d_colmax = nullptr;
     int* d_wmax = nullptr;
     unsigned* d_dmax = nullptr;
+    int* d_wmin = nullptr;
     auto cleanup = [&]() {
         dfree(d_norm, s); dfree(d_thr, s); dfree(d_w, s); dfree(d_nnzk, s);
         dfree(d_bmax, s); dfree(d_scale, s); dfree(d_colmax, s); dfree(d_wmax, s); dfree(d_dmax, s);
+        dfree(d_wmin, s);
     };
     // One system: the packed slot arrangement, with 16-bit column differences
     // when every |c - r| fits (the SpMV reads a row's slots four at a time).
@@ -441,6 +444,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     if ((rc = dalloc_t(&d_scale, (size_t)nseg * 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_wmax, 8, s))) return fail(rc);
     if ((rc = dalloc_t(&d_dmax, 1, s))) return fail(rc);
+    if ((rc = dalloc_t(&d_wmin, 8, s))) return fail(rc);
     if (n_e4m3) {
         if ((rc = dalloc_t(&d_colmax, (size_t)n, s))) return fail(rc);
         if ((rc = dalloc_t(&B->colscale, (size_t)n, s))) return fail(rc);
@@ -455,6 +459,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     if (!e) e = cudaMemsetAsync(d_bmax, 0, 8 * sizeof(VT) * (size_t)nseg, s);
     if (!e) e = cudaMemsetAsync(d_wmax, 0, 8 * sizeof(int), s);
     if (!e) e = cudaMemsetAsync(d_dmax, 0, sizeof(unsigned), s);
+    if (!e) e = cudaMemsetAsync(d_wmin, 0x7f, 8 * sizeof(int), s);  // 0x7f7f7f7f: above any width
     if (!e) e = cudaMemsetAsync(d_w, 0, sizeof(int64_t) * (size_t)q * (nsl + 1), s);
     if (!e && d_colmax) e = cudaMemsetAsync(d_colmax, 0, sizeof(VT) * (size_t)n, s);
     if (e) return fail(cuda_error(e, "bspai_bucket setup", __FILE__, __LINE__));
@@ -467,7 +472,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
         note_launch();
         k_classify<VT><<<g_rows, 256, 0, s>>>(n, nsl, S.sell->sptr, S.sell->col, S.val, S.rowlen, P, d_thr,
                                               B->id_sell, d_w, d_nnzk, d_bmax, d_colmax, d_wmax, slice_seg,
-                                              packed, d_dmax);
+                                              packed, d_dmax, d_wmin);
         note_launch();
         k_bucket_scales<VT><<<g_seg8, 256, 0, s>>>(P, nseg, d_bmax, d_scale);
         note_launch();
@@ -496,6 +501,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     float hscale[8] = {0};
     int hwmax[8] = {0};
     unsigned hdmax = 0;
+    int hwmin[8] = {0};
     for (int k = 0; k < q; ++k)
         if ((e = cudaMemcpyAsync(&slots[k], B->b[k].sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s)))
             return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
@@ -505,6 +511,7 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
     if (!e) e = cudaMemcpyAsync(hscale, d_scale, sizeof hscale, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(hwmax, d_wmax, sizeof hwmax, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(&hdmax, d_dmax, sizeof hdmax, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hwmin, d_wmin, sizeof hwmin, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return fail(cuda_error(e, "bucket sizes", __FILE__, __LINE__));
     double hnorm = 0.0;
@@ -520,6 +527,8 @@ static int bucket_impl(const BucketSrc<VT>& S, double bucket_eps, const int32_t*
         B->maxw[k] = hwmax[k];
         B->b[k].maxw = hwmax[k];
         B->b[k].packed = packed;
+        // every slice equally wide (a stencil's buckets): slice starts need no table
+        B->b[k].ellw = (packed && nsl > 0 && hwmin[k] == hwmax[k] && hwmax[k] > 0) ? hwmax[k] : 0;
         D.precs[k] = precs[k];
         D.sptr[k] = B->b[k].sptr;
         D.scale[k] = hscale[k];

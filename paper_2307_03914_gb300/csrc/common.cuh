@@ -79,6 +79,7 @@ struct Sell {
     int32_t maxw = -1;         // widest slice in slots per row (-1: unknown)
     int32_t packed = 0;        // 1: packed arrangement (groups of four slots per row)
     int16_t* col16 = nullptr;  // slots of 16-bit column differences c - r, or null
+    int32_t ellw = 0;          // > 0: every slice has this width (sptr[s] = 32 ellw s)
 };
 
 constexpr int16_t kCol16Pad = -32768;
@@ -110,6 +111,7 @@ struct BucketDev {
     int32_t maxw;              // widest slice of the bucket in slots per row (-1: unknown)
     int32_t packed;            // slot arrangement (Sell::packed)
     const int16_t* col16;      // 16-bit column differences (Sell::col16), or null: col
+    int32_t ellw;              // uniform slice width (Sell::ellw), or 0
 };
 
 struct BMDev {
@@ -131,6 +133,8 @@ struct bspai_matrix {
     double* norm_inf = nullptr;// device scalar ||A||_inf
     int32_t* rowlen = nullptr; // entries per row (null for a transposed A)
     int32_t* csr_row_ptr = nullptr; // copy of A's CSR row pointers (null for a transposed A)
+    bspai::Sell psell;         // A's structure in the packed slot arrangement (A v in u_p = fp32)
+    float* pval32 = nullptr;   // A rounded to fp32 in psell's slots
 };
 
 struct bspai_spai {
@@ -177,6 +181,10 @@ namespace bspai {
 int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t s);
 int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const double* val,
                   Sell* out, double** val64, float** val32, int32_t** rowlen, cudaStream_t s);
+// packed copy of a plain SELL structure with fp32 values (16-bit columns when they fit)
+int sell_packed_copy(const Sell& S, const float* val, Sell* out, float** pval, cudaStream_t s);
+// the view A v in u_p reads: the packed copy for fp32, the plain fp64 values for fp64
+BMDev up_view(const bspai_matrix* A, int up);
 void sell_free(Sell* S, cudaStream_t s);
 
 // launches (defined in spmv.cu)

@@ -850,10 +850,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
     const int n = W.n;
     const int tprec = W.ug;  // T matches u_g
     // A v: A in u_p, or A's buckets by the adaptive-precision SpMV (Alg 2.3 applied to A)
-    const BMDev Aview = W.BA ? W.BA->dev()
-                             : single_bucket_view(A->sell, W.up == BSPAI_FP64 ? (const void*)A->val64
-                                                                              : (const void*)A->val32,
-                                                  W.up);
+    const BMDev Aview = W.BA ? W.BA->dev() : up_view(A, W.up);
     const BMDev Mview = BM->dev();
     T* V = reinterpret_cast<T*>(W.V);
     T* w = reinterpret_cast<T*>(W.w);

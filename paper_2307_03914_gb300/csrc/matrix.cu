@@ -97,6 +97,118 @@ int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const doubl
     return BSPAI_OK;
 }
 
+// ------------------------------------------------ packed copy for A v in u_p
+// A's values rounded to fp32 in the packed slot arrangement (groups of four
+// slots per row, see Sell), with 16-bit column differences when every
+// |c - r| fits: the layout the vector-load SpMV kernel reads.
+
+// slice widths rounded up to four slots (times 32) and max |c - r| over the entries
+__global__ void k_packed_widths(int n, int nsl, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                                int64_t* __restrict__ w, unsigned* __restrict__ dmax, int* __restrict__ wmin) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)nsl * kSlice) return;
+    const int64_t s = r >> 5;
+    const int width = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    unsigned dm = 0;
+    if (r < n)
+        for (int l = 0; l < width; ++l) {
+            const int c = col[sptr[s] + ((int64_t)l << 5) + (r & 31)];
+            if (c < 0) continue;
+            const int64_t d = (int64_t)c - r;
+            const unsigned ad = (unsigned)(d < 0 ? -d : d);
+            dm = ad > dm ? ad : dm;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned t = __shfl_xor_sync(0xffffffffu, dm, o);
+        dm = t > dm ? t : dm;
+    }
+    if ((r & 31) == 0) {
+        w[s] = (int64_t)((width + 3) & ~3) * kSlice;
+        if (dm) atomicMax(dmax, dm);
+        atomicMin(wmin, (width + 3) & ~3);
+    }
+}
+
+__global__ void k_packed_fill(int n, int nsl, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, const int64_t* __restrict__ psptr,
+                              int32_t* __restrict__ pcol, int16_t* __restrict__ pcol16, float* __restrict__ pval) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)nsl * kSlice) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    const int width = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    const int pwidth = (int)((psptr[s + 1] - psptr[s]) >> 5);
+    for (int l = 0; l < pwidth; ++l) {
+        int c = -1;
+        float v = 0.0f;
+        if (r < n && l < width) {
+            const int64_t sp = sptr[s] + ((int64_t)l << 5) + lane;
+            c = col[sp];
+            if (c >= 0) v = val[sp];
+        }
+        const int64_t dp = sell_slot(psptr[s], lane, l, 1);
+        if (pcol16) pcol16[dp] = c < 0 ? kCol16Pad : (int16_t)(c - r);
+        else pcol[dp] = c;
+        pval[dp] = c < 0 ? 0.0f : v;
+    }
+}
+
+int sell_packed_copy(const Sell& S, const float* val, Sell* out, float** pval, cudaStream_t s) {
+    Sell P;
+    P.n = S.n;
+    P.nslices = S.nslices;
+    P.packed = 1;
+    int64_t* w = nullptr;
+    unsigned* dmax = nullptr;  // dmax[0]: max |c - r|; dmax[1]: narrowest packed width
+    auto done = [&](int code) {
+        dfree(w, s);
+        dfree(dmax, s);
+        if (code != BSPAI_OK) sell_free(&P, s);
+        return code;
+    };
+    int rc;
+    if ((rc = dalloc_t(&w, (size_t)S.nslices + 1, s))) return done(rc);
+    if ((rc = dalloc_t(&dmax, 2, s))) return done(rc);
+    if ((rc = dalloc_t(&P.sptr, (size_t)S.nslices + 1, s))) return done(rc);
+    cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), s);
+    if (!e) e = cudaMemsetAsync(dmax + 1, 0x7f, sizeof(unsigned), s);
+    if (e) return done(cuda_error(e, "memset", __FILE__, __LINE__));
+    const unsigned grid = (unsigned)ceil_div((int64_t)S.nslices * kSlice, 256);
+    if (S.nslices > 0) {
+        k_packed_widths<<<grid, 256, 0, s>>>(S.n, S.nslices, S.sptr, S.col, w, dmax,
+                                             reinterpret_cast<int*>(dmax + 1));
+        note_launch();
+        if ((e = cudaGetLastError())) return done(cuda_error(e, "k_packed_widths", __FILE__, __LINE__));
+    }
+    if ((rc = scan_exclusive_i64(w, P.sptr, S.nslices, s))) return done(rc);
+    unsigned hd[2] = {0, 0};
+    e = cudaMemcpyAsync(&P.slots, P.sptr + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(hd, dmax, sizeof hd, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return done(cuda_error(e, "packed sizes", __FILE__, __LINE__));
+    P.maxw = S.maxw < 0 ? -1 : ((S.maxw + 3) & ~3);
+    P.ellw = (S.nslices > 0 && P.maxw > 0 && (int)hd[1] == P.maxw) ? P.maxw : 0;
+    if (hd[0] <= 32767u) {
+        if ((rc = dalloc_t(&P.col16, (size_t)P.slots, s))) return done(rc);
+    } else {
+        if ((rc = dalloc_t(&P.col, (size_t)P.slots, s))) return done(rc);
+    }
+    float* v = nullptr;
+    if ((rc = dalloc_t(&v, (size_t)P.slots, s))) return done(rc);
+    if (S.nslices > 0) {
+        k_packed_fill<<<grid, 256, 0, s>>>(S.n, S.nslices, S.sptr, S.col, val, P.sptr, P.col, P.col16, v);
+        note_launch();
+        if ((e = cudaGetLastError())) {
+            dfree(v, s);
+            return done(cuda_error(e, "k_packed_fill", __FILE__, __LINE__));
+        }
+    }
+    *out = P;
+    *pval = v;
+    return done(BSPAI_OK);
+}
+
 __global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                   const double* __restrict__ val, double* __restrict__ out) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,6 +461,7 @@ int matrix_create(const bspai_csr_t* A, cudaStream_t s, bspai_matrix** out) {
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = cuda_error(e, "k_row_abs_sum_max", __FILE__, __LINE__);
         }
+        if (st == BSPAI_OK) st = sell_packed_copy(M->sell, M->val32, &M->psell, &M->pval32, s);
     }
     if (st != BSPAI_OK) {
         bspai_free(M);

@@ -245,8 +245,10 @@ int bspai_free(void* h) {
         auto* A = reinterpret_cast<bspai_matrix*>(h);
         cudaStream_t s = A->stream;
         sell_free(&A->sell, s);
+        sell_free(&A->psell, s);
         dfree(A->val64, s);
         dfree(A->val32, s);
+        dfree(A->pval32, s);
         dfree(A->norm_inf, s);
         dfree(A->rowlen, s);
         dfree(A->csr_row_ptr, s);

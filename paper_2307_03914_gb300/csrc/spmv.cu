@@ -592,9 +592,15 @@ struct PkRow {
     int ng;      // groups of four slots per row in the slice
     int c[4];
     V v[4], xv[4];
+    // (a uniform slice width needs no load: the matrix stream starts at once)
     __device__ __forceinline__ void ptrs(const BucketDev& B, int64_t s) {
-        sb = __ldg(B.sptr + s);
-        ng = (int)((__ldg(B.sptr + s + 1) - sb) >> 7);
+        if (B.ellw > 0) {
+            sb = s * ((int64_t)B.ellw << 5);
+            ng = B.ellw >> 2;
+        } else {
+            sb = __ldg(B.sptr + s);
+            ng = (int)((__ldg(B.sptr + s + 1) - sb) >> 7);
+        }
     }
     // indices and stored values of group grp (none when the slice has no
     // group); an fp16 value times its bucket's scale (exact: a power of two)
@@ -708,6 +714,42 @@ __global__ void __launch_bounds__(256, PkMinBlocks<P0, P1, ONE>::value)
     }
 }
 
+// One packed bucket whose rows have at most eight slots (two groups, e.g. a
+// 7-point stencil): both groups' indices and values are loaded before any
+// gather, then the partial sum is formed group by group in slot order.
+template <typename XT, typename YT, int P, bool I16>
+__global__ void __launch_bounds__(256, P == BSPAI_FP64 ? 4 : 6)
+    k_bspmv_pk2g(const __grid_constant__ BMDev M, const XT* __restrict__ x, YT* __restrict__ y,
+                 const int* __restrict__ jd, int64_t ldx, int64_t ldy, int yoff) {
+    if (jd) {
+        if (jd[1]) return;
+        const int64_t j = jd[0];
+        x += j * ldx;
+        y += (j + yoff) * ldy;
+    }
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)ceil_div(M.n, kSlice) * kSlice) return;
+    const int64_t s = r >> 5;
+    const int lane = (int)(r & 31);
+    const float sc = M.b[0].slicescale ? __ldg(M.b[0].slicescale + s) : M.b[0].scale;
+    PkRow<P, XT, I16> g0, g1;
+    g0.ptrs(M.b[0], s);
+    g1.sb = g0.sb;
+    g1.ng = g0.ng;
+    g0.load(M.b[0], 0, lane, r, sc);
+    g1.load(M.b[0], 1, lane, r, sc);
+    g0.gather(M.b[0], x, r);
+    g1.gather(M.b[0], x, r);
+    typename PkRow<P, XT, I16>::V acc = 0;
+    g0.accumulate(acc);
+    g1.accumulate(acc);
+    if constexpr (P != BSPAI_FP64 && std::is_same<YT, float>::value) {
+        if (r < M.n) y[r] = acc;  // fl32(fl64(0 + a)) = a
+    } else {
+        if (r < M.n) y[r] = from_f64<YT>(__dadd_rn(0.0, (double)acc));
+    }
+}
+
 // the compiled packed mixes (as pick_fix), for either index width; null if
 // the buckets are not all packed alike or the mix is not compiled
 template <typename XT, typename YT, bool I16, bool ONE>
@@ -733,6 +775,12 @@ static FixFn<XT, YT> pick_pk(const BMDev& M) {
         maxw = M.b[k].maxw > maxw ? M.b[k].maxw : maxw;
     }
     const bool i16 = M.b[0].col16 != nullptr, one = maxw <= 4;
+    if (M.q == 1 && !one && maxw <= 8) {
+        const int p = M.b[0].prec;
+        if (p == BSPAI_FP32) return i16 ? k_bspmv_pk2g<XT, YT, BSPAI_FP32, true> : k_bspmv_pk2g<XT, YT, BSPAI_FP32, false>;
+        if (p == BSPAI_FP64) return i16 ? k_bspmv_pk2g<XT, YT, BSPAI_FP64, true> : k_bspmv_pk2g<XT, YT, BSPAI_FP64, false>;
+        if (p == BSPAI_FP16) return i16 ? k_bspmv_pk2g<XT, YT, BSPAI_FP16, true> : k_bspmv_pk2g<XT, YT, BSPAI_FP16, false>;
+    }
     if (i16) return one ? pick_pk_mix<XT, YT, true, true>(M) : pick_pk_mix<XT, YT, true, false>(M);
     return one ? pick_pk_mix<XT, YT, false, true>(M) : pick_pk_mix<XT, YT, false, false>(M);
 }
@@ -767,9 +815,15 @@ BMDev single_bucket_view(const Sell& S, const void* val, int prec) {
     d.b[0].maxw = S.maxw;
     d.b[0].packed = S.packed;
     d.b[0].col16 = S.col16;
+    d.b[0].ellw = S.ellw;
     return d;
 }
 
+
+BMDev up_view(const bspai_matrix* A, int up) {
+    if (up == BSPAI_FP32 && A->pval32) return single_bucket_view(A->psell, A->pval32, BSPAI_FP32);
+    return single_bucket_view(A->sell, up == BSPAI_FP64 ? (const void*)A->val64 : (const void*)A->val32, up);
+}
 
 template <typename XT, typename YT>
 using TmaFn = void (*)(BMDev, const XT*, YT*, const int*, int64_t, int64_t, int, StageLayout);
@@ -943,6 +997,7 @@ BMDev bspai_bucketed::dev() const {
         d.b[k].maxw = maxw[k];
         d.b[k].packed = b[k].packed;
         d.b[k].col16 = b[k].col16;
+        d.b[k].ellw = b[k].ellw;
     }
     return d;
 }
@@ -1024,8 +1079,7 @@ int bspai_spmv_up(bspai_A_h A, const float* v, float* w, bspai_stream_t s) {
     if (!A || A->magic != kMagicA) return set_error(BSPAI_ERR_INVALID, "bspai_spmv_up: bad handle");
     if (!v || !w) return set_error(BSPAI_ERR_INVALID, "bspai_spmv_up: null vector");
     ProfScope ps(BSPAI_K_SPMV_A, (cudaStream_t)s);
-    return launch_bspmv(single_bucket_view(A->sell, A->val32, BSPAI_FP32), v, BSPAI_FP32, w, BSPAI_FP32,
-                        (cudaStream_t)s);
+    return launch_bspmv(up_view(A, BSPAI_FP32), v, BSPAI_FP32, w, BSPAI_FP32, (cudaStream_t)s);
 }
 
 }  // extern "C"

@@ -211,6 +211,7 @@ int bspai_matrix_transpose(bspai_A_h A, bspai_stream_t st, bspai_A_h* out) {
         p = nullptr;
         if (!rc) rc = gather_payload(T->sell, rowlen, map, 4, A->val32, &p, s);
         T->val32 = (float*)p;
+        if (!rc) rc = sell_packed_copy(T->sell, T->val32, &T->psell, &T->pval32, s);
         if (!rc) rc = dalloc_t(&T->norm_inf, 1, s);
         if (!rc) {
             cudaError_t e = cudaMemsetAsync(T->norm_inf, 0, sizeof(double), s);
