@@ -30,8 +30,15 @@ struct CwParams {
     int32_t q;
     int32_t precs[4];
     double eps;
-    double uk[4];
+    double uk_inv[4];  // 1 / u_k: a power of two, so eps s / u_k = (eps s) (1 / u_k) exactly
 };
+
+// a > b for non-negative doubles, by their bit patterns (the integer pipe)
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+    return __double_as_longlong(a) > __double_as_longlong(b);
+}
+
+constexpr int kCwCache = 8;  // products |m x| of a row's first slots kept in registers between the passes
 
 template <typename XT, typename YT>
 __global__ void __launch_bounds__(256) k_bspmv_cw(int n, const int64_t* __restrict__ sptr,
@@ -48,14 +55,25 @@ __global__ void __launch_bounds__(256) k_bspmv_cw(int n, const int64_t* __restri
         const int len = rowlen[r];
         // pass 1: s_i = (|M||x|)_i in fp64, ascending columns
         double si = 0.0;
-        for (int l = 0; l < len; ++l) {
+        double am[kCwCache];
+#pragma unroll
+        for (int l = 0; l < kCwCache; ++l) {
+            am[l] = 0.0;
+            if (l < len) {
+                const int64_t p = b + ((int64_t)l << 5);
+                am[l] = __dmul_rn(fabs((double)__ldg(val + p)), fabs((double)__ldg(x + __ldg(col + p))));
+                si = __dadd_rn(si, am[l]);
+            }
+        }
+        for (int l = kCwCache; l < len; ++l) {
             const int64_t p = b + ((int64_t)l << 5);
             si = __dadd_rn(si, __dmul_rn(fabs((double)__ldg(val + p)), fabs((double)__ldg(x + __ldg(col + p)))));
         }
         double thr[4];
         thr[0] = __longlong_as_double(0x7ff0000000000000LL);
+        const double es = __dmul_rn(P.eps, si);
 #pragma unroll
-        for (int k = 1; k < 4; ++k) thr[k] = k < P.q ? __ddiv_rn(__dmul_rn(P.eps, si), P.uk[k]) : 0.0;
+        for (int k = 1; k < 4; ++k) thr[k] = k < P.q ? __dmul_rn(es, P.uk_inv[k]) : 0.0;
         // pass 2: the bucket of every product, and the bucket partial sums
         double acc64 = 0.0;
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -64,15 +82,19 @@ __global__ void __launch_bounds__(256) k_bspmv_cw(int n, const int64_t* __restri
             const int64_t p = b + ((int64_t)l << 5);
             const float m = __ldg(val + p);
             const XT xv = __ldg(x + __ldg(col + p));
-            const double a = __dmul_rn(fabs((double)m), fabs((double)xv));
+            double a = 0.0;
+#pragma unroll
+            for (int c = 0; c < kCwCache; ++c)
+                if (c == l) a = am[c];
+            if (l >= kCwCache) a = __dmul_rn(fabs((double)m), fabs((double)xv));
             int k = 0;
-            if (P.q == 1 || a > thr[1]) {
+            if (P.q == 1 || gt_nonneg(a, thr[1])) {
                 k = 0;
-            } else if (a <= thr[P.q - 1]) {
+            } else if (!gt_nonneg(a, thr[P.q - 1])) {
                 k = P.q - 1;
             } else {
                 for (int bb = 1; bb <= P.q - 2; ++bb)
-                    if (a > thr[bb + 1] && a <= thr[bb]) k = bb;
+                    if (gt_nonneg(a, thr[bb + 1]) && !gt_nonneg(a, thr[bb])) k = bb;
             }
             if (ids) ids[o + l] = (int8_t)k;
 #pragma unroll
@@ -135,8 +157,8 @@ int bspai_apply_cw(bspai_M_h M, double bucket_eps, const int32_t* precs, int32_t
                              "bspai_apply_cw: buckets in fp64, fp32, bf16 or drop only (fp16 and e4m3 need a scale "
                              "fitted to each bucket's contents, one more pass per product)");
         P.precs[k] = f;
-        P.uk[k] = unit_roundoff(f);
-        if (k > 0 && !(P.uk[k] > P.uk[k - 1]))
+        P.uk_inv[k] = 1.0 / unit_roundoff(f);
+        if (k > 0 && !(unit_roundoff(f) > unit_roundoff(P.precs[k - 1])))
             return set_error(BSPAI_ERR_INVALID, "bspai_apply_cw: precisions must have increasing unit roundoff");
     }
     if ((x_prec != BSPAI_FP64 && x_prec != BSPAI_FP32) || (y_prec != BSPAI_FP64 && y_prec != BSPAI_FP32))
