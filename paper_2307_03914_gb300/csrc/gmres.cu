@@ -75,11 +75,12 @@ __global__ void k_state_init(GmresState* st, int kmax, double tau) {
     st->bar.err = 0;
 }
 
-__device__ __forceinline__ void block_rows(int n, int64_t& r0, int64_t& r1) {
-    int64_t chunk = ceil_div(ceil_div(n, gridDim.x), 32) * 32;
+__device__ __forceinline__ void block_rows(int n, int G, int64_t& r0, int64_t& r1) {
+    int64_t chunk = ceil_div(ceil_div(n, G), 32) * 32;
     r0 = (int64_t)blockIdx.x * chunk;
     r1 = r0 + chunk < n ? r0 + chunk : n;
 }
+__device__ __forceinline__ void block_rows(int n, int64_t& r0, int64_t& r1) { block_rows(n, (int)gridDim.x, r0, r1); }
 
 // Sum of `v` over the whole grid, identical in every block: block sum in a
 // fixed tree, partials to part[slot*G + block], barrier, then every block adds
@@ -141,26 +142,14 @@ __global__ void __launch_bounds__(512) k_gmres_start(T* __restrict__ V, int n, G
     }
 }
 
-// Givens rotations on column j of H, update of g and the tau test (fp64)
-__device__ void givens_step(int j, int kmax, double hn, double* H, double* cs, double* sn, double* g,
-                            GmresState* st) {
-    double* __restrict__ hc = H + (int64_t)j * (kmax + 1);
-    const double* __restrict__ c_ = cs;
-    const double* __restrict__ s_ = sn;
+// The new rotation of step j from the swept column (hc[j] = carry, the entry the
+// earlier rotations handed on, hc[j+1] = hn = h_{j+1,j}), the update of g and
+// the tau test (fp64)
+__device__ void givens_finish(int j, int kmax, double hn, double carry, double* __restrict__ hc, double* cs,
+                              double* sn, double* g, GmresState* st) {
+    hc[j] = carry;
     hc[j + 1] = hn;
-    // the previous rotations applied to the new column; the entry each rotation hands
-    // to the next stays in a register, so only the running value is a dependent chain
-    // (the stored coefficients and column entries are independent loads)
-    double carry = j > 0 ? hc[0] : 0.0;
-    for (int i = 0; i < j; ++i) {
-        const double ci = c_[i], si = s_[i], hi1 = hc[i + 1];
-        const double t1 = __dadd_rn(__dmul_rn(ci, carry), __dmul_rn(si, hi1));
-        const double t2 = __dadd_rn(__dmul_rn(-si, carry), __dmul_rn(ci, hi1));
-        hc[i] = t1;
-        carry = t2;
-    }
-    if (j > 0) hc[j] = carry;
-    const double a = hc[j], b = hc[j + 1];
+    const double a = carry, b = hn;
     const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
     double c = 1.0, s = 0.0;
     if (rr != 0.0) {
@@ -181,6 +170,28 @@ __device__ void givens_step(int j, int kmax, double hn, double* H, double* cs, d
     st->j = k;
     if (!fin) st->status = BSPAI_NONFINITE;
     st->done = (res <= __dmul_rn(st->tau, st->beta)) || hn == 0.0 || k >= kmax || !fin;
+}
+
+// rotation i of the earlier steps applied to the pair (carry, h_{i+1,j}): the
+// rotated h_{i,j} is returned, the entry handed on to rotation i + 1 stays in carry
+__device__ __forceinline__ double givens_apply(double ci, double si, double& carry, double hi1) {
+    const double t1 = __dadd_rn(__dmul_rn(ci, carry), __dmul_rn(si, hi1));
+    carry = __dadd_rn(__dmul_rn(-si, carry), __dmul_rn(ci, hi1));
+    return t1;
+}
+
+// Givens rotations on column j of H (written unrotated), update of g and the tau test (fp64)
+__device__ void givens_step(int j, int kmax, double hn, double* H, double* cs, double* sn, double* g,
+                            GmresState* st) {
+    double* __restrict__ hc = H + (int64_t)j * (kmax + 1);
+    const double* __restrict__ c_ = cs;
+    const double* __restrict__ s_ = sn;
+    // the previous rotations applied to the new column; the entry each rotation hands
+    // to the next stays in a register, so only the running value is a dependent chain
+    // (the stored coefficients and column entries are independent loads)
+    double carry = hc[0];
+    for (int i = 0; i < j; ++i) hc[i] = givens_apply(c_[i], s_[i], carry, hc[i + 1]);
+    givens_finish(j, kmax, hn, carry, hc, cs, sn, g, st);
 }
 
 template <typename T>
@@ -296,7 +307,9 @@ __device__ __forceinline__ bool tag_read(const unsigned long long* slot, unsigne
 }
 
 template <typename T>
-__device__ __forceinline__ void tag_arrive(T v, unsigned long long* tags, int set, unsigned seq, T* s_w) {
+__device__ __forceinline__ void tag_arrive(T v, unsigned long long* tags, int set, unsigned seq, T* s_w,
+                                           int G = -1) {
+    if (G < 0) G = gridDim.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
     v = warp_sum(v);
@@ -306,65 +319,122 @@ __device__ __forceinline__ void tag_arrive(T v, unsigned long long* tags, int se
         T t = lane < nw ? s_w[lane] : T(0);
         t = warp_sum(t);
         if (lane == 0)
-            tag_publish(t, tags + ((int64_t)set * gridDim.x + blockIdx.x) * TagWords<T>::W, seq);
+            tag_publish(t, tags + ((int64_t)set * G + blockIdx.x) * TagWords<T>::W, seq);
     }
 }
 
-// Warp 0 polls the slots of `set` until all carry `seq` (giving up after tmo
-// ns, or when another block has flagged an error), then every thread gets the
-// total; *s_ok = 0 after a timeout.
+// The lanes of one warp poll the G slots of `set` until all carry `seq`
+// (giving up after tmo ns, or when another block has flagged an error) and
+// add them in a fixed order (lane-strided, then a warp butterfly): every lane
+// gets the total, the same in every block.  False after a timeout.
 template <typename T>
-__device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, unsigned seq, GridBar* bar,
-                                      unsigned long long tmo, T* s_tot, int* s_ok) {
+__device__ __forceinline__ bool tag_poll_warp(const unsigned long long* tags, int set, unsigned seq, int G,
+                                              GridBar* bar, unsigned long long tmo, T* total) {
     constexpr int MS = kTagMaxBlocks / 32;
     constexpr int TW = TagWords<T>::W;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        const int G = gridDim.x;
-        const unsigned long long* base = tags + (int64_t)set * G * TW;
-        T val[MS];
-        unsigned pending = 0;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long* base = tags + (int64_t)set * G * TW;
+    T val[MS];
+    unsigned pending = 0;
 #pragma unroll
-        for (int m = 0; m < MS; ++m) {
-            val[m] = T(0);
-            if (lane + 32 * m < G) pending |= 1u << m;
-        }
-        int ok = 1;
-        unsigned long long t0 = 0;
-        for (int it = 0;; ++it) {
-#pragma unroll
-            for (int m = 0; m < MS; ++m)
-                if ((pending >> m) & 1u)
-                    if (tag_read(base + (int64_t)(lane + 32 * m) * TW, seq, &val[m])) pending &= ~(1u << m);
-            if (!__any_sync(0xffffffffu, pending != 0)) break;
-            int stop = 0;
-            if (lane == 0) {
-                const unsigned long long now = globaltimer_ns();
-                if (it == 0) t0 = now;
-                if (now - t0 > tmo) {
-                    atomicExch(&bar->err, 1);
-                    stop = 1;
-                } else if ((it & 63) == 63 && *(volatile int*)&bar->err) {
-                    stop = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0)) {
-                ok = 0;
-                break;
-            }
-        }
-        T t = T(0);
+    for (int m = 0; m < MS; ++m) {
+        val[m] = T(0);
+        if (lane + 32 * m < G) pending |= 1u << m;
+    }
+    bool ok = true;
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
 #pragma unroll
         for (int m = 0; m < MS; ++m)
-            if (lane + 32 * m < G) t = Ar<T>::add(t, val[m]);
-        t = warp_sum(t);
+            if ((pending >> m) & 1u)
+                if (tag_read(base + (int64_t)(lane + 32 * m) * TW, seq, &val[m])) pending &= ~(1u << m);
+        if (!__any_sync(0xffffffffu, pending != 0)) break;
+        int stop = 0;
         if (lane == 0) {
+            const unsigned long long now = globaltimer_ns();
+            if (it == 0) t0 = now;
+            if (now - t0 > tmo) {
+                atomicExch(&bar->err, 1);
+                stop = 1;
+            } else if ((it & 63) == 63 && *(volatile int*)&bar->err) {
+                stop = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+            ok = false;
+            break;
+        }
+    }
+    T t = T(0);
+#pragma unroll
+    for (int m = 0; m < MS; ++m)
+        if (lane + 32 * m < G) t = Ar<T>::add(t, val[m]);
+    *total = warp_sum(t);
+    return ok;
+}
+
+// Warp 0 polls the slots of `set` (tag_poll_warp), then every thread gets the
+// total; *s_ok = 0 after a timeout.  G: the blocks that publish (default: all).
+template <typename T>
+__device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, unsigned seq, GridBar* bar,
+                                      unsigned long long tmo, T* s_tot, int* s_ok, int G = -1) {
+    if (G < 0) G = gridDim.x;
+    if (threadIdx.x < 32) {
+        T t;
+        const bool ok = tag_poll_warp<T>(tags, set, seq, G, bar, tmo, &t);
+        if (threadIdx.x == 0) {
             *s_tot = t;
-            *s_ok = ok;
+            *s_ok = ok ? 1 : 0;
         }
     }
     __syncthreads();
     return *s_tot;
+}
+
+// The Givens block: with giv = 1 the last block of an on-chip MGS launch takes
+// no rows.  Its first warp reads every pass's total from the same tagged slots
+// as the other blocks (so the same values), applies rotation i - 1 of the
+// earlier steps to column j as soon as h_{i,j} has arrived -- while the other
+// blocks run the later passes -- and after the last pass forms the new
+// rotation, g and the tau test.  One thread's sweep over the earlier
+// rotations costs about 480 cycles per rotation on GB300's narrow fp64 pipe
+// (21 us at j = 90), and here it overlaps the passes instead of following the
+// last one.  Same operations in the same order as givens_step.
+template <typename T>
+__device__ void givens_block(int j, int kmax, double* H, double* cs, double* sn, double* g, GmresState* st,
+                             const unsigned long long* tags, int G, unsigned seq0, unsigned long long tmo) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double* __restrict__ hc = H + (int64_t)j * (kmax + 1);
+    double carry = 0.0;
+    T hz = T(0);
+    bool ok = true;
+    for (int i = 1; i <= j + 2; ++i) {
+        T h;
+        if (!tag_poll_warp<T>(tags, (i - 1) & 1, seq0 + (unsigned)i, G, &st->bar, tmo, &h)) {
+            ok = false;
+            break;
+        }
+        if (i == j + 2) {
+            hz = h;
+            break;
+        }
+        const int r = i - 1;  // h = h_{r,j}
+        if (lane == 0) {
+            if (r == 0) carry = (double)h;
+            else hc[r - 1] = givens_apply(cs[r - 1], sn[r - 1], carry, (double)h);
+        }
+    }
+    if (lane != 0) return;
+    if (!ok) {
+        st->status = BSPAI_TIMEOUT;
+        st->done = 1;
+        return;
+    }
+    // every block has read seq0 before its last partial, and this block read it
+    // at its start: advance it for the next launch
+    st->bar.seq = seq0 + (unsigned)j + 2u;
+    givens_finish(j, kmax, (double)Ar<T>::sqrt(hz), carry, hc, cs, sn, g, st);
 }
 
 // MGS step with the new vector z resident on chip: one block per SM owns a
@@ -378,7 +448,7 @@ __device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, u
 template <typename T, int R, int BD>
 __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ldv, int n, GmresState* st,
                                                      double* H, double* cs, double* sn, double* g,
-                                                     unsigned long long* tags, unsigned long long tmo) {
+                                                     unsigned long long* tags, unsigned long long tmo, int giv) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* zs = reinterpret_cast<T*>(smraw);
     __shared__ T s_w[32];
@@ -395,8 +465,13 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
     if (s_done) return;
     const int j = s_j, kmax = s_kmax;
     const unsigned seq0 = s_seq;
+    const int G = gridDim.x - giv;  // blocks that hold rows and publish partial sums
+    if (giv && blockIdx.x == G) {
+        givens_block<T>(j, kmax, H, cs, sn, g, st, tags, G, seq0, tmo);
+        return;
+    }
     int64_t r0, r1;
-    block_rows(n, r0, r1);
+    block_rows(n, G, r0, r1);
     const int nb = r1 > r0 ? (int)(r1 - r0) : 0;
     const int tid = threadIdx.x;
     constexpr int bd = BD;
@@ -419,7 +494,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
         const int lr = tid + t * bd;
         if (lr < nb) acc = Ar<T>::add(acc, Ar<T>::mul(vcur[t], zs[lr]));
     }
-    tag_arrive(acc, tags, 0, seq0 + 1u, s_w);
+    tag_arrive(acc, tags, 0, seq0 + 1u, s_w, G);
     for (int i = 1; i <= j + 1; ++i) {
         if (i <= j) {
             const T* vi = V + (int64_t)i * ldv + r0;
@@ -429,7 +504,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
                 if (lr < nb) vnext[t] = vi[lr];
             }
         }
-        const T h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok);
+        const T h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -437,7 +512,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
             }
             return;
         }
-        if (blockIdx.x == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
+        if (!giv && blockIdx.x == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
         acc = T(0);
 #pragma unroll
         for (int t = 0; t < R; ++t) {
@@ -448,11 +523,11 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
                 acc = Ar<T>::add(acc, Ar<T>::mul(i <= j ? vnext[t] : zr, zr));
             }
         }
-        tag_arrive(acc, tags, i & 1, seq0 + (unsigned)i + 1u, s_w);
+        tag_arrive(acc, tags, i & 1, seq0 + (unsigned)i + 1u, s_w, G);
 #pragma unroll
         for (int t = 0; t < R; ++t) vcur[t] = vnext[t];
     }
-    const T h2 = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok);
+    const T h2 = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -461,7 +536,8 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
         return;
     }
     // every block has read seq0 (its first slot carries seq0 + 1): advance it
-    if (blockIdx.x == 0 && tid == 0) st->bar.seq = seq0 + (unsigned)j + 2u;
+    // (with a Givens block, that block advances it: it may have started last)
+    if (!giv && blockIdx.x == 0 && tid == 0) st->bar.seq = seq0 + (unsigned)j + 2u;
     const T hn = Ar<T>::sqrt(h2);
     const bool norm = hn > T(0) && isfinite((double)hn);
 #pragma unroll
@@ -469,7 +545,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
         const int lr = tid + t * bd;
         if (lr < nb) z[lr] = norm ? Ar<T>::div(zs[lr], hn) : zs[lr];
     }
-    if (blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
+    if (!giv && blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
 }
 
 // y = R^-1 g by column-oriented back substitution (fp64), one block
@@ -561,7 +637,7 @@ __device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __fadd2_rn
 template <int P, int BD>
 __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64_t ldv, int n, GmresState* st,
                                                       double* H, double* cs, double* sn, double* g,
-                                                      unsigned long long* tags, unsigned long long tmo) {
+                                                      unsigned long long* tags, unsigned long long tmo, int giv) {
     __shared__ float s_w[32];
     __shared__ float s_tot;
     __shared__ unsigned s_seq;
@@ -576,8 +652,13 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
     if (s_done) return;
     const int j = s_j, kmax = s_kmax;
     const unsigned seq0 = s_seq;
+    const int G = gridDim.x - giv;  // blocks that hold rows and publish partial sums
+    if (giv && blockIdx.x == G) {
+        givens_block<float>(j, kmax, H, cs, sn, g, st, tags, G, seq0, tmo);
+        return;
+    }
     int64_t r0, r1;
-    block_rows(n, r0, r1);
+    block_rows(n, G, r0, r1);
     const int nb = r1 > r0 ? (int)(r1 - r0) : 0;
     const int tid = threadIdx.x;
     // pair q covers rows 2q, 2q + 1 of the chunk; the second may lie past nb
@@ -607,7 +688,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
         const int q = tid + t * BD;
         if (2 * q < nb) acc2 = __fadd2_rn(acc2, __fmul2_rn(vcur[t], zr[t]));
     }
-    tag_arrive(__fadd_rn(acc2.x, acc2.y), tags, 0, seq0 + 1u, s_w);
+    tag_arrive(__fadd_rn(acc2.x, acc2.y), tags, 0, seq0 + 1u, s_w, G);
     for (int i = 1; i <= j + 1; ++i) {
         if (i <= j) {
             const float* vi = V + (int64_t)i * ldv + r0;
@@ -617,7 +698,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
                 if (2 * q < nb) vnext[t] = ld2(vi, q);
             }
         }
-        const float h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok);
+        const float h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -625,7 +706,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
             }
             return;
         }
-        if (blockIdx.x == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
+        if (!giv && blockIdx.x == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
         const float2 h2 = make_float2(h, h);
         acc2 = zero2;
 #pragma unroll
@@ -636,11 +717,11 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
                 acc2 = __fadd2_rn(acc2, __fmul2_rn(i <= j ? vnext[t] : zr[t], zr[t]));
             }
         }
-        tag_arrive(__fadd_rn(acc2.x, acc2.y), tags, i & 1, seq0 + (unsigned)i + 1u, s_w);
+        tag_arrive(__fadd_rn(acc2.x, acc2.y), tags, i & 1, seq0 + (unsigned)i + 1u, s_w, G);
 #pragma unroll
         for (int t = 0; t < P; ++t) vcur[t] = vnext[t];
     }
-    const float hz = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok);
+    const float hz = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -648,7 +729,8 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
         }
         return;
     }
-    if (blockIdx.x == 0 && tid == 0) st->bar.seq = seq0 + (unsigned)j + 2u;
+    // (with a Givens block, that block advances it: it may have started last)
+    if (!giv && blockIdx.x == 0 && tid == 0) st->bar.seq = seq0 + (unsigned)j + 2u;
     const float hn = __fsqrt_rn(hz);
     const bool norm = hn > 0.0f && isfinite((double)hn);
 #pragma unroll
@@ -661,7 +743,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
             else z[2 * q] = zo.x;
         }
     }
-    if (blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
+    if (!giv && blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
 }
 
 // ---------------------------------------------------------------- host side
@@ -689,7 +771,8 @@ struct GmresWork {
     int res_bd = 1024;       // its block size
     int res_kind = 0;        // 1: k_mgs_res, 2: k_mgs_res2 (see ResInstance)
     int res_per_thread = 0;  // its rows (k_mgs_res) or row pairs (k_mgs_res2) per thread
-    int Gr = 0;              // its grid (at most one block per SM)
+    int Gr = 0;              // its blocks that hold rows (at most one block per SM)
+    int giv = 0;             // 1: one more block applies the Givens rotations during the passes
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
 
@@ -818,6 +901,8 @@ static int choose_mgs(GmresWork& W) {
     W.res_kind = ri.kind;
     W.res_per_thread = ri.per_thread;
     W.Gr = Gr;
+    // the Givens block needs an SM of its own (one block per SM at these sizes)
+    W.giv = Gr + 1 <= W.sms ? 1 : 0;
     W.res_smem = smem;
     return BSPAI_OK;
 }
@@ -889,8 +974,8 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
                 int nn = n;
                 int64_t ld = W.ldv;
                 if (W.res_fn) {
-                    void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &W.tags, &W.tmo_ns};
-                    BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr, W.res_bd, W.res_smem, args, s));
+                    void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &W.tags, &W.tmo_ns, &W.giv};
+                    BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr + W.giv, W.res_bd, W.res_smem, args, s));
                 } else {
                     void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};
                     BSPAI_TRY(coop_launch((void*)k_mgs<T>, W.G, args, s));
