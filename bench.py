@@ -331,6 +331,10 @@ def measure_batch(B, W, world, dist, barrier):
             "pairs": info["pairs"] * world, "solves_per_s": rate, "ms": ms, "ok": ok,
             "worst_fwd_err": worst, "total_gmres_iters": info["total_iters"], "max_iters": info["max_iters"],
             "ir_launches": info["ir_launches"], "cta_threads": info["block_threads"], "grid": info["grid"],
+            "schedule": {k: info[k] for k in ("block_threads", "mgs_rows", "z_shared_rows", "m_schedule")},
+            "tuning": {"candidates_ms": [[t["block_threads"], t["mgs_rows"], t["z_shared_rows"], t["m_schedule"],
+                                          round(t["ms"], 2)] for t in B.batch_tune_table()],
+                       "fields": "block_threads, mgs_rows, z_shared_rows, m_schedule, ms of the sample run (largest pairs, 4 per SM, 32 steps)"},
             "kmax": info["kmax"], "rows": n, "nnz_A": bw["A"].nnz, "storage_pct": kinfo["storage_pct"]}
 
 

@@ -101,7 +101,8 @@ typedef struct {
 
 typedef struct {
     double tau;            /* GMRES tolerance: stop when |g_{j+1}| <= tau ||M r||_2 (Alg 3.1) */
-    int32_t kmax;          /* max GMRES iterations per refinement step (no restart); 0 = min(n, 1000) */
+    int32_t kmax;          /* max GMRES iterations per refinement step (no restart unless
+                              basis_bytes_max asks); 0 = min(n, 1000) */
     int32_t i_max;         /* max refinement steps; 0 = 10 */
     int32_t x0_given;      /* 1: x holds the initial iterate; 0: x0 = M b in u_f (Alg 3.1) */
     int32_t max_blocks;    /* cap on the blocks (one per SM) of the cooperative GMRES kernels;
@@ -110,6 +111,19 @@ typedef struct {
     double u_stop;         /* stop when nbe <= u_stop or ||d||_inf <= u_stop ||x||_inf; 0 = 2^-53 */
     double stagnation;     /* stop when ||d_i|| > stagnation ||d_{i-1}||; 0 = 0.9 */
     double barrier_timeout_s; /* device grid-barrier time limit in seconds; 0 = 2.0 */
+    int64_t basis_bytes_max;  /* gmres_ir_solve*: cap on the device bytes of the Krylov basis
+                                 ((m + 1) vectors of n in u_g, n rounded up to 64); 0 = none.
+                                 When the kmax + 1 vectors exceed it, or their allocation fails
+                                 for lack of device memory (m halved until it fits, m >= 8),
+                                 each refinement step solves its correction equation by
+                                 restarted GMRES cycles of m steps: cycle c > 0 starts from
+                                 r - A d (u_r, stored in u), stops at the first cycle's level
+                                 |g| <= tau ||M r||_2, and the cycles end when one stops early,
+                                 meets that level, or they have taken kmax steps (at most
+                                 ceil(kmax / m) cycles); d sums the cycles' corrections (each
+                                 stored in u) in fp64.  The basis is rebuilt by each cycle
+                                 instead of being stored whole.  A cap below two vectors:
+                                 BSPAI_ERR_INVALID. */
 } bspai_opts_t;
 
 typedef struct {
@@ -121,6 +135,8 @@ typedef struct {
     double nbe[33];            /* ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) at each residual */
     double dx[32];             /* ||d_i||_inf / ||x_{i+1}||_inf */
     double relres[32];         /* |g_k| / ||M r||_2 at the end of each GMRES */
+    int32_t kmem;              /* steps per GMRES cycle the Krylov basis held (kmax unless capped) */
+    int32_t gmres_cycles[32];  /* GMRES cycles of each refinement step (1 unless capped) */
 } bspai_solve_info_t;
 
 /* Kernel-class timing, recorded with CUDA events on the launching stream. */
@@ -458,10 +474,51 @@ typedef struct {
     int32_t max_ir_steps;   /* most GMRES runs of any pair */
     int32_t max_iters;      /* most GMRES steps of any pair, summed over its refinement steps */
     int64_t total_iters;    /* GMRES steps over all pairs */
-    int32_t block_threads;  /* CTA size picked by the autotuner */
+    int32_t block_threads;  /* CTA size of the schedule used */
     int32_t grid;           /* CTAs of the persistent GMRES launch */
     int32_t kmax;           /* GMRES steps allowed per refinement step */
+    int32_t mgs_rows;       /* the schedule's MGS load tile (bspai_batch_schedule_t) */
+    int32_t z_shared_rows;  /* the schedule's z-in-shared-memory limit */
+    int32_t m_schedule;     /* the schedule's bucket order */
+    int32_t tuned_candidates; /* schedules timed by this call (0: cached or forced) */
+    float tune_ms;          /* their summed GPU time */
 } bspai_batch_info_t;
+
+/* A schedule of the batched GMRES launch.  For a given block_threads every
+ * schedule computes the same bits (the dot products of MGS are summed per
+ * thread over rows t, t + block_threads, ... and then over the CTA in a fixed
+ * tree); the other three fields move loads and storage only.
+ *   block_threads  CTA size: 128, 256 or 512 (one CTA per (system, RHS) pair).
+ *   mgs_rows       the MGS load tile: rows per thread whose loads one pass
+ *                  issues before any arithmetic (u_g fp32: 8 or 16; fp64: 4 or
+ *                  8; 0 = the smaller).
+ *   z_shared_rows  pairs of at most this many rows keep z, the vector being
+ *                  orthogonalised, in shared memory for the whole Arnoldi step
+ *                  (0 = never; -1 = as many rows as fit); limited by the
+ *                  shared memory left at the CTAs per SM that the registers
+ *                  allow.
+ *   m_schedule     the bucket schedule of the M products: 0 row-fused (each
+ *                  thread takes two rows at a time through every bucket), 1
+ *                  bucket-major (one sweep over the pair's rows per bucket,
+ *                  the partial sums carried in fp64 between sweeps). */
+typedef struct {
+    int32_t block_threads;
+    int32_t mgs_rows;
+    int32_t z_shared_rows;
+    int32_t m_schedule;
+} bspai_batch_schedule_t;
+
+/* Fixes the schedule of later gmres_ir_solve_batched calls made by the calling
+ * host thread (NULL: back to the autotuner).  Checked when the solve runs: a
+ * field outside its candidates, or z_shared_rows above what fits, gives
+ * BSPAI_ERR_INVALID there.  Here only block_threads and m_schedule are checked. */
+int bspai_batch_schedule_force(const bspai_batch_schedule_t* sched);
+
+/* The candidates the most recent autotuning (any thread) timed, in the order
+ * timed, and the GPU milliseconds of each one's sample run (the largest pairs,
+ * four per SM, 32 Arnoldi steps each): up to cap entries
+ * into sched / ms (host arrays); *count = the number the tuning timed. */
+int bspai_batch_tune_table(bspai_batch_schedule_t* sched, float* ms, int32_t cap, int32_t* count);
 
 /* BSPAI-GMRES-IR (Alg 3.1) for nsys independent systems with nrhs right-hand
  * sides each.  A, the pattern and M hold the systems block-diagonally: system s
@@ -474,8 +531,10 @@ typedef struct {
  * gmres_ir_solve, and its own left-preconditioned MGS-GMRES (vectors in u_g,
  * A v in u_p, bucketed M v, Givens in fp64).  Each refinement step of the
  * batch is one persistent launch in which a CTA takes pairs, largest systems
- * first, and runs each GMRES with CTA barriers only; the CTA size is chosen by
- * timing the candidates on the batch (cached per shape).  The operations of
+ * first, and runs each GMRES with CTA barriers only; the schedule of that
+ * launch (bspai_batch_schedule_t) is chosen by timing candidates on a sample
+ * run (the largest pairs, four per SM, 32 Arnoldi steps) in a staged search -- CTA size, then the MGS tile, then z
+ * in shared memory, then the bucket schedule -- and cached per shape.  The operations of
  * one refinement step (residuals, tests, the GMRES launch, tests) are captured
  * once into a CUDA graph and replayed for every step (launched directly while
  * kernel-class profiling is on).  kmax defaults to

@@ -58,19 +58,27 @@ class BucketInfo(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tau", C.c_double), ("kmax", C.c_int32), ("i_max", C.c_int32), ("x0_given", C.c_int32),
                 ("max_blocks", C.c_int32), ("u_stop", C.c_double), ("stagnation", C.c_double),
-                ("barrier_timeout_s", C.c_double)]
+                ("barrier_timeout_s", C.c_double), ("basis_bytes_max", C.c_int64)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("ir_steps", C.c_int32), ("stop_reason", C.c_int32),
                 ("total_iters", C.c_int32), ("gmres_iters", C.c_int32 * 32), ("nbe", C.c_double * 33),
-                ("dx", C.c_double * 32), ("relres", C.c_double * 32)]
+                ("dx", C.c_double * 32), ("relres", C.c_double * 32), ("kmem", C.c_int32),
+                ("gmres_cycles", C.c_int32 * 32)]
 
 
 class BatchInfo(C.Structure):
     _fields_ = [("pairs", C.c_int32), ("converged", C.c_int32), ("nonfinite", C.c_int32),
                 ("ir_launches", C.c_int32), ("max_ir_steps", C.c_int32), ("max_iters", C.c_int32),
-                ("total_iters", C.c_int64), ("block_threads", C.c_int32), ("grid", C.c_int32), ("kmax", C.c_int32)]
+                ("total_iters", C.c_int64), ("block_threads", C.c_int32), ("grid", C.c_int32), ("kmax", C.c_int32),
+                ("mgs_rows", C.c_int32), ("z_shared_rows", C.c_int32), ("m_schedule", C.c_int32),
+                ("tuned_candidates", C.c_int32), ("tune_ms", C.c_float)]
+
+
+class BatchSchedule(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("mgs_rows", C.c_int32), ("z_shared_rows", C.c_int32),
+                ("m_schedule", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -137,6 +145,9 @@ _sig("gmres_ir_solve", _i, [C.POINTER(CsrT), _vp, _vp, _vp, _i, _i, _i, _i, _d, 
                             C.POINTER(SolveInfo)])
 _sig("gmres_ir_solve_batched", _i, [_vp, _vp, C.c_int32, C.c_int32, _vp, _vp, _vp, _i, _i, _d, C.POINTER(Opts),
                                     _vp, _vp, C.POINTER(BatchInfo), _vp, _vp])
+_sig("bspai_batch_schedule_force", _i, [C.POINTER(BatchSchedule)])
+_sig("bspai_batch_tune_table", _i, [C.POINTER(BatchSchedule), C.POINTER(C.c_float), C.c_int32,
+                                    C.POINTER(C.c_int32)])
 _sig("gmres_ir_solve_h", _i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, C.POINTER(Opts), _vp, _vp,
                               C.POINTER(SolveInfo)])
 _sig("bspai_bucket_A", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, C.POINTER(_vp), C.POINTER(BucketInfo)])
@@ -248,8 +259,9 @@ class BMHandle(_Handle):
 
 
 def opts(tau=1e-4, kmax=0, i_max=0, x0_given=False, u_stop=0.0, stagnation=0.0, barrier_timeout_s=0.0,
-         max_blocks=0) -> Opts:
-    return Opts(tau, kmax, i_max, int(x0_given), int(max_blocks), u_stop, stagnation, barrier_timeout_s)
+         max_blocks=0, basis_bytes_max=0) -> Opts:
+    return Opts(tau, kmax, i_max, int(x0_given), int(max_blocks), u_stop, stagnation, barrier_timeout_s,
+                int(basis_bytes_max))
 
 
 def profile_enable(on: bool = True):
@@ -431,7 +443,8 @@ def _solve_info(si: SolveInfo) -> dict:
     k = si.ir_steps
     return dict(status=si.status, status_name=STATUS_NAMES[si.status], ir_steps=k, stop_reason=si.stop_reason,
                 total_iters=si.total_iters, gmres_iters=list(si.gmres_iters[:k]),
-                nbe=list(si.nbe[:min(33, k + 1)]), dx=list(si.dx[:k]), relres=list(si.relres[:k]))
+                nbe=list(si.nbe[:min(33, k + 1)]), dx=list(si.dx[:k]), relres=list(si.relres[:k]), kmem=si.kmem,
+                gmres_cycles=list(si.gmres_cycles[:k]))
 
 
 def probe_fma(prec="fp32", iters=4096, stream=None) -> dict:
@@ -528,6 +541,31 @@ def gmres_ir_solve_hb(Ah: AHandle, BA: BMHandle, b, BM: BMHandle, M: MHandle | N
     out = _solve_info(si)
     out["status"] = st
     return out
+
+
+def batch_schedule_force(block_threads: int | None = None, mgs_rows: int = 0, z_shared_rows: int = 0,
+                         m_schedule: int = 0) -> None:
+    """Fixes the schedule of this thread's later batched solves (block_threads
+    None: back to the autotuner); see bspai_batch_schedule_t."""
+    if block_threads is None:
+        _check(_lib.bspai_batch_schedule_force(None))
+        return
+    sc = BatchSchedule(int(block_threads), int(mgs_rows), int(z_shared_rows), int(m_schedule))
+    _check(_lib.bspai_batch_schedule_force(C.byref(sc)))
+
+
+def batch_tune_table() -> list[dict]:
+    """The candidates the most recent batch autotuning timed, in order, with the
+    GPU milliseconds of each one's sample run (the largest pairs, four per SM,
+    32 Arnoldi steps)."""
+    cnt = C.c_int32(0)
+    _check(_lib.bspai_batch_tune_table(None, None, 0, C.byref(cnt)))
+    n = cnt.value
+    sc = (BatchSchedule * max(n, 1))()
+    ms = (C.c_float * max(n, 1))()
+    _check(_lib.bspai_batch_tune_table(sc, ms, n, C.byref(cnt)))
+    return [dict(block_threads=sc[i].block_threads, mgs_rows=sc[i].mgs_rows, z_shared_rows=sc[i].z_shared_rows,
+                 m_schedule=sc[i].m_schedule, ms=float(ms[i])) for i in range(min(n, cnt.value))]
 
 
 def gmres_ir_solve_batched(Ah: AHandle, row_off, nrhs: int, B, BM: BMHandle, M: MHandle | None, X, u_g="fp32",

@@ -14,8 +14,12 @@
 // as CTA reductions, Givens rotations and the triangular solve in fp64 -- with
 // only CTA barriers, no grid-wide synchronisation.  Per-pair residuals and
 // stopping tests (Alg 3.1 loop) run as batched kernels between those launches.
-// The CTA size is chosen by timing the candidates on a short fixed-length
-// GMRES run of the batch (cached per batch shape).
+// The schedule of the GMRES launch -- CTA size, the MGS load tile, whether z
+// sits in shared memory, and the order in which M's buckets are swept -- is
+// picked by timing candidates on a short fixed-length GMRES run of the batch
+// (cached per batch shape).  Every candidate computes the same bits for a given
+// CTA size: the tile and the bucket order move loads and storage, not the
+// order of any sum.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -126,12 +130,45 @@ __device__ void givens_pair(int j, int kmax, double hn, double* H, double* cs, d
     *done = (*res <= __dmul_rn(tau, beta)) || hn == 0.0 || j + 1 >= kmax || !fin;
 }
 
-// y[lr] = (M x)_{r0 + lr} for the rows of one system, the CTA's threads
-// striding over them (kept out of line: the kernel calls it three times)
-template <typename XT, typename YT>
-__device__ __noinline__ void rows_apply(const BMDev& M, int r0, int ns, const XT* __restrict__ x, YT* __restrict__ y) {
-    // two rows per thread at a time (lr and lr + blockDim.x): two independent gather chains
+// y[lr] = (M x)_{r0 + lr} for the rows of one system, under a bucket schedule
+// (kept out of line: the kernel calls it three times).
+//   MS 0, row-fused: the CTA's threads stride over the rows, two rows per
+//     thread at a time (lr and lr + blockDim.x: two independent gather chains),
+//     each row through every bucket in turn.
+//   MS 1, bucket-major: one sweep over the rows per bucket; each row's
+//     partial sum (ascending columns, fp64 for an fp64 bucket, fp32 otherwise)
+//     is added in fp64 to the row's running sum in ys, so the sums and their
+//     order are those of the row-fused form (yi = 0, then yi + p_k for
+//     k = 0, 1, ...).  A row has the same owner thread in every sweep, so ys
+//     needs no barrier between sweeps.
+template <typename XT, typename YT, int MS>
+__device__ __noinline__ void rows_apply(const BMDev& M, int r0, int ns, const XT* __restrict__ x, YT* y,
+                                        double* __restrict__ ys) {
     const int bd = blockDim.x;
+    if (MS) {
+        bool first = true;
+        for (int k = 0; k < M.q; ++k) {
+            const BucketDev& B = M.b[k];
+            if (B.prec == BSPAI_DROP) continue;  // dropped entries are not stored
+            for (int lr = threadIdx.x; lr < ns; lr += bd) {
+                const int64_t r = r0 + lr, sl = r >> 5;
+                const int64_t sb = B.sptr[sl];
+                const int w = (int)((B.sptr[sl + 1] - sb) >> 5);
+                double p;
+                switch (B.prec) {
+                case BSPAI_FP64: p = row_partial_f64<XT>(B, sb, w, x, r); break;
+                case BSPAI_FP32: p = (double)row_partial_f32<BSPAI_FP32, XT>(B, sb, w, x, r); break;
+                case BSPAI_FP16: p = (double)row_partial_f32<BSPAI_FP16, XT>(B, sb, w, x, r); break;
+                case BSPAI_BF16: p = (double)row_partial_f32<BSPAI_BF16, XT>(B, sb, w, x, r); break;
+                default: p = (double)row_partial_f32<BSPAI_E4M3, XT>(B, sb, w, x, r); break;
+                }
+                ys[lr] = __dadd_rn(first ? 0.0 : ys[lr], p);
+            }
+            first = false;
+        }
+        for (int lr = threadIdx.x; lr < ns; lr += bd) y[lr] = from_f64<YT>(first ? 0.0 : ys[lr]);
+        return;
+    }
     int lr = threadIdx.x;
     for (; lr + bd < ns; lr += 2 * bd) {
         double ya, yb;
@@ -142,10 +179,12 @@ __device__ __noinline__ void rows_apply(const BMDev& M, int r0, int ns, const XT
     if (lr < ns) y[lr] = from_f64<YT>(bucketed_row<XT>(M, r0 + lr, x));
 }
 
-// rows per thread whose loads an MGS pass issues together
+// The MGS load tile: rows per thread whose loads a pass issues together (two
+// candidates per u_g for the autotuner)
 template <typename T>
 struct MgsU {
-    static constexpr int U = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int lo = sizeof(T) == 4 ? 8 : 4;
+    static constexpr int hi = 2 * lo;
 };
 
 struct PairState {
@@ -163,16 +202,23 @@ struct PairState {
     double* nbe;       // last normwise backward error
 };
 
-template <typename T>
+// U: the MGS load tile.  zcap: pairs of at most zcap rows keep z (the vector
+// being orthogonalised) in dynamic shared memory for the whole Arnoldi step
+// instead of in its basis slot, which takes the z load and store of every MGS
+// pass off the memory system; v_{j+1} is written to the basis once, at the
+// end.  MS: the bucket schedule of the M products.
+template <typename T, int U, int MS>
 __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ BMDev Av, const __grid_constant__ BMDev Mv,
                                                       const int32_t* __restrict__ row_off, int nsys, int n,
                                                       const int32_t* __restrict__ order, int npairs, int* queue,
                                                       const int32_t* __restrict__ status, const double* __restrict__ R,
-                                                      double* __restrict__ X, T* Vws, T* Wws, int64_t ldv,
-                                                      double* Hws, double* Sws, int kmax, double tau,
-                                                      int32_t* __restrict__ iters, int32_t* __restrict__ steps,
-                                                      double* __restrict__ relres, double* __restrict__ dmax,
-                                                      double* __restrict__ dxmax) {
+                                                      double* __restrict__ X, T* Vws, T* Wws, double* Yws, int64_t ldv,
+                                                      double* Hws, double* Sws, int kmax, double tau, int zcap,
+                                                      int32_t* __restrict__ iters,
+                                                      int32_t* __restrict__ steps, double* __restrict__ relres,
+                                                      double* __restrict__ dmax, double* __restrict__ dxmax) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    T* const s_z = reinterpret_cast<T*>(s_dyn);
     __shared__ T s_w[33];
     __shared__ double s_d[33];
     __shared__ int s_p, s_done;
@@ -199,7 +245,7 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
         const double* rr = R + (int64_t)rhs * n;
         double* xx = X + (int64_t)rhs * n;
         // s = M r (Alg 2.3), stored in u_g; beta = ||s||_2
-        rows_apply<double, T>(Mv, r0, ns, rr, V);
+        rows_apply<double, T, MS>(Mv, r0, ns, rr, V, Yws + (int64_t)blockIdx.x * ldv);
         T acc = T(0);
         for (int lr = tid; lr < ns; lr += bd) acc = Ar::add(acc, Ar::mul(V[lr], V[lr]));
         const T beta = Ar::sqrt(block_sum(acc, s_w));
@@ -212,10 +258,10 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
             for (int j = 0; j < kmax; ++j) {
                 __syncthreads();
                 const T* vj = V + (int64_t)j * ldv;
-                rows_apply<T, T>(Av, r0, ns, vj - r0, w);
+                rows_apply<T, T, 0>(Av, r0, ns, vj - r0, w, nullptr);
                 __syncthreads();
-                T* z = V + (int64_t)(j + 1) * ldv;
-                rows_apply<T, T>(Mv, r0, ns, w - r0, z);
+                T* z = ns <= zcap ? s_z : V + (int64_t)(j + 1) * ldv;
+                rows_apply<T, T, MS>(Mv, r0, ns, w - r0, z, Yws + (int64_t)blockIdx.x * ldv);
                 // modified Gram-Schmidt: pass i updates z by the previous coefficient and
                 // dots it with v_i; the last pass forms ||z||_2 (each thread owns its rows of z)
                 T hprev = T(0);
@@ -227,7 +273,6 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
                     // any store (z shares V's storage, so without this every load
                     // would wait for the previous row's store); the rows are still
                     // accumulated in the order tid, tid + bd, tid + 2 bd, ...
-                    constexpr int U = MgsU<T>::U;
                     for (int b0 = tid; b0 < ns; b0 += bd * U) {
                         T zr[U], pv[U], iv[U];
 #pragma unroll
@@ -257,8 +302,11 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
                         hprev = h;
                     } else {
                         const T hn = Ar::sqrt(h);
-                        if (hn > T(0) && isfinite((double)hn))
-                            for (int lr = tid; lr < ns; lr += bd) z[lr] = Ar::div(z[lr], hn);
+                        // v_{j+1} = z / h_{j+1,j} into the basis (in place when z lives there)
+                        const bool nz = hn > T(0) && isfinite((double)hn);
+                        T* vn = V + (int64_t)(j + 1) * ldv;
+                        if (nz || vn != z)
+                            for (int lr = tid; lr < ns; lr += bd) vn[lr] = nz ? Ar::div(z[lr], hn) : z[lr];
                         if (tid == 0) {
                             double rs;
                             int dn;
@@ -389,13 +437,66 @@ struct TuneKey {
         return std::tie(n, nsys, nrhs, ug, kmax) < std::tie(o.n, o.nsys, o.nrhs, o.ug, o.kmax);
     }
 };
+
+// One schedule of the batched GMRES launch (see bspai_batch_schedule_t)
+struct Sched {
+    int bd = 512;     // CTA size
+    int urows = 0;    // MGS load tile (rows per thread), 0: the smaller candidate
+    int zcap = 0;     // pairs of at most zcap rows keep z in shared memory
+    int msched = 0;   // 0 row-fused, 1 bucket-major
+};
+
 static std::mutex g_tune_mu;
-static std::map<TuneKey, int> g_tuned;  // CTA size per batch shape
+static std::map<TuneKey, Sched> g_tuned;  // schedule per batch shape
+static std::vector<bspai_batch_schedule_t> g_table_s;  // the last tuning's candidates, in the order timed
+static std::vector<float> g_table_ms;
+static thread_local bool t_forced = false;
+static thread_local Sched t_force;
 
 template <typename T>
-static int occupancy_blocks(int bd, int* occ) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_gmres_batch<T>, bd, 0);
+using BatchKernel = decltype(&k_gmres_batch<T, MgsU<T>::lo, 0>);
+
+template <typename T>
+static BatchKernel<T> batch_kernel(int urows, int msched) {
+    if (urows == MgsU<T>::hi) return msched ? k_gmres_batch<T, MgsU<T>::hi, 1> : k_gmres_batch<T, MgsU<T>::hi, 0>;
+    return msched ? k_gmres_batch<T, MgsU<T>::lo, 1> : k_gmres_batch<T, MgsU<T>::lo, 0>;
+}
+
+template <typename T>
+static int occupancy_blocks(BatchKernel<T> kern, int bd, size_t smem, int* occ) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, bd, smem);
     if (e) return cuda_error(e, "occupancy", __FILE__, __LINE__);
+    return BSPAI_OK;
+}
+
+// The largest z_shared_rows for this kernel and CTA size that keeps the CTAs per
+// SM its registers allow (0 when none fit); raises the kernel's dynamic shared
+// memory limit to the opt-in maximum on the way.
+template <typename T>
+static int zcap_limit(BatchKernel<T> kern, int bd, int* zmax) {
+    int dev = 0, sm_bytes = 0, blk_bytes = 0, occ0 = 0;
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&blk_bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+    const int dyn_max = blk_bytes - (int)fa.sharedSizeBytes;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    int rc = occupancy_blocks<T>(kern, bd, 0, &occ0);
+    if (rc) return rc;
+    *zmax = 0;
+    if (occ0 < 1) return BSPAI_OK;
+    // 1 KB of shared memory per CTA is reserved by the system
+    int bytes = sm_bytes / occ0 - (int)fa.sharedSizeBytes - 1024;
+    if (bytes > dyn_max) bytes = dyn_max;
+    for (int z = bytes / (int)sizeof(T) / 32 * 32; z >= 32; z -= 256) {
+        int occ = 0;
+        if ((rc = occupancy_blocks<T>(kern, bd, sizeof(T) * (size_t)z, &occ))) return rc;
+        if (occ >= occ0) {
+            *zmax = z;
+            return BSPAI_OK;
+        }
+    }
     return BSPAI_OK;
 }
 
@@ -499,15 +600,17 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
     const BMDev Av = single_bucket_view(A->sell, u_p == BSPAI_FP64 ? (const void*)A->val64 : (const void*)A->val32,
                                         u_p);
     const BMDev Mv = BM->dev();
-    // CTA size: cached per batch shape, else timed on a short fixed-length run
+    // schedule: forced by the caller's thread, cached per batch shape, or tuned below
     const size_t ws_budget = (size_t)24 << 30;
-    int sms = num_sms();
-    auto grid_for = [&](int bd, int* grid) -> int {
+    const int sms = num_sms();
+    const int nmax32 = (int)ceil_div(nmax > 0 ? nmax : 1, 32) * 32;
+    auto grid_for = [&](const Sched& c, int* grid) -> int {
         int occ = 0;
-        int r2 = occupancy_blocks<T>(bd, &occ);
+        int r2 = occupancy_blocks<T>(batch_kernel<T>(c.urows, c.msched), c.bd, sizeof(T) * (size_t)c.zcap, &occ);
         if (r2) return r2;
         if (occ < 1) return set_error(BSPAI_ERR_CUDA, "batched GMRES kernel does not fit on an SM");
-        const size_t per = sizeof(T) * (size_t)ldv * (kmax + 2) + sizeof(double) * ((size_t)(kmax + 1) * kmax + 4 * (kmax + 2));
+        const size_t per = sizeof(T) * (size_t)ldv * (kmax + 2) + sizeof(double) * (size_t)ldv +
+                           sizeof(double) * ((size_t)(kmax + 1) * kmax + 4 * (kmax + 2));
         int gmax = (int)(ws_budget / per);
         int gr = sms * occ;
         if (o.max_blocks > 0 && gr > o.max_blocks) gr = o.max_blocks;
@@ -516,36 +619,100 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         *grid = gr < 1 ? 1 : gr;
         return BSPAI_OK;
     };
-    int bd = 0;
+    // the z-in-shared-memory limit of each (tile, CTA size), which also raises the
+    // kernels' dynamic shared memory limit before any launch
+    const int cand_bd[3] = {128, 256, 512};
+    int zlim[2][2][3];  // [tile][bucket schedule][CTA size]: rows of z that fit
+    for (int u = 0; u < 2; ++u)
+        for (int m = 0; m < 2; ++m)
+            for (int c = 0; c < 3; ++c)
+                if ((rc = zcap_limit<T>(batch_kernel<T>(u ? MgsU<T>::hi : MgsU<T>::lo, m), cand_bd[c],
+                                        &zlim[u][m][c])))
+                    return done(rc);
+    auto zfit = [&](const Sched& c) {
+        const int u = c.urows == MgsU<T>::hi ? 1 : 0;
+        for (int k = 0; k < 3; ++k)
+            if (cand_bd[k] == c.bd) return zlim[u][c.msched ? 1 : 0][k];
+        return 0;
+    };
+    // the candidate the tuner tries: every pair of the batch, if it fits
+    auto zlimit = [&](const Sched& c) {
+        const int z = zfit(c);
+        return z < nmax32 ? z : nmax32;
+    };
+    Sched sch;
+    sch.urows = MgsU<T>::lo;
+    bool have = false;
     const TuneKey key{n, nsys, nrhs, ug, kmax};
-    {
+    if (t_forced) {
+        sch = t_force;
+        if (sch.urows == 0) sch.urows = MgsU<T>::lo;
+        if (sch.urows != MgsU<T>::lo && sch.urows != MgsU<T>::hi)
+            return done(set_error(BSPAI_ERR_INVALID, "batch schedule: mgs_rows must be %d or %d for this u_g",
+                                  MgsU<T>::lo, MgsU<T>::hi));
+        if (sch.zcap < 0) sch.zcap = zlimit(sch);  // as many rows as fit
+        if (sch.zcap > zfit(sch))
+            return done(set_error(BSPAI_ERR_INVALID,
+                                  "batch schedule: z_shared_rows %d exceeds the %d rows that fit in shared memory "
+                                  "at this CTA size and tile",
+                                  sch.zcap, zfit(sch)));
+        if (sch.zcap > nmax32) sch.zcap = nmax32;  // no pair is larger: the same schedule
+        have = true;
+    } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) bd = it->second;
+        if (it != g_tuned.end()) {
+            sch = it->second;
+            have = true;
+        }
     }
     // workspace for the largest grid among the candidates
     int gmax_all = 0;
-    for (int cand : {128, 256, 512}) {
+    for (int u = 0; u < 2; ++u)
+        for (int m = 0; m < 2; ++m)
+            for (int c = 0; c < 3; ++c)
+                for (int zs = 0; zs < 2; ++zs) {
+                    Sched cs;
+                    cs.bd = cand_bd[c];
+                    cs.urows = u ? MgsU<T>::hi : MgsU<T>::lo;
+                    cs.msched = m;
+                    cs.zcap = zs ? (zlim[u][m][c] < nmax32 ? zlim[u][m][c] : nmax32) : 0;
+                    int gr;
+                    if ((rc = grid_for(cs, &gr))) return done(rc);
+                    gmax_all = gr > gmax_all ? gr : gmax_all;
+                }
+    if (have) {
         int gr;
-        if ((rc = grid_for(cand, &gr))) return done(rc);
+        if ((rc = grid_for(sch, &gr))) return done(rc);
         gmax_all = gr > gmax_all ? gr : gmax_all;
     }
     T *Vws = nullptr, *Wws = nullptr;
-    double *Hws = nullptr, *Sws = nullptr;
+    double *Yws = nullptr, *Hws = nullptr, *Sws = nullptr;
     if ((rc = take((void**)&Vws, sizeof(T) * (size_t)gmax_all * ldv * (kmax + 1)))) return done(rc);
     if ((rc = take((void**)&Wws, sizeof(T) * (size_t)gmax_all * ldv))) return done(rc);
+    if ((rc = take((void**)&Yws, sizeof(double) * (size_t)gmax_all * ldv))) return done(rc);
     if ((rc = take((void**)&Hws, sizeof(double) * (size_t)gmax_all * (kmax + 1) * kmax))) return done(rc);
     if ((rc = take((void**)&Sws, sizeof(double) * (size_t)gmax_all * 4 * (kmax + 2)))) return done(rc);
-    auto launch_gmres = [&](int bdim, int grid, const double* Rin, double* Xout, int kcap, double tcap, PairState& St,
-                            cudaStream_t st) {
-        k_gmres_batch<T><<<grid, bdim, 0, st>>>(Av, Mv, row_off, nsys, n, d_order, npairs, d_queue, St.status, Rin,
-                                                Xout, Vws, Wws, ldv, Hws, Sws, kcap, tcap, St.iters, St.steps,
-                                                St.relres, St.dmax, St.dxmax);
+    auto launch_gmres = [&](const Sched& c, int grid, const double* Rin, double* Xout, int kcap, double tcap,
+                            PairState& St, cudaStream_t st, int np) {
+        batch_kernel<T>(c.urows, c.msched)<<<grid, c.bd, sizeof(T) * (size_t)c.zcap, st>>>(
+            Av, Mv, row_off, nsys, n, d_order, np, d_queue, St.status, Rin, Xout, Vws, Wws, Yws, ldv, Hws, Sws,
+            kcap, tcap, c.zcap, St.iters, St.steps, St.relres, St.dmax, St.dxmax);
         note_launch();
         return cudaGetLastError();
     };
-    if (bd == 0) {
-        // autotune: 8 Arnoldi steps (tau = 0) of every pair on the right-hand sides, into scratch
+    int tuned = 0;
+    float tune_ms = 0.0f;
+    if (!have) {
+        // autotune: a fixed sample -- the largest pairs, four per SM (the batch's time is
+        // in its large systems: MGS work grows with n_s k^2), 32 Arnoldi steps each
+        // (tau = 0) on the right-hand sides, into scratch -- for each candidate of a
+        // staged search (CTA size, then the MGS tile, then z in shared memory, then the
+        // bucket schedule), each stage keeping the fastest so far.  Timing every pair
+        // for 8 steps instead weighted the small systems and early steps, and picked
+        // 256-thread CTAs that ran the 512 x 8 batch 15 % slower than 512.
+        const int np_tune = npairs < 4 * sms ? npairs : 4 * sms;
+        const int k_tune = kmax < 32 ? kmax : 32;
         double* Xs = nullptr;
         void* ps2 = nullptr;
         if ((rc = take((void**)&Xs, sizeof(double) * (size_t)n * nrhs))) return done(rc);
@@ -572,29 +739,61 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
     } while (0)
         BSPAI_TUNE_TRY(cudaEventCreate(&ev.e0));
         BSPAI_TUNE_TRY(cudaEventCreate(&ev.e1));
+        std::vector<bspai_batch_schedule_t> tab_s;
+        std::vector<float> tab_ms;
         float best = 1e30f;
-        for (int cand : {128, 256, 512}) {
+        auto trial = [&](const Sched& c) -> int {
             int gr;
-            if ((rc = grid_for(cand, &gr))) return done(rc);
+            int r2 = grid_for(c, &gr);
+            if (r2) return r2;
             BSPAI_TUNE_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
             BSPAI_TUNE_TRY(cudaMemsetAsync(Xs, 0, sizeof(double) * (size_t)n * nrhs, s));
             BSPAI_TUNE_TRY(cudaEventRecord(ev.e0, s));
-            BSPAI_TUNE_TRY(launch_gmres(cand, gr, Bv, Xs, kmax < 8 ? kmax : 8, 0.0, T2, s));
+            BSPAI_TUNE_TRY(launch_gmres(c, gr, Bv, Xs, k_tune, 0.0, T2, s, np_tune));
             BSPAI_TUNE_TRY(cudaEventRecord(ev.e1, s));
             BSPAI_TUNE_TRY(cudaEventSynchronize(ev.e1));
             float ms = 0;
             BSPAI_TUNE_TRY(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+            tab_s.push_back(bspai_batch_schedule_t{c.bd, c.urows, c.zcap, c.msched});
+            tab_ms.push_back(ms);
+            tune_ms += ms;
+            ++tuned;
             if (ms < best) {
                 best = ms;
-                bd = cand;
+                sch = c;
             }
+            return BSPAI_OK;
+        };
+        for (int c = 0; c < 3; ++c) {
+            Sched cs;
+            cs.bd = cand_bd[c];
+            cs.urows = MgsU<T>::lo;
+            if ((rc = trial(cs))) return done(rc);
+        }
+        {
+            Sched cs = sch;
+            cs.urows = MgsU<T>::hi;
+            if ((rc = trial(cs))) return done(rc);
+        }
+        if (zlimit(sch) >= 32) {
+            Sched cs = sch;
+            cs.zcap = zlimit(sch);
+            if ((rc = trial(cs))) return done(rc);
+        }
+        {
+            Sched cs = sch;
+            cs.msched = 1;
+            if ((rc = trial(cs))) return done(rc);
         }
 #undef BSPAI_TUNE_TRY
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = bd;
+        g_tuned[key] = sch;
+        g_table_s = tab_s;
+        g_table_ms = tab_ms;
     }
+    const int bd = sch.bd;
     int grid = 0;
-    if ((rc = grid_for(bd, &grid))) return done(rc);
+    if ((rc = grid_for(sch, &grid))) return done(rc);
     // one refinement step: residuals, tests, the persistent GMRES launch, tests
     auto step = [&](cudaStream_t st) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(S.rmax, 0, sizeof(double) * npairs * 2, st);  // rmax, xmax
@@ -605,7 +804,7 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         note_launch();
         {
             ProfScope ps(BSPAI_K_MGS, st);
-            if ((e = launch_gmres(bd, grid, R, X, kmax, tau, S, st))) return e;
+            if ((e = launch_gmres(sch, grid, R, X, kmax, tau, S, st, npairs))) return e;
         }
         k_batch_after<<<(unsigned)ceil_div(npairs, 256), 256, 0, st>>>(npairs, S, ustop, stag);
         note_launch();
@@ -710,6 +909,11 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         info->block_threads = bd;
         info->grid = grid;
         info->kmax = kmax;
+        info->mgs_rows = sch.urows;
+        info->z_shared_rows = sch.zcap;
+        info->m_schedule = sch.msched;
+        info->tuned_candidates = tuned;
+        info->tune_ms = tune_ms;
     }
     done(BSPAI_OK);
     if (nonfin) return set_error(BSPAI_NONFINITE, "batched solve: %d pairs hit a non-finite value", nonfin);
@@ -724,6 +928,37 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
 using namespace bspai;
 
 extern "C" {
+
+int bspai_batch_schedule_force(const bspai_batch_schedule_t* sched) {
+    if (!sched) {
+        t_forced = false;
+        return BSPAI_OK;
+    }
+    if (sched->block_threads != 128 && sched->block_threads != 256 && sched->block_threads != 512)
+        return set_error(BSPAI_ERR_INVALID, "bspai_batch_schedule_force: block_threads must be 128, 256 or 512");
+    if (sched->m_schedule != 0 && sched->m_schedule != 1)
+        return set_error(BSPAI_ERR_INVALID, "bspai_batch_schedule_force: m_schedule must be 0 or 1");
+    if (sched->z_shared_rows < -1 || sched->mgs_rows < 0)
+        return set_error(BSPAI_ERR_INVALID, "bspai_batch_schedule_force: negative field");
+    t_force.bd = sched->block_threads;
+    t_force.urows = sched->mgs_rows;
+    t_force.zcap = sched->z_shared_rows;
+    t_force.msched = sched->m_schedule;
+    t_forced = true;
+    return BSPAI_OK;
+}
+
+int bspai_batch_tune_table(bspai_batch_schedule_t* sched, float* ms, int32_t cap, int32_t* count) {
+    if (!count || cap < 0 || (cap > 0 && (!sched || !ms)))
+        return set_error(BSPAI_ERR_INVALID, "bspai_batch_tune_table: bad arguments");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *count = (int32_t)g_table_s.size();
+    for (int32_t i = 0; i < cap && i < *count; ++i) {
+        sched[i] = g_table_s[i];
+        ms[i] = g_table_ms[i];
+    }
+    return BSPAI_OK;
+}
 
 int gmres_ir_solve_batched(bspai_A_h A, const int32_t* row_off, int32_t nsys, int32_t nrhs, const double* B,
                            bspai_BM_h BM, bspai_M_h M, bspai_prec_t u_g, bspai_prec_t u_p, double tol,

@@ -20,6 +20,9 @@ e4m3) to separate the cost of the formats from the cost of the mix.
 --batch NSYS NRHS runs the batched solver once on a batch of NSYS systems
 with NRHS right-hand sides (the 512 x 32 workload's size distribution), and
 prints its statistics and time (a short launch sequence for a profiler).
+With --schedule BD,MGS_ROWS,Z_ROWS,M_SCHED (repeatable; Z_ROWS -1 = every
+pair that fits) it solves the batch once per given schedule instead of autotuning and
+prints each one's time.
 --adaptive EPS ALPHA times the adaptive SPAI build (beta = 8, identity
 start) on the grid (median of --reps builds) and prints its statistics; with
 --once it builds exactly once (a short launch sequence for a profiler).
@@ -89,11 +92,12 @@ def main():
     p.add_argument("--batch", type=int, nargs=2, default=None, metavar=("NSYS", "NRHS"))
     p.add_argument("--adaptive", type=float, nargs=2, default=None, metavar=("EPS", "ALPHA"))
     p.add_argument("--spai-uf", action="store_true")
+    p.add_argument("--schedule", action="append", default=None, metavar="BD,MGS_ROWS,Z_ROWS,M_SCHED")
     a = p.parse_args()
     if a.spai_uf:
         return spai_uf(a.grid, a.reps, a.once)
     if a.batch:
-        return batch(a.batch[0], a.batch[1])
+        return batch(a.batch[0], a.batch[1], a.schedule)
     if a.adaptive:
         return adaptive(a.grid, a.adaptive[0], int(a.adaptive[1]), 1 if a.once else a.reps)
     wl = W.workload("convdiff3d", grid=a.grid)
@@ -213,7 +217,7 @@ def adaptive(grid, eps, alpha, reps):
     print(json.dumps({"grid": grid, "eps": eps, "alpha": alpha, "ms": float(np.median(ts)), "info": info}))
 
 
-def batch(nsys, nrhs):
+def batch(nsys, nrhs, schedules=None):
     bw = W.batch_workload(nsys=nsys, nrhs=nrhs)
     A = B.DeviceCSR.from_host(bw["A"])
     P = B.DeviceCSR.from_host(bw["pattern"], with_values=False)
@@ -224,12 +228,23 @@ def batch(nsys, nrhs):
     M, _ = B.bspai_build(A, P, bw["spai_eps"])
     BM, kinfo = B.bspai_bucket_batched(M, row_off, bw["bucket_eps"], bw["precs"])
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    info = B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, tol=bw["tau"])
-    e1.record()
-    torch.cuda.synchronize()
-    print(json.dumps({"batch": [nsys, nrhs], "rows": bw["A"].n, "ms": e0.elapsed_time(e1), **info}))
+    for sc in schedules or [None]:
+        if sc is not None:
+            bd, u, z, m = (int(v) for v in sc.split(","))
+            B.batch_schedule_force(bd, u, z, m)
+        X.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        try:
+            info = B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, tol=bw["tau"])
+        finally:
+            B.batch_schedule_force(None)
+        e1.record()
+        torch.cuda.synchronize()
+        out = {"batch": [nsys, nrhs], "rows": bw["A"].n, "ms": e0.elapsed_time(e1), **info}
+        if sc is None:
+            out["tuning"] = B.batch_tune_table()
+        print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

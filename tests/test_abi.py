@@ -65,7 +65,8 @@ def test_ctypes_structs_match_header_sizes():
     src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "bspai.h")).read(), flags=re.S)
     for cname, py in [("bspai_opts_t", bspai.Opts), ("bspai_solve_info_t", bspai.SolveInfo),
                       ("bspai_bucket_info_t", bspai.BucketInfo), ("bspai_build_info_t", bspai.BuildInfo),
-                      ("bspai_csr_t", bspai.CsrT), ("bspai_gmres_plan_t", bspai.GmresPlan)]:
+                      ("bspai_csr_t", bspai.CsrT), ("bspai_gmres_plan_t", bspai.GmresPlan),
+                      ("bspai_batch_info_t", bspai.BatchInfo), ("bspai_batch_schedule_t", bspai.BatchSchedule)]:
         body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", src).group(1)
         body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
         fields = re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*(?:\[[^\]]*\])?\s*;", body)

@@ -116,6 +116,68 @@ def test_batch_of_one_equals_single_solve(B):
     assert np.abs(xb - host(x)).max() <= 1e-12 * np.abs(host(x)).max()
 
 
+def _forced(B, bw, **sched):
+    B.batch_schedule_force(**sched)
+    try:
+        return _gpu_batch(B, bw)
+    finally:
+        B.batch_schedule_force(None)
+
+
+@pytest.mark.parametrize("bd", [128, 512])
+def test_batch_schedules_compute_the_same_bits(B, bd):
+    """For a given CTA size, every MGS tile, z placement and bucket order gives the
+    same solution bits, iteration counts and statuses (they move loads and storage,
+    not the order of any sum); the reference schedule also matches the oracle."""
+    bw = W.batch_workload(nsys=6, nrhs=3, nmin=60, nmax=1200, seed=5)
+    sizes = np.diff(bw["row_off"])
+    mid = int(np.sort(sizes)[len(sizes) // 2])  # z in shared memory for about half of the pairs
+    ref = _forced(B, bw, block_threads=bd)
+    assert ref["info"]["converged"] == ref["info"]["pairs"]
+    assert ref["info"]["tuned_candidates"] == 0 and ref["info"]["block_threads"] == bd
+    base = host(ref["X"])
+    lo = ref["info"]["mgs_rows"]
+    for sched in [dict(mgs_rows=2 * lo), dict(z_shared_rows=int(sizes.max())), dict(z_shared_rows=mid),
+                  dict(m_schedule=1), dict(mgs_rows=2 * lo, z_shared_rows=mid, m_schedule=1)]:
+        g = _forced(B, bw, block_threads=bd, **sched)
+        for k, v in sched.items():
+            assert g["info"][k] == v, (sched, g["info"])
+        assert np.array_equal(host(g["X"]), base), sched
+        assert np.array_equal(g["iters"], ref["iters"]) and np.array_equal(g["status"], ref["status"]), sched
+
+
+def test_batch_schedule_rejects_what_does_not_fit(B):
+    bw = W.batch_workload(nsys=2, nrhs=1, nmin=100, nmax=200, seed=9)
+    for sched, msg in [(dict(z_shared_rows=1 << 24), "z_shared_rows"), (dict(mgs_rows=3), "mgs_rows")]:
+        with pytest.raises(B.BspaiError) as e:
+            _forced(B, bw, block_threads=256, **sched)
+        assert e.value.status == B.ERR_INVALID and msg in str(e.value)
+    with pytest.raises(B.BspaiError):
+        B.batch_schedule_force(block_threads=100)
+
+
+def test_batch_autotuner_picks_the_fastest_candidate(B):
+    """A new batch shape is tuned: the staged search times at least the three CTA
+    sizes, the larger tile and the bucket-major order, and keeps the fastest; the
+    next call of the same shape reuses it without timing."""
+    bw = W.batch_workload(nsys=9, nrhs=2, nmin=200, nmax=3000, seed=13)
+    g = _gpu_batch(B, bw)
+    info = g["info"]
+    tab = B.batch_tune_table()
+    assert info["tuned_candidates"] == len(tab) >= 5, (info, tab)
+    assert all(t["ms"] > 0 for t in tab)
+    assert {t["block_threads"] for t in tab} >= {128, 256, 512}
+    assert any(t["m_schedule"] == 1 for t in tab)
+    best = min(tab, key=lambda t: t["ms"])
+    assert (best["block_threads"], best["mgs_rows"], best["z_shared_rows"], best["m_schedule"]) == \
+        (info["block_threads"], info["mgs_rows"], info["z_shared_rows"], info["m_schedule"])
+    assert abs(sum(t["ms"] for t in tab) - info["tune_ms"]) <= 1e-3 * info["tune_ms"] + 1e-3
+    g2 = _gpu_batch(B, bw)
+    assert g2["info"]["tuned_candidates"] == 0
+    assert g2["info"]["block_threads"] == info["block_threads"]
+    assert np.array_equal(host(g2["X"]), host(g["X"]))
+
+
 def test_batch_rejects_unaligned_offsets(B):
     bw = W.batch_workload(nsys=2, nrhs=1, nmin=100, nmax=200, seed=9)
     A = B.DeviceCSR.from_host(bw["A"])
