@@ -119,6 +119,14 @@ def _declare(L):
                                C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, _f64p,
                                _i32p, _f64p, _f64p, C.POINTER(C.c_int)]
     L.orc_gmres_ir.restype = C.c_int
+    L.orc_gmres_ir_m.argtypes = [C.POINTER(_System), _f64p, _f64p, C.c_int, C.c_int, C.c_double,
+                                 C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                                 _f64p, _i32p, _f64p, _f64p, C.POINTER(C.c_int), _i32p]
+    L.orc_gmres_ir_m.restype = C.c_int
+    L.orc_gmres_target.argtypes = [C.POINTER(_System), _f64p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                   _f64p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]
+    L.orc_gmres_target.restype = C.c_int
 
 
 def _i32(a):
@@ -396,8 +404,19 @@ def gmres(system: System, r, ug="fp32", up="fp32", tau=1e-4, kmax=500, step_seco
 UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24}
 
 
+def gmres_target(system: System, r, target, ug="fp32", up="fp32", tau=1e-4, kmax=500):
+    """GMRES on (M A) d = M r stopping at |g_{j+1}| <= target (target > 0) instead
+    of the tau test: (d, iterations, beta = ||M r||_2 in u_g, last |g|)."""
+    d = np.zeros(system.n)
+    it = C.c_int(0)
+    rr, be, rs = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    lib().orc_gmres_target(C.byref(system.s), _f64(r), FMT[ug], FMT[up], tau, float(target), int(kmax), d,
+                           C.byref(it), C.byref(rr), C.byref(be), C.byref(rs))
+    return d, it.value, be.value, rs.value
+
+
 def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, imax=10,
-             u_work=None, x0=None, u="fp64", u_r="dd", u_f="fp32") -> dict:
+             u_work=None, x0=None, u="fp64", u_r="dd", u_f="fp32", kmem=0) -> dict:
     """Alg 3.1 with working precision u (fp64, or fp32 for the (single,
     single, double) and (half, single, double) settings of Section 4) and
     residual precision u_r ("dd": Dot2, about twice fp64; "fp64": plain fp64).
@@ -411,15 +430,18 @@ def gmres_ir(system: System, muf, b, ug="fp32", up="fp32", tau=1e-4, kmax=500, i
     u_work = UNIT_ROUNDOFF[u] if u_work is None else u_work
     x = np.zeros(system.n) if x0 is None else _f64(x0).copy()
     its = np.zeros(imax, dtype=np.int32)
+    cyc = np.zeros(imax, dtype=np.int32)
     nbe = np.zeros(imax)
     dx = np.zeros(imax)
     stop = C.c_int(0)
-    steps = lib().orc_gmres_ir(C.byref(system.s), _f64(muf), _f64(b), FMT[ug], FMT[up], tau,
-                               int(kmax), int(imax), u_work, FMT[u], int(u_r == "dd"), FMT[u_f],
-                               int(x0 is not None), x, its, nbe, dx, C.byref(stop))
+    # kmem > 0: the Krylov basis capped at kmem + 1 vectors, each correction
+    # equation solved by restarted GMRES cycles (orc_gmres_ir_m)
+    steps = lib().orc_gmres_ir_m(C.byref(system.s), _f64(muf), _f64(b), FMT[ug], FMT[up], tau,
+                                 int(kmax), int(kmem), int(imax), u_work, FMT[u], int(u_r == "dd"), FMT[u_f],
+                                 int(x0 is not None), x, its, nbe, dx, C.byref(stop), cyc)
     nsteps = min(imax, steps + (1 if stop.value == 1 else 0))
     return dict(x=x, steps=steps, its=its[:max(steps, 0)].tolist(), nbe=nbe[:nsteps].tolist(),
-                dx=dx[:steps].tolist(), stop=stop.value)
+                dx=dx[:steps].tolist(), stop=stop.value, cycles=cyc[:max(steps, 0)].tolist())
 
 
 def transpose_csr(row_ptr, col, val):
@@ -437,7 +459,7 @@ class _Csr:
         self.n, self.row_ptr, self.col, self.val = n, row_ptr, col, val
 
 
-def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
+def adjoint(A, P, muf, x, g, kmax=500, imax=10, kmem=0) -> dict:
     """Adjoint of x = A^-1 b for a loss with dL/dx = g: lambda = A^-T g by the
     refinement driver in fp64 (u_g = u_p = fp64, tau = 1e-12) on A^T, left-
     preconditioned by M^T (q = 1, fp64); dL/db = lambda and dL/dA_ij =
@@ -447,7 +469,7 @@ def adjoint(A, P, muf, x, g, kmax=500, imax=10) -> dict:
     mrp, mcol, mval = transpose_csr(P.row_ptr, P.col, muf)
     At = _Csr(A.n, trp, tcol, tval)
     S = System(At, mrp, mcol, mval, np.zeros(len(mval), np.int8), ["fp64"])
-    out = gmres_ir(S, mval, g, "fp64", "fp64", 1e-12, kmax, imax)
+    out = gmres_ir(S, mval, g, "fp64", "fp64", 1e-12, kmax, imax, kmem=kmem)
     lam = out["x"]
     rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
     dA = -lam[rows] * np.asarray(x)[A.col]
@@ -472,7 +494,7 @@ def adjoint_grad_A(A, lam, x) -> np.ndarray:
 
 
 def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bucket_A=False, u="fp64",
-          u_r="dd", ug=None, up=None, adaptive=None, u_f="fp32") -> dict:
+          u_r="dd", ug=None, up=None, adaptive=None, u_f="fp32", kmem=0) -> dict:
     """Full oracle pipeline on a workload dict: SPAI -> bucketing -> GMRES-IR.
     bucket_A: A v inside GMRES by the bucketed SpMV on A's own buckets (same
     precisions and bucket_eps, thresholds from ||A||_inf; eq. nbe2).
@@ -496,6 +518,6 @@ def solve(wl: dict, bucket_eps=None, precs=None, kmax=500, imax=10, tau=None, bu
         a_stored, _, _ = bucket_store(A.row_ptr, A.col, A.val, a_ids, precs)
     S = System(A, P.row_ptr, P.col, stored, bk["ids"], precs, a_stored, a_ids)
     out = gmres_ir(S, muf, wl["b"], wl["u_g"] if ug is None else ug, wl["u_p"] if up is None else up,
-                   wl["tau"] if tau is None else tau, kmax, imax, u=u, u_r=u_r, u_f=u_f)
+                   wl["tau"] if tau is None else tau, kmax, imax, u=u, u_r=u_r, u_f=u_f, kmem=kmem)
     out.update(spai=sp, muf=muf, buckets=bk, stored=stored)
     return out

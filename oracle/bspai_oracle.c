@@ -789,6 +789,11 @@ void orc_gmres_time_steps(double* out) { g_step_seconds = out; }
 
 int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau, int kmax,
               double* d, int* iters, double* relres) {
+    return orc_gmres_target(S, r, ug, up, tau, 0.0, kmax, d, iters, relres, NULL, NULL);
+}
+
+int orc_gmres_target(const orc_system_t* S, const double* r, int ug, int up, double tau, double target, int kmax,
+                     double* d, int* iters, double* relres, double* beta_out, double* res_out) {
     double* step_seconds = g_step_seconds;
     g_step_seconds = NULL;
     int n = S->n;
@@ -850,7 +855,8 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
             g[j] = cs[j] * g[j];
             res = fabs(g[j + 1]);
             k = j + 1;
-            if (res <= tau * beta || hn == 0.0) {
+            /* the tau test, or |g_{j+1}| <= target when the caller fixes the level */
+            if (res <= (target > 0.0 ? target : tau * beta) || hn == 0.0) {
                 if (step_seconds) step_seconds[j] = omp_get_wtime() - t_step;
                 break;
             }
@@ -873,8 +879,53 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
     }
     if (iters) *iters = k;
     if (relres) *relres = beta > 0.0 ? res / beta : 0.0;
+    if (beta_out) *beta_out = beta;
+    if (res_out) *res_out = res;
     free(V); free(H); free(cs); free(sn); free(g); free(w); free(z); free(y);
     return 0;
+}
+
+/* The correction equation of one refinement step, A d = r, solved with a
+ * Krylov basis of at most kmem + 1 vectors: restarted GMRES cycles of kmem
+ * steps on (M A) e = M r_c, r_0 = r, r_c = r - A d_c in u_r (ur_dd: Dot2)
+ * rounded to u (format uw), d_{c+1} = d_c + e_c in fp64 (e_c stored in u).
+ * Cycle 0 stops by the tau test (|g| <= tau ||M r||_2, beta_0 = that norm);
+ * every later cycle stops when |g| <= tau beta_0, the same level; cycles end
+ * when one stops before its kmem steps, meets the level, breaks down, or when
+ * they have taken kmax steps in all (at most ceil(kmax / kmem) cycles).
+ * Returns the steps taken; *cycles = cycles run. */
+static int gmres_restarted(const orc_system_t* S, const double* r, int ug, int up, double tau, int kmax, int kmem,
+                           int uw, int ur_dd, double* d, double* relres, int* cycles) {
+    const int n = S->n;
+    double* rc = (double*)malloc(sizeof(double) * (size_t)n);
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int t = 0; t < n; ++t) d[t] = 0.0;
+    int steps = 0, c = 0;
+    double beta0 = 0.0, lvl = 0.0, res = 0.0;
+    while (steps < kmax) {
+        const double* rin = r;
+        if (c > 0) {
+            if (ur_dd) orc_residual_dd(n, S->arp, S->aci, S->av, d, r, rc);
+            else orc_residual_fp64(n, S->arp, S->aci, S->av, d, r, rc);
+            for (int t = 0; t < n; ++t) rc[t] = rf(rc[t], uw);
+            rin = rc;
+        }
+        int k = 0;
+        double beta = 0.0;
+        orc_gmres_target(S, rin, ug, up, tau, c == 0 ? 0.0 : lvl, kmem, e, &k, NULL, &beta, &res);
+        if (c == 0) {
+            beta0 = beta;
+            lvl = tau * beta0;
+        }
+        for (int t = 0; t < n; ++t) d[t] = d[t] + rf(e[t], uw);
+        steps += k;
+        ++c;
+        if (k < kmem || res <= lvl || !(beta > 0.0)) break;
+    }
+    if (relres) *relres = beta0 > 0.0 ? res / beta0 : 0.0;
+    if (cycles) *cycles = c;
+    free(rc); free(e);
+    return steps;
 }
 
 static double vnorm_inf(int n, const double* v) {
@@ -887,6 +938,14 @@ int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
                  int ug, int up, double tau, int kmax, int imax, double u_work,
                  int uw, int ur_dd, int uf,
                  int x0_given, double* x, int* its, double* nbe, double* dx, int* stop) {
+    return orc_gmres_ir_m(S, muf, b, ug, up, tau, kmax, 0, imax, u_work, uw, ur_dd, uf, x0_given, x, its, nbe, dx,
+                          stop, NULL);
+}
+
+int orc_gmres_ir_m(const orc_system_t* S, const double* muf, const double* b,
+                   int ug, int up, double tau, int kmax, int kmem, int imax, double u_work,
+                   int uw, int ur_dd, int uf,
+                   int x0_given, double* x, int* its, double* nbe, double* dx, int* stop, int* cycles) {
     int n = S->n;
     double* r = (double*)malloc(sizeof(double) * (size_t)n);
     double* d = (double*)malloc(sizeof(double) * (size_t)n);
@@ -910,7 +969,12 @@ int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
         nbe[i] = e;
         if (e <= u_work) { *stop = 1; its[i] = 0; dx[i] = 0.0; break; }
         int k = 0;
-        orc_gmres(S, r, ug, up, tau, kmax, d, &k, NULL);
+        if (kmem > 0 && kmem < kmax) {
+            k = gmres_restarted(S, r, ug, up, tau, kmax, kmem, uw, ur_dd, d, NULL, cycles ? cycles + i : NULL);
+        } else {
+            orc_gmres(S, r, ug, up, tau, kmax, d, &k, NULL);
+            if (cycles) cycles[i] = 1;
+        }
         its[i] = k;
         /* x = x + d in u, the correction first stored in u */
         for (int t = 0; t < n; ++t) {

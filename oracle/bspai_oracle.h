@@ -150,6 +150,10 @@ typedef struct {
 void orc_gmres_time_steps(double* out);
 int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau, int kmax,
               double* d, int* iters, double* relres);
+/* orc_gmres stopping at |g_{j+1}| <= target instead of the tau test when
+ * target > 0; also returns beta = ||M r||_2 (in u_g) and the last |g|. */
+int orc_gmres_target(const orc_system_t* S, const double* r, int ug, int up, double tau, double target, int kmax,
+                     double* d, int* iters, double* relres, double* beta_out, double* res_out);
 
 /* BSPAI-GMRES-IR driver (Alg 3.1 after the SPAI build).
  *   x0 = M b with the unbucketed M (values muf, arithmetic in u_f = format uf:
@@ -165,6 +169,15 @@ int orc_gmres(const orc_system_t* S, const double* r, int ug, int up, double tau
 int orc_gmres_ir(const orc_system_t* S, const double* muf, const double* b,
                  int ug, int up, double tau, int kmax, int imax, double u_work,
                  int uw, int ur_dd, int uf, int x0_given, double* x, int* its, double* nbe, double* dx, int* stop);
+/* The same driver with the Krylov basis capped at kmem + 1 vectors (kmem > 0
+ * and < kmax): each refinement step solves its correction equation by
+ * restarted GMRES cycles of kmem steps (see gmres_restarted: later cycles
+ * start from r - A d in u_r and stop at the first cycle's tau level), its[i]
+ * counting the steps of all cycles and cycles[i] (may be NULL) the cycles. */
+int orc_gmres_ir_m(const orc_system_t* S, const double* muf, const double* b,
+                   int ug, int up, double tau, int kmax, int kmem, int imax, double u_work,
+                   int uw, int ur_dd, int uf,
+                   int x0_given, double* x, int* its, double* nbe, double* dx, int* stop, int* cycles);
 
 #ifdef __cplusplus
 }

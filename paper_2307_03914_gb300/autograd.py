@@ -30,18 +30,33 @@ class SolverSettings:
     # right-hand sides solved at the same time, each on its own CUDA stream with
     # its cooperative GMRES kernels capped at (SM count / concurrent) blocks
     concurrent: int = 16
+    # device bytes the Krylov basis of one solve may take (bspai_opts_t
+    # basis_bytes_max); None: half of the device's free memory shared among the
+    # concurrent solves.  Where kmax + 1 vectors do not fit, each refinement step
+    # runs restarted GMRES cycles that rebuild a smaller basis instead of storing
+    # the whole one.
+    basis_bytes_max: int | None = None
+
+
+def _basis_cap(settings: SolverSettings, device, k: int) -> int:
+    if settings.basis_bytes_max is not None:
+        return int(settings.basis_bytes_max)
+    free, _ = torch.cuda.mem_get_info(device)
+    return max(1, free // (2 * k))
 
 
 def _solve_rhs(Ah, rhs, BM, M, out, settings: SolverSettings, what: str):
     """out[r] = A^-1 rhs[r] by BSPAI-GMRES-IR for every row r, several at once."""
     nr = rhs.shape[0]
     k = max(1, min(nr, settings.concurrent))
+    cap = _basis_cap(settings, rhs.device, k)
     if k == 1:
-        infos = [B.gmres_ir_solve(Ah, rhs[r], BM, M, out[r], u_g=settings.u_g, u_p=settings.u_p, tol=settings.tol)
-                 for r in range(nr)]
+        o = B.opts(tau=settings.tol, basis_bytes_max=cap)
+        infos = [B.gmres_ir_solve(Ah, rhs[r], BM, M, out[r], u_g=settings.u_g, u_p=settings.u_p, tol=settings.tol,
+                                  o=o) for r in range(nr)]
     else:
         sms = torch.cuda.get_device_properties(rhs.device).multi_processor_count
-        o = B.opts(tau=settings.tol, max_blocks=max(1, sms // k))
+        o = B.opts(tau=settings.tol, max_blocks=max(1, sms // k), basis_bytes_max=cap)
         main = torch.cuda.current_stream()
         streams = queue.Queue()
         for _ in range(k):

@@ -36,6 +36,7 @@ struct GmresState {
     int kmax;
     double beta;  // ||M r||_2 (in u_g)
     double tau;
+    double target;  // > 0: stop at |g| <= target instead of the tau test (restarted cycles)
     double res;   // |g_k|
     double hlast;
     GridBar bar;
@@ -62,13 +63,14 @@ struct Ar<double> {
     static __device__ __forceinline__ double from(double a) { return a; }
 };
 
-__global__ void k_state_init(GmresState* st, int kmax, double tau) {
+__global__ void k_state_init(GmresState* st, int kmax, double tau, double target) {
     st->j = 0;
     st->done = 0;
     st->status = BSPAI_OK;
     st->kmax = kmax;
     st->beta = 0.0;
     st->tau = tau;
+    st->target = target;
     st->res = 0.0;
     st->hlast = 0.0;
     st->bar.count = 0;
@@ -169,7 +171,8 @@ __device__ void givens_finish(int j, int kmax, double hn, double carry, double* 
     st->hlast = hn;
     st->j = k;
     if (!fin) st->status = BSPAI_NONFINITE;
-    st->done = (res <= __dmul_rn(st->tau, st->beta)) || hn == 0.0 || k >= kmax || !fin;
+    const double lvl = st->target > 0.0 ? st->target : __dmul_rn(st->tau, st->beta);
+    st->done = (res <= lvl) || hn == 0.0 || k >= kmax || !fin;
 }
 
 // rotation i of the earlier steps applied to the pair (carry, h_{i+1,j}): the
@@ -828,6 +831,7 @@ struct GmresWork {
         dfree(V, s); dfree(w, s); dfree(part, s); dfree(tags, s); dfree(st, s); dfree(H, s); dfree(cs, s);
         dfree(sn, s); dfree(g, s); dfree(y, s); dfree(norms, s);
         V = w = part = nullptr;
+        tags = nullptr;
         st = nullptr;
         H = cs = sn = g = y = norms = nullptr;
     }
@@ -930,7 +934,7 @@ struct GmresResult {
 // One GMRES solve of (M A) d = M r.  x != null: x += d; dout != null: d out.
 template <typename T>
 static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* BM, const double* r, double tau,
-                     double* x, double* dout, GmresResult& out) {
+                     double* x, double* dout, GmresResult& out, double target = 0.0) {
     cudaStream_t s = W.s;
     const int n = W.n;
     const int tprec = W.ug;  // T matches u_g
@@ -942,7 +946,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
     T* part = reinterpret_cast<T*>(W.part);
     {
         ProfScope ps(BSPAI_K_OTHER, s);
-        k_state_init<<<1, 1, 0, s>>>(W.st, W.kmax, tau);
+        k_state_init<<<1, 1, 0, s>>>(W.st, W.kmax, tau, target);
         note_launch();
         CUDA_LAUNCH_CHECK();
         CUDA_TRY(cudaMemsetAsync(W.norms, 0, 4 * sizeof(double), s));
@@ -1047,6 +1051,40 @@ __global__ void k_round_f32(int n, double* __restrict__ x) {
     if (i < n) x[i] = (double)__double2float_rn(x[i]);
 }
 
+// d += e in fp64 (e, a restarted cycle's correction, already stored in u); first: d = 0 + e
+__global__ void k_dacc_add(int n, double* __restrict__ d, const double* __restrict__ e, int first) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = __dadd_rn(first ? 0.0 : d[i], e[i]);
+}
+
+// x = fl_u(x + fl_u(d)) for a correction summed over restarted cycles, with
+// norms[0] = max |fl_u(d)|, norms[1] = max |x| (as k_gmres_update)
+__global__ void __launch_bounds__(256) k_apply_d(int n, double* __restrict__ x, const double* __restrict__ d,
+                                                 double* __restrict__ norms, int u32) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double dabs = 0.0, xabs = 0.0;
+    if (r < n) {
+        double dv = d[r];
+        if (u32) dv = (double)__double2float_rn(dv);
+        double xn = __dadd_rn(x[r], dv);
+        if (u32) xn = (double)__double2float_rn(xn);
+        x[r] = xn;
+        dabs = fabs(dv);
+        xabs = fabs(xn);
+        if (!(dabs <= 1.7976931348623157e308)) dabs = __longlong_as_double(0x7ff0000000000000LL);
+        if (!(xabs <= 1.7976931348623157e308)) xabs = __longlong_as_double(0x7ff0000000000000LL);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dabs = fmax(dabs, __shfl_xor_sync(0xffffffffu, dabs, o));
+        xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(norms, dabs);
+        atomic_max_nonneg(norms + 1, xabs);
+    }
+}
+
 static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, const bspai_bucketed* BM,
                     const bspai_spai* M, int u, int u_r, int u_g, int u_p, double tol, const bspai_opts_t* opts,
                     double* x, cudaStream_t s, bspai_solve_info_t* info) {
@@ -1070,19 +1108,48 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
     }
     double* r = nullptr;
     double* nrm = nullptr;
+    double *dacc = nullptr, *ecyc = nullptr, *rcyc = nullptr;  // restarted cycles only
     GmresWork W;
     int rc = BSPAI_OK;
     auto finish = [&](int code) {
         dfree(r, s);
         dfree(nrm, s);
+        dfree(dacc, s);
+        dfree(ecyc, s);
+        dfree(rcyc, s);
         W.release();
         inf.status = code;
         if (info) *info = inf;
         return code;
     };
+    // the Krylov basis: kmax + 1 vectors, or fewer (restarted cycles) when the caller's
+    // byte cap or the device's free memory asks
+    int km = kmax;
+    if (o.basis_bytes_max > 0) {
+        const int64_t vec = (int64_t)(u_g == BSPAI_FP64 ? 8 : 4) * (ceil_div(n, 64) * 64);
+        const int64_t fit = o.basis_bytes_max / vec - 1;
+        if (fit < 1)
+            return finish(set_error(BSPAI_ERR_INVALID,
+                                    "gmres_ir_solve: basis_bytes_max holds fewer than two Krylov vectors of order %d",
+                                    n));
+        if (fit < km) km = (int)fit;
+    }
     if ((rc = dalloc_t(&r, (size_t)n, s))) return finish(rc);
     if ((rc = dalloc_t(&nrm, 4, s))) return finish(rc);
-    if ((rc = W.alloc(n, kmax, u_g, u_p, o.barrier_timeout_s, o.max_blocks, s))) return finish(rc);
+    rc = W.alloc(n, km, u_g, u_p, o.barrier_timeout_s, o.max_blocks, s);
+    while (rc == BSPAI_ERR_NOMEM && km > 8) {
+        W.release();
+        (void)cudaGetLastError();  // the failed allocation's error is not the next launch's
+        km = km / 2 > 8 ? km / 2 : 8;
+        rc = W.alloc(n, km, u_g, u_p, o.barrier_timeout_s, o.max_blocks, s);
+    }
+    if (rc) return finish(rc);
+    if (km < kmax) {
+        if ((rc = dalloc_t(&dacc, (size_t)n, s))) return finish(rc);
+        if ((rc = dalloc_t(&ecyc, (size_t)n, s))) return finish(rc);
+        if ((rc = dalloc_t(&rcyc, (size_t)n, s))) return finish(rc);
+    }
+    inf.kmem = km;
     W.BA = BA;
     W.u32 = u == BSPAI_FP32;
     // ||A||_inf, ||b||_inf
@@ -1129,9 +1196,58 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
             break;
         }
         GmresResult gr;
-        rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, tau, x, nullptr, gr)
-                               : gmres_run<float>(W, A, BM, r, tau, x, nullptr, gr);
-        if (rc) return finish(rc);
+        int cycles = 1;
+        if (km >= kmax) {
+            rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, r, tau, x, nullptr, gr)
+                                   : gmres_run<float>(W, A, BM, r, tau, x, nullptr, gr);
+            if (rc) return finish(rc);
+        } else {
+            // restarted cycles of km steps on the correction equation A d = r: cycle c > 0
+            // starts from r - A d (u_r, stored in u) and stops at cycle 0's level tau beta_0
+            int steps = 0;
+            double lvl = 0.0, beta0 = 0.0;
+            GmresResult gc;
+            cycles = 0;
+            while (steps < kmax) {
+                const double* rin = r;
+                if (cycles > 0) {
+                    e = cudaMemsetAsync(nrm + 2, 0, 2 * sizeof(double), s);
+                    if (e) return finish(cuda_error(e, "memset", __FILE__, __LINE__));
+                    if ((rc = launch_residual_prec(A, dacc, r, rcyc, nrm + 2, u_r, u, s))) return finish(rc);
+                    rin = rcyc;
+                }
+                rc = u_g == BSPAI_FP64 ? gmres_run<double>(W, A, BM, rin, tau, nullptr, ecyc, gc, lvl)
+                                       : gmres_run<float>(W, A, BM, rin, tau, nullptr, ecyc, gc, lvl);
+                if (rc) return finish(rc);
+                if (cycles == 0) {
+                    beta0 = gc.beta;
+                    lvl = tau * beta0;
+                }
+                k_dacc_add<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, dacc, ecyc, cycles == 0);
+                note_launch();
+                steps += gc.k;
+                ++cycles;
+                if (gc.status == BSPAI_NONFINITE || gc.k < km || gc.res <= lvl || !(gc.beta > 0.0)) break;
+            }
+            {
+                ProfScope ps(BSPAI_K_UPDATE, s);
+                e = cudaMemsetAsync(W.norms, 0, 2 * sizeof(double), s);
+                if (e) return finish(cuda_error(e, "memset", __FILE__, __LINE__));
+                k_apply_d<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, x, dacc, W.norms, W.u32);
+                note_launch();
+            }
+            double hn2[2];
+            e = cudaMemcpyAsync(hn2, W.norms, sizeof hn2, cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            if (e) return finish(cuda_error(e, "restarted GMRES update", __FILE__, __LINE__));
+            gr.k = steps;
+            gr.status = gc.status;
+            gr.beta = beta0;
+            gr.res = gc.res;
+            gr.dmax = hn2[0];
+            gr.xmax = hn2[1];
+        }
+        inf.gmres_cycles[i] = cycles;
         inf.gmres_iters[i] = gr.k;
         inf.total_iters += gr.k;
         inf.relres[i] = gr.beta > 0 ? gr.res / gr.beta : 0.0;

@@ -202,6 +202,7 @@ void bspai_opts_default(bspai_opts_t* o) {
     o->u_stop = 0.0;
     o->stagnation = 0.0;
     o->barrier_timeout_s = 0.0;
+    o->basis_bytes_max = 0;
 }
 
 int bspai_profile_enable(int on) {

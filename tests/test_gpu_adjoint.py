@@ -119,6 +119,42 @@ def test_adjoint_matches_oracle_and_finite_differences(B, name, grid):
         assert abs(fd - gA[p]) <= 1e-5 * max(abs(fd), 1e-3), (p, fd, gA[p])
 
 
+def test_adjoint_with_a_capped_krylov_basis(B):
+    """Krylov bases recomputed instead of stored: with the basis capped at 12
+    vectors, the forward and adjoint solves restart their GMRES cycles, and the
+    gradients still match the oracle's adjoint (solved with the same cap) and the
+    uncapped GPU gradients to 1e-10."""
+    from paper_2307_03914_gb300 import autograd as AG
+
+    wl, A, P, bs, xt, rp, col, Pd = _problem(B, "convdiff2d", 21, nrhs=2, seed=4)
+    kmem = 11
+    cap = (kmem + 1) * 4 * (-(-A.n // 64) * 64)  # u_g = fp32 vectors, rows rounded up to 64
+
+    def grads(basis):
+        st = AG.SolverSettings(spai_eps=wl["spai_eps"], bucket_eps=2.0 ** -16, precs=wl["precs"],
+                               basis_bytes_max=basis)
+        aval = dev(A.val).requires_grad_(True)
+        b = dev(bs).requires_grad_(True)
+        x = AG.solve(aval, b, rp, col, Pd, st)
+        loss = ((x - dev(xt)) ** 2).sum()
+        loss.backward()
+        return host(b.grad), host(aval.grad), x.grad_fn
+
+    gb, gA, fn = grads(cap)
+    assert all(i["kmem"] == kmem for i in fn.adjoint_infos + fn.infos)
+    assert max(max(i["gmres_cycles"]) for i in fn.adjoint_infos) > 1
+    gb0, gA0, _ = grads(None)
+    assert np.abs(gb - gb0).max() <= 1e-10 * np.abs(gb0).max()
+    assert np.abs(gA - gA0).max() <= 1e-10 * np.abs(gA0).max()
+    muf = O.round_to(O.spai(A, P, wl["spai_eps"])["mval"], "fp32")
+    S = O.System(A, P.row_ptr, P.col, muf, np.zeros(P.nnz, np.int8), ["fp64"])
+    for r in range(2):
+        xo = O.gmres_ir(S, muf, bs[r], "fp64", "fp64", 1e-12, 500, 10)["x"]
+        adj = O.adjoint(A, P, muf, xo, 2 * (xo - xt[r]), kmem=kmem)
+        assert max(adj["info"]["cycles"]) > 1
+        assert np.abs(gb[r] - adj["db"]).max() <= 1e-10 * np.abs(adj["db"]).max()
+
+
 def test_adjoint_full_size_16_rhs(B):
     """2D diffusion 256^2 with a log-normal coefficient field, 16 right-hand
     sides: every adjoint solution satisfies A^T lambda = g to the level of u,
