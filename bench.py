@@ -406,10 +406,12 @@ def main():
     xt = torch.from_numpy(wl["x_true"]).cuda()
     stream = torch.cuda.current_stream()
 
-    def step(x, eps=args.bucket_eps, pl=precs, ug="fp32", up="fp32", tau=wl["tau"], A_in=Ad, P_in=Pd, b_in=bd):
+    def step(x, eps=args.bucket_eps, pl=precs, ug="fp32", up="fp32", tau=wl["tau"], A_in=Ad, P_in=Pd, b_in=bd,
+             basis=0):
         M, _ = B.bspai_build(A_in, P_in, wl["spai_eps"])
         BM, binfo = B.bspai_bucket(M, eps, pl)
-        info = B.gmres_ir_solve(A_in, b_in, BM, M, x, u_g=ug, u_p=up, tol=tau, o=B.opts(tau=tau, kmax=args.kmax))
+        info = B.gmres_ir_solve(A_in, b_in, BM, M, x, u_g=ug, u_p=up, tol=tau,
+                                o=B.opts(tau=tau, kmax=args.kmax, basis_bytes_max=basis))
         M.free()
         BM.free()
         return info, binfo
@@ -558,6 +560,34 @@ def main():
             "table3_eps_2^-37": leg("Table 3 buckets {fp64, fp32, fp16, drop}, eps = 2^-37", 2.0 ** -37,
                                     ["fp64", "fp32", "fp16", "drop"]),
         }
+
+    # ---------------- the headline solve with its Krylov basis capped (restarted cycles inside each
+    # refinement step, bspai_opts_t.basis_bytes_max): time and GMRES steps against the device memory saved
+    if not args.no_comparator:
+        vec = 4 * (-(-n // 64) * 64)
+        kfull = args.kmax if args.kmax > 0 else min(n, 1000)
+
+        def capped(m):
+            x = torch.empty(n, dtype=torch.float64, device="cuda")
+            step(x, basis=(m + 1) * vec)
+            barrier()
+            c0_ = torch.cuda.Event(enable_timing=True)
+            c1_ = torch.cuda.Event(enable_timing=True)
+            c0_.record(stream)
+            cinf, _ = step(x, basis=(m + 1) * vec)
+            c1_.record(stream)
+            barrier()
+            cms_ = c0_.elapsed_time(c1_)
+            cfe_ = float(((x - xt).abs().max() / xt.abs().max()).item())
+            good = cfe_ <= FE_TARGET and cinf["status"] == 0
+            return {"basis_vectors": m + 1, "basis_bytes": (m + 1) * vec, "solves_per_s":
+                    (1.0 if good else 0.0) / (cms_ / 1000.0), "ms_per_solve": cms_,
+                    "gmres_iters": cinf["gmres_iters"], "gmres_cycles": cinf["gmres_cycles"], "fwd_err": cfe_}
+
+        out["capped_basis"] = {"what": "the headline solve with the Krylov basis capped at m + 1 vectors of u_g = "
+                                       "fp32 (restarted GMRES cycles of m steps per refinement step)",
+                               "uncapped_basis_bytes": (kfull + 1) * vec,
+                               "m64": capped(64), "m32": capped(32)}
 
     # ---------------- cold-cache product times: L2 flushed (a 256 MiB write, twice L2) before each of 50
     # launches after 5 warm-ups, median; M w as inside GMRES (fp32 in and out), A v in u_p
