@@ -289,6 +289,19 @@ def job_rate(ms, ok, world, dist, device):
 
 
 # ------------------------------------------------------------------ extension legs
+def batch_roofline(info, prof):
+    """HBM roofline of the batched GMRES launches: the library's algorithmic bytes of
+    those launches (gmres_bytes) over their kernel-class event time."""
+    t_ms, nl = prof["mgs"]
+    if t_ms <= 0:
+        return None
+    hbm, src = peaks()
+    ach = info["gmres_bytes"] / (t_ms / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "kernel": "k_gmres_batch / k_gmres_team", "launches": nl, "ms_total": t_ms,
+            "algorithmic_bytes": info["gmres_bytes"], "peak_source": src}
+
+
 def measure_batch(B, W, world, dist, barrier):
     """SPAI build + per-system bucketing + batched GMRES-IR of the whole batch,
     timed with CUDA events after one warm-up run (which also autotunes)."""
@@ -309,8 +322,13 @@ def measure_batch(B, W, world, dist, barrier):
         info = B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, tol=bw["tau"])
         return info, kinfo
 
-    run()
+    # warm-up (autotunes), with the library's kernel-class events: the GMRES launches' time
+    B.profile_enable(True)
+    B.profile_read(reset=True)
+    winfo, _ = run()
     barrier()
+    prof = B.profile_read(reset=True)
+    B.profile_enable(False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
     e0.record(stream)
@@ -331,10 +349,13 @@ def measure_batch(B, W, world, dist, barrier):
             "pairs": info["pairs"] * world, "solves_per_s": rate, "ms": ms, "ok": ok,
             "worst_fwd_err": worst, "total_gmres_iters": info["total_iters"], "max_iters": info["max_iters"],
             "ir_launches": info["ir_launches"], "cta_threads": info["block_threads"], "grid": info["grid"],
-            "schedule": {k: info[k] for k in ("block_threads", "mgs_rows", "z_shared_rows", "m_schedule")},
+            "schedule": {k: info[k] for k in ("block_threads", "mgs_rows", "z_shared_rows", "m_schedule",
+                                              "team_rows")},
             "tuning": {"candidates_ms": [[t["block_threads"], t["mgs_rows"], t["z_shared_rows"], t["m_schedule"],
-                                          round(t["ms"], 2)] for t in B.batch_tune_table()],
-                       "fields": "block_threads, mgs_rows, z_shared_rows, m_schedule, ms of the sample run (largest pairs, 4 per SM, 32 steps)"},
+                                          t["team_rows"], round(t["ms"], 2)] for t in B.batch_tune_table()],
+                       "fields": "block_threads, mgs_rows, z_shared_rows, m_schedule, team_rows, ms of the sample "
+                                 "run (largest pairs, 4 per SM, 32 steps)"},
+            "roofline_gmres": batch_roofline(winfo, prof),
             "kmax": info["kmax"], "rows": n, "nnz_A": bw["A"].nnz, "storage_pct": kinfo["storage_pct"]}
 
 

@@ -480,8 +480,14 @@ typedef struct {
     int32_t mgs_rows;       /* the schedule's MGS load tile (bspai_batch_schedule_t) */
     int32_t z_shared_rows;  /* the schedule's z-in-shared-memory limit */
     int32_t m_schedule;     /* the schedule's bucket order */
+    int32_t team_rows;      /* the schedule's team mode (0: one CTA per pair) */
     int32_t tuned_candidates; /* schedules timed by this call (0: cached or forced) */
     float tune_ms;          /* their summed GPU time */
+    int64_t gmres_bytes;    /* algorithmic bytes of the refinement steps' GMRES launches: per
+                               Arnoldi step of a pair j + 2 of its vectors (the MGS reads and
+                               the new vector), and its two products at the batch's average
+                               bytes per row (A in u_p, bucketed M, int32 columns) plus four
+                               vectors */
 } bspai_batch_info_t;
 
 /* A schedule of the batched GMRES launch.  For a given block_threads every
@@ -500,12 +506,23 @@ typedef struct {
  *   m_schedule     the bucket schedule of the M products: 0 row-fused (each
  *                  thread takes two rows at a time through every bucket), 1
  *                  bucket-major (one sweep over the pair's rows per bucket,
- *                  the partial sums carried in fp64 between sweeps). */
+ *                  the partial sums carried in fp64 between sweeps).
+ *   team_rows      0: one CTA per pair (the four fields above).  Otherwise
+ *                  (u_g = FP32 only; a multiple of 1024, at most 8192) team
+ *                  mode: a pair of n_s rows runs on a team of
+ *                  ceil(n_s / team_rows) 512-thread CTAs (at most 32) of a
+ *                  cooperative launch, one launch per run of equal team size,
+ *                  each CTA holding its rows of z and of the basis vectors of
+ *                  the current MGS pass in registers; the dot products sum a
+ *                  thread's rows, the CTA's threads, then the team's CTAs in
+ *                  rank order (other bits than the one-CTA schedules, the same
+ *                  in every run).  The other fields are then ignored. */
 typedef struct {
     int32_t block_threads;
     int32_t mgs_rows;
     int32_t z_shared_rows;
     int32_t m_schedule;
+    int32_t team_rows;
 } bspai_batch_schedule_t;
 
 /* Fixes the schedule of later gmres_ir_solve_batched calls made by the calling
@@ -531,13 +548,18 @@ int bspai_batch_tune_table(bspai_batch_schedule_t* sched, float* ms, int32_t cap
  * gmres_ir_solve, and its own left-preconditioned MGS-GMRES (vectors in u_g,
  * A v in u_p, bucketed M v, Givens in fp64).  Each refinement step of the
  * batch is one persistent launch in which a CTA takes pairs, largest systems
- * first, and runs each GMRES with CTA barriers only; the schedule of that
- * launch (bspai_batch_schedule_t) is chosen by timing candidates on a sample
- * run (the largest pairs, four per SM, 32 Arnoldi steps) in a staged search -- CTA size, then the MGS tile, then z
- * in shared memory, then the bucket schedule -- and cached per shape.  The operations of
- * one refinement step (residuals, tests, the GMRES launch, tests) are captured
- * once into a CUDA graph and replayed for every step (launched directly while
- * kernel-class profiling is on).  kmax defaults to
+ * first, and runs each GMRES with CTA barriers only -- or, in team mode, one
+ * cooperative launch per run of pairs of equal team size, teams of CTAs taking
+ * pairs.  The schedule (bspai_batch_schedule_t) is chosen by timing
+ * candidates on a sample run (the largest pairs, four per SM, 32 Arnoldi
+ * steps) in a staged search -- CTA size, then the MGS tile, then z in shared
+ * memory, then the bucket schedule, then team mode at 8192 and 4096 rows per
+ * CTA (u_g = FP32) -- and cached per shape.  The operations of one refinement
+ * step (residuals, tests, the GMRES launches, tests) are captured once into a
+ * CUDA graph and replayed for every step (launched directly while
+ * kernel-class profiling is on, or if the capture fails).  A team exchange
+ * that waits longer than opts.barrier_timeout_s gives BSPAI_TIMEOUT.  kmax
+ * defaults to
  * min(largest system, 300).  pair_status (0 not converged, 1 nbe, 2 dx,
  * 3 stagnation, -1 non-finite) and pair_iters (device int32, nsys * nrhs,
  * pair p = rhs * nsys + system) may be NULL.  BM must come from

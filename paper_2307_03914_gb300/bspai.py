@@ -73,12 +73,13 @@ class BatchInfo(C.Structure):
                 ("ir_launches", C.c_int32), ("max_ir_steps", C.c_int32), ("max_iters", C.c_int32),
                 ("total_iters", C.c_int64), ("block_threads", C.c_int32), ("grid", C.c_int32), ("kmax", C.c_int32),
                 ("mgs_rows", C.c_int32), ("z_shared_rows", C.c_int32), ("m_schedule", C.c_int32),
-                ("tuned_candidates", C.c_int32), ("tune_ms", C.c_float)]
+                ("team_rows", C.c_int32), ("tuned_candidates", C.c_int32), ("tune_ms", C.c_float),
+                ("gmres_bytes", C.c_int64)]
 
 
 class BatchSchedule(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("mgs_rows", C.c_int32), ("z_shared_rows", C.c_int32),
-                ("m_schedule", C.c_int32)]
+                ("m_schedule", C.c_int32), ("team_rows", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -544,13 +545,13 @@ def gmres_ir_solve_hb(Ah: AHandle, BA: BMHandle, b, BM: BMHandle, M: MHandle | N
 
 
 def batch_schedule_force(block_threads: int | None = None, mgs_rows: int = 0, z_shared_rows: int = 0,
-                         m_schedule: int = 0) -> None:
+                         m_schedule: int = 0, team_rows: int = 0) -> None:
     """Fixes the schedule of this thread's later batched solves (block_threads
     None: back to the autotuner); see bspai_batch_schedule_t."""
     if block_threads is None:
         _check(_lib.bspai_batch_schedule_force(None))
         return
-    sc = BatchSchedule(int(block_threads), int(mgs_rows), int(z_shared_rows), int(m_schedule))
+    sc = BatchSchedule(int(block_threads), int(mgs_rows), int(z_shared_rows), int(m_schedule), int(team_rows))
     _check(_lib.bspai_batch_schedule_force(C.byref(sc)))
 
 
@@ -565,7 +566,8 @@ def batch_tune_table() -> list[dict]:
     ms = (C.c_float * max(n, 1))()
     _check(_lib.bspai_batch_tune_table(sc, ms, n, C.byref(cnt)))
     return [dict(block_threads=sc[i].block_threads, mgs_rows=sc[i].mgs_rows, z_shared_rows=sc[i].z_shared_rows,
-                 m_schedule=sc[i].m_schedule, ms=float(ms[i])) for i in range(min(n, cnt.value))]
+                 m_schedule=sc[i].m_schedule, team_rows=sc[i].team_rows, ms=float(ms[i]))
+            for i in range(min(n, cnt.value))]
 
 
 def gmres_ir_solve_batched(Ah: AHandle, row_off, nrhs: int, B, BM: BMHandle, M: MHandle | None, X, u_g="fp32",

@@ -30,6 +30,7 @@
 
 #include "common.cuh"
 #include "spmv_row.cuh"
+#include "tags.cuh"
 
 namespace bspai {
 
@@ -216,7 +217,8 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
                                                       double* Hws, double* Sws, int kmax, double tau, int zcap,
                                                       int32_t* __restrict__ iters,
                                                       int32_t* __restrict__ steps, double* __restrict__ relres,
-                                                      double* __restrict__ dmax, double* __restrict__ dxmax) {
+                                                      double* __restrict__ dmax, double* __restrict__ dxmax,
+                                                      unsigned long long* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     T* const s_z = reinterpret_cast<T*>(s_dyn);
     __shared__ T s_w[33];
@@ -317,6 +319,10 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
                     }
                 }
                 __syncthreads();
+                if (tid == 0 && work) {  // rows read by the j + 2 passes, rows of the step's products
+                    atomicAdd(work, (unsigned long long)(j + 2) * (unsigned long long)ns);
+                    atomicAdd(work + 1, (unsigned long long)ns);
+                }
                 k = j + 1;
                 res = s_res;
                 if (s_done) break;
@@ -354,6 +360,405 @@ __global__ void __launch_bounds__(512, 1) k_gmres_batch(const __grid_constant__ 
             relres[pair] = beta > T(0) ? res / (double)beta : 0.0;
             dmax[pair] = fin ? dm : __longlong_as_double(0x7ff0000000000000LL);
             dxmax[pair] = xm;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ teams
+// Team mode (u_g = fp32): a pair of n_s rows runs on a team of
+// G = ceil(n_s / team_rows) CTAs of one cooperative launch, each CTA owning a
+// contiguous chunk of the pair's rows.  As in the single-system on-chip MGS
+// kernel, z and the basis rows of the current and next pass stay in registers
+// (row pairs, packed two-lane arithmetic), so an MGS pass reads each basis row
+// once; the j + 2 reductions of an Arnoldi step, and the barriers between the
+// products (A v_j reads every rank's rows of v_j, M w every rank's rows of w),
+// are tagged-slot exchanges among the team's CTAs with bounded waits.  Data
+// another CTA of the launch wrote is read from L2 (ld.global.cg), after a
+// release/acquire pair of fences around the exchange.  The dot products sum a
+// thread's rows, then the CTA in a fixed tree, then the team's CTAs in rank
+// order: the same in every CTA and every run, but another order than the
+// one-CTA schedules (so other bits, within the same parity bars).
+constexpr int kTeamBD = 512;   // threads of a team CTA
+constexpr int kTeamP = 8;      // row pairs per thread: at most 8,192 rows of a pair per CTA
+                               // (16 pairs, as the single-system kernel holds, spill registers here)
+constexpr int kTeamMaxG = 32;  // CTAs of one team (one polling lane each)
+
+struct TeamArgs {
+    BMDev Av, Mv;
+    const int32_t* row_off;
+    int nsys, n;
+    const int32_t* order;  // this launch's pairs (a run of the size-sorted order)
+    int npairs;
+    int* queue;
+    const int32_t* status;
+    const double* R;
+    double* X;
+    float* V;  // per team: ldv x (kmax + 1)
+    float* W;  // per team: ldv (A v)
+    float* Z;  // per team: ldv (s = M r, then M w)
+    int64_t ldv;
+    double* H;  // per team: (kmax + 1) x kmax
+    double* S;  // per team: cs, sn, g, y (kmax + 2 each)
+    int kmax;
+    double tau;
+    int G;
+    unsigned long long* tags;  // per team: 2 sets x G slots x 2 words
+    GridBar* bar;              // err: a team exchange timed out
+    unsigned long long tmo;
+    int32_t *iters, *steps;
+    double *relres, *dmax, *dxmax;
+    unsigned long long* work;  // [0] rows read by MGS passes, [1] rows of the Arnoldi steps' products
+};
+
+struct TeamSync {
+    unsigned long long* tags;
+    GridBar* bar;
+    unsigned long long tmo;
+    int G, rank;
+    unsigned seq;  // exchanges so far: the same count in every CTA of the team
+};
+
+__device__ __forceinline__ float warp_max_nn(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max_nn(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <int OP, typename T>
+__device__ __forceinline__ T warp_comb(T v) {
+    if constexpr (OP == 0) return warp_sum(v);
+    else return warp_max_nn(v);
+}
+
+// First half of a team exchange: the CTA's threads' values combined (OP 0: a
+// sum in a fixed tree; OP 1: a max of non-negative values) and published in
+// the CTA's slot.  FENCE: the CTA's earlier writes are released with it.
+template <typename T, int OP, bool FENCE>
+__device__ __forceinline__ void team_arrive(TeamSync& ts, T v, T* s_w, T* s_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_comb<OP>(v);
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    ts.seq += 1u;
+    if (w == 0) {
+        T t = lane < nw ? s_w[lane] : T(0);
+        t = warp_comb<OP>(t);
+        if (lane == 0) {
+            if (ts.G == 1) {
+                *s_tot = t;
+            } else {
+                if (FENCE) __threadfence();
+                tag_publish(t, ts.tags + (int64_t)(ts.seq & 1u) * 2 * ts.G + (int64_t)ts.rank * TagWords<T>::W,
+                            ts.seq);
+            }
+        }
+    }
+}
+
+// Second half: warp 0 polls the team's slots until all carry this exchange's
+// number (giving up after tmo ns, or once any CTA of the launch has flagged an
+// error), combines them in rank order, and every thread gets the result.
+// *s_ok = 0 after a timeout.  FENCE: the other CTAs' released writes are
+// visible to this CTA's threads after it.
+template <typename T, int OP, bool FENCE>
+__device__ __forceinline__ T team_wait(TeamSync& ts, T* s_tot, int* s_ok) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        bool ok = true;
+        if (ts.G > 1) {
+            const unsigned long long* base = ts.tags + (int64_t)(ts.seq & 1u) * 2 * ts.G;
+            T val = T(0);
+            bool have = lane >= ts.G;
+            unsigned long long t0 = 0;
+            for (int it = 0;; ++it) {
+                if (!have) have = tag_read(base + (int64_t)lane * TagWords<T>::W, ts.seq, &val);
+                if (__all_sync(0xffffffffu, have)) break;
+                int stop = 0;
+                if (lane == 0) {
+                    const unsigned long long now = globaltimer_ns();
+                    if (it == 0) t0 = now;
+                    if (now - t0 > ts.tmo) {
+                        atomicExch(&ts.bar->err, 1);
+                        stop = 1;
+                    } else if ((it & 63) == 63 && *(volatile int*)&ts.bar->err) {
+                        stop = 1;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, stop, 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+            const T t = warp_comb<OP>(val);
+            if (FENCE) __threadfence();
+            if (lane == 0) *s_tot = t;
+        }
+        if (lane == 0) *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_tot;
+}
+
+// y[lr] = (M x)_{r0 + lr} in u_g for the rows lo .. hi - 1 of one pair, two
+// rows per thread at a time (as rows_apply); CG: x is read from L2
+template <typename XT, bool CG>
+__device__ __noinline__ void team_rows(const BMDev& M, int r0, int lo, int hi, const XT* __restrict__ x, float* y) {
+    const int bd = blockDim.x;
+    int lr = lo + threadIdx.x;
+    for (; lr + bd < hi; lr += 2 * bd) {
+        double ya, yb;
+        bucketed_row2<XT, CG>(M, r0 + lr, r0 + lr + bd, x, ya, yb);
+        y[lr] = from_f64<float>(ya);
+        y[lr + bd] = from_f64<float>(yb);
+    }
+    if (lr < hi) y[lr] = from_f64<float>(bucketed_row<XT, CG>(M, r0 + lr, x));
+}
+
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// The modified Gram-Schmidt passes of Arnoldi step j for one CTA of a team (z
+// from this CTA's rows of Z, the basis rows in registers; H column j written by
+// rank 0) and v_{j+1} = z / h_{j+1,j} into the basis; returns h_{j+1,j}.
+// Out of line, so that the register arrays of the passes have the kernel's
+// whole register budget.  *s_ok = 0 after a timed-out exchange.
+template <int P>
+__device__ __noinline__ float team_mgs(float* V, int64_t ldv, const float* Z, int lo, int nb, int j, int kmax,
+                                       double* H, TeamSync& ts, float* s_wf, float* s_totf, int* s_ok) {
+    constexpr int BD = kTeamBD;
+    const int tid = threadIdx.x, rank = ts.rank;
+    const float2 zero2 = make_float2(0.0f, 0.0f);
+    // this CTA's rows: pair q = tid + s BD covers rows lo + 2q, lo + 2q + 1
+    auto ld2 = [&](const float* base, int q) -> float2 {
+        const float* p2 = base + lo + 2 * q;
+        if (2 * q + 1 < nb) return __ldcg(reinterpret_cast<const float2*>(p2));
+        return make_float2(__ldcg(p2), 0.0f);
+    };
+    float2 zr[P], vcur[P], vnext[P];
+    // modified Gram-Schmidt: pass i takes z -= h_{i-1} v_{i-1} and dots z with v_i
+    // (the last pass forms ||z||^2), the loads of v_i issued before the wait
+    float2 acc2 = zero2;
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const int q = tid + t * BD;
+        zr[t] = zero2;
+        vcur[t] = zero2;
+        vnext[t] = zero2;
+        if (2 * q < nb) {
+            zr[t] = ld2(Z, q);
+            vcur[t] = ld2(V, q);
+            acc2 = __fadd2_rn(acc2, __fmul2_rn(vcur[t], zr[t]));
+        }
+    }
+    team_arrive<float, 0, false>(ts, __fadd_rn(acc2.x, acc2.y), s_wf, s_totf);
+    for (int i = 1; i <= j + 1; ++i) {
+        if (i <= j) {
+            const float* vi = V + (int64_t)i * ldv;
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int q = tid + t * BD;
+                if (2 * q < nb) vnext[t] = ld2(vi, q);
+            }
+        }
+        const float h = team_wait<float, 0, false>(ts, s_totf, s_ok);
+        if (!*s_ok) return 0.0f;
+        if (rank == 0 && tid == 0) H[(int64_t)j * (kmax + 1) + (i - 1)] = (double)h;
+        const float2 h2 = make_float2(h, h);
+        acc2 = zero2;
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const int q = tid + t * BD;
+            if (2 * q < nb) {
+                zr[t] = f2sub(zr[t], __fmul2_rn(h2, vcur[t]));
+                acc2 = __fadd2_rn(acc2, __fmul2_rn(i <= j ? vnext[t] : zr[t], zr[t]));
+            }
+        }
+        team_arrive<float, 0, false>(ts, __fadd_rn(acc2.x, acc2.y), s_wf, s_totf);
+#pragma unroll
+        for (int t = 0; t < P; ++t) vcur[t] = vnext[t];
+    }
+    const float hz = team_wait<float, 0, false>(ts, s_totf, s_ok);
+    if (!*s_ok) return 0.0f;
+    const float hn = __fsqrt_rn(hz);
+    const bool norm = hn > 0.0f && isfinite((double)hn);
+    float* vn = V + (int64_t)(j + 1) * ldv + lo;
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const int q = tid + t * BD;
+        if (2 * q < nb) {
+            float2 zo = zr[t];
+            if (norm) zo = make_float2(__fdiv_rn(zo.x, hn), __fdiv_rn(zo.y, hn));
+            if (2 * q + 1 < nb) *reinterpret_cast<float2*>(vn + 2 * q) = zo;
+            else vn[2 * q] = zo.x;
+        }
+    }
+    return hn;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTeamBD, 1) k_gmres_team(const __grid_constant__ TeamArgs a) {
+    constexpr int BD = kTeamBD;
+    extern __shared__ float s_y[];  // y of the pair in u_g (kmax entries)
+    __shared__ float s_wf[32];
+    __shared__ double s_wd[32];
+    __shared__ float s_totf;
+    __shared__ double s_totd;
+    __shared__ int s_ok, s_p, s_done;
+    __shared__ double s_res;
+    const int tid = threadIdx.x;
+    const int G = a.G, team = blockIdx.x / G, rank = blockIdx.x - team * G;
+    const int kmax = a.kmax;
+    const int64_t ldv = a.ldv;
+    float* V = a.V + (int64_t)team * ldv * (kmax + 1);
+    float* W = a.W + (int64_t)team * ldv;
+    float* Z = a.Z + (int64_t)team * ldv;
+    double* H = a.H + (int64_t)team * (kmax + 1) * kmax;
+    double* cs = a.S + (int64_t)team * 4 * (kmax + 2);
+    double* sn = cs + (kmax + 2);
+    double* g = sn + (kmax + 2);
+    double* y = g + (kmax + 2);
+    TeamSync ts{a.tags + (int64_t)team * 4 * G, a.bar, a.tmo, G, rank, 0u};
+    const float2 zero2 = make_float2(0.0f, 0.0f);
+    while (true) {
+        // the next pair: rank 0 takes it from the queue, the team learns it by an exchange
+        if (rank == 0 && tid == 0) s_p = atomicAdd(a.queue, 1);
+        __syncthreads();
+        team_arrive<float, 0, false>(ts, (rank == 0 && tid == 0) ? (float)s_p : 0.0f, s_wf, &s_totf);
+        const int p = (int)team_wait<float, 0, false>(ts, &s_totf, &s_ok);
+        if (!s_ok || p >= a.npairs) return;
+        const int pair = a.order[p];
+        if (a.status[pair] != 0) continue;
+        const int rhs = pair / a.nsys, sys = pair - rhs * a.nsys;
+        const int r0 = a.row_off[sys], ns = a.row_off[sys + 1] - r0;
+        const double* rr = a.R + (int64_t)rhs * a.n;
+        double* xx = a.X + (int64_t)rhs * a.n;
+        const int chunk = (int)(ceil_div(ceil_div(ns, G), 64) * 64);
+        const int lo = rank * chunk < ns ? rank * chunk : ns;
+        const int hi = lo + chunk < ns ? lo + chunk : ns;
+        const int nb = hi - lo;
+        // this CTA's rows: pair q = tid + s BD covers rows lo + 2q, lo + 2q + 1
+        auto ld2 = [&](const float* base, int q) -> float2 {
+            const float* p2 = base + lo + 2 * q;
+            if (2 * q + 1 < nb) return __ldcg(reinterpret_cast<const float2*>(p2));
+            return make_float2(__ldcg(p2), 0.0f);
+        };
+        auto st2 = [&](float* base, int q, float2 v) {
+            float* p2 = base + lo + 2 * q;
+            if (2 * q + 1 < nb) *reinterpret_cast<float2*>(p2) = v;
+            else *p2 = v.x;
+        };
+        float2 zr[P], vcur[P], vnext[P];
+        // s = M r (Alg 2.3) in u_g; beta = ||s||_2
+        team_rows<double, false>(a.Mv, r0, lo, hi, rr, Z);
+        __syncthreads();
+        float2 acc2 = zero2;
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const int q = tid + t * BD;
+            zr[t] = zero2;
+            if (2 * q < nb) {
+                zr[t] = ld2(Z, q);
+                acc2 = __fadd2_rn(acc2, __fmul2_rn(zr[t], zr[t]));
+            }
+        }
+        team_arrive<float, 0, false>(ts, __fadd_rn(acc2.x, acc2.y), s_wf, &s_totf);
+        const float beta = __fsqrt_rn(team_wait<float, 0, false>(ts, &s_totf, &s_ok));
+        if (!s_ok) return;
+        const bool fin = isfinite((double)beta);
+        int k = 0;
+        double res = (double)beta;
+        if (beta > 0.0f && fin) {
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int q = tid + t * BD;
+                if (2 * q < nb) st2(V, q, make_float2(__fdiv_rn(zr[t].x, beta), __fdiv_rn(zr[t].y, beta)));
+            }
+            if (rank == 0 && tid == 0) g[0] = (double)beta;
+            for (int j = 0; j < kmax; ++j) {
+                // barrier: v_j complete in every rank
+                __syncthreads();
+                team_arrive<float, 0, true>(ts, 0.0f, s_wf, &s_totf);
+                team_wait<float, 0, true>(ts, &s_totf, &s_ok);
+                if (!s_ok) return;
+                const float* vj = V + (int64_t)j * ldv;
+                team_rows<float, true>(a.Av, r0, lo, hi, vj - r0, W);
+                __syncthreads();
+                team_arrive<float, 0, true>(ts, 0.0f, s_wf, &s_totf);
+                team_wait<float, 0, true>(ts, &s_totf, &s_ok);
+                if (!s_ok) return;
+                team_rows<float, true>(a.Mv, r0, lo, hi, W - r0, Z);
+                __syncthreads();
+                const float hn = team_mgs<P>(V, ldv, Z, lo, nb, j, kmax, H, ts, s_wf, &s_totf, &s_ok);
+                if (!s_ok) return;
+                if (rank == 0 && tid == 0) {
+                    double rs;
+                    int dn;
+                    givens_pair(j, kmax, (double)hn, H, cs, sn, g, a.tau, (double)beta, &rs, &dn);
+                    s_res = rs;
+                    s_done = dn;
+                }
+                __syncthreads();
+                // every rank learns rank 0's stopping decision (the next barrier is the loop's)
+                team_arrive<float, 0, false>(ts, (rank == 0 && tid == 0) ? (float)s_done : 0.0f, s_wf, &s_totf);
+                const float dn = team_wait<float, 0, false>(ts, &s_totf, &s_ok);
+                if (!s_ok) return;
+                if (rank == 0 && tid == 0 && a.work) {
+                    atomicAdd(a.work, (unsigned long long)(j + 2) * (unsigned long long)ns);
+                    atomicAdd(a.work + 1, (unsigned long long)ns);
+                }
+                k = j + 1;
+                if (rank == 0) res = s_res;
+                if (dn != 0.0f) break;
+            }
+            // y = R^-1 g, column-oriented back substitution (fp64, rank 0)
+            if (rank == 0) {
+                __syncthreads();
+                for (int i = k - 1; i >= 0; --i) {
+                    const double* hc = H + (int64_t)i * (kmax + 1);
+                    if (tid == 0) y[i] = __ddiv_rn(g[i], hc[i]);
+                    __syncthreads();
+                    const double yi = y[i];
+                    for (int t = tid; t < i; t += BD) g[t] = __dsub_rn(g[t], __dmul_rn(hc[t], yi));
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+            team_arrive<float, 0, true>(ts, 0.0f, s_wf, &s_totf);
+            team_wait<float, 0, true>(ts, &s_totf, &s_ok);
+            if (!s_ok) return;
+            for (int t = tid; t < k; t += BD) s_y[t] = from_f64<float>(__ldcg(y + t));
+            __syncthreads();
+        }
+        // d = V y in u_g, x += d in fp64 (this CTA's rows)
+        double dm = 0.0, xm = 0.0;
+        for (int lr = lo + tid; lr < hi; lr += BD) {
+            float acc = 0.0f;
+            for (int jj = 0; jj < k; ++jj) acc = __fadd_rn(acc, __fmul_rn(__ldcg(V + (int64_t)jj * ldv + lr), s_y[jj]));
+            const double d = (double)acc;
+            const double xn = __dadd_rn(xx[r0 + lr], d);
+            xx[r0 + lr] = xn;
+            double ad = fabs(d), ax = fabs(xn);
+            if (!(ad <= 1.7976931348623157e308)) ad = __longlong_as_double(0x7ff0000000000000LL);
+            if (!(ax <= 1.7976931348623157e308)) ax = __longlong_as_double(0x7ff0000000000000LL);
+            dm = fmax(dm, ad);
+            xm = fmax(xm, ax);
+        }
+        team_arrive<double, 1, false>(ts, dm, s_wd, &s_totd);
+        dm = team_wait<double, 1, false>(ts, &s_totd, &s_ok);
+        if (!s_ok) return;
+        team_arrive<double, 1, false>(ts, xm, s_wd, &s_totd);
+        xm = team_wait<double, 1, false>(ts, &s_totd, &s_ok);
+        if (!s_ok) return;
+        if (rank == 0 && tid == 0) {
+            a.iters[pair] += k;
+            a.steps[pair] += 1;
+            a.relres[pair] = beta > 0.0f ? res / (double)beta : 0.0;
+            a.dmax[pair] = fin ? dm : __longlong_as_double(0x7ff0000000000000LL);
+            a.dxmax[pair] = xm;
         }
         __syncthreads();
     }
@@ -444,6 +849,7 @@ struct Sched {
     int urows = 0;    // MGS load tile (rows per thread), 0: the smaller candidate
     int zcap = 0;     // pairs of at most zcap rows keep z in shared memory
     int msched = 0;   // 0 row-fused, 1 bucket-major
+    int team = 0;     // > 0: team mode, rows of a pair per CTA of its team (u_g = fp32)
 };
 
 static std::mutex g_tune_mu;
@@ -650,6 +1056,8 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         if (sch.urows != MgsU<T>::lo && sch.urows != MgsU<T>::hi)
             return done(set_error(BSPAI_ERR_INVALID, "batch schedule: mgs_rows must be %d or %d for this u_g",
                                   MgsU<T>::lo, MgsU<T>::hi));
+        if (sch.team > 0 && sizeof(T) != 4)
+            return done(set_error(BSPAI_ERR_UNSUPPORTED, "batch schedule: team mode needs u_g = FP32"));
         if (sch.zcap < 0) sch.zcap = zlimit(sch);  // as many rows as fit
         if (sch.zcap > zfit(sch))
             return done(set_error(BSPAI_ERR_INVALID,
@@ -693,13 +1101,158 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
     if ((rc = take((void**)&Yws, sizeof(double) * (size_t)gmax_all * ldv))) return done(rc);
     if ((rc = take((void**)&Hws, sizeof(double) * (size_t)gmax_all * (kmax + 1) * kmax))) return done(rc);
     if ((rc = take((void**)&Sws, sizeof(double) * (size_t)gmax_all * 4 * (kmax + 2)))) return done(rc);
+    unsigned long long* d_work = nullptr;  // algorithmic work counters of the GMRES launches
+    if ((rc = take((void**)&d_work, 2 * sizeof(unsigned long long)))) return done(rc);
     auto launch_gmres = [&](const Sched& c, int grid, const double* Rin, double* Xout, int kcap, double tcap,
                             PairState& St, cudaStream_t st, int np) {
         batch_kernel<T>(c.urows, c.msched)<<<grid, c.bd, sizeof(T) * (size_t)c.zcap, st>>>(
             Av, Mv, row_off, nsys, n, d_order, np, d_queue, St.status, Rin, Xout, Vws, Wws, Yws, ldv, Hws, Sws,
-            kcap, tcap, c.zcap, St.iters, St.steps, St.relres, St.dmax, St.dxmax);
+            kcap, tcap, c.zcap, St.iters, St.steps, St.relres, St.dmax, St.dxmax, d_work);
         note_launch();
         return cudaGetLastError();
+    };
+    // ---- team mode (u_g = fp32): the size-sorted pairs split into runs of equal team
+    // size G = ceil(n_s / team_rows); one cooperative launch per run, largest first
+    struct TeamPhase {
+        int G, begin, count, grid;
+        int64_t ldv;
+    };
+    const int team_cands[2] = {kTeamP * 2 * kTeamBD, kTeamP * kTeamBD};  // 8,192 and 4,096 rows
+    const size_t team_smem = sizeof(float) * (size_t)(kmax + 1);
+    int occ_team = 0;
+    // every pair's rows must fit its team: at most kTeamMaxG CTAs of kTeamP * 2 * kTeamBD rows
+    const bool team_fits = nmax <= kTeamMaxG * kTeamP * 2 * kTeamBD;
+    if (t_forced && sch.team > 0 && !team_fits)
+        return done(set_error(BSPAI_ERR_UNSUPPORTED, "batch schedule: team mode holds systems of at most %d rows",
+                              kTeamMaxG * kTeamP * 2 * kTeamBD));
+    if constexpr (sizeof(T) == 4) if (team_fits) {
+        cudaError_t e0 = cudaFuncSetAttribute(k_gmres_team<kTeamP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)team_smem);
+        if (!e0) e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_team, k_gmres_team<kTeamP>, kTeamBD,
+                                                                    team_smem);
+        if (e0) return done(cuda_error(e0, "team kernel occupancy", __FILE__, __LINE__));
+    }
+    const int team_slots = sms * (occ_team > 0 ? occ_team : 1);  // co-resident CTAs of a team launch
+    auto sys_rows = [&](int pair) { return hoff[pair % nsys + 1] - hoff[pair % nsys]; };
+    auto plan_teams = [&](int tr, int np, std::vector<TeamPhase>& ph) {
+        ph.clear();
+        int b = 0;
+        while (b < np) {
+            auto gof = [&](int pr) {
+                const int gg = (sys_rows(pr) + tr - 1) / tr;
+                return gg < 1 ? 1 : (gg > kTeamMaxG ? kTeamMaxG : gg);
+            };
+            const int G = gof(hord[b]);
+            int e = b;
+            int nsmax = 0;
+            while (e < np && gof(hord[e]) == G) {
+                nsmax = sys_rows(hord[e]) > nsmax ? sys_rows(hord[e]) : nsmax;
+                ++e;
+            }
+            int nt = team_slots / G;
+            if (o.max_blocks > 0 && nt > o.max_blocks / G) nt = o.max_blocks / G;
+            if (nt > e - b) nt = e - b;
+            if (nt < 1) nt = 1;
+            ph.push_back(TeamPhase{G, b, e - b, nt * G, ceil_div(nsmax > 0 ? nsmax : 1, 64) * 64});
+            b = e;
+        }
+    };
+    // workspace for every candidate's largest run
+    int64_t tv_rows = 0;
+    int tmax_teams = 0, tmax_grid = 0;
+    std::vector<TeamPhase> phs;
+    if (occ_team > 0) {
+        for (int tr : team_cands) {
+            plan_teams(tr, npairs, phs);
+            for (const TeamPhase& ph : phs) {
+                const int nt = ph.grid / ph.G;
+                tv_rows = (int64_t)nt * ph.ldv > tv_rows ? (int64_t)nt * ph.ldv : tv_rows;
+                tmax_teams = nt > tmax_teams ? nt : tmax_teams;
+                tmax_grid = ph.grid > tmax_grid ? ph.grid : tmax_grid;
+            }
+        }
+        if (t_forced && sch.team > 0) {
+            plan_teams(sch.team, npairs, phs);
+            for (const TeamPhase& ph : phs) {
+                const int nt = ph.grid / ph.G;
+                tv_rows = (int64_t)nt * ph.ldv > tv_rows ? (int64_t)nt * ph.ldv : tv_rows;
+                tmax_teams = nt > tmax_teams ? nt : tmax_teams;
+                tmax_grid = ph.grid > tmax_grid ? ph.grid : tmax_grid;
+            }
+        }
+    }
+    float *TV = nullptr, *TW = nullptr, *TZ = nullptr;
+    double *TH = nullptr, *TS = nullptr;
+    unsigned long long* Ttags = nullptr;
+    GridBar* Tbar = nullptr;
+    int* d_tq = nullptr;  // one queue per run
+    if (occ_team > 0) {
+        if ((rc = take((void**)&TV, sizeof(float) * (size_t)tv_rows * (kmax + 1)))) return done(rc);
+        if ((rc = take((void**)&TW, sizeof(float) * (size_t)tv_rows))) return done(rc);
+        if ((rc = take((void**)&TZ, sizeof(float) * (size_t)tv_rows))) return done(rc);
+        if ((rc = take((void**)&TH, sizeof(double) * (size_t)tmax_teams * (kmax + 1) * kmax))) return done(rc);
+        if ((rc = take((void**)&TS, sizeof(double) * (size_t)tmax_teams * 4 * (kmax + 2)))) return done(rc);
+        if ((rc = take((void**)&Ttags, sizeof(unsigned long long) * 4 * (size_t)tmax_grid))) return done(rc);
+        if ((rc = take((void**)&Tbar, sizeof(GridBar)))) return done(rc);
+        if ((rc = take((void**)&d_tq, sizeof(int) * (kTeamMaxG + 1)))) return done(rc);
+        cudaError_t e0 = cudaMemsetAsync(Tbar, 0, sizeof(GridBar), s);
+        if (e0) return done(cuda_error(e0, "memset", __FILE__, __LINE__));
+    }
+    const unsigned long long team_tmo =
+        (unsigned long long)((o.barrier_timeout_s > 0 ? o.barrier_timeout_s : 2.0) * 1e9);
+    // the runs of one team-mode GMRES launch over the first np pairs of the order
+    auto launch_team = [&](int tr, int np, const double* Rin, double* Xout, int kcap, double tcap, PairState& St,
+                           cudaStream_t st) -> cudaError_t {
+        std::vector<TeamPhase> ph;
+        plan_teams(tr, np, ph);
+        cudaError_t e = cudaMemsetAsync(d_tq, 0, sizeof(int) * (kTeamMaxG + 1), st);
+        for (size_t i = 0; !e && i < ph.size(); ++i) {
+            e = cudaMemsetAsync(Ttags, 0, sizeof(unsigned long long) * 4 * (size_t)ph[i].grid, st);
+            if (e) break;
+            TeamArgs ta;
+            ta.Av = Av;
+            ta.Mv = Mv;
+            ta.row_off = row_off;
+            ta.nsys = nsys;
+            ta.n = n;
+            ta.order = d_order + ph[i].begin;
+            ta.npairs = ph[i].count;
+            ta.queue = d_tq + ph[i].G;
+            ta.status = St.status;
+            ta.R = Rin;
+            ta.X = Xout;
+            ta.V = TV;
+            ta.W = TW;
+            ta.Z = TZ;
+            ta.ldv = ph[i].ldv;
+            ta.H = TH;
+            ta.S = TS;
+            ta.kmax = kcap;
+            ta.tau = tcap;
+            ta.G = ph[i].G;
+            ta.tags = Ttags;
+            ta.bar = Tbar;
+            ta.tmo = team_tmo;
+            ta.iters = St.iters;
+            ta.steps = St.steps;
+            ta.relres = St.relres;
+            ta.dmax = St.dmax;
+            ta.dxmax = St.dxmax;
+            ta.work = d_work;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)ph[i].grid);
+            cfg.blockDim = dim3(kTeamBD);
+            cfg.dynamicSmemBytes = team_smem;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeCooperative;  // the CTAs of a team wait on one another
+            at[0].val.cooperative = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, k_gmres_team<kTeamP>, ta);
+            note_launch();
+        }
+        return e;
     };
     int tuned = 0;
     float tune_ms = 0.0f;
@@ -749,12 +1302,13 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
             BSPAI_TUNE_TRY(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
             BSPAI_TUNE_TRY(cudaMemsetAsync(Xs, 0, sizeof(double) * (size_t)n * nrhs, s));
             BSPAI_TUNE_TRY(cudaEventRecord(ev.e0, s));
-            BSPAI_TUNE_TRY(launch_gmres(c, gr, Bv, Xs, k_tune, 0.0, T2, s, np_tune));
+            if (c.team > 0) BSPAI_TUNE_TRY(launch_team(c.team, np_tune, Bv, Xs, k_tune, 0.0, T2, s));
+            else BSPAI_TUNE_TRY(launch_gmres(c, gr, Bv, Xs, k_tune, 0.0, T2, s, np_tune));
             BSPAI_TUNE_TRY(cudaEventRecord(ev.e1, s));
             BSPAI_TUNE_TRY(cudaEventSynchronize(ev.e1));
             float ms = 0;
             BSPAI_TUNE_TRY(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
-            tab_s.push_back(bspai_batch_schedule_t{c.bd, c.urows, c.zcap, c.msched});
+            tab_s.push_back(bspai_batch_schedule_t{c.bd, c.urows, c.zcap, c.msched, c.team});
             tab_ms.push_back(ms);
             tune_ms += ms;
             ++tuned;
@@ -785,6 +1339,20 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
             cs.msched = 1;
             if ((rc = trial(cs))) return done(rc);
         }
+        if (occ_team > 0)
+            for (int tr : team_cands) {
+                Sched cs;
+                cs.bd = kTeamBD;
+                cs.urows = MgsU<T>::lo;
+                cs.team = tr;
+                if ((rc = trial(cs))) return done(rc);
+            }
+        // a team exchange that ran out of time during tuning is an error like any other
+        {
+            int terr = 0;
+            if (Tbar) BSPAI_TUNE_TRY(cudaMemcpy(&terr, &Tbar->err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (terr) return done(set_error(BSPAI_TIMEOUT, "batched solve: a team exchange exceeded its time limit"));
+        }
 #undef BSPAI_TUNE_TRY
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = sch;
@@ -794,6 +1362,10 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
     const int bd = sch.bd;
     int grid = 0;
     if ((rc = grid_for(sch, &grid))) return done(rc);
+    {
+        cudaError_t e0 = cudaMemsetAsync(d_work, 0, 2 * sizeof(unsigned long long), s);
+        if (e0) return done(cuda_error(e0, "memset", __FILE__, __LINE__));
+    }
     // one refinement step: residuals, tests, the persistent GMRES launch, tests
     auto step = [&](cudaStream_t st) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(S.rmax, 0, sizeof(double) * npairs * 2, st);  // rmax, xmax
@@ -804,15 +1376,19 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         note_launch();
         {
             ProfScope ps(BSPAI_K_MGS, st);
-            if ((e = launch_gmres(sch, grid, R, X, kmax, tau, S, st, npairs))) return e;
+            if (sch.team > 0) {
+                if ((e = launch_team(sch.team, npairs, R, X, kmax, tau, S, st))) return e;
+            } else if ((e = launch_gmres(sch, grid, R, X, kmax, tau, S, st, npairs))) {
+                return e;
+            }
         }
         k_batch_after<<<(unsigned)ceil_div(npairs, 256), 256, 0, st>>>(npairs, S, ustop, stag);
         note_launch();
         return cudaGetLastError();
     };
-    static thread_local int* t_active = nullptr;
+    static thread_local int* t_active = nullptr;  // [0]: pairs still active, [1]: a team exchange timed out
     if (!t_active) {
-        cudaError_t e = cudaMallocHost(&t_active, sizeof(int));
+        cudaError_t e = cudaMallocHost(&t_active, 2 * sizeof(int));
         if (e != cudaSuccess) {
             t_active = nullptr;
             return done(cuda_error(e, "cudaMallocHost(active flag)", __FILE__, __LINE__));
@@ -856,7 +1432,13 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         }
         if (g) cudaGraphDestroy(g);
         if (cs) cudaStreamDestroy(cs);
-        if (e) return done(cuda_error(e, "capturing the batched refinement step", __FILE__, __LINE__));
+        if (e) {
+            // a step that cannot be captured (e.g. its cooperative team launches) runs directly
+            (void)cudaGetLastError();
+            if (gexec.e) cudaGraphExecDestroy(gexec.e);
+            gexec.e = nullptr;
+            graph_kernels = 0;
+        }
     }
     int ir = 0, launched = 0;
     for (; ir < imax; ++ir) {
@@ -868,10 +1450,13 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         } else {
             e = step(s);
         }
+        t_active[1] = 0;
         if (!e) e = cudaMemcpyAsync(t_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e && Tbar) e = cudaMemcpyAsync(t_active + 1, &Tbar->err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
         if (e) return done(cuda_error(e, "batched refinement step", __FILE__, __LINE__));
-        if (*t_active == 0) break;
+        if (t_active[1]) return done(set_error(BSPAI_TIMEOUT, "batched solve: a team exchange exceeded its time limit"));
+        if (t_active[0] == 0) break;
     }
     // results (a failure still releases the buffers through done())
 #define BSPAI_RES_TRY(expr)                                                          \
@@ -887,6 +1472,8 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
     BSPAI_RES_TRY(cudaMemcpyAsync(hnbe.data(), S.nbe, sizeof(double) * npairs, cudaMemcpyDeviceToHost, s));
     if (pair_status) BSPAI_RES_TRY(cudaMemcpyAsync(pair_status, S.status, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
     if (pair_iters) BSPAI_RES_TRY(cudaMemcpyAsync(pair_iters, S.iters, sizeof(int32_t) * npairs, cudaMemcpyDeviceToDevice, s));
+    unsigned long long hwork[2] = {0, 0};
+    BSPAI_RES_TRY(cudaMemcpyAsync(hwork, d_work, sizeof hwork, cudaMemcpyDeviceToHost, s));
     BSPAI_RES_TRY(cudaStreamSynchronize(s));
 #undef BSPAI_RES_TRY
     int conv = 0, nonfin = 0, maxit = 0, maxsteps = 0;
@@ -912,6 +1499,24 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         info->mgs_rows = sch.urows;
         info->z_shared_rows = sch.zcap;
         info->m_schedule = sch.msched;
+        info->team_rows = sch.team;
+        // algorithmic bytes of the GMRES launches: each MGS pass reads one basis vector's
+        // rows once (the last pass none, and v_{j+1} is written: j + 2 row-vectors per
+        // step); each step's A v and M w read A (values in u_p, int32 columns) and the
+        // bucketed M (stored values, int32 columns, e4m3 column scales) of the pair's
+        // rows at the batch's average entries per row, and gather / write four vectors
+        const double es = (double)sizeof(T);
+        const double upb = u_p == BSPAI_FP64 ? 8.0 : 4.0;
+        double mb = 0.0;
+        for (int k = 0; k < BM->q; ++k) {
+            const int f = BM->precs[k];
+            const double vb = f == BSPAI_FP64 ? 8 : f == BSPAI_FP32 ? 4 : (f == BSPAI_FP16 || f == BSPAI_BF16) ? 2
+                                                                      : f == BSPAI_E4M3 ? 1 : -1;
+            if (vb > 0) mb += (double)BM->nnz_k[k] * (vb + 4.0);
+            if (f == BSPAI_E4M3) mb += 4.0 * n;
+        }
+        const double per_row = n > 0 ? ((double)A->nnz * (upb + 4.0) + mb) / n + 4.0 * es : 0.0;
+        info->gmres_bytes = (int64_t)((double)hwork[0] * es + (double)hwork[1] * per_row);
         info->tuned_candidates = tuned;
         info->tune_ms = tune_ms;
     }
@@ -940,10 +1545,16 @@ int bspai_batch_schedule_force(const bspai_batch_schedule_t* sched) {
         return set_error(BSPAI_ERR_INVALID, "bspai_batch_schedule_force: m_schedule must be 0 or 1");
     if (sched->z_shared_rows < -1 || sched->mgs_rows < 0)
         return set_error(BSPAI_ERR_INVALID, "bspai_batch_schedule_force: negative field");
+    if (sched->team_rows != 0 &&
+        (sched->team_rows < 1024 || sched->team_rows > kTeamP * 2 * kTeamBD || sched->team_rows % 1024))
+        return set_error(BSPAI_ERR_INVALID,
+                         "bspai_batch_schedule_force: team_rows must be 0 or a multiple of 1024 up to %d",
+                         kTeamP * 2 * kTeamBD);
     t_force.bd = sched->block_threads;
     t_force.urows = sched->mgs_rows;
     t_force.zcap = sched->z_shared_rows;
     t_force.msched = sched->m_schedule;
+    t_force.team = sched->team_rows;
     t_forced = true;
     return BSPAI_OK;
 }

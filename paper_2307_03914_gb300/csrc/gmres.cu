@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tags.cuh"
 
 namespace bspai {
 
@@ -254,145 +255,7 @@ __global__ void __launch_bounds__(512) k_mgs(T* __restrict__ V, int64_t ldv, int
     }
 }
 
-// Tagged-slot grid reduction for k_mgs_res.  Every block owns one slot per
-// parity of the pass number; it publishes its partial sum there together with
-// the reduction's sequence number, value and number travelling in the same
-// 64-bit store (fp32: one word {seq, bits}; fp64: two words {seq, high half},
-// {seq, low half}).  A block has the grid total once every slot carries the
-// current number: no atomics, no fences and no separate read of the partials
-// after a release.  The sequence numbers continue across launches (the count
-// lives in GridBar::seq, advanced by block 0 after the kernel's last
-// reduction), so slots left by earlier reductions never match.  The partials
-// are added in the same fixed order as grid_wait (lane-strided, then a warp
-// butterfly), so the total is the same in every block and in every run.
-template <typename T>
-struct TagWords;
-template <>
-struct TagWords<float> {
-    static constexpr int W = 1;
-};
-template <>
-struct TagWords<double> {
-    static constexpr int W = 2;
-};
-constexpr int kTagMaxBlocks = 160;  // slots read per lane: kTagMaxBlocks / 32 (152 SMs)
-constexpr int kMgsBlocks = 64;      // fewest blocks the on-chip MGS kernel is given
-
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void tag_publish(float v, unsigned long long* slot, unsigned seq) {
-    st_relaxed_u64(slot, ((unsigned long long)seq << 32) | __float_as_uint(v));
-}
-__device__ __forceinline__ void tag_publish(double v, unsigned long long* slot, unsigned seq) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    st_relaxed_u64(slot, ((unsigned long long)seq << 32) | (b >> 32));
-    st_relaxed_u64(slot + 1, ((unsigned long long)seq << 32) | (b & 0xffffffffull));
-}
-// true (and *v set) once the slot carries `seq`
-__device__ __forceinline__ bool tag_read(const unsigned long long* slot, unsigned seq, float* v) {
-    const unsigned long long a = ld_relaxed_u64(slot);
-    if ((unsigned)(a >> 32) != seq) return false;
-    *v = __uint_as_float((unsigned)a);
-    return true;
-}
-__device__ __forceinline__ bool tag_read(const unsigned long long* slot, unsigned seq, double* v) {
-    const unsigned long long a = ld_relaxed_u64(slot), b = ld_relaxed_u64(slot + 1);
-    if ((unsigned)(a >> 32) != seq || (unsigned)(b >> 32) != seq) return false;
-    *v = __longlong_as_double((long long)((a << 32) | (b & 0xffffffffull)));
-    return true;
-}
-
-template <typename T>
-__device__ __forceinline__ void tag_arrive(T v, unsigned long long* tags, int set, unsigned seq, T* s_w,
-                                           int G = -1) {
-    if (G < 0) G = gridDim.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-    v = warp_sum(v);
-    if (lane == 0) s_w[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        T t = lane < nw ? s_w[lane] : T(0);
-        t = warp_sum(t);
-        if (lane == 0)
-            tag_publish(t, tags + ((int64_t)set * G + blockIdx.x) * TagWords<T>::W, seq);
-    }
-}
-
-// The lanes of one warp poll the G slots of `set` until all carry `seq`
-// (giving up after tmo ns, or when another block has flagged an error) and
-// add them in a fixed order (lane-strided, then a warp butterfly): every lane
-// gets the total, the same in every block.  False after a timeout.
-template <typename T>
-__device__ __forceinline__ bool tag_poll_warp(const unsigned long long* tags, int set, unsigned seq, int G,
-                                              GridBar* bar, unsigned long long tmo, T* total) {
-    constexpr int MS = kTagMaxBlocks / 32;
-    constexpr int TW = TagWords<T>::W;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long* base = tags + (int64_t)set * G * TW;
-    T val[MS];
-    unsigned pending = 0;
-#pragma unroll
-    for (int m = 0; m < MS; ++m) {
-        val[m] = T(0);
-        if (lane + 32 * m < G) pending |= 1u << m;
-    }
-    bool ok = true;
-    unsigned long long t0 = 0;
-    for (int it = 0;; ++it) {
-#pragma unroll
-        for (int m = 0; m < MS; ++m)
-            if ((pending >> m) & 1u)
-                if (tag_read(base + (int64_t)(lane + 32 * m) * TW, seq, &val[m])) pending &= ~(1u << m);
-        if (!__any_sync(0xffffffffu, pending != 0)) break;
-        int stop = 0;
-        if (lane == 0) {
-            const unsigned long long now = globaltimer_ns();
-            if (it == 0) t0 = now;
-            if (now - t0 > tmo) {
-                atomicExch(&bar->err, 1);
-                stop = 1;
-            } else if ((it & 63) == 63 && *(volatile int*)&bar->err) {
-                stop = 1;
-            }
-        }
-        if (__shfl_sync(0xffffffffu, stop, 0)) {
-            ok = false;
-            break;
-        }
-    }
-    T t = T(0);
-#pragma unroll
-    for (int m = 0; m < MS; ++m)
-        if (lane + 32 * m < G) t = Ar<T>::add(t, val[m]);
-    *total = warp_sum(t);
-    return ok;
-}
-
-// Warp 0 polls the slots of `set` (tag_poll_warp), then every thread gets the
-// total; *s_ok = 0 after a timeout.  G: the blocks that publish (default: all).
-template <typename T>
-__device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, unsigned seq, GridBar* bar,
-                                      unsigned long long tmo, T* s_tot, int* s_ok, int G = -1) {
-    if (G < 0) G = gridDim.x;
-    if (threadIdx.x < 32) {
-        T t;
-        const bool ok = tag_poll_warp<T>(tags, set, seq, G, bar, tmo, &t);
-        if (threadIdx.x == 0) {
-            *s_tot = t;
-            *s_ok = ok ? 1 : 0;
-        }
-    }
-    __syncthreads();
-    return *s_tot;
-}
+constexpr int kMgsBlocks = 64;  // fewest blocks the on-chip MGS kernel is given
 
 // The Givens block: with giv = 1 the last block of an on-chip MGS launch takes
 // no rows.  Its first warp reads every pass's total from the same tagged slots

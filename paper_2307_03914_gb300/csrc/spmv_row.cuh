@@ -44,6 +44,14 @@ __device__ __forceinline__ float decode<BSPAI_E4M3>(const void* val, int64_t p, 
     return __fmul_rn(float(e), __ldg(colscale + c));
 }
 
+// an entry of x: through the read-only path, or (CG) from L2 -- for a vector
+// that other blocks of the same launch write (the batched solver's teams)
+template <bool CG, typename XT>
+__device__ __forceinline__ XT ldx(const XT* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // column of slot p of row r, read through the read-only path
 __device__ __forceinline__ int sell_col_ldg(const BucketDev& B, int64_t p, int64_t r) {
     if (B.col16) {
@@ -56,7 +64,7 @@ __device__ __forceinline__ int sell_col_ldg(const BucketDev& B, int64_t p, int64
 // fp32 partial sum of one row over one narrow bucket (w slots per row of its
 // slice starting at sbase, either slot arrangement).  Loads are issued four
 // slots ahead of the (strictly sequential) accumulation.
-template <int PREC, typename XT>
+template <int PREC, typename XT, bool CG = false>
 __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t sbase, int w,
                                                  const XT* __restrict__ x, int64_t r) {
     // e4m3 scales: per column of M, or per row of a transposed M; fp16: per bucket or per slice
@@ -78,7 +86,7 @@ __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t sba
         for (int u = 0; u < 4; ++u) {
             if (c[u] >= 0) {
                 v[u] = decode<PREC>(B.val, p[u], sc, st, B.colscale ? c[u] : (int)r);
-                xv[u] = to_f32<XT>(__ldg(x + c[u]));
+                xv[u] = to_f32<XT>(ldx<CG>(x + c[u]));
             }
         }
 #pragma unroll
@@ -90,13 +98,13 @@ __device__ __forceinline__ float row_partial_f32(const BucketDev& B, int64_t sba
         const int c = sell_col_ldg(B, p, r);
         if (c >= 0) {
             const float v = decode<PREC>(B.val, p, sc, st, B.colscale ? c : (int)r);
-            acc = __fadd_rn(acc, __fmul_rn(v, to_f32<XT>(__ldg(x + c))));
+            acc = __fadd_rn(acc, __fmul_rn(v, to_f32<XT>(ldx<CG>(x + c))));
         }
     }
     return acc;
 }
 
-template <typename XT>
+template <typename XT, bool CG = false>
 __device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t sbase, int w,
                                                   const XT* __restrict__ x, int64_t r) {
     const double* val = reinterpret_cast<const double*>(B.val);
@@ -116,7 +124,7 @@ __device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t sb
         for (int u = 0; u < 4; ++u) {
             if (c[u] >= 0) {
                 v[u] = __ldg(val + p[u]);
-                xv[u] = (double)__ldg(x + c[u]);
+                xv[u] = (double)ldx<CG>(x + c[u]);
             }
         }
 #pragma unroll
@@ -126,7 +134,7 @@ __device__ __forceinline__ double row_partial_f64(const BucketDev& B, int64_t sb
     for (; l < w; ++l) {
         const int64_t p = sell_slot(sbase, lane, l, B.packed);
         const int c = sell_col_ldg(B, p, r);
-        if (c >= 0) acc = __dadd_rn(acc, __dmul_rn(__ldg(val + p), (double)__ldg(x + c)));
+        if (c >= 0) acc = __dadd_rn(acc, __dmul_rn(__ldg(val + p), (double)ldx<CG>(x + c)));
     }
     return acc;
 }
@@ -147,7 +155,7 @@ __device__ __forceinline__ float decode_rt(const BucketDev& B, int64_t p, int c,
 // y_i = sum_k y_i^(k) for row r of a bucketed matrix: each bucket's partial sum
 // in ascending column order (fp64 for an fp64 bucket, fp32 otherwise), the
 // partial sums added in fp64 in bucket order.
-template <typename XT>
+template <typename XT, bool CG = false>
 __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const XT* __restrict__ x) {
     const int64_t s = r >> 5;
     double yi = 0.0;
@@ -157,11 +165,11 @@ __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const 
         const int64_t sb = B.sptr[s];
         const int w = (int)((B.sptr[s + 1] - sb) >> 5);
         switch (B.prec) {
-        case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT>(B, sb, w, x, r)); break;
-        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT>(B, sb, w, x, r)); break;
-        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT>(B, sb, w, x, r)); break;
-        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT>(B, sb, w, x, r)); break;
-        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT>(B, sb, w, x, r)); break;
+        case BSPAI_FP64: yi = __dadd_rn(yi, row_partial_f64<XT, CG>(B, sb, w, x, r)); break;
+        case BSPAI_FP32: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP32, XT, CG>(B, sb, w, x, r)); break;
+        case BSPAI_FP16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_FP16, XT, CG>(B, sb, w, x, r)); break;
+        case BSPAI_BF16: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_BF16, XT, CG>(B, sb, w, x, r)); break;
+        case BSPAI_E4M3: yi = __dadd_rn(yi, (double)row_partial_f32<BSPAI_E4M3, XT, CG>(B, sb, w, x, r)); break;
         default: break;
         }
     }
@@ -173,7 +181,7 @@ __device__ __forceinline__ double bucketed_row(const BMDev& M, int64_t r, const 
 // with the loads of both rows issued together so that each thread keeps two
 // independent chains of gathers in flight.  Plain slot arrangement and int32
 // columns only: the batched bucketing, whose solver uses these, keeps them.
-template <int PREC, typename XT>
+template <int PREC, typename XT, bool CG = false>
 __device__ __forceinline__ void row_partial2_f32(const BucketDev& B, int64_t pa, int64_t ea, int64_t pb, int64_t eb,
                                                  const XT* __restrict__ x, int64_t ra, int64_t rb, float& acc_a,
                                                  float& acc_b) {
@@ -194,7 +202,7 @@ __device__ __forceinline__ void row_partial2_f32(const BucketDev& B, int64_t pa,
                 const int64_t p = u < 2 ? pa + 32 * u : pb + 32 * (u - 2);
                 const int64_t r = u < 2 ? ra : rb;
                 v[u] = decode<PREC>(B.val, p, u < 2 ? sca : scb, st, B.colscale ? c[u] : (int)r);
-                xv[u] = to_f32<XT>(__ldg(x + c[u]));
+                xv[u] = to_f32<XT>(ldx<CG>(x + c[u]));
             }
         }
         if (c[0] >= 0) aa = __fadd_rn(aa, __fmul_rn(v[0], xv[0]));
@@ -206,7 +214,7 @@ __device__ __forceinline__ void row_partial2_f32(const BucketDev& B, int64_t pa,
     acc_b = ab;
 }
 
-template <typename XT>
+template <typename XT, bool CG = false>
 __device__ __forceinline__ void row_partial2_f64(const BucketDev& B, int64_t pa, int64_t ea, int64_t pb, int64_t eb,
                                                  const XT* __restrict__ x, double& acc_a, double& acc_b) {
     const double* val = reinterpret_cast<const double*>(B.val);
@@ -223,7 +231,7 @@ __device__ __forceinline__ void row_partial2_f64(const BucketDev& B, int64_t pa,
             if (c[u] >= 0) {
                 const int64_t p = u < 2 ? pa + 32 * u : pb + 32 * (u - 2);
                 v[u] = __ldg(val + p);
-                xv[u] = (double)__ldg(x + c[u]);
+                xv[u] = (double)ldx<CG>(x + c[u]);
             }
         }
         if (c[0] >= 0) aa = __dadd_rn(aa, __dmul_rn(v[0], xv[0]));
@@ -236,7 +244,7 @@ __device__ __forceinline__ void row_partial2_f64(const BucketDev& B, int64_t pa,
 }
 
 // bucketed_row for two rows at once (the same sums, bucket by bucket in order)
-template <typename XT>
+template <typename XT, bool CG = false>
 __device__ __forceinline__ void bucketed_row2(const BMDev& M, int64_t ra, int64_t rb, const XT* __restrict__ x,
                                               double& ya, double& yb) {
     const int64_t sa = ra >> 5, sb = rb >> 5;
@@ -248,17 +256,17 @@ __device__ __forceinline__ void bucketed_row2(const BMDev& M, int64_t ra, int64_
         const int64_t pb = B.sptr[sb] + lb, eb = B.sptr[sb + 1];
         if (B.prec == BSPAI_FP64) {
             double a, b;
-            row_partial2_f64<XT>(B, pa, ea, pb, eb, x, a, b);
+            row_partial2_f64<XT, CG>(B, pa, ea, pb, eb, x, a, b);
             ta = __dadd_rn(ta, a);
             tb = __dadd_rn(tb, b);
             continue;
         }
         float a = 0.0f, b = 0.0f;
         switch (B.prec) {
-        case BSPAI_FP32: row_partial2_f32<BSPAI_FP32, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
-        case BSPAI_FP16: row_partial2_f32<BSPAI_FP16, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
-        case BSPAI_BF16: row_partial2_f32<BSPAI_BF16, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
-        case BSPAI_E4M3: row_partial2_f32<BSPAI_E4M3, XT>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_FP32: row_partial2_f32<BSPAI_FP32, XT, CG>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_FP16: row_partial2_f32<BSPAI_FP16, XT, CG>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_BF16: row_partial2_f32<BSPAI_BF16, XT, CG>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
+        case BSPAI_E4M3: row_partial2_f32<BSPAI_E4M3, XT, CG>(B, pa, ea, pb, eb, x, ra, rb, a, b); break;
         default: continue;  // dropped entries are not stored
         }
         ta = __dadd_rn(ta, (double)a);

@@ -19,10 +19,11 @@ lists of the same M (one fp32 bucket, one fp16 bucket, fp32 + fp16, fp16 +
 e4m3) to separate the cost of the formats from the cost of the mix.
 --batch NSYS NRHS runs the batched solver once on a batch of NSYS systems
 with NRHS right-hand sides (the 512 x 32 workload's size distribution), and
-prints its statistics and time (a short launch sequence for a profiler).
-With --schedule BD,MGS_ROWS,Z_ROWS,M_SCHED (repeatable; Z_ROWS -1 = every
-pair that fits) it solves the batch once per given schedule instead of autotuning and
-prints each one's time.
+prints its statistics, time, and the GMRES launches' kernel-class event time
+and algorithmic GB/s (a short launch sequence for a profiler).
+With --schedule BD,MGS_ROWS,Z_ROWS,M_SCHED[,TEAM_ROWS] (repeatable; Z_ROWS -1 =
+every pair that fits; TEAM_ROWS > 0: team mode) it solves the batch once per
+given schedule instead of autotuning and prints each one's time.
 --adaptive EPS ALPHA times the adaptive SPAI build (beta = 8, identity
 start) on the grid (median of --reps builds) and prints its statistics; with
 --once it builds exactly once (a short launch sequence for a profiler).
@@ -92,7 +93,7 @@ def main():
     p.add_argument("--batch", type=int, nargs=2, default=None, metavar=("NSYS", "NRHS"))
     p.add_argument("--adaptive", type=float, nargs=2, default=None, metavar=("EPS", "ALPHA"))
     p.add_argument("--spai-uf", action="store_true")
-    p.add_argument("--schedule", action="append", default=None, metavar="BD,MGS_ROWS,Z_ROWS,M_SCHED")
+    p.add_argument("--schedule", action="append", default=None, metavar="BD,MGS_ROWS,Z_ROWS,M_SCHED[,TEAM_ROWS]")
     a = p.parse_args()
     if a.spai_uf:
         return spai_uf(a.grid, a.reps, a.once)
@@ -230,10 +231,12 @@ def batch(nsys, nrhs, schedules=None):
     torch.cuda.synchronize()
     for sc in schedules or [None]:
         if sc is not None:
-            bd, u, z, m = (int(v) for v in sc.split(","))
-            B.batch_schedule_force(bd, u, z, m)
+            f = [int(v) for v in sc.split(",")] + [0]
+            B.batch_schedule_force(f[0], f[1], f[2], f[3], f[4])
         X.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.profile_enable(True)
+        B.profile_read(reset=True)
         e0.record()
         try:
             info = B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, tol=bw["tau"])
@@ -241,7 +244,11 @@ def batch(nsys, nrhs, schedules=None):
             B.batch_schedule_force(None)
         e1.record()
         torch.cuda.synchronize()
-        out = {"batch": [nsys, nrhs], "rows": bw["A"].n, "ms": e0.elapsed_time(e1), **info}
+        prof = B.profile_read(reset=True)
+        B.profile_enable(False)
+        gm = prof["mgs"][0]
+        out = {"batch": [nsys, nrhs], "rows": bw["A"].n, "ms": e0.elapsed_time(e1), "gmres_ms": gm,
+               "gmres_GBs": info["gmres_bytes"] / (gm / 1000.0) / 1e9 if gm > 0 else None, **info}
         if sc is None:
             out["tuning"] = B.batch_tune_table()
         print(json.dumps(out), flush=True)

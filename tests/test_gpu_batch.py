@@ -146,6 +146,56 @@ def test_batch_schedules_compute_the_same_bits(B, bd):
         assert np.array_equal(g["iters"], ref["iters"]) and np.array_equal(g["status"], ref["status"]), sched
 
 
+@pytest.mark.parametrize("team_rows", [1024, 2048])
+def test_batch_team_mode_matches_oracle_per_pair(B, team_rows):
+    """Team mode: pairs on teams of ceil(n_s / team_rows) CTAs (here up to 5) with z
+    in registers; every pair within 1e-12 of the oracle's own solve, GMRES counts
+    within the one-CTA bars, and a second run gives the same bits."""
+    bw = W.batch_workload(nsys=6, nrhs=2, nmin=300, nmax=5000, seed=21)
+    g = _forced(B, bw, block_threads=512, team_rows=team_rows)
+    info = g["info"]
+    assert info["team_rows"] == team_rows and info["converged"] == info["pairs"], info
+    sizes = np.diff(bw["row_off"])
+    assert -(-sizes.max() // team_rows) >= (4 if team_rows == 1024 else 2)  # teams of several CTAs
+    n = bw["A"].n
+    X = host(g["X"]).reshape(bw["nrhs"], n)
+    ro = bw["row_off"]
+    for s, m in enumerate(bw["mats"]):
+        wl = _system_wl(bw, s)
+        for r in range(bw["nrhs"]):
+            wl["b"] = bw["B"][r, ro[s]:ro[s] + m.n]
+            xt = bw["X_true"][r, ro[s]:ro[s] + m.n]
+            ref = O.solve(wl, bucket_eps=bw["bucket_eps"])
+            xg = X[r, ro[s]:ro[s] + m.n]
+            assert np.abs(xg - ref["x"]).max() <= 1e-12 * np.abs(ref["x"]).max(), (s, r)
+            assert np.abs(xg - xt).max() / np.abs(xt).max() <= 1e-10
+            assert abs(g["iters"][r * len(bw["mats"]) + s] - sum(ref["its"])) <= max(4, 0.15 * sum(ref["its"]))
+        assert np.all(X[:, ro[s] + m.n:ro[s + 1]] == 0)
+    g2 = _forced(B, bw, block_threads=512, team_rows=team_rows)
+    assert np.array_equal(host(g2["X"]), host(g["X"])) and np.array_equal(g2["iters"], g["iters"])
+
+
+def test_batch_team_mode_needs_fp32_krylov_vectors(B):
+    bw = W.batch_workload(nsys=2, nrhs=1, nmin=100, nmax=200, seed=9)
+    A = B.DeviceCSR.from_host(bw["A"])
+    P = B.DeviceCSR.from_host(bw["pattern"], with_values=False)
+    Ah = B.matrix_create(A)
+    M, _ = B.bspai_build(A, P, bw["spai_eps"])
+    row_off = dev(bw["row_off"])
+    BM, _ = B.bspai_bucket_batched(M, row_off, bw["bucket_eps"], bw["precs"])
+    Bd = dev(bw["B"].reshape(-1))
+    X = torch.zeros_like(Bd)
+    B.batch_schedule_force(512, team_rows=2048)
+    try:
+        with pytest.raises(B.BspaiError) as e:
+            B.gmres_ir_solve_batched(Ah, row_off, bw["nrhs"], Bd, BM, M, X, u_g="fp64", u_p="fp64", tol=1e-8)
+        assert e.value.status == B.ERR_UNSUPPORTED
+    finally:
+        B.batch_schedule_force(None)
+    with pytest.raises(B.BspaiError):
+        B.batch_schedule_force(512, team_rows=1000)
+
+
 def test_batch_schedule_rejects_what_does_not_fit(B):
     bw = W.batch_workload(nsys=2, nrhs=1, nmin=100, nmax=200, seed=9)
     for sched, msg in [(dict(z_shared_rows=1 << 24), "z_shared_rows"), (dict(mgs_rows=3), "mgs_rows")]:
@@ -164,13 +214,14 @@ def test_batch_autotuner_picks_the_fastest_candidate(B):
     g = _gpu_batch(B, bw)
     info = g["info"]
     tab = B.batch_tune_table()
-    assert info["tuned_candidates"] == len(tab) >= 5, (info, tab)
+    assert info["tuned_candidates"] == len(tab) >= 7, (info, tab)
+    assert {t["team_rows"] for t in tab} >= {0, 8192, 4096}
     assert all(t["ms"] > 0 for t in tab)
     assert {t["block_threads"] for t in tab} >= {128, 256, 512}
     assert any(t["m_schedule"] == 1 for t in tab)
     best = min(tab, key=lambda t: t["ms"])
-    assert (best["block_threads"], best["mgs_rows"], best["z_shared_rows"], best["m_schedule"]) == \
-        (info["block_threads"], info["mgs_rows"], info["z_shared_rows"], info["m_schedule"])
+    assert (best["block_threads"], best["mgs_rows"], best["z_shared_rows"], best["m_schedule"], best["team_rows"]) == \
+        (info["block_threads"], info["mgs_rows"], info["z_shared_rows"], info["m_schedule"], info["team_rows"])
     assert abs(sum(t["ms"] for t in tab) - info["tune_ms"]) <= 1e-3 * info["tune_ms"] + 1e-3
     g2 = _gpu_batch(B, bw)
     assert g2["info"]["tuned_candidates"] == 0
