@@ -24,8 +24,9 @@
 // in the fixed-pattern kernel: the gathered rows of A (B's u_f values
 // precomputed once), the
 // shadow (bitonic sort + ballot compaction), Abar in shared memory, the
-// Householder QR with warp-shuffle reductions, back substitution, sbar from
-// the gathered entries; the candidates by one sweep over the rows of B in I_k
+// Householder QR with warp-shuffle reductions (updated from pass to pass in
+// fp32, see k_spai_adaptive), back substitution, sbar from the gathered
+// entries; the candidates by one sweep over the rows of B in I_k
 // into an open-addressing hash table that also accumulates sbar^T B(I_k, j)
 // in exact fixed point (the u_f products summed exactly, then rounded once to
 // u_f), rho per candidate from that sum and the precomputed
@@ -54,40 +55,44 @@ struct AdaptiveCounters {
 
 // shared memory of one warp, 16-byte aligned pieces
 struct AdaptiveLayout {
-    size_t acc, J, Jn, stp, stpn, rbeg, eoff, picks, mv, rdiag, ecol, eq, eval, I, cv, sv, tab, region, total;
+    size_t acc, J, Js, stp, rbeg, eoff, picks, mv, rdiag, tw, ecol, eq, eval, I, Is, Ip, cv, sv, tab, region, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // jmax, lmax: bounds on |J| and |I|; gmax: on the gathered entries of rows J;
 // lp2: the shadow sort's length (a power of two >= gmax); H: the candidate
-// hash table's size (a power of two; every candidate passes through it).
+// hash table's size (a power of two; every candidate passes through it).  The
+// table's storage (tab, acc) is also the scratch of the shadow sort and of the
+// merge of new shadow rows, and holds the candidates and their rho while it is
+// emptied: H >= lp2 and H >= lmax (the host sizes it so).  The region holds
+// the factorised Abar from pass to pass.
 __host__ __device__ inline AdaptiveLayout adaptive_layout(int jmax, int lmax, int gmax, int lp2, int H) {
     AdaptiveLayout L{};
     size_t o = 0;
     L.acc = o;   o += al16((size_t)H * 8);  // the candidates' fixed-point sbar^T B e_j
     L.J = o;     o += al16((size_t)jmax * 4);
-    L.Jn = o;    o += al16((size_t)jmax * 4);
+    L.Js = o;    o += al16((size_t)jmax * 4);
     L.stp = o;   o += al16((size_t)jmax * 4);
-    L.stpn = o;  o += al16((size_t)jmax * 4);
     L.rbeg = o;  o += al16((size_t)jmax * 4);
     L.eoff = o;  o += al16((size_t)(jmax + 1) * 4);
     L.picks = o; o += al16((size_t)jmax * 4);
     L.mv = o;    o += al16((size_t)jmax * 4);
     L.rdiag = o; o += al16((size_t)jmax * 4);
+    L.tw = o;    o += al16((size_t)jmax * 4);
     L.ecol = o;  o += al16((size_t)gmax * 4);
     L.eq = o;    o += al16((size_t)gmax * 4);
     L.eval = o;  o += al16((size_t)gmax * 4);
     L.I = o;     o += al16((size_t)lmax * 4);
+    L.Is = o;    o += al16((size_t)lmax * 4);
+    L.Ip = o;    o += al16((size_t)lmax * 4);
     L.cv = o;    o += al16((size_t)lmax * 4);
     L.sv = o;    o += al16((size_t)lmax * 4);
     L.tab = o;   o += al16((size_t)H * 4);
-    L.region = o;  // Abar, or the shadow sort's keys, or the candidates and their rho
-    size_t r = (size_t)lmax * jmax * 4;
-    if ((size_t)lp2 * 4 > r) r = (size_t)lp2 * 4;
-    if ((size_t)H * 8 > r) r = (size_t)H * 8;
-    o += al16(r);
+    L.region = o;  // Abar (column-major, leading dimension lmax)
+    o += al16((size_t)lmax * jmax * 4);
     L.total = o;
+    (void)lp2;
     return L;
 }
 
@@ -152,32 +157,28 @@ __device__ __forceinline__ int pow2_at_least(int v) {
     return p;
 }
 
-// Gather every entry of rows J[0, nJ) of A: its column, its value in B
-// (a_jc d_j rounded to u_f, precomputed) and its q.  Returns the count
-// (<= nJ * rowmax).
-__device__ __forceinline__ int gather_rows(const int* J, int nJ, const int32_t* __restrict__ arp,
-                                           const int32_t* __restrict__ acol, const float* __restrict__ bval,
-                                           int* rbeg, int* eoff, int* ecol, int* eq, float* eval, int lane) {
-    for (int q = lane; q < nJ; q += 32) {
+// Gather every entry of rows J[q0, q1) of A -- the columns added by a pass --
+// after the L0 entries already gathered: its column, its value in B (a_jc d_j
+// rounded to u_f, precomputed) and its q.  eoff[q] is the first entry of
+// column q (eoff[q0] = L0 on entry).  Returns the new count (<= q1 * rowmax).
+__device__ __forceinline__ int gather_new_rows(const int* J, int q0, int q1, int L0, const int32_t* __restrict__ arp,
+                                               const int32_t* __restrict__ acol, const float* __restrict__ bval,
+                                               int* rbeg, int* eoff, int* ecol, int* eq, float* eval, int lane) {
+    for (int q = q0 + lane; q < q1; q += 32) {
         const int j = J[q];
         const int rb = arp[j];
         rbeg[q] = rb;
-        eoff[q] = arp[j + 1] - rb;
+        eoff[q + 1] = arp[j + 1] - rb;  // lengths first, offsets below
     }
     __syncwarp();
     if (lane == 0) {
-        int acc = 0;
-        for (int q = 0; q < nJ; ++q) {
-            const int len = eoff[q];
-            eoff[q] = acc;
-            acc += len;
-        }
-        eoff[nJ] = acc;
+        eoff[q0] = L0;
+        for (int q = q0; q < q1; ++q) eoff[q + 1] += eoff[q];
     }
     __syncwarp();
-    const int L = eoff[nJ];
-    for (int t = lane; t < L; t += 32) {
-        int lo = 0, hi = nJ;
+    const int L = eoff[q1];
+    for (int t = L0 + lane; t < L; t += 32) {
+        int lo = q0, hi = q1;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (eoff[mid] <= t) lo = mid;
@@ -192,26 +193,32 @@ __device__ __forceinline__ int gather_rows(const int* J, int nJ, const int32_t* 
     return L;
 }
 
-// The distinct columns among ecol[0, L) in ascending order into I (at most
-// lmax written); returns their number (which may exceed lmax).
-__device__ __forceinline__ int shadow_rows(const int* ecol, int L, int* keys, int* I, int lmax, int lane) {
-    const int LP = pow2_at_least(L > 2 ? L : 2);
-    for (int t = lane; t < LP; t += 32) keys[t] = t < L ? ecol[t] : INT_MAX;
+// The distinct columns among ecol[L0, L) that are not rows of the shadow yet
+// (Is[0, nI), sorted), ascending, into out (at most room written); returns
+// their number (which may exceed room).  keys: LP >= L - L0 ints of scratch,
+// left holding -1.
+__device__ __forceinline__ int new_shadow_rows(const int* ecol, int L0, int L, const int* Is, int nI, int* keys,
+                                               int* out, int room, int lane) {
+    const int cnt = L - L0;
+    const int LP = pow2_at_least(cnt > 2 ? cnt : 2);
+    for (int t = lane; t < LP; t += 32) keys[t] = t < cnt ? ecol[L0 + t] : INT_MAX;
     __syncwarp();
     warp_bitonic(keys, LP, lane);
-    int nI = 0;
-    for (int b0 = 0; b0 < L; b0 += 32) {
+    int nn = 0;
+    for (int b0 = 0; b0 < cnt; b0 += 32) {
         const int t = b0 + lane;
-        const int v = t < L ? keys[t] : INT_MAX;
-        const int prev = (t > 0 && t < L) ? keys[t - 1] : -1;
-        const bool flag = t < L && v != prev;
+        const int v = t < cnt ? keys[t] : INT_MAX;
+        const int prev = (t > 0 && t < cnt) ? keys[t - 1] : -1;
+        const bool flag = t < cnt && v != prev && !contains(Is, nI, v);
         const unsigned m = __ballot_sync(0xffffffffu, flag);
-        const int pos = nI + __popc(m & ((1u << lane) - 1u));
-        if (flag && pos < lmax) I[pos] = v;
-        nI += __popc(m);
+        const int pos = nn + __popc(m & ((1u << lane) - 1u));
+        if (flag && pos < room) out[pos] = v;
+        nn += __popc(m);
     }
     __syncwarp();
-    return nI;
+    for (int t = lane; t < LP; t += 32) keys[t] = -1;
+    __syncwarp();
+    return nn;
 }
 
 // Two tiers share this kernel.  The first runs every column with a small
@@ -221,6 +228,18 @@ __device__ __forceinline__ int shadow_rows(const int* ecol, int L, int* keys, in
 // tier (redo_list == nullptr) reruns exactly those columns (cols) from the
 // start with the full bounds.  Both run the same steps in the same order, so
 // a column's result does not depend on the tier that finished it.
+//
+// QR updating (the remark after Alg 2.1, Grote and Huckle's eqs. 14-15): the
+// Householder factorisation of Abar = B(I, J) is kept from pass to pass.  The
+// rows of Abar stay in the order they joined the shadow (Is/Ip: the sorted
+// row ids and their Abar rows, for lookups), the columns in the order they
+// joined J.  A pass that adds columns Jt and rows It needs no new row in the
+// old columns (B(It, J) = 0: It lies outside the old shadow), so Abar grows to
+// [[Abar, B(I, Jt)], [0, B(It, Jt)]]: the old reflectors (zero on the new
+// rows) are applied to the new columns, the new columns are factored below
+// the old ones, and Q^T ebar keeps its old entries (ebar's new rows are zero,
+// but for k).  The least-squares solution is that of a fresh factorisation up
+// to rounding.
 template <bool HALF>
 __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
     int n, int ncols, const int32_t* __restrict__ cols, const int32_t* __restrict__ arp,
@@ -241,65 +260,162 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
     const AdaptiveLayout LY = adaptive_layout(jmax, lmax, gmax, lp2, H);
     unsigned char* base = smem + LY.total * wib;
     long long* acc = reinterpret_cast<long long*>(base + LY.acc);
-    int* J = reinterpret_cast<int*>(base + LY.J);
-    int* Jn = reinterpret_cast<int*>(base + LY.Jn);
+    int* J = reinterpret_cast<int*>(base + LY.J);    // in the order the columns joined
+    int* Js = reinterpret_cast<int*>(base + LY.Js);  // the same, ascending (membership tests)
     int* stp = reinterpret_cast<int*>(base + LY.stp);
-    int* stpn = reinterpret_cast<int*>(base + LY.stpn);
     int* rbeg = reinterpret_cast<int*>(base + LY.rbeg);
     int* eoff = reinterpret_cast<int*>(base + LY.eoff);
     int* picks = reinterpret_cast<int*>(base + LY.picks);
     float* mv = reinterpret_cast<float*>(base + LY.mv);
     float* rdiag = reinterpret_cast<float*>(base + LY.rdiag);
+    float* tw = reinterpret_cast<float*>(base + LY.tw);  // 2 / v^T v of each reflector
     int* ecol = reinterpret_cast<int*>(base + LY.ecol);
     int* eq = reinterpret_cast<int*>(base + LY.eq);
     float* eval = reinterpret_cast<float*>(base + LY.eval);
-    int* I = reinterpret_cast<int*>(base + LY.I);
+    int* I = reinterpret_cast<int*>(base + LY.I);    // row id at each Abar row
+    int* Is = reinterpret_cast<int*>(base + LY.Is);  // row ids ascending
+    int* Ip = reinterpret_cast<int*>(base + LY.Ip);  // ... and their Abar rows
     float* cv = reinterpret_cast<float*>(base + LY.cv);
     float* sv = reinterpret_cast<float*>(base + LY.sv);
     int* tab = reinterpret_cast<int*>(base + LY.tab);
-    float* Ab = reinterpret_cast<float*>(base + LY.region);
-    int* keys = reinterpret_cast<int*>(base + LY.region);
-    float* rho = reinterpret_cast<float*>(base + LY.region + (size_t)H * 4);
+    float* Ab = reinterpret_cast<float*>(base + LY.region);  // column-major, leading dimension lmax
+    // candidates and their rho reuse the hash table's storage while it is emptied
+    int* keys = tab;
+    float* rho = reinterpret_cast<float*>(acc);
     for (int t = lane; t < H; t += 32) {  // empty; every pass leaves it empty again
         tab[t] = -1;
         acc[t] = 0;
     }
-
     if (lane == 0) {
         J[0] = (int)k;
+        Js[0] = (int)k;
         stp[0] = 0;
     }
     __syncwarp();
-    int nJ = 1;
-    int L = gather_rows(J, nJ, arp, acol, bval, rbeg, eoff, ecol, eq, eval, lane);
-    int nI = shadow_rows(ecol, L, keys, I, lmax, lane);  // <= rowmax <= lmax (host check)
-    int max_rows = nI;
-    float res_norm = 1.0f, r2sum = 1.0f;
+    int nJ = 1, nJ_old = 0;  // columns in J; columns already factored
+    int L = 0, nI = 0;       // entries gathered; rows of Abar
+    int max_rows = 0;
+    float res_norm = 1.0f, r2sum = 1.0f, fro2 = 0.0f;
     bool rankdef = false, conv = false, capped = false, redo = false;
     int solves = 0;
 
     for (int step = 0; step <= alpha; ++step) {
-        // ---- least squares on B(I, J): Abar (column-major, ld nI), ebar
-        for (int t = lane; t < nJ * nI; t += 32) Ab[t] = 0.0f;
-        for (int t = lane; t < nI; t += 32) cv[t] = 0.0f;
+        // ---- the new columns' rows of A, the shadow rows they add (checked against lmax
+        // before anything of the current factorisation changes).  In u_f = half every
+        // pass starts afresh instead, with Abar's rows in ascending order: half rounding
+        // is coarse enough that another operation order (the updated factors' or the
+        // rows' order of arrival) moves many near-tied picks against the fp64 scoring.
+        const int q0 = HALF ? 0 : nJ_old;  // first column gathered (and factored) in this pass
+        const int Lg = HALF ? 0 : L;       // its first entry
+        const int Ln = gather_new_rows(J, q0, nJ, Lg, arp, acol, bval, rbeg, eoff, ecol, eq, eval, lane);
+        // half: the whole shadow, ascending, into I (new: its rows beyond the old ones)
+        const int nnew = HALF ? new_shadow_rows(ecol, 0, Ln, Is, 0, keys, I, lmax, lane) - nI
+                              : new_shadow_rows(ecol, Lg, Ln, Is, nI, keys, I + nI, lmax - nI, lane);
+        if (nI + nnew > lmax) {  // never on the first pass: rowmax <= lmax (host check)
+            if (redo_list && nI + nnew <= cap_rows) redo = true;
+            else capped = true;
+            // the columns of this pass are not taken (in half they were merged into J:
+            // they are the ones added for this step)
+            if (HALF && lane == 0) {
+                int w = 0;
+                for (int q = 0; q < nJ; ++q)
+                    if (stp[q] != step) {
+                        J[w] = J[q];
+                        stp[w] = stp[q];
+                        ++w;
+                    }
+            }
+            __syncwarp();
+            nJ = nJ_old;
+            break;
+        }
+        const int nIn = nI + nnew;
+        if (HALF) {  // Abar's rows ascending: I is the sorted shadow
+            for (int u = lane; u < nIn; u += 32) {
+                Is[u] = I[u];
+                Ip[u] = u;
+            }
+            __syncwarp();
+        } else {
+            // merge the new rows (I[nI, nIn), ascending) into Is / Ip, through keys and acc
+            int* mIs = keys;
+            int* mIp = reinterpret_cast<int*>(acc);
+            for (int u = lane; u < nI; u += 32) {
+                const int pos = u + lb_i32(I + nI, nnew, Is[u]);
+                mIs[pos] = Is[u];
+                mIp[pos] = Ip[u];
+            }
+            for (int m = lane; m < nnew; m += 32) {
+                const int pos = m + lb_i32(Is, nI, I[nI + m]);
+                mIs[pos] = I[nI + m];
+                mIp[pos] = nI + m;
+            }
+            __syncwarp();
+            for (int u = lane; u < nIn; u += 32) {
+                Is[u] = mIs[u];
+                Ip[u] = mIp[u];
+            }
+            __syncwarp();  // (mIp lives in acc: every entry is read before any is cleared)
+            for (int u = lane; u < nIn; u += 32) {
+                mIs[u] = -1;
+                acc[u] = 0;
+            }
+            __syncwarp();
+        }
+        // the new entries' rows in Abar
+        for (int t = Lg + lane; t < Ln; t += 32) ecol[t] = Ip[lb_i32(Is, nIn, ecol[t])];
+        // ---- Abar grows: the old columns' new rows, the new columns, ebar's new rows
+        // (in half: all of Abar and ebar anew)
+        const int ld = lmax;
+        const int c0 = q0;                // first column factored in this pass
+        const int r0 = HALF ? 0 : nI;     // first row of ebar set in this pass
+        const int e0 = Lg;                // first entry scattered in this pass
+        for (int t = lane; t < c0 * nnew; t += 32) Ab[(t / nnew) * ld + nI + t % nnew] = 0.0f;
+        for (int t = lane; t < (nJ - c0) * nIn; t += 32) Ab[(c0 + t / nIn) * ld + t % nIn] = 0.0f;
+        for (int t = r0 + lane; t < nIn; t += 32) cv[t] = 0.0f;
         __syncwarp();
-        const int pk = lb_i32(I, nI, (int)k);
-        const bool k_in = pk < nI && I[pk] == (int)k;
-        if (lane == 0 && k_in) cv[pk] = 1.0f;
-        for (int t = lane; t < L; t += 32) {
-            const int p = lb_i32(I, nI, ecol[t]);
-            ecol[t] = p;  // from here on: the entry's row in Abar
-            Ab[eq[t] * nI + p] = eval[t];
+        const int uk = lb_i32(Is, nIn, (int)k);
+        const bool k_in = uk < nIn && Is[uk] == (int)k;
+        const int pk = k_in ? Ip[uk] : nIn;
+        if (lane == 0 && k_in && pk >= r0) cv[pk] = 1.0f;  // ebar's new rows: zero but for k
+        float f2 = 0.0f;
+        for (int t = e0 + lane; t < Ln; t += 32) {
+            Ab[eq[t] * ld + ecol[t]] = eval[t];
+            if (!HALF) f2 = F::add(f2, F::mul(eval[t], eval[t]));
         }
         __syncwarp();
+        if (HALF) {  // ||Abar||_F column by column, as a fresh factorisation forms it
+            for (int t = lane; t < nJ * nIn; t += 32) {
+                const float a = Ab[(t / nIn) * ld + t % nIn];
+                f2 = F::add(f2, F::mul(a, a));
+            }
+            fro2 = F::wsum(f2);
+        } else {
+            fro2 = F::add(fro2, F::wsum(f2));
+        }
+        nI = nIn;
+        L = Ln;
+        max_rows = max(max_rows, nI);
         rankdef = nI < nJ;
-        float fro = 0.0f;
-        for (int t = lane; t < nJ * nI; t += 32) fro = F::add(fro, F::mul(Ab[t], Ab[t]));
-        fro = F::sqrt(F::wsum(fro));
-        // Householder QR with the sign choice v_1 = x_1 + sign(x_1) ||x||, applied
-        // to ebar as well; warp-shuffle reductions for every norm and product
-        for (int c = 0; c < nJ && !rankdef; ++c) {
-            float* col_c = Ab + c * nI;
+        const float fro = F::sqrt(fro2);
+        // the old reflectors (zero on the new rows) on the new columns
+        for (int c = 0; c < c0 && !rankdef; ++c) {
+            const float* col_c = Ab + c * ld;
+            const float twoinv = tw[c];
+            for (int cc = c0; cc < nJ; ++cc) {
+                float* tgt = Ab + cc * ld;
+                float dot = 0.0f;
+                for (int p = c + lane; p < nI; p += 32) dot = F::add(dot, F::mul(col_c[p], tgt[p]));
+                dot = F::wsum(dot);
+                const float tau = F::mul(dot, twoinv);
+                for (int p = c + lane; p < nI; p += 32) tgt[p] = F::sub(tgt[p], F::mul(tau, col_c[p]));
+                __syncwarp();
+            }
+        }
+        // Householder QR of the new columns below the old ones, with the sign choice
+        // v_1 = x_1 + sign(x_1) ||x||, applied to ebar as well; warp-shuffle reductions
+        for (int c = c0; c < nJ && !rankdef; ++c) {
+            float* col_c = Ab + c * ld;
             float s2 = 0.0f;
             for (int p = c + lane; p < nI; p += 32) s2 = F::add(s2, F::mul(col_c[p], col_c[p]));
             s2 = F::wsum(s2);
@@ -314,10 +430,13 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             const float vtv = F::mul(F::mul(2.0f, sig), F::add(sig, fabsf(x0)));
             const float twoinv = F::div(2.0f, vtv);
             __syncwarp();
-            if (lane == 0) col_c[c] = v0;
+            if (lane == 0) {
+                col_c[c] = v0;
+                tw[c] = twoinv;
+            }
             __syncwarp();
             for (int cc = c + 1; cc <= nJ; ++cc) {
-                float* tgt = cc < nJ ? Ab + cc * nI : cv;
+                float* tgt = cc < nJ ? Ab + cc * ld : cv;
                 float dot = 0.0f;
                 for (int p = c + lane; p < nI; p += 32) dot = F::add(dot, F::mul(col_c[p], tgt[p]));
                 dot = F::wsum(dot);
@@ -330,12 +449,13 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             if (!(fabsf(rcc) > (float)nI * u_f * fro)) rankdef = true;
         }
         __syncwarp();
+        nJ_old = nJ;
         ++solves;
         if (rankdef) break;
         if (lane == 0) {
             for (int c = nJ - 1; c >= 0; --c) {
                 float s = cv[c];
-                for (int cc = c + 1; cc < nJ; ++cc) s = F::sub(s, F::mul(Ab[cc * nI + c], mv[cc]));
+                for (int cc = c + 1; cc < nJ; ++cc) s = F::sub(s, F::mul(Ab[cc * ld + c], mv[cc]));
                 mv[c] = F::div(s, rdiag[c]);
             }
         }
@@ -396,21 +516,18 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
         }
         __syncwarp();
         if (__any_sync(0xffffffffu, full)) {  // first tier only: the second's H exceeds every candidate count
-            for (int t = lane; t < H; t += 32) {
-                tab[t] = -1;
-                acc[t] = 0;
-            }
             if (redo_list) redo = true;
             else capped = true;
             break;
         }
-        // ---- rho per candidate while the table is emptied into keys/rho, and the
-        // mean of rho (<= ||sbar|| <= 1) as a fixed-point sum
+        // ---- rho per candidate while the table is emptied into keys/rho (in place: a
+        // candidate moves to a slot at or below its own, read before any write), and
+        // the mean of rho (<= ||sbar|| <= 1) as a fixed-point sum
         int nc = 0;
         long long rsum = 0;
         for (int b0 = 0; b0 < H; b0 += 32) {
             const int v = tab[b0 + lane];
-            const bool flag = v >= 0 && !contains(J, nJ, v);
+            const bool flag = v >= 0 && !contains(Js, nJ, v);
             float rj = 0.0f;
             long long av = 0;
             if (v >= 0) {
@@ -433,6 +550,7 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
                 rho[o] = rj;
             }
             nc += __popc(m);
+            __syncwarp();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
@@ -472,9 +590,19 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
             ++npick;
             __syncwarp();
         }
+        // the table's storage back to empty for the next pass
+        for (int t = lane; t < nc; t += 32) {
+            keys[t] = -1;
+            acc[t] = 0;
+        }
+        __syncwarp();
         if (npick == 0) break;
-        // ---- J u picks, ascending (lane 0; at most jmax + beta entries)
-        int nJn = 0;
+        if (nJ + npick > jmax) {  // only the first tier's jmax is below 1 + alpha beta
+            if (redo_list) redo = true;
+            else capped = true;
+            break;
+        }
+        // ---- the picks join J (ascending among themselves) and Js
         if (lane == 0) {
             for (int a = 1; a < npick; ++a) {  // insertion sort of the picks
                 const int v = picks[a];
@@ -485,48 +613,54 @@ __global__ void __launch_bounds__(256, 3) k_spai_adaptive(
                 }
                 picks[b + 1] = v;
             }
-            int a = 0, b = 0;
-            while ((a < nJ || b < npick) && nJn < jmax) {
-                if (b >= npick || (a < nJ && J[a] < picks[b])) {
-                    Jn[nJn] = J[a];
-                    stpn[nJn++] = stp[a++];
+            for (int a = 0; a < npick; ++a) {
+                if (HALF) {  // J ascending (every pass factors afresh, columns in this order)
+                    int b = nJ + a - 1;
+                    while (b >= 0 && J[b] > picks[a]) {
+                        J[b + 1] = J[b];
+                        stp[b + 1] = stp[b];
+                        --b;
+                    }
+                    J[b + 1] = picks[a];
+                    stp[b + 1] = step + 1;
                 } else {
-                    Jn[nJn] = picks[b++];
-                    stpn[nJn++] = step + 1;
+                    J[nJ + a] = picks[a];
+                    stp[nJ + a] = step + 1;
                 }
+                int b = nJ + a - 1;  // insertion into the sorted copy
+                while (b >= 0 && Js[b] > picks[a]) {
+                    Js[b + 1] = Js[b];
+                    --b;
+                }
+                Js[b + 1] = picks[a];
             }
-            if (a < nJ || b < npick) nJn = jmax + 1;  // would not fit
-        }
-        nJn = __shfl_sync(0xffffffffu, nJn, 0);
-        __syncwarp();
-        if (nJn > jmax) {  // only the first tier's jmax is below 1 + alpha beta
-            if (redo_list) redo = true;
-            else capped = true;
-            break;
-        }
-        const int Ln = gather_rows(Jn, nJn, arp, acol, bval, rbeg, eoff, ecol, eq, eval, lane);
-        const int nIn = shadow_rows(ecol, Ln, keys, I, lmax, lane);
-        if (nIn > lmax) {
-            if (redo_list && nIn <= cap_rows) redo = true;
-            else capped = true;
-            break;
-        }
-        for (int q = lane; q < nJn; q += 32) {
-            J[q] = Jn[q];
-            stp[q] = stpn[q];
         }
         __syncwarp();
-        nJ = nJn;
-        L = Ln;
-        nI = nIn;
-        max_rows = max(max_rows, nI);
+        nJ += npick;
     }
     if (redo) {
         if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = (int32_t)k;
         return;
     }
     if (rankdef) res_norm = 1.0f;
-    // M[k, J[q]] = mbar_q d_J[q]  (M = M'^T D)
+    // M[k, J[q]] = mbar_q d_J[q]  (M = M'^T D), the columns in ascending order
+    if (lane == 0) {
+        for (int a = 1; a < nJ; ++a) {
+            const int v = J[a], sa = stp[a];
+            const float ma = mv[a];
+            int b = a - 1;
+            while (b >= 0 && J[b] > v) {
+                J[b + 1] = J[b];
+                stp[b + 1] = stp[b];
+                mv[b + 1] = mv[b];
+                --b;
+            }
+            J[b + 1] = v;
+            stp[b + 1] = sa;
+            mv[b + 1] = ma;
+        }
+    }
+    __syncwarp();
     for (int q = lane; q < nJ; q += 32) {
         const int j = J[q];
         const int64_t o = (int64_t)q * n + k;
@@ -765,6 +899,9 @@ int bspai_build_adaptive(const bspai_csr_t* A, double spai_eps, int32_t alpha, i
         t.cmax = (int)(c < n ? c : n);
         t.H = pow2_len(t.cmax, true);  // more slots than candidates: no insertion can fail
         if (hcap > 0 && t.H > hcap) t.H = hcap;  // first tier: a full table reruns the column
+        // the table's storage is also the shadow sort's and the row merge's scratch
+        if (t.H < t.lp2) t.H = t.lp2;
+        if (t.H < lm) t.H = pow2_len(lm, false);
         t.per_warp = adaptive_layout(t.jmax, t.lmax, t.gmax, t.lp2, t.H).total;
         t.warps = 8;
         while (t.warps > 1 && t.per_warp * t.warps > smem_cap) t.warps >>= 1;
