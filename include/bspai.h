@@ -554,7 +554,8 @@ int bspai_batch_tune_table(bspai_batch_schedule_t* sched, float* ms, int32_t cap
  * candidates on a sample run (the largest pairs, four per SM, 32 Arnoldi
  * steps) in a staged search -- CTA size, then the MGS tile, then z in shared
  * memory, then the bucket schedule, then team mode at 8192 and 4096 rows per
- * CTA (u_g = FP32) -- and cached per shape.  The operations of one refinement
+ * CTA (u_g = FP32; tried only when the batch needs at most two team sizes) --
+ * and cached per shape.  The operations of one refinement
  * step (residuals, tests, the GMRES launches, tests) are captured once into a
  * CUDA graph and replayed for every step (launched directly while
  * kernel-class profiling is on, or if the capture fails).  A team exchange

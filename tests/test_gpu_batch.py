@@ -214,7 +214,8 @@ def test_batch_autotuner_picks_the_fastest_candidate(B):
     g = _gpu_batch(B, bw)
     info = g["info"]
     tab = B.batch_tune_table()
-    assert info["tuned_candidates"] == len(tab) >= 7, (info, tab)
+    assert info["tuned_candidates"] == len(tab) >= 5, (info, tab)
+    # sizes 200 .. 3000: one team size at 8,192 and 4,096 rows, so team mode is a candidate
     assert {t["team_rows"] for t in tab} >= {0, 8192, 4096}
     assert all(t["ms"] > 0 for t in tab)
     assert {t["block_threads"] for t in tab} >= {128, 256, 512}
