@@ -980,9 +980,13 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
     S.relres = S.dprev + npairs;
     S.nbe = S.relres + npairs;
     S.anorm = S.nbe + npairs + npairs;  // one spare slot of npairs
-    CUDA_TRY(cudaMemcpyAsync(d_order, hord.data(), sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(S.status, 0, sizeof(int32_t) * npairs * 3, s));
-    CUDA_TRY(cudaMemsetAsync(S.rmax, 0, sizeof(double) * ((size_t)npairs * 9 + nsys), s));
+    {
+        // (failures release the buffers taken so far)
+        cudaError_t e0 = cudaMemcpyAsync(d_order, hord.data(), sizeof(int32_t) * npairs, cudaMemcpyHostToDevice, s);
+        if (!e0) e0 = cudaMemsetAsync(S.status, 0, sizeof(int32_t) * npairs * 3, s);
+        if (!e0) e0 = cudaMemsetAsync(S.rmax, 0, sizeof(double) * ((size_t)npairs * 9 + nsys), s);
+        if (e0) return done(cuda_error(e0, "batch state", __FILE__, __LINE__));
+    }
     {
         ProfScope ps(BSPAI_K_OTHER, s);
         k_slice_seg_b<<<(unsigned)ceil_div(nsys, 256), 256, 0, s>>>(nsys, row_off, d_seg);
@@ -996,7 +1000,10 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
             k_pair_bmax<<<(unsigned)ceil_div((int64_t)n * nrhs, 256), 256, 0, s>>>(n, nrhs, nsys, Bv, d_seg, S.bmax);
             note_launch();
         }
-        CUDA_LAUNCH_CHECK();
+        {
+            const cudaError_t e0 = cudaGetLastError();
+            if (e0) return done(cuda_error(e0, "batch set-up kernels", __FILE__, __LINE__));
+        }
         // x0 = M b in u_f for every right-hand side (Alg 3.1)
         if (!o.x0_given)
             for (int r = 0; r < nrhs; ++r)
