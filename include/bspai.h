@@ -510,10 +510,12 @@ typedef struct {
  *   team_rows      0: one CTA per pair (the four fields above).  Otherwise
  *                  (u_g = FP32 only; a multiple of 1024, at most 8192) team
  *                  mode: a pair of n_s rows runs on a team of
- *                  ceil(n_s / team_rows) 512-thread CTAs (at most 32) of a
- *                  cooperative launch, one launch per run of equal team size,
- *                  each CTA holding its rows of z and of the basis vectors of
- *                  the current MGS pass in registers; the dot products sum a
+ *                  ceil(n_s / team_rows) 512-thread CTAs (at most 32) of one
+ *                  cooperative launch in which every team size has a group of
+ *                  CTAs in proportion to the sum of n_s^2 of its pairs (a team
+ *                  whose group has no pair left takes pairs of the groups of
+ *                  smaller pairs), each CTA holding its rows of z and of the
+ *                  basis vectors of the current MGS pass in registers; the dot products sum a
  *                  thread's rows, the CTA's threads, then the team's CTAs in
  *                  rank order (other bits than the one-CTA schedules, the same
  *                  in every run).  The other fields are then ignored. */
@@ -549,13 +551,12 @@ int bspai_batch_tune_table(bspai_batch_schedule_t* sched, float* ms, int32_t cap
  * A v in u_p, bucketed M v, Givens in fp64).  Each refinement step of the
  * batch is one persistent launch in which a CTA takes pairs, largest systems
  * first, and runs each GMRES with CTA barriers only -- or, in team mode, one
- * cooperative launch per run of pairs of equal team size, teams of CTAs taking
- * pairs.  The schedule (bspai_batch_schedule_t) is chosen by timing
+ * cooperative launch in which teams of CTAs take pairs.  The schedule (bspai_batch_schedule_t) is chosen by timing
  * candidates on a sample run (the largest pairs, four per SM, 32 Arnoldi
  * steps) in a staged search -- CTA size, then the MGS tile, then z in shared
  * memory, then the bucket schedule, then team mode at 8192 and 4096 rows per
- * CTA (u_g = FP32; tried only when the batch needs at most two team sizes) --
- * and cached per shape.  The operations of one refinement
+ * CTA (u_g = FP32; tried only when every pair takes the same team size) -- and
+ * cached per shape.  The operations of one refinement
  * step (residuals, tests, the GMRES launches, tests) are captured once into a
  * CUDA graph and replayed for every step (launched directly while
  * kernel-class profiling is on, or if the capture fails).  A team exchange

@@ -384,25 +384,38 @@ constexpr int kTeamP = 8;      // row pairs per thread: at most 8,192 rows of a 
                                // (16 pairs, as the single-system kernel holds, spill registers here)
 constexpr int kTeamMaxG = 32;  // CTAs of one team (one polling lane each)
 
+// One group of the launch: the pairs of one team size (a run of the
+// size-sorted order) and the CTAs given to them, with the group's share of the
+// workspace
+struct TeamGroup {
+    int G;        // CTAs per team
+    int begin;    // first pair of the run in the order
+    int count;    // its pairs
+    int cta0;     // first CTA of the group
+    int nteams;   // its teams
+    int64_t ldv;  // rows of a vector (largest system of the run, rounded up to 64)
+    int64_t voff, woff, hoff, soff, toff;  // the group's first team in V, W / Z, H, S, tags
+};
+constexpr int kTeamMaxGroups = 32;
+
 struct TeamArgs {
     BMDev Av, Mv;
     const int32_t* row_off;
     int nsys, n;
-    const int32_t* order;  // this launch's pairs (a run of the size-sorted order)
-    int npairs;
-    int* queue;
+    const int32_t* order;  // the size-sorted pairs (each group takes a run)
+    int* queue;            // one per group
     const int32_t* status;
     const double* R;
     double* X;
     float* V;  // per team: ldv x (kmax + 1)
     float* W;  // per team: ldv (A v)
     float* Z;  // per team: ldv (s = M r, then M w)
-    int64_t ldv;
     double* H;  // per team: (kmax + 1) x kmax
     double* S;  // per team: cs, sn, g, y (kmax + 2 each)
     int kmax;
     double tau;
-    int G;
+    int ngroups;
+    TeamGroup grp[kTeamMaxGroups];
     unsigned long long* tags;  // per team: 2 sets x G slots x 2 words
     GridBar* bar;              // err: a team exchange timed out
     unsigned long long tmo;
@@ -610,27 +623,42 @@ __global__ void __launch_bounds__(kTeamBD, 1) k_gmres_team(const __grid_constant
     __shared__ int s_ok, s_p, s_done;
     __shared__ double s_res;
     const int tid = threadIdx.x;
-    const int G = a.G, team = blockIdx.x / G, rank = blockIdx.x - team * G;
+    // this CTA's group, team and rank
+    int gi = 0;
+    while (gi + 1 < a.ngroups && (int)blockIdx.x >= a.grp[gi + 1].cta0) ++gi;
+    const TeamGroup& gr = a.grp[gi];
+    const int G = gr.G;
+    const int local = (int)blockIdx.x - gr.cta0;
+    if (local >= gr.nteams * G) return;  // (a CTA past the groups' teams: none is launched)
+    const int team = local / G, rank = local - team * G;
     const int kmax = a.kmax;
-    const int64_t ldv = a.ldv;
-    float* V = a.V + (int64_t)team * ldv * (kmax + 1);
-    float* W = a.W + (int64_t)team * ldv;
-    float* Z = a.Z + (int64_t)team * ldv;
-    double* H = a.H + (int64_t)team * (kmax + 1) * kmax;
-    double* cs = a.S + (int64_t)team * 4 * (kmax + 2);
+    const int64_t ldv = gr.ldv;
+    float* V = a.V + gr.voff + (int64_t)team * ldv * (kmax + 1);
+    float* W = a.W + gr.woff + (int64_t)team * ldv;
+    float* Z = a.Z + gr.woff + (int64_t)team * ldv;
+    double* H = a.H + gr.hoff + (int64_t)team * (kmax + 1) * kmax;
+    double* cs = a.S + gr.soff + (int64_t)team * 4 * (kmax + 2);
     double* sn = cs + (kmax + 2);
     double* g = sn + (kmax + 2);
     double* y = g + (kmax + 2);
-    TeamSync ts{a.tags + (int64_t)team * 4 * G, a.bar, a.tmo, G, rank, 0u};
+    TeamSync ts{a.tags + gr.toff + (int64_t)team * 4 * G, a.bar, a.tmo, G, rank, 0u};
     const float2 zero2 = make_float2(0.0f, 0.0f);
+    // the team's own group first, then (its queue empty) the groups of smaller pairs:
+    // their systems fit the team's workspace and its CTAs, and no team idles while
+    // pairs are left
+    int qg = gi;
     while (true) {
         // the next pair: rank 0 takes it from the queue, the team learns it by an exchange
-        if (rank == 0 && tid == 0) s_p = atomicAdd(a.queue, 1);
+        if (rank == 0 && tid == 0) s_p = atomicAdd(a.queue + qg, 1);
         __syncthreads();
         team_arrive<float, 0, false>(ts, (rank == 0 && tid == 0) ? (float)s_p : 0.0f, s_wf, &s_totf);
         const int p = (int)team_wait<float, 0, false>(ts, &s_totf, &s_ok);
-        if (!s_ok || p >= a.npairs) return;
-        const int pair = a.order[p];
+        if (!s_ok) return;
+        if (p >= a.grp[qg].count) {
+            if (++qg >= a.ngroups) return;
+            continue;
+        }
+        const int pair = a.order[a.grp[qg].begin + p];
         if (a.status[pair] != 0) continue;
         const int rhs = pair / a.nsys, sys = pair - rhs * a.nsys;
         const int r0 = a.row_off[sys], ns = a.row_off[sys + 1] - r0;
@@ -651,7 +679,7 @@ __global__ void __launch_bounds__(kTeamBD, 1) k_gmres_team(const __grid_constant
             if (2 * q + 1 < nb) *reinterpret_cast<float2*>(p2) = v;
             else *p2 = v.x;
         };
-        float2 zr[P], vcur[P], vnext[P];
+        float2 zr[P];
         // s = M r (Alg 2.3) in u_g; beta = ||s||_2
         team_rows<double, false>(a.Mv, r0, lo, hi, rr, Z);
         __syncthreads();
@@ -1119,11 +1147,10 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         return cudaGetLastError();
     };
     // ---- team mode (u_g = fp32): the size-sorted pairs split into runs of equal team
-    // size G = ceil(n_s / team_rows); one cooperative launch per run, largest first
-    struct TeamPhase {
-        int G, begin, count, grid;
-        int64_t ldv;
-    };
+    // size G = ceil(n_s / team_rows); all runs at once in one cooperative launch (several
+    // launches only if the runs' smallest teams do not fit the GPU together), each run a
+    // group of CTAs in proportion to its MGS work, estimated as the sum of n_s^2 (GMRES
+    // steps grow with the grid size, and an MGS pass reads n_s rows)
     const int team_cands[2] = {kTeamP * 2 * kTeamBD, kTeamP * kTeamBD};  // 8,192 and 4,096 rows
     const size_t team_smem = sizeof(float) * (size_t)(kmax + 1);
     int occ_team = 0;
@@ -1139,82 +1166,169 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
                                                                     team_smem);
         if (e0) return done(cuda_error(e0, "team kernel occupancy", __FILE__, __LINE__));
     }
-    const int team_slots = sms * (occ_team > 0 ? occ_team : 1);  // co-resident CTAs of a team launch
+    int team_slots = sms * (occ_team > 0 ? occ_team : 1);  // co-resident CTAs of a team launch
+    if (o.max_blocks > 0 && team_slots > o.max_blocks) team_slots = o.max_blocks;
     auto sys_rows = [&](int pair) { return hoff[pair % nsys + 1] - hoff[pair % nsys]; };
-    auto plan_teams = [&](int tr, int np, std::vector<TeamPhase>& ph) {
-        ph.clear();
-        int b = 0;
-        while (b < np) {
-            auto gof = [&](int pr) {
-                const int gg = (sys_rows(pr) + tr - 1) / tr;
-                return gg < 1 ? 1 : (gg > kTeamMaxG ? kTeamMaxG : gg);
-            };
+    struct TeamLaunch {
+        std::vector<TeamGroup> g;
+        int grid = 0;
+    };
+    // the launches (normally one) of team mode over the first np pairs; workspace offsets
+    // for kcap Arnoldi steps
+    auto plan_teams = [&](int tr, int np, int kcap, std::vector<TeamLaunch>& out) {
+        out.clear();
+        struct Run {
+            int G, begin, count;
+            int64_t ldv;
+            double w;
+        };
+        std::vector<Run> runs;
+        auto gof = [&](int pr) {
+            const int gg = (sys_rows(pr) + tr - 1) / tr;
+            return gg < 1 ? 1 : (gg > kTeamMaxG ? kTeamMaxG : gg);
+        };
+        for (int b = 0; b < np;) {
             const int G = gof(hord[b]);
-            int e = b;
-            int nsmax = 0;
+            int e = b, nsmax = 0;
+            double w = 0.0;
             while (e < np && gof(hord[e]) == G) {
-                nsmax = sys_rows(hord[e]) > nsmax ? sys_rows(hord[e]) : nsmax;
+                const double ns = (double)sys_rows(hord[e]);
+                nsmax = (int)ns > nsmax ? (int)ns : nsmax;
+                w += ns * ns;
                 ++e;
             }
-            int nt = team_slots / G;
-            if (o.max_blocks > 0 && nt > o.max_blocks / G) nt = o.max_blocks / G;
-            if (nt > e - b) nt = e - b;
-            if (nt < 1) nt = 1;
-            ph.push_back(TeamPhase{G, b, e - b, nt * G, ceil_div(nsmax > 0 ? nsmax : 1, 64) * 64});
+            runs.push_back(Run{G, b, e - b, ceil_div(nsmax > 0 ? nsmax : 1, 64) * 64, w > 0.0 ? w : 1.0});
             b = e;
         }
+        // pack the runs into launches whose one-team-each minimum fits the slots
+        size_t r0 = 0;
+        while (r0 < runs.size()) {
+            size_t r1 = r0;
+            int need = 0;
+            while (r1 < runs.size() && r1 - r0 < (size_t)kTeamMaxGroups && need + runs[r1].G <= team_slots)
+                need += runs[r1++].G;
+            if (r1 == r0) ++r1;  // a single run wider than the slots cannot occur (G <= 32 < slots)
+            double wsum = 0.0;
+            for (size_t r = r0; r < r1; ++r) wsum += runs[r].w;
+            std::vector<int> nt(r1 - r0);
+            int used = 0;
+            for (size_t r = r0; r < r1; ++r) {
+                int t = (int)((runs[r].w / wsum) * team_slots / runs[r].G);
+                t = t < 1 ? 1 : t;
+                t = t > runs[r].count ? runs[r].count : t;
+                nt[r - r0] = t;
+                used += t * runs[r].G;
+            }
+            while (used > team_slots) {  // too many: take teams from the most generously served run
+                size_t best = r1;
+                double bv = -1.0;
+                for (size_t r = r0; r < r1; ++r)
+                    if (nt[r - r0] > 1 && nt[r - r0] * runs[r].G / runs[r].w > bv) {
+                        bv = nt[r - r0] * runs[r].G / runs[r].w;
+                        best = r;
+                    }
+                if (best == r1) break;
+                --nt[best - r0];
+                used -= runs[best].G;
+            }
+            while (true) {  // CTAs left over: a team more for the most poorly served run that fits
+                size_t best = r1;
+                double bv = 1e300;
+                for (size_t r = r0; r < r1; ++r)
+                    if (nt[r - r0] < runs[r].count && used + runs[r].G <= team_slots &&
+                        nt[r - r0] * runs[r].G / runs[r].w < bv) {
+                        bv = nt[r - r0] * runs[r].G / runs[r].w;
+                        best = r;
+                    }
+                if (best == r1) break;
+                ++nt[best - r0];
+                used += runs[best].G;
+            }
+            TeamLaunch L;
+            int64_t voff = 0, woff = 0, hoffs = 0, soff = 0, toff = 0;
+            for (size_t r = r0; r < r1; ++r) {
+                TeamGroup gg;
+                gg.G = runs[r].G;
+                gg.begin = runs[r].begin;
+                gg.count = runs[r].count;
+                gg.cta0 = L.grid;
+                gg.nteams = nt[r - r0];
+                gg.ldv = runs[r].ldv;
+                gg.voff = voff;
+                gg.woff = woff;
+                gg.hoff = hoffs;
+                gg.soff = soff;
+                gg.toff = toff;
+                voff += (int64_t)gg.nteams * gg.ldv * (kcap + 1);
+                woff += (int64_t)gg.nteams * gg.ldv;
+                hoffs += (int64_t)gg.nteams * (kcap + 1) * kcap;
+                soff += (int64_t)gg.nteams * 4 * (kcap + 2);
+                toff += (int64_t)gg.nteams * 4 * gg.G;
+                L.grid += gg.nteams * gg.G;
+                L.g.push_back(gg);
+            }
+            out.push_back(L);
+            r0 = r1;
+        }
     };
-    // workspace for every candidate's largest run
-    int64_t tv_rows = 0;
-    int tmax_teams = 0, tmax_grid = 0;
-    std::vector<TeamPhase> phs;
+    // workspace: the largest launch of every candidate, over the whole batch and the
+    // tuning sample
+    int64_t tv = 0, tw = 0, th = 0, tsd = 0;
+    int tgrid = 0;
+    auto need_ws = [&](int tr, int np) {
+        std::vector<TeamLaunch> ls;
+        plan_teams(tr, np, kmax, ls);
+        for (const TeamLaunch& L : ls) {
+            int64_t v = 0, w = 0, h = 0, sd = 0;
+            for (const TeamGroup& gg : L.g) {
+                v += (int64_t)gg.nteams * gg.ldv * (kmax + 1);
+                w += (int64_t)gg.nteams * gg.ldv;
+                h += (int64_t)gg.nteams * (kmax + 1) * kmax;
+                sd += (int64_t)gg.nteams * 4 * (kmax + 2);
+            }
+            tv = v > tv ? v : tv;
+            tw = w > tw ? w : tw;
+            th = h > th ? h : th;
+            tsd = sd > tsd ? sd : tsd;
+            tgrid = L.grid > tgrid ? L.grid : tgrid;
+        }
+    };
+    const int np_sample = npairs < 4 * sms ? npairs : 4 * sms;  // the tuner's sample (below)
     if (occ_team > 0) {
         for (int tr : team_cands) {
-            plan_teams(tr, npairs, phs);
-            for (const TeamPhase& ph : phs) {
-                const int nt = ph.grid / ph.G;
-                tv_rows = (int64_t)nt * ph.ldv > tv_rows ? (int64_t)nt * ph.ldv : tv_rows;
-                tmax_teams = nt > tmax_teams ? nt : tmax_teams;
-                tmax_grid = ph.grid > tmax_grid ? ph.grid : tmax_grid;
-            }
+            need_ws(tr, npairs);
+            need_ws(tr, np_sample);
         }
-        if (t_forced && sch.team > 0) {
-            plan_teams(sch.team, npairs, phs);
-            for (const TeamPhase& ph : phs) {
-                const int nt = ph.grid / ph.G;
-                tv_rows = (int64_t)nt * ph.ldv > tv_rows ? (int64_t)nt * ph.ldv : tv_rows;
-                tmax_teams = nt > tmax_teams ? nt : tmax_teams;
-                tmax_grid = ph.grid > tmax_grid ? ph.grid : tmax_grid;
-            }
-        }
+        if (t_forced && sch.team > 0) need_ws(sch.team, npairs);
     }
     float *TV = nullptr, *TW = nullptr, *TZ = nullptr;
     double *TH = nullptr, *TS = nullptr;
     unsigned long long* Ttags = nullptr;
     GridBar* Tbar = nullptr;
-    int* d_tq = nullptr;  // one queue per run
+    int* d_tq = nullptr;  // one queue per group
     if (occ_team > 0) {
-        if ((rc = take((void**)&TV, sizeof(float) * (size_t)tv_rows * (kmax + 1)))) return done(rc);
-        if ((rc = take((void**)&TW, sizeof(float) * (size_t)tv_rows))) return done(rc);
-        if ((rc = take((void**)&TZ, sizeof(float) * (size_t)tv_rows))) return done(rc);
-        if ((rc = take((void**)&TH, sizeof(double) * (size_t)tmax_teams * (kmax + 1) * kmax))) return done(rc);
-        if ((rc = take((void**)&TS, sizeof(double) * (size_t)tmax_teams * 4 * (kmax + 2)))) return done(rc);
-        if ((rc = take((void**)&Ttags, sizeof(unsigned long long) * 4 * (size_t)tmax_grid))) return done(rc);
+        if ((rc = take((void**)&TV, sizeof(float) * (size_t)tv))) return done(rc);
+        if ((rc = take((void**)&TW, sizeof(float) * (size_t)tw))) return done(rc);
+        if ((rc = take((void**)&TZ, sizeof(float) * (size_t)tw))) return done(rc);
+        if ((rc = take((void**)&TH, sizeof(double) * (size_t)th))) return done(rc);
+        if ((rc = take((void**)&TS, sizeof(double) * (size_t)tsd))) return done(rc);
+        if ((rc = take((void**)&Ttags, sizeof(unsigned long long) * 4 * (size_t)tgrid))) return done(rc);
         if ((rc = take((void**)&Tbar, sizeof(GridBar)))) return done(rc);
-        if ((rc = take((void**)&d_tq, sizeof(int) * (kTeamMaxG + 1)))) return done(rc);
+        if ((rc = take((void**)&d_tq, sizeof(int) * kTeamMaxGroups))) return done(rc);
         cudaError_t e0 = cudaMemsetAsync(Tbar, 0, sizeof(GridBar), s);
         if (e0) return done(cuda_error(e0, "memset", __FILE__, __LINE__));
     }
     const unsigned long long team_tmo =
         (unsigned long long)((o.barrier_timeout_s > 0 ? o.barrier_timeout_s : 2.0) * 1e9);
-    // the runs of one team-mode GMRES launch over the first np pairs of the order
+    // team mode's launches over the first np pairs of the order
     auto launch_team = [&](int tr, int np, const double* Rin, double* Xout, int kcap, double tcap, PairState& St,
                            cudaStream_t st) -> cudaError_t {
-        std::vector<TeamPhase> ph;
-        plan_teams(tr, np, ph);
-        cudaError_t e = cudaMemsetAsync(d_tq, 0, sizeof(int) * (kTeamMaxG + 1), st);
-        for (size_t i = 0; !e && i < ph.size(); ++i) {
-            e = cudaMemsetAsync(Ttags, 0, sizeof(unsigned long long) * 4 * (size_t)ph[i].grid, st);
+        std::vector<TeamLaunch> ls;
+        plan_teams(tr, np, kcap, ls);
+        cudaError_t e = cudaSuccess;
+        for (size_t i = 0; !e && i < ls.size(); ++i) {
+            e = cudaMemsetAsync(d_tq, 0, sizeof(int) * kTeamMaxGroups, st);
+            if (!e) e = cudaMemsetAsync(Ttags, 0, sizeof(unsigned long long) * 4 * (size_t)ls[i].grid, st);
             if (e) break;
             TeamArgs ta;
             ta.Av = Av;
@@ -1222,21 +1336,20 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
             ta.row_off = row_off;
             ta.nsys = nsys;
             ta.n = n;
-            ta.order = d_order + ph[i].begin;
-            ta.npairs = ph[i].count;
-            ta.queue = d_tq + ph[i].G;
+            ta.order = d_order;
+            ta.queue = d_tq;
             ta.status = St.status;
             ta.R = Rin;
             ta.X = Xout;
             ta.V = TV;
             ta.W = TW;
             ta.Z = TZ;
-            ta.ldv = ph[i].ldv;
             ta.H = TH;
             ta.S = TS;
             ta.kmax = kcap;
             ta.tau = tcap;
-            ta.G = ph[i].G;
+            ta.ngroups = (int)ls[i].g.size();
+            for (size_t k2 = 0; k2 < ls[i].g.size(); ++k2) ta.grp[k2] = ls[i].g[k2];
             ta.tags = Ttags;
             ta.bar = Tbar;
             ta.tmo = team_tmo;
@@ -1247,7 +1360,7 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
             ta.dxmax = St.dxmax;
             ta.work = d_work;
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)ph[i].grid);
+            cfg.gridDim = dim3((unsigned)ls[i].grid);
             cfg.blockDim = dim3(kTeamBD);
             cfg.dynamicSmemBytes = team_smem;
             cfg.stream = st;
@@ -1271,7 +1384,7 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
         // bucket schedule), each stage keeping the fastest so far.  Timing every pair
         // for 8 steps instead weighted the small systems and early steps, and picked
         // 256-thread CTAs that ran the 512 x 8 batch 15 % slower than 512.
-        const int np_tune = npairs < 4 * sms ? npairs : 4 * sms;
+        const int np_tune = np_sample;
         const int k_tune = kmax < 32 ? kmax : 32;
         double* Xs = nullptr;
         void* ps2 = nullptr;
@@ -1346,16 +1459,16 @@ static int batch_ir(bspai_matrix* A, const int32_t* row_off, int nsys, int nrhs,
             cs.msched = 1;
             if ((rc = trial(cs))) return done(rc);
         }
-        // team mode, when its launches are few: the batch splits into one cooperative
-        // launch per team size, each ending on its own tail, which the sample (largest
-        // pairs, one size) cannot show; on the 512 x 32 batch (sizes 1e3 .. 6.4e4: eight
-        // team sizes at 8,192 rows) the sample favoured team mode by 6 % and the whole
-        // batch ran 3 % slower
+        // team mode, when every pair takes the same team size: the sample (the largest
+        // pairs) then stands for the batch.  On a batch of many sizes it does not: its
+        // small pairs run their products from L2 (a team's CTAs write the vectors they
+        // gather) on teams sized for them or, at the end, on larger ones; on the 512 x 32
+        // batch the sample favoured team mode by 9 % and the whole batch ran 13 % slower
         if (occ_team > 0)
             for (int tr : team_cands) {
-                std::vector<TeamPhase> ph;
-                plan_teams(tr, npairs, ph);
-                if (ph.size() > 2) continue;
+                std::vector<TeamLaunch> ls;
+                plan_teams(tr, npairs, kmax, ls);
+                if (ls.size() != 1 || ls[0].g.size() != 1) continue;
                 Sched cs;
                 cs.bd = kTeamBD;
                 cs.urows = MgsU<T>::lo;
