@@ -103,20 +103,17 @@ __device__ __forceinline__ int classify(double a, const double* thr, int q) {
     return k;
 }
 
-// bucket id of every entry; per-slice widths of every bucket; per-bucket
-// counts and max |m|; per-column max |m| of the e4m3 bucket
+// one row of k_classify (a live warp's rows): ids, per-slice widths, and the
+// warp's contributions to the block's counts and maxima
 template <typename VT>
-__global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int64_t* __restrict__ sptr,
-                                                  const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                                  const int32_t* __restrict__ rowlen,
-                                                  const __grid_constant__ BucketParams P,
-                                                  const double* __restrict__ thr_g, int8_t* __restrict__ id,
-                                                  int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
-                                                  VT* __restrict__ bmax, VT* __restrict__ colmax,
-                                                  int* __restrict__ wmax, const int32_t* __restrict__ slice_seg,
-                                                  int packed, unsigned* __restrict__ dmax, int* __restrict__ wmin) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= (int64_t)nslices * kSlice) return;
+__device__ __forceinline__ void classify_rows(int64_t r, int n, int nslices, const int64_t* __restrict__ sptr,
+                                              const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                              const int32_t* __restrict__ rowlen, const BucketParams& P,
+                                              const double* __restrict__ thr_g, int8_t* __restrict__ id,
+                                              int64_t* __restrict__ widths, VT* __restrict__ colmax,
+                                              const int32_t* __restrict__ slice_seg, int packed,
+                                              VT* __restrict__ bmax, bool one_seg, unsigned long long* s_cnt,
+                                              int* s_wmax, int* s_wmin, VT* s_bmax, unsigned* s_dmax) {
     unsigned dm = 0;  // max |c - r| of the row
     const int sg = seg_of(slice_seg, r >> 5);
     double thr[8];
@@ -157,7 +154,7 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
         const unsigned t = __shfl_xor_sync(0xffffffffu, dm, o);
         dm = t > dm ? t : dm;
     }
-    if (lane == 0 && dm) atomicMax(dmax, dm);
+    if (lane == 0 && dm) atomicMax(s_dmax, dm);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         if (k >= P.q) break;
@@ -172,17 +169,76 @@ __global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int6
         if (packed) w = (w + 3) & ~3;  // groups of four slots per row
         if (lane == 0) {
             widths[(int64_t)k * (nslices + 1) + (r >> 5)] = (int64_t)w * kSlice;
-            if (c) atomicAdd(nnzk + k, (unsigned long long)c);
-            if (m > VT(0)) atomic_max_nonneg(bmax + sg * 8 + k, m);
-            if (w) atomicMax(wmax + k, w);
-            atomicMin(wmin + k, w);
+            if (c) atomicAdd(s_cnt + k, (unsigned long long)c);
+            if (m > VT(0)) atomic_max_nonneg(one_seg ? s_bmax + k : bmax + sg * 8 + k, m);
+            if (w) atomicMax(s_wmax + k, w);
+            atomicMin(s_wmin + k, w);
         }
     }
+}
+
+
+// bucket id of every entry; per-slice widths of every bucket; per-bucket
+// counts and max |m|; per-column max |m| of the e4m3 bucket
+template <typename VT>
+__global__ void __launch_bounds__(256) k_classify(int n, int nslices, const int64_t* __restrict__ sptr,
+                                                  const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                  const int32_t* __restrict__ rowlen,
+                                                  const __grid_constant__ BucketParams P,
+                                                  const double* __restrict__ thr_g, int8_t* __restrict__ id,
+                                                  int64_t* __restrict__ widths, unsigned long long* __restrict__ nnzk,
+                                                  VT* __restrict__ bmax, VT* __restrict__ colmax,
+                                                  int* __restrict__ wmax, const int32_t* __restrict__ slice_seg,
+                                                  int packed, unsigned* __restrict__ dmax, int* __restrict__ wmin) {
+    // the warps' counts, widths and maxima meet in shared memory first: one
+    // global atomic per block and quantity instead of one per warp (max, min and
+    // integer sums: the totals do not depend on the order)
+    __shared__ unsigned long long s_cnt[8];
+    __shared__ int s_wmax[8], s_wmin[8];
+    __shared__ __align__(8) unsigned s_bmax[8 * (sizeof(VT) / 4)];
+    __shared__ unsigned s_dmax;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rows = (int64_t)nslices * kSlice;
+    const bool live = r < rows;  // whole warps (rows is a multiple of 32)
+    // the block's slices all in one segment (always for one system): bucket maxima in shared memory too
+    const int64_t rb = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t re = (rb + blockDim.x < rows ? rb + blockDim.x : rows) - 1;
+    const int sg0 = seg_of(slice_seg, rb >> 5);
+    const bool one_seg = seg_of(slice_seg, re >> 5) == sg0;
+    if (threadIdx.x < 8) {
+        s_cnt[threadIdx.x] = 0;
+        s_wmax[threadIdx.x] = 0;
+        s_wmin[threadIdx.x] = 0x7fffffff;
+        reinterpret_cast<VT*>(s_bmax)[threadIdx.x] = VT(0);
+    }
+    if (threadIdx.x == 0) s_dmax = 0;
+    __syncthreads();
+    if (live) classify_rows(r, n, nslices, sptr, col, val, rowlen, P, thr_g, id, widths, colmax, slice_seg, packed,
+                            bmax, one_seg, s_cnt, s_wmax, s_wmin, reinterpret_cast<VT*>(s_bmax), &s_dmax);
+    __syncthreads();
+    if ((int)threadIdx.x < P.q) {
+        const int k = threadIdx.x;
+        if (s_cnt[k]) atomicAdd(nnzk + k, s_cnt[k]);
+        if (s_wmax[k]) atomicMax(wmax + k, s_wmax[k]);
+        atomicMin(wmin + k, s_wmin[k]);
+        const VT m = reinterpret_cast<VT*>(s_bmax)[k];
+        if (one_seg && m > VT(0)) atomic_max_nonneg(bmax + sg0 * 8 + k, m);
+    }
+    if (threadIdx.x == 0 && s_dmax) atomicMax(dmax, s_dmax);
 }
 
 // least power of two s = 2^e with maxabs <= fmax * 2^e (1 if maxabs == 0)
 __device__ __forceinline__ float pow2_scale(double maxabs, double fmax) {
     if (!(maxabs > 0.0)) return 1.0f;
+    // both normal: maxabs = ma 2^Ea, fmax = mf 2^Ef with ma, mf in [1, 2), so
+    // e = Ea - Ef when ma <= mf and Ea - Ef + 1 otherwise (integer fields only)
+    const long long ab = __double_as_longlong(maxabs), fb = __double_as_longlong(fmax);
+    const int Ea = (int)((ab >> 52) & 0x7ff), Ef = (int)((fb >> 52) & 0x7ff);
+    if (Ea > 0 && Ea < 0x7ff && Ef > 0 && Ef < 0x7ff) {
+        const long long m = 0xfffffffffffffLL;
+        const int e = Ea - Ef + ((ab & m) > (fb & m) ? 1 : 0);
+        if (e >= -126 && e <= 127) return __int_as_float((e + 127) << 23);
+    }
     int E;
     frexp(maxabs / fmax, &E);
     int e = E - 2;

@@ -300,6 +300,66 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
     atomicMax(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));
 }
 
+// One value per warp (read from lane 0) combined across the block by `op`
+// (associative and commutative: max, min, integer add), valid in thread 0.
+// Every thread of the block calls it; s: blockDim.x / 32 slots of shared
+// memory that the caller does not touch between calls.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_combine(T v, T ident, T* s, Op op) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s[w] = v;
+    __syncthreads();
+    T t = ident;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = op(t, s[i]);
+    return t;
+}
+
+// Values already reduced over each warp (read from lane 0) combined across the
+// block by bit pattern, then one atomic_max_nonneg per block and address: the
+// same result as one atomic per warp, without a global atomic from every warp
+// on one address.  Every thread of the block calls it at the same point
+// (blockDim.x a multiple of 32); use it once per kernel.
+__device__ __forceinline__ void block_atomic_max_nonneg2(double* a0, double w0, double* a1, double w1) {
+    __shared__ unsigned long long s_bm[2][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_bm[0][w] = (unsigned long long)__double_as_longlong(w0);
+        s_bm[1][w] = (unsigned long long)__double_as_longlong(w1);
+    }
+    __syncthreads();
+    if (w == 0) {
+        const bool have = lane < (int)(blockDim.x >> 5);
+        unsigned long long b0 = have ? s_bm[0][lane] : 0ull, b1 = have ? s_bm[1][lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t0 = __shfl_xor_sync(0xffffffffu, b0, o);
+            const unsigned long long t1 = __shfl_xor_sync(0xffffffffu, b1, o);
+            b0 = t0 > b0 ? t0 : b0;
+            b1 = t1 > b1 ? t1 : b1;
+        }
+        if (lane == 0) {
+            if (b0) atomicMax(reinterpret_cast<unsigned long long*>(a0), b0);
+            if (b1) atomicMax(reinterpret_cast<unsigned long long*>(a1), b1);
+        }
+    }
+}
+__device__ __forceinline__ void block_atomic_max_nonneg(double* a0, double w0) {
+    __shared__ unsigned long long s_bm1[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_bm1[w] = (unsigned long long)__double_as_longlong(w0);
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long b0 = lane < (int)(blockDim.x >> 5) ? s_bm1[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t0 = __shfl_xor_sync(0xffffffffu, b0, o);
+            b0 = t0 > b0 ? t0 : b0;
+        }
+        if (lane == 0 && b0) atomicMax(reinterpret_cast<unsigned long long*>(a0), b0);
+    }
+}
+
 // Grid-wide barrier for cooperative launches (all blocks co-resident).
 // Generation counting: the last block to arrive resets the counter and bumps
 // the generation; the others wait for the bump.  Every wait is bounded by

@@ -414,24 +414,73 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
     if (!giv && blockIdx.x == 0 && tid == 0) givens_step(j, kmax, (double)hn, H, cs, sn, g, st);
 }
 
-// y = R^-1 g by column-oriented back substitution (fp64), one block
-__global__ void k_backsolve(const GmresState* st, const double* __restrict__ H, const double* __restrict__ g,
-                            double* __restrict__ y, int kmax) {
+// y = R^-1 g by column-oriented back substitution (fp64): for i = k-1 .. 0,
+// y_i = g_i / R_ii and g_t -= R_ti y_i for t < i (each g_t sees the same
+// operations in the same order as a plain column back substitution).  When
+// g and the triangle of R fit in kBackSmem bytes, the whole block first loads
+// them into shared memory with every load in flight at once, and warp 0 then
+// runs the k sequential rows from there; otherwise warp 0 alone streams the
+// columns from memory, loading column i - 1 (the first 32 kBackC rows in
+// registers) while row i divides and updates.  Launch: one block of
+// kBackThreads, kBackSmem bytes of dynamic shared memory.
+constexpr int kBackC = 8, kBackThreads = 256;
+constexpr size_t kBackSmem = 48 * 1024;
+__global__ void __launch_bounds__(kBackThreads) k_backsolve(const GmresState* st, const double* __restrict__ H,
+                                                            const double* __restrict__ g, double* __restrict__ y,
+                                                            int kmax) {
     extern __shared__ double sg[];
-    __shared__ double s_yi;
     const int k = st->j;
-    for (int t = threadIdx.x; t < k; t += blockDim.x) sg[t] = g[t];
-    __syncthreads();
-    for (int i = k - 1; i >= 0; --i) {
-        const double* hc = H + (int64_t)i * (kmax + 1);
-        if (threadIdx.x == 0) {
-            s_yi = __ddiv_rn(sg[i], hc[i]);
-            y[i] = s_yi;
+    const int lane = threadIdx.x & 31;
+    const bool staged = (size_t)k * (k + 3) / 2 * sizeof(double) <= kBackSmem;
+    if (staged) {
+        // sg[0, k): g; then column i of R (rows 0 .. i) at sg + k + i (i + 1) / 2
+        double* R = sg + k;
+        for (int t = threadIdx.x; t < k; t += blockDim.x) sg[t] = g[t];
+        const int tri = k * (k + 1) / 2;
+        for (int e = threadIdx.x; e < tri; e += blockDim.x) {
+            int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);  // column of packed entry e
+            while (i * (i + 1) / 2 > e) --i;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            R[e] = H[(int64_t)i * (kmax + 1) + (e - i * (i + 1) / 2)];
         }
         __syncthreads();
-        const double yi = s_yi;
-        for (int t = threadIdx.x; t < i; t += blockDim.x) sg[t] = __dsub_rn(sg[t], __dmul_rn(hc[t], yi));
-        __syncthreads();
+        if (threadIdx.x >= 32) return;
+        for (int i = k - 1; i >= 0; --i) {
+            const double* rc = R + i * (i + 1) / 2;
+            const double yi = __ddiv_rn(sg[i], rc[i]);
+            if (lane == 0) y[i] = yi;
+            for (int t = lane; t < i; t += 32) sg[t] = __dsub_rn(sg[t], __dmul_rn(rc[t], yi));
+            __syncwarp();
+        }
+        return;
+    }
+    if (threadIdx.x >= 32) return;
+    for (int t = lane; t < k; t += 32) sg[t] = g[t];
+    __syncwarp();
+    double nxt[kBackC], nd = 1.0;
+    auto fetch = [&](int i) {
+        const double* hc = H + (int64_t)i * (kmax + 1);
+#pragma unroll
+        for (int c = 0; c < kBackC; ++c) nxt[c] = lane + 32 * c < i ? hc[lane + 32 * c] : 0.0;
+        nd = hc[i];
+    };
+    if (k > 0) fetch(k - 1);
+    for (int i = k - 1; i >= 0; --i) {
+        double cur[kBackC];
+#pragma unroll
+        for (int c = 0; c < kBackC; ++c) cur[c] = nxt[c];
+        const double di = nd;
+        if (i > 0) fetch(i - 1);
+        const double yi = __ddiv_rn(sg[i], di);
+        if (lane == 0) y[i] = yi;
+#pragma unroll
+        for (int c = 0; c < kBackC; ++c) {
+            const int t = lane + 32 * c;
+            if (t < i) sg[t] = __dsub_rn(sg[t], __dmul_rn(cur[c], yi));
+        }
+        const double* hc = H + (int64_t)i * (kmax + 1);
+        for (int t = lane + 32 * kBackC; t < i; t += 32) sg[t] = __dsub_rn(sg[t], __dmul_rn(hc[t], yi));
+        __syncwarp();
     }
 }
 
@@ -450,8 +499,17 @@ __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, i
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dabs = 0.0, xabs = 0.0;
     if (r < n) {
+        // the products added in order of j; the loads of 8 columns issued before their adds
         T acc = T(0);
-        for (int jj = 0; jj < k; ++jj) acc = Ar<T>::add(acc, Ar<T>::mul(V[(int64_t)jj * ldv + r], sy[jj]));
+        int jj = 0;
+        for (; jj + 8 <= k; jj += 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)(jj + u) * ldv + r];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = Ar<T>::add(acc, Ar<T>::mul(v[u], sy[jj + u]));
+        }
+        for (; jj < k; ++jj) acc = Ar<T>::add(acc, Ar<T>::mul(V[(int64_t)jj * ldv + r], sy[jj]));
         double d = (double)acc;
         // working precision u = fp32: d stored in u, x = fl32(x + d) (x and d
         // are fp32 values, so the fp64 sum rounds to the correctly rounded fp32 sum)
@@ -473,10 +531,7 @@ __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, i
         dabs = fmax(dabs, __shfl_xor_sync(0xffffffffu, dabs, o));
         xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(norms, dabs);
-        atomic_max_nonneg(norms + 1, xabs);
-    }
+    block_atomic_max_nonneg2(norms, dabs, norms + 1, xabs);
 }
 
 __global__ void k_absmax(int n, const double* __restrict__ v, double* __restrict__ out) {
@@ -485,7 +540,7 @@ __global__ void k_absmax(int n, const double* __restrict__ v, double* __restrict
     if (!(a <= 1.7976931348623157e308)) a = __longlong_as_double(0x7ff0000000000000LL);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, a);
+    block_atomic_max_nonneg(out, a);
 }
 
 // k_mgs_res for fp32 with the rows of a thread taken in adjacent pairs: every
@@ -856,7 +911,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
     }
     {
         ProfScope ps(BSPAI_K_UPDATE, s);
-        k_backsolve<<<1, 1024, sizeof(double) * (size_t)(W.kmax + 1), s>>>(W.st, W.H, W.g, W.y, W.kmax);
+        k_backsolve<<<1, kBackThreads, kBackSmem, s>>>(W.st, W.H, W.g, W.y, W.kmax);
         note_launch();
         CUDA_LAUNCH_CHECK();
         if (n > 0) {
@@ -942,10 +997,7 @@ __global__ void __launch_bounds__(256) k_apply_d(int n, double* __restrict__ x, 
         dabs = fmax(dabs, __shfl_xor_sync(0xffffffffu, dabs, o));
         xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(norms, dabs);
-        atomic_max_nonneg(norms + 1, xabs);
-    }
+    block_atomic_max_nonneg2(norms, dabs, norms + 1, xabs);
 }
 
 static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, const bspai_bucketed* BM,

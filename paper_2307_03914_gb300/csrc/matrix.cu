@@ -7,17 +7,19 @@
 namespace bspai {
 
 // width of each 32-row slice (max row length), times 32
-__global__ void k_slice_width(int n, const int32_t* __restrict__ row_ptr, int64_t* __restrict__ w) {
+__global__ void __launch_bounds__(256) k_slice_width(int n, const int32_t* __restrict__ row_ptr,
+                                                     int64_t* __restrict__ w) {
+    __shared__ int s_len[8];
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nsl = ceil_div(n, kSlice);
-    if (r >= nsl * kSlice) return;
     int len = r < n ? row_ptr[r + 1] - row_ptr[r] : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
-    if ((r & 31) == 0) {
-        w[r >> 5] = (int64_t)len * kSlice;
-        if (len > 0) atomicMax(reinterpret_cast<unsigned long long*>(w + nsl), (unsigned long long)len);
-    }
+    if ((r & 31) == 0 && r < nsl * kSlice) w[r >> 5] = (int64_t)len * kSlice;
+    // the overall width: the block's maximum, one atomic per block
+    len = block_combine(len, 0, s_len, [](int a, int b) { return a > b ? a : b; });
+    if (threadIdx.x == 0 && len > 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(w + nsl), (unsigned long long)len);
 }
 
 // scatter the CSR rows into their slices; padding slots get column -1, value 0
@@ -105,10 +107,12 @@ int sell_from_csr(int n, const int32_t* row_ptr, const int32_t* col, const doubl
 // slice widths rounded up to four slots (times 32) and max |c - r| over the entries
 __global__ void k_packed_widths(int n, int nsl, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                 int64_t* __restrict__ w, unsigned* __restrict__ dmax, int* __restrict__ wmin) {
+    __shared__ unsigned s_dm[8];
+    __shared__ int s_wm[8];
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= (int64_t)nsl * kSlice) return;
+    const bool live = r < (int64_t)nsl * kSlice;  // whole warps
     const int64_t s = r >> 5;
-    const int width = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    const int width = live ? (int)((sptr[s + 1] - sptr[s]) >> 5) : 0;
     unsigned dm = 0;
     if (r < n)
         for (int l = 0; l < width; ++l) {
@@ -123,10 +127,14 @@ __global__ void k_packed_widths(int n, int nsl, const int64_t* __restrict__ sptr
         const unsigned t = __shfl_xor_sync(0xffffffffu, dm, o);
         dm = t > dm ? t : dm;
     }
-    if ((r & 31) == 0) {
-        w[s] = (int64_t)((width + 3) & ~3) * kSlice;
+    const int pw = (width + 3) & ~3;
+    if ((r & 31) == 0 && live) w[s] = (int64_t)pw * kSlice;
+    // the block's maximum distance and minimum width, one atomic each per block
+    dm = block_combine(dm, 0u, s_dm, [](unsigned a, unsigned b) { return a > b ? a : b; });
+    const int wm = block_combine(live ? pw : 0x7fffffff, 0x7fffffff, s_wm, [](int a, int b) { return a < b ? a : b; });
+    if (threadIdx.x == 0) {
         if (dm) atomicMax(dmax, dm);
-        atomicMin(wmin, (width + 3) & ~3);
+        atomicMin(wmin, wm);
     }
 }
 
@@ -218,9 +226,9 @@ __global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const
         for (int64_t p = sptr[s] + (r & 31); p < sptr[s + 1]; p += kSlice)
             if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
     }
-    // the max of the warp's rows first: one atomic per warp, not per row
+    // the max of the warp's rows, then of the block's warps: one atomic per block
     sum = warp_max_bits(sum);
-    if ((threadIdx.x & 31) == 0 && sum != 0.0) atomic_max_nonneg(out, sum);
+    block_atomic_max_nonneg(out, sum);
 }
 
 int launch_row_abs_sum_max(const Sell& S, const double* val, double* out, cudaStream_t s) {
@@ -290,10 +298,7 @@ __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __res
         rabs = fmax(rabs, __shfl_xor_sync(0xffffffffu, rabs, o));
         xabs = fmax(xabs, __shfl_xor_sync(0xffffffffu, xabs, o));
     }
-    if ((threadIdx.x & 31) == 0 && norms) {
-        atomic_max_nonneg(norms, rabs);
-        atomic_max_nonneg(norms + 1, xabs);
-    }
+    if (norms) block_atomic_max_nonneg2(norms, rabs, norms + 1, xabs);
 }
 
 // The same residual for nrhs right-hand sides of a block-diagonal batch

@@ -122,52 +122,109 @@ void prof_end(int cls, cudaStream_t s) {
 
 // ------------------------------------------------------------------ scan
 // Exclusive prefix sum of `count` int64 values into out[0..count] (out[count]
-// = total), one CTA: each thread sums a contiguous chunk, the chunk sums are
-// scanned across the block, then each thread writes its chunk.
-__global__ void k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t count) {
-    constexpr int T = 1024;
-    __shared__ int64_t warp_tot[32];
-    __shared__ int64_t s_carry;
-    const int tid = threadIdx.x;
-    int64_t chunk = (count + T - 1) / T;
-    int64_t lo = (int64_t)tid * chunk;
-    int64_t hi = lo + chunk < count ? lo + chunk : count;
+// = total).  Tiles of kScanTile values, one block each, in two launches:
+// k_scan_sums adds every tile, k_scan_apply gives each tile the sum of the
+// tiles before it plus its own exclusive scan.  Every global access is
+// coalesced (the tile is staged in shared memory, where each thread takes
+// kScanK consecutive values).  Integer sums: the result does not depend on
+// the order of the additions.
+constexpr int kScanT = 256, kScanK = 8, kScanTile = kScanT * kScanK;
+
+__device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t* s_w) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();  // s_w may still be read by an earlier call
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    int64_t t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_w[i];
+    return t;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_sums(const int64_t* __restrict__ in, int64_t count,
+                                                      int64_t* __restrict__ tsum) {
+    __shared__ int64_t s_w[kScanT / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanK; ++k) {
+        const int64_t i = base + k * kScanT + threadIdx.x;
+        if (i < count) v += in[i];
+    }
+    v = block_sum_i64(v, s_w);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                                                       int64_t count, const int64_t* __restrict__ tsum) {
+    __shared__ int64_t tile[kScanTile];
+    __shared__ int64_t s_w[kScanT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    // the tiles before this one
+    int64_t off = 0;
+    for (int t = tid; t < (int)blockIdx.x; t += kScanT) off += tsum[t];
+    off = block_sum_i64(off, s_w);
+#pragma unroll
+    for (int k = 0; k < kScanK; ++k) {
+        const int64_t i = base + k * kScanT + tid;
+        tile[k * kScanT + tid] = i < count ? in[i] : 0;
+    }
+    __syncthreads();
+    int64_t loc[kScanK];
     int64_t sum = 0;
-    for (int64_t i = lo; i < hi; ++i) sum += in[i];
-    // block-wide exclusive scan of the chunk sums
-    int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < kScanK; ++k) {
+        loc[k] = tile[tid * kScanK + k];
+        sum += loc[k];
+    }
+    // exclusive scan of the thread sums across the block
     int64_t v = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += t;
     }
-    if (lane == 31) warp_tot[w] = v;
+    __syncthreads();  // s_w was last read in block_sum_i64
+    if (lane == 31) s_w[w] = v;
     __syncthreads();
-    if (w == 0) {
-        int64_t t = warp_tot[lane];
-        int64_t u = t;
+    int64_t before = 0;
+    for (int i = 0; i < w; ++i) before += s_w[i];
+    int64_t run = off + before + v - sum;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, u, o);
-            if (lane >= o) u += y;
-        }
-        warp_tot[lane] = u - t;  // exclusive over warps
-        if (lane == 31) s_carry = u;
+    for (int k = 0; k < kScanK; ++k) {
+        tile[tid * kScanK + k] = run;
+        run += loc[k];
     }
     __syncthreads();
-    int64_t run = v - sum + warp_tot[w];
-    for (int64_t i = lo; i < hi; ++i) {
-        out[i] = run;
-        run += in[i];
+#pragma unroll
+    for (int k = 0; k < kScanK; ++k) {
+        const int64_t i = base + k * kScanT + tid;
+        if (i < count) out[i] = tile[k * kScanT + tid];
     }
-    if (tid == 0) out[count] = s_carry;
+    if (blockIdx.x == gridDim.x - 1 && tid == kScanT - 1) out[count] = run;
 }
 
 int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t count, cudaStream_t s) {
-    k_scan_i64<<<1, 1024, 0, s>>>(in, out, count);
+    if (count <= 0) {
+        CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return BSPAI_OK;
+    }
+    const int64_t tiles = ceil_div(count, (int64_t)kScanTile);
+    if (tiles > INT32_MAX) return set_error(BSPAI_ERR_UNSUPPORTED, "scan of %lld values", (long long)count);
+    int64_t* tsum = nullptr;
+    BSPAI_TRY(dalloc_t(&tsum, (size_t)tiles, s));
+    k_scan_sums<<<(unsigned)tiles, kScanT, 0, s>>>(in, count, tsum);
     note_launch();
-    CUDA_LAUNCH_CHECK();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_scan_apply<<<(unsigned)tiles, kScanT, 0, s>>>(in, out, count, tsum);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    dfree(tsum, s);
+    if (e != cudaSuccess) return cuda_error(e, "k_scan", __FILE__, __LINE__);
     return BSPAI_OK;
 }
 

@@ -41,20 +41,33 @@ int launch_row_absmax_inv(int n, const int32_t* row_ptr, const double* val, doub
 }
 
 // per column: |J_k| and the candidate count sum_{j in J_k} |row j of A|
-__global__ void k_spai_sizes(int n, const int64_t* __restrict__ msptr, const int32_t* __restrict__ mcol,
+__global__ void __launch_bounds__(256) k_spai_sizes(int n, const int64_t* __restrict__ msptr, const int32_t* __restrict__ mcol,
                              const int32_t* __restrict__ mrowlen, const int32_t* __restrict__ arp,
                              int* __restrict__ out) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int nJ = mrowlen[k];
-    const int64_t base = msptr[k >> 5] + (k & 31);
-    int L = 0;
-    for (int q = 0; q < nJ; ++q) {
-        const int j = mcol[base + (int64_t)q * kSlice];
-        L += arp[j + 1] - arp[j];
+    int nJ = 0, L = 0;
+    if (k < n) {
+        nJ = mrowlen[k];
+        const int64_t base = msptr[k >> 5] + (k & 31);
+        for (int q = 0; q < nJ; ++q) {
+            const int j = mcol[base + (int64_t)q * kSlice];
+            L += arp[j + 1] - arp[j];
+        }
     }
-    atomicMax(out, nJ);
-    atomicMax(out + 1, L);
+    // the warp's maxima, then the block's, then one atomic each
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nJ = max(nJ, __shfl_xor_sync(0xffffffffu, nJ, o));
+        L = max(L, __shfl_xor_sync(0xffffffffu, L, o));
+    }
+    __shared__ int s_nj[8], s_l[8];
+    auto mx = [](int a, int b) { return a > b ? a : b; };
+    nJ = block_combine(nJ, 0, s_nj, mx);
+    L = block_combine(L, 0, s_l, mx);
+    if (threadIdx.x == 0) {
+        atomicMax(out, nJ);
+        atomicMax(out + 1, L);
+    }
 }
 
 struct SpaiCounters {

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "spmv_row.cuh"
+#include "tma.cuh"
 
 namespace bspai {
 
@@ -150,32 +151,6 @@ struct StageLayout {
     int32_t ns;          // stages per warp
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
 // one stored value (in shared memory) of a narrow bucket to fp32: as decode_rt
 __device__ __forceinline__ float decode_sm(const BucketDev& B, const unsigned char* v, int i, int c, int64_t r,
                                            float sc) {
@@ -265,7 +240,7 @@ __global__ void __launch_bounds__(256) k_bspmv_tma(const __grid_constant__ BMDev
     load_window();
     if (lane == 0) {
         for (int t = 0; t < NS; ++t) mbar_init(bars + t, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     __syncwarp();
     for (int t = 0; t < NS && t < cnt; ++t) post(t, t);
