@@ -220,6 +220,14 @@ struct ProfScope {
 };
 
 int num_sms();
+// Blocks for a grid-stride loop over n items with bd threads per block: one
+// resident wave (per_sm blocks on every SM) at most, so that per-block
+// epilogues (one atomic per block) stay few.
+inline unsigned wave_grid(int64_t n, int bd = 256, int per_sm = 8) {
+    const int64_t need = (n + bd - 1) / bd;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    return (unsigned)(need < cap ? (need > 0 ? need : 1) : cap);
+}
 void note_launch();  // counts kernel launches (reported by bspai_launch_count)
 void count_launches(bool on);  // this thread's launches are (not) counted, e.g. during graph capture
 

@@ -321,11 +321,16 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
     __shared__ T s_tot;
     __shared__ unsigned s_seq;
     __shared__ int s_ok, s_j, s_done, s_kmax;
+    __shared__ __align__(16) unsigned long long s_slots[2 * kTagMaxBlocks + 2];  // warp 0's copies of the slots
+    __shared__ __align__(8) uint64_t s_mbar;
+    unsigned phase = 0;
     if (threadIdx.x == 0) {
         s_j = st->j;
         s_done = st->done;
         s_kmax = st->kmax;
         s_seq = *(volatile unsigned*)&st->bar.seq;  // reductions of this launch are s_seq + 1, s_seq + 2, ...
+        mbar_init(&s_mbar, 1);
+        mbar_init_fence();
     }
     __syncthreads();
     if (s_done) return;
@@ -370,7 +375,8 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
                 if (lr < nb) vnext[t] = vi[lr];
             }
         }
-        const T h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G);
+        const T h = tag_wait_bulk(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G, s_slots,
+                                  &s_mbar, phase);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -393,7 +399,8 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
 #pragma unroll
         for (int t = 0; t < R; ++t) vcur[t] = vnext[t];
     }
-    const T h2 = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G);
+    const T h2 = tag_wait_bulk(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G, s_slots,
+                               &s_mbar, phase);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -496,9 +503,8 @@ __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, i
     const int k = st->j;
     for (int t = threadIdx.x; t < k; t += blockDim.x) sy[t] = Ar<T>::from(y[t]);
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dabs = 0.0, xabs = 0.0;
-    if (r < n) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         // the products added in order of j; the loads of 8 columns issued before their adds
         T acc = T(0);
         int jj = 0;
@@ -521,10 +527,11 @@ __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, i
             if (u32) xn = (double)__double2float_rn(xn);
             x[r] = xn;
         }
-        dabs = fabs(d);
-        xabs = fabs(xn);
-        if (!(dabs <= 1.7976931348623157e308)) dabs = __longlong_as_double(0x7ff0000000000000LL);
-        if (!(xabs <= 1.7976931348623157e308)) xabs = __longlong_as_double(0x7ff0000000000000LL);
+        double da = fabs(d), xa = fabs(xn);
+        if (!(da <= 1.7976931348623157e308)) da = __longlong_as_double(0x7ff0000000000000LL);
+        if (!(xa <= 1.7976931348623157e308)) xa = __longlong_as_double(0x7ff0000000000000LL);
+        dabs = fmax(dabs, da);
+        xabs = fmax(xabs, xa);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -535,9 +542,12 @@ __global__ void __launch_bounds__(256) k_gmres_update(const T* __restrict__ V, i
 }
 
 __global__ void k_absmax(int n, const double* __restrict__ v, double* __restrict__ out) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double a = r < n ? fabs(v[r]) : 0.0;
-    if (!(a <= 1.7976931348623157e308)) a = __longlong_as_double(0x7ff0000000000000LL);
+    double a = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double t = fabs(v[r]);
+        if (!(t <= 1.7976931348623157e308)) t = __longlong_as_double(0x7ff0000000000000LL);
+        a = fmax(a, t);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
     block_atomic_max_nonneg(out, a);
@@ -563,11 +573,16 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
     __shared__ float s_tot;
     __shared__ unsigned s_seq;
     __shared__ int s_ok, s_j, s_done, s_kmax;
+    __shared__ __align__(16) unsigned long long s_slots[2 * kTagMaxBlocks + 2];  // warp 0's copies of the slots
+    __shared__ __align__(8) uint64_t s_mbar;
+    unsigned phase = 0;
     if (threadIdx.x == 0) {
         s_j = st->j;
         s_done = st->done;
         s_kmax = st->kmax;
         s_seq = *(volatile unsigned*)&st->bar.seq;
+        mbar_init(&s_mbar, 1);
+        mbar_init_fence();
     }
     __syncthreads();
     if (s_done) return;
@@ -619,7 +634,8 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
                 if (2 * q < nb) vnext[t] = ld2(vi, q);
             }
         }
-        const float h = tag_wait(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G);
+        const float h = tag_wait_bulk(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G,
+                                      s_slots, &s_mbar, phase);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -642,7 +658,8 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
 #pragma unroll
         for (int t = 0; t < P; ++t) vcur[t] = vnext[t];
     }
-    const float hz = tag_wait(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G);
+    const float hz = tag_wait_bulk(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G,
+                                   s_slots, &s_mbar, phase);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -915,7 +932,7 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
         note_launch();
         CUDA_LAUNCH_CHECK();
         if (n > 0) {
-            k_gmres_update<T><<<(unsigned)ceil_div(n, 256), 256, sizeof(T) * (size_t)(W.kmax + 1), s>>>(
+            k_gmres_update<T><<<wave_grid(n), 256, sizeof(T) * (size_t)(W.kmax + 1), s>>>(
                 V, W.ldv, n, W.st, W.y, x, dout, W.norms, W.u32);
             note_launch();
             CUDA_LAUNCH_CHECK();
@@ -979,18 +996,18 @@ __global__ void k_dacc_add(int n, double* __restrict__ d, const double* __restri
 // norms[0] = max |fl_u(d)|, norms[1] = max |x| (as k_gmres_update)
 __global__ void __launch_bounds__(256) k_apply_d(int n, double* __restrict__ x, const double* __restrict__ d,
                                                  double* __restrict__ norms, int u32) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dabs = 0.0, xabs = 0.0;
-    if (r < n) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         double dv = d[r];
         if (u32) dv = (double)__double2float_rn(dv);
         double xn = __dadd_rn(x[r], dv);
         if (u32) xn = (double)__double2float_rn(xn);
         x[r] = xn;
-        dabs = fabs(dv);
-        xabs = fabs(xn);
-        if (!(dabs <= 1.7976931348623157e308)) dabs = __longlong_as_double(0x7ff0000000000000LL);
-        if (!(xabs <= 1.7976931348623157e308)) xabs = __longlong_as_double(0x7ff0000000000000LL);
+        double da = fabs(dv), xa = fabs(xn);
+        if (!(da <= 1.7976931348623157e308)) da = __longlong_as_double(0x7ff0000000000000LL);
+        if (!(xa <= 1.7976931348623157e308)) xa = __longlong_as_double(0x7ff0000000000000LL);
+        dabs = fmax(dabs, da);
+        xabs = fmax(xabs, xa);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1073,7 +1090,7 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
         ProfScope ps(BSPAI_K_OTHER, s);
         cudaError_t e0 = cudaMemsetAsync(nrm, 0, 4 * sizeof(double), s);
         if (e0) return finish(cuda_error(e0, "memset", __FILE__, __LINE__));
-        k_absmax<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, b, nrm);
+        k_absmax<<<wave_grid(n), 256, 0, s>>>(n, b, nrm);
         note_launch();
         if (!o.x0_given) {
             // x0 = M b with the unbucketed M in u_f (fp32 or fp16), stored in fp64
@@ -1148,7 +1165,7 @@ static int ir_solve(bspai_matrix* A, const bspai_bucketed* BA, const double* b, 
                 ProfScope ps(BSPAI_K_UPDATE, s);
                 e = cudaMemsetAsync(W.norms, 0, 2 * sizeof(double), s);
                 if (e) return finish(cuda_error(e, "memset", __FILE__, __LINE__));
-                k_apply_d<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, x, dacc, W.norms, W.u32);
+                k_apply_d<<<wave_grid(n), 256, 0, s>>>(n, x, dacc, W.norms, W.u32);
                 note_launch();
             }
             double hn2[2];

@@ -219,12 +219,14 @@ int sell_packed_copy(const Sell& S, const float* val, Sell* out, float** pval, c
 
 __global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ col,
                                   const double* __restrict__ val, double* __restrict__ out) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double sum = 0.0;
-    if (r < n) {
+    double sum = 0.0;  // the largest row sum of this thread's rows
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = r >> 5;
+        double rs = 0.0;
         for (int64_t p = sptr[s] + (r & 31); p < sptr[s + 1]; p += kSlice)
-            if (col[p] >= 0) sum = __dadd_rn(sum, fabs(val[p]));
+            if (col[p] >= 0) rs = __dadd_rn(rs, fabs(val[p]));
+        // by bit pattern, as warp_max_bits and the atomic order them
+        if ((unsigned long long)__double_as_longlong(rs) > (unsigned long long)__double_as_longlong(sum)) sum = rs;
     }
     // the max of the warp's rows, then of the block's warps: one atomic per block
     sum = warp_max_bits(sum);
@@ -233,7 +235,7 @@ __global__ void k_row_abs_sum_max(int n, const int64_t* __restrict__ sptr, const
 
 int launch_row_abs_sum_max(const Sell& S, const double* val, double* out, cudaStream_t s) {
     if (S.n == 0) return BSPAI_OK;
-    k_row_abs_sum_max<<<(unsigned)ceil_div(S.n, 256), 256, 0, s>>>(S.n, S.sptr, S.col, val, out);
+    k_row_abs_sum_max<<<wave_grid(S.n), 256, 0, s>>>(S.n, S.sptr, S.col, val, out);
     note_launch();
     CUDA_LAUNCH_CHECK();
     return BSPAI_OK;
@@ -267,9 +269,8 @@ __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __res
                                                      const double* __restrict__ x,
                                                      const double* __restrict__ b, double* __restrict__ r,
                                                      double* __restrict__ norms) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double rabs = 0.0, xabs = 0.0;
-    if (i < n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i >> 5;
         double hi = b[i], lo = 0.0;
         const int64_t end = sptr[s + 1];
@@ -289,9 +290,10 @@ __global__ void __launch_bounds__(256) k_residual_dd(int n, const int64_t* __res
         double ri = __dadd_rn(hi, lo);
         if (U32) ri = (double)__double2float_rn(ri);
         r[i] = ri;
-        rabs = fabs(ri);
-        xabs = fabs(x[i]);
-        if (!(rabs <= 1.7976931348623157e308)) rabs = __longlong_as_double(0x7ff0000000000000LL);  // NaN -> Inf
+        double ra = fabs(ri);
+        if (!(ra <= 1.7976931348623157e308)) ra = __longlong_as_double(0x7ff0000000000000LL);  // NaN -> Inf
+        rabs = fmax(rabs, ra);
+        xabs = fmax(xabs, fabs(x[i]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -361,7 +363,7 @@ int launch_residual_prec(const bspai_matrix* A, const double* x, const double* b
                          int u_r, int u, cudaStream_t s) {
     if (A->n == 0) return BSPAI_OK;
     ProfScope ps(BSPAI_K_RESIDUAL, s);
-    const unsigned grid = (unsigned)ceil_div(A->n, 256);
+    const unsigned grid = wave_grid(A->n);
     const int64_t* sp = A->sell.sptr;
     const int32_t* ci = A->sell.col;
     if (u == BSPAI_FP32) {
@@ -460,7 +462,7 @@ int matrix_create(const bspai_csr_t* A, cudaStream_t s, bspai_matrix** out) {
             if (e != cudaSuccess) st = cuda_error(e, "memset", __FILE__, __LINE__);
         }
         if (st == BSPAI_OK && A->n > 0) {
-            k_row_abs_sum_max<<<(unsigned)ceil_div(A->n, 256), 256, 0, s>>>(A->n, M->sell.sptr, M->sell.col,
+            k_row_abs_sum_max<<<wave_grid(A->n), 256, 0, s>>>(A->n, M->sell.sptr, M->sell.col,
                                                                             M->val64, M->norm_inf);
             note_launch();
             cudaError_t e = cudaGetLastError();
