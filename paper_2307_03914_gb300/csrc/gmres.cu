@@ -314,7 +314,8 @@ __device__ void givens_block(int j, int kmax, double* H, double* cs, double* sn,
 template <typename T, int R, int BD>
 __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ldv, int n, GmresState* st,
                                                      double* H, double* cs, double* sn, double* g,
-                                                     unsigned long long* tags, unsigned long long tmo, int giv) {
+                                                     unsigned long long* tags, unsigned long long tmo, int giv,
+                                                     int bulk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* zs = reinterpret_cast<T*>(smraw);
     __shared__ T s_w[32];
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
             }
         }
         const T h = tag_wait_bulk(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G, s_slots,
-                                  &s_mbar, phase);
+                                  &s_mbar, phase, bulk != 0);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
         for (int t = 0; t < R; ++t) vcur[t] = vnext[t];
     }
     const T h2 = tag_wait_bulk(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G, s_slots,
-                               &s_mbar, phase);
+                               &s_mbar, phase, bulk != 0);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -568,7 +569,8 @@ __device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __fadd2_rn
 template <int P, int BD>
 __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64_t ldv, int n, GmresState* st,
                                                       double* H, double* cs, double* sn, double* g,
-                                                      unsigned long long* tags, unsigned long long tmo, int giv) {
+                                                      unsigned long long* tags, unsigned long long tmo, int giv,
+                                                      int bulk) {
     __shared__ float s_w[32];
     __shared__ float s_tot;
     __shared__ unsigned s_seq;
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
             }
         }
         const float h = tag_wait_bulk(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G,
-                                      s_slots, &s_mbar, phase);
+                                      s_slots, &s_mbar, phase, bulk != 0);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -659,7 +661,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
         for (int t = 0; t < P; ++t) vcur[t] = vnext[t];
     }
     const float hz = tag_wait_bulk(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G,
-                                   s_slots, &s_mbar, phase);
+                                   s_slots, &s_mbar, phase, bulk != 0);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -711,6 +713,7 @@ struct GmresWork {
     int res_per_thread = 0;  // its rows (k_mgs_res) or row pairs (k_mgs_res2) per thread
     int Gr = 0;              // its blocks that hold rows (at most one block per SM)
     int giv = 0;             // 1: one more block applies the Givens rotations during the passes
+    int bulk = 0;            // 1: warp 0 polls the reductions by bulk copies (tag_poll_warp_bulk)
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
 
@@ -809,6 +812,13 @@ static ResInstance pick_res(int64_t chunk) {
 // Use the on-chip MGS kernel when one block per SM can hold its rows of z on
 // chip (fp32: in registers; fp64: in shared memory, at most 200 KB) with at
 // most 32 (fp32) / 16 (fp64) rows per thread of a 512-thread block.
+// A block's bytes of one basis vector from which the MGS kernels poll their
+// reductions by bulk copies.  Measured (fp32, 64-128 blocks, 64-step GMRES
+// runs): load polling 5 % faster at 4 KB per block (n = 64,000), even at
+// 7 KB, bulk polling 11 / 3 / 4 % faster at 16 / 32 / 64 KB (n = 262,144 /
+// 512,000 / 2,097,152).
+constexpr int64_t kBulkPollBytes = 16 * 1024;
+
 static int choose_mgs(GmresWork& W) {
     W.res_fn = nullptr;
     // As few blocks as hold the rows of z on chip, but not fewer than kMgsBlocks: each
@@ -842,6 +852,8 @@ static int choose_mgs(GmresWork& W) {
     W.Gr = Gr;
     // the Givens block needs an SM of its own (one block per SM at these sizes)
     W.giv = Gr + 1 <= W.sms ? 1 : 0;
+    // poll by bulk copies where a block's loads of one basis vector would hold up a load poll
+    W.bulk = (int64_t)chunk * (int64_t)es >= kBulkPollBytes ? 1 : 0;
     W.res_smem = smem;
     return BSPAI_OK;
 }
@@ -913,7 +925,8 @@ static int gmres_run(GmresWork& W, const bspai_matrix* A, const bspai_bucketed* 
                 int nn = n;
                 int64_t ld = W.ldv;
                 if (W.res_fn) {
-                    void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &W.tags, &W.tmo_ns, &W.giv};
+                    void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &W.tags, &W.tmo_ns, &W.giv,
+                                    &W.bulk};
                     BSPAI_TRY(coop_launch_cfg(W.res_fn, W.Gr + W.giv, W.res_bd, W.res_smem, args, s));
                 } else {
                     void* args[] = {&V, &ld, &nn, &W.st, &W.H, &W.cs, &W.sn, &W.g, &part, &W.tmo_ns};

@@ -232,14 +232,19 @@ __device__ __forceinline__ T tag_wait(const unsigned long long* tags, int set, u
 }
 
 
-// tag_wait with warp 0 polling by bulk copies (tag_poll_warp_bulk)
+// tag_wait with warp 0 polling by bulk copies (tag_poll_warp_bulk) when `bulk`,
+// else by loads (tag_poll_warp): the same total either way.  The copy engine's
+// round trip is the longer one, so it pays only where the pass's own loads
+// would hold up a load poll.
 template <typename T>
 __device__ __forceinline__ T tag_wait_bulk(const unsigned long long* tags, int set, unsigned seq, GridBar* bar,
                                            unsigned long long tmo, T* s_tot, int* s_ok, int G,
-                                           unsigned long long* s_slots, uint64_t* mbar, unsigned& phase) {
+                                           unsigned long long* s_slots, uint64_t* mbar, unsigned& phase,
+                                           bool bulk) {
     if (threadIdx.x < 32) {
         T t;
-        const bool ok = tag_poll_warp_bulk<T>(tags, set, seq, G, bar, tmo, &t, s_slots, mbar, phase);
+        const bool ok = bulk ? tag_poll_warp_bulk<T>(tags, set, seq, G, bar, tmo, &t, s_slots, mbar, phase)
+                             : tag_poll_warp<T>(tags, set, seq, G, bar, tmo, &t);
         if (threadIdx.x == 0) {
             *s_tot = t;
             *s_ok = ok ? 1 : 0;
