@@ -256,6 +256,16 @@ __global__ void __launch_bounds__(512) k_mgs(T* __restrict__ V, int64_t ldv, int
 }
 
 constexpr int kMgsBlocks = 64;  // fewest blocks the on-chip MGS kernel is given
+// A block's bytes of one basis vector (at the instance's capacity) from which
+// an on-chip MGS instance polls its reductions by bulk copies
+// (tag_poll_warp_bulk) instead of loads.  Measured (fp32, 64-128 blocks,
+// 64-step GMRES runs): load polling 5 % faster at 4 KB per block
+// (n = 64,000), even at 7 KB; bulk polling 11 / 3 / 4 % faster at 16 / 32 /
+// 64 KB (n = 262,144 / 512,000 / 2,097,152); with 9 blocks per solve (16
+// right-hand sides side by side) and 29 KB per block, slower.  Instances whose
+// capacity is below the threshold are compiled without the bulk path (their
+// load poll's code unchanged); the others take it when the launch asks.
+constexpr int64_t kBulkPollBytes = 16 * 1024;
 
 // The Givens block: with giv = 1 the last block of an on-chip MGS launch takes
 // no rows.  Its first warp reads every pass's total from the same tagged slots
@@ -318,11 +328,12 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
                                                      int bulk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* zs = reinterpret_cast<T*>(smraw);
+    constexpr bool kBulk = (int64_t)R * BD * (int64_t)sizeof(T) >= kBulkPollBytes;  // and bulk: the launch's choice
     __shared__ T s_w[32];
     __shared__ T s_tot;
     __shared__ unsigned s_seq;
     __shared__ int s_ok, s_j, s_done, s_kmax;
-    __shared__ __align__(16) unsigned long long s_slots[2 * kTagMaxBlocks + 2];  // warp 0's copies of the slots
+    __shared__ __align__(16) unsigned long long s_slots[kBulk ? 2 * kTagMaxBlocks + 2 : 2];  // warp 0's copies
     __shared__ __align__(8) uint64_t s_mbar;
     unsigned phase = 0;
     if (threadIdx.x == 0) {
@@ -330,8 +341,10 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
         s_done = st->done;
         s_kmax = st->kmax;
         s_seq = *(volatile unsigned*)&st->bar.seq;  // reductions of this launch are s_seq + 1, s_seq + 2, ...
-        mbar_init(&s_mbar, 1);
-        mbar_init_fence();
+        if (kBulk) {
+            mbar_init(&s_mbar, 1);
+            mbar_init_fence();
+        }
     }
     __syncthreads();
     if (s_done) return;
@@ -377,7 +390,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
             }
         }
         const T h = tag_wait_bulk(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G, s_slots,
-                                  &s_mbar, phase, bulk != 0);
+                                  &s_mbar, phase, kBulk && bulk);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -401,7 +414,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
         for (int t = 0; t < R; ++t) vcur[t] = vnext[t];
     }
     const T h2 = tag_wait_bulk(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G, s_slots,
-                               &s_mbar, phase, bulk != 0);
+                               &s_mbar, phase, kBulk && bulk);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -425,34 +438,35 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res(T* __restrict__ V, int64_t ld
 // y = R^-1 g by column-oriented back substitution (fp64): for i = k-1 .. 0,
 // y_i = g_i / R_ii and g_t -= R_ti y_i for t < i (each g_t sees the same
 // operations in the same order as a plain column back substitution).  When
-// g and the triangle of R fit in kBackSmem bytes, the whole block first loads
-// them into shared memory with every load in flight at once, and warp 0 then
-// runs the k sequential rows from there; otherwise warp 0 alone streams the
-// columns from memory, loading column i - 1 (the first 32 kBackC rows in
-// registers) while row i divides and updates.  Launch: one block of
-// kBackThreads, kBackSmem bytes of dynamic shared memory.
-constexpr int kBackC = 8, kBackThreads = 256;
-constexpr size_t kBackSmem = 48 * 1024;
+// g and the triangle of R fit in kBackSmem bytes, the block first copies them
+// into shared memory with every load in flight at once, and warp 0 then runs
+// the k dependent rows from there.  Otherwise the whole block runs the rows:
+// thread x holds rows x + kBackThreads c of the current column in registers
+// and loads the next column's while the current row is processed, the owner
+// of row i divides, and one barrier per row hands y_i to the others.
+// Launch: one block of kBackThreads, kBackSmem bytes of dynamic shared memory.
+constexpr int kBackThreads = 512;
+constexpr size_t kBackSmem = 47 * 1024;  // with the static s_y, within the 48 KB a launch gets without opting in
+constexpr int kBackC = 8;  // rows per thread in the streamed form: k <= kBackThreads * kBackC
 __global__ void __launch_bounds__(kBackThreads) k_backsolve(const GmresState* st, const double* __restrict__ H,
                                                             const double* __restrict__ g, double* __restrict__ y,
                                                             int kmax) {
     extern __shared__ double sg[];
+    __shared__ double s_y[2];
     const int k = st->j;
-    const int lane = threadIdx.x & 31;
-    const bool staged = (size_t)k * (k + 3) / 2 * sizeof(double) <= kBackSmem;
-    if (staged) {
-        // sg[0, k): g; then column i of R (rows 0 .. i) at sg + k + i (i + 1) / 2
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int t = tid; t < k; t += blockDim.x) sg[t] = g[t];
+    if ((size_t)k * (k + 3) / 2 * sizeof(double) <= kBackSmem) {
+        // sg[0, k): g; then column i of R (rows 0 .. i) at sg + k + i (i + 1) / 2;
+        // warp w copies columns w, w + 16, ... (integer indexing only: the fp64 pipe is narrow)
         double* R = sg + k;
-        for (int t = threadIdx.x; t < k; t += blockDim.x) sg[t] = g[t];
-        const int tri = k * (k + 1) / 2;
-        for (int e = threadIdx.x; e < tri; e += blockDim.x) {
-            int i = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);  // column of packed entry e
-            while (i * (i + 1) / 2 > e) --i;
-            while ((i + 1) * (i + 2) / 2 <= e) ++i;
-            R[e] = H[(int64_t)i * (kmax + 1) + (e - i * (i + 1) / 2)];
+        for (int i = tid >> 5; i < k; i += blockDim.x >> 5) {
+            const double* hc = H + (int64_t)i * (kmax + 1);
+            double* rc = R + i * (i + 1) / 2;
+            for (int t = lane; t <= i; t += 32) rc[t] = hc[t];
         }
         __syncthreads();
-        if (threadIdx.x >= 32) return;
+        if (tid >= 32) return;
         for (int i = k - 1; i >= 0; --i) {
             const double* rc = R + i * (i + 1) / 2;
             const double yi = __ddiv_rn(sg[i], rc[i]);
@@ -462,33 +476,48 @@ __global__ void __launch_bounds__(kBackThreads) k_backsolve(const GmresState* st
         }
         return;
     }
-    if (threadIdx.x >= 32) return;
-    for (int t = lane; t < k; t += 32) sg[t] = g[t];
-    __syncwarp();
-    double nxt[kBackC], nd = 1.0;
+    // rows t = tid + kBackThreads c of column i (t <= i) in registers; g_t stays with its owner
+    double nxt[kBackC], cur[kBackC];
     auto fetch = [&](int i) {
         const double* hc = H + (int64_t)i * (kmax + 1);
 #pragma unroll
-        for (int c = 0; c < kBackC; ++c) nxt[c] = lane + 32 * c < i ? hc[lane + 32 * c] : 0.0;
-        nd = hc[i];
+        for (int c = 0; c < kBackC; ++c) {
+            const int t = tid + kBackThreads * c;
+            nxt[c] = t <= i ? hc[t] : 0.0;
+        }
     };
+    double gt[kBackC];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kBackC; ++c) {
+        const int t = tid + kBackThreads * c;
+        gt[c] = t < k ? sg[t] : 0.0;
+    }
     if (k > 0) fetch(k - 1);
     for (int i = k - 1; i >= 0; --i) {
-        double cur[kBackC];
 #pragma unroll
         for (int c = 0; c < kBackC; ++c) cur[c] = nxt[c];
-        const double di = nd;
         if (i > 0) fetch(i - 1);
-        const double yi = __ddiv_rn(sg[i], di);
-        if (lane == 0) y[i] = yi;
+        if (tid == i % kBackThreads) {
+            const int ci = i / kBackThreads;
+            double gi = 0.0, di = 1.0;
+#pragma unroll
+            for (int c = 0; c < kBackC; ++c)
+                if (c == ci) {
+                    gi = gt[c];
+                    di = cur[c];
+                }
+            const double yi = __ddiv_rn(gi, di);
+            s_y[i & 1] = yi;
+            y[i] = yi;
+        }
+        __syncthreads();
+        const double yi = s_y[i & 1];
 #pragma unroll
         for (int c = 0; c < kBackC; ++c) {
-            const int t = lane + 32 * c;
-            if (t < i) sg[t] = __dsub_rn(sg[t], __dmul_rn(cur[c], yi));
+            const int t = tid + kBackThreads * c;
+            if (t < i) gt[c] = __dsub_rn(gt[c], __dmul_rn(cur[c], yi));
         }
-        const double* hc = H + (int64_t)i * (kmax + 1);
-        for (int t = lane + 32 * kBackC; t < i; t += 32) sg[t] = __dsub_rn(sg[t], __dmul_rn(hc[t], yi));
-        __syncwarp();
     }
 }
 
@@ -571,11 +600,12 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
                                                       double* H, double* cs, double* sn, double* g,
                                                       unsigned long long* tags, unsigned long long tmo, int giv,
                                                       int bulk) {
+    constexpr bool kBulk = (int64_t)2 * P * BD * (int64_t)sizeof(float) >= kBulkPollBytes;
     __shared__ float s_w[32];
     __shared__ float s_tot;
     __shared__ unsigned s_seq;
     __shared__ int s_ok, s_j, s_done, s_kmax;
-    __shared__ __align__(16) unsigned long long s_slots[2 * kTagMaxBlocks + 2];  // warp 0's copies of the slots
+    __shared__ __align__(16) unsigned long long s_slots[kBulk ? 2 * kTagMaxBlocks + 2 : 2];  // warp 0's copies
     __shared__ __align__(8) uint64_t s_mbar;
     unsigned phase = 0;
     if (threadIdx.x == 0) {
@@ -583,8 +613,10 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
         s_done = st->done;
         s_kmax = st->kmax;
         s_seq = *(volatile unsigned*)&st->bar.seq;
-        mbar_init(&s_mbar, 1);
-        mbar_init_fence();
+        if (kBulk) {
+            mbar_init(&s_mbar, 1);
+            mbar_init_fence();
+        }
     }
     __syncthreads();
     if (s_done) return;
@@ -637,7 +669,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
             }
         }
         const float h = tag_wait_bulk(tags, (i - 1) & 1, seq0 + (unsigned)i, &st->bar, tmo, &s_tot, &s_ok, G,
-                                      s_slots, &s_mbar, phase, bulk != 0);
+                                      s_slots, &s_mbar, phase, kBulk && bulk);
         if (!s_ok) {
             if (blockIdx.x == 0 && tid == 0) {
                 st->status = BSPAI_TIMEOUT;
@@ -661,7 +693,7 @@ __global__ void __launch_bounds__(BD, 1) k_mgs_res2(float* __restrict__ V, int64
         for (int t = 0; t < P; ++t) vcur[t] = vnext[t];
     }
     const float hz = tag_wait_bulk(tags, (j + 1) & 1, seq0 + (unsigned)j + 2u, &st->bar, tmo, &s_tot, &s_ok, G,
-                                   s_slots, &s_mbar, phase, bulk != 0);
+                                   s_slots, &s_mbar, phase, kBulk && bulk);
     if (!s_ok) {
         if (blockIdx.x == 0 && tid == 0) {
             st->status = BSPAI_TIMEOUT;
@@ -713,7 +745,7 @@ struct GmresWork {
     int res_per_thread = 0;  // its rows (k_mgs_res) or row pairs (k_mgs_res2) per thread
     int Gr = 0;              // its blocks that hold rows (at most one block per SM)
     int giv = 0;             // 1: one more block applies the Givens rotations during the passes
-    int bulk = 0;            // 1: warp 0 polls the reductions by bulk copies (tag_poll_warp_bulk)
+    int bulk = 0;            // 1: an instance able to poll by bulk copies does (see kBulkPollBytes)
     size_t res_smem = 0;
     cudaStream_t s = nullptr;
 
@@ -812,13 +844,6 @@ static ResInstance pick_res(int64_t chunk) {
 // Use the on-chip MGS kernel when one block per SM can hold its rows of z on
 // chip (fp32: in registers; fp64: in shared memory, at most 200 KB) with at
 // most 32 (fp32) / 16 (fp64) rows per thread of a 512-thread block.
-// A block's bytes of one basis vector from which the MGS kernels poll their
-// reductions by bulk copies.  Measured (fp32, 64-128 blocks, 64-step GMRES
-// runs): load polling 5 % faster at 4 KB per block (n = 64,000), even at
-// 7 KB, bulk polling 11 / 3 / 4 % faster at 16 / 32 / 64 KB (n = 262,144 /
-// 512,000 / 2,097,152).
-constexpr int64_t kBulkPollBytes = 16 * 1024;
-
 static int choose_mgs(GmresWork& W) {
     W.res_fn = nullptr;
     // As few blocks as hold the rows of z on chip, but not fewer than kMgsBlocks: each
@@ -852,8 +877,10 @@ static int choose_mgs(GmresWork& W) {
     W.Gr = Gr;
     // the Givens block needs an SM of its own (one block per SM at these sizes)
     W.giv = Gr + 1 <= W.sms ? 1 : 0;
-    // poll by bulk copies where a block's loads of one basis vector would hold up a load poll
-    W.bulk = (int64_t)chunk * (int64_t)es >= kBulkPollBytes ? 1 : 0;
+    // bulk-copy polling where it was measured to pay: at least kMgsBlocks blocks (a solve
+    // confined to a few SMs, as each of several concurrent right-hand sides is, polls few
+    // slots and the copy engine's round trip loses) and kBulkPollBytes of a vector per block
+    W.bulk = Gr >= kMgsBlocks && (int64_t)chunk * (int64_t)es >= kBulkPollBytes ? 1 : 0;
     W.res_smem = smem;
     return BSPAI_OK;
 }
