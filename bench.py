@@ -37,10 +37,11 @@ METRIC = "GMRES-IR solves/s at fwd err<=1e-10; bucketed M·v GB/s vs GB300 HBM p
 UNIT = "solves/s"
 FE_TARGET = 1e-10
 # DRAM bytes over algorithmic bytes of the MGS kernel (k_mgs_res2<16, 512>, z in registers, 128
-# blocks) from one ncu capture of an Arnoldi step (j = 20, 128^3): dram read + write 188.20 MB against
-# (j+1) n 4 + n 4 = 184.55 MB.  Both grow linearly in j, so the per-launch traffic of the timed
-# launches is this ratio times their algorithmic bytes.
-MGS_TRAFFIC_RATIO = 188.20 / 184.55
+# blocks, reductions polled by bulk copies) from one ncu capture of an Arnoldi step (j = 20, 128^3,
+# kmax 64): dram read + write 184.62 + 4.02 = 188.64 MB against (j+1) n 4 + n 4 = 184.55 MB.  Both grow
+# linearly in j, so the per-launch traffic of the timed launches is this ratio times their
+# algorithmic bytes.
+MGS_TRAFFIC_RATIO = 188.64 / 184.55
 
 
 def parse():
