@@ -177,7 +177,8 @@ __device__ __forceinline__ bool tag_poll_warp_bulk(const unsigned long long* tag
             mbar_arrive_expect(mbar, bytes);
             bulk_g2s(s_slots, tags + a0, bytes, mbar);
         }
-        const bool got = mbar_wait_bounded(mbar, phase & 1u, tmo);
+        // one decision for the warp (a lane's own wait could end just past the limit)
+        const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(mbar, phase & 1u, tmo));
         phase++;
         if (!got) {
             mbar_wait_bounded(mbar, (phase - 1) & 1u, tmo);
