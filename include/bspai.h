@@ -376,13 +376,17 @@ int bspai_gmres(bspai_A_h A, bspai_BM_h BM, const double* r, bspai_prec_t u_g, b
  * memory), 1 = k_mgs_res (the new vector held on chip; per_thread rows per
  * thread), 2 = k_mgs_res2 (fp32, the new vector in registers; per_thread
  * pairs of adjacent rows per thread); block_threads and blocks give the
- * launch.  A query only: nothing is launched or allocated.  n < 1:
+ * launch; poll_bulk = 1 when the on-chip kernel's warp 0 reads the grid
+ * reductions' slots by bulk copies into shared memory instead of by loads
+ * (at least 16 KB of each basis vector per block and at least 64 blocks),
+ * 0 otherwise.  A query only: nothing is launched or allocated.  n < 1:
  * BSPAI_ERR_INVALID; another u_g: BSPAI_ERR_UNSUPPORTED. */
 typedef struct {
     int32_t kernel;
     int32_t per_thread;
     int32_t block_threads;
     int32_t blocks;
+    int32_t poll_bulk;
 } bspai_gmres_plan_t;
 int bspai_gmres_plan(int32_t n, bspai_prec_t u_g, int32_t max_blocks, bspai_gmres_plan_t* out);
 

@@ -137,7 +137,7 @@ _sig("bspai_apply_cw", _i, [_vp, _d, C.POINTER(C.c_int32), C.c_int32, _vp, _i, _
 
 class GmresPlan(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("per_thread", C.c_int32), ("block_threads", C.c_int32),
-                ("blocks", C.c_int32)]
+                ("blocks", C.c_int32), ("poll_bulk", C.c_int32)]
 
 
 _sig("bspai_gmres_plan", _i, [C.c_int32, _i, C.c_int32, C.POINTER(GmresPlan)])
@@ -476,7 +476,7 @@ def gmres_plan(n: int, u_g="fp32", max_blocks=0) -> dict:
     p = GmresPlan()
     _check(_lib.bspai_gmres_plan(n, PREC[u_g], max_blocks, C.byref(p)))
     return dict(kernel=MGS_KERNELS[p.kernel], per_thread=p.per_thread, block_threads=p.block_threads,
-                blocks=p.blocks)
+                blocks=p.blocks, poll="bulk" if p.poll_bulk else "loads")
 
 
 def gmres(Ah: AHandle, BM: BMHandle, r, d, u_g="fp32", u_p="fp32", o: Opts | None = None, stream=None) -> dict:

@@ -1388,6 +1388,7 @@ int bspai_gmres_plan(int32_t n, bspai_prec_t u_g, int32_t max_blocks, bspai_gmre
         out->per_thread = W.res_per_thread;
         out->block_threads = W.res_bd;
         out->blocks = W.Gr;
+        out->poll_bulk = W.bulk;
         return BSPAI_OK;
     }
     int occ = 0, occ2 = 0;

@@ -7,7 +7,8 @@ holds on chip): a sweep of 3D convection-diffusion grids reaches every one of
 them, and each case asserts through bspai_gmres_plan which one ran.  The
 largest case is the benchmark's own 128^3 workload with its bucketing
 (eps = 2^-10, buckets {fp64, fp32, fp16, e4m3}), where k_mgs_res2 with 16 row
-pairs per thread of a 512-thread block runs on 128 blocks.
+pairs per thread of a 512-thread block runs on 128 blocks, its reductions
+polled by bulk copies.
 
 Both sides get the oracle's M (fp64 SPAI rounded to u_f = fp32), bucketed by
 each side (bit-exact, checked elsewhere), and the same residual r of
@@ -30,20 +31,21 @@ pytestmark = pytest.mark.gpu
 BENCH_EPS = 2.0 ** -10
 TOL = {"fp32": 1e-4, "fp64": 1e-10}
 
-# (grid, u_g, kernel, rows or row pairs per thread, block threads); 152 SMs
+# (grid, u_g, kernel, rows or row pairs per thread, block threads, how warp 0 reads the
+# reduction slots: by loads, or by bulk copies from 16 KB of a vector per block); 152 SMs
 SWEEP = [
-    (40, "fp32", "k_mgs_res", 1, 1024),     # n = 64,000: a chunk of <= 1024 rows per block
-    (48, "fp32", "k_mgs_res2", 1, 1024),    # n = 110,592
-    (64, "fp32", "k_mgs_res2", 2, 1024),    # n = 262,144
-    (80, "fp32", "k_mgs_res2", 4, 1024),    # n = 512,000
-    (88, "fp32", "k_mgs_res2", 12, 512),    # n = 681,472
-    (94, "fp32", "k_mgs_res2", 14, 512),    # n = 830,584
-    (100, "fp32", "k_mgs_res2", 16, 512),   # n = 1,000,000
-    (40, "fp64", "k_mgs_res", 1, 1024),
-    (48, "fp64", "k_mgs_res", 2, 1024),
-    (64, "fp64", "k_mgs_res", 4, 1024),
-    (80, "fp64", "k_mgs_res", 8, 1024),
-    (110, "fp64", "k_mgs", 0, 512),         # n = 1,331,000: beyond on-chip rows, the streaming kernel
+    (40, "fp32", "k_mgs_res", 1, 1024, "loads"),     # n = 64,000: a chunk of <= 1024 rows per block
+    (48, "fp32", "k_mgs_res2", 1, 1024, "loads"),    # n = 110,592
+    (64, "fp32", "k_mgs_res2", 2, 1024, "bulk"),     # n = 262,144
+    (80, "fp32", "k_mgs_res2", 4, 1024, "bulk"),     # n = 512,000
+    (88, "fp32", "k_mgs_res2", 12, 512, "bulk"),     # n = 681,472
+    (94, "fp32", "k_mgs_res2", 14, 512, "bulk"),     # n = 830,584
+    (100, "fp32", "k_mgs_res2", 16, 512, "bulk"),    # n = 1,000,000
+    (40, "fp64", "k_mgs_res", 1, 1024, "loads"),
+    (48, "fp64", "k_mgs_res", 2, 1024, "loads"),     # 13.8 KB of a vector per block
+    (64, "fp64", "k_mgs_res", 4, 1024, "bulk"),
+    (80, "fp64", "k_mgs_res", 8, 1024, "bulk"),
+    (110, "fp64", "k_mgs", 0, 512, "loads"),         # n = 1,331,000: beyond on-chip rows, the streaming kernel
 ]
 
 
@@ -85,15 +87,16 @@ def _compare(B, wl, bk, S, r, ug, k):
     return err
 
 
-@pytest.mark.parametrize("grid,ug,kernel,per_thread,bd", SWEEP,
-                         ids=[f"{g}^3-{u}-{k}<{p},{b}>" for g, u, k, p, b in SWEEP])
-def test_mgs_instance_matches_oracle(B, grid, ug, kernel, per_thread, bd):
+@pytest.mark.parametrize("grid,ug,kernel,per_thread,bd,poll", SWEEP,
+                         ids=[f"{g}^3-{u}-{k}<{p},{b}>-{q}" for g, u, k, p, b, q in SWEEP])
+def test_mgs_instance_matches_oracle(B, grid, ug, kernel, per_thread, bd, poll):
     n = grid ** 3
     plan = B.gmres_plan(n, ug)
-    assert (plan["kernel"], plan["per_thread"], plan["block_threads"]) == (kernel, per_thread, bd), plan
+    assert (plan["kernel"], plan["per_thread"], plan["block_threads"], plan["poll"]) == \
+        (kernel, per_thread, bd, poll), plan
     wl, bk, S, r = _case(B, grid, 2.0 ** -16, ["fp64", "fp32", "fp16", "e4m3"])
     err = _compare(B, wl, bk, S, r, ug, 16)
-    print(f"{grid}^3 {ug} {kernel}<{per_thread},{bd}> x {plan['blocks']}: max rel diff {err:.2e}")
+    print(f"{grid}^3 {ug} {kernel}<{per_thread},{bd}> x {plan['blocks']} ({poll}): max rel diff {err:.2e}")
 
 
 def test_mgs_bench_instance_128(B):
@@ -101,7 +104,7 @@ def test_mgs_bench_instance_128(B):
     k_mgs_res2 with 16 row pairs per thread, 512 threads, 128 blocks --
     24 Arnoldi steps against the oracle."""
     plan = B.gmres_plan(128 ** 3, "fp32")
-    assert plan == dict(kernel="k_mgs_res2", per_thread=16, block_threads=512, blocks=128), plan
+    assert plan == dict(kernel="k_mgs_res2", per_thread=16, block_threads=512, blocks=128, poll="bulk"), plan
     wl, bk, S, r = _case(B, 128, BENCH_EPS, ["fp64", "fp32", "fp16", "e4m3"])
     assert bk["info"]["nnz_k"][2] > 0 and bk["info"]["nnz_k"][3] > 0  # the fp16 + e4m3 form of M w
     err = _compare(B, wl, bk, S, r, "fp32", 24)
